@@ -1,0 +1,283 @@
+"""Python binding of the GB300 interpolative-decomposition library (libgbid.so).
+
+Argument marshalling only: every step of the decomposition runs in the CUDA
+kernels behind the C ABI declared in include/gbid.h. PyTorch supplies device
+memory (outputs and workspace) and the current stream. There is no CPU
+fallback: if the library is not built, or a tensor is not on a CUDA device,
+the call raises.
+
+Method (Advani & O'Hagan, arXiv 2105.07076): rank-k interpolative
+decomposition A ~= A[:, J] Z from a column-pivoted Householder QR stopped
+after k pivots (Sec. 2.1, Sec. 4.1), with Z P = [I  R11^{-1} R12]; for m > n
+the method runs on A^T and returns a row ID A ~= Z^T A[J, :] (Sec. 2 footnote).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libgbid.so")
+
+ID_OK = 0
+ID_RANK_DEFICIENT = 1
+ID_EINVAL = -1
+ID_ENOMEM = -2
+ID_ECUDA = -3
+ID_ENONFINITE = -4
+ID_ETIMEOUT = -5
+STATUS_NAMES = {0: "ID_OK", 1: "ID_RANK_DEFICIENT", -1: "ID_EINVAL", -2: "ID_ENOMEM", -3: "ID_ECUDA",
+                -4: "ID_ENONFINITE", -5: "ID_ETIMEOUT"}
+
+ID_F64 = 0
+ID_F32 = 1
+_DTYPES = {torch.float64: ID_F64, torch.float32: ID_F32}
+
+
+class IdOpts(ctypes.Structure):
+    _fields_ = [("nb", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+
+
+class IdInfo(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("rank", ctypes.c_int32), ("transposed", ctypes.c_int32),
+                ("n_recompute", ctypes.c_int32), ("n_gt2", ctypes.c_int64), ("max_abs_z", ctypes.c_double),
+                ("r00", ctypes.c_double), ("nb", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+
+    def as_dict(self):
+        return {"status": self.status, "status_name": STATUS_NAMES.get(self.status, str(self.status)),
+                "rank": self.rank, "transposed": bool(self.transposed), "n_recompute": self.n_recompute,
+                "n_gt2": self.n_gt2, "max_abs_z": self.max_abs_z, "r00": self.r00, "nb": self.nb}
+
+
+# Return codes that mean the call itself failed; device-detected conditions
+# (ID_RANK_DEFICIENT, ID_ENONFINITE, ID_ETIMEOUT) come back in the info dict.
+_CALL_ERRORS = (ID_EINVAL, ID_ENOMEM, ID_ECUDA)
+
+
+class IdError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}")
+        self.status = status
+
+
+_lib = None
+
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_SIG = {
+    "id_workspace_size": (ctypes.c_size_t, [ctypes.c_int, _I64, _I64, _I64, _P]),
+    "id_cpqr_workspace_size": (ctypes.c_size_t, [ctypes.c_int, _I64, _I64, _I64, _I64, _P]),
+    "id_decompose_host_workspace_size": (ctypes.c_size_t, [ctypes.c_int, _I64, _I64, _I64, _P]),
+    "id_decompose": (ctypes.c_int, [_P, ctypes.c_int, _I64, _I64, _I64, _I64, _P, _P, _P, _I64, _P,
+                                    ctypes.c_size_t, _P, _P]),
+    "id_decompose_host": (ctypes.c_int, [_P, ctypes.c_int, _I64, _I64, _I64, _I64, _P, _P, _P, _I64, _P,
+                                         ctypes.c_size_t, _P, _P]),
+    "id_cpqr": (ctypes.c_int, [_P, ctypes.c_int, _I64, _I64, _I64, _I64, _P, _P, _P, _P, ctypes.c_size_t, _P, _P]),
+    "id_solve": (ctypes.c_int, [_P, ctypes.c_int, _I64, _I64, _I64, _P, _I64, _P]),
+    "id_info_read": (ctypes.c_int, [_P, _P, _P]),
+    "id_launch_count": (ctypes.c_int64, [ctypes.c_int, _I64, _I64, _I64, _P]),
+    "id_trace_enable": (ctypes.c_int, [ctypes.c_int]),
+    "id_trace_read": (ctypes.c_int, [_P, _P, ctypes.c_int]),
+    "id_version": (ctypes.c_char_p, []),
+}
+
+TRACE_KINDS = ("cpqr", "solve", "sketch", "copy_in", "scatter")
+
+
+def lib():
+    """The loaded libgbid.so (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                               "(there is no CPU fallback)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIG.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return list(_SIG)
+
+
+def _opts(nb: int):
+    o = IdOpts()
+    o.nb = int(nb)
+    return o
+
+
+def _stream(dev) -> int:
+    return torch.cuda.current_stream(dev).cuda_stream
+
+
+def _check_cuda_matrix(A: torch.Tensor, name: str):
+    if not isinstance(A, torch.Tensor) or not A.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor (no CPU fallback)")
+    if A.dtype not in _DTYPES:
+        raise ValueError(f"{name} must be float32 or float64")
+    if A.dim() != 2 or A.stride(1) != 1:
+        raise ValueError(f"{name} must be 2-D with unit column stride (row-major)")
+
+
+def workspace_size(dtype: torch.dtype, m: int, n: int, k: int, nb: int = 0) -> int:
+    o = _opts(nb)
+    return int(lib().id_workspace_size(_DTYPES[dtype], m, n, k, ctypes.byref(o)))
+
+
+@dataclass
+class Workspace:
+    """Device scratch for id_decompose (reusable across calls of the same size)."""
+    buf: torch.Tensor
+
+    @staticmethod
+    def for_problem(dtype, m, n, k, nb=0, device="cuda", host_io=False):
+        o = _opts(nb)
+        if host_io:
+            nbytes = int(lib().id_decompose_host_workspace_size(_DTYPES[dtype], m, n, k, ctypes.byref(o)))
+        else:
+            nbytes = int(lib().id_workspace_size(_DTYPES[dtype], m, n, k, ctypes.byref(o)))
+        if nbytes == 0:
+            raise IdError(ID_EINVAL, "workspace size")
+        return Workspace(torch.empty(nbytes, dtype=torch.uint8, device=device))
+
+
+def id_decompose(A: torch.Tensor, k: int, *, nb: int = 0, workspace: Workspace | None = None,
+                 out: tuple | None = None, sync: bool = True):
+    """Rank-k ID of a CUDA matrix A (m x n, row-major, float32/float64).
+
+    Returns (J, Z, info): J int32 (k,), Z (k, max(m,n)) of A's dtype, info a
+    dict (when sync) or None. m <= n: A ~= A[:, J] @ Z; m > n: A ~= Z.T @ A[J, :].
+    With sync=False nothing waits for the GPU (usable inside CUDA-graph capture);
+    read the status later with ``read_info(workspace)``.
+    """
+    _check_cuda_matrix(A, "A")
+    m, n = A.shape
+    nz = max(m, n)
+    dev = A.device
+    if workspace is None:
+        workspace = Workspace.for_problem(A.dtype, m, n, k, nb, dev)
+    if out is None:
+        J = torch.empty(k, dtype=torch.int32, device=dev)
+        Z = torch.empty(k, nz, dtype=A.dtype, device=dev)
+    else:
+        J, Z = out
+    o = _opts(nb)
+    info = IdInfo()
+    with torch.cuda.device(dev):
+        rc = lib().id_decompose(A.data_ptr(), _DTYPES[A.dtype], m, n, A.stride(0), k, ctypes.byref(o),
+                                J.data_ptr(), Z.data_ptr(), Z.stride(0), workspace.buf.data_ptr(),
+                                workspace.buf.numel(), ctypes.byref(info) if sync else None, _stream(dev))
+    if rc in _CALL_ERRORS:
+        raise IdError(rc, "id_decompose")
+    return J, Z, (info.as_dict() if sync else None)
+
+
+def read_info(workspace: Workspace) -> dict:
+    info = IdInfo()
+    dev = workspace.buf.device
+    with torch.cuda.device(dev):
+        rc = lib().id_info_read(workspace.buf.data_ptr(), ctypes.byref(info), _stream(dev))
+    if rc in _CALL_ERRORS:
+        raise IdError(rc, "id_info_read")
+    return info.as_dict()
+
+
+def id_decompose_host(A: torch.Tensor, k: int, *, nb: int = 0, workspace: Workspace | None = None,
+                      out: tuple | None = None, device="cuda"):
+    """The same ID for a HOST matrix (ideally pinned): copies in, decomposes, copies J, Z back, waits."""
+    if A.is_cuda or A.dtype not in _DTYPES or A.dim() != 2 or A.stride(1) != 1:
+        raise ValueError("A must be a 2-D row-major float32/float64 CPU tensor")
+    m, n = A.shape
+    nz = max(m, n)
+    if workspace is None:
+        workspace = Workspace.for_problem(A.dtype, m, n, k, nb, device, host_io=True)
+    if out is None:
+        pin = A.is_pinned()
+        J = torch.empty(k, dtype=torch.int32, pin_memory=pin)
+        Z = torch.empty(k, nz, dtype=A.dtype, pin_memory=pin)
+    else:
+        J, Z = out
+    o = _opts(nb)
+    info = IdInfo()
+    dev = workspace.buf.device
+    with torch.cuda.device(dev):
+        rc = lib().id_decompose_host(A.data_ptr(), _DTYPES[A.dtype], m, n, A.stride(0), k, ctypes.byref(o),
+                                     J.data_ptr(), Z.data_ptr(), Z.stride(0), workspace.buf.data_ptr(),
+                                     workspace.buf.numel(), ctypes.byref(info), _stream(dev))
+    if rc in _CALL_ERRORS:
+        raise IdError(rc, "id_decompose_host")
+    return J, Z, info.as_dict()
+
+
+def id_cpqr(Xcm: torch.Tensor, m: int, k: int, *, nb: int = 0, workspace: torch.Tensor | None = None):
+    """k-step CPQR in place of a column-major m x n matrix.
+
+    ``Xcm`` is a CUDA tensor of shape (n, ldx): row l holds column l of X (so
+    X = Xcm[:, :m].T), ldx >= m a multiple of 8. Returns (perm, tau, info).
+    """
+    if not Xcm.is_cuda or Xcm.dtype not in _DTYPES or Xcm.dim() != 2 or Xcm.stride(1) != 1:
+        raise ValueError("Xcm must be a 2-D contiguous CUDA float32/float64 tensor")
+    n, ldx = Xcm.shape[0], Xcm.stride(0)
+    dev = Xcm.device
+    o = _opts(nb)
+    if workspace is None:
+        nbytes = int(lib().id_cpqr_workspace_size(_DTYPES[Xcm.dtype], m, n, ldx, k, ctypes.byref(o)))
+        if nbytes == 0:
+            raise IdError(ID_EINVAL, "id_cpqr_workspace_size")
+        workspace = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    perm = torch.empty(n, dtype=torch.int32, device=dev)
+    tau = torch.empty(k, dtype=torch.float64, device=dev)
+    info = IdInfo()
+    with torch.cuda.device(dev):
+        rc = lib().id_cpqr(Xcm.data_ptr(), _DTYPES[Xcm.dtype], m, n, ldx, k, ctypes.byref(o), perm.data_ptr(),
+                           tau.data_ptr(), workspace.data_ptr(), workspace.numel(), ctypes.byref(info),
+                           _stream(dev))
+    if rc in _CALL_ERRORS:
+        raise IdError(rc, "id_cpqr")
+    return perm, tau, info.as_dict()
+
+
+def id_solve(Xcm: torch.Tensor, k: int) -> torch.Tensor:
+    """T = R11^{-1} R12 (FP64, k x (n-k)) from a matrix factored by ``id_cpqr``."""
+    if not Xcm.is_cuda or Xcm.dtype not in _DTYPES or Xcm.dim() != 2 or Xcm.stride(1) != 1:
+        raise ValueError("Xcm must be a 2-D contiguous CUDA float32/float64 tensor")
+    n, ldx = Xcm.shape[0], Xcm.stride(0)
+    dev = Xcm.device
+    T = torch.empty(k, max(n - k, 1), dtype=torch.float64, device=dev)
+    with torch.cuda.device(dev):
+        rc = lib().id_solve(Xcm.data_ptr(), _DTYPES[Xcm.dtype], n, ldx, k, T.data_ptr(), T.stride(0), _stream(dev))
+    if rc < 0:
+        raise IdError(rc, "id_solve")
+    return T[:, : n - k]
+
+
+def launch_count(dtype: torch.dtype, m: int, n: int, k: int, nb: int = 0) -> int:
+    """Kernel launches one id_decompose call enqueues (as the library counts them)."""
+    o = _opts(nb)
+    return int(lib().id_launch_count(_DTYPES[dtype], m, n, k, ctypes.byref(o)))
+
+
+def trace_enable(capacity: int = 4096) -> None:
+    if lib().id_trace_enable(int(capacity)) != ID_OK:
+        raise IdError(ID_ECUDA, "id_trace_enable")
+
+
+def trace_read() -> dict:
+    """{kind: (total_ms, launches)} for the launches traced since the last read."""
+    nk = len(TRACE_KINDS)
+    ms = (ctypes.c_double * nk)()
+    cnt = (ctypes.c_int64 * nk)()
+    if lib().id_trace_read(ms, cnt, nk) < 0:
+        raise IdError(ID_ECUDA, "id_trace_read")
+    return {name: (ms[i], cnt[i]) for i, name in enumerate(TRACE_KINDS)}
+
+
+def version() -> str:
+    return lib().id_version().decode()

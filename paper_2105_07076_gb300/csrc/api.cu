@@ -1,0 +1,286 @@
+// C ABI of the ID library: argument checks, workspace layout, launch order.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include "common.cuh"
+#include "cpqr.cuh"
+#include "gbid.h"
+#include "trace.cuh"
+
+namespace gbid {
+namespace {
+
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+// Panel width actually used. Left-looking (nb = k) unless the per-step
+// corrections through all k stored reflectors, about 2 k (m + n) operations
+// per step, would outgrow what a compact-WY update every 32 steps costs,
+// about m n per step (one extra pass over the trailing matrix).
+int pick_nb(int m, int n, int k, const id_opts* opts) {
+    int nb = (opts && opts->nb > 0) ? opts->nb : 0;
+    if (nb == 0) {
+        const double lazy = 2.0 * k * ((double)m + (double)n);
+        const double wy = (double)m * (double)n;
+        nb = lazy <= wy ? k : 32;
+    }
+    if (nb > k) nb = k;
+    if (nb > kMaxPanel) nb = kMaxPanel;
+    if (nb < 1) nb = 1;
+    return nb;
+}
+
+struct Layout {
+    size_t info, state, W, F, xbuf, ssq, sync, vn1, vn2, perm, tau, part3, aux, T, total;
+    int m, n, ldw, nb, ldf;
+};
+
+// m, n: working (X) dimensions, m <= n. with_w: reserve W/perm/tau (id_decompose)
+// or take them from the caller (id_cpqr). with_t: reserve the FP64 T buffer.
+Layout make_layout(id_dtype dt, int m, int n, int k, const id_opts* opts, bool with_w, bool with_t,
+                   int ldw = 0) {
+    Layout L{};
+    const size_t s = dt == ID_F64 ? 8 : 4;
+    L.m = m;
+    L.n = n;
+    L.ldw = ldw > 0 ? ldw : (int)round_up(m, 8);
+    L.nb = pick_nb(m, n, k, opts);
+    L.ldf = (int)round_up(L.nb, 4);
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes); return o; };
+    L.info = take(sizeof(DevInfo));
+    L.state = take(sizeof(State));
+    L.W = with_w ? take(s * (size_t)L.ldw * n) : 0;
+    L.F = take(s * (size_t)L.ldf * n);
+    L.xbuf = take(s * (size_t)L.ldw);
+    L.ssq = take(8 * (size_t)kMaxParts);
+    L.sync = take(sync_bytes(k));
+    L.vn1 = take(8 * (size_t)n);
+    L.vn2 = take(8 * (size_t)n);
+    L.perm = with_w ? take(4 * (size_t)n) : 0;
+    L.tau = with_w ? take(8 * (size_t)k) : 0;
+    L.part3 = take(sizeof(ArgMax) * kMaxParts);
+    L.aux = take(s * kMaxPanel);
+    L.T = with_t ? take(8 * (size_t)k * (n - k > 0 ? n - k : 1)) : 0;
+    L.total = off;
+    return L;
+}
+
+CpqrPlan make_plan(const Layout& L, char* base, void* W, int32_t* perm, double* tau, int k, int64_t mu, int64_t nu) {
+    CpqrPlan P{};
+    P.m = L.m;
+    P.n = L.n;
+    P.ldw = L.ldw;
+    P.k = k;
+    P.nb = L.nb;
+    P.m_user = mu;
+    P.n_user = nu;
+    P.W = W ? W : base + L.W;
+    P.F = base + L.F;
+    P.ldf = L.ldf;
+    P.xbuf = base + L.xbuf;
+    P.ssq = reinterpret_cast<double*>(base + L.ssq);
+    P.sync = base + L.sync;
+    P.vn1 = reinterpret_cast<double*>(base + L.vn1);
+    P.vn2 = reinterpret_cast<double*>(base + L.vn2);
+    P.perm = perm ? perm : reinterpret_cast<int*>(base + L.perm);
+    P.tau = tau ? tau : reinterpret_cast<double*>(base + L.tau);
+    P.part3 = reinterpret_cast<ArgMax*>(base + L.part3);
+    P.aux = base + L.aux;
+    P.st = reinterpret_cast<State*>(base + L.state);
+    return P;
+}
+
+bool sizes_ok(int64_t m, int64_t n, int64_t k) {
+    if (m < 1 || n < 1 || k < 1) return false;
+    const int64_t mn = m < n ? m : n, mx = m < n ? n : m;
+    if (k > mn) return false;
+    // k indexes a grid dimension of the Z scatter and sizes the solve's tile
+    if (k > 16384) return false;
+    // the pivot-step cluster keeps a 1/8 share of a column in shared memory
+    // and one GEMV CTA owns at most 256 of 2048 * 256 trailing columns
+    if (mx > (int64_t)kMaxParts * 256 || mn > 65536) return false;
+    return true;
+}
+
+int configure_once() {
+    static int done = 0;   // per process; attributes apply to every device the kernels run on
+    if (done) return 0;
+    if (cpqr_configure<double>() != cudaSuccess) return -1;
+    if (cpqr_configure<float>() != cudaSuccess) return -1;
+    if (solve_configure() != cudaSuccess) return -1;
+    done = 1;
+    return 0;
+}
+
+int read_info(const void* work, id_info* info, cudaStream_t s) {
+    const DevInfo* d = reinterpret_cast<const DevInfo*>(work);
+    if (cudaMemcpyAsync(info, &d->info, sizeof(id_info), cudaMemcpyDeviceToHost, s) != cudaSuccess) return ID_ECUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return ID_ECUDA;
+    return info->status;
+}
+
+template <typename T>
+int decompose_impl(const void* A, int64_t m, int64_t n, int64_t lda, int64_t k, const id_opts* opts, int32_t* J,
+                   void* Z, int64_t ldz, void* work, size_t work_bytes, id_info* info, cudaStream_t s) {
+    const int trans = m > n ? 1 : 0;
+    const int mx = (int)(trans ? n : m), nx = (int)(trans ? m : n);
+    const id_dtype dt = sizeof(T) == 8 ? ID_F64 : ID_F32;
+    const Layout L = make_layout(dt, mx, nx, (int)k, opts, true, true);
+    if (work_bytes < L.total) return ID_ENOMEM;
+    if (configure_once()) return ID_ECUDA;
+    char* base = static_cast<char*>(work);
+    CpqrPlan P = make_plan(L, base, nullptr, nullptr, nullptr, (int)k, m, n);
+    DevInfo* dinfo = reinterpret_cast<DevInfo*>(base + L.info);
+    if (cudaMemsetAsync(dinfo, 0, sizeof(DevInfo), s) != cudaSuccess) return ID_ECUDA;
+    if (copy_in<T>(A, lda, trans, P, s) != cudaSuccess) return ID_ECUDA;
+    if (cpqr_run<T>(P, s) != cudaSuccess) return ID_ECUDA;
+    double* Tm = reinterpret_cast<double*>(base + L.T);
+    const int ldt = nx - (int)k > 0 ? nx - (int)k : 1;
+    if (solve_run<T>(P.W, P.ldw, (int)k, nx, Tm, ldt, s) != cudaSuccess) return ID_ECUDA;
+    if (scatter_z<T>(P.perm, Tm, ldt, (int)k, nx, Z, ldz, J, dinfo, s) != cudaSuccess) return ID_ECUDA;
+    if (finalize_info(P.st, dinfo, (int)k, trans, P.nb, s) != cudaSuccess) return ID_ECUDA;
+    if (info) return read_info(work, info, s);
+    return ID_OK;
+}
+
+template <typename T>
+int cpqr_impl(void* X, int64_t m, int64_t n, int64_t ldx, int64_t k, const id_opts* opts, int32_t* perm,
+              double* tau, void* work, size_t work_bytes, id_info* info, cudaStream_t s) {
+    const id_dtype dt = sizeof(T) == 8 ? ID_F64 : ID_F32;
+    const Layout L = make_layout(dt, (int)m, (int)n, (int)k, opts, false, false, (int)ldx);
+    if (work_bytes < L.total) return ID_ENOMEM;
+    if (configure_once()) return ID_ECUDA;
+    char* base = static_cast<char*>(work);
+    CpqrPlan P = make_plan(L, base, X, perm, tau, (int)k, m, n);
+    DevInfo* dinfo = reinterpret_cast<DevInfo*>(base + L.info);
+    if (cudaMemsetAsync(dinfo, 0, sizeof(DevInfo), s) != cudaSuccess) return ID_ECUDA;
+    if (zero_pad<T>(P, s) != cudaSuccess) return ID_ECUDA;
+    if (cpqr_run<T>(P, s) != cudaSuccess) return ID_ECUDA;
+    if (finalize_info(P.st, dinfo, (int)k, 0, P.nb, s) != cudaSuccess) return ID_ECUDA;
+    if (info) return read_info(work, info, s);
+    return ID_OK;
+}
+
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+}  // namespace
+}  // namespace gbid
+
+using namespace gbid;
+
+extern "C" {
+
+size_t id_cpqr_workspace_size(id_dtype dtype, int64_t m, int64_t n, int64_t ldx, int64_t k, const id_opts* opts) {
+    if ((dtype != ID_F64 && dtype != ID_F32) || !sizes_ok(m, n, k) || m > n || ldx < m || ldx % 8 != 0) return 0;
+    return make_layout(dtype, (int)m, (int)n, (int)k, opts, false, false, (int)ldx).total;
+}
+
+size_t id_workspace_size(id_dtype dtype, int64_t m, int64_t n, int64_t k, const id_opts* opts) {
+    if ((dtype != ID_F64 && dtype != ID_F32) || !sizes_ok(m, n, k)) return 0;
+    const int mx = (int)(m > n ? n : m), nx = (int)(m > n ? m : n);
+    return make_layout(dtype, mx, nx, (int)k, opts, true, true).total;
+}
+
+int id_decompose(const void* A, id_dtype dtype, int64_t m, int64_t n, int64_t lda, int64_t k, const id_opts* opts,
+                 int32_t* J, void* Z, int64_t ldz, void* work, size_t work_bytes, id_info* info, void* stream) {
+    if (!A || !J || !Z || !work) return ID_EINVAL;
+    if (dtype != ID_F64 && dtype != ID_F32) return ID_EINVAL;
+    if (!sizes_ok(m, n, k)) return ID_EINVAL;
+    const int64_t nz = m > n ? m : n;
+    if (lda < n || ldz < nz) return ID_EINVAL;
+    if (!aligned(work, 256)) return ID_EINVAL;
+    if (opts && opts->nb < 0) return ID_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (dtype == ID_F64) return decompose_impl<double>(A, m, n, lda, k, opts, J, Z, ldz, work, work_bytes, info, s);
+    return decompose_impl<float>(A, m, n, lda, k, opts, J, Z, ldz, work, work_bytes, info, s);
+}
+
+size_t id_decompose_host_workspace_size(id_dtype dtype, int64_t m, int64_t n, int64_t k, const id_opts* opts) {
+    const size_t base = id_workspace_size(dtype, m, n, k, opts);
+    if (!base) return 0;
+    const size_t s = dtype == ID_F64 ? 8 : 4;
+    const int64_t nz = m > n ? m : n;
+    return base + align_up(s * (size_t)m * n) + align_up(4 * (size_t)k) + align_up(s * (size_t)k * nz);
+}
+
+int id_decompose_host(const void* A_host, id_dtype dtype, int64_t m, int64_t n, int64_t lda, int64_t k,
+                      const id_opts* opts, int32_t* J_host, void* Z_host, int64_t ldz, void* work, size_t work_bytes,
+                      id_info* info, void* stream) {
+    if (!A_host || !J_host || !Z_host || !work) return ID_EINVAL;
+    if (dtype != ID_F64 && dtype != ID_F32) return ID_EINVAL;
+    if (!sizes_ok(m, n, k)) return ID_EINVAL;
+    const int64_t nz = m > n ? m : n;
+    if (lda < n || ldz < nz) return ID_EINVAL;
+    if (!aligned(work, 256)) return ID_EINVAL;
+    const size_t need = id_decompose_host_workspace_size(dtype, m, n, k, opts);
+    if (work_bytes < need) return ID_ENOMEM;
+    const size_t s = dtype == ID_F64 ? 8 : 4;
+    const size_t base = id_workspace_size(dtype, m, n, k, opts);
+    char* w = static_cast<char*>(work);
+    char* dA = w + base;
+    int32_t* dJ = reinterpret_cast<int32_t*>(dA + align_up(s * (size_t)m * n));
+    char* dZ = reinterpret_cast<char*>(dJ) + align_up(4 * (size_t)k);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (cudaMemcpy2DAsync(dA, s * n, A_host, s * lda, s * n, m, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return ID_ECUDA;
+    const int rc = id_decompose(dA, dtype, m, n, n, k, opts, dJ, dZ, nz, work, base, nullptr, stream);
+    if (rc != ID_OK) return rc;
+    if (cudaMemcpyAsync(J_host, dJ, 4 * (size_t)k, cudaMemcpyDeviceToHost, st) != cudaSuccess) return ID_ECUDA;
+    if (cudaMemcpy2DAsync(Z_host, s * ldz, dZ, s * nz, s * nz, k, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return ID_ECUDA;
+    id_info tmp;
+    id_info* out = info ? info : &tmp;
+    return read_info(work, out, st);
+}
+
+int id_cpqr(void* X, id_dtype dtype, int64_t m, int64_t n, int64_t ldx, int64_t k, const id_opts* opts,
+            int32_t* perm, double* tau, void* work, size_t work_bytes, id_info* info, void* stream) {
+    if (!X || !perm || !tau || !work) return ID_EINVAL;
+    if (dtype != ID_F64 && dtype != ID_F32) return ID_EINVAL;
+    if (!sizes_ok(m, n, k) || m > n) return ID_EINVAL;
+    if (ldx < m || ldx % 8 != 0) return ID_EINVAL;
+    if (!aligned(work, 256) || !aligned(X, 16)) return ID_EINVAL;
+    if (opts && opts->nb < 0) return ID_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (dtype == ID_F64) return cpqr_impl<double>(X, m, n, ldx, k, opts, perm, tau, work, work_bytes, info, s);
+    return cpqr_impl<float>(X, m, n, ldx, k, opts, perm, tau, work, work_bytes, info, s);
+}
+
+int id_solve(const void* X, id_dtype dtype, int64_t n, int64_t ldx, int64_t k, double* T, int64_t ldt, void* stream) {
+    if (!X || !T) return ID_EINVAL;
+    if (dtype != ID_F64 && dtype != ID_F32) return ID_EINVAL;
+    if (k < 1 || n < k || ldx < k || (n > k && ldt < n - k)) return ID_EINVAL;
+    if (n > ((int64_t)1 << 30) || ldx > ((int64_t)1 << 30)) return ID_EINVAL;
+    if (configure_once()) return ID_ECUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = dtype == ID_F64 ? solve_run<double>(X, (int)ldx, (int)k, (int)n, T, (int)ldt, s)
+                                    : solve_run<float>(X, (int)ldx, (int)k, (int)n, T, (int)ldt, s);
+    return e == cudaSuccess ? ID_OK : ID_ECUDA;
+}
+
+int id_info_read(const void* work, id_info* info, void* stream) {
+    if (!work || !info) return ID_EINVAL;
+    return read_info(work, info, static_cast<cudaStream_t>(stream));
+}
+
+int64_t id_launch_count(id_dtype dtype, int64_t m, int64_t n, int64_t k, const id_opts* opts) {
+    (void)opts;
+    if ((dtype != ID_F64 && dtype != ID_F32) || !sizes_ok(m, n, k)) return -1;
+    const int64_t nx = m > n ? m : n;
+    // copy-in, persistent CPQR, back substitution (when n > k), Z scatter, status
+    return 4 + (nx > k ? 1 : 0);
+}
+
+int id_trace_enable(int capacity) { return trace_enable(capacity) == 0 ? ID_OK : ID_ECUDA; }
+
+int id_trace_read(double* ms, int64_t* launches, int nkinds) {
+    if (!ms || !launches || nkinds < 1) return ID_EINVAL;
+    return trace_read(ms, launches, nkinds);
+}
+
+const char* id_version(void) { return "gbid 0.1 (sm_103a)"; }
+
+}  // extern "C"

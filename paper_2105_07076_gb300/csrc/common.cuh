@@ -1,0 +1,73 @@
+// Shared device-side definitions of the ID library (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gbid.h"
+
+namespace gbid {
+
+constexpr int kWarp = 32;
+constexpr int kMaxParts = 2048;     // argmax partial slots per producer kernel
+
+// Device-side status bits collected during a decomposition.
+enum : int { kStatNonFinite = 1, kStatTimeout = 2, kStatOverflow = 4 };
+
+// One candidate of the pivot search: residual norm, original index, position.
+struct __align__(16) ArgMax {
+    double val;
+    int orig;
+    int pos;
+};
+
+// Total order used for pivot selection: larger norm wins, equal norms go to
+// the smaller ORIGINAL column index. An empty slot has val = -1.
+__device__ __forceinline__ bool better(const ArgMax& a, const ArgMax& b) {
+    return a.val > b.val || (a.val == b.val && a.orig < b.orig);
+}
+
+__device__ __forceinline__ ArgMax warp_argmax(ArgMax a) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        ArgMax b;
+        b.val = __shfl_xor_sync(0xffffffffu, a.val, o);
+        b.orig = __shfl_xor_sync(0xffffffffu, a.orig, o);
+        b.pos = __shfl_xor_sync(0xffffffffu, a.pos, o);
+        if (better(b, a)) a = b;
+    }
+    return a;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Per-decomposition device state. Lives in the workspace.
+struct State {
+    int p;              // pivot position of the current step
+    int status;         // kStat* bits
+    int rank;           // first j with a negligible |R_jj| (k if none)
+    int n_recompute;
+    double x0;          // x_j of the current pivot column after the lazy update
+    double beta;        // R_jj
+    double tau;         // reflector scalar
+    double scale;       // 1 / (x_0 - beta): scales x into v with v_0 = 1
+    double r00;         // |R_00|
+    double rank_tol;    // max(m, n) * eps(working precision)
+};
+
+// Device copy of id_info kept in the workspace.
+struct DevInfo {
+    id_info info;
+    unsigned long long n_gt2;
+    unsigned long long max_abs_z_bits;
+};
+
+inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+
+}  // namespace gbid

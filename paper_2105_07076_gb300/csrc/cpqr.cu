@@ -1,0 +1,768 @@
+// Column-pivoted Householder QR, truncated after k pivots (Sec. 2.1; the early
+// stop proposed in Sec. 4.1), for sm_103a.
+//
+// Working matrix W is column-major (column l at W + l*ldw), m <= n, ldw a
+// multiple of 8, rows m..ldw-1 kept at zero so 16-byte vector loads may run
+// over them.
+//
+// All k pivot steps run in one persistent cooperative kernel (k_cpqr); its
+// phases are described above the kernel. The left-looking form (nb = k) never
+// rewrites the trailing matrix: each step corrects its product through the
+// panel factor F. With nb < k a compact-WY update W_trail -= V F^T runs every
+// nb steps and F restarts.
+//
+// The norm downdate follows Drmac & Bujanovic (LAPACK Working Note 176): the
+// downdated estimate nu_l * sqrt(1 - (r_l / nu_l)^2) is replaced by an exact
+// recompute once (nu_new / nu_last_exact)^2 falls below sqrt(eps_64).
+#include <cuda_runtime.h>
+#include <float.h>
+#include <math.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+#include "cpqr.cuh"
+#include "trace.cuh"
+
+namespace gbid {
+
+constexpr int kThreads = 256;              // threads per CTA of the persistent CPQR kernel
+constexpr size_t kCpqrSmemMax = 200 * 1024;  // dynamic shared memory (v cached when it fits)
+
+template <typename T> struct Vec;
+template <> struct Vec<double> { using type = double2; static constexpr int n = 2; };
+template <> struct Vec<float> { using type = float4; static constexpr int n = 4; };
+
+__device__ __forceinline__ double dot_vec(const double2& a, const double2& b, double acc) {
+    acc = fma(a.x, b.x, acc);
+    return fma(a.y, b.y, acc);
+}
+__device__ __forceinline__ float dot_vec(const float4& a, const float4& b, float acc) {
+    acc = fmaf(a.x, b.x, acc);
+    acc = fmaf(a.y, b.y, acc);
+    acc = fmaf(a.z, b.z, acc);
+    return fmaf(a.w, b.w, acc);
+}
+
+__device__ __forceinline__ ArgMax empty_argmax() {
+    ArgMax a;
+    a.val = -1.0;
+    a.orig = 0x7fffffff;
+    a.pos = -1;
+    return a;
+}
+
+// Block-wide argmax; result valid in every thread (blockDim.x <= 1024).
+__device__ ArgMax block_argmax(ArgMax a) {
+    __shared__ ArgMax red[32];
+    a = warp_argmax(a);
+    const int w = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
+    const int nw = blockDim.x / kWarp;
+    __syncthreads();
+    if (lane == 0) red[w] = a;
+    __syncthreads();
+    a = lane < nw ? red[lane] : empty_argmax();
+    return warp_argmax(a);
+}
+
+// Deterministic block sum (fixed thread-to-element map and tree order).
+__device__ double block_sum(double v) {
+    __shared__ double red[32];
+    v = warp_sum(v);
+    const int w = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
+    const int nw = blockDim.x / kWarp;
+    __syncthreads();
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    v = lane < nw ? red[lane] : 0.0;
+    return warp_sum(v);
+}
+
+// ------------------------------------------------------------------ copy-in --
+// X (m x n, m <= n) into column-major W. trans == 0: X(i,l) = A[i*lda + l]
+// (A is m x n row-major). trans == 1: X(i,l) = A[l*lda + i] (A is the user's
+// n x m row-major matrix with more rows than columns; X = A^T). Rows m..ldw-1
+// of W are zeroed.
+template <typename T>
+__global__ void __launch_bounds__(256) k_copy_in(const T* __restrict__ A, int64_t lda, int trans, int m, int n,
+                                                 T* __restrict__ W, int ldw) {
+    __shared__ T tile[32][33];
+    const int i0 = blockIdx.x * 32, l0 = blockIdx.y * 32;
+    const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
+    if (!trans) {
+        for (int q = ty; q < 32; q += 8) {
+            const int i = i0 + q, l = l0 + tx;
+            tile[q][tx] = (i < m && l < n) ? A[(int64_t)i * lda + l] : T(0);
+        }
+        __syncthreads();
+        for (int q = ty; q < 32; q += 8) {
+            const int l = l0 + q, i = i0 + tx;
+            if (l < n && i < ldw) W[(int64_t)l * ldw + i] = tile[tx][q];
+        }
+    } else {
+        for (int q = ty; q < 32; q += 8) {
+            const int l = l0 + q, i = i0 + tx;
+            if (l < n && i < ldw) W[(int64_t)l * ldw + i] = (i < m) ? A[(int64_t)l * lda + i] : T(0);
+        }
+    }
+}
+
+// Zero rows m..ldw-1 of every column (id_cpqr path, user-provided X).
+template <typename T>
+__global__ void k_zero_pad(T* W, int ldw, int m, int n) {
+    const int64_t pad = ldw - m;
+    const int64_t total = pad * n;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t l = e / pad, i = m + e % pad;
+        W[l * ldw + i] = T(0);
+    }
+}
+
+// ---------------------------------------------------------- grid barrier --
+// Barrier across the co-resident CTAs of the cooperative launch: one
+// monotonically growing arrival counter; barrier number b completes when the
+// counter reaches (b + 1) * gridDim.x. The wait is bounded: after
+// kSpinLimit polls it records kStatTimeout and returns; once that bit is set
+// every later wait returns at once and the step loop stops, so the kernel
+// always terminates.
+constexpr unsigned long long kSpinLimit = 1ull << 22;
+
+__device__ __forceinline__ bool timed_out(const State* st) {
+    return (*(const volatile int*)&st->status & kStatTimeout) != 0;
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Wait until *p >= target (bounded). Returns false on timeout.
+__device__ bool wait_geq(const unsigned* p, unsigned target, State* st) {
+    unsigned long long spins = 0;
+    while (ld_acquire(p) < target) {
+        if (timed_out(st)) return false;
+        if (++spins > kSpinLimit) {
+            atomicOr(&st->status, kStatTimeout);
+            return false;
+        }
+        __nanosleep(32);
+    }
+    return true;
+}
+
+__device__ void grid_sync(unsigned* bar, unsigned& epoch, State* st) {
+    __syncthreads();
+    ++epoch;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        red_release_add(bar, 1u);
+        wait_geq(bar, epoch * gridDim.x, st);
+        __threadfence();
+    }
+    __syncthreads();
+}
+
+// L2-coherent loads: data written by other CTAs of the same launch must not be
+// served from this SM's L1.
+template <typename T> __device__ __forceinline__ T ld(const T* p) { return __ldcg(p); }
+__device__ __forceinline__ ArgMax ld_argmax(const ArgMax* p) {
+    const int4 v = __ldcg(reinterpret_cast<const int4*>(p));
+    ArgMax a;
+    a.val = __hiloint2double(v.y, v.x);
+    a.orig = v.z;
+    a.pos = v.w;
+    return a;
+}
+
+// VN consecutive entries of the reflector v = x * scale (v_j = 1, zero outside
+// rows j..m-1), rebuilt from the pivot column when v is not cached.
+template <typename T, typename V, int VN>
+__device__ __forceinline__ V v_at(const T* xbuf, int i, int j, int m, double scale) {
+    V out;
+    T* o = reinterpret_cast<T*>(&out);
+#pragma unroll
+    for (int q = 0; q < VN; ++q) {
+        const int ii = i + q;
+        o[q] = ii < j || ii >= m ? T(0) : (ii == j ? T(1) : (T)((double)__ldcg(xbuf + ii) * scale));
+    }
+    return out;
+}
+
+struct KParams {
+    void* W;
+    int ldw, m, n, k, nb;
+    void* F;
+    int ldf;
+    void* xbuf;       // ldw: pivot column after the lazy update (rows >= j)
+    double* vn1;
+    double* vn2;
+    int* perm;
+    double* tau;
+    ArgMax* part;     // gridDim.x argmax partials
+    double* ssq;      // gridDim.x partial sums of squares
+    void* aux;        // kMaxPanel
+    unsigned* bar;    // grid-barrier arrival counter, zero on entry
+    unsigned* auxcnt; // k per-step counters of finished aux entries, zero on entry
+    int* ctr;         // k + 1 column-queue counters, zero on entry
+    State* st;
+    double rank_tol;
+    int rows_per_cta; // row chunk of the pivot-column phase (multiple of 32)
+};
+
+// WY tile: W(i, l) -= sum_{c < nbw} V(i, c) F(l, c), 64 x 64 tile at (i0, l0).
+template <typename T>
+__device__ void wy_tile(T* W, int ldw, int m, int n, int i0, int l0, int j0, int nbw, const T* F, int ldf,
+                        T* Vs, T* Fs) {
+    constexpr int TM = 64, TN = 64, TK = 16;
+    const int t = threadIdx.x;
+    const bool act = t < 256;   // 16 x 16 threads own the 64 x 64 tile
+    const int tx = t % 16, ty = (t / 16) % 16;
+    T acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+    for (int c0 = 0; c0 < nbw; c0 += TK) {
+        __syncthreads();
+        for (int e = t; e < TK * TM; e += kThreads) {
+            const int c = e / TM, i = e % TM;
+            Vs[c * TM + i] = (c0 + c < nbw && i0 + i < m) ? ld(W + (int64_t)(j0 + c0 + c) * ldw + i0 + i) : T(0);
+        }
+        for (int e = t; e < TK * TN; e += kThreads) {
+            const int l = e / TK, c = e % TK;
+            Fs[c * (TN + 1) + l] = (c0 + c < nbw && l0 + l < n) ? ld(F + (int64_t)(l0 + l) * ldf + c0 + c) : T(0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int c = 0; c < TK; ++c) {
+            T va[4], fb[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) va[a] = Vs[c * TM + tx * 4 + a];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) fb[b] = Fs[c * (TN + 1) + ty * 4 + b];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) acc[a][b] += va[a] * fb[b];
+        }
+    }
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        const int l = l0 + ty * 4 + b;
+        if (!act || l >= n) continue;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const int i = i0 + tx * 4 + a;
+            if (i < m) W[(int64_t)l * ldw + i] = ld(W + (int64_t)l * ldw + i) - acc[a][b];
+        }
+    }
+    __syncthreads();
+}
+
+constexpr int kFRegs = 8;   // panel entries per lane held in registers (panels up to 256 wide)
+
+// Shared-memory plan of k_cpqr (dynamic part): vrow_s | fco | v_s.
+struct SmemPlan {
+    bool smem_v;    // v cached in shared memory
+    size_t bytes;   // dynamic shared memory
+};
+
+// ------------------------------------------------------- persistent CPQR --
+// One cooperative launch runs all k pivot steps. Per step j (panel start j0,
+// jj = j - j0):
+//  A. pivot p = argmax over the CTAs' partials (ties: smallest original
+//     index); swap columns j <-> p; x = W(:, p) - V F(p, :)^T on rows >= j
+//     (the pivot column brought up to date with the panel's reflectors), each
+//     CTA on its row chunk; partial ||x(j+1:m)||^2.            -- grid barrier
+//  B. beta = -sign(x_j) ||x||, tau = (beta - x_j) / beta, v = x / (x_j - beta)
+//     with v_j = 1, written to W(:, j); aux = -tau V^T v (one CTA per panel
+//     column, published through a counter); then the trailing product, one
+//     warp per column taken from a queue (order reversed on odd steps so the
+//     tail of one sweep is still in L2 when the next starts):
+//       g = W(j:m, l)^T v,  F(l, jj) = tau g + F(l, 0:jj) aux,
+//       R(j, l) = W(j, l) - F(l, 0:jj) V(j, 0:jj)^T - F(l, jj),
+//     and the FP64 norm downdate nu_l <- nu_l sqrt(1 - (R(j,l)/nu_l)^2),
+//     replaced by an exact recompute when (nu_new / nu_exact)^2 <= sqrt(eps_64)
+//     (Drmac & Bujanovic, LAPACK Working Note 176); partial argmax.
+//                                                               -- grid barrier
+//  C. every nb steps (nb < k): compact-WY update W_trail -= V F^T. -- barrier
+// Every wait (grid barrier, aux counter) is bounded and ends the kernel early
+// with kStatTimeout instead of hanging.
+template <typename T, bool kSmemV>
+__global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
+    using V = typename Vec<T>::type;
+    constexpr int VN = Vec<T>::n;
+    constexpr int NW = kThreads / kWarp;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    T* vrow_s = reinterpret_cast<T*>(smem_raw);
+    T* fco = vrow_s + kMaxPanel + 4;
+    T* v_s = fco + kMaxPanel + 4;                      // 16-byte aligned
+    __shared__ T wy_s[16 * 64 + 16 * 65];              // WY-update tiles
+    __shared__ T red[NW][kWarp];
+    __shared__ double sc[4];
+
+    T* W = static_cast<T*>(P.W);
+    T* F = static_cast<T*>(P.F);
+    T* xbuf = static_cast<T*>(P.xbuf);
+    T* aux = static_cast<T*>(P.aux);
+    State* st = P.st;
+    const int m = P.m, n = P.n, ldw = P.ldw, ldf = P.ldf;
+    const int t = threadIdx.x, lane = t % kWarp, w = t / kWarp;
+    const int G = gridDim.x;
+    const double tol3z = sqrt(DBL_EPSILON);
+    unsigned epoch = 0;
+
+    // ---- column norms, perm, first argmax partials
+    {
+        if (blockIdx.x == 0 && t == 0) {
+            st->rank = P.k;
+            st->rank_tol = P.rank_tol;
+        }
+        ArgMax best = empty_argmax();
+        for (int l = blockIdx.x * NW + w; l < n; l += G * NW) {
+            const T* col = W + (int64_t)l * ldw;
+            double s = 0.0;
+            for (int i = lane; i < m; i += kWarp) {
+                const double x = (double)ld(col + i);
+                s = fma(x, x, s);
+            }
+            s = warp_sum(s);
+            if (lane == 0) {
+                const double nu = sqrt(s);
+                P.vn1[l] = nu;
+                P.vn2[l] = nu;
+                P.perm[l] = l;
+                if (!isfinite(s)) atomicOr(&st->status, kStatNonFinite);
+                ArgMax c;
+                c.val = isfinite(nu) ? nu : -1.0;
+                c.orig = l;
+                c.pos = l;
+                if (better(c, best)) best = c;
+            }
+        }
+        best = block_argmax(best);
+        if (t == 0) P.part[blockIdx.x] = best;
+    }
+    grid_sync(P.bar, epoch, st);
+
+    const int RC = P.rows_per_cta;
+    const int r0 = blockIdx.x * RC;
+    const int r1 = min(r0 + RC, m);
+
+    for (int j = 0; j < P.k; ++j) {
+        if (timed_out(st)) break;
+        const int j0 = j / P.nb * P.nb;
+        const int jj = j - j0;
+
+        // ---- A: pivot, swap, lazy update of the pivot column
+        ArgMax best = empty_argmax();
+        for (int e = t; e < G; e += kThreads) {
+            const ArgMax c = ld_argmax(P.part + e);
+            if (better(c, best)) best = c;
+        }
+        best = block_argmax(best);
+        const int p = best.pos >= j ? best.pos : j;
+        if (blockIdx.x == 0 && p != j) {
+            if (t == 0) {
+                const double a = ld(P.vn1 + j), b = ld(P.vn1 + p);
+                P.vn1[j] = b;
+                P.vn1[p] = a;
+            } else if (t == 32) {
+                const double a = ld(P.vn2 + j), b = ld(P.vn2 + p);
+                P.vn2[j] = b;
+                P.vn2[p] = a;
+            } else if (t == 64) {
+                const int a = ld(P.perm + j), b = ld(P.perm + p);
+                P.perm[j] = b;
+                P.perm[p] = a;
+            }
+        }
+        for (int c = t; c < jj; c += kThreads) fco[c] = ld(F + (int64_t)p * ldf + c);
+        __syncthreads();
+        double ssq = 0.0;
+        for (int rt = r0; rt < r1; rt += kWarp) {
+            const int r = rt + lane;
+            T acc = T(0);
+            if (r < r1 && r >= j) {
+                T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+                int c = w;
+                for (; c + 3 * NW < jj; c += 4 * NW) {
+                    a0 += ld(W + (int64_t)(j0 + c) * ldw + r) * fco[c];
+                    a1 += ld(W + (int64_t)(j0 + c + NW) * ldw + r) * fco[c + NW];
+                    a2 += ld(W + (int64_t)(j0 + c + 2 * NW) * ldw + r) * fco[c + 2 * NW];
+                    a3 += ld(W + (int64_t)(j0 + c + 3 * NW) * ldw + r) * fco[c + 3 * NW];
+                }
+                for (; c < jj; c += NW) a0 += ld(W + (int64_t)(j0 + c) * ldw + r) * fco[c];
+                acc = (a0 + a1) + (a2 + a3);
+            }
+            red[w][lane] = acc;
+            __syncthreads();
+            if (w == 0 && r < r1) {
+                T s = T(0);
+#pragma unroll
+                for (int g = 0; g < NW; ++g) s += red[g][lane];
+                const T a = ld(W + (int64_t)p * ldw + r);
+                const T b = ld(W + (int64_t)j * ldw + r);
+                const T x = r >= j ? a - s : a;
+                W[(int64_t)p * ldw + r] = b;
+                if (r < j) W[(int64_t)j * ldw + r] = x;   // R entries travel with their column
+                else xbuf[r] = x;
+                if (r > j) ssq = fma((double)x, (double)x, ssq);
+                if (r == j) st->x0 = (double)x;
+            }
+            __syncthreads();
+        }
+        if (w == 0) {
+            ssq = warp_sum(ssq);
+            if (lane == 0) P.ssq[blockIdx.x] = ssq;
+        }
+        grid_sync(P.bar, epoch, st);
+
+        // ---- B1: reflector scalars (same arithmetic in every CTA)
+        {
+            double s = 0.0;
+            for (int e = t; e < G; e += kThreads) s += ld(P.ssq + e);
+            s = block_sum(s);
+            if (t == 0) {
+                const double x0 = ld(&st->x0);
+                const double alpha = sqrt(fma(x0, x0, s));
+                double beta = 0.0, tau = 0.0, scale = 0.0;
+                if (alpha != 0.0) {
+                    beta = x0 >= 0.0 ? -alpha : alpha;
+                    tau = (beta - x0) / beta;
+                    scale = 1.0 / (x0 - beta);
+                }
+                sc[0] = beta;
+                sc[1] = tau;
+                sc[2] = scale;
+                if (blockIdx.x == 0) {
+                    st->beta = beta;
+                    st->tau = tau;
+                    P.tau[j] = tau;
+                    if (j == 0) st->r00 = fabs(beta);
+                    const double r00 = j == 0 ? fabs(beta) : ld(&st->r00);
+                    if (r00 == 0.0 || fabs(beta) <= P.rank_tol * r00) atomicMin(&st->rank, j);
+                    if (!isfinite(beta)) atomicOr(&st->status, kStatNonFinite);
+                }
+            }
+            __syncthreads();
+        }
+        const double beta = sc[0], tau = sc[1], scale = sc[2];
+        // v on this CTA's rows into W(:, j) (reflector storage, v_j = 1 implicit)
+        for (int r = max(r0, j) + t; r < r1; r += kThreads)
+            W[(int64_t)j * ldw + r] = r == j ? (T)beta : (T)((double)ld(xbuf + r) * scale);
+
+        // ---- B2: aux = -tau V(j:m, 0:jj)^T v, one CTA per panel column
+        for (int c = blockIdx.x; c < jj; c += G) {
+            const T* vc = W + (int64_t)(j0 + c) * ldw;
+            T acc = T(0);
+            if (t == 0) acc = ld(vc + j);   // v_j = 1
+            for (int i = j + 1 + t; i < m; i += 4 * kThreads) {
+                T xs[4], vs4[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int ii = i + u * kThreads;
+                    xs[u] = ii < m ? ld(xbuf + ii) : T(0);
+                    vs4[u] = ii < m ? ld(vc + ii) : T(0);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) acc += vs4[u] * (T)((double)xs[u] * scale);
+            }
+            const double tot = block_sum((double)acc);
+            if (t == 0) {
+                aux[c] = (T)(-tau * tot);
+                __threadfence();
+                red_release_add(P.auxcnt + j, 1u);
+            }
+        }
+
+        // ---- B3: trailing product, one warp per column from a queue
+        if (j + 1 < n) {
+            const int j_al = j & ~(VN - 1);
+            const int m_pad = (m + VN - 1) / VN * VN;
+            for (int c = t; c < jj; c += kThreads) vrow_s[c] = ld(W + (int64_t)(j0 + c) * ldw + j);
+            if (kSmemV)
+                for (int i = j_al + t; i < m_pad; i += kThreads)
+                    v_s[i - j_al] = i < j || i >= m ? T(0) : (i == j ? T(1) : (T)((double)ld(xbuf + i) * scale));
+            __syncthreads();
+            const T tauT = (T)tau;
+            const int ncols = n - j - 1;
+            const bool rev = (j & 1) != 0;   // alternate sweep direction: the last columns read stay in L2
+            int* ctr = P.ctr + j;
+            ArgMax bestc = empty_argmax();
+            bool aux_ready = false;
+            T auxr[kFRegs];                  // aux[lane + 32 q], loaded once the counter says it is complete
+            int idx = 0;
+            if (lane == 0) idx = atomicAdd(ctr, 1);
+            idx = __shfl_sync(0xffffffffu, idx, 0);
+            while (idx < ncols) {
+                const int l = rev ? n - 1 - idx : j + 1 + idx;
+                int nidx = 0;
+                if (lane == 0) nidx = atomicAdd(ctr, 1);   // next column, in flight meanwhile
+                const bool moved = l == p && p != j;        // column p carries the old column j's F row
+                const T* frow = F + (int64_t)(moved ? j : l) * ldf;
+                T wjl = T(0);
+                double nu = 0.0, nu2 = 1.0;
+                int orig = 0;
+                if (lane == 0) {
+                    wjl = ld(W + (int64_t)l * ldw + j);
+                    nu = ld(P.vn1 + l);
+                    nu2 = ld(P.vn2 + l);
+                    orig = ld(P.perm + l);
+                }
+                T fr[kFRegs];
+#pragma unroll
+                for (int q = 0; q < kFRegs; ++q) {
+                    const int c = lane + q * kWarp;
+                    fr[q] = c < jj ? ld(frow + c) : T(0);
+                }
+                // g = W(j_al:m_pad, l)^T v, eight 16-byte loads per lane in flight
+                const T* col = W + (int64_t)l * ldw;
+                T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+                constexpr int S = kWarp * VN;
+                for (int i0 = j_al + lane * VN; i0 < m_pad; i0 += 8 * S) {
+                    V xv[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int i = i0 + u * S;
+                        if (i < m_pad) xv[u] = __ldcg(reinterpret_cast<const V*>(col + i));
+                    }
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int i = i0 + u * S;
+                        if (i < m_pad) {
+                            const V yv = kSmemV ? *reinterpret_cast<const V*>(v_s + (i - j_al))
+                                                : v_at<T, V, VN>(xbuf, i, j, m, scale);
+                            if (u % 4 == 0) a0 = dot_vec(xv[u], yv, a0);
+                            else if (u % 4 == 1) a1 = dot_vec(xv[u], yv, a1);
+                            else if (u % 4 == 2) a2 = dot_vec(xv[u], yv, a2);
+                            else a3 = dot_vec(xv[u], yv, a3);
+                        }
+                    }
+                }
+                if (!aux_ready) {
+                    int ok = 1;
+                    if (lane == 0) ok = wait_geq(P.auxcnt + j, (unsigned)jj, st) ? 1 : 0;
+                    ok = __shfl_sync(0xffffffffu, ok, 0);
+                    if (!ok) break;
+#pragma unroll
+                    for (int q = 0; q < kFRegs; ++q) {
+                        const int c = lane + q * kWarp;
+                        auxr[q] = c < jj ? ld(aux + c) : T(0);
+                    }
+                    aux_ready = true;
+                }
+                T s1 = T(0), s2 = T(0);
+#pragma unroll
+                for (int q = 0; q < kFRegs; ++q) {
+                    const int c = lane + q * kWarp;
+                    if (c < jj) {
+                        if (moved) F[(int64_t)p * ldf + c] = fr[q];
+                        s1 += fr[q] * auxr[q];
+                        s2 += fr[q] * vrow_s[c];
+                    }
+                }
+                for (int c = lane + kFRegs * kWarp; c < jj; c += kWarp) {   // panels wider than kFRegs * 32
+                    const T fv = ld(frow + c);
+                    if (moved) F[(int64_t)p * ldf + c] = fv;
+                    s1 += fv * ld(aux + c);
+                    s2 += fv * vrow_s[c];
+                }
+                const T g = warp_sum((a0 + a1) + (a2 + a3));
+                s1 = warp_sum(s1);
+                s2 = warp_sum(s2);
+                const T f = tauT * g + s1;
+                int flagged = 0;
+                if (lane == 0) {
+                    F[(int64_t)l * ldf + jj] = f;
+                    const T rjl = wjl - s2 - f;
+                    W[(int64_t)l * ldw + j] = rjl;
+                    ArgMax cnd;
+                    cnd.orig = orig;
+                    cnd.pos = l;
+                    cnd.val = 0.0;
+                    if (nu != 0.0) {
+                        const double q = fabs((double)rjl) / nu;
+                        double temp = (1.0 - q) * (1.0 + q);
+                        temp = temp > 0.0 ? temp : 0.0;
+                        const double ratio = nu / nu2;
+                        if (temp * ratio * ratio <= tol3z) {
+                            flagged = 1;
+                        } else {
+                            cnd.val = nu * sqrt(temp);
+                            P.vn1[l] = cnd.val;
+                        }
+                    }
+                    if (!flagged && better(cnd, bestc)) bestc = cnd;
+                }
+                flagged = __shfl_sync(0xffffffffu, flagged, 0);
+                if (flagged) {
+                    // cancellation: exact ||W(j+1:m, l) - V F(l, 0:jj+1)^T|| by this warp
+                    orig = __shfl_sync(0xffffffffu, orig, 0);
+                    double sacc = 0.0;
+                    for (int i = j + 1 + lane; i < m; i += kWarp) {
+                        T y = ld(col + i);
+                        for (int c = 0; c < jj; ++c) y -= ld(W + (int64_t)(j0 + c) * ldw + i) * ld(frow + c);
+                        // the current reflector (other CTAs may still be writing it to W(:, j))
+                        const T vi = kSmemV ? v_s[i - j_al] : (T)((double)ld(xbuf + i) * scale);
+                        y -= vi * f;
+                        sacc = fma((double)y, (double)y, sacc);
+                    }
+                    sacc = warp_sum(sacc);
+                    if (lane == 0) {
+                        const double nv = sqrt(sacc);
+                        P.vn1[l] = nv;
+                        P.vn2[l] = nv;
+                        ArgMax cnd;
+                        cnd.val = nv;
+                        cnd.orig = orig;
+                        cnd.pos = l;
+                        if (better(cnd, bestc)) bestc = cnd;
+                        atomicAdd(&st->n_recompute, 1);
+                    }
+                }
+                idx = __shfl_sync(0xffffffffu, nidx, 0);
+            }
+            bestc = block_argmax(bestc);
+            if (t == 0) P.part[blockIdx.x] = bestc;
+        }
+        grid_sync(P.bar, epoch, st);
+
+        // ---- C: compact-WY trailing update at the end of a panel
+        if (j + 1 < P.k && jj == P.nb - 1 && m > j + 1) {
+            const int je = j + 1;
+            const int tm = (m - je + 63) / 64, tn = (n - je + 63) / 64;
+            for (int tile = blockIdx.x; tile < tm * tn; tile += G)
+                wy_tile<T>(W, ldw, m, n, je + (tile % tm) * 64, je + (tile / tm) * 64, j0, P.nb, F, ldf, wy_s,
+                           wy_s + 16 * 64);
+            grid_sync(P.bar, epoch, st);
+        }
+    }
+}
+
+// ------------------------------------------------------------------- host --
+// Shared-memory bytes of k_cpqr for m working rows; v is cached in shared
+// memory when it fits in kCpqrSmemMax.
+template <typename T>
+static SmemPlan cpqr_smem(int m) {
+    const int vn = Vec<T>::n;
+    const size_t m_pad = (size_t)(m + vn - 1) / vn * vn;
+    const size_t fixed = sizeof(T) * 2 * ((size_t)kMaxPanel + 4);
+    const size_t vbytes = sizeof(T) * (m_pad + 8);
+    SmemPlan pl;
+    pl.smem_v = fixed + vbytes <= kCpqrSmemMax;
+    pl.bytes = fixed + (pl.smem_v ? vbytes : 0);
+    return pl;
+}
+
+static int g_nsm = 0;
+
+template <typename T>
+cudaError_t cpqr_configure() {
+    cudaError_t e = cudaFuncSetAttribute(k_cpqr<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kCpqrSmemMax);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_cpqr<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCpqrSmemMax);
+    if (e != cudaSuccess) return e;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    return cudaDeviceGetAttribute(&g_nsm, cudaDevAttrMultiProcessorCount, dev);
+}
+
+template <typename T>
+cudaError_t copy_in(const void* A, int64_t lda, int trans, const CpqrPlan& P, cudaStream_t s) {
+    dim3 grid(ceil_div(P.ldw, 32), ceil_div(P.n, 32));
+    k_copy_in<T><<<grid, 256, 0, s>>>(static_cast<const T*>(A), lda, trans, P.m, P.n, static_cast<T*>(P.W), P.ldw);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t zero_pad(const CpqrPlan& P, cudaStream_t s) {
+    if (P.ldw == P.m) return cudaSuccess;
+    k_zero_pad<T><<<304, 256, 0, s>>>(static_cast<T*>(P.W), P.ldw, P.m, P.n);
+    return cudaGetLastError();
+}
+
+template <typename T>
+int cpqr_grid(int m) {
+    const SmemPlan pl = cpqr_smem<T>(m);
+    int occ = 0;
+    if (pl.smem_v) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cpqr<T, true>, kThreads, pl.bytes);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cpqr<T, false>, kThreads, pl.bytes);
+    if (occ < 1) return 0;
+    return std::min(kMaxParts, g_nsm * occ);
+}
+
+template <typename T>
+cudaError_t cpqr_run(const CpqrPlan& P, cudaStream_t s) {
+    const double eps = sizeof(T) == 8 ? DBL_EPSILON : (double)FLT_EPSILON;
+    const SmemPlan pl = cpqr_smem<T>(P.m);
+    const int G = cpqr_grid<T>(P.m);
+    if (G < 1) return cudaErrorInvalidConfiguration;
+
+    cudaError_t e = cudaMemsetAsync(P.st, 0, sizeof(State), s);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(P.sync, 0, sync_bytes(P.k), s);
+    if (e != cudaSuccess) return e;
+    if (e != cudaSuccess) return e;
+
+    KParams K;
+    K.W = P.W;
+    K.ldw = P.ldw;
+    K.m = P.m;
+    K.n = P.n;
+    K.k = P.k;
+    K.nb = P.nb;
+    K.F = P.F;
+    K.ldf = P.ldf;
+    K.xbuf = P.xbuf;
+    K.vn1 = P.vn1;
+    K.vn2 = P.vn2;
+    K.perm = P.perm;
+    K.tau = P.tau;
+    K.part = P.part3;
+    K.ssq = P.ssq;
+    K.aux = P.aux;
+    char* sync = reinterpret_cast<char*>(P.sync);
+    K.bar = reinterpret_cast<unsigned*>(sync);
+    K.auxcnt = reinterpret_cast<unsigned*>(sync + 64);
+    K.ctr = reinterpret_cast<int*>(sync + 64 + 4 * (size_t)P.k);   // see sync_bytes()
+    K.st = P.st;
+    K.rank_tol = (double)(P.m_user > P.n_user ? P.m_user : P.n_user) * eps;
+    K.rows_per_cta = (int)round_up(ceil_div(P.m, G), kWarp);
+
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(G);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = pl.bytes;
+    cfg.stream = s;
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeCooperative;
+    attr.val.cooperative = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    const int tr = trace_begin(TraceKind::kCpqr, s);
+    if (pl.smem_v) e = cudaLaunchKernelEx(&cfg, k_cpqr<T, true>, K);
+    else e = cudaLaunchKernelEx(&cfg, k_cpqr<T, false>, K);
+    trace_end(tr, s);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+template cudaError_t cpqr_configure<double>();
+template cudaError_t cpqr_configure<float>();
+template int cpqr_grid<double>(int);
+template int cpqr_grid<float>(int);
+template cudaError_t copy_in<double>(const void*, int64_t, int, const CpqrPlan&, cudaStream_t);
+template cudaError_t copy_in<float>(const void*, int64_t, int, const CpqrPlan&, cudaStream_t);
+template cudaError_t zero_pad<double>(const CpqrPlan&, cudaStream_t);
+template cudaError_t zero_pad<float>(const CpqrPlan&, cudaStream_t);
+template cudaError_t cpqr_run<double>(const CpqrPlan&, cudaStream_t);
+template cudaError_t cpqr_run<float>(const CpqrPlan&, cudaStream_t);
+
+}  // namespace gbid

@@ -1,0 +1,50 @@
+// Internal interface of the CPQR kernels (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace gbid {
+
+constexpr int kMaxPanel = 512;                  // largest panel width nb
+
+// Device buffers and sizes of one truncated CPQR. The working matrix is
+// m x n column-major (m <= n), leading dimension ldw (multiple of 8).
+struct CpqrPlan {
+    int m, n, ldw, k, nb;
+    int64_t m_user, n_user;   // the caller's dimensions (for the rank tolerance)
+    void* W;                  // m x n working matrix (T)
+    void* F;                  // n x ldf row-major panel factor (T)
+    int ldf;
+    void* xbuf;               // ldw: pivot column after the lazy update (T)
+    double* ssq;              // kMaxParts partial sums of squares
+    void* sync;               // sync_bytes(k): barrier counter, per-step aux and column-queue counters
+    double* vn1;              // n: residual norm estimates
+    double* vn2;              // n: norms at the last exact computation
+    int* perm;                // n
+    double* tau;              // k
+    ArgMax* part3;            // kMaxParts argmax partials of the previous step
+    void* aux;                // kMaxPanel (T)
+    State* st;
+};
+
+// Bytes of the zero-initialised synchronisation area of one CPQR: a 64-byte
+// grid-barrier slot, k per-step aux counters and k + 1 column-queue counters.
+inline size_t sync_bytes(int k) { return 64 + 4 * (size_t)k + 4 * ((size_t)k + 1); }
+
+template <typename T> cudaError_t cpqr_configure();
+template <typename T> cudaError_t copy_in(const void* A, int64_t lda, int trans, const CpqrPlan& P, cudaStream_t s);
+template <typename T> cudaError_t zero_pad(const CpqrPlan& P, cudaStream_t s);
+template <typename T> cudaError_t cpqr_run(const CpqrPlan& P, cudaStream_t s);
+template <typename T> int cpqr_grid(int m);   // CTAs of the cooperative launch (0: cannot launch)
+
+// Back substitution T = R11^{-1} R12 (FP64) and Z assembly.
+template <typename T> cudaError_t solve_run(const void* W, int ldw, int k, int n, double* Tm, int ldt, cudaStream_t s);
+template <typename T> cudaError_t scatter_z(const int* perm, const double* Tm, int ldt, int k, int n, void* Z,
+                                            int64_t ldz, int32_t* J, DevInfo* info, cudaStream_t s);
+cudaError_t solve_configure();
+cudaError_t finalize_info(const State* st, DevInfo* info, int k, int transposed, int nb, cudaStream_t s);
+
+}  // namespace gbid

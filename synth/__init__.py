@@ -27,7 +27,9 @@ Uniform matrices of size 784x1000) are reproduced by ``paper_dataset``.
 """
 from __future__ import annotations
 
+import ctypes
 import math
+import os
 
 import numpy as np
 import torch
@@ -44,6 +46,20 @@ __all__ = [
 ]
 
 
+def _preload_cuda_linalg(device) -> None:
+    """Load torch's CUDA linear-algebra library by absolute path.
+
+    torch opens it lazily by bare name on the first GPU QR; under a profiler
+    that injects itself into the process that lookup can fail, so the
+    generators load it explicitly first.
+    """
+    if torch.device(device).type != "cuda":
+        return
+    path = os.path.join(os.path.dirname(torch.__file__), "lib", "libtorch_cuda_linalg.so")
+    if os.path.exists(path):
+        ctypes.CDLL(path, mode=ctypes.RTLD_GLOBAL)
+
+
 def _gen(seed: int, device) -> torch.Generator:
     g = torch.Generator(device=torch.device(device))
     g.manual_seed(int(seed))
@@ -53,6 +69,7 @@ def _gen(seed: int, device) -> torch.Generator:
 def haar(rows: int, cols: int, seed: int, device="cpu", dtype=torch.float64) -> torch.Tensor:
     """rows x cols matrix with Haar-distributed orthonormal columns (rows >= cols)."""
     assert rows >= cols
+    _preload_cuda_linalg(device)
     g = _gen(seed, device)
     G = torch.randn(rows, cols, generator=g, device=device, dtype=dtype)
     Q, R = torch.linalg.qr(G, mode="reduced")

@@ -1,0 +1,269 @@
+"""GPU path vs the FP64 CPU oracle, element by element, through the C ABI.
+
+Tolerances (stated by the method's accuracy targets):
+  * pivots: identical to the oracle's up to the first step where the oracle's
+    two best residual norms lie within TOL_PIV (1e-6 relative in FP64;
+    64 u_32 sqrt(m) in FP32, the FP32 rounding level of a residual norm);
+    the whole GPU sequence must pass the oracle's greedy replay with TOL_PIV;
+  * Z: ||Z_gpu - Z_oracle(J_gpu)||_F / ||Z_oracle(J_gpu)||_F <= 1e-10 (FP64),
+    1e-4 (FP32), with Z_oracle(J_gpu) the oracle's ID for the GPU's pivots;
+  * reconstruction error <= 1.05 x the oracle's (+ 20 eps for exact-rank inputs);
+  * Z[:, J] = I exactly; n_gt2 and max|Z| equal to what Z holds.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import id_oracle as orc
+
+pytestmark = pytest.mark.gpu
+
+TOL_Z = {torch.float64: 1e-10, torch.float32: 1e-4}
+
+
+def tol_piv(dtype, m):
+    return 1e-6 if dtype == torch.float64 else 64 * 2.0 ** -24 * math.sqrt(m)
+
+
+@pytest.fixture(scope="module")
+def gbid():
+    import __graft_entry__ as g
+
+    g.build()
+    import paper_2105_07076_gb300 as m
+
+    return m
+
+
+def run_and_check(gbid, A64: np.ndarray, k: int, dtype, nb=0, exact_rank=False, lda_pad=0):
+    m, n = A64.shape
+    At = torch.as_tensor(A64).to(dtype)
+    if lda_pad:
+        big = torch.zeros(m, n + lda_pad, dtype=dtype)
+        big[:, :n] = At
+        Ad = big.cuda()[:, :n]
+    else:
+        Ad = At.cuda()
+    J, Z, info = gbid.id_decompose(Ad, k, nb=nb)
+    A_exact = At.double().numpy()            # the values the GPU saw
+    transposed = m > n
+    X = A_exact.T if transposed else A_exact
+    Jg = J.cpu().numpy().astype(np.int64)
+    Zg = Z.cpu().double().numpy()
+    tp = tol_piv(dtype, min(m, n))
+    assert info["status"] in (gbid.ID_OK, gbid.ID_RANK_DEFICIENT), info
+    assert info["transposed"] == transposed
+    ok, worst = orc.verify_pivots(X, Jg, tp)
+    assert ok, f"greedy replay margin {worst.max():.3e} > {tp:.1e} at step {int(np.argmax(worst))}"
+    Jo, Zo, oinfo = orc.interp_decomp(A_exact, k)
+    near = np.flatnonzero(oinfo["gap"] < tp)
+    first = int(near[0]) if near.size else k
+    assert np.array_equal(Jg[:first], Jo[:first]), (Jg[:first], Jo[:first])
+    Zr = orc.interp_decomp(A_exact, k, pivots=Jg)[1]
+    rel = np.linalg.norm(Zg - Zr) / np.linalg.norm(Zr)
+    assert rel <= TOL_Z[dtype], rel
+    assert np.array_equal(Zg[:, Jg], np.eye(k))
+    err_g = orc.rel_error(A_exact, Jg, Zg, transposed)
+    err_o = orc.rel_error(A_exact, Jo, Zo, transposed)
+    slack = 20 * np.finfo(np.float64).eps if dtype == torch.float64 else 20 * 2.0 ** -24
+    assert err_g <= 1.05 * err_o + slack, (err_g, err_o)
+    if exact_rank:
+        assert err_g <= (1e-12 if dtype == torch.float64 else 1e-5)
+    assert info["n_gt2"] == int(np.count_nonzero(np.abs(Zg) > 2.0))
+    assert info["max_abs_z"] == pytest.approx(float(np.abs(Zg).max()), rel=1e-6 if dtype == torch.float32 else 0)
+    return J, Z, info, oinfo
+
+
+# ---------------------------------------------------- the small workload ---
+@pytest.mark.parametrize("nb", [0, 8, 1, 20])
+def test_lowrank_200x400_k20_f64(gbid, nb):
+    A = synth.lowrank(200, 400, synth.spectrum("pow2_half", 200), 1).numpy()
+    _, _, info, _ = run_and_check(gbid, A, 20, torch.float64, nb=nb)
+    assert info["rank"] == 20
+    assert info["nb"] == (20 if nb == 0 else nb)
+
+
+def test_lowrank_200x400_k20_f32(gbid):
+    A = synth.lowrank(200, 400, synth.spectrum("pow2_half", 200), 1).numpy()
+    run_and_check(gbid, A, 20, torch.float32)
+
+
+# ------------------------------------------- ragged, multi-tile, odd shapes ---
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("shape,k,nb", [
+    ((333, 517), 37, 0), ((333, 517), 37, 5), ((333, 517), 37, 16),
+    ((37, 1000), 10, 0), ((1, 7), 1, 0), ((5, 9), 5, 0), ((64, 96), 64, 0), ((48, 48), 48, 7),
+    ((517, 333), 29, 0), ((1000, 37), 12, 4), ((257, 1031), 64, 32),
+])
+def test_shapes(gbid, dtype, shape, k, nb):
+    rng = np.random.default_rng(hash((shape, k, nb)) % 2**32)
+    m, n = shape
+    r = min(m, n)
+    s = np.exp(-np.arange(r) / max(1.0, r / 6.0))
+    A = synth.lowrank(m, n, s, 40 + k).numpy() * rng.uniform(0.5, 2.0)
+    run_and_check(gbid, A, k, dtype, nb=nb)
+
+
+def test_leading_dimension_padding(gbid):
+    A = synth.lowrank(120, 250, np.exp(-np.arange(120) / 10.0), 9).numpy()
+    run_and_check(gbid, A, 15, torch.float64, lda_pad=13)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_exact_rank_reconstruction(gbid, dtype):
+    A = synth.lowrank(300, 600, synth.spectrum("exp64", 300, rank=40), 7).numpy()
+    run_and_check(gbid, A, 40, dtype, exact_rank=True)
+
+
+def test_lazy_vs_blocked_agree(gbid):
+    A = torch.as_tensor(synth.lowrank(260, 700, np.exp(-np.arange(260) / 40.0), 5).numpy()).cuda()
+    J1, Z1, _ = gbid.id_decompose(A, 60, nb=60)
+    J2, Z2, _ = gbid.id_decompose(A, 60, nb=16)
+    assert torch.equal(J1, J2)
+    assert (torch.linalg.norm(Z1 - Z2) / torch.linalg.norm(Z1)).item() < 1e-12
+
+
+def test_deterministic(gbid):
+    A = torch.as_tensor(synth.lowrank(300, 500, np.exp(-np.arange(300) / 30.0), 6).numpy()).cuda()
+    J1, Z1, _ = gbid.id_decompose(A, 50)
+    J2, Z2, _ = gbid.id_decompose(A, 50)
+    assert torch.equal(J1, J2) and torch.equal(Z1, Z2)
+
+
+# --------------------------------------------------------- degenerate inputs ---
+def test_ties_and_zero_columns(gbid):
+    rng = np.random.default_rng(21)
+    A = rng.standard_normal((40, 90))
+    A[:, 10] = 0.0
+    A[:, 33] = 0.0
+    A[:, 50] = A[:, 7]          # duplicate column: exact tie, smaller index first
+    A[:, 60] = -A[:, 7]
+    run_and_check(gbid, A, 25, torch.float64)
+
+
+def test_rank_deficient_status(gbid):
+    A = synth.lowrank(60, 100, synth.spectrum("exp64", 60, rank=9), 8).numpy()
+    J, Z, info = gbid.id_decompose(torch.as_tensor(A).cuda(), 15)
+    _, _, oinfo = orc.interp_decomp(A, 15)
+    assert info["status"] == gbid.ID_RANK_DEFICIENT
+    assert info["rank"] == oinfo["rank"] == 9
+    assert np.array_equal(J.cpu().numpy()[:9], orc.interp_decomp(A, 15)[0][:9])
+
+
+def test_all_zero_matrix(gbid):
+    J, Z, info = gbid.id_decompose(torch.zeros(20, 30, dtype=torch.float64, device="cuda"), 5)
+    assert info["status"] == gbid.ID_RANK_DEFICIENT and info["rank"] == 0
+    assert J.cpu().tolist() == [0, 1, 2, 3, 4]
+
+
+@pytest.mark.parametrize("bad", [float("nan"), float("inf")])
+def test_non_finite_input(gbid, bad):
+    A = torch.randn(30, 50, dtype=torch.float64)
+    A[3, 17] = bad
+    _, _, info = gbid.id_decompose(A.cuda(), 5)
+    assert info["status"] == gbid.ID_ENONFINITE
+
+
+def test_paper_boolean_dataset_ties(gbid):
+    A = synth.paper_dataset("boolean", seed=5, m=60, n=80)
+    run_and_check(gbid, A, 20, torch.float64)
+
+
+@pytest.mark.parametrize("name,e_id", [("boolean", 0.553), ("gaussian", 0.776), ("uniform", 0.390)])
+def test_paper_table_statistics_on_gpu(gbid, name, e_id):
+    """Table 2 (rank-190 ID error) and Table 1 (max |Z| = 1) on the GPU path."""
+    A = synth.paper_dataset(name, seed=2021)
+    _, _, info, _ = run_and_check(gbid, A, 190, torch.float64)
+    J, Z, _ = gbid.id_decompose(torch.as_tensor(A).cuda(), 190)
+    err = orc.rel_error(A, J.cpu().numpy(), Z.cpu().numpy())
+    assert err == pytest.approx(e_id, abs=0.005)
+    assert info["max_abs_z"] <= 1.0 + 1e-9
+
+
+# ------------------------------------------------------ lower-level calls ---
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_cpqr_and_solve_entry_points(gbid, dtype):
+    A = synth.lowrank(150, 260, np.exp(-np.arange(150) / 12.0), 3).numpy()
+    m, n, k = 150, 260, 24
+    ldx = 152
+    Xcm = torch.zeros(n, ldx, dtype=dtype)
+    Xcm[:, :m] = torch.as_tensor(A.T).to(dtype)
+    Xd = Xcm.cuda()
+    perm, tau, info = gbid.id_cpqr(Xd, m, k)
+    A_exact = torch.as_tensor(A).to(dtype).double().numpy()
+    f = orc.cpqr(A_exact, k)
+    pg = perm.cpu().numpy()
+    assert np.array_equal(pg[:k], f["perm"][:k])
+    assert sorted(pg.tolist()) == list(range(n))
+    R = Xd.cpu().double().numpy().T[:k, :]
+    tol = 1e-12 if dtype == torch.float64 else 1e-5
+    assert np.allclose(np.abs(np.diag(R[:, :k])), f["nu"], rtol=tol * 100)
+    Rg = np.triu(R)
+    Ro = np.triu(f["F"][:k, :])
+    assert np.linalg.norm(Rg - Ro) / np.linalg.norm(Ro) < tol * 100
+    assert np.allclose(tau.cpu().numpy(), f["tau"], rtol=tol * 1e3, atol=tol)
+    T = gbid.id_solve(Xd, k).cpu().numpy()
+    To = orc.back_substitute(Ro[:, :k], Ro[:, k:])
+    assert np.linalg.norm(T - To) / np.linalg.norm(To) < TOL_Z[dtype]
+
+
+def test_host_buffers_entry_point(gbid):
+    A = synth.lowrank(200, 400, synth.spectrum("pow2_half", 200), 1)
+    Ah = A.pin_memory()
+    J, Z, info = gbid.id_decompose_host(Ah, 20)
+    Jd, Zd, _ = gbid.id_decompose(A.cuda(), 20)
+    assert torch.equal(J, Jd.cpu()) and torch.equal(Z, Zd.cpu())
+
+
+# ---------------------------------------------- full size, sampled checks ---
+@pytest.fixture(scope="module")
+def c2_inputs():
+    m, n = 4096, 8192
+    A = synth.lowrank(m, n, synth.spectrum("exp64", m), 2, device="cuda")
+    Ar = synth.lowrank(m, n, synth.spectrum("exp64", m, rank=256), 2, device="cuda")
+    return A, Ar
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_full_size_4096x8192_k256(gbid, c2_inputs, dtype):
+    """Same launch configuration as the bench; sampled oracle checks."""
+    A64, _ = c2_inputs
+    A = A64.to(dtype)
+    k = 256
+    J, Z, info = gbid.id_decompose(A, k)
+    assert info["status"] == gbid.ID_OK and info["rank"] == k
+    Ah = A.double().cpu().numpy()
+    Jg = J.cpu().numpy().astype(np.int64)
+    Zg = Z.double().cpu().numpy()
+    assert len(set(Jg.tolist())) == k
+    assert np.array_equal(Zg[:, Jg], np.eye(k))
+    # first 6 pivots replayed by the oracle's exact greedy rule
+    ok, worst = orc.verify_pivots(Ah, Jg[:6], tol_piv(dtype, 4096))
+    assert ok, worst
+    # 24 sampled columns of Z against the oracle's least-squares Z for J_gpu
+    rng = np.random.default_rng(0)
+    rest = np.setdiff1d(np.arange(8192), Jg)
+    cols = rng.choice(rest, 24, replace=False)
+    C = Ah[:, Jg]
+    Zs, *_ = np.linalg.lstsq(C, Ah[:, cols], rcond=None)
+    rel = np.linalg.norm(Zg[:, cols] - Zs) / np.linalg.norm(Zs)
+    assert rel <= TOL_Z[dtype], rel
+    # error between the Eckart-Young floor and a small multiple of it
+    err = np.linalg.norm(Ah - C @ Zg) / np.linalg.norm(Ah)
+    tail = synth.tail_bound(synth.spectrum("exp64", 4096), k)
+    assert tail * (1 - 1e-6) <= err <= 3.0 * tail, (err, tail)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_full_size_exact_rank_256(gbid, c2_inputs, dtype):
+    _, Ar64 = c2_inputs
+    A = Ar64.to(dtype)
+    J, Z, info = gbid.id_decompose(A, 256)
+    Ah = A.double().cpu().numpy()
+    Jg = J.cpu().numpy().astype(np.int64)
+    Zg = Z.double().cpu().numpy()
+    err = np.linalg.norm(Ah - Ah[:, Jg] @ Zg) / np.linalg.norm(Ah)
+    assert err <= (1e-12 if dtype == torch.float64 else 1e-5), err
