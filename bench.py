@@ -32,7 +32,6 @@ M, N, K_RANK = 4096, 8192, 256
 WORKLOAD = "id_4096x8192_k256"
 METRIC = "IDs/s and effective TFLOP/s at stated rel. Frobenius error vs FP64 plain ID"
 UNIT = "IDs/s"
-ORACLE_SAMPLE_STEPS = 12       # pivot steps of the oracle timed for the CPU baseline
 REF_SAMPLE_STEPS = 4           # pivot steps per --impl reference step
 
 
@@ -150,24 +149,30 @@ from oracle import id_oracle as orc
 A = np.load(sys.argv[2])
 s = int(sys.argv[3])
 reps = int(sys.argv[4])
+full = sys.argv[5] == "full"
 out = []
 for _ in range(reps):
     t0 = time.perf_counter()
-    orc.cpqr(A, s)
+    if full:
+        orc.interp_decomp(A, s)
+    else:
+        orc.cpqr(A, s)
     out.append(time.perf_counter() - t0)
 print(json.dumps(out))
 """
 
 
-def time_oracle(A_cpu_np, steps, reps):
-    """Seconds per call of the oracle's first `steps` pivot steps, single-threaded, in a fresh process."""
+def time_oracle(A_cpu_np, steps, reps, full=False):
+    """Seconds per call of the oracle (its first `steps` pivot steps, or a whole rank-`steps` ID
+    when `full`), single-threaded, in a fresh process."""
     import numpy as np
 
     with tempfile.TemporaryDirectory() as d:
         path = os.path.join(d, "A.npy")
         np.save(path, A_cpu_np)
         env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-        r = subprocess.run([sys.executable, "-c", ORACLE_SNIPPET, ROOT, path, str(steps), str(reps)],
+        r = subprocess.run([sys.executable, "-c", ORACLE_SNIPPET, ROOT, path, str(steps), str(reps),
+                            "full" if full else "steps"],
                            capture_output=True, text=True, env=env, timeout=1800)
         if r.returncode != 0:
             raise RuntimeError(r.stderr[-2000:])
@@ -342,10 +347,10 @@ def run_gbid(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         A_np = results["f64"]["A"].cpu().numpy()
-        secs = time_oracle(A_np, ORACLE_SAMPLE_STEPS, 1)
-        cpu = {"value": oracle_ids_per_s(secs[0], ORACLE_SAMPLE_STEPS), "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"first {ORACLE_SAMPLE_STEPS} of {K_RANK} pivot steps of the FP64 oracle on the same "
-                         f"matrix ({secs[0]:.1f} s), extrapolated to a full ID by the CPQR flop count"}
+        secs = time_oracle(A_np, K_RANK, 1, full=True)
+        cpu = {"value": 1.0 / secs[0], "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"one complete rank-{K_RANK} ID of the same 4096 x 8192 FP64 matrix by the oracle "
+                         f"({secs[0]:.1f} s, numpy, one thread)"}
     if world > 1 and dist.is_initialized():
         dist.barrier()
     if rank != 0:

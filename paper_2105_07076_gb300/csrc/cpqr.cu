@@ -78,6 +78,20 @@ __device__ double block_sum(double v) {
     return warp_sum(v);
 }
 
+// Deterministic block sum in the working precision.
+template <typename T>
+__device__ T block_sum_t(T v) {
+    __shared__ T red_t[32];
+    v = warp_sum(v);
+    const int w = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
+    const int nw = blockDim.x / kWarp;
+    __syncthreads();
+    if (lane == 0) red_t[w] = v;
+    __syncthreads();
+    v = lane < nw ? red_t[lane] : T(0);
+    return warp_sum(v);
+}
+
 // ------------------------------------------------------------------ copy-in --
 // X (m x n, m <= n) into column-major W. trans == 0: X(i,l) = A[i*lda + l]
 // (A is m x n row-major). trans == 1: X(i,l) = A[l*lda + i] (A is the user's
@@ -182,13 +196,13 @@ __device__ __forceinline__ ArgMax ld_argmax(const ArgMax* p) {
 // VN consecutive entries of the reflector v = x * scale (v_j = 1, zero outside
 // rows j..m-1), rebuilt from the pivot column when v is not cached.
 template <typename T, typename V, int VN>
-__device__ __forceinline__ V v_at(const T* xbuf, int i, int j, int m, double scale) {
+__device__ __forceinline__ V v_at(const T* xbuf, int i, int j, int m, T scale) {
     V out;
     T* o = reinterpret_cast<T*>(&out);
 #pragma unroll
     for (int q = 0; q < VN; ++q) {
         const int ii = i + q;
-        o[q] = ii < j || ii >= m ? T(0) : (ii == j ? T(1) : (T)((double)__ldcg(xbuf + ii) * scale));
+        o[q] = ii < j || ii >= m ? T(0) : (ii == j ? T(1) : __ldcg(xbuf + ii) * scale);
     }
     return out;
 }
@@ -453,9 +467,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
             __syncthreads();
         }
         const double beta = sc[0], tau = sc[1], scale = sc[2];
+        // v = x * scale in the working precision, formed identically wherever it is
+        // needed (FP64 arithmetic is scarce on this GPU: no conversions here in FP32)
+        const T scaleT = (T)scale;
         // v on this CTA's rows into W(:, j) (reflector storage, v_j = 1 implicit)
         for (int r = max(r0, j) + t; r < r1; r += kThreads)
-            W[(int64_t)j * ldw + r] = r == j ? (T)beta : (T)((double)ld(xbuf + r) * scale);
+            W[(int64_t)j * ldw + r] = r == j ? (T)beta : ld(xbuf + r) * scaleT;
 
         // ---- B2: aux = -tau V(j:m, 0:jj)^T v, one CTA per panel column
         for (int c = blockIdx.x; c < jj; c += G) {
@@ -471,11 +488,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
                     vs4[u] = ii < m ? ld(vc + ii) : T(0);
                 }
 #pragma unroll
-                for (int u = 0; u < 4; ++u) acc += vs4[u] * (T)((double)xs[u] * scale);
+                for (int u = 0; u < 4; ++u) acc += vs4[u] * (xs[u] * scaleT);
             }
-            const double tot = block_sum((double)acc);
+            const T tot = block_sum_t(acc);
             if (t == 0) {
-                aux[c] = (T)(-tau * tot);
+                aux[c] = -(T)tau * tot;
                 __threadfence();
                 red_release_add(P.auxcnt + j, 1u);
             }
@@ -488,7 +505,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
             for (int c = t; c < jj; c += kThreads) vrow_s[c] = ld(W + (int64_t)(j0 + c) * ldw + j);
             if (kSmemV)
                 for (int i = j_al + t; i < m_pad; i += kThreads)
-                    v_s[i - j_al] = i < j || i >= m ? T(0) : (i == j ? T(1) : (T)((double)ld(xbuf + i) * scale));
+                    v_s[i - j_al] = i < j || i >= m ? T(0) : (i == j ? T(1) : ld(xbuf + i) * scaleT);
             __syncthreads();
             const T tauT = (T)tau;
             const int ncols = n - j - 1;
@@ -537,7 +554,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
                         const int i = i0 + u * S;
                         if (i < m_pad) {
                             const V yv = kSmemV ? *reinterpret_cast<const V*>(v_s + (i - j_al))
-                                                : v_at<T, V, VN>(xbuf, i, j, m, scale);
+                                                : v_at<T, V, VN>(xbuf, i, j, m, scaleT);
                             if (u % 4 == 0) a0 = dot_vec(xv[u], yv, a0);
                             else if (u % 4 == 1) a1 = dot_vec(xv[u], yv, a1);
                             else if (u % 4 == 2) a2 = dot_vec(xv[u], yv, a2);
@@ -609,7 +626,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
                         T y = ld(col + i);
                         for (int c = 0; c < jj; ++c) y -= ld(W + (int64_t)(j0 + c) * ldw + i) * ld(frow + c);
                         // the current reflector (other CTAs may still be writing it to W(:, j))
-                        const T vi = kSmemV ? v_s[i - j_al] : (T)((double)ld(xbuf + i) * scale);
+                        const T vi = kSmemV ? v_s[i - j_al] : ld(xbuf + i) * scaleT;
                         y -= vi * f;
                         sacc = fma((double)y, (double)y, sacc);
                     }
