@@ -114,6 +114,27 @@ int id_decompose_host(const void* A_host, id_dtype dtype, int64_t m, int64_t n, 
                       const id_opts* opts, int32_t* J_host, void* Z_host, int64_t ldz,
                       void* work, size_t work_bytes, id_info* info, void* stream);
 
+/* id_decompose_noalloc -- id_decompose for callers that cannot allocate
+ * device memory (for example code running while a global-mode stream capture
+ * is active, plug-ins whose host framework owns all device memory, real-time
+ * loops that must not take allocator locks). It takes no workspace: the
+ * scratch is a fixed array of ID_NOALLOC_SCRATCH_BYTES inside the library,
+ * which every GPU that loads the library keeps until the process exits. The
+ * paper has no counterpart; this is a deployment convenience.
+ *
+ *   Arguments as for id_decompose, minus work/work_bytes.
+ *   Returns ID_ENOMEM, before enqueuing anything, when
+ *   id_workspace_size(dtype, m, n, k, opts) > ID_NOALLOC_SCRATCH_BYTES.
+ *   The first call on a device looks up the array's device address (with that
+ *   device current); make that first call before any stream capture.
+ *   All calls share the one array: calls that may overlap on the GPU (other
+ *   streams, other host threads) race on it and must be serialised by the
+ *   caller. Each call re-initialises the state it needs, so the contents left
+ *   by an earlier call do not matter. Calls no allocating routine. */
+#define ID_NOALLOC_SCRATCH_BYTES (32u << 20)
+int id_decompose_noalloc(const void* A, id_dtype dtype, int64_t m, int64_t n, int64_t lda, int64_t k,
+                         const id_opts* opts, int32_t* J, void* Z, int64_t ldz, id_info* info, void* stream);
+
 /* Bytes of device workspace id_cpqr needs (its X, perm and tau belong to the
  * caller and are not counted). Returns 0 for invalid arguments. */
 size_t id_cpqr_workspace_size(id_dtype dtype, int64_t m, int64_t n, int64_t ldx, int64_t k, const id_opts* opts);

@@ -78,6 +78,7 @@ _SIG = {
     "id_cpqr": (ctypes.c_int, [_P, ctypes.c_int, _I64, _I64, _I64, _I64, _P, _P, _P, _P, ctypes.c_size_t, _P, _P]),
     "id_solve": (ctypes.c_int, [_P, ctypes.c_int, _I64, _I64, _I64, _P, _I64, _P]),
     "id_info_read": (ctypes.c_int, [_P, _P, _P]),
+    "id_decompose_noalloc": (ctypes.c_int, [_P, ctypes.c_int, _I64, _I64, _I64, _I64, _P, _P, _P, _I64, _P, _P]),
     "id_launch_count": (ctypes.c_int64, [ctypes.c_int, _I64, _I64, _I64, _P]),
     "id_trace_enable": (ctypes.c_int, [ctypes.c_int]),
     "id_trace_read": (ctypes.c_int, [_P, _P, ctypes.c_int]),
@@ -177,6 +178,30 @@ def id_decompose(A: torch.Tensor, k: int, *, nb: int = 0, workspace: Workspace |
     if rc in _CALL_ERRORS:
         raise IdError(rc, "id_decompose")
     return J, Z, (info.as_dict() if sync else None)
+
+
+NOALLOC_SCRATCH_BYTES = 32 << 20   # ID_NOALLOC_SCRATCH_BYTES in gbid.h
+
+
+def id_decompose_noalloc(A: torch.Tensor, k: int, *, nb: int = 0, out: tuple | None = None):
+    """The ID with the library's fixed scratch instead of a workspace, for callers that
+    cannot allocate device memory (only J and Z are allocated here, unless ``out`` is given)."""
+    _check_cuda_matrix(A, "A")
+    m, n = A.shape
+    dev = A.device
+    if out is None:
+        J = torch.empty(k, dtype=torch.int32, device=dev)
+        Z = torch.empty(k, max(m, n), dtype=A.dtype, device=dev)
+    else:
+        J, Z = out
+    o = _opts(nb)
+    info = IdInfo()
+    with torch.cuda.device(dev):
+        rc = lib().id_decompose_noalloc(A.data_ptr(), _DTYPES[A.dtype], m, n, A.stride(0), k, ctypes.byref(o),
+                                        J.data_ptr(), Z.data_ptr(), Z.stride(0), ctypes.byref(info), _stream(dev))
+    if rc in _CALL_ERRORS:
+        raise IdError(rc, "id_decompose_noalloc")
+    return J, Z, info.as_dict()
 
 
 def read_info(workspace: Workspace) -> dict:
