@@ -514,6 +514,67 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
             ArgMax bestc = empty_argmax();
             bool aux_ready = false;
             T auxr[kFRegs];                  // aux[lane + 32 q], loaded once the counter says it is complete
+            // Epilogues are batched: lane q owns the q-th finished column of the
+            // current batch, so the FP64 downdate of 32 columns is one pass of
+            // full-warp FP64 instructions instead of 32 single-lane ones.
+            int nbat = 0;                    // columns in the batch (warp-uniform)
+            int b_l = -1, b_orig = 0;
+            T b_r = T(0), b_f = T(0);
+            double b_nu = 0.0, b_nu2 = 1.0;
+            auto flush = [&]() {
+                int flagged = 0;
+                if (lane < nbat) {
+                    ArgMax cnd;
+                    cnd.orig = b_orig;
+                    cnd.pos = b_l;
+                    cnd.val = 0.0;
+                    if (b_nu != 0.0) {
+                        const double q = fabs((double)b_r) / b_nu;
+                        double temp = (1.0 - q) * (1.0 + q);
+                        temp = temp > 0.0 ? temp : 0.0;
+                        const double ratio = b_nu / b_nu2;
+                        if (temp * ratio * ratio <= tol3z) {
+                            flagged = 1;
+                        } else {
+                            cnd.val = b_nu * sqrt(temp);
+                            P.vn1[b_l] = cnd.val;
+                        }
+                    }
+                    if (!flagged && better(cnd, bestc)) bestc = cnd;
+                }
+                unsigned fm = __ballot_sync(0xffffffffu, flagged);
+                while (fm) {
+                    // cancellation: exact ||W(j+1:m, l) - V F(l, 0:jj+1)^T|| by the whole warp
+                    const int src = __ffs(fm) - 1;
+                    fm &= fm - 1;
+                    const int l = __shfl_sync(0xffffffffu, b_l, src);
+                    const T f = __shfl_sync(0xffffffffu, b_f, src);
+                    const T* frow = F + (int64_t)((l == p && p != j) ? j : l) * ldf;
+                    const T* col = W + (int64_t)l * ldw;
+                    double sacc = 0.0;
+                    for (int i = j + 1 + lane; i < m; i += kWarp) {
+                        T y = ld(col + i);
+                        for (int c = 0; c < jj; ++c) y -= ld(W + (int64_t)(j0 + c) * ldw + i) * ld(frow + c);
+                        // the current reflector (other CTAs may still be writing it to W(:, j))
+                        const T vi = kSmemV ? v_s[i - (j & ~(VN - 1))] : ld(xbuf + i) * scaleT;
+                        y -= vi * f;
+                        sacc = fma((double)y, (double)y, sacc);
+                    }
+                    sacc = warp_sum(sacc);
+                    if (lane == src) {
+                        const double nv = sqrt(sacc);
+                        P.vn1[l] = nv;
+                        P.vn2[l] = nv;
+                        ArgMax cnd;
+                        cnd.val = nv;
+                        cnd.orig = b_orig;
+                        cnd.pos = l;
+                        if (better(cnd, bestc)) bestc = cnd;
+                        atomicAdd(&st->n_recompute, 1);
+                    }
+                }
+                nbat = 0;
+            };
             int idx = 0;
             if (lane == 0) idx = atomicAdd(ctr, 1);
             idx = __shfl_sync(0xffffffffu, idx, 0);
@@ -523,14 +584,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
                 if (lane == 0) nidx = atomicAdd(ctr, 1);   // next column, in flight meanwhile
                 const bool moved = l == p && p != j;        // column p carries the old column j's F row
                 const T* frow = F + (int64_t)(moved ? j : l) * ldf;
+                const int slot = nbat;
                 T wjl = T(0);
-                double nu = 0.0, nu2 = 1.0;
-                int orig = 0;
-                if (lane == 0) {
+                if (lane == slot) {                         // this column's epilogue operands
+                    b_l = l;
                     wjl = ld(W + (int64_t)l * ldw + j);
-                    nu = ld(P.vn1 + l);
-                    nu2 = ld(P.vn2 + l);
-                    orig = ld(P.perm + l);
+                    b_nu = ld(P.vn1 + l);
+                    b_nu2 = ld(P.vn2 + l);
+                    b_orig = ld(P.perm + l);
                 }
                 T fr[kFRegs];
 #pragma unroll
@@ -594,57 +655,17 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
                 s1 = warp_sum(s1);
                 s2 = warp_sum(s2);
                 const T f = tauT * g + s1;
-                int flagged = 0;
-                if (lane == 0) {
+                if (lane == slot) {
+                    b_f = f;
+                    b_r = wjl - s2 - f;                     // R(j, l)
                     F[(int64_t)l * ldf + jj] = f;
-                    const T rjl = wjl - s2 - f;
-                    W[(int64_t)l * ldw + j] = rjl;
-                    ArgMax cnd;
-                    cnd.orig = orig;
-                    cnd.pos = l;
-                    cnd.val = 0.0;
-                    if (nu != 0.0) {
-                        const double q = fabs((double)rjl) / nu;
-                        double temp = (1.0 - q) * (1.0 + q);
-                        temp = temp > 0.0 ? temp : 0.0;
-                        const double ratio = nu / nu2;
-                        if (temp * ratio * ratio <= tol3z) {
-                            flagged = 1;
-                        } else {
-                            cnd.val = nu * sqrt(temp);
-                            P.vn1[l] = cnd.val;
-                        }
-                    }
-                    if (!flagged && better(cnd, bestc)) bestc = cnd;
+                    W[(int64_t)l * ldw + j] = b_r;
                 }
-                flagged = __shfl_sync(0xffffffffu, flagged, 0);
-                if (flagged) {
-                    // cancellation: exact ||W(j+1:m, l) - V F(l, 0:jj+1)^T|| by this warp
-                    orig = __shfl_sync(0xffffffffu, orig, 0);
-                    double sacc = 0.0;
-                    for (int i = j + 1 + lane; i < m; i += kWarp) {
-                        T y = ld(col + i);
-                        for (int c = 0; c < jj; ++c) y -= ld(W + (int64_t)(j0 + c) * ldw + i) * ld(frow + c);
-                        // the current reflector (other CTAs may still be writing it to W(:, j))
-                        const T vi = kSmemV ? v_s[i - j_al] : ld(xbuf + i) * scaleT;
-                        y -= vi * f;
-                        sacc = fma((double)y, (double)y, sacc);
-                    }
-                    sacc = warp_sum(sacc);
-                    if (lane == 0) {
-                        const double nv = sqrt(sacc);
-                        P.vn1[l] = nv;
-                        P.vn2[l] = nv;
-                        ArgMax cnd;
-                        cnd.val = nv;
-                        cnd.orig = orig;
-                        cnd.pos = l;
-                        if (better(cnd, bestc)) bestc = cnd;
-                        atomicAdd(&st->n_recompute, 1);
-                    }
-                }
+                ++nbat;
                 idx = __shfl_sync(0xffffffffu, nidx, 0);
+                if (nbat == kWarp || idx >= ncols) flush();
             }
+            if (nbat > 0) flush();   // only reached after a timed-out wait
             bestc = block_argmax(bestc);
             if (t == 0) P.part[blockIdx.x] = bestc;
         }
