@@ -193,16 +193,16 @@ __device__ __forceinline__ ArgMax ld_argmax(const ArgMax* p) {
     return a;
 }
 
-// VN consecutive entries of the reflector v = x * scale (v_j = 1, zero outside
-// rows j..m-1), rebuilt from the pivot column when v is not cached.
+// VN consecutive entries of the pivot column x restricted to rows j+1..m-1
+// (zero elsewhere), read from global memory when it is not cached.
 template <typename T, typename V, int VN>
-__device__ __forceinline__ V v_at(const T* xbuf, int i, int j, int m, T scale) {
+__device__ __forceinline__ V x_at(const T* xbuf, int i, int j, int m) {
     V out;
     T* o = reinterpret_cast<T*>(&out);
 #pragma unroll
     for (int q = 0; q < VN; ++q) {
         const int ii = i + q;
-        o[q] = ii < j || ii >= m ? T(0) : (ii == j ? T(1) : __ldcg(xbuf + ii) * scale);
+        o[q] = ii <= j || ii >= m ? T(0) : __ldcg(xbuf + ii);
     }
     return out;
 }
@@ -222,7 +222,6 @@ struct KParams {
     void* aux;        // kMaxPanel
     unsigned* bar;    // grid-barrier arrival counter, zero on entry
     unsigned* auxcnt; // k per-step counters of finished aux entries, zero on entry
-    int* ctr;         // k + 1 column-queue counters, zero on entry
     State* st;
     double rank_tol;
     int rows_per_cta; // row chunk of the pivot-column phase (multiple of 32)
@@ -319,6 +318,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
     __shared__ T wy_s[16 * 64 + 16 * 65];              // WY-update tiles
     __shared__ T red[NW][kWarp];
     __shared__ double sc[4];
+    __shared__ int qctr;   // column queue of this CTA
 
     T* W = static_cast<T*>(P.W);
     T* F = static_cast<T*>(P.F);
@@ -367,6 +367,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
     const int RC = P.rows_per_cta;
     const int r0 = blockIdx.x * RC;
     const int r1 = min(r0 + RC, m);
+    double r00 = 0.0;   // |R_00| (thread 0)
 
     for (int j = 0; j < P.k; ++j) {
         if (timed_out(st)) break;
@@ -441,9 +442,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
         {
             double s = 0.0;
             for (int e = t; e < G; e += kThreads) s += ld(P.ssq + e);
+            if (t == kThreads - 1) sc[3] = ld(&st->x0);   // visible after block_sum's barriers
             s = block_sum(s);
             if (t == 0) {
-                const double x0 = ld(&st->x0);
+                const double x0 = sc[3];
                 const double alpha = sqrt(fma(x0, x0, s));
                 double beta = 0.0, tau = 0.0, scale = 0.0;
                 if (alpha != 0.0) {
@@ -454,12 +456,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
                 sc[0] = beta;
                 sc[1] = tau;
                 sc[2] = scale;
+                if (j == 0) r00 = fabs(beta);     // |R_00|, identical in every CTA
                 if (blockIdx.x == 0) {
                     st->beta = beta;
                     st->tau = tau;
                     P.tau[j] = tau;
-                    if (j == 0) st->r00 = fabs(beta);
-                    const double r00 = j == 0 ? fabs(beta) : ld(&st->r00);
+                    if (j == 0) st->r00 = r00;
                     if (r00 == 0.0 || fabs(beta) <= P.rank_tol * r00) atomicMin(&st->rank, j);
                     if (!isfinite(beta)) atomicOr(&st->status, kStatNonFinite);
                 }
@@ -467,8 +469,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
             __syncthreads();
         }
         const double beta = sc[0], tau = sc[1], scale = sc[2];
-        // v = x * scale in the working precision, formed identically wherever it is
-        // needed (FP64 arithmetic is scarce on this GPU: no conversions here in FP32)
+        // v = x * scale (v_j = 1) in the working precision. The stored reflector
+        // is formed elementwise; the products with v below use
+        // v^T y = scale * x(j+1:m)^T y(j+1:m) + y_j, so no per-element scaling
+        // (and no FP64 conversion in FP32) is needed on the hot loops.
         const T scaleT = (T)scale;
         // v on this CTA's rows into W(:, j) (reflector storage, v_j = 1 implicit)
         for (int r = max(r0, j) + t; r < r1; r += kThreads)
@@ -478,7 +482,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
         for (int c = blockIdx.x; c < jj; c += G) {
             const T* vc = W + (int64_t)(j0 + c) * ldw;
             T acc = T(0);
-            if (t == 0) acc = ld(vc + j);   // v_j = 1
             for (int i = j + 1 + t; i < m; i += 4 * kThreads) {
                 T xs[4], vs4[4];
 #pragma unroll
@@ -488,11 +491,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
                     vs4[u] = ii < m ? ld(vc + ii) : T(0);
                 }
 #pragma unroll
-                for (int u = 0; u < 4; ++u) acc += vs4[u] * (xs[u] * scaleT);
+                for (int u = 0; u < 4; ++u) acc += vs4[u] * xs[u];
             }
             const T tot = block_sum_t(acc);
             if (t == 0) {
-                aux[c] = -(T)tau * tot;
+                aux[c] = -(T)tau * (scaleT * tot + ld(vc + j));   // V(:, c)^T v with v_j = 1
                 __threadfence();
                 red_release_add(P.auxcnt + j, 1u);
             }
@@ -505,12 +508,21 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
             for (int c = t; c < jj; c += kThreads) vrow_s[c] = ld(W + (int64_t)(j0 + c) * ldw + j);
             if (kSmemV)
                 for (int i = j_al + t; i < m_pad; i += kThreads)
-                    v_s[i - j_al] = i < j || i >= m ? T(0) : (i == j ? T(1) : ld(xbuf + i) * scaleT);
+                    v_s[i - j_al] = i <= j || i >= m ? T(0) : ld(xbuf + i);
+            if (t == 0) qctr = 0;
             __syncthreads();
             const T tauT = (T)tau;
             const int ncols = n - j - 1;
-            const bool rev = (j & 1) != 0;   // alternate sweep direction: the last columns read stay in L2
-            int* ctr = P.ctr + j;
+            // Each CTA owns a contiguous, balanced range of trailing columns (so
+            // every SM gets the same work) and its warps share it through a
+            // shared-memory counter. The sweep direction alternates every step:
+            // the columns a CTA reads last in step j it reads first in step j+1,
+            // while they are still in L2.
+            const bool rev = (j & 1) != 0;
+            const int per = ncols / G, rem = ncols % G;
+            const int c_lo = blockIdx.x * per + min((int)blockIdx.x, rem);
+            const int c_cnt = per + ((int)blockIdx.x < rem ? 1 : 0);
+            int* ctr = &qctr;
             ArgMax bestc = empty_argmax();
             bool aux_ready = false;
             T auxr[kFRegs];                  // aux[lane + 32 q], loaded once the counter says it is complete
@@ -556,7 +568,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
                         T y = ld(col + i);
                         for (int c = 0; c < jj; ++c) y -= ld(W + (int64_t)(j0 + c) * ldw + i) * ld(frow + c);
                         // the current reflector (other CTAs may still be writing it to W(:, j))
-                        const T vi = kSmemV ? v_s[i - (j & ~(VN - 1))] : ld(xbuf + i) * scaleT;
+                        const T vi = ld(xbuf + i) * scaleT;
                         y -= vi * f;
                         sacc = fma((double)y, (double)y, sacc);
                     }
@@ -578,8 +590,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
             int idx = 0;
             if (lane == 0) idx = atomicAdd(ctr, 1);
             idx = __shfl_sync(0xffffffffu, idx, 0);
-            while (idx < ncols) {
-                const int l = rev ? n - 1 - idx : j + 1 + idx;
+            while (idx < c_cnt) {
+                const int l = j + 1 + c_lo + (rev ? c_cnt - 1 - idx : idx);
                 int nidx = 0;
                 if (lane == 0) nidx = atomicAdd(ctr, 1);   // next column, in flight meanwhile
                 const bool moved = l == p && p != j;        // column p carries the old column j's F row
@@ -615,7 +627,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
                         const int i = i0 + u * S;
                         if (i < m_pad) {
                             const V yv = kSmemV ? *reinterpret_cast<const V*>(v_s + (i - j_al))
-                                                : v_at<T, V, VN>(xbuf, i, j, m, scaleT);
+                                                : x_at<T, V, VN>(xbuf, i, j, m);
                             if (u % 4 == 0) a0 = dot_vec(xv[u], yv, a0);
                             else if (u % 4 == 1) a1 = dot_vec(xv[u], yv, a1);
                             else if (u % 4 == 2) a2 = dot_vec(xv[u], yv, a2);
@@ -651,11 +663,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
                     s1 += fv * ld(aux + c);
                     s2 += fv * vrow_s[c];
                 }
-                const T g = warp_sum((a0 + a1) + (a2 + a3));
+                const T gx = warp_sum((a0 + a1) + (a2 + a3));   // x(j+1:m)^T W(j+1:m, l)
                 s1 = warp_sum(s1);
                 s2 = warp_sum(s2);
-                const T f = tauT * g + s1;
                 if (lane == slot) {
+                    const T g = scaleT * gx + wjl;          // v^T W(j:m, l)
+                    const T f = tauT * g + s1;
                     b_f = f;
                     b_r = wjl - s2 - f;                     // R(j, l)
                     F[(int64_t)l * ldf + jj] = f;
@@ -663,7 +676,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
                 }
                 ++nbat;
                 idx = __shfl_sync(0xffffffffu, nidx, 0);
-                if (nbat == kWarp || idx >= ncols) flush();
+                if (nbat == kWarp || idx >= c_cnt) flush();
             }
             if (nbat > 0) flush();   // only reached after a timed-out wait
             bestc = block_argmax(bestc);
@@ -769,7 +782,6 @@ cudaError_t cpqr_run(const CpqrPlan& P, cudaStream_t s) {
     char* sync = reinterpret_cast<char*>(P.sync);
     K.bar = reinterpret_cast<unsigned*>(sync);
     K.auxcnt = reinterpret_cast<unsigned*>(sync + 64);
-    K.ctr = reinterpret_cast<int*>(sync + 64 + 4 * (size_t)P.k);   // see sync_bytes()
     K.st = P.st;
     K.rank_tol = (double)(P.m_user > P.n_user ? P.m_user : P.n_user) * eps;
     K.rows_per_cta = (int)round_up(ceil_div(P.m, G), kWarp);

@@ -20,7 +20,7 @@ struct CpqrPlan {
     int ldf;
     void* xbuf;               // ldw: pivot column after the lazy update (T)
     double* ssq;              // kMaxParts partial sums of squares
-    void* sync;               // sync_bytes(k): barrier counter, per-step aux and column-queue counters
+    void* sync;               // sync_bytes(k): barrier counter and per-step aux counters
     double* vn1;              // n: residual norm estimates
     double* vn2;              // n: norms at the last exact computation
     int* perm;                // n
@@ -31,8 +31,8 @@ struct CpqrPlan {
 };
 
 // Bytes of the zero-initialised synchronisation area of one CPQR: a 64-byte
-// grid-barrier slot, k per-step aux counters and k + 1 column-queue counters.
-inline size_t sync_bytes(int k) { return 64 + 4 * (size_t)k + 4 * ((size_t)k + 1); }
+// grid-barrier slot and k per-step aux counters.
+inline size_t sync_bytes(int k) { return 64 + 4 * (size_t)k; }
 
 template <typename T> cudaError_t cpqr_configure();
 template <typename T> cudaError_t copy_in(const void* A, int64_t lda, int trans, const CpqrPlan& P, cudaStream_t s);

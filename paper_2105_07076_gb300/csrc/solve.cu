@@ -23,7 +23,8 @@ constexpr size_t kSolveSmemMax = 200 * 1024;
 template <typename T>
 __global__ void __launch_bounds__(kSolveThreads) k_trsm(const T* __restrict__ W, int ldw, int k, int nrhs, int tb,
                                                         double* __restrict__ Tm, int ldt) {
-    extern __shared__ double B[];   // k x tb
+    extern __shared__ double B[];   // k x tb, then k reciprocals of R's diagonal
+    double* rinv = B + (size_t)k * tb;
     const int t = threadIdx.x;
     const int c0 = blockIdx.x * tb;
     const int rg_count = kSolveThreads / tb;
@@ -31,13 +32,15 @@ __global__ void __launch_bounds__(kSolveThreads) k_trsm(const T* __restrict__ W,
         const int c = e / k, i = e % k;
         B[i * tb + c] = (c0 + c < nrhs) ? (double)W[(int64_t)(k + c0 + c) * ldw + i] : 0.0;
     }
+    for (int i = t; i < k; i += kSolveThreads) rinv[i] = 1.0 / (double)W[(int64_t)i * ldw + i];
     const int c = t % tb, rg = t / tb;
     for (int i = k - 1; i >= 0; --i) {
         __syncthreads();
-        if (t < tb) B[i * tb + t] = B[i * tb + t] / (double)W[(int64_t)i * ldw + i];
+        if (t < tb) B[i * tb + t] *= rinv[i];
         __syncthreads();
         const double ti = B[i * tb + c];
         const T* Rcol = W + (int64_t)i * ldw;
+#pragma unroll 4
         for (int r = rg; r < i; r += rg_count) B[r * tb + c] = fma(-(double)Rcol[r], ti, B[r * tb + c]);
     }
     __syncthreads();
@@ -49,7 +52,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_trsm(const T* __restrict__ W,
 
 static int solve_tb(int k) {
     int tb = 32;
-    while (tb > 1 && (size_t)k * tb * sizeof(double) > kSolveSmemMax) tb /= 2;
+    while (tb > 1 && (size_t)k * (tb + 1) * sizeof(double) > kSolveSmemMax) tb /= 2;
     return tb;
 }
 
@@ -64,7 +67,7 @@ cudaError_t solve_run(const void* W, int ldw, int k, int n, double* Tm, int ldt,
     const int nrhs = n - k;
     if (nrhs <= 0) return cudaSuccess;
     const int tb = solve_tb(k);
-    const size_t smem = (size_t)k * tb * sizeof(double);
+    const size_t smem = (size_t)k * (tb + 1) * sizeof(double);
     const int tr = trace_begin(TraceKind::kSolve, s);
     k_trsm<T><<<ceil_div(nrhs, tb), kSolveThreads, smem, s>>>(static_cast<const T*>(W), ldw, k, nrhs, tb, Tm, ldt);
     trace_end(tr, s);
