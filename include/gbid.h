@@ -165,6 +165,26 @@ int id_cpqr(void* X, id_dtype dtype, int64_t m, int64_t n, int64_t ldx, int64_t 
 int id_solve(const void* X, id_dtype dtype, int64_t n, int64_t ldx, int64_t k,
              double* T, int64_t ldt, void* stream);
 
+/* id_sketch -- Gaussian row sketch Y = Omega A for the randomized ID.
+ *
+ * The sketch replaces A by a short matrix with the same column space
+ * relations (the randomized route to the skeleton set; Sec. 2.2 takes the
+ * randomized step by sampling columns instead). Computed on the tensor cores:
+ * A's FP32 values are rounded to BF16 (nearest even) in shared memory,
+ * products are accumulated in FP32.
+ *
+ *   A      [in]  m x n FP32 row-major, lda >= n, lda a multiple of 4, 16-byte aligned.
+ *   Omega  [in]  l x m BF16 row-major (uint16 bit patterns), ldo >= m, ldo a
+ *                multiple of 8, 16-byte aligned; 1 <= l <= 640.
+ *   Y      [out] l x n FP32 row-major, ldy >= n.
+ *   work   [in]  id_sketch_workspace_size() bytes of device scratch, 256-byte aligned.
+ *   dtype must be ID_F32. info / stream as for id_decompose.
+ * Returns ID_OK, ID_EINVAL (sizes, strides, alignment), ID_ENOMEM, ID_ECUDA,
+ * or ID_ETIMEOUT (through info) if a bounded device wait expired. */
+size_t id_sketch_workspace_size(void);
+int id_sketch(const void* A, id_dtype dtype, int64_t m, int64_t n, int64_t lda, const uint16_t* Omega_bf16, int64_t l,
+              int64_t ldo, float* Y, int64_t ldy, void* work, size_t work_bytes, id_info* info, void* stream);
+
 /* id_info_read -- copy the device-side status of the last call that used
  * `work` to *info (host) and wait for `stream`. Returns info->status. */
 int id_info_read(const void* work, id_info* info, void* stream);

@@ -79,6 +79,9 @@ _SIG = {
     "id_solve": (ctypes.c_int, [_P, ctypes.c_int, _I64, _I64, _I64, _P, _I64, _P]),
     "id_info_read": (ctypes.c_int, [_P, _P, _P]),
     "id_decompose_noalloc": (ctypes.c_int, [_P, ctypes.c_int, _I64, _I64, _I64, _I64, _P, _P, _P, _I64, _P, _P]),
+    "id_sketch_workspace_size": (ctypes.c_size_t, []),
+    "id_sketch": (ctypes.c_int, [_P, ctypes.c_int, _I64, _I64, _I64, _P, _I64, _I64, _P, _I64, _P, ctypes.c_size_t, _P,
+                                 _P]),
     "id_launch_count": (ctypes.c_int64, [ctypes.c_int, _I64, _I64, _I64, _P]),
     "id_trace_enable": (ctypes.c_int, [ctypes.c_int]),
     "id_trace_read": (ctypes.c_int, [_P, _P, ctypes.c_int]),
@@ -202,6 +205,31 @@ def id_decompose_noalloc(A: torch.Tensor, k: int, *, nb: int = 0, out: tuple | N
     if rc in _CALL_ERRORS:
         raise IdError(rc, "id_decompose_noalloc")
     return J, Z, info.as_dict()
+
+
+def id_sketch(A: torch.Tensor, omega: torch.Tensor, *, out: torch.Tensor | None = None, sync: bool = True):
+    """Y = omega @ A on the tensor cores (A FP32 m x n rounded to BF16 in shared memory,
+    omega BF16 l x m, FP32 accumulation). Returns (Y, info)."""
+    _check_cuda_matrix(A, "A")
+    if A.dtype != torch.float32:
+        raise ValueError("A must be float32")
+    if not omega.is_cuda or omega.dtype != torch.bfloat16 or omega.dim() != 2 or omega.stride(1) != 1:
+        raise ValueError("omega must be a row-major CUDA bfloat16 matrix")
+    m, n = A.shape
+    l = omega.shape[0]
+    if omega.shape[1] != m:
+        raise ValueError("omega must have A.shape[0] columns")
+    dev = A.device
+    Y = out if out is not None else torch.empty(l, n, dtype=torch.float32, device=dev)
+    work = torch.empty(int(lib().id_sketch_workspace_size()), dtype=torch.uint8, device=dev)
+    info = IdInfo()
+    with torch.cuda.device(dev):
+        rc = lib().id_sketch(A.data_ptr(), ID_F32, m, n, A.stride(0), omega.data_ptr(), l, omega.stride(0),
+                             Y.data_ptr(), Y.stride(0), work.data_ptr(), work.numel(),
+                             ctypes.byref(info) if sync else None, _stream(dev))
+    if rc in _CALL_ERRORS:
+        raise IdError(rc, "id_sketch")
+    return Y, (info.as_dict() if sync else None)
 
 
 def read_info(workspace: Workspace) -> dict:

@@ -111,6 +111,7 @@ int configure_once() {
     if (cpqr_configure<double>() != cudaSuccess) return -1;
     if (cpqr_configure<float>() != cudaSuccess) return -1;
     if (solve_configure() != cudaSuccess) return -1;
+    if (sketch_configure() != cudaSuccess) return -1;
     done = 1;
     return 0;
 }
@@ -259,6 +260,30 @@ int id_solve(const void* X, id_dtype dtype, int64_t n, int64_t ldx, int64_t k, d
     cudaError_t e = dtype == ID_F64 ? solve_run<double>(X, (int)ldx, (int)k, (int)n, T, (int)ldt, s)
                                     : solve_run<float>(X, (int)ldx, (int)k, (int)n, T, (int)ldt, s);
     return e == cudaSuccess ? ID_OK : ID_ECUDA;
+}
+
+size_t id_sketch_workspace_size(void) { return 1024; }
+
+int id_sketch(const void* A, id_dtype dtype, int64_t m, int64_t n, int64_t lda, const uint16_t* Omega_bf16, int64_t l,
+              int64_t ldo, float* Y, int64_t ldy, void* work, size_t work_bytes, id_info* info, void* stream) {
+    if (!A || !Omega_bf16 || !Y || !work) return ID_EINVAL;
+    if (dtype != ID_F32) return ID_EINVAL;
+    if (m < 1 || n < 1 || l < 1 || l > 640 || m > ((int64_t)1 << 31) - 1 || n > ((int64_t)1 << 31) - 1)
+        return ID_EINVAL;
+    if (lda < n || lda % 4 != 0 || ldo < m || ldo % 8 != 0 || ldy < n) return ID_EINVAL;
+    if (!aligned(A, 16) || !aligned(Omega_bf16, 16) || !aligned(work, 256)) return ID_EINVAL;
+    if (work_bytes < id_sketch_workspace_size()) return ID_ENOMEM;
+    if (configure_once()) return ID_ECUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    char* base = static_cast<char*>(work);
+    DevInfo* dinfo = reinterpret_cast<DevInfo*>(base);
+    State* st = reinterpret_cast<State*>(base + align_up(sizeof(DevInfo)));
+    if (cudaMemsetAsync(work, 0, id_sketch_workspace_size(), s) != cudaSuccess) return ID_ECUDA;
+    const int rc = sketch_run(static_cast<const float*>(A), m, n, lda, Omega_bf16, l, ldo, Y, ldy, &st->status, s);
+    if (rc != ID_OK) return rc;
+    if (finalize_info(st, dinfo, 0, 0, 0, s) != cudaSuccess) return ID_ECUDA;
+    if (info) return read_info(work, info, s);
+    return ID_OK;
 }
 
 int id_info_read(const void* work, id_info* info, void* stream) {

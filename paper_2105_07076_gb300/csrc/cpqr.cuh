@@ -45,6 +45,11 @@ template <typename T> cudaError_t solve_run(const void* W, int ldw, int k, int n
 template <typename T> cudaError_t scatter_z(const int* perm, const double* Tm, int ldt, int k, int n, void* Z,
                                             int64_t ldz, int32_t* J, DevInfo* info, cudaStream_t s);
 cudaError_t solve_configure();
+
+// Y = Omega A on tcgen05 tensor cores (sketch.cu). Returns an id_status.
+cudaError_t sketch_configure();
+int sketch_run(const float* A, int64_t m, int64_t n, int64_t lda, const uint16_t* Om, int64_t l, int64_t ldo, float* Y,
+               int64_t ldy, int* status, cudaStream_t s);
 cudaError_t finalize_info(const State* st, DevInfo* info, int k, int transposed, int nb, cudaStream_t s);
 
 }  // namespace gbid
