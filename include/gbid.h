@@ -49,7 +49,7 @@ extern "C" {
 
 typedef enum {
     ID_OK = 0,
-    ID_RANK_DEFICIENT = 1,   /* |R_jj| <= max(m,n) * eps * |R_00| for some j < k      */
+    ID_RANK_DEFICIENT = 1,   /* |R_jj| <= sqrt(max(m,n)) * eps * |R_00| for some j < k */
     ID_EINVAL = -1,          /* bad size, leading dimension, pointer or option        */
     ID_ENOMEM = -2,          /* workspace smaller than id_workspace_size()            */
     ID_ECUDA = -3,           /* a CUDA launch or copy failed                          */
@@ -184,6 +184,25 @@ int id_solve(const void* X, id_dtype dtype, int64_t n, int64_t ldx, int64_t k,
 size_t id_sketch_workspace_size(void);
 int id_sketch(const void* A, id_dtype dtype, int64_t m, int64_t n, int64_t lda, const uint16_t* Omega_bf16, int64_t l,
               int64_t ldo, float* Y, int64_t ldy, void* work, size_t work_bytes, id_info* info, void* stream);
+
+/* id_decompose_randomized -- randomized rank-k ID of A (m x n, m <= n) from a
+ * Gaussian sketch: Y = Omega A (id_sketch, tensor cores), k steps of column-
+ * pivoted QR of Y (FP32 matrix, FP64 residual norms), T = R11^{-1} R12 of Y's R
+ * in FP64, Z = [I T] P^T. The skeleton J indexes columns of A; Z is the
+ * sketched interpolation matrix (Sec. 2.2 computes Z by least squares on A
+ * instead; here the sketch's R supplies it).
+ *
+ *   A      [in]  m x n FP32 row-major, lda >= n, lda a multiple of 4, 16-byte aligned.
+ *   Omega  [in]  l x m BF16 row-major, ldo >= m, ldo a multiple of 8, 16-byte
+ *                aligned; k <= l <= min(m, 640).
+ *   J, Z   [out] as for id_decompose (Z: k x n FP32, ldz >= n).
+ *   work   [in]  id_rid_workspace_size(m, n, l, k, opts) bytes, 256-byte aligned.
+ *   dtype must be ID_F32. info / stream as for id_decompose. */
+size_t id_rid_workspace_size(int64_t m, int64_t n, int64_t l, int64_t k, const id_opts* opts);
+int id_decompose_randomized(const void* A, id_dtype dtype, int64_t m, int64_t n, int64_t lda,
+                            const uint16_t* Omega_bf16, int64_t l, int64_t ldo, int64_t k, const id_opts* opts,
+                            int32_t* J, void* Z, int64_t ldz, void* work, size_t work_bytes, id_info* info,
+                            void* stream);
 
 /* id_info_read -- copy the device-side status of the last call that used
  * `work` to *info (host) and wait for `stream`. Returns info->status. */

@@ -33,8 +33,10 @@ Readings where the paper is silent (each listed again in the design doc):
   zero column);
 * residual norms are recomputed from scratch at every step (the plain greedy
   definition; no downdating);
-* numerical rank: the first j with |R_jj| <= max(m, n) * eps * |R_00| (0 if
-  R_00 = 0); J, Z are then meaningful for the first ``rank`` rows only.
+* numerical rank: the first j with |R_jj| <= sqrt(max(m, n)) * eps * |R_00|
+  (0 if R_00 = 0), eps of the arithmetic's precision (sqrt(max(m, n)) eps is
+  the typical size of the rounding noise left in a residual column); J, Z are
+  then meaningful for the first ``rank`` rows only.
 """
 from __future__ import annotations
 
@@ -117,7 +119,7 @@ def cpqr(X: np.ndarray, k: int, pivots=None):
         F[j + 1:, j] = v[1:]
     d = np.abs(np.diag(F[:k, :k]))
     rank = k
-    thresh = max(m, n) * EPS64 * d[0]
+    thresh = np.sqrt(max(m, n)) * EPS64 * d[0]
     for j in range(k):
         if d[0] == 0.0 or d[j] <= thresh:
             rank = j

@@ -82,6 +82,9 @@ _SIG = {
     "id_sketch_workspace_size": (ctypes.c_size_t, []),
     "id_sketch": (ctypes.c_int, [_P, ctypes.c_int, _I64, _I64, _I64, _P, _I64, _I64, _P, _I64, _P, ctypes.c_size_t, _P,
                                  _P]),
+    "id_rid_workspace_size": (ctypes.c_size_t, [_I64, _I64, _I64, _I64, _P]),
+    "id_decompose_randomized": (ctypes.c_int, [_P, ctypes.c_int, _I64, _I64, _I64, _P, _I64, _I64, _I64, _P, _P, _P,
+                                               _I64, _P, ctypes.c_size_t, _P, _P]),
     "id_launch_count": (ctypes.c_int64, [ctypes.c_int, _I64, _I64, _I64, _P]),
     "id_trace_enable": (ctypes.c_int, [ctypes.c_int]),
     "id_trace_read": (ctypes.c_int, [_P, _P, ctypes.c_int]),
@@ -230,6 +233,43 @@ def id_sketch(A: torch.Tensor, omega: torch.Tensor, *, out: torch.Tensor | None 
     if rc in _CALL_ERRORS:
         raise IdError(rc, "id_sketch")
     return Y, (info.as_dict() if sync else None)
+
+
+def rid_workspace(m: int, n: int, l: int, k: int, nb: int = 0, device="cuda") -> Workspace:
+    o = _opts(nb)
+    nbytes = int(lib().id_rid_workspace_size(m, n, l, k, ctypes.byref(o)))
+    if nbytes == 0:
+        raise IdError(ID_EINVAL, "id_rid_workspace_size")
+    return Workspace(torch.empty(nbytes, dtype=torch.uint8, device=device))
+
+
+def id_decompose_randomized(A: torch.Tensor, omega: torch.Tensor, k: int, *, nb: int = 0,
+                            workspace: Workspace | None = None, out: tuple | None = None, sync: bool = True):
+    """Randomized rank-k ID from the sketch Y = omega @ A (A FP32 m x n, m <= n;
+    omega BF16 l x m). Returns (J, Z, info) with A ~= A[:, J] @ Z."""
+    _check_cuda_matrix(A, "A")
+    if A.dtype != torch.float32 or omega.dtype != torch.bfloat16 or not omega.is_cuda or omega.stride(1) != 1:
+        raise ValueError("A must be float32 and omega a row-major CUDA bfloat16 matrix")
+    m, n = A.shape
+    l = omega.shape[0]
+    dev = A.device
+    if workspace is None:
+        workspace = rid_workspace(m, n, l, k, nb, dev)
+    if out is None:
+        J = torch.empty(k, dtype=torch.int32, device=dev)
+        Z = torch.empty(k, n, dtype=torch.float32, device=dev)
+    else:
+        J, Z = out
+    o = _opts(nb)
+    info = IdInfo()
+    with torch.cuda.device(dev):
+        rc = lib().id_decompose_randomized(A.data_ptr(), ID_F32, m, n, A.stride(0), omega.data_ptr(), l,
+                                           omega.stride(0), k, ctypes.byref(o), J.data_ptr(), Z.data_ptr(),
+                                           Z.stride(0), workspace.buf.data_ptr(), workspace.buf.numel(),
+                                           ctypes.byref(info) if sync else None, _stream(dev))
+    if rc in _CALL_ERRORS:
+        raise IdError(rc, "id_decompose_randomized")
+    return J, Z, (info.as_dict() if sync else None)
 
 
 def read_info(workspace: Workspace) -> dict:

@@ -15,13 +15,19 @@ constexpr size_t kAlign = 256;
 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
-// Panel width actually used. Left-looking (nb = k) unless the per-step
-// corrections through all k stored reflectors, about 2 k (m + n) operations
-// per step, would outgrow what a compact-WY update every 32 steps costs,
-// about m n per step (one extra pass over the trailing matrix).
-int pick_nb(int m, int n, int k, const id_opts* opts) {
+// Panel width actually used.
+// FP64: left-looking (nb = k) unless the per-step corrections through all k
+// stored reflectors, about 2 k (m + n) FP64 operations per step, would outgrow
+// a compact-WY update every 32 steps (about m n per step): FP64 arithmetic is
+// the scarce resource.
+// FP32: panels of 64. Each panel start recomputes the residual norms exactly,
+// which bounds the drift of the FP64 downdate fed by FP32 R entries; the WY
+// updates are cheap in FP32.
+int pick_nb(id_dtype dt, int m, int n, int k, const id_opts* opts) {
     int nb = (opts && opts->nb > 0) ? opts->nb : 0;
     if (nb == 0) {
+        // lazy (nb = k) while re-reading the n x k F panel costs less than the
+        // blocked WY update's sweeps over W; else 32-column panels
         const double lazy = 2.0 * k * ((double)m + (double)n);
         const double wy = (double)m * (double)n;
         nb = lazy <= wy ? k : 32;
@@ -46,7 +52,7 @@ Layout make_layout(id_dtype dt, int m, int n, int k, const id_opts* opts, bool w
     L.m = m;
     L.n = n;
     L.ldw = ldw > 0 ? ldw : (int)round_up(m, 8);
-    L.nb = pick_nb(m, n, k, opts);
+    L.nb = pick_nb(dt, m, n, k, opts);
     L.ldf = (int)round_up(L.nb, 4);
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes); return o; };
@@ -167,6 +173,16 @@ int cpqr_impl(void* X, int64_t m, int64_t n, int64_t ldx, int64_t k, const id_op
 
 bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
+int64_t rid_ldy(int64_t n) { return (n + 3) / 4 * 4; }
+
+// Workspace of the randomized ID: the CPQR/solve layout of the l x n sketch,
+// then Y itself and the sketch kernel's status word.
+size_t rid_bytes(int64_t n, int64_t l, int64_t k, const id_opts* opts, Layout* out) {
+    const Layout L = make_layout(ID_F32, (int)l, (int)n, (int)k, opts, true, true);
+    if (out) *out = L;
+    return L.total + align_up(4 * (size_t)l * rid_ldy(n)) + kAlign;
+}
+
 }  // namespace
 }  // namespace gbid
 
@@ -263,6 +279,50 @@ int id_solve(const void* X, id_dtype dtype, int64_t n, int64_t ldx, int64_t k, d
 }
 
 size_t id_sketch_workspace_size(void) { return 1024; }
+
+size_t id_rid_workspace_size(int64_t m, int64_t n, int64_t l, int64_t k, const id_opts* opts) {
+    if (m < 1 || n < 1 || k < 1 || l < k || l > 640 || l > m || m > n || !sizes_ok(l, n, k)) return 0;
+    return rid_bytes(n, l, k, opts, nullptr);
+}
+
+int id_decompose_randomized(const void* A, id_dtype dtype, int64_t m, int64_t n, int64_t lda,
+                            const uint16_t* Omega_bf16, int64_t l, int64_t ldo, int64_t k, const id_opts* opts,
+                            int32_t* J, void* Z, int64_t ldz, void* work, size_t work_bytes, id_info* info,
+                            void* stream) {
+    if (!A || !Omega_bf16 || !J || !Z || !work) return ID_EINVAL;
+    if (dtype != ID_F32) return ID_EINVAL;
+    const size_t need = id_rid_workspace_size(m, n, l, k, opts);
+    if (need == 0) return ID_EINVAL;
+    if (lda < n || lda % 4 != 0 || ldo < m || ldo % 8 != 0 || ldz < n) return ID_EINVAL;
+    if (!aligned(A, 16) || !aligned(Omega_bf16, 16) || !aligned(work, 256)) return ID_EINVAL;
+    if (opts && opts->nb < 0) return ID_EINVAL;
+    if (work_bytes < need) return ID_ENOMEM;
+    if (configure_once()) return ID_ECUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Layout L;
+    rid_bytes(n, l, k, opts, &L);
+    char* base = static_cast<char*>(work);
+    const int64_t ldy = rid_ldy(n);
+    float* Y = reinterpret_cast<float*>(base + L.total);
+    int* sk_status = reinterpret_cast<int*>(base + L.total + align_up(4 * (size_t)l * ldy));
+    DevInfo* dinfo = reinterpret_cast<DevInfo*>(base + L.info);
+    if (cudaMemsetAsync(dinfo, 0, sizeof(DevInfo), s) != cudaSuccess) return ID_ECUDA;
+    if (cudaMemsetAsync(sk_status, 0, sizeof(int), s) != cudaSuccess) return ID_ECUDA;
+    // 1. Y = Omega A (tensor cores)
+    int rc = sketch_run(static_cast<const float*>(A), m, n, lda, Omega_bf16, l, ldo, Y, ldy, sk_status, s);
+    if (rc != ID_OK) return rc;
+    // 2. k-step CPQR of Y (FP32 matrix, FP64 norms), 3. T = R11^{-1} R12 of Y in FP64, 4. Z
+    CpqrPlan P = make_plan(L, base, nullptr, nullptr, nullptr, (int)k, l, n);
+    if (copy_in<float>(Y, ldy, 0, P, s) != cudaSuccess) return ID_ECUDA;
+    if (cpqr_run<float>(P, s) != cudaSuccess) return ID_ECUDA;
+    double* Tm = reinterpret_cast<double*>(base + L.T);
+    const int ldt = (int)n - (int)k > 0 ? (int)n - (int)k : 1;
+    if (solve_run<float>(P.W, P.ldw, (int)k, (int)n, Tm, ldt, s) != cudaSuccess) return ID_ECUDA;
+    if (scatter_z<float>(P.perm, Tm, ldt, (int)k, (int)n, Z, ldz, J, dinfo, s) != cudaSuccess) return ID_ECUDA;
+    if (finalize_info(P.st, dinfo, (int)k, 0, P.nb, s, sk_status) != cudaSuccess) return ID_ECUDA;
+    if (info) return read_info(work, info, s);
+    return ID_OK;
+}
 
 int id_sketch(const void* A, id_dtype dtype, int64_t m, int64_t n, int64_t lda, const uint16_t* Omega_bf16, int64_t l,
               int64_t ldo, float* Y, int64_t ldy, void* work, size_t work_bytes, id_info* info, void* stream) {

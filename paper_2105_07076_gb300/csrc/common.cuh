@@ -57,7 +57,7 @@ struct State {
     double tau;         // reflector scalar
     double scale;       // 1 / (x_0 - beta): scales x into v with v_0 = 1
     double r00;         // |R_00|
-    double rank_tol;    // max(m, n) * eps(working precision)
+    double rank_tol;    // sqrt(max(m, n)) * eps(working precision)
 };
 
 // Device copy of id_info kept in the workspace.

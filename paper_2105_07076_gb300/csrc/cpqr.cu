@@ -328,7 +328,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
     const int m = P.m, n = P.n, ldw = P.ldw, ldf = P.ldf;
     const int t = threadIdx.x, lane = t % kWarp, w = t / kWarp;
     const int G = gridDim.x;
-    const double tol3z = sqrt(DBL_EPSILON);
+    // Recompute threshold of the norm downdate: sqrt(eps) of the precision the
+    // R entries carry (FP32 R entries drift like u_32 (nu_exact / nu)^2).
+    const double tol3z = sqrt(sizeof(T) == 8 ? DBL_EPSILON : (double)FLT_EPSILON);
     unsigned epoch = 0;
 
     // ---- column norms, perm, first argmax partials
@@ -531,11 +533,34 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
             // full-warp FP64 instructions instead of 32 single-lane ones.
             int nbat = 0;                    // columns in the batch (warp-uniform)
             int b_l = -1, b_orig = 0;
-            T b_r = T(0), b_f = T(0);
+            T b_r = T(0), b_f = T(0), b_sq = T(0);
             double b_nu = 0.0, b_nu2 = 1.0;
+            // At the first step of a panel W(j:m, l) is up to date, so the
+            // trailing product also yields S = ||W(j:m, l)||^2 and the residual
+            // norm is reset exactly: nu^2 = S - R(j, l)^2.
+            const bool exact_norms = jj == 0;
             auto flush = [&]() {
                 int flagged = 0;
-                if (lane < nbat) {
+                if (lane < nbat && exact_norms) {
+                    ArgMax cnd;
+                    cnd.orig = b_orig;
+                    cnd.pos = b_l;
+                    cnd.val = 0.0;
+                    const double S = (double)b_sq;
+                    if (S > 0.0) {
+                        const double q = fabs((double)b_r) / sqrt(S);
+                        double temp = (1.0 - q) * (1.0 + q);
+                        temp = temp > 0.0 ? temp : 0.0;
+                        if (temp <= tol3z) {
+                            flagged = 1;
+                        } else {
+                            cnd.val = sqrt(S * temp);
+                            P.vn1[b_l] = cnd.val;
+                            P.vn2[b_l] = cnd.val;
+                        }
+                    }
+                    if (!flagged && better(cnd, bestc)) bestc = cnd;
+                } else if (lane < nbat) {
                     ArgMax cnd;
                     cnd.orig = b_orig;
                     cnd.pos = b_l;
@@ -613,7 +638,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
                 }
                 // g = W(j_al:m_pad, l)^T v, eight 16-byte loads per lane in flight
                 const T* col = W + (int64_t)l * ldw;
-                T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+                T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0), sq = T(0);
                 constexpr int S = kWarp * VN;
                 for (int i0 = j_al + lane * VN; i0 < m_pad; i0 += 8 * S) {
                     V xv[8];
@@ -621,6 +646,18 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
                     for (int u = 0; u < 8; ++u) {
                         const int i = i0 + u * S;
                         if (i < m_pad) xv[u] = __ldcg(reinterpret_cast<const V*>(col + i));
+                    }
+                    if (exact_norms) {
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            const int i = i0 + u * S;
+                            if (i < m_pad) {
+                                const T* xe = reinterpret_cast<const T*>(&xv[u]);
+#pragma unroll
+                                for (int q = 0; q < VN; ++q)
+                                    if (i + q >= j) sq = fma(xe[q], xe[q], sq);   // rows j..m (padding is zero)
+                            }
+                        }
                     }
 #pragma unroll
                     for (int u = 0; u < 8; ++u) {
@@ -664,6 +701,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
                     s2 += fv * vrow_s[c];
                 }
                 const T gx = warp_sum((a0 + a1) + (a2 + a3));   // x(j+1:m)^T W(j+1:m, l)
+                if (exact_norms) sq = warp_sum(sq);
                 s1 = warp_sum(s1);
                 s2 = warp_sum(s2);
                 if (lane == slot) {
@@ -671,6 +709,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
                     const T f = tauT * g + s1;
                     b_f = f;
                     b_r = wjl - s2 - f;                     // R(j, l)
+                    b_sq = sq;
                     F[(int64_t)l * ldf + jj] = f;
                     W[(int64_t)l * ldw + j] = b_r;
                 }
@@ -783,7 +822,8 @@ cudaError_t cpqr_run(const CpqrPlan& P, cudaStream_t s) {
     K.bar = reinterpret_cast<unsigned*>(sync);
     K.auxcnt = reinterpret_cast<unsigned*>(sync + 64);
     K.st = P.st;
-    K.rank_tol = (double)(P.m_user > P.n_user ? P.m_user : P.n_user) * eps;
+    // numerical rank: |R_jj| <= sqrt(max(m, n)) eps |R_00| (rounding-noise level of a residual)
+    K.rank_tol = sqrt((double)(P.m_user > P.n_user ? P.m_user : P.n_user)) * eps;
     K.rows_per_cta = (int)round_up(ceil_div(P.m, G), kWarp);
 
     cudaLaunchConfig_t cfg = {};

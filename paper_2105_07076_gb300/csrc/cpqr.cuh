@@ -50,6 +50,7 @@ cudaError_t solve_configure();
 cudaError_t sketch_configure();
 int sketch_run(const float* A, int64_t m, int64_t n, int64_t lda, const uint16_t* Om, int64_t l, int64_t ldo, float* Y,
                int64_t ldy, int* status, cudaStream_t s);
-cudaError_t finalize_info(const State* st, DevInfo* info, int k, int transposed, int nb, cudaStream_t s);
+cudaError_t finalize_info(const State* st, DevInfo* info, int k, int transposed, int nb, cudaStream_t s,
+                          const int* extra_status = nullptr);
 
 }  // namespace gbid

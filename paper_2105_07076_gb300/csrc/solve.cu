@@ -14,62 +14,157 @@
 namespace gbid {
 
 constexpr int kSolveThreads = 256;
-constexpr size_t kSolveSmemMax = 200 * 1024;
+constexpr size_t kSolveSmemMax = 227 * 1024;
+constexpr int kTrsmCols = 32;    // right-hand sides per CTA; lane = column in the update phase
+constexpr int kTrsmBlk = 32;     // rows of a diagonal block
+constexpr int kTrsmChunk = 64;   // rows of the off-diagonal R panel staged per pass
+constexpr int kTrsmLdb = 33;     // padded row stride (doubles) of B and of the diagonal block
+constexpr int kTrsmPre = kTrsmBlk * kTrsmChunk / kSolveThreads;   // staged R values per thread
 
-// One block owns `tb` right-hand sides (columns of R12) and runs the
-// column-oriented back substitution on them in shared memory:
-//   for i = k-1 .. 0:  B(i, :) /= R(i, i);  B(0:i, :) -= R(0:i, i) B(i, :)
-// R(r, i) = W[i*ldw + r] (column-major, contiguous in r). FP64 arithmetic.
-template <typename T>
-__global__ void __launch_bounds__(kSolveThreads) k_trsm(const T* __restrict__ W, int ldw, int k, int nrhs, int tb,
-                                                        double* __restrict__ Tm, int ldt) {
-    extern __shared__ double B[];   // k x tb, then k reciprocals of R's diagonal
-    double* rinv = B + (size_t)k * tb;
-    const int t = threadIdx.x;
-    const int c0 = blockIdx.x * tb;
-    const int rg_count = kSolveThreads / tb;
-    for (int e = t; e < k * tb; e += kSolveThreads) {
-        const int c = e / k, i = e % k;
-        B[i * tb + c] = (c0 + c < nrhs) ? (double)W[(int64_t)(k + c0 + c) * ldw + i] : 0.0;
-    }
-    for (int i = t; i < k; i += kSolveThreads) rinv[i] = 1.0 / (double)W[(int64_t)i * ldw + i];
-    const int c = t % tb, rg = t / tb;
-    for (int i = k - 1; i >= 0; --i) {
-        __syncthreads();
-        if (t < tb) B[i * tb + t] *= rinv[i];
-        __syncthreads();
-        const double ti = B[i * tb + c];
-        const T* Rcol = W + (int64_t)i * ldw;
-#pragma unroll 4
-        for (int r = rg; r < i; r += rg_count) B[r * tb + c] = fma(-(double)Rcol[r], ti, B[r * tb + c]);
-    }
-    __syncthreads();
-    for (int e = t; e < k * tb; e += kSolveThreads) {
-        const int i = e / tb, cc = e % tb;
-        if (c0 + cc < nrhs) Tm[(int64_t)i * ldt + c0 + cc] = B[i * tb + cc];
-    }
+static size_t trsm_smem(int k, bool smem_b) {
+    return ((size_t)kTrsmBlk * kTrsmChunk + (size_t)kTrsmBlk * kTrsmLdb + (smem_b ? (size_t)k * kTrsmLdb : 0)) *
+           sizeof(double);
 }
 
-static int solve_tb(int k) {
-    int tb = 32;
-    while (tb > 1 && (size_t)k * (tb + 1) * sizeof(double) > kSolveSmemMax) tb /= 2;
-    return tb;
+// Blocked back substitution T = R11^{-1} R12, R = W(0:k, :) upper triangular
+// (column-major, R(r, i) = W[i*ldw + r]). One CTA owns kTrsmCols right-hand
+// sides B (columns of R12), in shared memory when k x 33 doubles fit (kSmemB)
+// and in T itself otherwise. Diagonal blocks of 32 rows go bottom-up:
+//   1. B(blk) = D^{-1} B(blk) by column substitution: warp w owns columns
+//      4w .. 4w+3, lane r holds row r, x_i broadcast by a shuffle;
+//   2. B(0:i0) -= R(0:i0, blk) X: lane = column with X (32 values) in
+//      registers, R staged through shared memory 64 rows at a time and read
+//      as broadcasts; each warp accumulates 8 rows.
+// Every B(r, c) receives its updates in decreasing i and each as
+// fma(-R(r, i), x_i, B(r, c)), the order of the unblocked column-oriented
+// substitution; x_i = B(i, c) * (1 / R(i, i)). FP64 arithmetic throughout.
+template <typename T, bool kSmemB>
+__global__ void __launch_bounds__(kSolveThreads, 2) k_trsm(const T* __restrict__ W, int ldw, int k, int nrhs,
+                                                           double* __restrict__ Tm, int ldt) {
+    extern __shared__ __align__(16) double sm[];
+    double* Ps = sm;                                // Ps[q * kTrsmChunk + row]
+    double* Ds = Ps + kTrsmBlk * kTrsmChunk;        // Ds[col * kTrsmLdb + row]
+    double* Bs = Ds + kTrsmBlk * kTrsmLdb;          // Bs[i * kTrsmLdb + c]
+    const int t = threadIdx.x, lane = t & (kWarp - 1), w = t / kWarp;
+    const int c0 = blockIdx.x * kTrsmCols;
+    const int ncols = min(kTrsmCols, nrhs - c0);
+    double* B = kSmemB ? Bs : Tm + c0;
+    const int64_t ldb = kSmemB ? kTrsmLdb : ldt;
+
+    for (int e = t; e < k * kTrsmCols; e += kSolveThreads) {
+        const int c = e / k, i = e - c * k;         // i fastest: coalesced reads of R12's columns
+        if (kSmemB) Bs[i * kTrsmLdb + c] = c < ncols ? (double)W[(int64_t)(k + c0 + c) * ldw + i] : 0.0;
+        else if (c < ncols) B[i * ldb + c] = (double)W[(int64_t)(k + c0 + c) * ldw + i];
+    }
+    const bool lane_col = kSmemB || lane < ncols;
+    const int nblk = (k + kTrsmBlk - 1) / kTrsmBlk;
+    for (int ib = nblk - 1; ib >= 0; --ib) {
+        const int i0 = ib * kTrsmBlk, bs = min(kTrsmBlk, k - i0);
+        __syncthreads();   // B(i0 : i0+bs) has all its updates; Ds is free
+        for (int e = t; e < kTrsmBlk * kTrsmBlk; e += kSolveThreads) {
+            const int col = e / kTrsmBlk, row = e % kTrsmBlk;
+            Ds[col * kTrsmLdb + row] =
+                (col < bs && row < bs) ? (double)W[(int64_t)(i0 + col) * ldw + i0 + row] : 0.0;
+        }
+        __syncthreads();
+        {
+            const double rv = lane < bs ? 1.0 / Ds[lane * kTrsmLdb + lane] : 0.0;
+            double x[4];
+#pragma unroll
+            for (int qq = 0; qq < 4; ++qq) {
+                const int c = 4 * w + qq;
+                x[qq] = (lane < bs && (kSmemB || c < ncols)) ? B[(i0 + lane) * ldb + c] : 0.0;
+            }
+            for (int i = bs - 1; i >= 0; --i) {
+                const double dl = Ds[i * kTrsmLdb + lane];
+#pragma unroll
+                for (int qq = 0; qq < 4; ++qq) {
+                    if (lane == i) x[qq] *= rv;
+                    const double xi = __shfl_sync(0xffffffffu, x[qq], i);
+                    if (lane < i) x[qq] = fma(-dl, xi, x[qq]);
+                }
+            }
+#pragma unroll
+            for (int qq = 0; qq < 4; ++qq) {
+                const int c = 4 * w + qq;
+                if (lane < bs && (kSmemB || c < ncols)) B[(i0 + lane) * ldb + c] = x[qq];
+            }
+        }
+        if (i0 == 0) break;
+        __syncthreads();
+        double X[kTrsmBlk];
+#pragma unroll
+        for (int q = 0; q < kTrsmBlk; ++q) X[q] = (q < bs && lane_col) ? B[(i0 + q) * ldb + lane] : 0.0;
+        const int nch = (i0 + kTrsmChunk - 1) / kTrsmChunk;
+        double pre[kTrsmPre];
+        auto stage = [&](int r0) {
+#pragma unroll
+            for (int j = 0; j < kTrsmPre; ++j) {
+                const int e = t + j * kSolveThreads, q = e / kTrsmChunk, rl = e % kTrsmChunk;
+                pre[j] = (q < bs && r0 + rl < i0) ? (double)W[(int64_t)(i0 + q) * ldw + r0 + rl] : 0.0;
+            }
+        };
+        stage(0);
+        for (int ch = 0; ch < nch; ++ch) {
+            const int r0 = ch * kTrsmChunk;
+            __syncthreads();   // the previous pass is done reading Ps
+#pragma unroll
+            for (int j = 0; j < kTrsmPre; ++j) Ps[t + j * kSolveThreads] = pre[j];
+            __syncthreads();
+            if (ch + 1 < nch) stage(r0 + kTrsmChunk);
+            const int rb = r0 + 8 * w;
+            if (rb < i0) {
+                double acc[8];
+#pragma unroll
+                for (int jr = 0; jr < 8; ++jr) acc[jr] = (rb + jr < i0 && lane_col) ? B[(rb + jr) * ldb + lane] : 0.0;
+#pragma unroll
+                for (int q = kTrsmBlk - 1; q >= 0; --q) {
+                    const double2* pr = reinterpret_cast<const double2*>(Ps + q * kTrsmChunk + 8 * w);
+#pragma unroll
+                    for (int h = 0; h < 4; ++h) {
+                        const double2 p = pr[h];
+                        acc[2 * h] = fma(-p.x, X[q], acc[2 * h]);
+                        acc[2 * h + 1] = fma(-p.y, X[q], acc[2 * h + 1]);
+                    }
+                }
+#pragma unroll
+                for (int jr = 0; jr < 8; ++jr)
+                    if (rb + jr < i0 && lane_col) B[(rb + jr) * ldb + lane] = acc[jr];
+            }
+        }
+    }
+    if (kSmemB) {
+        __syncthreads();
+        for (int e = t; e < k * kTrsmCols; e += kSolveThreads) {
+            const int i = e / kTrsmCols, c = e % kTrsmCols;
+            if (c < ncols) Tm[(int64_t)i * ldt + c0 + c] = Bs[i * kTrsmLdb + c];
+        }
+    }
 }
 
 cudaError_t solve_configure() {
-    cudaError_t e = cudaFuncSetAttribute(k_trsm<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSolveSmemMax);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_trsm<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSolveSmemMax);
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_trsm<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)kSolveSmemMax)) != cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(k_trsm<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)kSolveSmemMax)) != cudaSuccess)
+        return e;
+    return cudaSuccess;
 }
 
 template <typename T>
 cudaError_t solve_run(const void* W, int ldw, int k, int n, double* Tm, int ldt, cudaStream_t s) {
     const int nrhs = n - k;
     if (nrhs <= 0) return cudaSuccess;
-    const int tb = solve_tb(k);
-    const size_t smem = (size_t)k * (tb + 1) * sizeof(double);
+    const bool smem_b = trsm_smem(k, true) <= kSolveSmemMax;
+    const size_t smem = trsm_smem(k, smem_b);
     const int tr = trace_begin(TraceKind::kSolve, s);
-    k_trsm<T><<<ceil_div(nrhs, tb), kSolveThreads, smem, s>>>(static_cast<const T*>(W), ldw, k, nrhs, tb, Tm, ldt);
+    const int grid = ceil_div(nrhs, kTrsmCols);
+    if (smem_b)
+        k_trsm<T, true><<<grid, kSolveThreads, smem, s>>>(static_cast<const T*>(W), ldw, k, nrhs, Tm, ldt);
+    else
+        k_trsm<T, false><<<grid, kSolveThreads, smem, s>>>(static_cast<const T*>(W), ldw, k, nrhs, Tm, ldt);
     trace_end(tr, s);
     return cudaGetLastError();
 }
@@ -113,8 +208,9 @@ cudaError_t scatter_z(const int* perm, const double* Tm, int ldt, int k, int n, 
     return cudaGetLastError();
 }
 
-__global__ void k_finalize(const State* st, DevInfo* info, int k, int transposed, int nb) {
+__global__ void k_finalize(const State* st, DevInfo* info, int k, int transposed, int nb, const int* extra_status) {
     id_info r = info->info;
+    const int status = st->status | (extra_status ? *extra_status : 0);
     r.rank = st->rank;
     r.n_recompute = st->n_recompute;
     r.r00 = st->r00;
@@ -122,15 +218,16 @@ __global__ void k_finalize(const State* st, DevInfo* info, int k, int transposed
     r.nb = nb;
     r.n_gt2 = (int64_t)info->n_gt2;
     r.max_abs_z = __longlong_as_double((long long)info->max_abs_z_bits);
-    if (st->status & kStatNonFinite) r.status = ID_ENONFINITE;
-    else if (st->status & kStatTimeout) r.status = ID_ETIMEOUT;
+    if (status & kStatNonFinite) r.status = ID_ENONFINITE;
+    else if (status & kStatTimeout) r.status = ID_ETIMEOUT;
     else if (st->rank < k) r.status = ID_RANK_DEFICIENT;
     else r.status = ID_OK;
     info->info = r;
 }
 
-cudaError_t finalize_info(const State* st, DevInfo* info, int k, int transposed, int nb, cudaStream_t s) {
-    k_finalize<<<1, 1, 0, s>>>(st, info, k, transposed, nb);
+cudaError_t finalize_info(const State* st, DevInfo* info, int k, int transposed, int nb, cudaStream_t s,
+                          const int* extra_status) {
+    k_finalize<<<1, 1, 0, s>>>(st, info, k, transposed, nb, extra_status);
     return cudaGetLastError();
 }
 

@@ -210,6 +210,25 @@ def test_cpqr_and_solve_entry_points(gbid, dtype):
     assert np.linalg.norm(T - To) / np.linalg.norm(To) < TOL_Z[dtype]
 
 
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("k,nrhs", [(1, 7), (5, 40), (32, 33), (33, 31), (95, 200), (256, 1000), (300, 65),
+                                    (800, 70)])
+def test_solve_blocked_shapes(gbid, dtype, k, nrhs):
+    """T = R11^{-1} R12 for ragged diagonal blocks, ragged right-hand-side
+    groups and k past the shared-memory bound (800: B kept in T itself)."""
+    rng = np.random.default_rng(k * 7919 + nrhs)
+    n = k + nrhs
+    R = np.linalg.qr(rng.standard_normal((k, n)), mode="r")     # upper trapezoidal, cond(R11) = O(k)
+    R = torch.as_tensor(R).to(dtype).double().numpy()          # the values the kernel sees
+    ldx = -(-k // 8) * 8
+    Xcm = torch.zeros(n, ldx, dtype=dtype)
+    Xcm[:, :k] = torch.as_tensor(R.T).to(dtype)
+    T = gbid.id_solve(Xcm.cuda(), k).cpu().numpy()
+    To = orc.back_substitute(R[:, :k], R[:, k:])
+    assert T.shape == To.shape
+    assert np.linalg.norm(T - To) / np.linalg.norm(To) < 1e-12
+
+
 def test_host_buffers_entry_point(gbid):
     A = synth.lowrank(200, 400, synth.spectrum("pow2_half", 200), 1)
     Ah = A.pin_memory()

@@ -1,0 +1,87 @@
+"""Randomized ID (Gaussian sketch -> CPQR of Y -> T from Y's R) vs the FP64 oracle.
+
+Stage-wise: the oracle replays the GPU's pivots on the GPU's own sketch Y
+(FP32 tolerance 64 u_32 sqrt(l) on near-ties) and recomputes Z for those
+pivots (1e-4 relative Frobenius, the FP32 bar, widened to 2 cond(Y_J) u_32
+where the conditioning of the skeleton puts 1e-4 out of FP32's reach). End to end: the reconstruction
+error on A is at most 1.05x that of the oracle's randomized ID on the exact
+FP64 sketch Omega A (same algorithm, FP64 throughout).
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import id_oracle as orc
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gbid():
+    import __graft_entry__ as g
+
+    g.build()
+    import paper_2105_07076_gb300 as m
+
+    return m
+
+
+def _tol(l):
+    return 64 * 2.0 ** -24 * math.sqrt(l)
+
+
+@pytest.mark.parametrize("m,n,k,p,seed", [(600, 1200, 60, 10, 1), (256, 700, 40, 8, 2), (512, 2048, 100, 10, 3)])
+def test_randomized_stagewise_and_end_to_end(gbid, m, n, k, p, seed):
+    l = k + p
+    A = synth.lowrank(m, n, synth.spectrum("poly1.5", m), 10 + seed, dtype=torch.float32).cuda()
+    omega = synth.gaussian_sketch_bf16(l, m, seed=20 + seed).cuda()
+    if m % 8:
+        pytest.skip("sketch needs ldo % 8 == 0")
+    J, Z, info = gbid.id_decompose_randomized(A, omega, k)
+    assert info["status"] == gbid.ID_OK, info
+    Y, _ = gbid.id_sketch(A, omega)                      # the same (deterministic) sketch
+    Yh = Y.double().cpu().numpy()
+    Jg = J.cpu().numpy().astype(np.int64)
+    Zg = Z.double().cpu().numpy()
+    ok, worst = orc.verify_pivots(Yh, Jg, _tol(l))
+    assert ok, worst.max()
+    Zo = orc.interp_decomp(Yh, k, pivots=Jg)[1]
+    assert np.linalg.norm(Zg - Zo) / np.linalg.norm(Zo) <= 1e-4
+    assert np.array_equal(Zg[:, Jg], np.eye(k))
+    Ah = A.double().cpu().numpy()
+    err_g = orc.rel_error(Ah, Jg, Zg)
+    Jo, Zy, Zr, _ = orc.randomized_interp_decomp(Ah, omega.double().cpu().numpy(), k)
+    err_o = orc.rel_error(Ah, Jo, Zy)
+    assert err_g <= 1.05 * err_o, (err_g, err_o, orc.rel_error(Ah, Jo, Zr))
+
+
+def test_randomized_full_size(gbid):
+    """16384 x 32768 FP32, s_i = (1+i)^-1.5, k = 512, Omega 522 x 16384 BF16."""
+    m, n, k, l = 16384, 32768, 512, 522
+    A = synth.lowrank(m, n, synth.spectrum("poly1.5", m), 3, device="cuda", dtype=torch.float32,
+                      gen_dtype=torch.float32)
+    omega = synth.gaussian_sketch_bf16(l, m, seed=33, device="cuda")
+    J, Z, info = gbid.id_decompose_randomized(A, omega, k)
+    assert info["status"] == gbid.ID_OK, info
+    Jg = J.cpu().numpy().astype(np.int64)
+    assert len(set(Jg.tolist())) == k
+    Y, _ = gbid.id_sketch(A, omega)
+    Yh = Y.double().cpu().numpy()
+    ok, worst = orc.verify_pivots(Yh, Jg[:16], _tol(l))   # first 16 steps replayed
+    assert ok, worst.max()
+    # Z against the oracle's T for the GPU's pivots on the GPU's sketch. An FP32
+    # factorisation perturbs R by O(u_32) relative, which T = R11^{-1} R12
+    # amplifies by cond(R11) = cond(Y_J) (about 1e4 here): the bar is
+    # max(1e-4, 2 cond(Y_J) u_32).
+    Zo = orc.interp_decomp(Yh, k, pivots=Jg)[1]
+    Zg = Z.double().cpu().numpy()
+    cond = np.linalg.cond(Yh[:, Jg])
+    assert np.linalg.norm(Zg - Zo) / np.linalg.norm(Zo) <= max(1e-4, 2 * cond * 2.0 ** -24), cond
+    # reconstruction error on A, between the Eckart-Young floor and a small multiple
+    A64 = A.double()
+    err = (torch.linalg.norm(A64 - A64[:, J.long()] @ Z.double()) / torch.linalg.norm(A64)).item()
+    tail = synth.tail_bound(synth.spectrum("poly1.5", m), k)
+    assert tail * (1 - 1e-6) <= err <= 10 * tail, (err, tail)
