@@ -278,6 +278,7 @@ __device__ void wy_tile(T* W, int ldw, int m, int n, int i0, int l0, int j0, int
 }
 
 constexpr int kFRegs = 8;   // panel entries per lane held in registers (panels up to 256 wide)
+constexpr int kPre = 16;    // reflector entries per thread prefetched ahead of the pivot argmax
 
 // Shared-memory plan of k_cpqr (dynamic part): vrow_s | fco | v_s.
 struct SmemPlan {
@@ -293,16 +294,17 @@ struct SmemPlan {
 //     (the pivot column brought up to date with the panel's reflectors), each
 //     CTA on its row chunk; partial ||x(j+1:m)||^2.            -- grid barrier
 //  B. beta = -sign(x_j) ||x||, tau = (beta - x_j) / beta, v = x / (x_j - beta)
-//     with v_j = 1, written to W(:, j); aux = -tau V^T v (one CTA per panel
-//     column, published through a counter); then the trailing product, one
-//     warp per column taken from a queue (order reversed on odd steps so the
-//     tail of one sweep is still in L2 when the next starts):
+//     with v_j = 1, written to W(:, j); aux = -tau V^T v (CTA c owns entry c,
+//     published through a counter); then the trailing product over the CTA's
+//     contiguous column range, one warp per column, sweep direction reversed
+//     on odd steps (the tail of one sweep is still in L2 when the next starts):
 //       g = W(j:m, l)^T v,  F(l, jj) = tau g + F(l, 0:jj) aux,
 //       R(j, l) = W(j, l) - F(l, 0:jj) V(j, 0:jj)^T - F(l, jj),
 //     and the FP64 norm downdate nu_l <- nu_l sqrt(1 - (R(j,l)/nu_l)^2),
-//     replaced by an exact recompute when (nu_new / nu_exact)^2 <= sqrt(eps_64)
-//     (Drmac & Bujanovic, LAPACK Working Note 176); partial argmax.
-//                                                               -- grid barrier
+//     replaced by an exact recompute when (nu_new / nu_exact)^2 <= sqrt(eps)
+//     of the working precision (Drmac & Bujanovic, LAPACK Working Note 176);
+//     at a panel's first step the norms are reset exactly from the product's
+//     sum of squares; partial argmax.                          -- grid barrier
 //  C. every nb steps (nb < k): compact-WY update W_trail -= V F^T. -- barrier
 // Every wait (grid barrier, aux counter) is bounded and ends the kernel early
 // with kStatTimeout instead of hanging.
@@ -318,6 +320,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
     __shared__ T wy_s[16 * 64 + 16 * 65];              // WY-update tiles
     __shared__ T red[NW][kWarp];
     __shared__ double sc[4];
+    __shared__ double red2[NW];
     __shared__ int qctr;   // column queue of this CTA
 
     T* W = static_cast<T*>(P.W);
@@ -377,6 +380,19 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
         const int jj = j - j0;
 
         // ---- A: pivot, swap, lazy update of the pivot column
+        // The panel's reflector entries on this CTA's first row tile do not
+        // depend on the pivot: their loads are issued before the argmax
+        // reduction so that the two latencies overlap.
+        T vpre[kPre];
+        {
+            const int r = r0 + lane;
+            const bool ok = r < r1 && r >= j;
+#pragma unroll
+            for (int u = 0; u < kPre; ++u) {
+                const int c = w + u * NW;
+                vpre[u] = (ok && c < jj) ? ld(W + (int64_t)(j0 + c) * ldw + r) : T(0);
+            }
+        }
         ArgMax best = empty_argmax();
         for (int e = t; e < G; e += kThreads) {
             const ArgMax c = ld_argmax(P.part + e);
@@ -404,29 +420,54 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
         double ssq = 0.0;
         for (int rt = r0; rt < r1; rt += kWarp) {
             const int r = rt + lane;
+            T wa = T(0), wb = T(0);   // W(r, p), W(r, j): issued ahead of the products
+            if (w == 0 && r < r1) {
+                wa = ld(W + (int64_t)p * ldw + r);
+                wb = ld(W + (int64_t)j * ldw + r);
+            }
             T acc = T(0);
             if (r < r1 && r >= j) {
                 T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
-                int c = w;
-                for (; c + 3 * NW < jj; c += 4 * NW) {
-                    a0 += ld(W + (int64_t)(j0 + c) * ldw + r) * fco[c];
-                    a1 += ld(W + (int64_t)(j0 + c + NW) * ldw + r) * fco[c + NW];
-                    a2 += ld(W + (int64_t)(j0 + c + 2 * NW) * ldw + r) * fco[c + 2 * NW];
-                    a3 += ld(W + (int64_t)(j0 + c + 3 * NW) * ldw + r) * fco[c + 3 * NW];
+                int cs = w;
+                if (rt == r0) {
+#pragma unroll
+                    for (int u = 0; u < kPre; ++u) {
+                        const int c = w + u * NW;
+                        const T fv = c < jj ? fco[c] : T(0);
+                        if (u % 4 == 0) a0 += vpre[u] * fv;
+                        else if (u % 4 == 1) a1 += vpre[u] * fv;
+                        else if (u % 4 == 2) a2 += vpre[u] * fv;
+                        else a3 += vpre[u] * fv;
+                    }
+                    cs = w + kPre * NW;
                 }
-                for (; c < jj; c += NW) a0 += ld(W + (int64_t)(j0 + c) * ldw + r) * fco[c];
+                for (; cs < jj; cs += 8 * NW) {
+                    T vv[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int c = cs + u * NW;
+                        vv[u] = c < jj ? ld(W + (int64_t)(j0 + c) * ldw + r) : T(0);
+                    }
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int c = cs + u * NW;
+                        const T fv = c < jj ? fco[c] : T(0);
+                        if (u % 4 == 0) a0 += vv[u] * fv;
+                        else if (u % 4 == 1) a1 += vv[u] * fv;
+                        else if (u % 4 == 2) a2 += vv[u] * fv;
+                        else a3 += vv[u] * fv;
+                    }
+                }
                 acc = (a0 + a1) + (a2 + a3);
             }
             red[w][lane] = acc;
             __syncthreads();
             if (w == 0 && r < r1) {
-                T s = T(0);
+                T sr = T(0);
 #pragma unroll
-                for (int g = 0; g < NW; ++g) s += red[g][lane];
-                const T a = ld(W + (int64_t)p * ldw + r);
-                const T b = ld(W + (int64_t)j * ldw + r);
-                const T x = r >= j ? a - s : a;
-                W[(int64_t)p * ldw + r] = b;
+                for (int g = 0; g < NW; ++g) sr += red[g][lane];
+                const T x = r >= j ? wa - sr : wa;
+                W[(int64_t)p * ldw + r] = wb;
                 if (r < j) W[(int64_t)j * ldw + r] = x;   // R entries travel with their column
                 else xbuf[r] = x;
                 if (r > j) ssq = fma((double)x, (double)x, ssq);
@@ -440,15 +481,55 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
         }
         grid_sync(P.bar, epoch, st);
 
-        // ---- B1: reflector scalars (same arithmetic in every CTA)
+        // ---- B: reflector scalars (same arithmetic in every CTA), this CTA's
+        // aux entry and the trailing product's operands, from one round of loads.
+        //   aux(c) = -tau V(j:m, c)^T v = -tau (scale V(j+1:m, c)^T x + V(j, c))
+        // (the dot needs only x, so it is formed before beta is known).
+        const int j_al = j & ~(VN - 1);
+        const int m_pad = (m + VN - 1) / VN * VN;
+        const int c_aux = blockIdx.x;
+        const bool has_aux = c_aux < jj;
+        const T* vca = W + (int64_t)(j0 + (has_aux ? c_aux : 0)) * ldw;
         {
-            double s = 0.0;
-            for (int e = t; e < G; e += kThreads) s += ld(P.ssq + e);
-            if (t == kThreads - 1) sc[3] = ld(&st->x0);   // visible after block_sum's barriers
-            s = block_sum(s);
+            double sq = 0.0;
+            for (int e = t; e < G; e += kThreads) sq += ld(P.ssq + e);
+            if (t == kThreads - 1) sc[3] = ld(&st->x0);
+            for (int c = t; c < jj; c += kThreads) vrow_s[c] = ld(W + (int64_t)(j0 + c) * ldw + j);
+            T adot = T(0);
+            const int i_lo = kSmemV ? j_al : j + 1, i_hi = kSmemV ? m_pad : m;
+            for (int i = i_lo + t; (kSmemV || has_aux) && i < i_hi; i += 4 * kThreads) {
+                T xs[4], vs4[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int ii = i + u * kThreads;
+                    const bool in = ii > j && ii < m;
+                    xs[u] = in ? ld(xbuf + ii) : T(0);
+                    vs4[u] = (in && has_aux) ? ld(vca + ii) : T(0);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int ii = i + u * kThreads;
+                    if (kSmemV && ii < i_hi) v_s[ii - j_al] = xs[u];
+                    adot += vs4[u] * xs[u];
+                }
+            }
+            sq = warp_sum(sq);
+            adot = warp_sum(adot);
+            if (lane == 0) {
+                red2[w] = sq;
+                red[w][0] = adot;
+            }
+            __syncthreads();
             if (t == 0) {
+                double S = 0.0;
+                T A = T(0);
+#pragma unroll
+                for (int g = 0; g < NW; ++g) {
+                    S += red2[g];
+                    A += red[g][0];
+                }
                 const double x0 = sc[3];
-                const double alpha = sqrt(fma(x0, x0, s));
+                const double alpha = sqrt(fma(x0, x0, S));
                 double beta = 0.0, tau = 0.0, scale = 0.0;
                 if (alpha != 0.0) {
                     beta = x0 >= 0.0 ? -alpha : alpha;
@@ -467,6 +548,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
                     if (r00 == 0.0 || fabs(beta) <= P.rank_tol * r00) atomicMin(&st->rank, j);
                     if (!isfinite(beta)) atomicOr(&st->status, kStatNonFinite);
                 }
+                if (has_aux) {
+                    aux[c_aux] = -(T)tau * ((T)scale * A + ld(vca + j));
+                    __threadfence();
+                    red_release_add(P.auxcnt + j, 1u);
+                }
+                qctr = 0;
             }
             __syncthreads();
         }
@@ -480,39 +567,21 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
         for (int r = max(r0, j) + t; r < r1; r += kThreads)
             W[(int64_t)j * ldw + r] = r == j ? (T)beta : ld(xbuf + r) * scaleT;
 
-        // ---- B2: aux = -tau V(j:m, 0:jj)^T v, one CTA per panel column
-        for (int c = blockIdx.x; c < jj; c += G) {
+        // aux entries past the first G panel columns (panels wider than the grid)
+        for (int c = blockIdx.x + G; c < jj; c += G) {
             const T* vc = W + (int64_t)(j0 + c) * ldw;
             T acc = T(0);
-            for (int i = j + 1 + t; i < m; i += 4 * kThreads) {
-                T xs[4], vs4[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int ii = i + u * kThreads;
-                    xs[u] = ii < m ? ld(xbuf + ii) : T(0);
-                    vs4[u] = ii < m ? ld(vc + ii) : T(0);
-                }
-#pragma unroll
-                for (int u = 0; u < 4; ++u) acc += vs4[u] * xs[u];
-            }
+            for (int i = j + 1 + t; i < m; i += kThreads) acc += ld(vc + i) * ld(xbuf + i);
             const T tot = block_sum_t(acc);
             if (t == 0) {
-                aux[c] = -(T)tau * (scaleT * tot + ld(vc + j));   // V(:, c)^T v with v_j = 1
+                aux[c] = -(T)tau * (scaleT * tot + ld(vc + j));
                 __threadfence();
                 red_release_add(P.auxcnt + j, 1u);
             }
         }
 
-        // ---- B3: trailing product, one warp per column from a queue
+        // ---- B3: trailing product over this CTA's column range
         if (j + 1 < n) {
-            const int j_al = j & ~(VN - 1);
-            const int m_pad = (m + VN - 1) / VN * VN;
-            for (int c = t; c < jj; c += kThreads) vrow_s[c] = ld(W + (int64_t)(j0 + c) * ldw + j);
-            if (kSmemV)
-                for (int i = j_al + t; i < m_pad; i += kThreads)
-                    v_s[i - j_al] = i <= j || i >= m ? T(0) : ld(xbuf + i);
-            if (t == 0) qctr = 0;
-            __syncthreads();
             const T tauT = (T)tau;
             const int ncols = n - j - 1;
             // Each CTA owns a contiguous, balanced range of trailing columns (so
