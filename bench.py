@@ -7,6 +7,14 @@ the same matrix is measured in the same run and reported beside it.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gbid|reference]
 
+The line also carries, under "randomized", the randomized ID of a 16384 x
+32768 FP32 matrix (s_i = (1+i)^-1.5, k = 512): BF16 Gaussian sketch on the
+tensor cores, CPQR of the 522 x 32768 sketch, FP64 solve; and under
+"batched", 4096 uneven FP32 IDs (m ~ U[32, 256], n ~ U[m, 4m], k ~ U[8, 64])
+in one persistent launch; and under "latency", back-to-back 200 x 400 FP64
+IDs at k = 20 (--only randomized / batched / latency runs that workload
+alone; --only id skips all three).
+
 Multi-GPU (N > 1, launched by torchrun): every rank decomposes its own copy
 (independent replicas, no collective on the data path); value = total IDs/s.
 --impl reference times the FP64 CPU oracle on a bounded sample of the same
@@ -65,6 +73,11 @@ def load_peaks():
     except Exception:
         return 6800.0, "fallback"
 
+
+# dram__bytes_read.sum + dram__bytes_write.sum of one k_cpqr launch on this
+# workload, from the ncu capture summarised in profiles/ (bytes per launch).
+# Set to None whenever k_cpqr changes until it is captured again.
+NCU_TRAFFIC = {"f64": 56.85e9, "f32": 12.15e9}
 
 # FP64 ALU peak: 152 SMs x 2 FP64 FMA per clock x 2 flops x 2.07 GHz (a DFMA
 # microbenchmark on this GPU measured 1.196 TFLOP/s).
@@ -279,6 +292,178 @@ def e2e_rate(gbid, A, steps):
     return 1000.0 / ms, h2d, d2h
 
 
+# Randomized ID workload reported beside the headline: 16384 x 32768 FP32,
+# s_i = (1+i)^-1.5, k = 512, Omega 522 x 16384 (N(0,1) rounded to BF16).
+RM, RN, RK, RL = 16384, 32768, 512, 522
+
+
+def randomized_block(gbid, dev, steps):
+    """ms per randomized ID (sketch, CPQR of Y, solve, Z), its kernels, and the
+    error on A. A (2.1 GB) exceeds L2, so no flush is needed between IDs."""
+    import torch
+
+    import synth
+
+    A = synth.lowrank(RM, RN, synth.spectrum("poly1.5", RM), 3, device=dev, dtype=torch.float32,
+                      gen_dtype=torch.float32)
+    om = synth.gaussian_sketch_bf16(RL, RM, seed=33, device=dev)
+    ws = gbid.rid_workspace(RM, RN, RL, RK, device=dev)
+    J = torch.empty(RK, dtype=torch.int32, device=dev)
+    Z = torch.empty(RK, RN, dtype=torch.float32, device=dev)
+    for _ in range(3):
+        gbid.id_decompose_randomized(A, om, RK, workspace=ws, out=(J, Z), sync=False)
+    torch.cuda.synchronize()
+    gbid.trace_enable(8 * steps + 8)
+    s = torch.cuda.current_stream()
+    ev = []
+    for _ in range(steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        gbid.id_decompose_randomized(A, om, RK, workspace=ws, out=(J, Z), sync=False)
+        e1.record(s)
+        ev.append((e0, e1))
+    torch.cuda.synchronize()
+    ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    tr = gbid.trace_read()
+    gbid.trace_enable(0)
+    info = gbid.read_info(ws)
+    per = {k: v[0] / v[1] for k, v in tr.items() if v[1]}
+    with torch.no_grad():
+        torch.backends.cuda.matmul.allow_tf32 = False
+        C = A[:, J.long()]
+        num = den = 0.0
+        for c0 in range(0, RN, 4096):          # FP32 products, FP64 sums, 4096 columns at a time
+            Ac = A[:, c0:c0 + 4096]
+            num += torch.sum((Ac - C @ Z[:, c0:c0 + 4096]).double() ** 2).item()
+            den += torch.sum(Ac.double() ** 2).item()
+        err = math.sqrt(num / den)
+    tail = synth.tail_bound(synth.spectrum("poly1.5", RM), RK)
+    sk = per.get("sketch", float("nan"))
+    sk_tflops = 2.0 * RL * RM * RN / (sk * 1e-3) / 1e12
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            bf16 = float(json.load(f)["bf16_tflops"])
+        src = "measured burst bf16 (MEASURED_PEAKS.json)"
+    except Exception:
+        bf16, src = 1900.0, "fallback"
+    del A, C
+    return {"workload": f"rid_{RM}x{RN}_k{RK}_l{RL}", "ms_per_step": ms, "value": 1000.0 / ms, "unit": UNIT,
+            "kernel_ms": per, "rel_err": err, "tail_bound": tail, "status": info["status_name"],
+            "dtype": "bf16 sketch (FP32 accumulate), f32 CPQR, f64 solve, one least-squares refinement "
+                     "(double-float Gram, f64 Cholesky, f32-accurate GEMMs)",
+            "sketch_roofline": {"bound": "tensor", "achieved": sk_tflops, "peak": bf16, "unit": "TFLOP/s",
+                                "frac": sk_tflops / bf16, "peak_source": src}}
+
+
+BATCH_COUNT = 4096
+
+
+def latency_block(gbid, dev, steps):
+    """The small-ID latency workload: 200 x 400 FP64, s_i = 2^(-i/2), k = 20
+    (seed 1), back-to-back IDs in one stream (A is 640 KB and stays in L2).
+    Reported plainly and replayed from a CUDA graph of 20 IDs."""
+    import torch
+
+    import synth
+
+    A = synth.lowrank(200, 400, synth.spectrum("pow2_half", 200), 1, device=dev)
+    k = 20
+    ws = gbid.Workspace.for_problem(A.dtype, 200, 400, k, device=dev)
+    J = torch.empty(k, dtype=torch.int32, device=dev)
+    Z = torch.empty(k, 400, dtype=A.dtype, device=dev)
+    for _ in range(5):
+        gbid.id_decompose(A, k, workspace=ws, out=(J, Z), sync=False)
+    torch.cuda.synchronize()
+    reps = max(50, 20 * steps)
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(reps):
+        gbid.id_decompose(A, k, workspace=ws, out=(J, Z), sync=False)
+    e1.record(s)
+    torch.cuda.synchronize()
+    us = e0.elapsed_time(e1) * 1e3 / reps
+    us_graph = None
+    try:
+        g = torch.cuda.CUDAGraph()
+        cs = torch.cuda.Stream()
+        cs.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(cs):
+            with torch.cuda.graph(g, stream=cs):
+                for _ in range(20):
+                    gbid.id_decompose(A, k, workspace=ws, out=(J, Z), sync=False)
+        torch.cuda.current_stream().wait_stream(cs)
+        g.replay()
+        torch.cuda.synchronize()
+        e0.record(s)
+        for _ in range(max(3, reps // 20)):
+            g.replay()
+        e1.record(s)
+        torch.cuda.synchronize()
+        us_graph = e0.elapsed_time(e1) * 1e3 / (20 * max(3, reps // 20))
+    except Exception as exc:                 # capture refused: report the stream-ordered figure only
+        print(f"latency graph capture: {exc}", file=sys.stderr)
+        torch.cuda.synchronize()
+    best = us_graph if us_graph is not None else us
+    info = gbid.read_info(ws)
+    err = rel_error_gpu(A, J, Z)
+    trail = sum((200 - j) * (400 - j) for j in range(k)) * 8
+    return {"workload": "id_200x400_k20_f64", "us_per_id": us, "us_per_id_graph": us_graph,
+            "value": 1e6 / best, "unit": UNIT, "rel_err": err, "tail_bound": 2.0 ** -10,
+            "status": info["status_name"],
+            "l2_gbs_trailing_bytes": trail / (best * 1e-6) / 1e9,
+            "note": "trailing-GEMV bytes s*sum_j (m-j)(n-j) over the best per-ID time (A stays in L2)"}
+
+
+def batched_block(gbid, dev, steps):
+    """The batched form: 4096 FP32 matrices, m ~ U[32, 256], n ~ U[m, 4m],
+    k ~ U[8, 64], s_i = exp(-8 i / m), 10% non-negative sparse (seed 4), all
+    decomposed by one persistent launch. The inputs plus scratch (about 1.7 GB)
+    exceed L2, so no flush is needed between launches."""
+    import torch
+
+    import synth
+
+    probs = synth.batched_uneven(BATCH_COUNT, 4, dtype=torch.float32, device=dev)
+    mats = [p["A"] for p in probs]
+    ks = [p["k"] for p in probs]
+    plan = gbid.BatchedPlan(mats, ks)
+    for _ in range(3):
+        plan.run()
+    torch.cuda.synchronize()
+    s = torch.cuda.current_stream()
+    ev = []
+    for _ in range(steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        plan.run()
+        e1.record(s)
+        ev.append((e0, e1))
+    torch.cuda.synchronize()
+    ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    infos = plan.read_infos()
+    flops = sum(flops_cpqr(min(p["m"], p["n"]), max(p["m"], p["n"]), p["k"]) +
+                flops_solve(max(p["m"], p["n"]), p["k"]) for p in probs)
+    ratios = []
+    for p, J, Z in zip(probs, plan.J, plan.Z):
+        if p["kind"] != "lowrank":
+            continue
+        A64 = p["A"].double()
+        err = (torch.linalg.norm(A64 - A64[:, J.long()] @ Z.double()) / torch.linalg.norm(A64)).item()
+        tail = synth.tail_bound(synth.spectrum("exp8m", min(p["m"], p["n"]), m=p["m"]), p["k"])
+        if tail > 1e-5:        # below that the FP32 rounding of the input dominates the floor
+            ratios.append(err / tail)
+    statuses = {}
+    for i in infos:
+        statuses[i["status_name"]] = statuses.get(i["status_name"], 0) + 1
+    return {"workload": f"batched_{BATCH_COUNT}_uneven_f32", "ms_per_launch": ms,
+            "value": BATCH_COUNT * 1000.0 / ms, "unit": UNIT, "eff_tflops": flops / (ms * 1e-3) / 1e12,
+            "launches_per_step": 1, "statuses": statuses,
+            "err_over_tail": {"median": statistics.median(ratios), "max": max(ratios)}}
+
+
 def run_gbid(args):
     import torch
     import torch.distributed as dist
@@ -294,6 +479,16 @@ def run_gbid(args):
     import paper_2105_07076_gb300 as gbid
 
     dev = torch.device("cuda", local)
+    if args.only in ("randomized", "batched", "latency"):  # one side workload alone (profiling aid)
+        if args.only == "randomized":
+            side = randomized_block(gbid, dev, max(2, min(args.steps, 5)))
+        elif args.only == "latency":
+            side = latency_block(gbid, dev, args.steps)
+        else:
+            side = batched_block(gbid, dev, max(3, min(args.steps, 10)))
+        if rank == 0:
+            print(json.dumps(dict(side, n_gpus=world, steps=args.steps, warmup=args.warmup)), flush=True)
+        return 0
     hbm_peak, peak_src = load_peaks()
     flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)   # 256 MB > L2
     results = {}
@@ -324,13 +519,14 @@ def run_gbid(args):
         if name == "f64":
             achieved = fp64_flops_executed(M, N, K_RANK) / (cp_avg * 1e-3) / 1e12
             roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None, "kernel": "k_cpqr<double>",
+                    "frac": achieved / FP64_PEAK_TFLOPS, "traffic": NCU_TRAFFIC["f64"], "kernel": "k_cpqr<double>",
                     "kernel_ms": cp_avg,
                     "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (DFMA probe: 1.196)"}
         else:
             achieved = bytes_cpqr(M, N, K_RANK, s) / (cp_avg * 1e-3) / 1e9
             roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                    "frac": achieved / hbm_peak, "traffic": None, "kernel": "k_cpqr<float>", "kernel_ms": cp_avg,
+                    "frac": achieved / hbm_peak, "traffic": NCU_TRAFFIC["f32"], "kernel": "k_cpqr<float>",
+                    "kernel_ms": cp_avg,
                     "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured"
                     else "fallback"}
         eff = (flops_cpqr(M, N, K_RANK) + flops_solve(N, K_RANK)) / (mean_ms * 1e-3) / 1e12
@@ -343,6 +539,10 @@ def run_gbid(args):
         t = torch.tensor([1.0 / e2e_v], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_v = world / t.item()
+
+    rid = randomized_block(gbid, dev, max(2, min(args.steps, 5))) if args.only == "all" else None
+    bat = batched_block(gbid, dev, max(3, min(args.steps, 10))) if args.only == "all" else None
+    lat = latency_block(gbid, dev, args.steps) if args.only == "all" else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -375,6 +575,9 @@ def run_gbid(args):
                 "rel_err": r32["rel_err"], "status": r32["status"], "roofline": r32["roofline"],
                 "speedup_vs_f64": r32["value"] / r64["value"]},
         "solve_ms": {"f64": r64["solve_ms"], "f32": r32["solve_ms"]},
+        "randomized": rid,
+        "batched": bat,
+        "latency": lat,
         "cpu_baseline": cpu,
     }
     print(json.dumps(line), flush=True)
@@ -388,6 +591,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gbid", choices=["gbid", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only", default="all", choices=["all", "id", "randomized", "batched", "latency"],
+                    help="id: the 4096 x 8192 ID alone; randomized / batched: that side workload alone")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

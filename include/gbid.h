@@ -65,7 +65,11 @@ typedef struct {
      * never rewritten; every step corrects its product through the stored
      * reflectors). */
     int32_t nb;
-    int32_t reserved[7];
+    /* id_decompose_randomized only: 0 (default) = one least-squares
+     * refinement of T against A_J after the sketch (see id_refine); -1 = none
+     * (T stays the sketch's R11^{-1} R12). */
+    int32_t refine;
+    int32_t reserved[6];
 } id_opts;
 
 typedef struct {
@@ -77,7 +81,8 @@ typedef struct {
     double  max_abs_z;    /* largest |Z_ij|                                       */
     double  r00;          /* |R_00|, the largest column norm                      */
     int32_t nb;           /* panel width actually used                            */
-    int32_t reserved[5];
+    int32_t refined;      /* 1 when a least-squares refinement was applied to Z   */
+    int32_t reserved[4];
 } id_info;
 
 /* Bytes of device workspace id_decompose needs for this problem (k <= 16384).
@@ -204,6 +209,91 @@ int id_decompose_randomized(const void* A, id_dtype dtype, int64_t m, int64_t n,
                             int32_t* J, void* Z, int64_t ldz, void* work, size_t work_bytes, id_info* info,
                             void* stream);
 
+/* id_refine -- one least-squares refinement of an ID's interpolation matrix
+ * against A (the LS problem of Sec. 2.1, min ||A - C Z||_F with C = A[:, J]):
+ *     Z <- Z + (C^T C)^{-1} C^T (A - C Z),   Z[:, J] kept = I.
+ * For the randomized ID the skeleton J and the first Z come from the sketch;
+ * one step lands on the least-squares Z for that J up to rounding (the
+ * problem is linear), which is the Z Sec. 2.2 asks for.
+ * Arithmetic: C^T C in FP64 (products of FP32 values are exact in FP64) and
+ * its Cholesky factor U in FP64; U^{-1} in FP64, applied in FP32; the
+ * residual A - C Z and C^T times it as FP32-accurate GEMMs (cuBLAS, FP32
+ * compute emulated on the BF16 tensor cores where that is faster).
+ *   A     [in]     m x n FP32 row-major, lda >= n, m <= n (a column ID).
+ *   J     [in]     k skeleton columns (distinct, in [0, n)).
+ *   Z     [in,out] k x n FP32 row-major, ldz >= n; Z[:, J] = I on entry.
+ *   work  [in]     id_refine_workspace_size() bytes, 256-byte aligned.
+ *   info  [out]    HOST pointer or NULL (as for id_decompose): status ID_OK,
+ *                  refined = 1, and the Z statistics after the update. If
+ *                  C^T C is not numerically positive definite (rank(C) < k)
+ *                  Z is left unchanged and refined = 0.
+ * dtype must be ID_F32 (an FP64 ID's T = R11^{-1} R12 already solves the LS
+ * problem to FP64 accuracy). */
+size_t id_refine_workspace_size(id_dtype dtype, int64_t m, int64_t n, int64_t k);
+int id_refine(const void* A, id_dtype dtype, int64_t m, int64_t n, int64_t lda, int64_t k, const int32_t* J,
+              void* Z, int64_t ldz, void* work, size_t work_bytes, id_info* info, void* stream);
+
+/* id_backward -- gradient of a scalar loss L(Z) through the ID with the
+ * skeleton J held fixed (the differentiable form of Sec. 2.1's least-squares
+ * Z; the paper itself differentiates nothing):
+ *   Z[:, J] = I is constant, Z[:, rest] = T = C^+ B, C = A[:, J], B = A[:, rest];
+ *   with W = (C^T C)^{-1} dZ[:, rest]:
+ *   dA[:, rest] = C W,   dA[:, J] = (B - C T) W^T - C W T^T.
+ *   A   [in]  m x n FP32 row-major (m <= n), lda >= n.
+ *   J   [in]  k skeleton columns; Z [in] k x n FP32 (ldz >= n), the ID's Z for J.
+ *   dZ  [in]  k x n FP32 (lddz >= n): dL/dZ (its columns at J are ignored).
+ *   dA  [out] m x n FP32 (ldda >= n): dL/dA.
+ *   work [in] id_backward_workspace_size() bytes, 256-byte aligned.
+ * W is formed in FP64 (C^T C by exact products and double-float sums, its
+ * FP64 Cholesky factor applied twice), the products with C, A - C Z and Z as
+ * FP32-accurate GEMMs. info (HOST or NULL): ID_OK, ID_RANK_DEFICIENT if C^T C
+ * is not numerically positive definite (dA is then meaningless), ID_EINVAL
+ * for a J entry outside [0, n). dtype must be ID_F32. */
+size_t id_backward_workspace_size(id_dtype dtype, int64_t m, int64_t n, int64_t k);
+int id_backward(const void* A, id_dtype dtype, int64_t m, int64_t n, int64_t lda, int64_t k, const int32_t* J,
+                const void* Z, int64_t ldz, const void* dZ, int64_t lddz, void* dA, int64_t ldda, void* work,
+                size_t work_bytes, id_info* info, void* stream);
+
+/* ---------------------------------------------------------------- batched --
+ * id_decompose_batched -- rank-k IDs of many independent small matrices, of
+ * uneven sizes, in ONE persistent launch (Sec. 2.1 for each matrix, with the
+ * m > n route of the Sec. 2 footnote per matrix). The paper's use case of
+ * many small IDs (a hierarchical compression) has no batched form in the
+ * paper itself; the arithmetic per matrix is that of id_decompose:
+ * Householder CPQR stopped after k pivots (residual norms taken exactly every
+ * step, ties to the smallest original index), T = R11^{-1} R12 in FP64.
+ *
+ *   problems   [in]  DEVICE array of `count` id_problem descriptors, read by
+ *                    the kernel (so the call can be captured in a CUDA graph
+ *                    and replayed with the same descriptors).
+ *   dtype      [in]  element type of every A and Z.
+ *   batch_work [in]  DEVICE scratch of ID_BATCHED_WORK_BYTES (the work queue).
+ *   infos      [out] DEVICE array of `count` id_info, one per problem. A
+ *                    descriptor that breaks a rule below gets status ID_EINVAL
+ *                    there; the other problems are still decomposed.
+ * Per problem: 1 <= k <= min(m, n), k <= ID_BATCHED_MAX_K,
+ * min(m, n) <= ID_BATCHED_MAX_MIN_DIM, lda >= n, ldz >= max(m, n), and `work`
+ * 256-byte aligned with id_batched_problem_workspace_size() bytes. A is read
+ * only; J (k int32) and Z (k x max(m, n), row-major) are as for id_decompose.
+ * Nothing is waited for; the call returns after enqueuing a 4-byte memset and
+ * one kernel. Returns ID_OK, ID_EINVAL (bad dtype, count < 0, NULL pointer),
+ * ID_ENOMEM (batch_work too small) or ID_ECUDA. count == 0 enqueues nothing.
+ * The paper has no batched entry point; this one is the library's own. */
+#define ID_BATCHED_MAX_K 64
+#define ID_BATCHED_MAX_MIN_DIM 1024
+#define ID_BATCHED_WORK_BYTES 256
+typedef struct {
+    const void* A;   /* m x n, row-major, leading dimension lda            */
+    int64_t m, n, lda, k;
+    int32_t* J;      /* k                                                   */
+    void* Z;         /* k x max(m, n), row-major, leading dimension ldz     */
+    int64_t ldz;
+    void* work;      /* id_batched_problem_workspace_size() bytes, scratch  */
+} id_problem;
+size_t id_batched_problem_workspace_size(id_dtype dtype, int64_t m, int64_t n, int64_t k);
+int id_decompose_batched(const id_problem* problems, int64_t count, id_dtype dtype, void* batch_work,
+                         size_t batch_work_bytes, id_info* infos, void* stream);
+
 /* id_info_read -- copy the device-side status of the last call that used
  * `work` to *info (host) and wait for `stream`. Returns info->status. */
 int id_info_read(const void* work, id_info* info, void* stream);
@@ -219,7 +309,7 @@ int64_t id_launch_count(id_dtype dtype, int64_t m, int64_t n, int64_t k, const i
  * id_trace_read waits for the recorded events, writes per class the summed
  * milliseconds and launch counts into ms[0..nkinds) and launches[0..nkinds)
  * (classes: 0 persistent CPQR, 1 back substitution, 2 sketch, 3 copy-in,
- * 4 Z scatter), clears the records and returns how many were read.
+ * 4 Z scatter, 5 batched ID), clears the records and returns how many were read.
  * Process-wide state; not thread-safe. */
 int id_trace_enable(int capacity);
 int id_trace_read(double* ms, int64_t* launches, int nkinds);

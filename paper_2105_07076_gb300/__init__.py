@@ -38,18 +38,20 @@ _DTYPES = {torch.float64: ID_F64, torch.float32: ID_F32}
 
 
 class IdOpts(ctypes.Structure):
-    _fields_ = [("nb", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+    _fields_ = [("nb", ctypes.c_int32), ("refine", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
 
 
 class IdInfo(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("rank", ctypes.c_int32), ("transposed", ctypes.c_int32),
                 ("n_recompute", ctypes.c_int32), ("n_gt2", ctypes.c_int64), ("max_abs_z", ctypes.c_double),
-                ("r00", ctypes.c_double), ("nb", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+                ("r00", ctypes.c_double), ("nb", ctypes.c_int32), ("refined", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
 
     def as_dict(self):
         return {"status": self.status, "status_name": STATUS_NAMES.get(self.status, str(self.status)),
                 "rank": self.rank, "transposed": bool(self.transposed), "n_recompute": self.n_recompute,
-                "n_gt2": self.n_gt2, "max_abs_z": self.max_abs_z, "r00": self.r00, "nb": self.nb}
+                "n_gt2": self.n_gt2, "max_abs_z": self.max_abs_z, "r00": self.r00, "nb": self.nb,
+                "refined": bool(self.refined)}
 
 
 # Return codes that mean the call itself failed; device-detected conditions
@@ -85,13 +87,20 @@ _SIG = {
     "id_rid_workspace_size": (ctypes.c_size_t, [_I64, _I64, _I64, _I64, _P]),
     "id_decompose_randomized": (ctypes.c_int, [_P, ctypes.c_int, _I64, _I64, _I64, _P, _I64, _I64, _I64, _P, _P, _P,
                                                _I64, _P, ctypes.c_size_t, _P, _P]),
+    "id_batched_problem_workspace_size": (ctypes.c_size_t, [ctypes.c_int, _I64, _I64, _I64]),
+    "id_decompose_batched": (ctypes.c_int, [_P, _I64, ctypes.c_int, _P, ctypes.c_size_t, _P, _P]),
+    "id_refine_workspace_size": (ctypes.c_size_t, [ctypes.c_int, _I64, _I64, _I64]),
+    "id_backward_workspace_size": (ctypes.c_size_t, [ctypes.c_int, _I64, _I64, _I64]),
+    "id_backward": (ctypes.c_int, [_P, ctypes.c_int, _I64, _I64, _I64, _I64, _P, _P, _I64, _P, _I64, _P, _I64, _P,
+                                   ctypes.c_size_t, _P, _P]),
+    "id_refine": (ctypes.c_int, [_P, ctypes.c_int, _I64, _I64, _I64, _I64, _P, _P, _I64, _P, ctypes.c_size_t, _P, _P]),
     "id_launch_count": (ctypes.c_int64, [ctypes.c_int, _I64, _I64, _I64, _P]),
     "id_trace_enable": (ctypes.c_int, [ctypes.c_int]),
     "id_trace_read": (ctypes.c_int, [_P, _P, ctypes.c_int]),
     "id_version": (ctypes.c_char_p, []),
 }
 
-TRACE_KINDS = ("cpqr", "solve", "sketch", "copy_in", "scatter")
+TRACE_KINDS = ("cpqr", "solve", "sketch", "copy_in", "scatter", "batched", "refine")
 
 
 def lib():
@@ -114,9 +123,10 @@ def exported_symbols():
     return list(_SIG)
 
 
-def _opts(nb: int):
+def _opts(nb: int, refine: bool = True):
     o = IdOpts()
     o.nb = int(nb)
+    o.refine = 0 if refine else -1
     return o
 
 
@@ -235,18 +245,19 @@ def id_sketch(A: torch.Tensor, omega: torch.Tensor, *, out: torch.Tensor | None 
     return Y, (info.as_dict() if sync else None)
 
 
-def rid_workspace(m: int, n: int, l: int, k: int, nb: int = 0, device="cuda") -> Workspace:
-    o = _opts(nb)
+def rid_workspace(m: int, n: int, l: int, k: int, nb: int = 0, device="cuda", refine: bool = True) -> Workspace:
+    o = _opts(nb, refine)
     nbytes = int(lib().id_rid_workspace_size(m, n, l, k, ctypes.byref(o)))
     if nbytes == 0:
         raise IdError(ID_EINVAL, "id_rid_workspace_size")
     return Workspace(torch.empty(nbytes, dtype=torch.uint8, device=device))
 
 
-def id_decompose_randomized(A: torch.Tensor, omega: torch.Tensor, k: int, *, nb: int = 0,
+def id_decompose_randomized(A: torch.Tensor, omega: torch.Tensor, k: int, *, nb: int = 0, refine: bool = True,
                             workspace: Workspace | None = None, out: tuple | None = None, sync: bool = True):
     """Randomized rank-k ID from the sketch Y = omega @ A (A FP32 m x n, m <= n;
-    omega BF16 l x m). Returns (J, Z, info) with A ~= A[:, J] @ Z."""
+    omega BF16 l x m). Returns (J, Z, info) with A ~= A[:, J] @ Z. With refine
+    (the default) Z gets one least-squares refinement against A_J."""
     _check_cuda_matrix(A, "A")
     if A.dtype != torch.float32 or omega.dtype != torch.bfloat16 or not omega.is_cuda or omega.stride(1) != 1:
         raise ValueError("A must be float32 and omega a row-major CUDA bfloat16 matrix")
@@ -254,13 +265,13 @@ def id_decompose_randomized(A: torch.Tensor, omega: torch.Tensor, k: int, *, nb:
     l = omega.shape[0]
     dev = A.device
     if workspace is None:
-        workspace = rid_workspace(m, n, l, k, nb, dev)
+        workspace = rid_workspace(m, n, l, k, nb, dev, refine)
     if out is None:
         J = torch.empty(k, dtype=torch.int32, device=dev)
         Z = torch.empty(k, n, dtype=torch.float32, device=dev)
     else:
         J, Z = out
-    o = _opts(nb)
+    o = _opts(nb, refine)
     info = IdInfo()
     with torch.cuda.device(dev):
         rc = lib().id_decompose_randomized(A.data_ptr(), ID_F32, m, n, A.stride(0), omega.data_ptr(), l,
@@ -270,6 +281,79 @@ def id_decompose_randomized(A: torch.Tensor, omega: torch.Tensor, k: int, *, nb:
     if rc in _CALL_ERRORS:
         raise IdError(rc, "id_decompose_randomized")
     return J, Z, (info.as_dict() if sync else None)
+
+
+def id_refine(A: torch.Tensor, J: torch.Tensor, Z: torch.Tensor, *, workspace: Workspace | None = None,
+              sync: bool = True):
+    """One least-squares refinement of Z (k x n FP32, in place) against the FP32 CUDA matrix A
+    (m x n, m <= n) for the skeleton J: Z <- Z + (C^T C)^{-1} C^T (A - C Z), C = A[:, J]."""
+    _check_cuda_matrix(A, "A")
+    if A.dtype != torch.float32 or Z.dtype != torch.float32 or not Z.is_cuda or Z.stride(1) != 1:
+        raise ValueError("A and Z must be row-major float32 CUDA matrices")
+    if J.dtype != torch.int32 or not J.is_cuda:
+        raise ValueError("J must be an int32 CUDA vector")
+    m, n = A.shape
+    k = J.numel()
+    dev = A.device
+    if workspace is None:
+        nbytes = int(lib().id_refine_workspace_size(ID_F32, m, n, k))
+        if nbytes == 0:
+            raise IdError(ID_EINVAL, "id_refine_workspace_size")
+        workspace = Workspace(torch.empty(nbytes, dtype=torch.uint8, device=dev))
+    info = IdInfo()
+    with torch.cuda.device(dev):
+        rc = lib().id_refine(A.data_ptr(), ID_F32, m, n, A.stride(0), k, J.data_ptr(), Z.data_ptr(), Z.stride(0),
+                             workspace.buf.data_ptr(), workspace.buf.numel(), ctypes.byref(info) if sync else None,
+                             _stream(dev))
+    if rc in _CALL_ERRORS:
+        raise IdError(rc, "id_refine")
+    return Z, (info.as_dict() if sync else None)
+
+
+def id_backward(A: torch.Tensor, J: torch.Tensor, Z: torch.Tensor, dZ: torch.Tensor, *,
+                workspace: Workspace | None = None, out: torch.Tensor | None = None, sync: bool = True):
+    """dL/dA through the ID with the skeleton J frozen, given dL/dZ (FP32 CUDA, A m x n with m <= n)."""
+    _check_cuda_matrix(A, "A")
+    for name, X in (("Z", Z), ("dZ", dZ)):
+        if X.dtype != torch.float32 or not X.is_cuda or X.dim() != 2 or X.stride(1) != 1:
+            raise ValueError(f"{name} must be a row-major float32 CUDA matrix")
+    if A.dtype != torch.float32 or J.dtype != torch.int32 or not J.is_cuda:
+        raise ValueError("A must be float32 and J an int32 CUDA vector")
+    m, n = A.shape
+    k = J.numel()
+    dev = A.device
+    if workspace is None:
+        nbytes = int(lib().id_backward_workspace_size(ID_F32, m, n, k))
+        if nbytes == 0:
+            raise IdError(ID_EINVAL, "id_backward_workspace_size")
+        workspace = Workspace(torch.empty(nbytes, dtype=torch.uint8, device=dev))
+    dA = out if out is not None else torch.empty(m, n, dtype=torch.float32, device=dev)
+    info = IdInfo()
+    with torch.cuda.device(dev):
+        rc = lib().id_backward(A.data_ptr(), ID_F32, m, n, A.stride(0), k, J.data_ptr(), Z.data_ptr(), Z.stride(0),
+                               dZ.data_ptr(), dZ.stride(0), dA.data_ptr(), dA.stride(0), workspace.buf.data_ptr(),
+                               workspace.buf.numel(), ctypes.byref(info) if sync else None, _stream(dev))
+    if rc in _CALL_ERRORS:
+        raise IdError(rc, "id_backward")
+    return dA, (info.as_dict() if sync else None)
+
+
+class IdFunction(torch.autograd.Function):
+    """Z = ID(A) with the skeleton frozen after the forward pass (FP32 CUDA, m <= n):
+    forward runs id_decompose, backward id_backward."""
+
+    @staticmethod
+    def forward(ctx, A, k):
+        J, Z, _ = id_decompose(A.contiguous(), k, sync=False)
+        ctx.save_for_backward(A, J, Z)
+        ctx.mark_non_differentiable(J)
+        return J, Z
+
+    @staticmethod
+    def backward(ctx, dJ, dZ):
+        A, J, Z = ctx.saved_tensors
+        dA, _ = id_backward(A.contiguous(), J, Z, dZ.contiguous(), sync=False)
+        return dA, None
 
 
 def read_info(workspace: Workspace) -> dict:
@@ -374,3 +458,91 @@ def trace_read() -> dict:
 
 def version() -> str:
     return lib().id_version().decode()
+
+
+# ------------------------------------------------------------------ batched --
+BATCHED_MAX_K = 64            # ID_BATCHED_MAX_K in gbid.h
+BATCHED_MAX_MIN_DIM = 1024    # ID_BATCHED_MAX_MIN_DIM
+BATCHED_WORK_BYTES = 256      # ID_BATCHED_WORK_BYTES
+
+
+class IdProblem(ctypes.Structure):
+    _fields_ = [("A", ctypes.c_void_p), ("m", ctypes.c_int64), ("n", ctypes.c_int64), ("lda", ctypes.c_int64),
+                ("k", ctypes.c_int64), ("J", ctypes.c_void_p), ("Z", ctypes.c_void_p), ("ldz", ctypes.c_int64),
+                ("work", ctypes.c_void_p)]
+
+
+class BatchedPlan:
+    """Descriptors, outputs and scratch of id_decompose_batched for a fixed list
+    of CUDA matrices (one dtype, one device). ``run()`` enqueues one memset and
+    one kernel and never waits or allocates, so it can be captured in a CUDA
+    graph and replayed. Problems are queued largest first (k m n descending) so
+    that the persistent CTAs finish together; outputs keep the caller's order.
+    """
+
+    def __init__(self, mats: list, ks: list):
+        if len(mats) != len(ks):
+            raise ValueError("one k per matrix")
+        if not mats:
+            raise ValueError("empty batch")
+        dt = mats[0].dtype
+        dev = mats[0].device
+        for A in mats:
+            _check_cuda_matrix(A, "A")
+            if A.dtype != dt or A.device != dev:
+                raise ValueError("every matrix must share one dtype and device")
+        self.dtype, self.device, self.mats, self.ks = dt, dev, list(mats), [int(k) for k in ks]
+        sizes = []
+        for A, k in zip(self.mats, self.ks):
+            nbytes = int(lib().id_batched_problem_workspace_size(_DTYPES[dt], A.shape[0], A.shape[1], k))
+            if nbytes == 0:
+                raise IdError(ID_EINVAL, f"batched problem {tuple(A.shape)} k={k}")
+            sizes.append(nbytes)
+        offs, total = [], 0
+        for nb in sizes:
+            offs.append(total)
+            total += (nb + 255) // 256 * 256
+        self.work = torch.empty(total, dtype=torch.uint8, device=dev)
+        self.J = [torch.empty(k, dtype=torch.int32, device=dev) for k in self.ks]
+        self.Z = [torch.empty(k, max(A.shape), dtype=dt, device=dev) for A, k in zip(self.mats, self.ks)]
+        order = sorted(range(len(self.mats)), key=lambda i: -self.ks[i] * self.mats[i].shape[0] * self.mats[i].shape[1])
+        self.order = order
+        arr = (IdProblem * len(order))()
+        base = self.work.data_ptr()
+        for slot, i in enumerate(order):
+            A = self.mats[i]
+            arr[slot] = IdProblem(A.data_ptr(), A.shape[0], A.shape[1], A.stride(0), self.ks[i],
+                                  self.J[i].data_ptr(), self.Z[i].data_ptr(), self.Z[i].stride(0), base + offs[i])
+        raw = torch.frombuffer(bytearray(bytes(arr)), dtype=torch.uint8)
+        self.desc = raw.to(dev)
+        self.infos = torch.zeros(len(order) * ctypes.sizeof(IdInfo), dtype=torch.uint8, device=dev)
+        self.batch_work = torch.zeros(BATCHED_WORK_BYTES, dtype=torch.uint8, device=dev)
+
+    def __len__(self):
+        return len(self.mats)
+
+    def run(self):
+        with torch.cuda.device(self.device):
+            rc = lib().id_decompose_batched(self.desc.data_ptr(), len(self.order), _DTYPES[self.dtype],
+                                            self.batch_work.data_ptr(), self.batch_work.numel(),
+                                            self.infos.data_ptr(), _stream(self.device))
+        if rc in _CALL_ERRORS:
+            raise IdError(rc, "id_decompose_batched")
+
+    def read_infos(self) -> list:
+        """Per-problem info dicts in the caller's order (waits for the device)."""
+        raw = self.infos.cpu().numpy().tobytes()
+        sz = ctypes.sizeof(IdInfo)
+        out = [None] * len(self.order)
+        for slot, i in enumerate(self.order):
+            out[i] = IdInfo.from_buffer_copy(raw[slot * sz:(slot + 1) * sz]).as_dict()
+        return out
+
+
+def id_decompose_batched(mats: list, ks: list, *, sync: bool = True):
+    """Rank-k_i IDs of the CUDA matrices mats[i] in one launch. Returns (Js, Zs, infos, plan);
+    infos is None when sync is False (read them later with plan.read_infos())."""
+    plan = BatchedPlan(mats, ks)
+    plan.run()
+    return plan.J, plan.Z, (plan.read_infos() if sync else None), plan
+

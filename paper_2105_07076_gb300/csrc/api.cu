@@ -177,10 +177,13 @@ int64_t rid_ldy(int64_t n) { return (n + 3) / 4 * 4; }
 
 // Workspace of the randomized ID: the CPQR/solve layout of the l x n sketch,
 // then Y itself and the sketch kernel's status word.
-size_t rid_bytes(int64_t n, int64_t l, int64_t k, const id_opts* opts, Layout* out) {
+bool rid_refine(const id_opts* opts) { return !opts || opts->refine >= 0; }
+
+size_t rid_bytes(int64_t m, int64_t n, int64_t l, int64_t k, const id_opts* opts, Layout* out) {
     const Layout L = make_layout(ID_F32, (int)l, (int)n, (int)k, opts, true, true);
     if (out) *out = L;
-    return L.total + align_up(4 * (size_t)l * rid_ldy(n)) + kAlign;
+    const size_t base = L.total + align_up(4 * (size_t)l * rid_ldy(n)) + kAlign;
+    return base + (rid_refine(opts) ? refine_bytes(m, n, k) : 0);
 }
 
 }  // namespace
@@ -282,7 +285,7 @@ size_t id_sketch_workspace_size(void) { return 1024; }
 
 size_t id_rid_workspace_size(int64_t m, int64_t n, int64_t l, int64_t k, const id_opts* opts) {
     if (m < 1 || n < 1 || k < 1 || l < k || l > 640 || l > m || m > n || !sizes_ok(l, n, k)) return 0;
-    return rid_bytes(n, l, k, opts, nullptr);
+    return rid_bytes(m, n, l, k, opts, nullptr);
 }
 
 int id_decompose_randomized(const void* A, id_dtype dtype, int64_t m, int64_t n, int64_t lda,
@@ -300,7 +303,7 @@ int id_decompose_randomized(const void* A, id_dtype dtype, int64_t m, int64_t n,
     if (configure_once()) return ID_ECUDA;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     Layout L;
-    rid_bytes(n, l, k, opts, &L);
+    rid_bytes(m, n, l, k, opts, &L);
     char* base = static_cast<char*>(work);
     const int64_t ldy = rid_ldy(n);
     float* Y = reinterpret_cast<float*>(base + L.total);
@@ -320,6 +323,63 @@ int id_decompose_randomized(const void* A, id_dtype dtype, int64_t m, int64_t n,
     if (solve_run<float>(P.W, P.ldw, (int)k, (int)n, Tm, ldt, s) != cudaSuccess) return ID_ECUDA;
     if (scatter_z<float>(P.perm, Tm, ldt, (int)k, (int)n, Z, ldz, J, dinfo, s) != cudaSuccess) return ID_ECUDA;
     if (finalize_info(P.st, dinfo, (int)k, 0, P.nb, s, sk_status) != cudaSuccess) return ID_ECUDA;
+    // 5. one least-squares refinement of T against A_J
+    if (rid_refine(opts)) {
+        void* rws = base + L.total + align_up(4 * (size_t)l * ldy) + kAlign;
+        rc = refine_run(static_cast<const float*>(A), m, n, lda, (int)k, J, static_cast<float*>(Z), ldz, rws, dinfo,
+                        s);
+        if (rc != ID_OK) return rc;
+    }
+    if (info) return read_info(work, info, s);
+    return ID_OK;
+}
+
+size_t id_backward_workspace_size(id_dtype dtype, int64_t m, int64_t n, int64_t k) {
+    if (dtype != ID_F32 || m < 1 || n < 1 || k < 1 || k > m || m > n || k > 16384) return 0;
+    if (m > ((int64_t)1 << 31) - 1 || n > ((int64_t)1 << 31) - 1) return 0;
+    return align_up(sizeof(DevInfo)) + backward_bytes(m, n, k);
+}
+
+int id_backward(const void* A, id_dtype dtype, int64_t m, int64_t n, int64_t lda, int64_t k, const int32_t* J,
+                const void* Z, int64_t ldz, const void* dZ, int64_t lddz, void* dA, int64_t ldda, void* work,
+                size_t work_bytes, id_info* info, void* stream) {
+    if (!A || !J || !Z || !dZ || !dA || !work) return ID_EINVAL;
+    const size_t need = id_backward_workspace_size(dtype, m, n, k);
+    if (need == 0) return ID_EINVAL;
+    if (lda < n || ldz < n || lddz < n || ldda < n || !aligned(work, 256)) return ID_EINVAL;
+    if (work_bytes < need) return ID_ENOMEM;
+    if (configure_once()) return ID_ECUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    DevInfo* dinfo = static_cast<DevInfo*>(work);
+    if (refine_info_init(dinfo, (int)k, s) != cudaSuccess) return ID_ECUDA;
+    const int rc = backward_run(static_cast<const float*>(A), m, n, lda, (int)k, J, static_cast<const float*>(Z), ldz,
+                                static_cast<const float*>(dZ), lddz, static_cast<float*>(dA), ldda,
+                                static_cast<char*>(work) + align_up(sizeof(DevInfo)), dinfo, s);
+    if (rc != ID_OK) return rc;
+    if (info) return read_info(work, info, s);
+    return ID_OK;
+}
+
+size_t id_refine_workspace_size(id_dtype dtype, int64_t m, int64_t n, int64_t k) {
+    if (dtype != ID_F32 || m < 1 || n < 1 || k < 1 || k > m || m > n || k > 16384) return 0;
+    if (m > ((int64_t)1 << 31) - 1 || n > ((int64_t)1 << 31) - 1) return 0;
+    return align_up(sizeof(DevInfo)) + refine_bytes(m, n, k);
+}
+
+int id_refine(const void* A, id_dtype dtype, int64_t m, int64_t n, int64_t lda, int64_t k, const int32_t* J, void* Z,
+              int64_t ldz, void* work, size_t work_bytes, id_info* info, void* stream) {
+    if (!A || !J || !Z || !work) return ID_EINVAL;
+    const size_t need = id_refine_workspace_size(dtype, m, n, k);
+    if (need == 0) return ID_EINVAL;
+    if (lda < n || ldz < n || !aligned(work, 256)) return ID_EINVAL;
+    if (work_bytes < need) return ID_ENOMEM;
+    if (configure_once()) return ID_ECUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    DevInfo* dinfo = static_cast<DevInfo*>(work);
+    if (refine_info_init(dinfo, (int)k, s) != cudaSuccess) return ID_ECUDA;
+    const int rc = refine_run(static_cast<const float*>(A), m, n, lda, (int)k, J, static_cast<float*>(Z), ldz,
+                              static_cast<char*>(work) + align_up(sizeof(DevInfo)), dinfo, s);
+    if (rc != ID_OK) return rc;
     if (info) return read_info(work, info, s);
     return ID_OK;
 }

@@ -1,0 +1,546 @@
+// Batched ID: many small, unevenly sized matrices in one persistent launch
+// (Sec. 2.1 applied to every matrix of the batch independently).
+//
+// The grid is sized to the resident capacity of the GPU; each CTA takes
+// problems from an atomic queue and runs the whole ID of one matrix:
+//   1. X (A, or A^T when m > n: the Sec. 2 footnote) is copied column-major
+//      into the problem's scratch W; column norms give the first pivot.
+//   2. k Householder steps, right-looking and unblocked. Columns are never
+//      moved: perm maps positions to columns of W. Warp 0 forms the
+//      reflector of the pivot column (beta = -sign(x_j) ||x||, v_j = 1,
+//      tau = (beta - x_j) / beta); then every warp updates a group of
+//      trailing columns held in registers, W(j:m, l) -= tau v (v^T W(j:m, l)),
+//      and takes the EXACT squared residual norm ||W(j+1:m, l)||^2 of the
+//      updated column (the data are already in registers, so this costs what
+//      a downdate would; squares of y / 2^e, 2^e near the largest column
+//      norm, summed in the working precision) for the next pivot's argmax
+//      (ties: smallest original column index).
+//   3. T = R11^{-1} R12 by back substitution in FP64 (R11 staged in shared
+//      memory; a warp solves four right-hand sides at a time, lane = row),
+//      written straight into Z through perm; Z[:, J] = I, J = perm[0:k].
+// Per-problem status (argument check, non-finite input, numerical rank) goes
+// to that problem's id_info. Nothing waits on another CTA: the only shared
+// state is the queue counter.
+#include <cuda_runtime.h>
+#include <float.h>
+#include <math.h>
+
+#include <mutex>
+
+#include "common.cuh"
+#include "cpqr.cuh"
+#include "gbid.h"
+#include "trace.cuh"
+
+namespace gbid {
+namespace {
+
+constexpr int kBThreads = 256;
+constexpr int kBWarps = kBThreads / kWarp;
+constexpr int kBRows = 8;                    // rows per lane per pass (256-row chunks)
+constexpr int kBCopy = 16;                   // loads in flight per thread in the copy-in
+constexpr int kBMaxK = ID_BATCHED_MAX_K;
+constexpr int kBMaxM = ID_BATCHED_MAX_MIN_DIM;
+
+__host__ __device__ inline size_t b_align(size_t x) { return (x + 255) & ~size_t(255); }
+
+struct BLayout {
+    size_t perm, total;
+    int ldw;
+};
+
+__host__ __device__ inline BLayout b_layout(int s, int64_t mx, int64_t nx) {
+    BLayout L;
+    L.ldw = (int)((mx + 3) / 4 * 4);
+    L.perm = b_align((size_t)s * L.ldw * nx);
+    L.total = L.perm + b_align(4 * (size_t)nx);
+    return L;
+}
+
+__device__ ArgMax b_block_argmax(ArgMax a, ArgMax* red) {
+    a = warp_argmax(a);
+    const int w = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
+    __syncthreads();
+    if (lane == 0) red[w] = a;
+    __syncthreads();
+    a = lane < kBWarps ? red[lane] : empty_argmax();
+    return warp_argmax(a);
+}
+
+__device__ double b_block_sum(double v, double* red) {
+    v = warp_sum(v);
+    const int w = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
+    __syncthreads();
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    v = lane < kBWarps ? red[lane] : 0.0;
+    return warp_sum(v);
+}
+
+__device__ double b_block_max(double v, double* red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const int w = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
+    __syncthreads();
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    v = lane < kBWarps ? red[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Pivot candidate in the working precision: the SQUARED residual norm (same
+// order as the norm, no square root), ties to the smaller original index.
+// Comparing in T keeps the per-column epilogue off the FP64 pipe, which on
+// this GPU runs one warp instruction per 16 clocks per SM.
+template <typename T>
+struct Cand {
+    T val;
+    int orig, pos;
+};
+
+template <typename T>
+__device__ __forceinline__ Cand<T> cand_empty() {
+    Cand<T> c;
+    c.val = T(-1);
+    c.orig = 0x7fffffff;
+    c.pos = -1;
+    return c;
+}
+
+template <typename T>
+__device__ __forceinline__ bool cand_better(const Cand<T>& a, const Cand<T>& b) {
+    return a.val > b.val || (a.val == b.val && a.orig < b.orig);
+}
+
+template <typename T>
+__device__ __forceinline__ ArgMax cand_to_argmax(const Cand<T>& c) {
+    ArgMax a;
+    a.val = (double)c.val;
+    a.orig = c.orig;
+    a.pos = c.pos;
+    return a;
+}
+
+// Trailing update of the CG columns at positions pos0 .. pos0+CG-1 (those
+// below nx) by one warp, and their exact squared residual norms on rows
+// j+1..mx-1.
+// The squares are taken of y * ysc, ysc a power of two near 1 / max column
+// norm, so they neither overflow nor underflow in the working precision.
+template <typename T, int CG>
+__device__ void b_update_group(T* W, int ldw, const int* perm, int mx, int nx, int j, int pos0, T tauT, T ysc,
+                               const T* v_s, Cand<T>& best) {
+    const int lane = threadIdx.x % kWarp;
+    int col[CG];
+    bool ok[CG];
+#pragma unroll
+    for (int g = 0; g < CG; ++g) {
+        ok[g] = pos0 + g < nx;
+        col[g] = ok[g] ? perm[pos0 + g] : 0;
+    }
+    T d[CG];
+    T ss[CG];   // sums of squares in the working precision (at most 8 terms per lane per chunk)
+#pragma unroll
+    for (int g = 0; g < CG; ++g) {
+        d[g] = T(0);
+        ss[g] = T(0);
+    }
+    if (mx - j <= kWarp * kBRows) {
+        // the whole column segment fits in registers: one read, one write
+        T x[CG][kBRows];
+#pragma unroll
+        for (int g = 0; g < CG; ++g)
+#pragma unroll
+            for (int q = 0; q < kBRows; ++q) {
+                const int i = j + lane + kWarp * q;
+                x[g][q] = (ok[g] && i < mx) ? W[(int64_t)col[g] * ldw + i] : T(0);
+            }
+#pragma unroll
+        for (int q = 0; q < kBRows; ++q) {
+            const int i = j + lane + kWarp * q;
+            const T vi = i < mx ? v_s[i] : T(0);
+#pragma unroll
+            for (int g = 0; g < CG; ++g) d[g] += vi * x[g][q];
+        }
+#pragma unroll
+        for (int g = 0; g < CG; ++g) d[g] = warp_sum(d[g]);
+#pragma unroll
+        for (int q = 0; q < kBRows; ++q) {
+            const int i = j + lane + kWarp * q;
+            if (i < mx) {
+                const T vi = v_s[i];
+#pragma unroll
+                for (int g = 0; g < CG; ++g) {
+                    const T y = x[g][q] - (tauT * d[g]) * vi;
+                    if (ok[g]) W[(int64_t)col[g] * ldw + i] = y;
+                    if (i > j) ss[g] += (y * ysc) * (y * ysc);
+                }
+            }
+        }
+    } else {
+        for (int i0 = j; i0 < mx; i0 += kWarp * kBRows) {
+#pragma unroll
+            for (int q = 0; q < kBRows; ++q) {
+                const int i = i0 + lane + kWarp * q;
+                if (i < mx) {
+                    const T vi = v_s[i];
+#pragma unroll
+                    for (int g = 0; g < CG; ++g)
+                        if (ok[g]) d[g] += vi * W[(int64_t)col[g] * ldw + i];
+                }
+            }
+        }
+#pragma unroll
+        for (int g = 0; g < CG; ++g) d[g] = warp_sum(d[g]);
+        for (int i0 = j; i0 < mx; i0 += kWarp * kBRows) {
+#pragma unroll
+            for (int q = 0; q < kBRows; ++q) {
+                const int i = i0 + lane + kWarp * q;
+                if (i < mx) {
+                    const T vi = v_s[i];
+#pragma unroll
+                    for (int g = 0; g < CG; ++g) {
+                        if (!ok[g]) continue;
+                        T* p = W + (int64_t)col[g] * ldw + i;
+                        const T y = *p - (tauT * d[g]) * vi;
+                        *p = y;
+                        if (i > j) ss[g] += (y * ysc) * (y * ysc);
+                    }
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int g = 0; g < CG; ++g) {
+        const T s = warp_sum(ss[g]);
+        if (ok[g]) {
+            Cand<T> c;
+            c.val = isfinite(s) ? s : T(-1);
+            c.orig = col[g];
+            c.pos = pos0 + g;
+            if (cand_better(c, best)) best = c;
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBThreads, 3) k_id_batched(const id_problem* __restrict__ probs, int count,
+                                                        unsigned* queue, id_info* __restrict__ infos) {
+    constexpr int CG = sizeof(T) == 4 ? 4 : 2;          // trailing columns per warp and pass
+    const double eps = sizeof(T) == 8 ? DBL_EPSILON : (double)FLT_EPSILON;
+    __shared__ T v_s[kBMaxM];
+    __shared__ double r11[kBMaxK][kBMaxK + 1];
+    __shared__ double rinv[kBMaxK];
+    __shared__ ArgMax red_a[kBWarps];
+    __shared__ double red_d[kBWarps];
+    __shared__ double sc[2];
+    __shared__ int s_b;
+    const int t = threadIdx.x, lane = t % kWarp, w = t / kWarp;
+
+    for (;;) {
+        __syncthreads();
+        if (t == 0) s_b = (int)atomicAdd(queue, 1u);
+        __syncthreads();
+        const int b = s_b;
+        if (b >= count) break;
+        const id_problem pr = probs[b];
+        const int64_t mn = pr.m < pr.n ? pr.m : pr.n;
+        const bool valid = pr.A && pr.J && pr.Z && pr.work && pr.m >= 1 && pr.n >= 1 && pr.k >= 1 && pr.k <= mn &&
+                           pr.k <= kBMaxK && mn <= kBMaxM && pr.lda >= pr.n &&
+                           pr.ldz >= (pr.m > pr.n ? pr.m : pr.n) && (reinterpret_cast<uintptr_t>(pr.work) & 255) == 0;
+        if (!valid) {
+            if (t == 0) {
+                id_info r = {};
+                r.status = ID_EINVAL;
+                infos[b] = r;
+            }
+            continue;
+        }
+        const bool trans = pr.m > pr.n;
+        const int mx = (int)mn, nx = (int)(trans ? pr.m : pr.n), k = (int)pr.k;
+        const BLayout L = b_layout(sizeof(T), mx, nx);
+        const int ldw = L.ldw;
+        T* W = static_cast<T*>(pr.work);
+        int* perm = reinterpret_cast<int*>(static_cast<char*>(pr.work) + L.perm);
+        const T* A = static_cast<const T*>(pr.A);
+
+        // 1. X -> W (column-major) with the column norms and the first pivot;
+        //    kBCopy loads in flight per thread
+        ArgMax best = empty_argmax();
+        int nonfinite = 0;
+        if (!trans) {
+            // thread per column: the rows of A are read coalesced across the warp
+            for (int l = t; l < nx; l += kBThreads) {
+                double s = 0.0;
+                for (int i0 = 0; i0 < mx; i0 += kBCopy) {
+                    T v[kBCopy];
+#pragma unroll
+                    for (int q = 0; q < kBCopy; ++q)
+                        v[q] = i0 + q < mx ? A[(int64_t)(i0 + q) * pr.lda + l] : T(0);
+#pragma unroll
+                    for (int q = 0; q < kBCopy; ++q) {
+                        if (i0 + q < mx) W[(int64_t)l * ldw + i0 + q] = v[q];
+                        s = fma((double)v[q], (double)v[q], s);
+                    }
+                }
+                perm[l] = l;
+                if (!isfinite(s)) nonfinite = 1;
+                ArgMax c;
+                c.val = isfinite(s) ? s : -1.0;
+                c.orig = l;
+                c.pos = l;
+                if (better(c, best)) best = c;
+            }
+        } else {
+            // warp per column of X = row of A (contiguous)
+            for (int l = w; l < nx; l += kBWarps) {
+                double s = 0.0;
+                for (int i0 = lane; i0 < mx; i0 += kWarp * kBCopy) {
+                    T v[kBCopy];
+#pragma unroll
+                    for (int q = 0; q < kBCopy; ++q) {
+                        const int i = i0 + kWarp * q;
+                        v[q] = i < mx ? A[(int64_t)l * pr.lda + i] : T(0);
+                    }
+#pragma unroll
+                    for (int q = 0; q < kBCopy; ++q) {
+                        const int i = i0 + kWarp * q;
+                        if (i < mx) W[(int64_t)l * ldw + i] = v[q];
+                        s = fma((double)v[q], (double)v[q], s);
+                    }
+                }
+                s = warp_sum(s);
+                if (lane == 0) {
+                    perm[l] = l;
+                    if (!isfinite(s)) nonfinite = 1;
+                    ArgMax c;
+                    c.val = isfinite(s) ? s : -1.0;
+                    c.orig = l;
+                    c.pos = l;
+                    if (better(c, best)) best = c;
+                }
+            }
+        }
+        nonfinite = __syncthreads_or(nonfinite);
+        best = b_block_argmax(best, red_a);
+        T ysc = T(1);
+        if (best.val > 0.0) {
+            int e2;
+            frexp(sqrt(best.val), &e2);
+            ysc = (T)ldexp(1.0, -e2);
+        }
+
+        // 2. k Householder steps
+        double r00 = 0.0;
+        int rank = k;
+        const double rank_tol = sqrt((double)nx) * eps;   // |R_jj| <= sqrt(max(m, n)) eps |R_00|
+        for (int j = 0; j < k; ++j) {
+            const int p = best.pos >= j ? best.pos : j;
+            if (t == 0 && p != j) {
+                const int a = perm[j];
+                perm[j] = perm[p];
+                perm[p] = a;
+            }
+            __syncthreads();
+            T* xj = W + (int64_t)perm[j] * ldw;
+            if (w == 0) {
+                double ss = 0.0;
+                for (int i0 = j + 1 + lane; i0 < mx; i0 += kWarp * kBRows) {
+                    T v[kBRows];
+#pragma unroll
+                    for (int q = 0; q < kBRows; ++q) v[q] = i0 + kWarp * q < mx ? xj[i0 + kWarp * q] : T(0);
+#pragma unroll
+                    for (int q = 0; q < kBRows; ++q) ss = fma((double)v[q], (double)v[q], ss);
+                }
+                ss = warp_sum(ss);
+                const double x0 = (double)xj[j];
+                const double alpha = sqrt(fma(x0, x0, ss));
+                double beta = 0.0, tau = 0.0, scale = 0.0;
+                if (alpha != 0.0) {
+                    beta = x0 >= 0.0 ? -alpha : alpha;
+                    tau = (beta - x0) / beta;
+                    scale = 1.0 / (x0 - beta);
+                }
+                const T scaleT = (T)scale;
+                for (int i0 = j + 1 + lane; i0 < mx; i0 += kWarp * kBRows) {
+                    T v[kBRows];
+#pragma unroll
+                    for (int q = 0; q < kBRows; ++q) v[q] = i0 + kWarp * q < mx ? xj[i0 + kWarp * q] : T(0);
+#pragma unroll
+                    for (int q = 0; q < kBRows; ++q) {
+                        const int i = i0 + kWarp * q;
+                        if (i < mx) {
+                            xj[i] = v[q] * scaleT;
+                            v_s[i] = v[q] * scaleT;
+                        }
+                    }
+                }
+                if (lane == 0) {
+                    xj[j] = (T)beta;
+                    v_s[j] = T(1);
+                    sc[0] = beta;
+                    sc[1] = tau;
+                }
+            }
+            __syncthreads();
+            const double beta = sc[0];
+            if (j == 0) r00 = fabs(beta);
+            if (rank == k && (r00 == 0.0 || fabs(beta) <= rank_tol * r00)) rank = j;
+            const T tauT = (T)sc[1];
+            // the last step still updates: it writes row k-1 of R12
+            Cand<T> bw = cand_empty<T>();
+            for (int pos0 = j + 1 + w * CG; pos0 < nx; pos0 += kBWarps * CG)
+                b_update_group<T, CG>(W, ldw, perm, mx, nx, j, pos0, tauT, ysc, v_s, bw);
+            best = b_block_argmax(cand_to_argmax(bw), red_a);   // its barriers also order this step's writes
+        }
+
+        // 3. T = R11^{-1} R12 (FP64), Z, J
+        for (int e0 = t; e0 < k * k; e0 += 4 * kBThreads) {
+            double v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int e = e0 + u * kBThreads, i = e / k, q = e % k;
+                v[u] = (e < k * k && i <= q) ? (double)W[(int64_t)perm[q] * ldw + i] : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int e = e0 + u * kBThreads;
+                if (e < k * k) r11[e / k][e % k] = v[u];
+            }
+        }
+        __syncthreads();
+        for (int i = t; i < k; i += kBThreads) rinv[i] = 1.0 / r11[i][i];
+        __syncthreads();
+        // R(r, i) / R(i, i) above the diagonal: the substitution then needs one
+        // FMA per step, b_r -= (R(r,i) / R(i,i)) b_i, and one scaling at the end
+        for (int e = t; e < k * k; e += kBThreads) {
+            const int r = e / k, i = e % k;
+            if (r < i) r11[r][i] *= rinv[i];
+        }
+        __syncthreads();
+        T* Z = static_cast<T*>(pr.Z);
+        const int64_t ldz = pr.ldz;
+        T zmax = T(1);                  // the identity block holds ones
+        float gt2 = 0.0f;
+        for (int l0 = k + 4 * w; l0 < nx; l0 += 4 * kBWarps) {
+            double x[4][2];
+            int colq[4];
+#pragma unroll
+            for (int qq = 0; qq < 4; ++qq) {
+                const int l = l0 + qq;
+                colq[qq] = l < nx ? perm[l] : -1;
+#pragma unroll
+                for (int s = 0; s < 2; ++s) {
+                    const int i = lane + kWarp * s;
+                    x[qq][s] = (colq[qq] >= 0 && i < k) ? (double)W[(int64_t)colq[qq] * ldw + i] : 0.0;
+                }
+            }
+            // b_i (final once rows > i are applied) is broadcast; rows below 32
+            // only when k > 32; x = b / diag(R) at the end
+            const bool two = k > kWarp;
+            for (int i = k - 1; i >= 0; --i) {
+                const int own = i % kWarp, sl = i / kWarp;
+#pragma unroll
+                for (int qq = 0; qq < 4; ++qq) {
+                    const double bi = __shfl_sync(0xffffffffu, sl ? x[qq][1] : x[qq][0], own);
+                    if (lane < i) x[qq][0] = fma(-r11[lane][i], bi, x[qq][0]);
+                    if (two && lane + kWarp < i) x[qq][1] = fma(-r11[lane + kWarp][i], bi, x[qq][1]);
+                }
+            }
+#pragma unroll
+            for (int qq = 0; qq < 4; ++qq) {
+                x[qq][0] *= lane < k ? rinv[lane] : 0.0;
+                if (two) x[qq][1] *= lane + kWarp < k ? rinv[lane + kWarp] : 0.0;
+            }
+#pragma unroll
+            for (int qq = 0; qq < 4; ++qq) {
+                if (colq[qq] < 0) continue;
+#pragma unroll
+                for (int s = 0; s < 2; ++s) {
+                    const int i = lane + kWarp * s;
+                    if (i < k) {
+                        const T z = (T)x[qq][s];
+                        Z[(int64_t)i * ldz + colq[qq]] = z;
+                        const T a = fabs(z);
+                        zmax = a == a ? fmax(zmax, a) : T(INFINITY);
+                        if (a > T(2)) gt2 += 1.0f;
+                    }
+                }
+            }
+        }
+        for (int e = t; e < k * k; e += kBThreads) {
+            const int i = e / k, l = e % k;
+            Z[(int64_t)i * ldz + perm[l]] = i == l ? T(1) : T(0);
+        }
+        for (int l = t; l < k; l += kBThreads) pr.J[l] = perm[l];
+        const double zmax_b = b_block_max((double)zmax, red_d);
+        const double gt2_b = b_block_sum((double)gt2, red_d);
+        if (t == 0) {
+            id_info r = {};
+            r.status = nonfinite ? ID_ENONFINITE : (rank < k ? ID_RANK_DEFICIENT : ID_OK);
+            r.rank = rank;
+            r.transposed = trans ? 1 : 0;
+            r.n_recompute = 0;
+            r.n_gt2 = (int64_t)gt2_b;
+            r.max_abs_z = zmax_b;
+            r.r00 = r00;
+            r.nb = 1;
+            infos[b] = r;
+        }
+    }
+}
+
+int g_bnsm = 0;
+int g_bocc[2] = {0, 0};
+std::mutex g_bmu;
+
+template <typename T>
+int batched_grid(int count) {
+    const int slot = sizeof(T) == 8 ? 0 : 1;
+    {
+        std::lock_guard<std::mutex> lk(g_bmu);
+        if (g_bnsm == 0) {
+            int dev = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&g_bnsm, cudaDevAttrMultiProcessorCount, dev);
+        }
+        if (g_bocc[slot] == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_bocc[slot], k_id_batched<T>, kBThreads, 0);
+    }
+    const int cap = g_bnsm * (g_bocc[slot] > 0 ? g_bocc[slot] : 1);
+    return count < cap ? count : cap;
+}
+
+}  // namespace
+}  // namespace gbid
+
+using namespace gbid;
+
+extern "C" size_t id_batched_problem_workspace_size(id_dtype dtype, int64_t m, int64_t n, int64_t k) {
+    if (dtype != ID_F64 && dtype != ID_F32) return 0;
+    const int64_t mn = m < n ? m : n, mx = m < n ? n : m;
+    if (m < 1 || n < 1 || k < 1 || k > mn || k > kBMaxK || mn > kBMaxM || mx > (int64_t)1 << 24) return 0;
+    return b_layout(dtype == ID_F64 ? 8 : 4, mn, mx).total;
+}
+
+extern "C" int id_decompose_batched(const id_problem* problems, int64_t count, id_dtype dtype, void* batch_work,
+                                    size_t batch_work_bytes, id_info* infos, void* stream) {
+    if (dtype != ID_F64 && dtype != ID_F32) return ID_EINVAL;
+    if (count < 0 || count > INT32_MAX) return ID_EINVAL;
+    if (count == 0) return ID_OK;
+    if (!problems || !batch_work || !infos) return ID_EINVAL;
+    if (batch_work_bytes < ID_BATCHED_WORK_BYTES) return ID_ENOMEM;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    unsigned* queue = static_cast<unsigned*>(batch_work);
+    if (cudaMemsetAsync(queue, 0, sizeof(unsigned), s) != cudaSuccess) return ID_ECUDA;
+    const int tr = trace_begin(TraceKind::kBatched, s);
+    if (dtype == ID_F64) {
+        const int g = batched_grid<double>((int)count);
+        k_id_batched<double><<<g, kBThreads, 0, s>>>(problems, (int)count, queue, infos);
+    } else {
+        const int g = batched_grid<float>((int)count);
+        k_id_batched<float><<<g, kBThreads, 0, s>>>(problems, (int)count, queue, infos);
+    }
+    trace_end(tr, s);
+    return cudaGetLastError() == cudaSuccess ? ID_OK : ID_ECUDA;
+}

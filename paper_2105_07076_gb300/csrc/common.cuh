@@ -27,6 +27,14 @@ __device__ __forceinline__ bool better(const ArgMax& a, const ArgMax& b) {
     return a.val > b.val || (a.val == b.val && a.orig < b.orig);
 }
 
+__device__ __forceinline__ ArgMax empty_argmax() {
+    ArgMax a;
+    a.val = -1.0;
+    a.orig = 0x7fffffff;
+    a.pos = -1;
+    return a;
+}
+
 __device__ __forceinline__ ArgMax warp_argmax(ArgMax a) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {

@@ -44,14 +44,6 @@ __device__ __forceinline__ float dot_vec(const float4& a, const float4& b, float
     return fmaf(a.w, b.w, acc);
 }
 
-__device__ __forceinline__ ArgMax empty_argmax() {
-    ArgMax a;
-    a.val = -1.0;
-    a.orig = 0x7fffffff;
-    a.pos = -1;
-    return a;
-}
-
 // Block-wide argmax; result valid in every thread (blockDim.x <= 1024).
 __device__ ArgMax block_argmax(ArgMax a) {
     __shared__ ArgMax red[32];

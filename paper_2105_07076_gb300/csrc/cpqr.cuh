@@ -53,4 +53,17 @@ int sketch_run(const float* A, int64_t m, int64_t n, int64_t lda, const uint16_t
 cudaError_t finalize_info(const State* st, DevInfo* info, int k, int transposed, int nb, cudaStream_t s,
                           const int* extra_status = nullptr);
 
+// One least-squares refinement of Z against A (refine.cu). Returns an id_status;
+// updates info->info.refined and the Z statistics.
+size_t refine_bytes(int64_t m, int64_t n, int64_t k);
+cudaError_t refine_info_init(DevInfo* dinfo, int k, cudaStream_t s);   // status ID_OK, rank k, statistics zero
+int refine_run(const float* A, int64_t m, int64_t n, int64_t lda, int k, const int32_t* J, float* Z, int64_t ldz,
+               void* ws, DevInfo* dinfo, cudaStream_t s);
+
+// Gradient through the ID with the skeleton frozen (refine.cu). Returns an id_status.
+size_t backward_bytes(int64_t m, int64_t n, int64_t k);
+int backward_run(const float* A, int64_t m, int64_t n, int64_t lda, int k, const int32_t* J, const float* Z,
+                 int64_t ldz, const float* dZ, int64_t lddz, float* dA, int64_t ldda, void* ws, DevInfo* dinfo,
+                 cudaStream_t s);
+
 }  // namespace gbid

@@ -1,0 +1,598 @@
+// One least-squares refinement of an ID's interpolation matrix against A:
+//     Z <- Z + (C^T C)^{-1} C^T (A - C Z),   C = A[:, J]
+// (the least-squares problem of Sec. 2.1, min ||A - C Z||_F, taken one exact
+// Newton step from the Z the sketch gives; Sec. 2.2 asks for this Z).
+//
+//   1. C = A[:, J] gathered.
+//   2. G = C^T C with every product exact and the sums in double-float
+//      (about 48 bits), on the FP32 pipe (k_gram).
+//   3. G = U^T U by a blocked Cholesky in FP64 (32-wide panels: a one-warp
+//      diagonal factorisation, a forward substitution for the panel row, a
+//      tiled rank-32 update of the trailing upper triangle). A non-positive
+//      pivot (rank(C) < k) sets a flag and Z is left unchanged.
+//   4. U^{-1} by the library's blocked back substitution (R11 = U, R12 = I),
+//      rounded to FP32.
+//   5. Over column blocks of 4096: R_b = A_b - C Z_b, H_b = C^T R_b as
+//      FP32-accurate GEMMs (cuBLAS, FP32 compute emulated on the BF16 tensor
+//      cores where that is faster). Columns of J give R_b = 0 exactly
+//      (Z[:, J] = I), so they receive no update.
+//   6. D = U^{-1} (U^{-T} H) (FP32 GEMMs; the correction needs relative
+//      accuracy cond(U) u_32 only), Z += D, Z[:, J] = I restored, Z
+//      statistics recomputed.
+// cuBLAS runs only the plain GEMMs of step 5 and 6; it gets its workspace
+// from the caller's, so nothing is allocated per call (one handle per device
+// is created on first use).
+#include <cublas_v2.h>
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include <map>
+#include <mutex>
+
+#include "common.cuh"
+#include "cpqr.cuh"
+#include "gbid.h"
+#include "trace.cuh"
+
+namespace gbid {
+namespace {
+
+constexpr int kRThreads = 256;
+constexpr int kCholB = 32;
+constexpr int64_t kResCols = 4096;
+constexpr size_t kCublasWs = 32u << 20;
+
+size_t al(size_t x) { return (x + 255) / 256 * 256; }
+
+constexpr int kGramSplit = 16;   // row chunks of the Gram matrix
+
+struct RefLayout {
+    size_t flag, C32, Wa, Gp, Uinv64, Uinv32, Rb, H, Y1, cws, total;
+};
+
+RefLayout ref_layout(int64_t m, int64_t n, int64_t k) {
+    RefLayout L;
+    size_t off = 0;
+    auto take = [&](size_t b) {
+        const size_t o = off;
+        off = al(off + b);
+        return o;
+    };
+    L.flag = take(16);
+    L.C32 = take(4 * (size_t)m * k);
+    L.Wa = take(8 * (size_t)k * 2 * k);
+    L.Gp = take(8 * (size_t)kGramSplit * k * k);
+    L.Uinv64 = take(8 * (size_t)k * k);
+    L.Uinv32 = take(4 * (size_t)k * k);
+    L.Rb = take(4 * (size_t)m * (size_t)(n < kResCols ? n : kResCols));
+    L.H = take(4 * (size_t)k * n);
+    L.Y1 = take(4 * (size_t)k * n);
+    L.cws = take(kCublasWs);
+    L.total = off;
+    return L;
+}
+
+// flag[0]: 1 = C^T C not positive definite, 2 = a J entry outside [0, n).
+__global__ void k_check_j(const int32_t* J, int k, int64_t n, int* flag) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < k; c += gridDim.x * blockDim.x)
+        if (J[c] < 0 || J[c] >= n) flag[0] = 2;
+}
+
+__global__ void k_gather(const float* __restrict__ A, int64_t lda, int m, int k, int64_t n,
+                         const int32_t* __restrict__ J, float* __restrict__ C32) {
+    const int64_t total = (int64_t)m * k;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / k;
+        const int c = (int)(e % k);
+        const int jc = J[c];
+        const float v = (jc >= 0 && jc < n) ? A[i * lda + jc] : 0.0f;   // bad J: flagged, never read out of range
+        C32[e] = v;
+    }
+}
+
+// G = C^T C from C (m x k row-major FP32), upper triangle. Every product is
+// split exactly (p = a b, e = fma(a, b, -p)) and summed in double-float (a
+// pair of FP32 values, about 48 significant bits; TwoSum for the high part),
+// so the FP64 pipe, scarce on this GPU, is not used. 64 x 64 output tiles
+// (tile row <= tile column), 16 outputs per thread; blockIdx.z splits the m
+// rows into chunks whose FP64 partials P[z] are summed by k_gram_sum.
+constexpr int kGT = 64;       // output tile
+constexpr int kGK = 32;       // rows of C staged per pass
+
+// (hi, lo) += p + e with TwoSum on the high part; explicit round-to-nearest
+// intrinsics keep the compiler from contracting the error terms into FMAs.
+__device__ __forceinline__ void df_add(float& hi, float& lo, float p, float e) {
+    const float s = __fadd_rn(hi, p);
+    const float bp = __fsub_rn(s, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(p, bp));
+    lo = __fadd_rn(lo, __fadd_rn(err, e));
+    hi = s;
+}
+
+__global__ void __launch_bounds__(256) k_gram(const float* __restrict__ C, int m, int k, int rows_per,
+                                              double* __restrict__ P) {
+    const int ti = blockIdx.y, tj = blockIdx.x;
+    if (ti > tj) return;
+    __shared__ float As[kGK][kGT], Bs[kGK][kGT];
+    const int i0 = ti * kGT, j0 = tj * kGT;
+    const int r_lo = blockIdx.z * rows_per, r_hi = min(m, r_lo + rows_per);
+    const int t = threadIdx.x, ty = t / 16, tx = t % 16;
+    float hi[4][4], lo[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) hi[a][b] = lo[a][b] = 0.0f;
+    for (int r0 = r_lo; r0 < r_hi; r0 += kGK) {
+        __syncthreads();
+        for (int e = t; e < kGK * kGT; e += 256) {
+            const int rr = e / kGT, c = e % kGT, r = r0 + rr;
+            As[rr][c] = (r < r_hi && i0 + c < k) ? C[(int64_t)r * k + i0 + c] : 0.0f;
+            Bs[rr][c] = (r < r_hi && j0 + c < k) ? C[(int64_t)r * k + j0 + c] : 0.0f;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int rr = 0; rr < kGK; ++rr) {
+            float av[4], bv[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) av[a] = As[rr][ty * 4 + a];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) bv[b] = Bs[rr][tx * 4 + b];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    const float p = __fmul_rn(av[a], bv[b]);
+                    const float e = fmaf(av[a], bv[b], -p);   // exact: a b = p + e
+                    df_add(hi[a][b], lo[a][b], p, e);
+                }
+        }
+    }
+    double* Pz = P + (size_t)blockIdx.z * k * k;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int i = i0 + ty * 4 + a, j = j0 + tx * 4 + b;
+            if (i < k && j < k && i <= j) Pz[(int64_t)j * k + i] = (double)hi[a][b] + (double)lo[a][b];
+        }
+}
+
+__global__ void k_gram_sum(const double* __restrict__ P, int nz, int k, double* __restrict__ G) {
+    const int64_t total = (int64_t)k * k;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int j = (int)(e / k), i = (int)(e % k);
+        if (i > j) continue;
+        double s = 0.0;
+        for (int z = 0; z < nz; ++z) s += P[(size_t)z * total + e];
+        G[e] = s;
+    }
+}
+
+// Wa = [G | I] column-major with leading dimension k; G's upper triangle is
+// written by k_gram_sum, so only the identity half is set here.
+__global__ void k_identity_half(double* Wa, int k) {
+    const int64_t total = (int64_t)k * k;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(e / k), r = (int)(e % k);
+        Wa[(int64_t)(k + c) * k + r] = r == c ? 1.0 : 0.0;
+    }
+}
+
+// Diagonal block (b <= 32) at p0: D = U_D^T U_D in place. 256 threads: per
+// step j one thread takes the square root, the row is scaled by its
+// reciprocal, and the rank-1 update of the remaining upper triangle is spread
+// over all threads.
+__global__ void __launch_bounds__(256) k_chol_diag(double* G, int ld, int p0, int b, int* flag) {
+    __shared__ double D[kCholB][kCholB + 1];
+    __shared__ double rj_s;
+    const int t = threadIdx.x;
+    for (int e = t; e < kCholB * kCholB; e += blockDim.x) {
+        const int r = e / kCholB, c = e % kCholB;
+        D[r][c] = (c < b && r <= c) ? G[(int64_t)(p0 + c) * ld + p0 + r] : 0.0;
+    }
+    __syncthreads();
+    for (int j = 0; j < b; ++j) {
+        if (t == 0) {
+            const double d = D[j][j];
+            double u = 1.0;
+            if (!(d > 0.0) || !isfinite(d)) {
+                if (flag[0] == 0) flag[0] = 1;
+            } else {
+                u = sqrt(d);
+            }
+            D[j][j] = u;
+            rj_s = 1.0 / u;
+        }
+        __syncthreads();
+        if (t > j && t < b) D[j][t] *= rj_s;
+        __syncthreads();
+        // D(r, c) -= U(j, r) U(j, c) for j < r <= c < b
+        const int w = b - j - 1;
+        for (int e = t; e < w * w; e += blockDim.x) {
+            const int r = j + 1 + e / w, c = j + 1 + e % w;
+            if (r <= c) D[r][c] -= D[j][r] * D[j][c];
+        }
+        __syncthreads();
+    }
+    for (int e = t; e < kCholB * kCholB; e += blockDim.x) {
+        const int r = e / kCholB, c = e % kCholB;
+        if (c < b && r <= c) G[(int64_t)(p0 + c) * ld + p0 + r] = D[r][c];
+    }
+}
+
+// Panel row: U(p0:p0+b, c) = U_D^{-T} G(p0:p0+b, c) for c >= p0 + b. A warp per
+// column, lane = row of the panel: forward substitution with x_q broadcast.
+__global__ void __launch_bounds__(256) k_chol_row(double* G, int ld, int p0, int b, int k) {
+    __shared__ double U[kCholB][kCholB + 1];
+    __shared__ double rinv[kCholB];
+    for (int e = threadIdx.x; e < kCholB * kCholB; e += blockDim.x) {
+        const int r = e / kCholB, q = e % kCholB;
+        U[r][q] = (r < b && q < b && r <= q) ? G[(int64_t)(p0 + q) * ld + p0 + r] : 0.0;
+    }
+    __syncthreads();
+    if (threadIdx.x < b) rinv[threadIdx.x] = 1.0 / U[threadIdx.x][threadIdx.x];
+    __syncthreads();
+    const int lane = threadIdx.x % kWarp;
+    const int c = p0 + b + blockIdx.x * (blockDim.x / kWarp) + threadIdx.x / kWarp;
+    if (c >= k) return;                           // warp-uniform
+    double* col = G + (int64_t)c * ld + p0;
+    double x = lane < b ? col[lane] : 0.0;
+    for (int q = 0; q < b; ++q) {
+        const double xq = __shfl_sync(0xffffffffu, x, q) * rinv[q];
+        if (lane == q) x = xq;
+        if (lane > q) x = fma(-U[q][lane], xq, x);
+    }
+    if (lane < b) col[lane] = x;
+}
+
+// Trailing update G(r, c) -= sum_{q < b} U(p0+q, r) U(p0+q, c), p0+b <= r, c < k,
+// on 32 x 32 tiles of the upper triangle (tile row <= tile column).
+__global__ void k_chol_update(double* G, int ld, int p0, int b, int k) {
+    const int t0 = p0 + b;
+    const int tr = blockIdx.y, tc = blockIdx.x;
+    if (tr > tc) return;
+    __shared__ double Ur[kCholB][kCholB + 1], Uc[kCholB][kCholB + 1];
+    const int r0 = t0 + tr * kCholB, c0 = t0 + tc * kCholB;
+    for (int e = threadIdx.x; e < kCholB * kCholB; e += blockDim.x) {
+        const int q = e / kCholB, i = e % kCholB;
+        Ur[q][i] = (q < b && r0 + i < k) ? G[(int64_t)(r0 + i) * ld + p0 + q] : 0.0;
+        Uc[q][i] = (q < b && c0 + i < k) ? G[(int64_t)(c0 + i) * ld + p0 + q] : 0.0;
+    }
+    __syncthreads();
+    const int i = threadIdx.x % kCholB, jg = threadIdx.x / kCholB;   // 8 groups of 4 columns
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int q = 0; q < b; ++q) {
+        const double u = Ur[q][i];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) acc[a] = fma(u, Uc[q][jg * 4 + a], acc[a]);
+    }
+    const int r = r0 + i;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int c = c0 + jg * 4 + a;
+        if (r < k && c < k && r <= c) G[(int64_t)c * ld + r] -= acc[a];
+    }
+}
+
+__global__ void k_to_f32(const double* __restrict__ x, float* __restrict__ y, int64_t n) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        y[e] = (float)x[e];
+}
+
+// Z += D (k x n, D row-major with leading dimension n) when the factorisation
+// succeeded; then Z[:, J] = I again and the Z statistics of the result.
+__global__ void k_apply(float* Z, int64_t ldz, const float* __restrict__ D, int k, int n, const int* flag) {
+    if (flag[0]) return;
+    const int i = blockIdx.y;
+    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < n; l += gridDim.x * blockDim.x)
+        Z[(int64_t)i * ldz + l] += D[(int64_t)i * n + l];
+}
+
+__global__ void k_restore_identity(float* Z, int64_t ldz, const int32_t* J, int k, const int* flag) {
+    if (flag[0]) return;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < k * k; e += gridDim.x * blockDim.x) {
+        const int i = e / k, l = e % k;
+        Z[(int64_t)i * ldz + J[l]] = i == l ? 1.0f : 0.0f;
+    }
+}
+
+__global__ void k_zstats(const float* Z, int64_t ldz, int k, int n, const int* flag, DevInfo* info) {
+    if (flag[0]) return;
+    const int i = blockIdx.y;
+    unsigned long long gt2 = 0;
+    double amax = 0.0;
+    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < n; l += gridDim.x * blockDim.x) {
+        const double a = fabs((double)Z[(int64_t)i * ldz + l]);
+        gt2 += a > 2.0 ? 1ull : 0ull;
+        amax = a == a ? fmax(amax, a) : INFINITY;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        gt2 += __shfl_xor_sync(0xffffffffu, gt2, o);
+        amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    }
+    if (threadIdx.x % kWarp == 0) {
+        if (gt2) atomicAdd(&info->n_gt2, gt2);
+        atomicMax(&info->max_abs_z_bits, (unsigned long long)__double_as_longlong(amax));
+    }
+}
+
+__global__ void k_reset_stats(DevInfo* info, const int* flag) {
+    if (flag[0]) return;
+    info->n_gt2 = 0;
+    info->max_abs_z_bits = 0;
+}
+
+__global__ void k_ref_finalize(DevInfo* info, const int* flag) {
+    id_info r = info->info;
+    r.refined = flag[0] ? 0 : 1;
+    if (flag[0] == 2) r.status = ID_EINVAL;
+    if (!flag[0]) {
+        r.n_gt2 = (int64_t)info->n_gt2;
+        r.max_abs_z = __longlong_as_double((long long)info->max_abs_z_bits);
+    }
+    info->info = r;
+}
+
+__global__ void k_info_init(DevInfo* d, int k) {
+    DevInfo z = {};
+    z.info.status = ID_OK;
+    z.info.rank = k;
+    *d = z;
+}
+
+std::mutex g_cb_mu;
+std::map<int, cublasHandle_t> g_cb;
+
+cublasHandle_t cublas_handle() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    std::lock_guard<std::mutex> lk(g_cb_mu);
+    auto it = g_cb.find(dev);
+    if (it != g_cb.end()) return it->second;
+    cublasHandle_t h = nullptr;
+    if (cublasCreate(&h) != CUBLAS_STATUS_SUCCESS) return nullptr;
+    g_cb[dev] = h;
+    return h;
+}
+
+// FP32-accurate GEMM (column-major arguments as cuBLAS takes them).
+bool sgemm(cublasHandle_t h, cublasOperation_t ta, cublasOperation_t tb, int M, int N, int K, float alpha,
+           const float* A, int lda, const float* B, int ldb, float beta, float* C, int ldc) {
+    cublasStatus_t st = cublasGemmEx(h, ta, tb, M, N, K, &alpha, A, CUDA_R_32F, lda, B, CUDA_R_32F, ldb, &beta, C,
+                                     CUDA_R_32F, ldc, CUBLAS_COMPUTE_32F_EMULATED_16BFX9, CUBLAS_GEMM_DEFAULT);
+    if (st == CUBLAS_STATUS_SUCCESS) return true;
+    st = cublasGemmEx(h, ta, tb, M, N, K, &alpha, A, CUDA_R_32F, lda, B, CUDA_R_32F, ldb, &beta, C, CUDA_R_32F, ldc,
+                      CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT);
+    return st == CUBLAS_STATUS_SUCCESS;
+}
+
+int grid_for(int64_t n) {
+    const int64_t g = (n + kRThreads - 1) / kRThreads;
+    return (int)(g < 4096 ? (g > 0 ? g : 1) : 4096);
+}
+
+// Backward pass (gradient through the ID with J frozen). G64 = dZ with the
+// columns of J zeroed, in FP64.
+__global__ void k_mask_j(const int32_t* J, int k, int64_t n, unsigned char* mask) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < k; c += gridDim.x * blockDim.x)
+        if (J[c] >= 0 && J[c] < n) mask[J[c]] = 1;
+}
+
+__global__ void k_gz(const float* __restrict__ dZ, int64_t lddz, int k, int n, const unsigned char* __restrict__ mask,
+                     double* __restrict__ G64) {
+    const int i = blockIdx.y;
+    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < n; l += gridDim.x * blockDim.x)
+        G64[(int64_t)i * n + l] = mask[l] ? 0.0 : (double)dZ[(int64_t)i * lddz + l];
+}
+
+// dA[:, J[c]] = dC[:, c] (dC row-major m x k)
+__global__ void k_scatter_dc(const float* __restrict__ dC, int m, int k, const int32_t* __restrict__ J, int64_t n,
+                             float* dA, int64_t ldda) {
+    const int64_t total = (int64_t)m * k;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / k;
+        const int c = (int)(e % k);
+        const int jc = J[c];
+        if (jc >= 0 && jc < n) dA[i * ldda + jc] = dC[e];
+    }
+}
+
+__global__ void k_bwd_finalize(DevInfo* info, const int* flag) {
+    id_info r = info->info;
+    if (flag[0] == 2) r.status = ID_EINVAL;
+    else if (flag[0] == 1) r.status = ID_RANK_DEFICIENT;
+    info->info = r;
+}
+
+// Steps 1-4 shared by the refinement and the backward pass: C = A[:, J],
+// G = C^T C (double-float), G = U^T U (FP64, flag[0] = 1 if not positive
+// definite), U^{-1} in FP64 (row-major k x k).
+void factor_skeleton(const float* A, int64_t m, int64_t n, int64_t lda, int k, const int32_t* J, float* C32,
+                     double* Gp, double* Wa, double* Uinv64, int* flag, cudaStream_t s) {
+    k_check_j<<<1, kRThreads, 0, s>>>(J, k, n, flag);
+    k_gather<<<grid_for(m * k), kRThreads, 0, s>>>(A, lda, (int)m, k, n, J, C32);
+    const int nt = ceil_div(k, kGT);
+    const int rows_per = (int)round_up(ceil_div(m, kGramSplit), kGK);
+    k_gram<<<dim3(nt, nt, kGramSplit), 256, 0, s>>>(C32, (int)m, k, rows_per, Gp);
+    k_gram_sum<<<grid_for((int64_t)k * k), kRThreads, 0, s>>>(Gp, kGramSplit, k, Wa);
+    k_identity_half<<<grid_for((int64_t)k * k), kRThreads, 0, s>>>(Wa, k);
+    for (int p0 = 0; p0 < k; p0 += kCholB) {
+        const int b = k - p0 < kCholB ? k - p0 : kCholB;
+        k_chol_diag<<<1, 256, 0, s>>>(Wa, k, p0, b, flag);
+        const int rest = k - p0 - b;
+        if (rest > 0) {
+            k_chol_row<<<ceil_div(rest, 8), 256, 0, s>>>(Wa, k, p0, b, k);
+            const int nt2 = ceil_div(rest, kCholB);
+            k_chol_update<<<dim3(nt2, nt2), kRThreads, 0, s>>>(Wa, k, p0, b, k);
+        }
+    }
+    solve_run<double>(Wa, k, k, 2 * k, Uinv64, k, s);
+}
+
+}  // namespace
+
+size_t refine_bytes(int64_t m, int64_t n, int64_t k) { return ref_layout(m, n, k).total; }
+
+cudaError_t refine_info_init(DevInfo* dinfo, int k, cudaStream_t s) {
+    k_info_init<<<1, 1, 0, s>>>(dinfo, k);
+    return cudaGetLastError();
+}
+
+int refine_run(const float* A, int64_t m, int64_t n, int64_t lda, int k, const int32_t* J, float* Z, int64_t ldz,
+               void* ws, DevInfo* dinfo, cudaStream_t s) {
+    const RefLayout L = ref_layout(m, n, k);
+    char* base = static_cast<char*>(ws);
+    int* flag = reinterpret_cast<int*>(base + L.flag);
+    float* C32 = reinterpret_cast<float*>(base + L.C32);
+    double* Gp = reinterpret_cast<double*>(base + L.Gp);
+    double* Wa = reinterpret_cast<double*>(base + L.Wa);
+    double* Uinv64 = reinterpret_cast<double*>(base + L.Uinv64);
+    float* Uinv32 = reinterpret_cast<float*>(base + L.Uinv32);
+    float* Rb = reinterpret_cast<float*>(base + L.Rb);
+    float* H = reinterpret_cast<float*>(base + L.H);
+    float* Y1 = reinterpret_cast<float*>(base + L.Y1);
+    cublasHandle_t h = cublas_handle();
+    if (!h) return ID_ECUDA;
+    std::lock_guard<std::mutex> lk(g_cb_mu);   // one stream/workspace binding of the handle at a time
+    if (cublasSetStream(h, s) != CUBLAS_STATUS_SUCCESS) return ID_ECUDA;
+    if (cublasSetWorkspace(h, base + L.cws, kCublasWs) != CUBLAS_STATUS_SUCCESS) return ID_ECUDA;
+    if (cudaMemsetAsync(flag, 0, 16, s) != cudaSuccess) return ID_ECUDA;
+    const int tr = trace_begin(TraceKind::kRefine, s);
+    factor_skeleton(A, m, n, lda, k, J, C32, Gp, Wa, Uinv64, flag, s);
+    if (cudaGetLastError() != cudaSuccess) return ID_ECUDA;
+    k_to_f32<<<grid_for((int64_t)k * k), kRThreads, 0, s>>>(Uinv64, Uinv32, (int64_t)k * k);
+    // 5. H = C^T (A - C Z), by column blocks. Column-major views: A row-major
+    //    m x n is A^T (n x m, ld lda); Z is Z^T (n x k, ld ldz); C is C^T (k x m, ld k).
+    for (int64_t b0 = 0; b0 < n; b0 += kResCols) {
+        const int nb = (int)(n - b0 < kResCols ? n - b0 : kResCols);
+        if (cudaMemcpy2DAsync(Rb, (size_t)nb * 4, A + b0, (size_t)lda * 4, (size_t)nb * 4, (size_t)m,
+                              cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+            return ID_ECUDA;
+        // R_b^T (nb x m) -= Z_b^T (nb x k) C^T (k x m)
+        if (!sgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, nb, (int)m, k, -1.0f, Z + b0, (int)ldz, C32, k, 1.0f, Rb, nb))
+            return ID_ECUDA;
+        // H_b^T (nb x k) = R_b^T (nb x m) C (m x k)
+        if (!sgemm(h, CUBLAS_OP_N, CUBLAS_OP_T, nb, k, (int)m, 1.0f, Rb, nb, C32, k, 0.0f, H + b0, (int)n))
+            return ID_ECUDA;
+    }
+    // 6. Y1 = U^{-T} H, D = U^{-1} Y1 (into H). Uinv32 row-major k x k is the
+    //    column-major (U^{-1})^T.  Y1^T (n x k) = H^T U^{-1};  D^T = Y1^T U^{-T}.
+    if (!sgemm(h, CUBLAS_OP_N, CUBLAS_OP_T, (int)n, k, k, 1.0f, H, (int)n, Uinv32, k, 0.0f, Y1, (int)n))
+        return ID_ECUDA;
+    if (!sgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, (int)n, k, k, 1.0f, Y1, (int)n, Uinv32, k, 0.0f, H, (int)n))
+        return ID_ECUDA;
+    dim3 g2(ceil_div(n, kRThreads) < 1024 ? ceil_div(n, kRThreads) : 1024, k);
+    k_apply<<<g2, kRThreads, 0, s>>>(Z, ldz, H, k, (int)n, flag);
+    k_restore_identity<<<grid_for((int64_t)k * k), kRThreads, 0, s>>>(Z, ldz, J, k, flag);
+    k_reset_stats<<<1, 1, 0, s>>>(dinfo, flag);
+    k_zstats<<<g2, kRThreads, 0, s>>>(Z, ldz, k, (int)n, flag, dinfo);
+    k_ref_finalize<<<1, 1, 0, s>>>(dinfo, flag);
+    trace_end(tr, s);
+    return cudaGetLastError() == cudaSuccess ? ID_OK : ID_ECUDA;
+}
+
+struct BwdLayout {
+    size_t flag, mask, C32, Gp, Wa, Uinv64, G64, Y64, W32, Rb, dC, M1, cws, total;
+};
+
+static BwdLayout bwd_layout(int64_t m, int64_t n, int64_t k) {
+    BwdLayout L;
+    size_t off = 0;
+    auto take = [&](size_t b) {
+        const size_t o = off;
+        off = al(off + b);
+        return o;
+    };
+    L.flag = take(16);
+    L.mask = take((size_t)n);
+    L.C32 = take(4 * (size_t)m * k);
+    L.Gp = take(8 * (size_t)kGramSplit * k * k);
+    L.Wa = take(8 * (size_t)k * 2 * k);
+    L.Uinv64 = take(8 * (size_t)k * k);
+    L.G64 = take(8 * (size_t)k * n);
+    L.Y64 = take(8 * (size_t)k * n);
+    L.W32 = take(4 * (size_t)k * n);
+    L.Rb = take(4 * (size_t)m * (size_t)(n < kResCols ? n : kResCols));
+    L.dC = take(4 * (size_t)m * k);
+    L.M1 = take(4 * (size_t)k * k);
+    L.cws = take(kCublasWs);
+    L.total = off;
+    return L;
+}
+
+size_t backward_bytes(int64_t m, int64_t n, int64_t k) { return bwd_layout(m, n, k).total; }
+
+// Gradient of L(Z) through the ID with J frozen: Z[:, rest] = T = C^+ B
+// (C = A[:, J], B = A[:, rest]); with W = (C^T C)^{-1} dZ_rest:
+//   dA[:, rest] = C W,   dA[:, J] = (B - C T) W^T - C W T^T.
+// In full-width form (W zero on J, R = A - C Z zero on J):
+//   dA = C W (all columns, zero on J), dC = R W^T - C (W Z^T), dA[:, J] = dC.
+// W is formed in FP64 (U^{-1} applied twice with DGEMM: the gradient carries
+// cond(C)^2); the products with C, R and Z are FP32-accurate GEMMs.
+int backward_run(const float* A, int64_t m, int64_t n, int64_t lda, int k, const int32_t* J, const float* Z,
+                 int64_t ldz, const float* dZ, int64_t lddz, float* dA, int64_t ldda, void* ws, DevInfo* dinfo,
+                 cudaStream_t s) {
+    const BwdLayout L = bwd_layout(m, n, k);
+    char* base = static_cast<char*>(ws);
+    int* flag = reinterpret_cast<int*>(base + L.flag);
+    unsigned char* mask = reinterpret_cast<unsigned char*>(base + L.mask);
+    float* C32 = reinterpret_cast<float*>(base + L.C32);
+    double* Gp = reinterpret_cast<double*>(base + L.Gp);
+    double* Wa = reinterpret_cast<double*>(base + L.Wa);
+    double* Uinv64 = reinterpret_cast<double*>(base + L.Uinv64);
+    double* G64 = reinterpret_cast<double*>(base + L.G64);
+    double* Y64 = reinterpret_cast<double*>(base + L.Y64);
+    float* W32 = reinterpret_cast<float*>(base + L.W32);
+    float* Rb = reinterpret_cast<float*>(base + L.Rb);
+    float* dC = reinterpret_cast<float*>(base + L.dC);
+    float* M1 = reinterpret_cast<float*>(base + L.M1);
+    cublasHandle_t h = cublas_handle();
+    if (!h) return ID_ECUDA;
+    std::lock_guard<std::mutex> lk(g_cb_mu);
+    if (cublasSetStream(h, s) != CUBLAS_STATUS_SUCCESS) return ID_ECUDA;
+    if (cublasSetWorkspace(h, base + L.cws, kCublasWs) != CUBLAS_STATUS_SUCCESS) return ID_ECUDA;
+    if (cudaMemsetAsync(flag, 0, 16, s) != cudaSuccess) return ID_ECUDA;
+    if (cudaMemsetAsync(mask, 0, (size_t)n, s) != cudaSuccess) return ID_ECUDA;
+    const int tr = trace_begin(TraceKind::kRefine, s);
+    factor_skeleton(A, m, n, lda, k, J, C32, Gp, Wa, Uinv64, flag, s);
+    k_mask_j<<<1, kRThreads, 0, s>>>(J, k, n, mask);
+    dim3 g2(ceil_div(n, kRThreads) < 1024 ? ceil_div(n, kRThreads) : 1024, k);
+    k_gz<<<g2, kRThreads, 0, s>>>(dZ, lddz, k, (int)n, mask, G64);
+    // W = U^{-1} U^{-T} G (FP64). Row-major k x n matrices are column-major n x k
+    // (ld n); Uinv64 row-major is the column-major (U^{-1})^T.
+    const double one = 1.0, zero = 0.0;
+    if (cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_T, (int)n, k, k, &one, G64, (int)n, Uinv64, k, &zero, Y64, (int)n) !=
+        CUBLAS_STATUS_SUCCESS)
+        return ID_ECUDA;
+    if (cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, (int)n, k, k, &one, Y64, (int)n, Uinv64, k, &zero, G64, (int)n) !=
+        CUBLAS_STATUS_SUCCESS)
+        return ID_ECUDA;
+    k_to_f32<<<grid_for((int64_t)k * n), kRThreads, 0, s>>>(G64, W32, (int64_t)k * n);
+    // dA = C W: dA^T (n x m, ld ldda) = W^T (n x k) C^T (k x m)
+    if (!sgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, (int)n, (int)m, k, 1.0f, W32, (int)n, C32, k, 0.0f, dA, (int)ldda))
+        return ID_ECUDA;
+    // dC = sum_b R_b W_b^T: dC^T (k x m, ld k) += W_b (k x nb) R_b^T (nb x m)
+    for (int64_t b0 = 0; b0 < n; b0 += kResCols) {
+        const int nb = (int)(n - b0 < kResCols ? n - b0 : kResCols);
+        if (cudaMemcpy2DAsync(Rb, (size_t)nb * 4, A + b0, (size_t)lda * 4, (size_t)nb * 4, (size_t)m,
+                              cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+            return ID_ECUDA;
+        if (!sgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, nb, (int)m, k, -1.0f, Z + b0, (int)ldz, C32, k, 1.0f, Rb, nb))
+            return ID_ECUDA;
+        if (!sgemm(h, CUBLAS_OP_T, CUBLAS_OP_N, k, (int)m, nb, 1.0f, W32 + b0, (int)n, Rb, nb, b0 == 0 ? 0.0f : 1.0f,
+                   dC, k))
+            return ID_ECUDA;
+    }
+    // M1 = W Z^T (k x k; the buffer read row-major is M1): M1^T = Z W^T
+    if (!sgemm(h, CUBLAS_OP_T, CUBLAS_OP_N, k, k, (int)n, 1.0f, Z, (int)ldz, W32, (int)n, 0.0f, M1, k))
+        return ID_ECUDA;
+    // dC -= C M1: dC^T (k x m) -= M1^T (k x k) C^T (k x m)
+    if (!sgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, k, (int)m, k, -1.0f, M1, k, C32, k, 1.0f, dC, k)) return ID_ECUDA;
+    k_scatter_dc<<<grid_for(m * k), kRThreads, 0, s>>>(dC, (int)m, k, J, n, dA, ldda);
+    k_bwd_finalize<<<1, 1, 0, s>>>(dinfo, flag);
+    trace_end(tr, s);
+    return cudaGetLastError() == cudaSuccess ? ID_OK : ID_ECUDA;
+}
+
+}  // namespace gbid

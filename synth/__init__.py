@@ -167,8 +167,7 @@ def batched_uneven(count: int, seed: int, *, m_range=(32, 256), k_range=(8, 64),
             A = torch.as_tensor(np.where(mask, vals, 0.0), dtype=dtype, device=device)
             kind = "sparse"
         else:
-            A = lowrank(m, n, spectrum("exp8m", min(m, n), m=m), sub, device="cpu").to(
-                dtype=dtype, device=device)
+            A = lowrank(m, n, spectrum("exp8m", min(m, n), m=m), sub, device=device).to(dtype=dtype)
             kind = "lowrank"
         out.append({"m": m, "n": n, "k": k, "A": A.contiguous(), "kind": kind})
     return out

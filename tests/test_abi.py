@@ -79,6 +79,41 @@ def test_argument_errors_return_before_any_launch(gbid):
     assert L.id_cpqr(fake, 0, 10, 20, 12, 5, None, fake, fake, ws, 1 << 20, None, None) == gbid.ID_EINVAL
     # id_solve: k > n
     assert L.id_solve(fake, 0, 5, 8, 6, fake, 1, None) == gbid.ID_EINVAL
+    # id_decompose_batched: count < 0, NULL descriptors, bad dtype, small queue scratch; count 0 is a no-op
+    assert L.id_decompose_batched(fake, -1, 1, fake, 256, fake, None) == gbid.ID_EINVAL
+    assert L.id_decompose_batched(None, 3, 1, fake, 256, fake, None) == gbid.ID_EINVAL
+    assert L.id_decompose_batched(fake, 3, 9, fake, 256, fake, None) == gbid.ID_EINVAL
+    assert L.id_decompose_batched(fake, 3, 1, fake, 16, fake, None) == gbid.ID_ENOMEM
+    assert L.id_decompose_batched(None, 0, 1, None, 0, None, None) == gbid.ID_OK
+
+
+def test_refine_rules(gbid):
+    L = gbid.lib()
+    fake = ctypes.c_void_p(256)
+    assert L.id_refine_workspace_size(1, 100, 300, 20) > 100 * 20 * 12
+    assert L.id_refine_workspace_size(0, 100, 300, 20) == 0      # FP32 only
+    assert L.id_refine_workspace_size(1, 300, 100, 20) == 0      # a column ID (m <= n)
+    assert L.id_refine_workspace_size(1, 100, 300, 101) == 0     # k <= m
+    assert L.id_refine(None, 1, 100, 300, 300, 20, fake, fake, 300, fake, 1 << 30, None, None) == gbid.ID_EINVAL
+    assert L.id_refine(fake, 1, 100, 300, 299, 20, fake, fake, 300, fake, 1 << 30, None, None) == gbid.ID_EINVAL
+    assert L.id_refine(fake, 1, 100, 300, 300, 20, fake, fake, 300, fake, 1024, None, None) == gbid.ID_ENOMEM
+    # the randomized workspace grows by the refinement's unless it is switched off
+    o_on, o_off = gbid._opts(0, True), gbid._opts(0, False)
+    on = L.id_rid_workspace_size(1000, 3000, 70, 60, ctypes.byref(o_on))
+    off = L.id_rid_workspace_size(1000, 3000, 70, 60, ctypes.byref(o_off))
+    assert on > off
+
+
+def test_batched_workspace_rules(gbid):
+    L = gbid.lib()
+    assert L.id_batched_problem_workspace_size(1, 100, 300, 20) >= 100 * 300 * 4 + 300 * 4
+    assert L.id_batched_problem_workspace_size(0, 100, 300, 20) >= 100 * 300 * 8
+    # the m > n route: the same working size
+    assert L.id_batched_problem_workspace_size(1, 300, 100, 20) == L.id_batched_problem_workspace_size(1, 100, 300, 20)
+    assert L.id_batched_problem_workspace_size(1, 100, 300, gbid.BATCHED_MAX_K + 1) == 0
+    assert L.id_batched_problem_workspace_size(1, gbid.BATCHED_MAX_MIN_DIM + 1, 5000, 8) == 0
+    assert L.id_batched_problem_workspace_size(1, 10, 20, 11) == 0
+    assert L.id_batched_problem_workspace_size(1, 10, 20, 0) == 0
 
 
 def test_binding_refuses_cpu_tensors(gbid):

@@ -1,0 +1,81 @@
+"""id_backward (gradient through the ID with the skeleton frozen) vs the oracle.
+
+The oracle's ``id_grad`` (pinned by central differences on the CPU) is the
+reference. The gradient contains (C^T C)^{-1}, so it carries cond(C)^2: the GPU
+forms W in FP64 and the products with C, A - C Z and Z in FP32, and the bar is
+max(1e-4, 8 sqrt(n) cond(C) u_32) relative (Frobenius).
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import id_oracle as orc
+
+pytestmark = pytest.mark.gpu
+U32 = 2.0 ** -24
+
+
+@pytest.fixture(scope="module")
+def gbid():
+    import __graft_entry__ as g
+
+    g.build()
+    import paper_2105_07076_gb300 as m
+
+    return m
+
+
+@pytest.mark.parametrize("m,n,k,spec", [(120, 300, 16, "poly2"), (512, 1024, 64, "poly2"), (64, 64, 10, "exp64"),
+                                        (96, 5000, 24, "poly1.5")])
+def test_backward_matches_oracle(gbid, m, n, k, spec):
+    A = synth.lowrank(m, n, synth.spectrum(spec, m), 5, dtype=torch.float32).cuda()
+    J, Z, info = gbid.id_decompose(A, k)
+    assert info["status"] == gbid.ID_OK
+    g = torch.Generator(device="cuda").manual_seed(m + n + k)
+    dZ = torch.randn(k, n, generator=g, device="cuda")
+    dA, binfo = gbid.id_backward(A, J, Z, dZ)
+    assert binfo["status"] == gbid.ID_OK
+    Ah = A.double().cpu().numpy()
+    Jg = J.cpu().numpy().astype(np.int64)
+    rest = np.setdiff1d(np.arange(n), Jg)
+    perm = np.concatenate([Jg, rest])
+    ref = orc.id_grad(Ah, Jg, perm, dZ.double().cpu().numpy())
+    cond = np.linalg.cond(Ah[:, Jg])
+    bar = max(1e-4, 8 * math.sqrt(n) * cond * U32)
+    err = np.linalg.norm(dA.double().cpu().numpy() - ref) / np.linalg.norm(ref)
+    assert err <= bar, (err, bar, cond)
+
+
+def test_backward_ignores_dz_on_the_skeleton(gbid):
+    A = synth.lowrank(100, 250, synth.spectrum("poly2", 100), 6, dtype=torch.float32).cuda()
+    k = 12
+    J, Z, _ = gbid.id_decompose(A, k)
+    dZ = torch.randn(k, 250, device="cuda")
+    dA1, _ = gbid.id_backward(A, J, Z, dZ)
+    dZ2 = dZ.clone()
+    dZ2[:, J.long()] = 1e3
+    dA2, _ = gbid.id_backward(A, J, Z, dZ2)
+    assert torch.equal(dA1, dA2)
+
+
+def test_autograd_function(gbid):
+    """torch.autograd through IdFunction agrees with id_backward for L = <G, Z>."""
+    A = synth.lowrank(80, 200, synth.spectrum("poly2", 80), 8, dtype=torch.float32).cuda().requires_grad_(True)
+    k = 10
+    J, Z = gbid.IdFunction.apply(A, k)
+    G = torch.randn_like(Z)
+    (G * Z).sum().backward()
+    dA, _ = gbid.id_backward(A.detach(), J, Z.detach(), G)
+    assert torch.equal(A.grad, dA)
+
+
+def test_backward_rank_deficient(gbid):
+    A = torch.randn(60, 150, device="cuda")
+    A[:, 5] = A[:, 2]
+    J = torch.tensor([2, 5, 9], dtype=torch.int32, device="cuda")
+    Z = torch.zeros(3, 150, device="cuda")
+    dA, info = gbid.id_backward(A, J, Z, torch.randn(3, 150, device="cuda"))
+    assert info["status"] == gbid.ID_RANK_DEFICIENT

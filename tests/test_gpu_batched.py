@@ -1,0 +1,169 @@
+"""Batched ID (one persistent launch over many uneven matrices) vs the FP64 oracle.
+
+Each problem is checked as the single-matrix ID is: the GPU's pivots must pass
+the oracle's greedy replay (FP64: margin 1e-6; FP32: 64 u_32 sqrt(m), the
+FP32 rounding level of a residual norm) up to the numerical rank, Z must match
+the oracle's Z for the GPU's pivots (FP64 1e-10; FP32 max(1e-4, 2 cond(X_J)
+u_32)), and Z[:, J] = I exactly.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import id_oracle as orc
+
+pytestmark = pytest.mark.gpu
+U32 = 2.0 ** -24
+
+
+@pytest.fixture(scope="module")
+def gbid():
+    import __graft_entry__ as g
+
+    g.build()
+    import paper_2105_07076_gb300 as m
+
+    return m
+
+
+def _check_problem(A, k, J, Z, info, dtype, check_pivots=True):
+    Ah = A.double().cpu().numpy()
+    m, n = Ah.shape
+    trans = m > n
+    X = Ah.T if trans else Ah
+    Jg = J.cpu().numpy().astype(np.int64)
+    Zg = Z.double().cpu().numpy()
+    assert info["transposed"] == trans
+    Jo, Zo_free, io = orc.interp_decomp(Ah, k)
+    rank = io["rank"]
+    if dtype == torch.float64:
+        assert info["rank"] == rank, (info, rank)
+    r = min(rank, info["rank"])
+    assert len(set(Jg.tolist())) == k
+    assert np.array_equal(Zg[np.arange(k), Jg], np.ones(k))
+    assert np.count_nonzero(Zg[:, Jg]) == k
+    if check_pivots and r > 0:
+        tol = 1e-6 if dtype == torch.float64 else 64 * U32 * math.sqrt(X.shape[0])
+        ok, worst = orc.verify_pivots(X, Jg[:r], tol)
+        assert ok, (worst.max(), np.argmax(worst))
+    if rank == k and info["status"] == 0:
+        Zo = orc.interp_decomp(Ah, k, pivots=Jg)[1]
+        cond = np.linalg.cond(X[:, Jg])
+        bar = 1e-10 if dtype == torch.float64 else max(1e-4, 2 * cond * U32)
+        assert np.linalg.norm(Zg - Zo) / np.linalg.norm(Zo) <= bar, cond
+        assert info["max_abs_z"] == pytest.approx(np.abs(Zg).max(), rel=1e-12)
+        assert info["n_gt2"] == int(np.count_nonzero(np.abs(Zg) > 2.0))
+
+
+def _mixed_batch(dtype, count, seed):
+    probs = synth.batched_uneven(count, seed, m_range=(8, 96), k_range=(1, 40), dtype=dtype)
+    mats = [p["A"].cuda() for p in probs]
+    ks = [p["k"] for p in probs]
+    # the m > n route and a ragged leading dimension
+    g = torch.Generator().manual_seed(seed)
+    T = synth.lowrank(90, 40, synth.spectrum("exp8m", 40, m=40), seed + 1).to(dtype)
+    mats.append(T.cuda())
+    ks.append(12)
+    big = torch.randn(50, 77, generator=g, dtype=torch.float64).to(dtype)
+    mats.append(big.cuda()[:, :70])
+    ks.append(20)
+    return mats, ks
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+def test_batched_mixed_shapes(gbid, dtype):
+    mats, ks = _mixed_batch(dtype, 40, 4)
+    Js, Zs, infos, plan = gbid.id_decompose_batched(mats, ks)
+    for A, k, J, Z, info in zip(mats, ks, Js, Zs, infos):
+        assert info["status"] in (gbid.ID_OK, gbid.ID_RANK_DEFICIENT), info
+        _check_problem(A, k, J, Z, info, dtype)
+
+
+def test_batched_matches_single_id(gbid):
+    """FP64: the batched kernel and id_decompose agree on pivots; Z to 1e-12."""
+    mats, ks = _mixed_batch(torch.float64, 16, 9)
+    Js, Zs, infos, _ = gbid.id_decompose_batched(mats, ks)
+    for A, k, J, Z, info in zip(mats, ks, Js, Zs, infos):
+        if info["status"] != gbid.ID_OK:
+            continue
+        J1, Z1, i1 = gbid.id_decompose(A.contiguous(), k)
+        assert torch.equal(J.cpu(), J1.cpu())
+        assert (torch.linalg.norm(Z - Z1) / torch.linalg.norm(Z1)).item() < 1e-12
+
+
+def test_batched_bad_descriptor_is_isolated(gbid):
+    """A problem whose k breaks the rules gets ID_EINVAL; the rest still run."""
+    mats, ks = _mixed_batch(torch.float32, 6, 11)
+    plan = gbid.BatchedPlan(mats, ks)
+    # corrupt one descriptor on the device: k = min(m, n) + 1
+    import ctypes
+
+    victim = plan.order.index(2)
+    off = victim * ctypes.sizeof(gbid.IdProblem) + gbid.IdProblem.k.offset
+    A = mats[2]
+    bad = torch.tensor([min(A.shape) + 1], dtype=torch.int64).view(torch.uint8).cuda()
+    plan.desc[off:off + 8] = bad
+    plan.run()
+    infos = plan.read_infos()
+    assert infos[2]["status"] == gbid.ID_EINVAL
+    for i, info in enumerate(infos):
+        if i != 2:
+            assert info["status"] in (gbid.ID_OK, gbid.ID_RANK_DEFICIENT)
+            _check_problem(mats[i], ks[i], plan.J[i], plan.Z[i], info, torch.float32, check_pivots=False)
+
+
+def test_batched_graph_capture_replay(gbid):
+    mats, ks = _mixed_batch(torch.float32, 24, 13)
+    plan = gbid.BatchedPlan(mats, ks)
+    plan.run()
+    torch.cuda.synchronize()
+    ref = [z.clone() for z in plan.Z]
+    for z in plan.Z:
+        z.fill_(float("nan"))
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            plan.run()
+    torch.cuda.current_stream().wait_stream(s)
+    g.replay()
+    torch.cuda.synchronize()
+    for a, b in zip(ref, plan.Z):
+        assert torch.equal(a, b)
+
+
+def test_batched_nonfinite_and_zero_matrix(gbid):
+    A = torch.randn(20, 30, dtype=torch.float64)
+    A[3, 7] = float("nan")
+    Zm = torch.zeros(16, 24, dtype=torch.float64)
+    Js, Zs, infos, _ = gbid.id_decompose_batched([A.cuda(), Zm.cuda()], [5, 4])
+    assert infos[0]["status"] == gbid.ID_ENONFINITE
+    assert infos[1]["status"] == gbid.ID_RANK_DEFICIENT and infos[1]["rank"] == 0
+    # all-zero columns tie at norm 0: the smallest original indices win
+    assert Js[1].cpu().tolist() == [0, 1, 2, 3]
+
+
+def test_batched_full_workload_4096(gbid):
+    """4096 FP32 problems, m ~ U[32, 256], n ~ U[m, 4m], k ~ U[8, 64], 10% sparse:
+    every problem's identity block and status; oracle checks on a sample; the
+    reconstruction error of every low-rank problem above its Eckart-Young floor."""
+    probs = synth.batched_uneven(4096, 4, dtype=torch.float32, device="cuda")
+    mats = [p["A"] for p in probs]
+    ks = [p["k"] for p in probs]
+    Js, Zs, infos, plan = gbid.id_decompose_batched(mats, ks)
+    for i, (p, J, Z, info) in enumerate(zip(probs, Js, Zs, infos)):
+        assert info["status"] in (gbid.ID_OK, gbid.ID_RANK_DEFICIENT), (i, info)
+        k = p["k"]
+        assert torch.equal(Z[torch.arange(k, device=Z.device), J.long()], torch.ones(k, device=Z.device))
+        if p["kind"] == "lowrank":
+            A64 = p["A"].double().cuda()
+            err = (torch.linalg.norm(A64 - A64[:, J.long()] @ Z.double()) / torch.linalg.norm(A64)).item()
+            s = synth.spectrum("exp8m", min(p["m"], p["n"]), m=p["m"])
+            # the floor of the FP64 matrix, less the FP32 rounding of the input
+            assert err >= synth.tail_bound(s, k) * (1 - 1e-4) - 1e-6, (i, err)
+    for i in range(0, 4096, 512):
+        _check_problem(mats[i], ks[i], Js[i], Zs[i], infos[i], torch.float32)

@@ -1,6 +1,6 @@
 """Randomized ID (Gaussian sketch -> CPQR of Y -> T from Y's R) vs the FP64 oracle.
 
-Stage-wise: the oracle replays the GPU's pivots on the GPU's own sketch Y
+Stage-wise (refinement off): the oracle replays the GPU's pivots on the GPU's own sketch Y
 (FP32 tolerance 64 u_32 sqrt(l) on near-ties) and recomputes Z for those
 pivots (1e-4 relative Frobenius, the FP32 bar, widened to 2 cond(Y_J) u_32
 where the conditioning of the skeleton puts 1e-4 out of FP32's reach). End to end: the reconstruction
@@ -40,8 +40,9 @@ def test_randomized_stagewise_and_end_to_end(gbid, m, n, k, p, seed):
     omega = synth.gaussian_sketch_bf16(l, m, seed=20 + seed).cuda()
     if m % 8:
         pytest.skip("sketch needs ldo % 8 == 0")
-    J, Z, info = gbid.id_decompose_randomized(A, omega, k)
+    J, Z, info = gbid.id_decompose_randomized(A, omega, k, refine=False)
     assert info["status"] == gbid.ID_OK, info
+    assert not info["refined"]
     Y, _ = gbid.id_sketch(A, omega)                      # the same (deterministic) sketch
     Yh = Y.double().cpu().numpy()
     Jg = J.cpu().numpy().astype(np.int64)
@@ -56,6 +57,18 @@ def test_randomized_stagewise_and_end_to_end(gbid, m, n, k, p, seed):
     Jo, Zy, Zr, _ = orc.randomized_interp_decomp(Ah, omega.double().cpu().numpy(), k)
     err_o = orc.rel_error(Ah, Jo, Zy)
     assert err_g <= 1.05 * err_o, (err_g, err_o, orc.rel_error(Ah, Jo, Zr))
+    # with the refinement: the least-squares Z for the GPU's skeleton, and an
+    # error at most 1.05x that of the oracle's refined randomized ID
+    J2, Z2, info2 = gbid.id_decompose_randomized(A, omega, k)
+    assert info2["status"] == gbid.ID_OK and info2["refined"]
+    assert torch.equal(J2, J)
+    Z2h = Z2.double().cpu().numpy()
+    assert np.array_equal(Z2h[:, Jg], np.eye(k))
+    Zls = orc.ls_interp(Ah, Jg)
+    cond = np.linalg.cond(Ah[:, Jg])
+    assert np.linalg.norm(Z2h - Zls) / np.linalg.norm(Zls) <= max(1e-4, 2 * math.sqrt(k) * cond * 2.0 ** -24)
+    err_r = orc.rel_error(Ah, Jg, Z2h)
+    assert err_r <= 1.05 * orc.rel_error(Ah, Jo, Zr), (err_r, orc.rel_error(Ah, Jo, Zr))
 
 
 def test_randomized_full_size(gbid):
@@ -64,7 +77,7 @@ def test_randomized_full_size(gbid):
     A = synth.lowrank(m, n, synth.spectrum("poly1.5", m), 3, device="cuda", dtype=torch.float32,
                       gen_dtype=torch.float32)
     omega = synth.gaussian_sketch_bf16(l, m, seed=33, device="cuda")
-    J, Z, info = gbid.id_decompose_randomized(A, omega, k)
+    J, Z, info = gbid.id_decompose_randomized(A, omega, k, refine=False)
     assert info["status"] == gbid.ID_OK, info
     Jg = J.cpu().numpy().astype(np.int64)
     assert len(set(Jg.tolist())) == k
@@ -85,3 +98,12 @@ def test_randomized_full_size(gbid):
     err = (torch.linalg.norm(A64 - A64[:, J.long()] @ Z.double()) / torch.linalg.norm(A64)).item()
     tail = synth.tail_bound(synth.spectrum("poly1.5", m), k)
     assert tail * (1 - 1e-6) <= err <= 10 * tail, (err, tail)
+    # one refinement lands on the least-squares Z for J (FP64 lstsq on the GPU as the reference)
+    Jr, Zr, info_r = gbid.id_decompose_randomized(A, omega, k)
+    assert info_r["status"] == gbid.ID_OK and info_r["refined"] and torch.equal(Jr, J)
+    C = A64[:, J.long()]
+    Zls = torch.linalg.lstsq(C, A64).solution
+    err_ls = (torch.linalg.norm(A64 - C @ Zls) / torch.linalg.norm(A64)).item()
+    err_r = (torch.linalg.norm(A64 - C @ Zr.double()) / torch.linalg.norm(A64)).item()
+    assert err_r <= 1.01 * err_ls, (err_r, err_ls, err)
+    assert err_r < err
