@@ -320,7 +320,8 @@ int id_decompose_randomized(const void* A, id_dtype dtype, int64_t m, int64_t n,
     if (cpqr_run<float>(P, s) != cudaSuccess) return ID_ECUDA;
     double* Tm = reinterpret_cast<double*>(base + L.T);
     const int ldt = (int)n - (int)k > 0 ? (int)n - (int)k : 1;
-    if (solve_run<float>(P.W, P.ldw, (int)k, (int)n, Tm, ldt, s) != cudaSuccess) return ID_ECUDA;
+    // with the refinement on, this T only seeds the least-squares step: FP32 arithmetic suffices
+    if (solve_run<float>(P.W, P.ldw, (int)k, (int)n, Tm, ldt, s, rid_refine(opts)) != cudaSuccess) return ID_ECUDA;
     if (scatter_z<float>(P.perm, Tm, ldt, (int)k, (int)n, Z, ldz, J, dinfo, s) != cudaSuccess) return ID_ECUDA;
     if (finalize_info(P.st, dinfo, (int)k, 0, P.nb, s, sk_status) != cudaSuccess) return ID_ECUDA;
     // 5. one least-squares refinement of T against A_J

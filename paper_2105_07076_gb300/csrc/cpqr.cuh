@@ -41,7 +41,11 @@ template <typename T> cudaError_t cpqr_run(const CpqrPlan& P, cudaStream_t s);
 template <typename T> int cpqr_grid(int m);   // CTAs of the cooperative launch (0: cannot launch)
 
 // Back substitution T = R11^{-1} R12 (FP64) and Z assembly.
-template <typename T> cudaError_t solve_run(const void* W, int ldw, int k, int n, double* Tm, int ldt, cudaStream_t s);
+// T = R11^{-1} R12 (FP64 arithmetic; FP32 when fp32_arith and T = float, for a
+// T that only seeds a least-squares refinement).
+template <typename T>
+cudaError_t solve_run(const void* W, int ldw, int k, int n, double* Tm, int ldt, cudaStream_t s,
+                      bool fp32_arith = false);
 template <typename T> cudaError_t scatter_z(const int* perm, const double* Tm, int ldt, int k, int n, void* Z,
                                             int64_t ldz, int32_t* J, DevInfo* info, cudaStream_t s);
 cudaError_t solve_configure();

@@ -21,9 +21,9 @@ constexpr int kTrsmChunk = 64;   // rows of the off-diagonal R panel staged per 
 constexpr int kTrsmLdb = 33;     // padded row stride (doubles) of B and of the diagonal block
 constexpr int kTrsmPre = kTrsmBlk * kTrsmChunk / kSolveThreads;   // staged R values per thread
 
-static size_t trsm_smem(int k, bool smem_b) {
+static size_t trsm_smem(int k, bool smem_b, size_t acc_bytes = sizeof(double)) {
     return ((size_t)kTrsmBlk * kTrsmChunk + (size_t)kTrsmBlk * kTrsmLdb + (smem_b ? (size_t)k * kTrsmLdb : 0)) *
-           sizeof(double);
+           acc_bytes;
 }
 
 // Blocked back substitution T = R11^{-1} R12, R = W(0:k, :) upper triangular
@@ -37,24 +37,27 @@ static size_t trsm_smem(int k, bool smem_b) {
 //      as broadcasts; each warp accumulates 8 rows.
 // Every B(r, c) receives its updates in decreasing i and each as
 // fma(-R(r, i), x_i, B(r, c)), the order of the unblocked column-oriented
-// substitution; x_i = B(i, c) * (1 / R(i, i)). FP64 arithmetic throughout.
-template <typename T, bool kSmemB>
+// substitution; x_i = B(i, c) * (1 / R(i, i)). Arithmetic in Acc: FP64 (the
+// default), or FP32 for a T that only seeds a least-squares refinement.
+template <typename T, bool kSmemB, typename Acc = double>
 __global__ void __launch_bounds__(kSolveThreads, 2) k_trsm(const T* __restrict__ W, int ldw, int k, int nrhs,
                                                            double* __restrict__ Tm, int ldt) {
-    extern __shared__ __align__(16) double sm[];
-    double* Ps = sm;                                // Ps[q * kTrsmChunk + row]
-    double* Ds = Ps + kTrsmBlk * kTrsmChunk;        // Ds[col * kTrsmLdb + row]
-    double* Bs = Ds + kTrsmBlk * kTrsmLdb;          // Bs[i * kTrsmLdb + c]
+    static_assert(kSmemB || sizeof(Acc) == sizeof(double), "B kept in T requires FP64 arithmetic");
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    Acc* sm = reinterpret_cast<Acc*>(sm_raw);
+    Acc* Ps = sm;                                   // Ps[q * kTrsmChunk + row]
+    Acc* Ds = Ps + kTrsmBlk * kTrsmChunk;           // Ds[col * kTrsmLdb + row]
+    Acc* Bs = Ds + kTrsmBlk * kTrsmLdb;             // Bs[i * kTrsmLdb + c]
     const int t = threadIdx.x, lane = t & (kWarp - 1), w = t / kWarp;
     const int c0 = blockIdx.x * kTrsmCols;
     const int ncols = min(kTrsmCols, nrhs - c0);
-    double* B = kSmemB ? Bs : Tm + c0;
+    Acc* B = kSmemB ? Bs : reinterpret_cast<Acc*>(Tm + c0);
     const int64_t ldb = kSmemB ? kTrsmLdb : ldt;
 
     for (int e = t; e < k * kTrsmCols; e += kSolveThreads) {
         const int c = e / k, i = e - c * k;         // i fastest: coalesced reads of R12's columns
-        if (kSmemB) Bs[i * kTrsmLdb + c] = c < ncols ? (double)W[(int64_t)(k + c0 + c) * ldw + i] : 0.0;
-        else if (c < ncols) B[i * ldb + c] = (double)W[(int64_t)(k + c0 + c) * ldw + i];
+        if (kSmemB) Bs[i * kTrsmLdb + c] = c < ncols ? (Acc)W[(int64_t)(k + c0 + c) * ldw + i] : Acc(0);
+        else if (c < ncols) B[i * ldb + c] = (Acc)W[(int64_t)(k + c0 + c) * ldw + i];
     }
     const bool lane_col = kSmemB || lane < ncols;
     const int nblk = (k + kTrsmBlk - 1) / kTrsmBlk;
@@ -64,23 +67,23 @@ __global__ void __launch_bounds__(kSolveThreads, 2) k_trsm(const T* __restrict__
         for (int e = t; e < kTrsmBlk * kTrsmBlk; e += kSolveThreads) {
             const int col = e / kTrsmBlk, row = e % kTrsmBlk;
             Ds[col * kTrsmLdb + row] =
-                (col < bs && row < bs) ? (double)W[(int64_t)(i0 + col) * ldw + i0 + row] : 0.0;
+                (col < bs && row < bs) ? (Acc)W[(int64_t)(i0 + col) * ldw + i0 + row] : Acc(0);
         }
         __syncthreads();
         {
-            const double rv = lane < bs ? 1.0 / Ds[lane * kTrsmLdb + lane] : 0.0;
-            double x[4];
+            const Acc rv = lane < bs ? Acc(1) / Ds[lane * kTrsmLdb + lane] : Acc(0);
+            Acc x[4];
 #pragma unroll
             for (int qq = 0; qq < 4; ++qq) {
                 const int c = 4 * w + qq;
-                x[qq] = (lane < bs && (kSmemB || c < ncols)) ? B[(i0 + lane) * ldb + c] : 0.0;
+                x[qq] = (lane < bs && (kSmemB || c < ncols)) ? B[(i0 + lane) * ldb + c] : Acc(0);
             }
             for (int i = bs - 1; i >= 0; --i) {
-                const double dl = Ds[i * kTrsmLdb + lane];
+                const Acc dl = Ds[i * kTrsmLdb + lane];
 #pragma unroll
                 for (int qq = 0; qq < 4; ++qq) {
                     if (lane == i) x[qq] *= rv;
-                    const double xi = __shfl_sync(0xffffffffu, x[qq], i);
+                    const Acc xi = __shfl_sync(0xffffffffu, x[qq], i);
                     if (lane < i) x[qq] = fma(-dl, xi, x[qq]);
                 }
             }
@@ -92,16 +95,16 @@ __global__ void __launch_bounds__(kSolveThreads, 2) k_trsm(const T* __restrict__
         }
         if (i0 == 0) break;
         __syncthreads();
-        double X[kTrsmBlk];
+        Acc X[kTrsmBlk];
 #pragma unroll
-        for (int q = 0; q < kTrsmBlk; ++q) X[q] = (q < bs && lane_col) ? B[(i0 + q) * ldb + lane] : 0.0;
+        for (int q = 0; q < kTrsmBlk; ++q) X[q] = (q < bs && lane_col) ? B[(i0 + q) * ldb + lane] : Acc(0);
         const int nch = (i0 + kTrsmChunk - 1) / kTrsmChunk;
-        double pre[kTrsmPre];
+        Acc pre[kTrsmPre];
         auto stage = [&](int r0) {
 #pragma unroll
             for (int j = 0; j < kTrsmPre; ++j) {
                 const int e = t + j * kSolveThreads, q = e / kTrsmChunk, rl = e % kTrsmChunk;
-                pre[j] = (q < bs && r0 + rl < i0) ? (double)W[(int64_t)(i0 + q) * ldw + r0 + rl] : 0.0;
+                pre[j] = (q < bs && r0 + rl < i0) ? (Acc)W[(int64_t)(i0 + q) * ldw + r0 + rl] : Acc(0);
             }
         };
         stage(0);
@@ -114,18 +117,15 @@ __global__ void __launch_bounds__(kSolveThreads, 2) k_trsm(const T* __restrict__
             if (ch + 1 < nch) stage(r0 + kTrsmChunk);
             const int rb = r0 + 8 * w;
             if (rb < i0) {
-                double acc[8];
+                Acc acc[8];
 #pragma unroll
-                for (int jr = 0; jr < 8; ++jr) acc[jr] = (rb + jr < i0 && lane_col) ? B[(rb + jr) * ldb + lane] : 0.0;
+                for (int jr = 0; jr < 8; ++jr)
+                    acc[jr] = (rb + jr < i0 && lane_col) ? B[(rb + jr) * ldb + lane] : Acc(0);
 #pragma unroll
                 for (int q = kTrsmBlk - 1; q >= 0; --q) {
-                    const double2* pr = reinterpret_cast<const double2*>(Ps + q * kTrsmChunk + 8 * w);
+                    const Acc* pr = Ps + q * kTrsmChunk + 8 * w;   // broadcast reads
 #pragma unroll
-                    for (int h = 0; h < 4; ++h) {
-                        const double2 p = pr[h];
-                        acc[2 * h] = fma(-p.x, X[q], acc[2 * h]);
-                        acc[2 * h + 1] = fma(-p.y, X[q], acc[2 * h + 1]);
-                    }
+                    for (int h = 0; h < 8; ++h) acc[h] = fma(-pr[h], X[q], acc[h]);
                 }
 #pragma unroll
                 for (int jr = 0; jr < 8; ++jr)
@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(kSolveThreads, 2) k_trsm(const T* __restrict__
         __syncthreads();
         for (int e = t; e < k * kTrsmCols; e += kSolveThreads) {
             const int i = e / kTrsmCols, c = e % kTrsmCols;
-            if (c < ncols) Tm[(int64_t)i * ldt + c0 + c] = Bs[i * kTrsmLdb + c];
+            if (c < ncols) Tm[(int64_t)i * ldt + c0 + c] = (double)Bs[i * kTrsmLdb + c];
         }
     }
 }
@@ -150,17 +150,27 @@ cudaError_t solve_configure() {
     if ((e = cudaFuncSetAttribute(k_trsm<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)kSolveSmemMax)) != cudaSuccess)
         return e;
+    if ((e = cudaFuncSetAttribute(k_trsm<float, true, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)kSolveSmemMax)) != cudaSuccess)
+        return e;
     return cudaSuccess;
 }
 
 template <typename T>
-cudaError_t solve_run(const void* W, int ldw, int k, int n, double* Tm, int ldt, cudaStream_t s) {
+cudaError_t solve_run(const void* W, int ldw, int k, int n, double* Tm, int ldt, cudaStream_t s, bool fp32_arith) {
     const int nrhs = n - k;
     if (nrhs <= 0) return cudaSuccess;
+    const int grid = ceil_div(nrhs, kTrsmCols);
+    if (fp32_arith && sizeof(T) == 4 && trsm_smem(k, true, sizeof(float)) <= kSolveSmemMax) {
+        const int tr = trace_begin(TraceKind::kSolve, s);
+        k_trsm<float, true, float><<<grid, kSolveThreads, trsm_smem(k, true, sizeof(float)), s>>>(
+            static_cast<const float*>(W), ldw, k, nrhs, Tm, ldt);
+        trace_end(tr, s);
+        return cudaGetLastError();
+    }
     const bool smem_b = trsm_smem(k, true) <= kSolveSmemMax;
     const size_t smem = trsm_smem(k, smem_b);
     const int tr = trace_begin(TraceKind::kSolve, s);
-    const int grid = ceil_div(nrhs, kTrsmCols);
     if (smem_b)
         k_trsm<T, true><<<grid, kSolveThreads, smem, s>>>(static_cast<const T*>(W), ldw, k, nrhs, Tm, ldt);
     else
@@ -231,8 +241,8 @@ cudaError_t finalize_info(const State* st, DevInfo* info, int k, int transposed,
     return cudaGetLastError();
 }
 
-template cudaError_t solve_run<double>(const void*, int, int, int, double*, int, cudaStream_t);
-template cudaError_t solve_run<float>(const void*, int, int, int, double*, int, cudaStream_t);
+template cudaError_t solve_run<double>(const void*, int, int, int, double*, int, cudaStream_t, bool);
+template cudaError_t solve_run<float>(const void*, int, int, int, double*, int, cudaStream_t, bool);
 template cudaError_t scatter_z<double>(const int*, const double*, int, int, int, void*, int64_t, int32_t*, DevInfo*,
                                        cudaStream_t);
 template cudaError_t scatter_z<float>(const int*, const double*, int, int, int, void*, int64_t, int32_t*, DevInfo*,
