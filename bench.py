@@ -12,8 +12,9 @@ The line also carries, under "randomized", the randomized ID of a 16384 x
 tensor cores, CPQR of the 522 x 32768 sketch, FP64 solve; and under
 "batched", 4096 uneven FP32 IDs (m ~ U[32, 256], n ~ U[m, 4m], k ~ U[8, 64])
 in one persistent launch; and under "latency", back-to-back 200 x 400 FP64
-IDs at k = 20 (--only randomized / batched / latency runs that workload
-alone; --only id skips all three).
+IDs at k = 20; and under "differentiable", 256 IDs of 512 x 1024 at k = 64
+forward (batched) and backward (--only randomized / batched / latency /
+differentiable runs that workload alone; --only id skips them).
 
 Multi-GPU (N > 1, launched by torchrun): every rank decomposes its own copy
 (independent replicas, no collective on the data path); value = total IDs/s.
@@ -359,6 +360,70 @@ def randomized_block(gbid, dev, steps):
 BATCH_COUNT = 4096
 
 
+def differentiable_block(gbid, dev, steps):
+    """The differentiable form: 256 FP32 matrices 512 x 1024, s_i = (1+i)^-2,
+    k = 64 (seed 5): forward by one batched launch, then dL/dA for
+    L = <G, Z> (G ~ N(0,1), seed 5) by id_backward per matrix, the 256 backward
+    calls replayed from one CUDA graph (stream-ordered, one shared workspace)."""
+    import torch
+
+    import synth
+
+    nb, m, n, k = 256, 512, 1024, 64
+    s_ = synth.spectrum("poly2", m)
+    mats = [synth.lowrank(m, n, s_, 5000 + b, device=dev, dtype=torch.float32, gen_dtype=torch.float32)
+            for b in range(nb)]
+    g = torch.Generator(device=dev).manual_seed(5)
+    Gs = [torch.randn(k, n, generator=g, device=dev) for _ in range(nb)]
+    plan = gbid.BatchedPlan(mats, [k] * nb)
+    nbytes = int(gbid.lib().id_backward_workspace_size(gbid.ID_F32, m, n, k))
+    ws = gbid.Workspace(torch.empty(nbytes, dtype=torch.uint8, device=dev))
+    dAs = [torch.empty(m, n, device=dev) for _ in range(nb)]
+
+    def backward_all():
+        for A, J, Z, G, dA in zip(mats, plan.J, plan.Z, Gs, dAs):
+            gbid.id_backward(A, J, Z, G, workspace=ws, out=dA, sync=False)
+
+    plan.run()
+    backward_all()
+    torch.cuda.synchronize()
+    graph = None
+    try:
+        graph = torch.cuda.CUDAGraph()
+        cs = torch.cuda.Stream()
+        cs.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(cs):
+            with torch.cuda.graph(graph, stream=cs):
+                backward_all()
+        torch.cuda.current_stream().wait_stream(cs)
+        torch.cuda.synchronize()
+    except Exception as exc:
+        print(f"backward graph capture: {exc}", file=sys.stderr)
+        graph = None
+        torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    ev = []
+    for _ in range(max(3, min(steps, 10))):
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(st)
+        plan.run()
+        e1.record(st)
+        if graph is not None:
+            graph.replay()
+        else:
+            backward_all()
+        e2.record(st)
+        ev.append((e0, e1, e2))
+    torch.cuda.synchronize()
+    fwd = statistics.mean(a.elapsed_time(b) for a, b, _ in ev)
+    bwd = statistics.mean(b.elapsed_time(c) for _, b, c in ev)
+    infos = plan.read_infos()
+    ok = sum(1 for i in infos if i["status_name"] == "ID_OK")
+    return {"workload": "diff_256x512x1024_k64_f32", "fwd_ms": fwd, "bwd_ms": bwd,
+            "value": nb * 1000.0 / (fwd + bwd), "unit": "IDs/s (forward + backward)",
+            "bwd_graph": graph is not None, "statuses_ok": ok}
+
+
 def latency_block(gbid, dev, steps):
     """The small-ID latency workload: 200 x 400 FP64, s_i = 2^(-i/2), k = 20
     (seed 1), back-to-back IDs in one stream (A is 640 KB and stays in L2).
@@ -479,11 +544,13 @@ def run_gbid(args):
     import paper_2105_07076_gb300 as gbid
 
     dev = torch.device("cuda", local)
-    if args.only in ("randomized", "batched", "latency"):  # one side workload alone (profiling aid)
+    if args.only in ("randomized", "batched", "latency", "differentiable"):  # one side workload alone
         if args.only == "randomized":
             side = randomized_block(gbid, dev, max(2, min(args.steps, 5)))
         elif args.only == "latency":
             side = latency_block(gbid, dev, args.steps)
+        elif args.only == "differentiable":
+            side = differentiable_block(gbid, dev, args.steps)
         else:
             side = batched_block(gbid, dev, max(3, min(args.steps, 10)))
         if rank == 0:
@@ -543,6 +610,7 @@ def run_gbid(args):
     rid = randomized_block(gbid, dev, max(2, min(args.steps, 5))) if args.only == "all" else None
     bat = batched_block(gbid, dev, max(3, min(args.steps, 10))) if args.only == "all" else None
     lat = latency_block(gbid, dev, args.steps) if args.only == "all" else None
+    dif = differentiable_block(gbid, dev, args.steps) if args.only == "all" else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -578,6 +646,7 @@ def run_gbid(args):
         "randomized": rid,
         "batched": bat,
         "latency": lat,
+        "differentiable": dif,
         "cpu_baseline": cpu,
     }
     print(json.dumps(line), flush=True)
@@ -591,7 +660,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gbid", choices=["gbid", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--only", default="all", choices=["all", "id", "randomized", "batched", "latency"],
+    ap.add_argument("--only", default="all",
+                    choices=["all", "id", "randomized", "batched", "latency", "differentiable"],
                     help="id: the 4096 x 8192 ID alone; randomized / batched: that side workload alone")
     args = ap.parse_args()
     if args.warmup < 3:
