@@ -128,7 +128,7 @@ __device__ __forceinline__ ArgMax cand_to_argmax(const Cand<T>& c) {
 // j+1..mx-1.
 // The squares are taken of y * ysc, ysc a power of two near 1 / max column
 // norm, so they neither overflow nor underflow in the working precision.
-template <typename T, int CG>
+template <typename T, int CG, int R>
 __device__ void b_update_group(T* W, int ldw, const int* perm, int mx, int nx, int j, int pos0, T tauT, T ysc,
                                const T* v_s, Cand<T>& best) {
     const int lane = threadIdx.x % kWarp;
@@ -146,18 +146,18 @@ __device__ void b_update_group(T* W, int ldw, const int* perm, int mx, int nx, i
         d[g] = T(0);
         ss[g] = T(0);
     }
-    if (mx - j <= kWarp * kBRows) {
+    if (mx - j <= kWarp * R) {
         // the whole column segment fits in registers: one read, one write
-        T x[CG][kBRows];
+        T x[CG][R];
 #pragma unroll
         for (int g = 0; g < CG; ++g)
 #pragma unroll
-            for (int q = 0; q < kBRows; ++q) {
+            for (int q = 0; q < R; ++q) {
                 const int i = j + lane + kWarp * q;
                 x[g][q] = (ok[g] && i < mx) ? W[(int64_t)col[g] * ldw + i] : T(0);
             }
 #pragma unroll
-        for (int q = 0; q < kBRows; ++q) {
+        for (int q = 0; q < R; ++q) {
             const int i = j + lane + kWarp * q;
             const T vi = i < mx ? v_s[i] : T(0);
 #pragma unroll
@@ -166,7 +166,7 @@ __device__ void b_update_group(T* W, int ldw, const int* perm, int mx, int nx, i
 #pragma unroll
         for (int g = 0; g < CG; ++g) d[g] = warp_sum(d[g]);
 #pragma unroll
-        for (int q = 0; q < kBRows; ++q) {
+        for (int q = 0; q < R; ++q) {
             const int i = j + lane + kWarp * q;
             if (i < mx) {
                 const T vi = v_s[i];
@@ -179,9 +179,9 @@ __device__ void b_update_group(T* W, int ldw, const int* perm, int mx, int nx, i
             }
         }
     } else {
-        for (int i0 = j; i0 < mx; i0 += kWarp * kBRows) {
+        for (int i0 = j; i0 < mx; i0 += kWarp * R) {
 #pragma unroll
-            for (int q = 0; q < kBRows; ++q) {
+            for (int q = 0; q < R; ++q) {
                 const int i = i0 + lane + kWarp * q;
                 if (i < mx) {
                     const T vi = v_s[i];
@@ -193,9 +193,9 @@ __device__ void b_update_group(T* W, int ldw, const int* perm, int mx, int nx, i
         }
 #pragma unroll
         for (int g = 0; g < CG; ++g) d[g] = warp_sum(d[g]);
-        for (int i0 = j; i0 < mx; i0 += kWarp * kBRows) {
+        for (int i0 = j; i0 < mx; i0 += kWarp * R) {
 #pragma unroll
-            for (int q = 0; q < kBRows; ++q) {
+            for (int q = 0; q < R; ++q) {
                 const int i = i0 + lane + kWarp * q;
                 if (i < mx) {
                     const T vi = v_s[i];
@@ -388,10 +388,18 @@ __global__ void __launch_bounds__(kBThreads, 3) k_id_batched(const id_problem* _
             if (j == 0) r00 = fabs(beta);
             if (rank == k && (r00 == 0.0 || fabs(beta) <= rank_tol * r00)) rank = j;
             const T tauT = (T)sc[1];
-            // the last step still updates: it writes row k-1 of R12
+            // the last step still updates: it writes row k-1 of R12. Column segments
+            // of up to 256 rows stay in registers CG columns at a time, up to 512
+            // rows CG / 2 columns at a time; longer ones take two passes.
             Cand<T> bw = cand_empty<T>();
-            for (int pos0 = j + 1 + w * CG; pos0 < nx; pos0 += kBWarps * CG)
-                b_update_group<T, CG>(W, ldw, perm, mx, nx, j, pos0, tauT, ysc, v_s, bw);
+            if (mx - j > kWarp * kBRows && mx - j <= 2 * kWarp * kBRows) {
+                constexpr int CG2 = CG / 2;
+                for (int pos0 = j + 1 + w * CG2; pos0 < nx; pos0 += kBWarps * CG2)
+                    b_update_group<T, CG2, 2 * kBRows>(W, ldw, perm, mx, nx, j, pos0, tauT, ysc, v_s, bw);
+            } else {
+                for (int pos0 = j + 1 + w * CG; pos0 < nx; pos0 += kBWarps * CG)
+                    b_update_group<T, CG, kBRows>(W, ldw, perm, mx, nx, j, pos0, tauT, ysc, v_s, bw);
+            }
             best = b_block_argmax(cand_to_argmax(bw), red_a);   // its barriers also order this step's writes
         }
 

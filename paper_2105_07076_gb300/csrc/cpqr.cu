@@ -300,7 +300,9 @@ struct SmemPlan {
 //  C. every nb steps (nb < k): compact-WY update W_trail -= V F^T. -- barrier
 // Every wait (grid barrier, aux counter) is bounded and ends the kernel early
 // with kStatTimeout instead of hanging.
-template <typename T, bool kSmemV>
+// kShort: the instance for matrices of at most 5 * 32 * VN rows, which also
+// compiles the two-columns-per-round mode of the trailing product.
+template <typename T, bool kSmemV, bool kShort>
 __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
     using V = typename Vec<T>::type;
     constexpr int VN = Vec<T>::n;
@@ -489,17 +491,18 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
             for (int c = t; c < jj; c += kThreads) vrow_s[c] = ld(W + (int64_t)(j0 + c) * ldw + j);
             T adot = T(0);
             const int i_lo = kSmemV ? j_al : j + 1, i_hi = kSmemV ? m_pad : m;
-            for (int i = i_lo + t; (kSmemV || has_aux) && i < i_hi; i += 4 * kThreads) {
-                T xs[4], vs4[4];
+            constexpr int kBU = 8;   // loads in flight per thread and operand
+            for (int i = i_lo + t; (kSmemV || has_aux) && i < i_hi; i += kBU * kThreads) {
+                T xs[kBU], vs4[kBU];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
+                for (int u = 0; u < kBU; ++u) {
                     const int ii = i + u * kThreads;
                     const bool in = ii > j && ii < m;
                     xs[u] = in ? ld(xbuf + ii) : T(0);
                     vs4[u] = (in && has_aux) ? ld(vca + ii) : T(0);
                 }
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
+                for (int u = 0; u < kBU; ++u) {
                     const int ii = i + u * kThreads;
                     if (kSmemV && ii < i_hi) v_s[ii - j_al] = xs[u];
                     adot += vs4[u] * xs[u];
@@ -673,10 +676,121 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
                 }
                 nbat = 0;
             };
+            // Short columns (at most 4 vector loads per lane) and a panel no wider
+            // than a warp: each warp takes two columns per round of loads, so one
+            // L2 round trip serves both (the sketch of a randomized ID has ~520 rows).
+            constexpr int S = kWarp * VN;
+            const bool pair = kShort && (m_pad - j_al) <= 4 * S && jj <= kWarp;
             int idx = 0;
-            if (lane == 0) idx = atomicAdd(ctr, 1);
+            if (lane == 0) idx = atomicAdd(ctr, pair ? 2 : 1);
             idx = __shfl_sync(0xffffffffu, idx, 0);
             while (idx < c_cnt) {
+                if (pair) {
+                    const int idx1 = idx + 1;
+                    const bool has1 = idx1 < c_cnt;
+                    const int l0 = j + 1 + c_lo + (rev ? c_cnt - 1 - idx : idx);
+                    const int l1 = has1 ? j + 1 + c_lo + (rev ? c_cnt - 1 - idx1 : idx1) : l0;
+                    int nidx = 0;
+                    if (lane == 0) nidx = atomicAdd(ctr, 2);
+                    const bool mv0 = l0 == p && p != j, mv1 = has1 && l1 == p && p != j;
+                    const int s0 = nbat, s1i = nbat + 1;
+                    T wjl0 = T(0), wjl1 = T(0);
+                    if (lane == s0) {
+                        b_l = l0;
+                        wjl0 = ld(W + (int64_t)l0 * ldw + j);
+                        b_nu = ld(P.vn1 + l0);
+                        b_nu2 = ld(P.vn2 + l0);
+                        b_orig = ld(P.perm + l0);
+                    }
+                    if (has1 && lane == s1i) {
+                        b_l = l1;
+                        wjl1 = ld(W + (int64_t)l1 * ldw + j);
+                        b_nu = ld(P.vn1 + l1);
+                        b_nu2 = ld(P.vn2 + l1);
+                        b_orig = ld(P.perm + l1);
+                    }
+                    const T f0 = lane < jj ? ld(F + (int64_t)(mv0 ? j : l0) * ldf + lane) : T(0);
+                    const T f1 = (has1 && lane < jj) ? ld(F + (int64_t)(mv1 ? j : l1) * ldf + lane) : T(0);
+                    const T* cp0 = W + (int64_t)l0 * ldw;
+                    const T* cp1 = W + (int64_t)l1 * ldw;
+                    V xv[8];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int i = j_al + lane * VN + u * S;
+                        if (i < m_pad) {
+                            xv[u] = __ldcg(reinterpret_cast<const V*>(cp0 + i));
+                            if (has1) xv[4 + u] = __ldcg(reinterpret_cast<const V*>(cp1 + i));
+                        }
+                    }
+                    T a0 = T(0), a1 = T(0), q0 = T(0), q1 = T(0);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int i = j_al + lane * VN + u * S;
+                        if (i < m_pad) {
+                            const V yv = kSmemV ? *reinterpret_cast<const V*>(v_s + (i - j_al))
+                                                : x_at<T, V, VN>(xbuf, i, j, m);
+                            a0 = dot_vec(xv[u], yv, a0);
+                            if (has1) a1 = dot_vec(xv[4 + u], yv, a1);
+                            if (exact_norms) {
+                                const T* x0e = reinterpret_cast<const T*>(&xv[u]);
+                                const T* x1e = reinterpret_cast<const T*>(&xv[4 + u]);
+#pragma unroll
+                                for (int q = 0; q < VN; ++q)
+                                    if (i + q >= j) {
+                                        q0 = fma(x0e[q], x0e[q], q0);
+                                        if (has1) q1 = fma(x1e[q], x1e[q], q1);
+                                    }
+                            }
+                        }
+                    }
+                    if (!aux_ready) {
+                        int ok = 1;
+                        if (lane == 0) ok = wait_geq(P.auxcnt + j, (unsigned)jj, st) ? 1 : 0;
+                        ok = __shfl_sync(0xffffffffu, ok, 0);
+                        if (!ok) break;
+                        auxr[0] = lane < jj ? ld(aux + lane) : T(0);
+                        aux_ready = true;
+                    }
+                    T s10 = T(0), s20 = T(0), s11 = T(0), s21 = T(0);
+                    if (lane < jj) {
+                        s10 = f0 * auxr[0];
+                        s20 = f0 * vrow_s[lane];
+                        s11 = f1 * auxr[0];
+                        s21 = f1 * vrow_s[lane];
+                        if (mv0) F[(int64_t)p * ldf + lane] = f0;
+                        if (mv1) F[(int64_t)p * ldf + lane] = f1;
+                    }
+                    a0 = warp_sum(a0);
+                    a1 = warp_sum(a1);
+                    s10 = warp_sum(s10);
+                    s20 = warp_sum(s20);
+                    s11 = warp_sum(s11);
+                    s21 = warp_sum(s21);
+                    if (exact_norms) {
+                        q0 = warp_sum(q0);
+                        q1 = warp_sum(q1);
+                    }
+                    if (lane == s0) {
+                        const T f = tauT * (scaleT * a0 + wjl0) + s10;
+                        b_f = f;
+                        b_r = wjl0 - s20 - f;
+                        b_sq = q0;
+                        F[(int64_t)l0 * ldf + jj] = f;
+                        W[(int64_t)l0 * ldw + j] = b_r;
+                    }
+                    if (has1 && lane == s1i) {
+                        const T f = tauT * (scaleT * a1 + wjl1) + s11;
+                        b_f = f;
+                        b_r = wjl1 - s21 - f;
+                        b_sq = q1;
+                        F[(int64_t)l1 * ldf + jj] = f;
+                        W[(int64_t)l1 * ldw + j] = b_r;
+                    }
+                    nbat += has1 ? 2 : 1;
+                    idx = __shfl_sync(0xffffffffu, nidx, 0);
+                    if (nbat >= kWarp - 1 || idx >= c_cnt) flush();
+                    continue;
+                }
                 const int l = j + 1 + c_lo + (rev ? c_cnt - 1 - idx : idx);
                 int nidx = 0;
                 if (lane == 0) nidx = atomicAdd(ctr, 1);   // next column, in flight meanwhile
@@ -700,7 +814,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
                 // g = W(j_al:m_pad, l)^T v, eight 16-byte loads per lane in flight
                 const T* col = W + (int64_t)l * ldw;
                 T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0), sq = T(0);
-                constexpr int S = kWarp * VN;
                 for (int i0 = j_al + lane * VN; i0 < m_pad; i0 += 8 * S) {
                     V xv[8];
 #pragma unroll
@@ -813,12 +926,22 @@ static SmemPlan cpqr_smem(int m) {
 
 static int g_nsm = 0;
 
+// Matrices short enough for the kShort instance (v always fits in shared memory).
+// FP32 only: the FP64 instance spills and measured slower on a 200 x 400 ID
+// (550 against 504 us).
+template <typename T>
+static bool short_rows(int m) {
+    return sizeof(T) == 4 && m <= 5 * kWarp * Vec<T>::n;
+}
+
 template <typename T>
 cudaError_t cpqr_configure() {
-    cudaError_t e = cudaFuncSetAttribute(k_cpqr<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_cpqr<T, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kCpqrSmemMax);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_cpqr<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCpqrSmemMax);
+    e = cudaFuncSetAttribute(k_cpqr<T, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCpqrSmemMax);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_cpqr<T, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCpqrSmemMax);
     if (e != cudaSuccess) return e;
     int dev = 0;
     cudaGetDevice(&dev);
@@ -843,8 +966,11 @@ template <typename T>
 int cpqr_grid(int m) {
     const SmemPlan pl = cpqr_smem<T>(m);
     int occ = 0;
-    if (pl.smem_v) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cpqr<T, true>, kThreads, pl.bytes);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cpqr<T, false>, kThreads, pl.bytes);
+    if (short_rows<T>(m))
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cpqr<T, true, true>, kThreads, pl.bytes);
+    else if (pl.smem_v)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cpqr<T, true, false>, kThreads, pl.bytes);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cpqr<T, false, false>, kThreads, pl.bytes);
     if (occ < 1) return 0;
     return std::min(kMaxParts, g_nsm * occ);
 }
@@ -901,8 +1027,9 @@ cudaError_t cpqr_run(const CpqrPlan& P, cudaStream_t s) {
     cfg.attrs = &attr;
     cfg.numAttrs = 1;
     const int tr = trace_begin(TraceKind::kCpqr, s);
-    if (pl.smem_v) e = cudaLaunchKernelEx(&cfg, k_cpqr<T, true>, K);
-    else e = cudaLaunchKernelEx(&cfg, k_cpqr<T, false>, K);
+    if (short_rows<T>(P.m)) e = cudaLaunchKernelEx(&cfg, k_cpqr<T, true, true>, K);
+    else if (pl.smem_v) e = cudaLaunchKernelEx(&cfg, k_cpqr<T, true, false>, K);
+    else e = cudaLaunchKernelEx(&cfg, k_cpqr<T, false, false>, K);
     trace_end(tr, s);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();

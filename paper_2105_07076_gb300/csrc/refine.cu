@@ -24,6 +24,7 @@
 // is created on first use).
 #include <cublas_v2.h>
 #include <cuda_runtime.h>
+#include <float.h>
 #include <math.h>
 
 #include <map>
@@ -47,7 +48,7 @@ size_t al(size_t x) { return (x + 255) / 256 * 256; }
 constexpr int kGramSplit = 16;   // row chunks of the Gram matrix
 
 struct RefLayout {
-    size_t flag, C32, Wa, Gp, Uinv64, Uinv32, Rb, H, Y1, cws, total;
+    size_t flag, C32, Wa, Gp, gdiag, Uinv64, Uinv32, Rb, H, Y1, cws, total;
 };
 
 RefLayout ref_layout(int64_t m, int64_t n, int64_t k) {
@@ -62,6 +63,7 @@ RefLayout ref_layout(int64_t m, int64_t n, int64_t k) {
     L.C32 = take(4 * (size_t)m * k);
     L.Wa = take(8 * (size_t)k * 2 * k);
     L.Gp = take(8 * (size_t)kGramSplit * k * k);
+    L.gdiag = take(8 * (size_t)k);
     L.Uinv64 = take(8 * (size_t)k * k);
     L.Uinv32 = take(4 * (size_t)k * k);
     L.Rb = take(4 * (size_t)m * (size_t)(n < kResCols ? n : kResCols));
@@ -157,7 +159,8 @@ __global__ void __launch_bounds__(256) k_gram(const float* __restrict__ C, int m
         }
 }
 
-__global__ void k_gram_sum(const double* __restrict__ P, int nz, int k, double* __restrict__ G) {
+__global__ void k_gram_sum(const double* __restrict__ P, int nz, int k, double* __restrict__ G,
+                           double* __restrict__ gdiag) {
     const int64_t total = (int64_t)k * k;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         const int j = (int)(e / k), i = (int)(e % k);
@@ -165,6 +168,7 @@ __global__ void k_gram_sum(const double* __restrict__ P, int nz, int k, double* 
         double s = 0.0;
         for (int z = 0; z < nz; ++z) s += P[(size_t)z * total + e];
         G[e] = s;
+        if (i == j) gdiag[i] = s;
     }
 }
 
@@ -182,7 +186,10 @@ __global__ void k_identity_half(double* Wa, int k) {
 // step j one thread takes the square root, the row is scaled by its
 // reciprocal, and the rank-1 update of the remaining upper triangle is spread
 // over all threads.
-__global__ void __launch_bounds__(256) k_chol_diag(double* G, int ld, int p0, int b, int* flag) {
+// A pivot at or below 64 eps of its column's squared norm (the original G(j, j))
+// counts as zero: C is then numerically rank deficient for normal equations.
+__global__ void __launch_bounds__(256) k_chol_diag(double* G, int ld, int p0, int b, const double* gdiag,
+                                                   int* flag) {
     __shared__ double D[kCholB][kCholB + 1];
     __shared__ double rj_s;
     const int t = threadIdx.x;
@@ -195,7 +202,7 @@ __global__ void __launch_bounds__(256) k_chol_diag(double* G, int ld, int p0, in
         if (t == 0) {
             const double d = D[j][j];
             double u = 1.0;
-            if (!(d > 0.0) || !isfinite(d)) {
+            if (!(d > 64.0 * DBL_EPSILON * gdiag[p0 + j]) || !isfinite(d)) {
                 if (flag[0] == 0) flag[0] = 1;
             } else {
                 u = sqrt(d);
@@ -409,17 +416,17 @@ __global__ void k_bwd_finalize(DevInfo* info, const int* flag) {
 // G = C^T C (double-float), G = U^T U (FP64, flag[0] = 1 if not positive
 // definite), U^{-1} in FP64 (row-major k x k).
 void factor_skeleton(const float* A, int64_t m, int64_t n, int64_t lda, int k, const int32_t* J, float* C32,
-                     double* Gp, double* Wa, double* Uinv64, int* flag, cudaStream_t s) {
+                     double* Gp, double* Wa, double* Uinv64, double* gdiag, int* flag, cudaStream_t s) {
     k_check_j<<<1, kRThreads, 0, s>>>(J, k, n, flag);
     k_gather<<<grid_for(m * k), kRThreads, 0, s>>>(A, lda, (int)m, k, n, J, C32);
     const int nt = ceil_div(k, kGT);
     const int rows_per = (int)round_up(ceil_div(m, kGramSplit), kGK);
     k_gram<<<dim3(nt, nt, kGramSplit), 256, 0, s>>>(C32, (int)m, k, rows_per, Gp);
-    k_gram_sum<<<grid_for((int64_t)k * k), kRThreads, 0, s>>>(Gp, kGramSplit, k, Wa);
+    k_gram_sum<<<grid_for((int64_t)k * k), kRThreads, 0, s>>>(Gp, kGramSplit, k, Wa, gdiag);
     k_identity_half<<<grid_for((int64_t)k * k), kRThreads, 0, s>>>(Wa, k);
     for (int p0 = 0; p0 < k; p0 += kCholB) {
         const int b = k - p0 < kCholB ? k - p0 : kCholB;
-        k_chol_diag<<<1, 256, 0, s>>>(Wa, k, p0, b, flag);
+        k_chol_diag<<<1, 256, 0, s>>>(Wa, k, p0, b, gdiag, flag);
         const int rest = k - p0 - b;
         if (rest > 0) {
             k_chol_row<<<ceil_div(rest, 8), 256, 0, s>>>(Wa, k, p0, b, k);
@@ -459,7 +466,7 @@ int refine_run(const float* A, int64_t m, int64_t n, int64_t lda, int k, const i
     if (cublasSetWorkspace(h, base + L.cws, kCublasWs) != CUBLAS_STATUS_SUCCESS) return ID_ECUDA;
     if (cudaMemsetAsync(flag, 0, 16, s) != cudaSuccess) return ID_ECUDA;
     const int tr = trace_begin(TraceKind::kRefine, s);
-    factor_skeleton(A, m, n, lda, k, J, C32, Gp, Wa, Uinv64, flag, s);
+    factor_skeleton(A, m, n, lda, k, J, C32, Gp, Wa, Uinv64, reinterpret_cast<double*>(base + L.gdiag), flag, s);
     if (cudaGetLastError() != cudaSuccess) return ID_ECUDA;
     k_to_f32<<<grid_for((int64_t)k * k), kRThreads, 0, s>>>(Uinv64, Uinv32, (int64_t)k * k);
     // 5. H = C^T (A - C Z), by column blocks. Column-major views: A row-major
@@ -493,7 +500,7 @@ int refine_run(const float* A, int64_t m, int64_t n, int64_t lda, int k, const i
 }
 
 struct BwdLayout {
-    size_t flag, mask, C32, Gp, Wa, Uinv64, G64, Y64, W32, Rb, dC, M1, cws, total;
+    size_t flag, mask, C32, Gp, gdiag, Wa, Uinv64, G64, Y64, W32, Rb, dC, M1, cws, total;
 };
 
 static BwdLayout bwd_layout(int64_t m, int64_t n, int64_t k) {
@@ -508,6 +515,7 @@ static BwdLayout bwd_layout(int64_t m, int64_t n, int64_t k) {
     L.mask = take((size_t)n);
     L.C32 = take(4 * (size_t)m * k);
     L.Gp = take(8 * (size_t)kGramSplit * k * k);
+    L.gdiag = take(8 * (size_t)k);
     L.Wa = take(8 * (size_t)k * 2 * k);
     L.Uinv64 = take(8 * (size_t)k * k);
     L.G64 = take(8 * (size_t)k * n);
@@ -555,7 +563,7 @@ int backward_run(const float* A, int64_t m, int64_t n, int64_t lda, int k, const
     if (cudaMemsetAsync(flag, 0, 16, s) != cudaSuccess) return ID_ECUDA;
     if (cudaMemsetAsync(mask, 0, (size_t)n, s) != cudaSuccess) return ID_ECUDA;
     const int tr = trace_begin(TraceKind::kRefine, s);
-    factor_skeleton(A, m, n, lda, k, J, C32, Gp, Wa, Uinv64, flag, s);
+    factor_skeleton(A, m, n, lda, k, J, C32, Gp, Wa, Uinv64, reinterpret_cast<double*>(base + L.gdiag), flag, s);
     k_mask_j<<<1, kRThreads, 0, s>>>(J, k, n, mask);
     dim3 g2(ceil_div(n, kRThreads) < 1024 ? ceil_div(n, kRThreads) : 1024, k);
     k_gz<<<g2, kRThreads, 0, s>>>(dZ, lddz, k, (int)n, mask, G64);
