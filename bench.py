@@ -474,9 +474,25 @@ def latency_block(gbid, dev, steps):
     info = gbid.read_info(ws)
     err = rel_error_gpu(A, J, Z)
     trail = sum((200 - j) * (400 - j) for j in range(k)) * 8
+    # the same matrix in FP32, which the default sends to the thread-block-cluster kernel
+    A32 = A.float()
+    ws32 = gbid.Workspace.for_problem(A32.dtype, 200, 400, k, device=dev)
+    Z32 = torch.empty(k, 400, dtype=A32.dtype, device=dev)
+    for _ in range(5):
+        gbid.id_decompose(A32, k, workspace=ws32, out=(J, Z32), sync=False)
+    torch.cuda.synchronize()
+    e0.record(s)
+    for _ in range(reps):
+        gbid.id_decompose(A32, k, workspace=ws32, out=(J, Z32), sync=False)
+    e1.record(s)
+    torch.cuda.synchronize()
+    us32 = e0.elapsed_time(e1) * 1e3 / reps
+    info32 = gbid.read_info(ws32)
     return {"workload": "id_200x400_k20_f64", "us_per_id": us, "us_per_id_graph": us_graph,
             "value": 1e6 / best, "unit": UNIT, "rel_err": err, "tail_bound": 2.0 ** -10,
             "status": info["status_name"],
+            "f32": {"us_per_id": us32, "engine": info32["engine"], "rel_err": rel_error_gpu(A32, J, Z32)},
+            "engine": info["engine"],
             "l2_gbs_trailing_bytes": trail / (best * 1e-6) / 1e9,
             "note": "trailing-GEMV bytes s*sum_j (m-j)(n-j) over the best per-ID time (A stays in L2)"}
 

@@ -69,7 +69,12 @@ typedef struct {
      * refinement of T against A_J after the sketch (see id_refine); -1 = none
      * (T stays the sketch's R11^{-1} R12). */
     int32_t refine;
-    int32_t reserved[6];
+    /* id_decompose only: 0 (default) = choose; 1 = the persistent grid-wide
+     * CPQR; 2 = one thread-block cluster holding the matrix in distributed
+     * shared memory (small problems: k <= 64, min(m, n) <= 1024, the matrix
+     * within 8 CTAs' shared memory; ID_EINVAL if it does not fit). */
+    int32_t engine;
+    int32_t reserved[5];
 } id_opts;
 
 typedef struct {
@@ -82,7 +87,8 @@ typedef struct {
     double  r00;          /* |R_00|, the largest column norm                      */
     int32_t nb;           /* panel width actually used                            */
     int32_t refined;      /* 1 when a least-squares refinement was applied to Z   */
-    int32_t reserved[4];
+    int32_t engine;       /* 1 persistent grid CPQR, 2 cluster, 3 batched kernel  */
+    int32_t reserved[3];
 } id_info;
 
 /* Bytes of device workspace id_decompose needs for this problem (k <= 16384).

@@ -34,24 +34,27 @@ STATUS_NAMES = {0: "ID_OK", 1: "ID_RANK_DEFICIENT", -1: "ID_EINVAL", -2: "ID_ENO
 
 ID_F64 = 0
 ID_F32 = 1
+ENGINE_AUTO, ENGINE_GRID, ENGINE_CLUSTER = 0, 1, 2
+ENGINE_NAMES = {1: "grid", 2: "cluster", 3: "batched"}
 _DTYPES = {torch.float64: ID_F64, torch.float32: ID_F32}
 
 
 class IdOpts(ctypes.Structure):
-    _fields_ = [("nb", ctypes.c_int32), ("refine", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+    _fields_ = [("nb", ctypes.c_int32), ("refine", ctypes.c_int32), ("engine", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
 
 
 class IdInfo(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("rank", ctypes.c_int32), ("transposed", ctypes.c_int32),
                 ("n_recompute", ctypes.c_int32), ("n_gt2", ctypes.c_int64), ("max_abs_z", ctypes.c_double),
                 ("r00", ctypes.c_double), ("nb", ctypes.c_int32), ("refined", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("engine", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
     def as_dict(self):
         return {"status": self.status, "status_name": STATUS_NAMES.get(self.status, str(self.status)),
                 "rank": self.rank, "transposed": bool(self.transposed), "n_recompute": self.n_recompute,
                 "n_gt2": self.n_gt2, "max_abs_z": self.max_abs_z, "r00": self.r00, "nb": self.nb,
-                "refined": bool(self.refined)}
+                "refined": bool(self.refined), "engine": ENGINE_NAMES.get(self.engine, self.engine)}
 
 
 # Return codes that mean the call itself failed; device-detected conditions
@@ -123,10 +126,11 @@ def exported_symbols():
     return list(_SIG)
 
 
-def _opts(nb: int, refine: bool = True):
+def _opts(nb: int, refine: bool = True, engine: int = 0):
     o = IdOpts()
     o.nb = int(nb)
     o.refine = 0 if refine else -1
+    o.engine = int(engine)
     return o
 
 
@@ -165,14 +169,16 @@ class Workspace:
         return Workspace(torch.empty(nbytes, dtype=torch.uint8, device=device))
 
 
-def id_decompose(A: torch.Tensor, k: int, *, nb: int = 0, workspace: Workspace | None = None,
-                 out: tuple | None = None, sync: bool = True):
+def id_decompose(A: torch.Tensor, k: int, *, nb: int = 0, engine: int = ENGINE_AUTO,
+                 workspace: Workspace | None = None, out: tuple | None = None, sync: bool = True):
     """Rank-k ID of a CUDA matrix A (m x n, row-major, float32/float64).
 
     Returns (J, Z, info): J int32 (k,), Z (k, max(m,n)) of A's dtype, info a
     dict (when sync) or None. m <= n: A ~= A[:, J] @ Z; m > n: A ~= Z.T @ A[J, :].
     With sync=False nothing waits for the GPU (usable inside CUDA-graph capture);
-    read the status later with ``read_info(workspace)``.
+    read the status later with ``read_info(workspace)``. engine: ENGINE_AUTO
+    (small problems on one thread-block cluster, others on the persistent grid),
+    ENGINE_GRID or ENGINE_CLUSTER.
     """
     _check_cuda_matrix(A, "A")
     m, n = A.shape
@@ -185,7 +191,7 @@ def id_decompose(A: torch.Tensor, k: int, *, nb: int = 0, workspace: Workspace |
         Z = torch.empty(k, nz, dtype=A.dtype, device=dev)
     else:
         J, Z = out
-    o = _opts(nb)
+    o = _opts(nb, engine=engine)
     info = IdInfo()
     with torch.cuda.device(dev):
         rc = lib().id_decompose(A.data_ptr(), _DTYPES[A.dtype], m, n, A.stride(0), k, ctypes.byref(o),
@@ -366,7 +372,8 @@ def read_info(workspace: Workspace) -> dict:
     return info.as_dict()
 
 
-def id_decompose_host(A: torch.Tensor, k: int, *, nb: int = 0, workspace: Workspace | None = None,
+def id_decompose_host(A: torch.Tensor, k: int, *, nb: int = 0, engine: int = ENGINE_AUTO,
+                      workspace: Workspace | None = None,
                       out: tuple | None = None, device="cuda"):
     """The same ID for a HOST matrix (ideally pinned): copies in, decomposes, copies J, Z back, waits."""
     if A.is_cuda or A.dtype not in _DTYPES or A.dim() != 2 or A.stride(1) != 1:
@@ -381,7 +388,7 @@ def id_decompose_host(A: torch.Tensor, k: int, *, nb: int = 0, workspace: Worksp
         Z = torch.empty(k, nz, dtype=A.dtype, pin_memory=pin)
     else:
         J, Z = out
-    o = _opts(nb)
+    o = _opts(nb, engine=engine)
     info = IdInfo()
     dev = workspace.buf.device
     with torch.cuda.device(dev):
@@ -435,9 +442,10 @@ def id_solve(Xcm: torch.Tensor, k: int) -> torch.Tensor:
     return T[:, : n - k]
 
 
-def launch_count(dtype: torch.dtype, m: int, n: int, k: int, nb: int = 0) -> int:
-    """Kernel launches one id_decompose call enqueues (as the library counts them)."""
-    o = _opts(nb)
+def launch_count(dtype: torch.dtype, m: int, n: int, k: int, nb: int = 0, engine: int = ENGINE_AUTO) -> int:
+    """Kernel launches one id_decompose call enqueues (as the library counts them; -1 if the
+    engine cannot take the problem)."""
+    o = _opts(nb, engine=engine)
     return int(lib().id_launch_count(_DTYPES[dtype], m, n, k, ctypes.byref(o)))
 
 

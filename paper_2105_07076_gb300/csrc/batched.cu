@@ -494,6 +494,7 @@ __global__ void __launch_bounds__(kBThreads, 3) k_id_batched(const id_problem* _
             r.max_abs_z = zmax_b;
             r.r00 = r00;
             r.nb = 1;
+            r.engine = 3;
             infos[b] = r;
         }
     }

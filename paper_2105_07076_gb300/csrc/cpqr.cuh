@@ -64,6 +64,13 @@ cudaError_t refine_info_init(DevInfo* dinfo, int k, cudaStream_t s);   // status
 int refine_run(const float* A, int64_t m, int64_t n, int64_t lda, int k, const int32_t* J, float* Z, int64_t ldz,
                void* ws, DevInfo* dinfo, cudaStream_t s);
 
+// Small IDs on one thread-block cluster (cluster.cu): the cluster size a
+// problem gets (0 if it does not fit) and the launch (+ statistics kernel).
+template <typename T> int cluster_size(int64_t m, int64_t n, int64_t k);
+template <typename T>
+cudaError_t cluster_run(const void* A, int64_t lda, int trans, int mx, int nx, int k, int32_t* J, void* Z,
+                        int64_t ldz, DevInfo* dinfo, cudaStream_t s);
+
 // Gradient through the ID with the skeleton frozen (refine.cu). Returns an id_status.
 size_t backward_bytes(int64_t m, int64_t n, int64_t k);
 int backward_run(const float* A, int64_t m, int64_t n, int64_t lda, int k, const int32_t* J, const float* Z,

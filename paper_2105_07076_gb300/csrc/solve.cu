@@ -226,6 +226,7 @@ __global__ void k_finalize(const State* st, DevInfo* info, int k, int transposed
     r.r00 = st->r00;
     r.transposed = transposed;
     r.nb = nb;
+    r.engine = 1;
     r.n_gt2 = (int64_t)info->n_gt2;
     r.max_abs_z = __longlong_as_double((long long)info->max_abs_z_bits);
     if (status & kStatNonFinite) r.status = ID_ENONFINITE;

@@ -87,6 +87,23 @@ def test_argument_errors_return_before_any_launch(gbid):
     assert L.id_decompose_batched(None, 0, 1, None, 0, None, None) == gbid.ID_OK
 
 
+def test_engine_option(gbid):
+    L = gbid.lib()
+    fake = ctypes.c_void_p(256)
+    ws = ctypes.c_void_p(4096)
+    bad = gbid._opts(0, engine=3)
+    assert L.id_decompose(fake, 0, 10, 20, 20, 5, ctypes.byref(bad), fake, fake, 20, ws, 1 << 20, None,
+                          None) == gbid.ID_EINVAL
+    cl = gbid._opts(0, engine=gbid.ENGINE_CLUSTER)
+    # a small problem fits one cluster (kernel + statistics kernel); a large one does not
+    assert L.id_launch_count(0, 200, 400, 20, ctypes.byref(cl)) == 2
+    assert L.id_launch_count(0, 4096, 8192, 256, ctypes.byref(cl)) == -1
+    grid = gbid._opts(0, engine=gbid.ENGINE_GRID)
+    assert L.id_launch_count(0, 200, 400, 20, ctypes.byref(grid)) == 5
+    assert L.id_launch_count(1, 200, 400, 20, None) == 2          # FP32: the default takes the cluster
+    assert L.id_launch_count(0, 200, 400, 20, None) == 5          # FP64: the grid kernel
+
+
 def test_refine_rules(gbid):
     L = gbid.lib()
     fake = ctypes.c_void_p(256)

@@ -28,14 +28,48 @@ def tol_piv(dtype, m):
     return 1e-6 if dtype == torch.float64 else 64 * 2.0 ** -24 * math.sqrt(m)
 
 
-@pytest.fixture(scope="module")
-def gbid():
+class _Engine:
+    """The binding with id_decompose's engine fixed (every other name passes through)."""
+
+    def __init__(self, mod, engine):
+        self._mod = mod
+        self.engine = engine
+
+    def __getattr__(self, name):
+        return getattr(self._mod, name)
+
+    def id_decompose(self, A, k, **kw):
+        eng = self.engine
+        if eng == self._mod.ENGINE_CLUSTER and self._mod.launch_count(A.dtype, A.shape[0], A.shape[1], k,
+                                                                       engine=eng) < 0:
+            eng = self._mod.ENGINE_GRID          # too large for one cluster
+        kw.setdefault("engine", eng)
+        return self._mod.id_decompose(A, k, **kw)
+
+
+# Every test runs on the persistent grid kernel and, where the problem fits one
+# cluster's shared memory, on the thread-block-cluster kernel.
+@pytest.fixture(scope="module", params=[1, 2], ids=["grid", "cluster"])
+def gbid(request):
     import __graft_entry__ as g
 
     g.build()
     import paper_2105_07076_gb300 as m
 
-    return m
+    return _Engine(m, request.param)
+
+
+def test_engine_choice(gbid):
+    """The default: FP32 problems that fit one cluster go to it; FP64 and large problems to the grid."""
+    m = gbid._mod
+    A = synth.lowrank(200, 400, synth.spectrum("pow2_half", 200), 1, device="cuda")
+    assert m.id_decompose(A.float(), 20)[2]["engine"] == "cluster"
+    assert m.id_decompose(A, 20)[2]["engine"] == "grid"
+    assert m.id_decompose(A, 20, engine=m.ENGINE_CLUSTER)[2]["engine"] == "cluster"
+    B = torch.randn(2000, 3000, dtype=torch.float32, device="cuda")
+    assert m.id_decompose(B, 100)[2]["engine"] == "grid"       # beyond one cluster's shared memory
+    with pytest.raises(m.IdError):
+        m.id_decompose(B, 100, engine=m.ENGINE_CLUSTER)
 
 
 def run_and_check(gbid, A64: np.ndarray, k: int, dtype, nb=0, exact_rank=False, lda_pad=0):
@@ -83,7 +117,8 @@ def test_lowrank_200x400_k20_f64(gbid, nb):
     A = synth.lowrank(200, 400, synth.spectrum("pow2_half", 200), 1).numpy()
     _, _, info, _ = run_and_check(gbid, A, 20, torch.float64, nb=nb)
     assert info["rank"] == 20
-    assert info["nb"] == (20 if nb == 0 else nb)
+    if info["engine"] == "grid":
+        assert info["nb"] == (20 if nb == 0 else nb)
 
 
 def test_lowrank_200x400_k20_f32(gbid):
@@ -232,7 +267,7 @@ def test_solve_blocked_shapes(gbid, dtype, k, nrhs):
 def test_host_buffers_entry_point(gbid):
     A = synth.lowrank(200, 400, synth.spectrum("pow2_half", 200), 1)
     Ah = A.pin_memory()
-    J, Z, info = gbid.id_decompose_host(Ah, 20)
+    J, Z, info = gbid.id_decompose_host(Ah, 20, engine=gbid.engine)
     Jd, Zd, _ = gbid.id_decompose(A.cuda(), 20)
     assert torch.equal(J, Jd.cpu()) and torch.equal(Z, Zd.cpu())
 
@@ -249,6 +284,8 @@ def c2_inputs():
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
 def test_full_size_4096x8192_k256(gbid, c2_inputs, dtype):
     """Same launch configuration as the bench; sampled oracle checks."""
+    if gbid.engine == 2:
+        pytest.skip("too large for one cluster: the grid kernel, as in the other run")
     A64, _ = c2_inputs
     A = A64.to(dtype)
     k = 256
@@ -278,6 +315,8 @@ def test_full_size_4096x8192_k256(gbid, c2_inputs, dtype):
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
 def test_full_size_exact_rank_256(gbid, c2_inputs, dtype):
+    if gbid.engine == 2:
+        pytest.skip("too large for one cluster: the grid kernel, as in the other run")
     _, Ar64 = c2_inputs
     A = Ar64.to(dtype)
     J, Z, info = gbid.id_decompose(A, 256)
