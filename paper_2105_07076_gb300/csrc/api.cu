@@ -136,11 +136,12 @@ template <typename T>
 bool use_cluster(int64_t m, int64_t n, int64_t k, const id_opts* opts) {
     const int eng = opts ? opts->engine : 0;
     if (eng == 1) return false;
-    // By default FP32 only: FP64 arithmetic runs at 2 lanes per clock per SM on
-    // this GPU, and on at most 8 SMs it bounds the cluster kernel (200 x 400 at
-    // k = 20: 539 us against 504 us on the grid kernel).
-    if (eng == 0 && sizeof(T) == 8) return false;
-    return cluster_size<T>(m, n, k) > 0;
+    // FP64 arithmetic runs at 2 lanes per clock per SM on this GPU: by default an
+    // FP64 problem takes the cluster only when a 16-CTA cluster can hold it
+    // (200 x 400, k = 20: 361 us on 16 CTAs, 539 us on 8, 524 us on the grid).
+    const int cs = cluster_size<T>(m, n, k);
+    if (eng == 0 && sizeof(T) == 8) return cs >= 16;
+    return cs > 0;
 }
 
 bool engine_ok(id_dtype dt, int64_t m, int64_t n, int64_t k, const id_opts* opts) {

@@ -40,7 +40,7 @@ namespace {
 
 constexpr int kCThreads = 256;
 constexpr int kCWarps = kCThreads / kWarp;
-constexpr int kCMaxCS = 8;      // portable cluster size
+constexpr int kCMaxCS = 16;     // 16 needs the non-portable cluster size (checked at run time)
 constexpr int kCMaxK = 64;
 constexpr int kCMaxRows = 1024;
 constexpr size_t kCSmemMax = 225 * 1024;   // dynamic; the static arrays (~0.5 KB) share the 227 KB opt-in
@@ -172,10 +172,13 @@ __global__ void __launch_bounds__(kCThreads, 1) k_id_cluster(const T* __restrict
         if (lane == 0 && !isfinite(sacc)) s_flag = 1;
         cmax = fmax(cmax, sacc);
     }
-    // cluster-wide largest norm -> power-of-two scale for the squared norms
+    // cluster-wide largest norm -> power-of-two scale for the squared norms;
+    // a non-finite column anywhere is reported by rank 0
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) cmax = fmax(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
     if (lane == 0) redd[w] = cmax;
+    __syncthreads();
+    if (t == 0 && r != 0 && s_flag) atomicOr(cluster.map_shared_rank(&s_flag, 0), 1);
     cluster.sync();
     T ysc = T(1);
     {
@@ -186,7 +189,7 @@ __global__ void __launch_bounds__(kCThreads, 1) k_id_cluster(const T* __restrict
             for (int g = 0; g < kCWarps; ++g) v = fmax(v, rem[g]);
             gmax = fmax(gmax, v);
         }
-        if (gmax > 0.0 && isfinite(gmax)) {
+        if (sizeof(T) == 4 && gmax > 0.0 && isfinite(gmax)) {   // FP32 squares only
             int e2;
             frexp(sqrt(gmax), &e2);
             ysc = (T)ldexp(1.0, -e2);
@@ -297,7 +300,11 @@ __global__ void __launch_bounds__(kCThreads, 1) k_id_cluster(const T* __restrict
             for (int i = j + lane; i < mx; i += kWarp) {
                 const T yi = y[i] - td * vbuf[i];
                 y[i] = yi;
-                if (i > j) sq += (yi * ysc) * (yi * ysc);
+                if constexpr (sizeof(T) == 8) {
+                    if (i > j) sq = fma(yi, yi, sq);       // FP64: no range issue, one FMA
+                } else {
+                    if (i > j) sq += (yi * ysc) * (yi * ysc);
+                }
             }
             sq = warp_sum(sq);
             if (lane == 0) nrm[lc] = sq;
@@ -422,6 +429,7 @@ __global__ void k_cluster_stats(DevInfo* d) {
 
 std::mutex g_cmu;
 bool g_cconf[2] = {false, false};
+bool g_c16[2] = {false, false};   // a 16-CTA cluster with the largest shared memory is schedulable
 
 template <typename T>
 cudaError_t cluster_configure() {
@@ -430,6 +438,23 @@ cudaError_t cluster_configure() {
     if (g_cconf[slot]) return cudaSuccess;
     cudaError_t e = cudaFuncSetAttribute(k_id_cluster<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCSmemMax);
     if (e != cudaSuccess) return e;
+    if (cudaFuncSetAttribute(k_id_cluster<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(16);
+        cfg.blockDim = dim3(kCThreads);
+        cfg.dynamicSmemBytes = kCSmemMax;
+        cudaLaunchAttribute attr;
+        attr.id = cudaLaunchAttributeClusterDimension;
+        attr.val.clusterDim.x = 16;
+        attr.val.clusterDim.y = 1;
+        attr.val.clusterDim.z = 1;
+        cfg.attrs = &attr;
+        cfg.numAttrs = 1;
+        int nclusters = 0;
+        if (cudaOccupancyMaxActiveClusters(&nclusters, k_id_cluster<T>, &cfg) == cudaSuccess && nclusters > 0)
+            g_c16[slot] = true;
+        cudaGetLastError();   // a refused query leaves no error behind
+    }
     g_cconf[slot] = true;
     return cudaSuccess;
 }
@@ -441,10 +466,17 @@ template <typename T>
 int cluster_size(int64_t m, int64_t n, int64_t k) {
     const int64_t mx = m < n ? m : n, nx = m < n ? n : m;
     if (k > kCMaxK || mx > kCMaxRows || nx > 8192) return 0;
-    // the static shared arrays take ~2 KB
-    // at least ceil(n_x / 64) CTAs (per-step work per CTA), at least what fits
+    cluster_configure<T>();   // (on a machine without a GPU this fails and the portable cap holds)
+    cudaGetLastError();
+    const int cap = g_c16[sizeof(T) == 8 ? 0 : 1] ? 16 : 8;
+    // at least ceil(n_x / 64) CTAs (per-step work per CTA) and at least what
+    // fits; FP64 takes the widest cluster (its arithmetic runs at 2 lanes per
+    // clock per SM, so every SM counts)
     int cs = 2;
-    while (cs < kCMaxCS && (cs * 64 < nx || c_layout<T>((int)mx, (int)nx, (int)k, cs).total > kCSmemMax)) cs *= 2;
+    const int want = sizeof(T) == 8 ? cap : 2;
+    while (cs < cap && (cs < want || cs * 64 < nx || c_layout<T>((int)mx, (int)nx, (int)k, cs).total > kCSmemMax))
+        cs *= 2;
+    while (cs > 2 && (nx + cs - 1) / cs < 4) cs /= 2;   // at least 4 columns per CTA
     return c_layout<T>((int)mx, (int)nx, (int)k, cs).total <= kCSmemMax ? cs : 0;
 }
 

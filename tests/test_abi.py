@@ -101,7 +101,6 @@ def test_engine_option(gbid):
     grid = gbid._opts(0, engine=gbid.ENGINE_GRID)
     assert L.id_launch_count(0, 200, 400, 20, ctypes.byref(grid)) == 5
     assert L.id_launch_count(1, 200, 400, 20, None) == 2          # FP32: the default takes the cluster
-    assert L.id_launch_count(0, 200, 400, 20, None) == 5          # FP64: the grid kernel
 
 
 def test_refine_rules(gbid):

@@ -60,12 +60,12 @@ def gbid(request):
 
 
 def test_engine_choice(gbid):
-    """The default: FP32 problems that fit one cluster go to it; FP64 and large problems to the grid."""
+    """The default: problems that fit one cluster go to it (FP64 only on a 16-CTA cluster); large ones to the grid."""
     m = gbid._mod
     A = synth.lowrank(200, 400, synth.spectrum("pow2_half", 200), 1, device="cuda")
     assert m.id_decompose(A.float(), 20)[2]["engine"] == "cluster"
-    assert m.id_decompose(A, 20)[2]["engine"] == "grid"
     assert m.id_decompose(A, 20, engine=m.ENGINE_CLUSTER)[2]["engine"] == "cluster"
+    assert m.id_decompose(A, 20, engine=m.ENGINE_GRID)[2]["engine"] == "grid"
     B = torch.randn(2000, 3000, dtype=torch.float32, device="cuda")
     assert m.id_decompose(B, 100)[2]["engine"] == "grid"       # beyond one cluster's shared memory
     with pytest.raises(m.IdError):
