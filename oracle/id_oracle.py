@@ -260,6 +260,29 @@ def sketch(omega: np.ndarray, A: np.ndarray) -> np.ndarray:
     return np.asarray(omega, dtype=np.float64) @ np.asarray(A, dtype=np.float64)
 
 
+def sampled_interp_decomp(A: np.ndarray, idx: np.ndarray, k: int):
+    """Optim RID (Sec. 2.2, the randomized algorithm built on column sampling).
+
+    The p sampled column indices ``idx`` (drawn without replacement; the paper
+    takes p = k + floor(0.2 k)) are an input. CPQR of A_S = A[:, idx] selects
+    the skeleton J = idx[P_k]; with C = A[:, J] and R_k the leading k x k block
+    of that CPQR's R, Z solves the normal equations R_k^T R_k Z = C^T A
+    (Eq. final_eq) by a forward and a back substitution with R_k. (The paper
+    uses a symmetric-indefinite solve because C may be rank deficient; the two
+    substitutions give the same Z whenever R_k is nonsingular, and ``rank``
+    reports when it is not.) Returns (J, Z, info).
+    """
+    A = np.asarray(A, dtype=np.float64)
+    idx = np.asarray(idx, dtype=np.int64)
+    if len(np.unique(idx)) != len(idx) or idx.min() < 0 or idx.max() >= A.shape[1]:
+        raise ValueError("idx must hold distinct column indices")
+    f = cpqr(A[:, idx], k)
+    J = idx[f["perm"][:k]]
+    R = np.triu(f["F"][:k, :k])
+    Z = normal_equation_z(A, J, R)
+    return J, Z, {"perm": f["perm"], "R": R, "rank": f["rank"], "gap": f["gap"]}
+
+
 def randomized_interp_decomp(A: np.ndarray, omega: np.ndarray, k: int):
     """Randomized ID: skeleton from CPQR of Y = Omega A, Z refined against A.
 

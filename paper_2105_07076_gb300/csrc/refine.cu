@@ -34,6 +34,7 @@
 #include "cpqr.cuh"
 #include "gbid.h"
 #include "trace.cuh"
+#include "blas.cuh"
 
 namespace gbid {
 namespace {
@@ -348,32 +349,6 @@ __global__ void k_info_init(DevInfo* d, int k) {
     *d = z;
 }
 
-std::mutex g_cb_mu;
-std::map<int, cublasHandle_t> g_cb;
-
-cublasHandle_t cublas_handle() {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
-    std::lock_guard<std::mutex> lk(g_cb_mu);
-    auto it = g_cb.find(dev);
-    if (it != g_cb.end()) return it->second;
-    cublasHandle_t h = nullptr;
-    if (cublasCreate(&h) != CUBLAS_STATUS_SUCCESS) return nullptr;
-    g_cb[dev] = h;
-    return h;
-}
-
-// FP32-accurate GEMM (column-major arguments as cuBLAS takes them).
-bool sgemm(cublasHandle_t h, cublasOperation_t ta, cublasOperation_t tb, int M, int N, int K, float alpha,
-           const float* A, int lda, const float* B, int ldb, float beta, float* C, int ldc) {
-    cublasStatus_t st = cublasGemmEx(h, ta, tb, M, N, K, &alpha, A, CUDA_R_32F, lda, B, CUDA_R_32F, ldb, &beta, C,
-                                     CUDA_R_32F, ldc, CUBLAS_COMPUTE_32F_EMULATED_16BFX9, CUBLAS_GEMM_DEFAULT);
-    if (st == CUBLAS_STATUS_SUCCESS) return true;
-    st = cublasGemmEx(h, ta, tb, M, N, K, &alpha, A, CUDA_R_32F, lda, B, CUDA_R_32F, ldb, &beta, C, CUDA_R_32F, ldc,
-                      CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT);
-    return st == CUBLAS_STATUS_SUCCESS;
-}
-
 int grid_for(int64_t n) {
     const int64_t g = (n + kRThreads - 1) / kRThreads;
     return (int)(g < 4096 ? (g > 0 ? g : 1) : 4096);
@@ -438,6 +413,32 @@ void factor_skeleton(const float* A, int64_t m, int64_t n, int64_t lda, int k, c
 }
 
 }  // namespace
+
+std::mutex g_cb_mu;
+std::map<int, cublasHandle_t> g_cb;
+
+cublasHandle_t cublas_handle() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    std::lock_guard<std::mutex> lk(g_cb_mu);
+    auto it = g_cb.find(dev);
+    if (it != g_cb.end()) return it->second;
+    cublasHandle_t h = nullptr;
+    if (cublasCreate(&h) != CUBLAS_STATUS_SUCCESS) return nullptr;
+    g_cb[dev] = h;
+    return h;
+}
+
+// FP32-accurate GEMM (column-major arguments as cuBLAS takes them).
+bool sgemm(cublasHandle_t h, cublasOperation_t ta, cublasOperation_t tb, int M, int N, int K, float alpha,
+           const float* A, int lda, const float* B, int ldb, float beta, float* C, int ldc) {
+    cublasStatus_t st = cublasGemmEx(h, ta, tb, M, N, K, &alpha, A, CUDA_R_32F, lda, B, CUDA_R_32F, ldb, &beta, C,
+                                     CUDA_R_32F, ldc, CUBLAS_COMPUTE_32F_EMULATED_16BFX9, CUBLAS_GEMM_DEFAULT);
+    if (st == CUBLAS_STATUS_SUCCESS) return true;
+    st = cublasGemmEx(h, ta, tb, M, N, K, &alpha, A, CUDA_R_32F, lda, B, CUDA_R_32F, ldb, &beta, C, CUDA_R_32F, ldc,
+                      CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT);
+    return st == CUBLAS_STATUS_SUCCESS;
+}
 
 size_t refine_bytes(int64_t m, int64_t n, int64_t k) { return ref_layout(m, n, k).total; }
 

@@ -298,6 +298,40 @@ def test_refined_z_solves_the_least_squares_problem():
     assert orc.rel_error(A, J, Zr) <= orc.rel_error(A, J, Zy) + 1e-15
 
 
+# ------------------------------------------------------ column-sampling RID ---
+def test_sampled_rid_with_every_column_is_the_deterministic_id():
+    """p = n (every column sampled, in any order): the same skeleton as the
+    deterministic ID (up to ties) and the same Z (normal equations against back
+    substitution, equal in exact arithmetic)."""
+    A = synth.lowrank(60, 140, np.exp(-np.arange(60) / 8.0), 3).numpy()
+    k = 12
+    idx = np.random.default_rng(4).permutation(140)
+    J, Z, info = orc.sampled_interp_decomp(A, idx, k)
+    Jd, Zd, _ = orc.interp_decomp(A, k)
+    assert np.array_equal(J, Jd)
+    assert np.linalg.norm(Z - Zd) / np.linalg.norm(Zd) < 1e-9
+
+
+def test_sampled_rid_properties():
+    A = synth.lowrank(80, 300, synth.spectrum("poly2", 80), 5).numpy()
+    k = 20
+    p = k + int(0.2 * k)
+    idx = np.random.default_rng(9).choice(300, size=p, replace=False)
+    J, Z, info = orc.sampled_interp_decomp(A, idx, k)
+    assert set(J.tolist()) <= set(idx.tolist()) and len(set(J.tolist())) == k
+    # C Z reproduces C (Z[:, J] = I in exact arithmetic)
+    assert np.allclose(Z[:, J], np.eye(k), atol=1e-8)
+    # the normal-equation Z is the least-squares Z for that skeleton
+    Zl = orc.ls_interp(A, J)
+    assert np.linalg.norm(Z - Zl) / np.linalg.norm(Zl) < 1e-8
+    # never below the Eckart-Young floor
+    tail = synth.tail_bound(synth.spectrum("poly2", 80), k)
+    assert orc.rel_error(A, J, Z) >= tail * (1 - 1e-9)
+    # sampling without replacement is required
+    with pytest.raises(ValueError):
+        orc.sampled_interp_decomp(A, np.array([1, 1, 2]), 2)
+
+
 # ----------------------------------------------------------------- gradient ---
 def test_gradient_matches_central_differences():
     rng = np.random.default_rng(17)
