@@ -13,8 +13,10 @@ tensor cores, CPQR of the 522 x 32768 sketch, FP64 solve; and under
 "batched", 4096 uneven FP32 IDs (m ~ U[32, 256], n ~ U[m, 4m], k ~ U[8, 64])
 in one persistent launch; and under "latency", back-to-back 200 x 400 FP64
 IDs at k = 20; and under "differentiable", 256 IDs of 512 x 1024 at k = 64
-forward (batched) and backward (--only randomized / batched / latency /
-differentiable runs that workload alone; --only id skips them).
+forward (batched) and backward; and under "sampled", the paper's
+column-sampling Optim RID of the headline matrices (p = 307 sampled columns)
+(--only randomized / batched / latency / differentiable runs that workload
+alone; --only id skips them; --only sampled keeps the ID and the sampled RID).
 
 Multi-GPU (N > 1, launched by torchrun): every rank decomposes its own copy
 (independent replicas, no collective on the data path); value = total IDs/s.
@@ -357,6 +359,43 @@ def randomized_block(gbid, dev, steps):
                                 "frac": sk_tflops / bf16, "peak_source": src}}
 
 
+def sampled_block(gbid, dev, steps, mats):
+    """The column-sampling Optim RID (Sec. 2.2) of the headline matrices: p =
+    k + floor(0.2 k) = 307 columns drawn without replacement (seed 7), CPQR of
+    the 4096 x 307 sample, Z from the normal equations against all of A. ms per
+    ID, the stage split, and the error on A beside the deterministic ID's."""
+    import numpy as np
+    import torch
+
+    p = K_RANK + int(0.2 * K_RANK)
+    idx = np.random.default_rng(7).choice(N, size=p, replace=False).astype(np.int32)
+    out = {"workload": f"optim_rid_{M}x{N}_k{K_RANK}_p{p}"}
+    for name, A in mats.items():
+        ws = gbid.sampled_workspace(A.dtype, M, N, p, K_RANK, device=dev)
+        for _ in range(3):
+            gbid.id_decompose_sampled(A, idx, K_RANK, workspace=ws, sync=False)
+        torch.cuda.synchronize()
+        gbid.trace_enable(4 * steps + 8)
+        s = torch.cuda.current_stream()
+        ev = []
+        for _ in range(steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            J, Z, _ = gbid.id_decompose_sampled(A, idx, K_RANK, workspace=ws, sync=False)
+            e1.record(s)
+            ev.append((e0, e1))
+        torch.cuda.synchronize()
+        ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+        tr = gbid.trace_read()
+        gbid.trace_enable(0)
+        info = gbid.read_info(ws)
+        out[name] = {"ms_per_step": ms, "value": 1000.0 / ms, "unit": UNIT, "status": info["status_name"],
+                     "kernel_ms": {k: v[0] / v[1] for k, v in tr.items() if v[1]},
+                     "rel_err": rel_error_gpu(A, J, Z)}
+    return out
+
+
 BATCH_COUNT = 4096
 
 
@@ -623,6 +662,8 @@ def run_gbid(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_v = world / t.item()
 
+    samp = sampled_block(gbid, dev, max(3, min(args.steps, 10)), {n: r["A"] for n, r in results.items()}) \
+        if args.only in ("all", "sampled") else None
     rid = randomized_block(gbid, dev, max(2, min(args.steps, 5))) if args.only == "all" else None
     bat = batched_block(gbid, dev, max(3, min(args.steps, 10))) if args.only == "all" else None
     lat = latency_block(gbid, dev, args.steps) if args.only == "all" else None
@@ -660,6 +701,7 @@ def run_gbid(args):
                 "speedup_vs_f64": r32["value"] / r64["value"]},
         "solve_ms": {"f64": r64["solve_ms"], "f32": r32["solve_ms"]},
         "randomized": rid,
+        "sampled": samp,
         "batched": bat,
         "latency": lat,
         "differentiable": dif,
@@ -677,8 +719,9 @@ def main():
     ap.add_argument("--impl", default="gbid", choices=["gbid", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only", default="all",
-                    choices=["all", "id", "randomized", "batched", "latency", "differentiable"],
-                    help="id: the 4096 x 8192 ID alone; randomized / batched: that side workload alone")
+                    choices=["all", "id", "sampled", "randomized", "batched", "latency", "differentiable"],
+                    help="id: the 4096 x 8192 ID alone; sampled: the ID and the column-sampling RID of the same "
+                         "matrices; randomized / batched / latency / differentiable: that side workload alone")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -215,6 +215,30 @@ int id_decompose_randomized(const void* A, id_dtype dtype, int64_t m, int64_t n,
                             int32_t* J, void* Z, int64_t ldz, void* work, size_t work_bytes, id_info* info,
                             void* stream);
 
+/* id_decompose_sampled -- the paper's randomized algorithm, Optim RID
+ * (Sec. 2.2): sample p columns of A without replacement (the sample is an
+ * input: the caller draws it; the paper takes p = k + floor(0.2 k)), run the
+ * column-pivoted QR on A_S = A[:, idx] for k steps, take J = idx[P_k] and
+ * C = A[:, J], and solve the normal equations R_k^T R_k Z = C^T A
+ * (Eq. final_eq) for Z against ALL of A, in FP64.
+ *   A    [in]  m x n row-major, n <= lda < 2^31, dtype (not modified).
+ *   idx  [in]  HOST array of p distinct column indices in [0, n); k <= p <= n.
+ *   J    [out] k skeleton columns of A in pivot order; Z [out] k x n
+ *              (n <= ldz < 2^31).
+ *   work [in]  id_sampled_workspace_size() bytes, 256-byte aligned.
+ * FP64 data solve with the CPQR's own R_k (the paper's route). FP32 data: the
+ * CPQR runs in FP32, whose R_k the normal equations would square, so the
+ * factor is rebuilt from C (C^T C from exact products with double-float sums,
+ * FP64 Cholesky) -- the same matrix in exact arithmetic. Z[:, J] = I exactly.
+ * When R_k is numerically singular (the paper switches to a
+ * symmetric-indefinite solve there) the status is ID_RANK_DEFICIENT, `rank`
+ * is the CPQR's numerical rank and Z is not reliable: call again with
+ * k <= rank. Returns as id_decompose. */
+size_t id_sampled_workspace_size(id_dtype dtype, int64_t m, int64_t n, int64_t p, int64_t k, const id_opts* opts);
+int id_decompose_sampled(const void* A, id_dtype dtype, int64_t m, int64_t n, int64_t lda, const int32_t* idx,
+                         int64_t p, int64_t k, const id_opts* opts, int32_t* J, void* Z, int64_t ldz, void* work,
+                         size_t work_bytes, id_info* info, void* stream);
+
 /* id_refine -- one least-squares refinement of an ID's interpolation matrix
  * against A (the LS problem of Sec. 2.1, min ||A - C Z||_F with C = A[:, J]):
  *     Z <- Z + (C^T C)^{-1} C^T (A - C Z),   Z[:, J] kept = I.
@@ -315,7 +339,9 @@ int64_t id_launch_count(id_dtype dtype, int64_t m, int64_t n, int64_t k, const i
  * id_trace_read waits for the recorded events, writes per class the summed
  * milliseconds and launch counts into ms[0..nkinds) and launches[0..nkinds)
  * (classes: 0 persistent CPQR, 1 back substitution, 2 sketch, 3 copy-in,
- * 4 Z scatter, 5 batched ID), clears the records and returns how many were read.
+ * 4 Z scatter, 5 batched ID, 6 least-squares refinement and gradient, 7 the
+ * normal-equation Z of the column-sampling RID), clears the records and
+ * returns how many were read.
  * Process-wide state; not thread-safe. */
 int id_trace_enable(int capacity);
 int id_trace_read(double* ms, int64_t* launches, int nkinds);

@@ -92,6 +92,9 @@ _SIG = {
                                                _I64, _P, ctypes.c_size_t, _P, _P]),
     "id_batched_problem_workspace_size": (ctypes.c_size_t, [ctypes.c_int, _I64, _I64, _I64]),
     "id_decompose_batched": (ctypes.c_int, [_P, _I64, ctypes.c_int, _P, ctypes.c_size_t, _P, _P]),
+    "id_sampled_workspace_size": (ctypes.c_size_t, [ctypes.c_int, _I64, _I64, _I64, _I64, _P]),
+    "id_decompose_sampled": (ctypes.c_int, [_P, ctypes.c_int, _I64, _I64, _I64, _P, _I64, _I64, _P, _P, _P, _I64, _P,
+                                            ctypes.c_size_t, _P, _P]),
     "id_refine_workspace_size": (ctypes.c_size_t, [ctypes.c_int, _I64, _I64, _I64]),
     "id_backward_workspace_size": (ctypes.c_size_t, [ctypes.c_int, _I64, _I64, _I64]),
     "id_backward": (ctypes.c_int, [_P, ctypes.c_int, _I64, _I64, _I64, _I64, _P, _P, _I64, _P, _I64, _P, _I64, _P,
@@ -103,7 +106,7 @@ _SIG = {
     "id_version": (ctypes.c_char_p, []),
 }
 
-TRACE_KINDS = ("cpqr", "solve", "sketch", "copy_in", "scatter", "batched", "refine")
+TRACE_KINDS = ("cpqr", "solve", "sketch", "copy_in", "scatter", "batched", "refine", "sampled_z")
 
 
 def lib():
@@ -286,6 +289,44 @@ def id_decompose_randomized(A: torch.Tensor, omega: torch.Tensor, k: int, *, nb:
                                            ctypes.byref(info) if sync else None, _stream(dev))
     if rc in _CALL_ERRORS:
         raise IdError(rc, "id_decompose_randomized")
+    return J, Z, (info.as_dict() if sync else None)
+
+
+def sampled_workspace(dtype: torch.dtype, m: int, n: int, p: int, k: int, *, nb: int = 0,
+                      device=None) -> Workspace:
+    """Workspace for id_decompose_sampled with p sampled columns."""
+    o = _opts(nb)
+    nbytes = int(lib().id_sampled_workspace_size(_DTYPES[dtype], m, n, p, k, ctypes.byref(o)))
+    if nbytes == 0:
+        raise IdError(ID_EINVAL, "id_sampled_workspace_size")
+    return Workspace(torch.empty(nbytes, dtype=torch.uint8, device=device))
+
+
+def id_decompose_sampled(A: torch.Tensor, idx, k: int, *, nb: int = 0, workspace: Workspace | None = None,
+                         sync: bool = True):
+    """The paper's Optim RID: CPQR of the sampled columns A[:, idx] (idx: p distinct
+    column indices, host sequence), J = idx[P_k], Z from the normal equations against
+    all of A. Returns (J, Z, info) with A ~= A[:, J] @ Z."""
+    _check_cuda_matrix(A, "A")
+    import numpy as _np
+
+    ih = _np.ascontiguousarray(_np.asarray(idx, dtype=_np.int32))
+    m, n = A.shape
+    p = ih.size
+    dev = A.device
+    o = _opts(nb)
+    if workspace is None:
+        workspace = sampled_workspace(A.dtype, m, n, p, k, nb=nb, device=dev)
+    J = torch.empty(k, dtype=torch.int32, device=dev)
+    Z = torch.empty(k, n, dtype=A.dtype, device=dev)
+    info = IdInfo()
+    with torch.cuda.device(dev):
+        rc = lib().id_decompose_sampled(A.data_ptr(), _DTYPES[A.dtype], m, n, A.stride(0),
+                                        ih.ctypes.data_as(ctypes.c_void_p), p, k, ctypes.byref(o), J.data_ptr(),
+                                        Z.data_ptr(), Z.stride(0), workspace.buf.data_ptr(), workspace.buf.numel(),
+                                        ctypes.byref(info) if sync else None, _stream(dev))
+    if rc in _CALL_ERRORS:
+        raise IdError(rc, "id_decompose_sampled")
     return J, Z, (info.as_dict() if sync else None)
 
 

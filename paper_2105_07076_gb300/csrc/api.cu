@@ -1,5 +1,7 @@
 // C ABI of the ID library: argument checks, workspace layout, launch order.
 #include <cuda_runtime.h>
+
+#include <vector>
 #include <stdint.h>
 #include <string.h>
 
@@ -361,6 +363,70 @@ int id_decompose_randomized(const void* A, id_dtype dtype, int64_t m, int64_t n,
                         s);
         if (rc != ID_OK) return rc;
     }
+    if (info) return read_info(work, info, s);
+    return ID_OK;
+}
+
+// ---------------------------------------------------------------- Optim RID --
+namespace {
+size_t sampled_bytes(id_dtype dt, int64_t m, int64_t n, int64_t p, int64_t k, const id_opts* opts, Layout* out) {
+    const Layout L = make_layout(dt, (int)m, (int)p, (int)k, opts, true, false);
+    if (out) *out = L;
+    return L.total + align_up(4 * (size_t)p) + sampled_z_bytes(m, n, k);
+}
+
+bool sampled_sizes_ok(int64_t m, int64_t n, int64_t p, int64_t k) {
+    if (m < 1 || n < 1 || p < 1 || k < 1 || p > n || k > p || k > m || k > 16384) return false;
+    if (m > ((int64_t)1 << 31) - 1 || n > ((int64_t)1 << 31) - 1) return false;
+    return sizes_ok(m, p, k);
+}
+}  // namespace
+
+size_t id_sampled_workspace_size(id_dtype dtype, int64_t m, int64_t n, int64_t p, int64_t k, const id_opts* opts) {
+    if ((dtype != ID_F64 && dtype != ID_F32) || !sampled_sizes_ok(m, n, p, k)) return 0;
+    return sampled_bytes(dtype, m, n, p, k, opts, nullptr);
+}
+
+int id_decompose_sampled(const void* A, id_dtype dtype, int64_t m, int64_t n, int64_t lda, const int32_t* idx,
+                         int64_t p, int64_t k, const id_opts* opts, int32_t* J, void* Z, int64_t ldz, void* work,
+                         size_t work_bytes, id_info* info, void* stream) {
+    if (!A || !idx || !J || !Z || !work) return ID_EINVAL;
+    const size_t need = id_sampled_workspace_size(dtype, m, n, p, k, opts);
+    if (need == 0) return ID_EINVAL;
+    if (lda < n || ldz < n || !aligned(work, 256)) return ID_EINVAL;
+    if (lda > INT32_MAX || ldz > INT32_MAX) return ID_EINVAL;   // leading dimensions of the FP64 GEMMs
+    if (opts && opts->nb < 0) return ID_EINVAL;
+    {   // the sample: distinct indices in [0, n)
+        std::vector<unsigned char> seen((size_t)n, 0);
+        for (int64_t l = 0; l < p; ++l) {
+            if (idx[l] < 0 || idx[l] >= n || seen[(size_t)idx[l]]) return ID_EINVAL;
+            seen[(size_t)idx[l]] = 1;
+        }
+    }
+    if (work_bytes < need) return ID_ENOMEM;
+    if (configure_once()) return ID_ECUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Layout L;
+    sampled_bytes(dtype, m, n, p, k, opts, &L);
+    char* base = static_cast<char*>(work);
+    int32_t* idx_dev = reinterpret_cast<int32_t*>(base + L.total);
+    void* zws = base + L.total + align_up(4 * (size_t)p);
+    DevInfo* dinfo = reinterpret_cast<DevInfo*>(base + L.info);
+    if (cudaMemsetAsync(dinfo, 0, sizeof(DevInfo), s) != cudaSuccess) return ID_ECUDA;
+    if (cudaMemcpyAsync(idx_dev, idx, 4 * (size_t)p, cudaMemcpyHostToDevice, s) != cudaSuccess) return ID_ECUDA;
+    CpqrPlan P = make_plan(L, base, nullptr, nullptr, nullptr, (int)k, m, p);
+    const bool f64 = dtype == ID_F64;
+    // 1. A_S = A[:, idx] into the working layout, 2. k CPQR steps on it
+    if ((f64 ? sample_gather_run<double>(A, lda, (int)m, idx_dev, (int)p, P.W, P.ldw, s)
+             : sample_gather_run<float>(A, lda, (int)m, idx_dev, (int)p, P.W, P.ldw, s)) != cudaSuccess)
+        return ID_ECUDA;
+    if ((f64 ? cpqr_run<double>(P, s) : cpqr_run<float>(P, s)) != cudaSuccess) return ID_ECUDA;
+    if (finalize_info(P.st, dinfo, (int)k, 0, P.nb, s) != cudaSuccess) return ID_ECUDA;
+    // 3. J = idx[P_k], 4. Z from the normal equations against all of A
+    if (sample_map_j(P.perm, idx_dev, (int)k, J, s) != cudaSuccess) return ID_ECUDA;
+    const int rc = f64 ? sampled_z_run<double>(A, m, n, lda, (int)k, J, P.W, P.ldw, Z, ldz, zws, dinfo, s)
+                       : sampled_z_run<float>(A, m, n, lda, (int)k, J, P.W, P.ldw, Z, ldz, zws, dinfo, s);
+    if (rc != ID_OK) return rc;
     if (info) return read_info(work, info, s);
     return ID_OK;
 }

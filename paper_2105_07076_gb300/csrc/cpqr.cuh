@@ -71,6 +71,17 @@ template <typename T>
 cudaError_t cluster_run(const void* A, int64_t lda, int trans, int mx, int nx, int k, int32_t* J, void* Z,
                         int64_t ldz, DevInfo* dinfo, cudaStream_t s);
 
+// Column-sampling Optim RID pieces (refine.cu): W <- A[:, idx]; J = idx[perm];
+// Z from the normal equations in FP64 (an id_status).
+template <typename T>
+cudaError_t sample_gather_run(const void* A, int64_t lda, int m, const int32_t* idx, int p, void* W, int ldw,
+                              cudaStream_t s);
+cudaError_t sample_map_j(const int* perm, const int32_t* idx, int k, int32_t* J, cudaStream_t s);
+size_t sampled_z_bytes(int64_t m, int64_t n, int64_t k);
+template <typename T>
+int sampled_z_run(const void* A, int64_t m, int64_t n, int64_t lda, int k, const int32_t* J, const void* W, int ldw,
+                  void* Z, int64_t ldz, void* ws, DevInfo* dinfo, cudaStream_t s);
+
 // Gradient through the ID with the skeleton frozen (refine.cu). Returns an id_status.
 size_t backward_bytes(int64_t m, int64_t n, int64_t k);
 int backward_run(const float* A, int64_t m, int64_t n, int64_t lda, int k, const int32_t* J, const float* Z,

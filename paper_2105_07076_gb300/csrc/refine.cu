@@ -173,6 +173,55 @@ __global__ void k_gram_sum(const double* __restrict__ P, int nz, int k, double* 
     }
 }
 
+// B = C^T A (k x n, FP64 row-major) from C (m x k row-major FP32) and A (m x n
+// row-major FP32, lda), with the products exact and the sums in double-float
+// as in k_gram: the right-hand side of the normal equations to about 48 bits
+// without the FP64 pipe. 64 x 64 output tiles, 16 outputs per thread, every
+// tile sums all m rows.
+__global__ void __launch_bounds__(256) k_ctb(const float* __restrict__ C, const float* __restrict__ A, int64_t lda,
+                                             int m, int k, int n, double* __restrict__ B) {
+    __shared__ float Cs[kGK][kGT], As[kGK][kGT];
+    const int i0 = blockIdx.y * kGT, j0 = blockIdx.x * kGT;
+    const int t = threadIdx.x, ty = t / 16, tx = t % 16;
+    float hi[4][4], lo[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) hi[a][b] = lo[a][b] = 0.0f;
+    for (int r0 = 0; r0 < m; r0 += kGK) {
+        __syncthreads();
+        for (int e = t; e < kGK * kGT; e += 256) {
+            const int rr = e / kGT, c = e % kGT, r = r0 + rr;
+            Cs[rr][c] = (r < m && i0 + c < k) ? C[(int64_t)r * k + i0 + c] : 0.0f;
+            As[rr][c] = (r < m && j0 + c < n) ? A[(int64_t)r * lda + j0 + c] : 0.0f;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int rr = 0; rr < kGK; ++rr) {
+            float cv[4], av[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) cv[a] = Cs[rr][ty * 4 + a];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) av[b] = As[rr][tx * 4 + b];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    const float p = __fmul_rn(cv[a], av[b]);
+                    const float e = fmaf(cv[a], av[b], -p);
+                    df_add(hi[a][b], lo[a][b], p, e);
+                }
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int i = i0 + ty * 4 + a, j = j0 + tx * 4 + b;
+            if (i < k && j < n) B[(int64_t)i * n + j] = (double)hi[a][b] + (double)lo[a][b];
+        }
+}
+
 // Wa = [G | I] column-major with leading dimension k; G's upper triangle is
 // written by k_gram_sum, so only the identity half is set here.
 __global__ void k_identity_half(double* Wa, int k) {
@@ -384,6 +433,87 @@ __global__ void k_bwd_finalize(DevInfo* info, const int* flag) {
     id_info r = info->info;
     if (flag[0] == 2) r.status = ID_EINVAL;
     else if (flag[0] == 1) r.status = ID_RANK_DEFICIENT;
+    info->info = r;
+}
+
+// ---- column-sampling Optim RID (Sec. 2.2) ----
+// W (column-major, ldw) <- A[:, idx[l]], padding rows zero.
+template <typename T>
+__global__ void k_gather_sample(const T* __restrict__ A, int64_t lda, int m, const int32_t* __restrict__ idx, int p,
+                                T* __restrict__ W, int ldw) {
+    const int64_t total = (int64_t)ldw * p;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int l = (int)(e / ldw), i = (int)(e % ldw);
+        W[e] = i < m ? A[(int64_t)i * lda + idx[l]] : T(0);
+    }
+}
+
+__global__ void k_map_j(const int* __restrict__ perm, const int32_t* __restrict__ idx, int k, int32_t* J) {
+    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < k; l += gridDim.x * blockDim.x) J[l] = idx[perm[l]];
+}
+
+template <typename T>
+__global__ void k_gather_f64(const T* __restrict__ A, int64_t lda, int m, int k, const int32_t* __restrict__ J,
+                             double* __restrict__ C64) {
+    const int64_t total = (int64_t)m * k;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / k;
+        const int c = (int)(e % k);
+        C64[e] = (double)A[i * lda + J[c]];
+    }
+}
+
+// Wr (k x 2k, column-major, ld k) = [R_k | I], R_k from the CPQR's W (R(i, q) = W[q*ldw + i], i <= q).
+template <typename T>
+__global__ void k_rk_identity(const T* __restrict__ W, int ldw, int k, double* __restrict__ Wr) {
+    const int64_t total = (int64_t)k * 2 * k;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(e / k), r = (int)(e % k);
+        Wr[e] = c < k ? (r <= c ? (double)W[(int64_t)c * ldw + r] : 0.0) : (r == c - k ? 1.0 : 0.0);
+    }
+}
+
+template <typename T>
+__global__ void k_z_from64(const double* __restrict__ Z64, int k, int n, T* __restrict__ Z, int64_t ldz) {
+    const int i = blockIdx.y;
+    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < n; l += gridDim.x * blockDim.x)
+        Z[(int64_t)i * ldz + l] = (T)Z64[(int64_t)i * n + l];
+}
+
+template <typename T>
+__global__ void k_identity_at_j(T* Z, int64_t ldz, const int32_t* J, int k) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < k * k; e += gridDim.x * blockDim.x) {
+        const int i = e / k, l = e % k;
+        Z[(int64_t)i * ldz + J[l]] = i == l ? T(1) : T(0);
+    }
+}
+
+template <typename T>
+__global__ void k_zstats_t(const T* Z, int64_t ldz, int k, int n, DevInfo* info) {
+    const int i = blockIdx.y;
+    unsigned long long gt2 = 0;
+    double amax = 0.0;
+    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < n; l += gridDim.x * blockDim.x) {
+        const double a = fabs((double)Z[(int64_t)i * ldz + l]);
+        gt2 += a > 2.0 ? 1ull : 0ull;
+        amax = a == a ? fmax(amax, a) : INFINITY;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        gt2 += __shfl_xor_sync(0xffffffffu, gt2, o);
+        amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    }
+    if (threadIdx.x % kWarp == 0) {
+        if (gt2) atomicAdd(&info->n_gt2, gt2);
+        atomicMax(&info->max_abs_z_bits, (unsigned long long)__double_as_longlong(amax));
+    }
+}
+
+__global__ void k_sampled_finalize(DevInfo* info, const int* flag) {
+    id_info r = info->info;
+    if (flag[0] == 1 && r.status == ID_OK) r.status = ID_RANK_DEFICIENT;   // C^T C not positive definite
+    r.n_gt2 = (int64_t)info->n_gt2;
+    r.max_abs_z = __longlong_as_double((long long)info->max_abs_z_bits);
     info->info = r;
 }
 
@@ -603,5 +733,121 @@ int backward_run(const float* A, int64_t m, int64_t n, int64_t lda, int k, const
     trace_end(tr, s);
     return cudaGetLastError() == cudaSuccess ? ID_OK : ID_ECUDA;
 }
+
+// ------------------------------------------------ column-sampling Optim RID --
+struct SampLayout {
+    size_t flag, C32, Gp, gdiag, Wa, Uinv64, M64, C64, B64, Z64, cws, total;
+};
+
+static SampLayout samp_layout(int64_t m, int64_t n, int64_t k) {
+    SampLayout L;
+    size_t off = 0;
+    auto take = [&](size_t b) {
+        const size_t o = off;
+        off = al(off + b);
+        return o;
+    };
+    L.flag = take(16);
+    L.C32 = take(4 * (size_t)m * k);
+    L.Gp = take(8 * (size_t)kGramSplit * k * k);
+    L.gdiag = take(8 * (size_t)k);
+    L.Wa = take(8 * (size_t)k * 2 * k);
+    L.Uinv64 = take(8 * (size_t)k * k);
+    L.M64 = take(8 * (size_t)k * k);
+    L.C64 = take(8 * (size_t)m * k);
+    L.B64 = take(8 * (size_t)k * n);
+    L.Z64 = take(8 * (size_t)k * n);
+    L.cws = take(kCublasWs);
+    L.total = off;
+    return L;
+}
+
+size_t sampled_z_bytes(int64_t m, int64_t n, int64_t k) { return samp_layout(m, n, k).total; }
+
+template <typename T>
+cudaError_t sample_gather_run(const void* A, int64_t lda, int m, const int32_t* idx, int p, void* W, int ldw,
+                              cudaStream_t s) {
+    k_gather_sample<T><<<grid_for((int64_t)ldw * p), kRThreads, 0, s>>>(static_cast<const T*>(A), lda, m, idx, p,
+                                                                      static_cast<T*>(W), ldw);
+    return cudaGetLastError();
+}
+
+cudaError_t sample_map_j(const int* perm, const int32_t* idx, int k, int32_t* J, cudaStream_t s) {
+    k_map_j<<<ceil_div(k, kRThreads), kRThreads, 0, s>>>(perm, idx, k, J);
+    return cudaGetLastError();
+}
+
+// Z of Optim RID: R_k^T R_k Z = C^T A in FP64. FP64 data: R_k is the CPQR's own
+// factor (the paper's route) and B = C^T A is a DGEMM. FP32 data: the CPQR's
+// R_k carries FP32 rounding, which the normal equations would square, so U with
+// U^T U = C^T C is formed from C itself (exact products, double-float sums,
+// FP64 Cholesky) -- the same matrix in exact arithmetic -- and B = C^T A comes
+// from k_ctb (exact products, double-float sums). Then M = U^{-1} U^{-T} and
+// Z = M B in FP64; Z[:, J] is set to the identity it equals in exact arithmetic.
+template <typename T>
+int sampled_z_run(const void* Av, int64_t m, int64_t n, int64_t lda, int k, const int32_t* J, const void* W, int ldw,
+                  void* Zv, int64_t ldz, void* ws, DevInfo* dinfo, cudaStream_t s) {
+    const T* A = static_cast<const T*>(Av);
+    T* Z = static_cast<T*>(Zv);
+    const SampLayout L = samp_layout(m, n, k);
+    char* base = static_cast<char*>(ws);
+    int* flag = reinterpret_cast<int*>(base + L.flag);
+    double* Wa = reinterpret_cast<double*>(base + L.Wa);
+    double* Uinv64 = reinterpret_cast<double*>(base + L.Uinv64);
+    double* M64 = reinterpret_cast<double*>(base + L.M64);
+    double* C64 = reinterpret_cast<double*>(base + L.C64);
+    double* B64 = reinterpret_cast<double*>(base + L.B64);
+    double* Z64 = reinterpret_cast<double*>(base + L.Z64);
+    cublasHandle_t h = cublas_handle();
+    if (!h) return ID_ECUDA;
+    std::lock_guard<std::mutex> lk(g_cb_mu);
+    if (cublasSetStream(h, s) != CUBLAS_STATUS_SUCCESS) return ID_ECUDA;
+    if (cublasSetWorkspace(h, base + L.cws, kCublasWs) != CUBLAS_STATUS_SUCCESS) return ID_ECUDA;
+    if (cudaMemsetAsync(flag, 0, 16, s) != cudaSuccess) return ID_ECUDA;
+    const int tr = trace_begin(TraceKind::kSampledZ, s);
+    const double one = 1.0, zero = 0.0;
+    if (sizeof(T) == 8) {
+        const double* A64 = reinterpret_cast<const double*>(Av);
+        k_rk_identity<T><<<grid_for((int64_t)2 * k * k), kRThreads, 0, s>>>(static_cast<const T*>(W), ldw, k, Wa);
+        if (solve_run<double>(Wa, k, k, 2 * k, Uinv64, k, s) != cudaSuccess) return ID_ECUDA;
+        k_gather_f64<T><<<grid_for(m * k), kRThreads, 0, s>>>(A, lda, (int)m, k, J, C64);
+        // B = C^T A: B^T (n x k) = A^T (n x m) C (m x k); row-major arrays read as column-major transposes
+        if (cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_T, (int)n, k, (int)m, &one, A64, (int)lda, C64, k, &zero, B64,
+                        (int)n) != CUBLAS_STATUS_SUCCESS)
+            return ID_ECUDA;
+    } else {
+        float* C32 = reinterpret_cast<float*>(base + L.C32);
+        factor_skeleton(reinterpret_cast<const float*>(A), m, n, lda, k, J, C32,
+                        reinterpret_cast<double*>(base + L.Gp), Wa, Uinv64, reinterpret_cast<double*>(base + L.gdiag),
+                        flag, s);
+        k_ctb<<<dim3(ceil_div(n, kGT), ceil_div(k, kGT)), 256, 0, s>>>(C32, reinterpret_cast<const float*>(A), lda,
+                                                                       (int)m, k, (int)n, B64);
+    }
+    // M = U^{-1} U^{-T} (= (C^T C)^{-1}); Uinv64 row-major reads as U^{-T} column-major
+    if (cublasDgemm(h, CUBLAS_OP_T, CUBLAS_OP_N, k, k, k, &one, Uinv64, k, Uinv64, k, &zero, M64, k) !=
+        CUBLAS_STATUS_SUCCESS)
+        return ID_ECUDA;
+    // Z = M B: Z^T (n x k) = B^T M^T
+    double* Zd = sizeof(T) == 8 ? reinterpret_cast<double*>(Zv) : Z64;
+    const int ldzd = sizeof(T) == 8 ? (int)ldz : (int)n;
+    if (cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_T, (int)n, k, k, &one, B64, (int)n, M64, k, &zero, Zd, ldzd) !=
+        CUBLAS_STATUS_SUCCESS)
+        return ID_ECUDA;
+    dim3 g2(ceil_div(n, kRThreads) < 1024 ? ceil_div(n, kRThreads) : 1024, k);
+    if (sizeof(T) == 4) k_z_from64<T><<<g2, kRThreads, 0, s>>>(Z64, k, (int)n, Z, ldz);
+    k_identity_at_j<T><<<grid_for((int64_t)k * k), kRThreads, 0, s>>>(Z, ldz, J, k);
+    k_zstats_t<T><<<g2, kRThreads, 0, s>>>(Z, ldz, k, (int)n, dinfo);
+    k_sampled_finalize<<<1, 1, 0, s>>>(dinfo, flag);
+    trace_end(tr, s);
+    return cudaGetLastError() == cudaSuccess ? ID_OK : ID_ECUDA;
+}
+
+template cudaError_t sample_gather_run<double>(const void*, int64_t, int, const int32_t*, int, void*, int,
+                                               cudaStream_t);
+template cudaError_t sample_gather_run<float>(const void*, int64_t, int, const int32_t*, int, void*, int, cudaStream_t);
+template int sampled_z_run<double>(const void*, int64_t, int64_t, int64_t, int, const int32_t*, const void*, int,
+                                   void*, int64_t, void*, DevInfo*, cudaStream_t);
+template int sampled_z_run<float>(const void*, int64_t, int64_t, int64_t, int, const int32_t*, const void*, int,
+                                  void*, int64_t, void*, DevInfo*, cudaStream_t);
 
 }  // namespace gbid

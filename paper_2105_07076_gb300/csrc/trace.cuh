@@ -6,7 +6,7 @@
 
 namespace gbid {
 
-enum class TraceKind : int { kCpqr = 0, kSolve = 1, kSketch = 2, kCopyIn = 3, kScatter = 4, kBatched = 5, kRefine = 6, kCount = 7 };
+enum class TraceKind : int { kCpqr = 0, kSolve = 1, kSketch = 2, kCopyIn = 3, kScatter = 4, kBatched = 5, kRefine = 6, kSampledZ = 7, kCount = 8 };
 
 bool trace_on();
 int trace_begin(TraceKind k, cudaStream_t s);   // returns a record id, -1 when not tracing

@@ -120,6 +120,33 @@ def test_refine_rules(gbid):
     assert on > off
 
 
+def test_sampled_rules(gbid):
+    """Optim RID: p sampled columns, k <= p <= n, k <= m; the sample is checked
+    on the host (distinct, in range) before anything reaches the device."""
+    L = gbid.lib()
+    fake = ctypes.c_void_p(256)
+    o = gbid._opts(0)
+    assert L.id_sampled_workspace_size(0, 300, 1000, 228, 190, ctypes.byref(o)) > 300 * 228 * 8
+    assert L.id_sampled_workspace_size(1, 1000, 600, 36, 30, ctypes.byref(o)) > 0     # tall A: CPQR of 1000 x 36
+    assert L.id_sampled_workspace_size(0, 300, 1000, 1001, 190, None) == 0             # p > n
+    assert L.id_sampled_workspace_size(0, 300, 1000, 100, 190, None) == 0              # k > p
+    assert L.id_sampled_workspace_size(0, 100, 1000, 228, 190, None) == 0              # k > m
+    assert L.id_sampled_workspace_size(3, 300, 1000, 228, 190, None) == 0              # dtype
+
+    def call(idx, p=None, k=2, work_bytes=1 << 30, lda=80):
+        arr = (ctypes.c_int32 * len(idx))(*idx)
+        return L.id_decompose_sampled(fake, 0, 50, 80, lda, arr, len(idx) if p is None else p, k, None, fake, fake,
+                                      80, fake, work_bytes, None, None)
+
+    assert call([1, 1, 2, 3]) == gbid.ID_EINVAL           # repeated column
+    assert call([0, 5, 80, 2]) == gbid.ID_EINVAL           # out of range
+    assert call([-1, 2, 3, 4]) == gbid.ID_EINVAL
+    assert call([0, 1, 2, 3], k=5) == gbid.ID_EINVAL       # k > p
+    assert call([0, 1, 2, 3], lda=79) == gbid.ID_EINVAL
+    assert call([0, 1, 2, 3], lda=1 << 31) == gbid.ID_EINVAL
+    assert call([0, 1, 2, 3], work_bytes=64) == gbid.ID_ENOMEM
+
+
 def test_batched_workspace_rules(gbid):
     L = gbid.lib()
     assert L.id_batched_problem_workspace_size(1, 100, 300, 20) >= 100 * 300 * 4 + 300 * 4
