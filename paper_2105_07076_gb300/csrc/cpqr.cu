@@ -297,6 +297,10 @@ struct SmemPlan {
 //     of the working precision (Drmac & Bujanovic, LAPACK Working Note 176);
 //     at a panel's first step the norms are reset exactly from the product's
 //     sum of squares; partial argmax.                          -- grid barrier
+//     In FP64 (outside a panel's first step) the product takes a row-slab
+//     form instead: every warp covers one row slab of every column of the
+//     CTA, so the warps finish together (no tail of whole columns), and the
+//     epilogue runs a lane per column (FP64 arithmetic on full warps).
 //  C. every nb steps (nb < k): compact-WY update W_trail -= V F^T. -- barrier
 // Every wait (grid barrier, aux counter) is bounded and ends the kernel early
 // with kStatTimeout instead of hanging.
@@ -316,6 +320,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
     __shared__ double sc[4];
     __shared__ double red2[NW];
     __shared__ int qctr;   // column queue of this CTA
+    __shared__ double nu_s[2][kWarp], nu2_s[2][kWarp];   // slab-form epilogue operands
+    __shared__ int orig_s[2][kWarp];
+    __shared__ int abort_s;
 
     T* W = static_cast<T*>(P.W);
     T* F = static_cast<T*>(P.F);
@@ -505,7 +512,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
                 for (int u = 0; u < kBU; ++u) {
                     const int ii = i + u * kThreads;
                     if (kSmemV && ii < i_hi) v_s[ii - j_al] = xs[u];
-                    adot += vs4[u] * xs[u];
+                    if (has_aux) adot += vs4[u] * xs[u];
                 }
             }
             sq = warp_sum(sq);
@@ -681,6 +688,207 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
             // L2 round trip serves both (the sketch of a randomized ID has ~520 rows).
             constexpr int S = kWarp * VN;
             const bool pair = kShort && (m_pad - j_al) <= 4 * S && jj <= kWarp;
+            if (sizeof(T) == 8 && !exact_norms) {
+                // FP64: balanced row-slab form. Warp w takes the same row slab of every
+                // column of a group of GC columns (GC accumulators per lane), so the
+                // warps of a CTA finish a group together. Loads run PD columns ahead
+                // of the products. The lane partials are reduced across the warp in
+                // transposed form (lane q ends with the sum of column q: about one
+                // add per column), and the slabs' sums meet in shared memory. The
+                // epilogue then runs one lane per column: the panel products
+                // F(l, :) aux and F(l, :) V(j, :)^T by all threads (TPC per column),
+                // the scalar part (F(l, jj), R(j, l), the norm downdate) by one warp.
+                constexpr int GC = 16;                          // columns per group
+                constexpr int TPC = kThreads / GC;              // threads per column in the panel products
+                constexpr int UR = 4;                           // row units (S rows) of a slab per pass
+                constexpr int PD = 1;                           // columns whose loads run ahead
+                T* part_s = wy_s;                               // [2][NW][32] slab sums (phase C's tiles are idle)
+                T* auxs = part_s + 2 * NW * kWarp;              // [kMaxPanel]
+                T* s1_s = auxs + kMaxPanel;                     // [2][32] F(l, :) aux
+                T* s2_s = s1_s + 2 * kWarp;                     // [2][32] F(l, :) V(j, :)^T
+                T* wj_s = s2_s + 2 * kWarp;                     // [2][32] W(j, l)
+                const int nU = (m_pad - j_al + S - 1) / S;
+                const int uw0 = w * nU / NW, uw1 = (w + 1) * nU / NW;
+                auto col_of = [&](int q) { return j + 1 + c_lo + (rev ? c_cnt - 1 - q : q); };
+                for (int g0 = 0, gi = 0; g0 < c_cnt; g0 += GC, ++gi) {
+                    const int ncg = min(GC, c_cnt - g0);
+                    const int pb = gi & 1;
+                    T* part = part_s + pb * NW * kWarp;
+                    // the scalar epilogue's operands, loaded now and stored after the products
+                    const int pk = t / GC, pq = t % GC;
+                    double pre = 0.0;
+                    if (pk < 4 && pq < ncg) {
+                        const int l = col_of(g0 + pq);
+                        if (pk == 0) pre = (double)ld(W + (int64_t)l * ldw + j);
+                        else if (pk == 1) pre = ld(P.vn1 + l);
+                        else if (pk == 2) pre = ld(P.vn2 + l);
+                        else pre = (double)ld(P.perm + l);
+                    }
+                    T acc[GC];
+#pragma unroll
+                    for (int cc = 0; cc < GC; ++cc) acc[cc] = T(0);
+                    for (int u0 = uw0; u0 < uw1; u0 += UR) {
+                        V xv[PD + 1][UR];
+                        auto load_col = [&](V(&x)[UR], int cc) {
+                            const T* col = W + (int64_t)col_of(g0 + cc) * ldw;
+#pragma unroll
+                            for (int ur = 0; ur < UR; ++ur) {
+                                const int i = j_al + (u0 + ur) * S + lane * VN;
+                                if (u0 + ur < uw1 && i < m_pad) x[ur] = __ldcg(reinterpret_cast<const V*>(col + i));
+                            }
+                        };
+#pragma unroll
+                        for (int q = 0; q < PD; ++q)
+                            if (q < ncg) load_col(xv[q], q);
+#pragma unroll
+                        for (int cc = 0; cc < GC; ++cc) {
+                            if (cc < ncg) {
+                                if (cc + PD < ncg) load_col(xv[(cc + PD) % (PD + 1)], cc + PD);
+#pragma unroll
+                                for (int ur = 0; ur < UR; ++ur) {
+                                    const int i = j_al + (u0 + ur) * S + lane * VN;
+                                    if (u0 + ur < uw1 && i < m_pad) {
+                                        const V yv = kSmemV ? *reinterpret_cast<const V*>(v_s + (i - j_al))
+                                                            : x_at<T, V, VN>(xbuf, i, j, m);
+                                        acc[cc] = dot_vec(xv[cc % (PD + 1)][ur], yv, acc[cc]);
+                                    }
+                                }
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int o = GC / 2; o >= 1; o >>= 1) {
+                        const bool hi = (lane & o) != 0;
+#pragma unroll
+                        for (int q = 0; q < o; ++q) {
+                            const T send = hi ? acc[q] : acc[q + o];
+                            const T keep = hi ? acc[q + o] : acc[q];
+                            acc[q] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+                        }
+                    }
+                    if (GC < kWarp) acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], GC);
+                    if (lane < GC) part[w * kWarp + lane] = acc[0];
+                    if (pk < 4 && pq < ncg) {
+                        if (pk == 0) wj_s[pb * kWarp + pq] = (T)pre;
+                        else if (pk == 1) nu_s[pb][pq] = pre;
+                        else if (pk == 2) nu2_s[pb][pq] = pre;
+                        else orig_s[pb][pq] = (int)pre;
+                    }
+                    if (gi == 0 && w == 0) {   // the panel's aux entries, complete once the counter reaches jj
+                        int ok = 1;
+                        if (lane == 0) ok = wait_geq(P.auxcnt + j, (unsigned)jj, st) ? 1 : 0;
+                        ok = __shfl_sync(0xffffffffu, ok, 0);
+                        if (ok)
+                            for (int c = lane; c < jj; c += kWarp) auxs[c] = ld(aux + c);
+                        if (lane == 0) abort_s = !ok;
+                    }
+                    __syncthreads();
+                    if (abort_s) break;
+                    {   // panel products, TPC threads per column, 16 loads in flight per thread
+                        const int cc = t / TPC, seg = t % TPC;
+                        T s1 = T(0), s2 = T(0);
+                        if (cc < ncg) {
+                            const int l = col_of(g0 + cc);
+                            const bool moved = l == p && p != j;   // column p carries the old column j's F row
+                            const T* frow = F + (int64_t)(moved ? j : l) * ldf;
+                            for (int c0 = seg; c0 < jj; c0 += 16 * TPC) {
+                                T fv[16];
+#pragma unroll
+                                for (int b = 0; b < 16; ++b) {
+                                    const int c = c0 + b * TPC;
+                                    fv[b] = c < jj ? ld(frow + c) : T(0);
+                                }
+#pragma unroll
+                                for (int b = 0; b < 16; ++b) {
+                                    const int c = c0 + b * TPC;
+                                    if (c < jj) {
+                                        if (moved) F[(int64_t)p * ldf + c] = fv[b];
+                                        s1 += fv[b] * auxs[c];
+                                        s2 += fv[b] * vrow_s[c];
+                                    }
+                                }
+                            }
+                        }
+#pragma unroll
+                        for (int o = TPC / 2; o >= 1; o >>= 1) {
+                            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+                            s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+                        }
+                        if (cc < ncg && seg == 0) {
+                            s1_s[pb * kWarp + cc] = s1;
+                            s2_s[pb * kWarp + cc] = s2;
+                        }
+                    }
+                    __syncthreads();
+                    if (w == (gi + (int)blockIdx.x) % NW) {   // scalar epilogue, lane q <-> column q of the group
+                        int flagged = 0, l = -1;
+                        T f = T(0);
+                        if (lane < ncg) {
+                            l = col_of(g0 + lane);
+                            T gx = T(0);
+#pragma unroll
+                            for (int w2 = 0; w2 < NW; ++w2) gx += part[w2 * kWarp + lane];
+                            const T wjl = wj_s[pb * kWarp + lane];
+                            const T g = scaleT * gx + wjl;          // v^T W(j:m, l)
+                            f = tauT * g + s1_s[pb * kWarp + lane];
+                            const T r = wjl - s2_s[pb * kWarp + lane] - f;   // R(j, l)
+                            F[(int64_t)l * ldf + jj] = f;
+                            W[(int64_t)l * ldw + j] = r;
+                            ArgMax cnd;
+                            cnd.orig = orig_s[pb][lane];
+                            cnd.pos = l;
+                            cnd.val = 0.0;
+                            const double nu = nu_s[pb][lane];
+                            if (nu != 0.0) {
+                                // nu_new^2 = (nu - |r|)(nu + |r|); recompute when it falls to
+                                // sqrt(eps) of the last exact norm squared
+                                const double ra = fabs((double)r);
+                                double t2 = (nu - ra) * (nu + ra);
+                                t2 = t2 > 0.0 ? t2 : 0.0;
+                                const double nu2 = nu2_s[pb][lane];
+                                if (t2 <= tol3z * nu2 * nu2) {
+                                    flagged = 1;
+                                } else {
+                                    cnd.val = sqrt(t2);
+                                    P.vn1[l] = cnd.val;
+                                }
+                            }
+                            if (!flagged && better(cnd, bestc)) bestc = cnd;
+                        }
+                        unsigned fm = __ballot_sync(0xffffffffu, flagged);
+                        while (fm) {
+                            // cancellation: exact ||W(j+1:m, l) - V F(l, 0:jj+1)^T|| by the whole warp
+                            const int src = __ffs(fm) - 1;
+                            fm &= fm - 1;
+                            const int lr = __shfl_sync(0xffffffffu, l, src);
+                            const T fr = __shfl_sync(0xffffffffu, f, src);
+                            const int origr = orig_s[pb][src];
+                            const T* frow = F + (int64_t)((lr == p && p != j) ? j : lr) * ldf;
+                            const T* col = W + (int64_t)lr * ldw;
+                            double sacc = 0.0;
+                            for (int i = j + 1 + lane; i < m; i += kWarp) {
+                                T y = ld(col + i);
+                                for (int c = 0; c < jj; ++c) y -= ld(W + (int64_t)(j0 + c) * ldw + i) * ld(frow + c);
+                                const T vi = ld(xbuf + i) * scaleT;   // the current reflector
+                                y -= vi * fr;
+                                sacc = fma((double)y, (double)y, sacc);
+                            }
+                            sacc = warp_sum(sacc);
+                            if (lane == src) {
+                                const double nv = sqrt(sacc);
+                                P.vn1[lr] = nv;
+                                P.vn2[lr] = nv;
+                                ArgMax cnd;
+                                cnd.val = nv;
+                                cnd.orig = origr;
+                                cnd.pos = lr;
+                                if (better(cnd, bestc)) bestc = cnd;
+                                atomicAdd(&st->n_recompute, 1);
+                            }
+                        }
+                    }
+                }
+            } else {
             int idx = 0;
             if (lane == 0) idx = atomicAdd(ctr, pair ? 2 : 1);
             idx = __shfl_sync(0xffffffffu, idx, 0);
@@ -892,6 +1100,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
                 if (nbat == kWarp || idx >= c_cnt) flush();
             }
             if (nbat > 0) flush();   // only reached after a timed-out wait
+            }
             bestc = block_argmax(bestc);
             if (t == 0) P.part[blockIdx.x] = bestc;
         }
