@@ -199,14 +199,15 @@ int id_sketch(const void* A, id_dtype dtype, int64_t m, int64_t n, int64_t lda, 
 /* id_decompose_randomized -- randomized rank-k ID of A (m x n, m <= n) from a
  * Gaussian sketch: Y = Omega A (id_sketch, tensor cores), k steps of column-
  * pivoted QR of Y (FP32 matrix, FP64 residual norms), T = R11^{-1} R12 of Y's R
- * in FP64, Z = [I T] P^T. The skeleton J indexes columns of A; Z is the
- * sketched interpolation matrix (Sec. 2.2 computes Z by least squares on A
- * instead; here the sketch's R supplies it).
+ * in FP64, Z = [I T] P^T. The skeleton J indexes columns of A. By default
+ * (opts->refine = 0) Z is then refined once against A (id_refine): the
+ * least-squares Z for J that Sec. 2.2 asks for; opts->refine = -1 keeps the
+ * sketch's Z (T then comes from Y's R in FP64 instead of FP32).
  *
- *   A      [in]  m x n FP32 row-major, lda >= n, lda a multiple of 4, 16-byte aligned.
+ *   A      [in]  m x n FP32 row-major, n <= lda < 2^31, lda a multiple of 4, 16-byte aligned.
  *   Omega  [in]  l x m BF16 row-major, ldo >= m, ldo a multiple of 8, 16-byte
  *                aligned; k <= l <= min(m, 640).
- *   J, Z   [out] as for id_decompose (Z: k x n FP32, ldz >= n).
+ *   J, Z   [out] as for id_decompose (Z: k x n FP32, n <= ldz < 2^31).
  *   work   [in]  id_rid_workspace_size(m, n, l, k, opts) bytes, 256-byte aligned.
  *   dtype must be ID_F32. info / stream as for id_decompose. */
 size_t id_rid_workspace_size(int64_t m, int64_t n, int64_t l, int64_t k, const id_opts* opts);
@@ -249,9 +250,9 @@ int id_decompose_sampled(const void* A, id_dtype dtype, int64_t m, int64_t n, in
  * its Cholesky factor U in FP64; U^{-1} in FP64, applied in FP32; the
  * residual A - C Z and C^T times it as FP32-accurate GEMMs (cuBLAS, FP32
  * compute emulated on the BF16 tensor cores where that is faster).
- *   A     [in]     m x n FP32 row-major, lda >= n, m <= n (a column ID).
+ *   A     [in]     m x n FP32 row-major, n <= lda < 2^31, m <= n (a column ID).
  *   J     [in]     k skeleton columns (distinct, in [0, n)).
- *   Z     [in,out] k x n FP32 row-major, ldz >= n; Z[:, J] = I on entry.
+ *   Z     [in,out] k x n FP32 row-major, n <= ldz < 2^31; Z[:, J] = I on entry.
  *   work  [in]     id_refine_workspace_size() bytes, 256-byte aligned.
  *   info  [out]    HOST pointer or NULL (as for id_decompose): status ID_OK,
  *                  refined = 1, and the Z statistics after the update. If
@@ -269,7 +270,7 @@ int id_refine(const void* A, id_dtype dtype, int64_t m, int64_t n, int64_t lda, 
  *   Z[:, J] = I is constant, Z[:, rest] = T = C^+ B, C = A[:, J], B = A[:, rest];
  *   with W = (C^T C)^{-1} dZ[:, rest]:
  *   dA[:, rest] = C W,   dA[:, J] = (B - C T) W^T - C W T^T.
- *   A   [in]  m x n FP32 row-major (m <= n), lda >= n.
+ *   A   [in]  m x n FP32 row-major (m <= n), n <= lda < 2^31 (ldz, lddz, ldda too).
  *   J   [in]  k skeleton columns; Z [in] k x n FP32 (ldz >= n), the ID's Z for J.
  *   dZ  [in]  k x n FP32 (lddz >= n): dL/dZ (its columns at J are ignored).
  *   dA  [out] m x n FP32 (ldda >= n): dL/dA.

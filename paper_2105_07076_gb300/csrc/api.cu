@@ -329,6 +329,7 @@ int id_decompose_randomized(const void* A, id_dtype dtype, int64_t m, int64_t n,
     const size_t need = id_rid_workspace_size(m, n, l, k, opts);
     if (need == 0) return ID_EINVAL;
     if (lda < n || lda % 4 != 0 || ldo < m || ldo % 8 != 0 || ldz < n) return ID_EINVAL;
+    if (lda > INT32_MAX || ldz > INT32_MAX) return ID_EINVAL;   // leading dimensions of the refinement's GEMMs
     if (!aligned(A, 16) || !aligned(Omega_bf16, 16) || !aligned(work, 256)) return ID_EINVAL;
     if (opts && opts->nb < 0) return ID_EINVAL;
     if (work_bytes < need) return ID_ENOMEM;
@@ -444,6 +445,7 @@ int id_backward(const void* A, id_dtype dtype, int64_t m, int64_t n, int64_t lda
     const size_t need = id_backward_workspace_size(dtype, m, n, k);
     if (need == 0) return ID_EINVAL;
     if (lda < n || ldz < n || lddz < n || ldda < n || !aligned(work, 256)) return ID_EINVAL;
+    if (lda > INT32_MAX || ldz > INT32_MAX || lddz > INT32_MAX || ldda > INT32_MAX) return ID_EINVAL;
     if (work_bytes < need) return ID_ENOMEM;
     if (configure_once()) return ID_ECUDA;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -469,6 +471,7 @@ int id_refine(const void* A, id_dtype dtype, int64_t m, int64_t n, int64_t lda, 
     const size_t need = id_refine_workspace_size(dtype, m, n, k);
     if (need == 0) return ID_EINVAL;
     if (lda < n || ldz < n || !aligned(work, 256)) return ID_EINVAL;
+    if (lda > INT32_MAX || ldz > INT32_MAX) return ID_EINVAL;   // leading dimensions of the GEMMs
     if (work_bytes < need) return ID_ENOMEM;
     if (configure_once()) return ID_ECUDA;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
