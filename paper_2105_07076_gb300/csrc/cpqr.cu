@@ -151,7 +151,7 @@ __device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
 __device__ bool wait_geq(const unsigned* p, unsigned target, State* st) {
     unsigned long long spins = 0;
     while (ld_acquire(p) < target) {
-        if (timed_out(st)) return false;
+        if ((spins & 31) == 31 && timed_out(st)) return false;   // another CTA gave up
         if (++spins > kSpinLimit) {
             atomicOr(&st->status, kStatTimeout);
             return false;
@@ -270,7 +270,8 @@ __device__ void wy_tile(T* W, int ldw, int m, int n, int i0, int l0, int j0, int
 }
 
 constexpr int kFRegs = 8;   // panel entries per lane held in registers (panels up to 256 wide)
-constexpr int kPre = 16;    // reflector entries per thread prefetched ahead of the pivot argmax
+// reflector entries per thread prefetched ahead of the pivot argmax (panels up to 8 * kPre wide)
+template <typename T> constexpr int pre_entries() { return sizeof(T) == 4 ? 32 : 16; }
 
 // Shared-memory plan of k_cpqr (dynamic part): vrow_s | fco | v_s.
 struct SmemPlan {
@@ -384,6 +385,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
         // The panel's reflector entries on this CTA's first row tile do not
         // depend on the pivot: their loads are issued before the argmax
         // reduction so that the two latencies overlap.
+        constexpr int kPre = pre_entries<T>();
         T vpre[kPre];
         {
             const int r = r0 + lane;
@@ -416,13 +418,18 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
                 P.perm[p] = a;
             }
         }
+        // W(r, p), W(r, j) of the first row tile go out together with the F-row loads
+        T wa = T(0), wb = T(0);
+        if (w == 0 && r0 + lane < r1) {
+            wa = ld(W + (int64_t)p * ldw + r0 + lane);
+            wb = ld(W + (int64_t)j * ldw + r0 + lane);
+        }
         for (int c = t; c < jj; c += kThreads) fco[c] = ld(F + (int64_t)p * ldf + c);
         __syncthreads();
         double ssq = 0.0;
         for (int rt = r0; rt < r1; rt += kWarp) {
             const int r = rt + lane;
-            T wa = T(0), wb = T(0);   // W(r, p), W(r, j): issued ahead of the products
-            if (w == 0 && r < r1) {
+            if (rt != r0 && w == 0 && r < r1) {   // later row tiles (matrices taller than 32 rows per CTA)
                 wa = ld(W + (int64_t)p * ldw + r);
                 wb = ld(W + (int64_t)j * ldw + r);
             }
@@ -492,13 +499,15 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
         const bool has_aux = c_aux < jj;
         const T* vca = W + (int64_t)(j0 + (has_aux ? c_aux : 0)) * ldw;
         {
-            double sq = 0.0;
-            for (int e = t; e < G; e += kThreads) sq += ld(P.ssq + e);
+            double sq = t < G ? ld(P.ssq + t) : 0.0;
+            const double sq_b = t + kThreads < G ? ld(P.ssq + t + kThreads) : 0.0;
+            for (int e = t + 2 * kThreads; e < G; e += kThreads) sq += ld(P.ssq + e);
+            sq += sq_b;
             if (t == kThreads - 1) sc[3] = ld(&st->x0);
             for (int c = t; c < jj; c += kThreads) vrow_s[c] = ld(W + (int64_t)(j0 + c) * ldw + j);
             T adot = T(0);
             const int i_lo = kSmemV ? j_al : j + 1, i_hi = kSmemV ? m_pad : m;
-            constexpr int kBU = 8;   // loads in flight per thread and operand
+            constexpr int kBU = sizeof(T) == 4 ? 16 : 8;   // loads in flight per thread and operand
             for (int i = i_lo + t; (kSmemV || has_aux) && i < i_hi; i += kBU * kThreads) {
                 T xs[kBU], vs4[kBU];
 #pragma unroll
