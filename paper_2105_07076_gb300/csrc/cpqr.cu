@@ -217,6 +217,7 @@ struct KParams {
     State* st;
     double rank_tol;
     int rows_per_cta; // row chunk of the pivot-column phase (multiple of 32)
+    int short_mode;   // short matrices with panels of at most 32: one grid barrier per step
 };
 
 // WY tile: W(i, l) -= sum_{c < nbw} V(i, c) F(l, c), 64 x 64 tile at (i0, l0).
@@ -316,6 +317,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
     T* vrow_s = reinterpret_cast<T*>(smem_raw);
     T* fco = vrow_s + kMaxPanel + 4;
     T* v_s = fco + kMaxPanel + 4;                      // 16-byte aligned
+    const int ldv = (P.m + Vec<T>::n - 1) / Vec<T>::n * Vec<T>::n + 8;   // v_s length; the panel copy follows
+    T* vpan_s = v_s + ldv;                             // short mode: the panel's reflectors, ldv per column
     __shared__ T wy_s[16 * 64 + 16 * 65];              // WY-update tiles
     __shared__ T red[NW][kWarp];
     __shared__ double sc[4];
@@ -324,6 +327,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
     __shared__ double nu_s[2][kWarp], nu2_s[2][kWarp];   // slab-form epilogue operands
     __shared__ int orig_s[2][kWarp];
     __shared__ int abort_s;
+    __shared__ T aux_s[kWarp];     // short mode: aux of the current step
+    __shared__ T x0_s;
 
     T* W = static_cast<T*>(P.W);
     T* F = static_cast<T*>(P.F);
@@ -381,6 +386,130 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
         const int j0 = j / P.nb * P.nb;
         const int jj = j - j0;
 
+        const bool shortm = kShort && P.short_mode;
+        const int j_al = j & ~(VN - 1);
+        const int m_pad = (m + VN - 1) / VN * VN;
+        int p = j;
+        if (shortm) {
+            // ---- A+B for short matrices (panels of at most 32): every CTA forms the
+            // pivot column, the reflector and aux itself from its shared-memory copy
+            // of the panel's reflectors, so the step needs one grid barrier instead
+            // of two, and no aux counter. The arithmetic is the same in every CTA.
+            // Rows t + 256 u of W(:, j) go out first (they do not depend on the pivot):
+            // the CTA that writes the columns j and p then needs no further round trip.
+            constexpr int kSR = (5 * kWarp * VN + kThreads - 1) / kThreads;   // rows per thread (m <= 5 * 32 * VN)
+            T wj_r[kSR], wp_r[kSR];
+#pragma unroll
+            for (int u = 0; u < kSR; ++u) {
+                const int i = t + u * kThreads;
+                wj_r[u] = i < m ? ld(W + (int64_t)j * ldw + i) : T(0);
+            }
+            ArgMax best = empty_argmax();
+            for (int e = t; e < G; e += kThreads) {
+                const ArgMax c = ld_argmax(P.part + e);
+                if (better(c, best)) best = c;
+            }
+            best = block_argmax(best);
+            p = best.pos >= j ? best.pos : j;
+            if (blockIdx.x == 0 && p != j) {
+                if (t == 0) {
+                    const double a = ld(P.vn1 + j), b = ld(P.vn1 + p);
+                    P.vn1[j] = b;
+                    P.vn1[p] = a;
+                } else if (t == 32) {
+                    const double a = ld(P.vn2 + j), b = ld(P.vn2 + p);
+                    P.vn2[j] = b;
+                    P.vn2[p] = a;
+                } else if (t == 64) {
+                    const int a = ld(P.perm + j), b = ld(P.perm + p);
+                    P.perm[j] = b;
+                    P.perm[p] = a;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kSR; ++u) {
+                const int i = t + u * kThreads;
+                wp_r[u] = i < m ? ld(W + (int64_t)p * ldw + i) : T(0);
+            }
+            for (int c = t; c < jj; c += kThreads) fco[c] = ld(F + (int64_t)p * ldf + c);
+            __syncthreads();
+            // x(i) = W(i, p) - sum_c V(i, c) F(p, c) on rows j..m-1; v_s = x below row j
+            double sq = 0.0;
+#pragma unroll
+            for (int u = 0; u < kSR; ++u) {
+                const int i = t + u * kThreads;
+                if (i >= j_al && i < m_pad) {
+                    T x = T(0);
+                    if (i >= j && i < m) {
+                        T acc = T(0);
+                        for (int c = 0; c < jj; ++c) acc += vpan_s[c * ldv + i] * fco[c];
+                        x = wp_r[u] - acc;
+                    }
+                    if (i == j) x0_s = x;
+                    v_s[i - j_al] = i > j ? x : T(0);
+                    if (i > j) sq = fma((double)x, (double)x, sq);
+                }
+            }
+            const double S = block_sum(sq);   // synchronises: x0_s and v_s are visible after it
+            if (t == 0) {
+                const double x0 = (double)x0_s;
+                const double alpha = sqrt(fma(x0, x0, S));
+                double beta = 0.0, tau = 0.0, scale = 0.0;
+                if (alpha != 0.0) {
+                    beta = x0 >= 0.0 ? -alpha : alpha;
+                    tau = (beta - x0) / beta;
+                    scale = 1.0 / (x0 - beta);
+                }
+                sc[0] = beta;
+                sc[1] = tau;
+                sc[2] = scale;
+                if (j == 0) r00 = fabs(beta);
+                if (blockIdx.x == 0) {
+                    st->beta = beta;
+                    st->tau = tau;
+                    P.tau[j] = tau;
+                    if (j == 0) st->r00 = r00;
+                    if (r00 == 0.0 || fabs(beta) <= P.rank_tol * r00) atomicMin(&st->rank, j);
+                    if (!isfinite(beta)) atomicOr(&st->status, kStatNonFinite);
+                }
+                qctr = 0;
+            }
+            __syncthreads();
+            const T tauT = (T)sc[1], scaleT = (T)sc[2];
+            // aux(c) = -tau (scale V(j+1:m, c)^T x(j+1:m) + V(j, c)), one warp per entry
+            for (int c = w; c < jj; c += NW) {
+                T a = T(0);
+                for (int i = j + 1 + lane; i < m; i += kWarp) a += vpan_s[c * ldv + i] * v_s[i - j_al];
+                a = warp_sum(a);
+                if (lane == 0) aux_s[c] = -tauT * (scaleT * a + vpan_s[c * ldv + j]);
+            }
+            for (int c = t; c < jj; c += kThreads) vrow_s[c] = vpan_s[c * ldv + j];
+            __syncthreads();   // the panel copy's column jj is rewritten next
+            for (int i = t; i < ldv; i += kThreads)
+                vpan_s[jj * ldv + i] = (i > j && i < m) ? v_s[i - j_al] * scaleT : T(0);
+            // The columns j and p: the CTA whose trailing range holds position p
+            // (CTA 0 when p = j) writes them, so its own product reads the new
+            // column p and nobody else touches either column in this step.
+            const int ncols = n - j - 1;
+            int owner = 0;
+            if (p != j) {
+                const int q = p - j - 1, per = ncols / G, rem = ncols % G;
+                owner = q < rem * (per + 1) ? q / (per + 1) : rem + (q - rem * (per + 1)) / per;
+            }
+            if ((int)blockIdx.x == owner) {
+                const T betaT = (T)sc[0];
+#pragma unroll
+                for (int u = 0; u < kSR; ++u) {
+                    const int i = t + u * kThreads;
+                    if (i < m) {
+                        if (p != j) W[(int64_t)p * ldw + i] = wj_r[u];   // the old column j moves to p
+                        if (i >= j || p != j)
+                            W[(int64_t)j * ldw + i] = i < j ? wp_r[u] : (i == j ? betaT : v_s[i - j_al] * scaleT);
+                    }
+                }
+            }
+            __syncthreads();
+        } else {
         // ---- A: pivot, swap, lazy update of the pivot column
         // The panel's reflector entries on this CTA's first row tile do not
         // depend on the pivot: their loads are issued before the argmax
@@ -402,7 +531,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
             if (better(c, best)) best = c;
         }
         best = block_argmax(best);
-        const int p = best.pos >= j ? best.pos : j;
+        p = best.pos >= j ? best.pos : j;
         if (blockIdx.x == 0 && p != j) {
             if (t == 0) {
                 const double a = ld(P.vn1 + j), b = ld(P.vn1 + p);
@@ -493,8 +622,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
         // aux entry and the trailing product's operands, from one round of loads.
         //   aux(c) = -tau V(j:m, c)^T v = -tau (scale V(j+1:m, c)^T x + V(j, c))
         // (the dot needs only x, so it is formed before beta is known).
-        const int j_al = j & ~(VN - 1);
-        const int m_pad = (m + VN - 1) / VN * VN;
         const int c_aux = blockIdx.x;
         const bool has_aux = c_aux < jj;
         const T* vca = W + (int64_t)(j0 + (has_aux ? c_aux : 0)) * ldw;
@@ -568,15 +695,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
             }
             __syncthreads();
         }
-        const double beta = sc[0], tau = sc[1], scale = sc[2];
-        // v = x * scale (v_j = 1) in the working precision. The stored reflector
-        // is formed elementwise; the products with v below use
-        // v^T y = scale * x(j+1:m)^T y(j+1:m) + y_j, so no per-element scaling
-        // (and no FP64 conversion in FP32) is needed on the hot loops.
-        const T scaleT = (T)scale;
-        // v on this CTA's rows into W(:, j) (reflector storage, v_j = 1 implicit)
-        for (int r = max(r0, j) + t; r < r1; r += kThreads)
-            W[(int64_t)j * ldw + r] = r == j ? (T)beta : ld(xbuf + r) * scaleT;
+        {
+            const T scaleT = (T)sc[2];
+            // v on this CTA's rows into W(:, j) (reflector storage, v_j = 1 implicit)
+            for (int r = max(r0, j) + t; r < r1; r += kThreads)
+                W[(int64_t)j * ldw + r] = r == j ? (T)sc[0] : ld(xbuf + r) * scaleT;
+        }
 
         // aux entries past the first G panel columns (panels wider than the grid)
         for (int c = blockIdx.x + G; c < jj; c += G) {
@@ -585,11 +709,18 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
             for (int i = j + 1 + t; i < m; i += kThreads) acc += ld(vc + i) * ld(xbuf + i);
             const T tot = block_sum_t(acc);
             if (t == 0) {
-                aux[c] = -(T)tau * (scaleT * tot + ld(vc + j));
+                aux[c] = -(T)sc[1] * ((T)sc[2] * tot + ld(vc + j));
                 __threadfence();
                 red_release_add(P.auxcnt + j, 1u);
             }
         }
+        }   // phases A and B (grid path)
+        // v = x * scale (v_j = 1) in the working precision. The stored reflector
+        // is formed elementwise; the products with v below use
+        // v^T y = scale * x(j+1:m)^T y(j+1:m) + y_j, so no per-element scaling
+        // (and no FP64 conversion in FP32) is needed on the hot loops.
+        const double tau = sc[1], scale = sc[2];
+        const T scaleT = (T)scale;
 
         // ---- B3: trailing product over this CTA's column range
         if (j + 1 < n) {
@@ -673,7 +804,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
                         T y = ld(col + i);
                         for (int c = 0; c < jj; ++c) y -= ld(W + (int64_t)(j0 + c) * ldw + i) * ld(frow + c);
                         // the current reflector (other CTAs may still be writing it to W(:, j))
-                        const T vi = ld(xbuf + i) * scaleT;
+                        const T vi = (shortm ? v_s[i - j_al] : ld(xbuf + i)) * scaleT;
                         y -= vi * f;
                         sacc = fma((double)y, (double)y, sacc);
                     }
@@ -962,10 +1093,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
                     }
                     if (!aux_ready) {
                         int ok = 1;
-                        if (lane == 0) ok = wait_geq(P.auxcnt + j, (unsigned)jj, st) ? 1 : 0;
+                        if (lane == 0 && !shortm) ok = wait_geq(P.auxcnt + j, (unsigned)jj, st) ? 1 : 0;
                         ok = __shfl_sync(0xffffffffu, ok, 0);
                         if (!ok) break;
-                        auxr[0] = lane < jj ? ld(aux + lane) : T(0);
+                        auxr[0] = lane < jj ? (shortm ? aux_s[lane] : ld(aux + lane)) : T(0);
                         aux_ready = true;
                     }
                     T s10 = T(0), s20 = T(0), s11 = T(0), s21 = T(0);
@@ -1065,13 +1196,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
                 }
                 if (!aux_ready) {
                     int ok = 1;
-                    if (lane == 0) ok = wait_geq(P.auxcnt + j, (unsigned)jj, st) ? 1 : 0;
+                    if (lane == 0 && !shortm) ok = wait_geq(P.auxcnt + j, (unsigned)jj, st) ? 1 : 0;
                     ok = __shfl_sync(0xffffffffu, ok, 0);
                     if (!ok) break;
 #pragma unroll
                     for (int q = 0; q < kFRegs; ++q) {
                         const int c = lane + q * kWarp;
-                        auxr[q] = c < jj ? ld(aux + c) : T(0);
+                        auxr[q] = c < jj ? (shortm ? aux_s[c < kWarp ? c : 0] : ld(aux + c)) : T(0);
                     }
                     aux_ready = true;
                 }
@@ -1088,7 +1219,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
                 for (int c = lane + kFRegs * kWarp; c < jj; c += kWarp) {   // panels wider than kFRegs * 32
                     const T fv = ld(frow + c);
                     if (moved) F[(int64_t)p * ldf + c] = fv;
-                    s1 += fv * ld(aux + c);
+                    s1 += fv * ld(aux + c);   // (never in short mode: its panels are at most 32 wide)
                     s2 += fv * vrow_s[c];
                 }
                 const T gx = warp_sum((a0 + a1) + (a2 + a3));   // x(j+1:m)^T W(j+1:m, l)
@@ -1128,6 +1259,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
 }
 
 // ------------------------------------------------------------------- host --
+// Matrices short enough for the kShort instance (v always fits in shared memory).
+// FP32 only: the FP64 instance spills and measured slower on a 200 x 400 ID
+// (550 against 504 us).
+template <typename T>
+static bool short_rows(int m) {
+    return sizeof(T) == 4 && m <= 5 * kWarp * Vec<T>::n;
+}
+
 // Shared-memory bytes of k_cpqr for m working rows; v is cached in shared
 // memory when it fits in kCpqrSmemMax.
 template <typename T>
@@ -1139,18 +1278,13 @@ static SmemPlan cpqr_smem(int m) {
     SmemPlan pl;
     pl.smem_v = fixed + vbytes <= kCpqrSmemMax;
     pl.bytes = fixed + (pl.smem_v ? vbytes : 0);
+    // short matrices keep a copy of the panel's reflectors (up to 32 columns of v's length)
+    if (short_rows<T>(m)) pl.bytes += (size_t)kWarp * vbytes;
     return pl;
 }
 
 static int g_nsm = 0;
 
-// Matrices short enough for the kShort instance (v always fits in shared memory).
-// FP32 only: the FP64 instance spills and measured slower on a 200 x 400 ID
-// (550 against 504 us).
-template <typename T>
-static bool short_rows(int m) {
-    return sizeof(T) == 4 && m <= 5 * kWarp * Vec<T>::n;
-}
 
 template <typename T>
 cudaError_t cpqr_configure() {
@@ -1233,6 +1367,7 @@ cudaError_t cpqr_run(const CpqrPlan& P, cudaStream_t s) {
     // numerical rank: |R_jj| <= sqrt(max(m, n)) eps |R_00| (rounding-noise level of a residual)
     K.rank_tol = sqrt((double)(P.m_user > P.n_user ? P.m_user : P.n_user)) * eps;
     K.rows_per_cta = (int)round_up(ceil_div(P.m, G), kWarp);
+    K.short_mode = short_rows<T>(P.m) && P.nb <= kWarp ? 1 : 0;
 
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(G);
