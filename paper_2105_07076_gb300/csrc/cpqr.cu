@@ -228,11 +228,23 @@ __device__ void wy_tile(T* W, int ldw, int m, int n, int i0, int l0, int j0, int
     const int t = threadIdx.x;
     const bool act = t < 256;   // 16 x 16 threads own the 64 x 64 tile
     const int tx = t % 16, ty = (t / 16) % 16;
-    T acc[4][4];
+    T acc[4][4], wv[4][4];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+    // FP32: the tile of W goes out first, its loads overlapping the staging of
+    // V and F (FP64 keeps the registers for the rest of the kernel)
+    constexpr bool kPreW = sizeof(T) == 4;
+#pragma unroll
+    for (int b = 0; b < 4 && kPreW; ++b) {
+        const int l = l0 + ty * 4 + b;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const int i = i0 + tx * 4 + a;
+            wv[a][b] = (act && l < n && i < m) ? ld(W + (int64_t)l * ldw + i) : T(0);
+        }
+    }
     for (int c0 = 0; c0 < nbw; c0 += TK) {
         __syncthreads();
         for (int e = t; e < TK * TM; e += kThreads) {
@@ -264,7 +276,7 @@ __device__ void wy_tile(T* W, int ldw, int m, int n, int i0, int l0, int j0, int
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
             const int i = i0 + tx * 4 + a;
-            if (i < m) W[(int64_t)l * ldw + i] = ld(W + (int64_t)l * ldw + i) - acc[a][b];
+            if (i < m) W[(int64_t)l * ldw + i] = (kPreW ? wv[a][b] : ld(W + (int64_t)l * ldw + i)) - acc[a][b];
         }
     }
     __syncthreads();
