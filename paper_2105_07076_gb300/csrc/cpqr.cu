@@ -185,6 +185,29 @@ __device__ __forceinline__ ArgMax ld_argmax(const ArgMax* p) {
     return a;
 }
 
+// Trailing-product loads with an L2 eviction hint. The sweep over a CTA's
+// columns reverses every step, so the columns read in the second half of one
+// sweep are read first in the next: those are loaded evict_last, the others
+// evict_first.
+__device__ __forceinline__ uint64_t l2_policy(bool last) {
+    uint64_t pol;
+    if (last) asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    else asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+__device__ __forceinline__ double2 ld_hint(const double2* p, uint64_t pol) {
+    double2 v;
+    asm volatile("ld.global.cg.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;" : "=d"(v.x), "=d"(v.y) : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ float4 ld_hint(const float4* p, uint64_t pol) {
+    float4 v;
+    asm volatile("ld.global.cg.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "l"(p), "l"(pol));
+    return v;
+}
+
 // VN consecutive entries of the pivot column x restricted to rows j+1..m-1
 // (zero elsewhere), read from global memory when it is not cached.
 template <typename T, typename V, int VN>
@@ -354,6 +377,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
     // R entries carry (FP32 R entries drift like u_32 (nu_exact / nu)^2).
     const double tol3z = sqrt(sizeof(T) == 8 ? DBL_EPSILON : (double)FLT_EPSILON);
     unsigned epoch = 0;
+    const uint64_t pol_last = l2_policy(true), pol_first = l2_policy(false);
 
     // ---- column norms, perm, first argmax partials
     {
@@ -883,10 +907,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
                         V xv[PD + 1][UR];
                         auto load_col = [&](V(&x)[UR], int cc) {
                             const T* col = W + (int64_t)col_of(g0 + cc) * ldw;
+                            const uint64_t pol = 2 * (g0 + cc) >= c_cnt ? pol_last : pol_first;
 #pragma unroll
                             for (int ur = 0; ur < UR; ++ur) {
                                 const int i = j_al + (u0 + ur) * S + lane * VN;
-                                if (u0 + ur < uw1 && i < m_pad) x[ur] = __ldcg(reinterpret_cast<const V*>(col + i));
+                                if (u0 + ur < uw1 && i < m_pad) x[ur] = ld_hint(reinterpret_cast<const V*>(col + i), pol);
                             }
                         };
 #pragma unroll
@@ -1078,8 +1103,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
                     for (int u = 0; u < 4; ++u) {
                         const int i = j_al + lane * VN + u * S;
                         if (i < m_pad) {
-                            xv[u] = __ldcg(reinterpret_cast<const V*>(cp0 + i));
-                            if (has1) xv[4 + u] = __ldcg(reinterpret_cast<const V*>(cp1 + i));
+                            xv[u] = ld_hint(reinterpret_cast<const V*>(cp0 + i), 2 * idx >= c_cnt ? pol_last : pol_first);
+                            if (has1)
+                                xv[4 + u] = ld_hint(reinterpret_cast<const V*>(cp1 + i), 2 * idx1 >= c_cnt ? pol_last : pol_first);
                         }
                     }
                     T a0 = T(0), a1 = T(0), q0 = T(0), q1 = T(0);
@@ -1173,13 +1199,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
                 }
                 // g = W(j_al:m_pad, l)^T v, eight 16-byte loads per lane in flight
                 const T* col = W + (int64_t)l * ldw;
+                const uint64_t pol = 2 * idx >= c_cnt ? pol_last : pol_first;
                 T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0), sq = T(0);
                 for (int i0 = j_al + lane * VN; i0 < m_pad; i0 += 8 * S) {
                     V xv[8];
 #pragma unroll
                     for (int u = 0; u < 8; ++u) {
                         const int i = i0 + u * S;
-                        if (i < m_pad) xv[u] = __ldcg(reinterpret_cast<const V*>(col + i));
+                        if (i < m_pad) xv[u] = ld_hint(reinterpret_cast<const V*>(col + i), pol);
                     }
                     if (exact_norms) {
 #pragma unroll
