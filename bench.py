@@ -14,7 +14,9 @@ tensor cores, CPQR of the 522 x 32768 sketch, FP64 solve; and under
 in one persistent launch; and under "latency", back-to-back 200 x 400 FP64
 IDs at k = 20; and under "differentiable", 256 IDs of 512 x 1024 at k = 64
 forward (batched) and backward; and under "sampled", the paper's
-column-sampling Optim RID of the headline matrices (p = 307 sampled columns)
+column-sampling Optim RID of the headline matrices (p = 307 sampled columns),
+and under "listing", the paper's listing outputs of the same matrices (Z from
+the normal equations, approx = C @ Z)
 (--only randomized / batched / latency / differentiable runs that workload
 alone; --only id skips them; --only sampled keeps the ID and the sampled RID).
 
@@ -396,6 +398,45 @@ def sampled_block(gbid, dev, steps, mats):
     return out
 
 
+def listing_block(gbid, dev, steps, mats):
+    """The paper's listing outputs on the headline matrices: Z from the normal
+    equations R_k^T R_k Z = C^T A (Eq. final_eq) instead of the back
+    substitution, and approx = C @ Z. ms per ID (normal-equation route), ms per
+    reconstruction, and the error of approx."""
+    import torch
+
+    out = {"workload": f"listing_{M}x{N}_k{K_RANK}"}
+    for name, A in mats.items():
+        ws = gbid.Workspace.for_problem(A.dtype, M, N, K_RANK, device=dev, normal_eq=True)
+        J = torch.empty(K_RANK, dtype=torch.int32, device=dev)
+        Z = torch.empty(K_RANK, N, dtype=A.dtype, device=dev)
+        approx = torch.empty(M, N, dtype=A.dtype, device=dev)
+        rws = gbid.Workspace(torch.empty(gbid.lib().id_reconstruct_workspace_size(gbid._DTYPES[A.dtype], M, N, K_RANK, 0),
+                                         dtype=torch.uint8, device=dev))
+        for _ in range(3):
+            gbid.id_decompose(A, K_RANK, normal_eq=True, workspace=ws, out=(J, Z), sync=False)
+            gbid.id_reconstruct(A, J, Z, out=approx, workspace=rws, sync=False)
+        torch.cuda.synchronize()
+        s = torch.cuda.current_stream()
+        ev = []
+        for _ in range(steps):
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            e[0].record(s)
+            gbid.id_decompose(A, K_RANK, normal_eq=True, workspace=ws, out=(J, Z), sync=False)
+            e[1].record(s)
+            gbid.id_reconstruct(A, J, Z, out=approx, workspace=rws, sync=False)
+            e[2].record(s)
+            ev.append(e)
+        torch.cuda.synchronize()
+        id_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in ev)
+        rc_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in ev)
+        info = gbid.read_info(ws)
+        err = (torch.linalg.norm(A.double() - approx.double()) / torch.linalg.norm(A.double())).item()
+        out[name] = {"id_ms": id_ms, "reconstruct_ms": rc_ms, "value": 1000.0 / (id_ms + rc_ms), "unit": UNIT,
+                     "status": info["status_name"], "rel_err": err}
+    return out
+
+
 BATCH_COUNT = 4096
 
 
@@ -664,6 +705,8 @@ def run_gbid(args):
 
     samp = sampled_block(gbid, dev, max(3, min(args.steps, 10)), {n: r["A"] for n, r in results.items()}) \
         if args.only in ("all", "sampled") else None
+    lst = listing_block(gbid, dev, max(3, min(args.steps, 10)), {n: r["A"] for n, r in results.items()}) \
+        if args.only in ("all", "sampled") else None
     rid = randomized_block(gbid, dev, max(2, min(args.steps, 5))) if args.only == "all" else None
     bat = batched_block(gbid, dev, max(3, min(args.steps, 10))) if args.only == "all" else None
     lat = latency_block(gbid, dev, args.steps) if args.only == "all" else None
@@ -702,6 +745,7 @@ def run_gbid(args):
         "solve_ms": {"f64": r64["solve_ms"], "f32": r32["solve_ms"]},
         "randomized": rid,
         "sampled": samp,
+        "listing": lst,
         "batched": bat,
         "latency": lat,
         "differentiable": dif,
@@ -720,8 +764,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only", default="all",
                     choices=["all", "id", "sampled", "randomized", "batched", "latency", "differentiable"],
-                    help="id: the 4096 x 8192 ID alone; sampled: the ID and the column-sampling RID of the same "
-                         "matrices; randomized / batched / latency / differentiable: that side workload alone")
+                    help="id: the 4096 x 8192 ID alone; sampled: the ID, the column-sampling RID and the paper's "
+                         "listing outputs (normal-equation Z, C @ Z) of the same matrices; randomized / batched / "
+                         "latency / differentiable: that side workload alone")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

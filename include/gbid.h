@@ -74,7 +74,15 @@ typedef struct {
      * shared memory (small problems: k <= 64, min(m, n) <= 1024, the matrix
      * within 8 CTAs' shared memory; ID_EINVAL if it does not fit). */
     int32_t engine;
-    int32_t reserved[5];
+    /* id_decompose only: how Z is formed from the k pivots. 0 (default) =
+     * Z P = [I  R11^{-1} R12], the back substitution with the CPQR's R;
+     * 1 = the paper's own route (Sec. 2.1, Eq. final_eq): the normal equations
+     * R_k^T R_k Z = C^T A with C = A[:, J], solved in FP64 (as
+     * id_decompose_sampled does). Equal in exact arithmetic; the normal
+     * equations carry cond(C)^2 instead of cond(C). Column IDs only (m <= n;
+     * ID_EINVAL otherwise) and the grid engine (engine 2 is ID_EINVAL). */
+    int32_t zsolve;
+    int32_t reserved[4];
 } id_opts;
 
 typedef struct {
@@ -332,6 +340,24 @@ int id_info_read(const void* work, id_info* info, void* stream);
 /* Number of kernel launches one id_decompose call enqueues for this problem
  * (memsets excluded). Returns -1 for invalid arguments. */
 int64_t id_launch_count(id_dtype dtype, int64_t m, int64_t n, int64_t k, const id_opts* opts);
+
+/* id_reconstruct -- the ID's approximation of A (the `approx = C @ Z` that
+ * the paper's listings return with the skeleton and Z, Sec. 2.1):
+ *   transposed = 0 (column ID, Z k x n): Out = A[:, J] Z   (m x n);
+ *   transposed = 1 (row ID of an m > n matrix, Z k x m): Out = Z^T A[J, :].
+ *   A    [in]  m x n row-major, n <= lda < 2^31, dtype (not modified).
+ *   J    [in]  k indices (columns of A, or rows when transposed).
+ *   Z    [in]  k x n (k x m when transposed) row-major, ldz >= that width, < 2^31.
+ *   Out  [out] m x n row-major, n <= ldo < 2^31.
+ *   work [in]  id_reconstruct_workspace_size() bytes, 256-byte aligned.
+ * The skeleton is gathered, then one GEMM: FP64 data in FP64, FP32 data in
+ * FP32-accurate products (cuBLAS, FP32 compute emulated on the BF16 tensor
+ * cores). info (HOST or NULL): status ID_EINVAL if a J entry is out of range
+ * (Out is then unspecified), else ID_OK. */
+size_t id_reconstruct_workspace_size(id_dtype dtype, int64_t m, int64_t n, int64_t k, int32_t transposed);
+int id_reconstruct(const void* A, id_dtype dtype, int64_t m, int64_t n, int64_t lda, int64_t k, const int32_t* J,
+                   const void* Z, int64_t ldz, int32_t transposed, void* Out, int64_t ldo, void* work,
+                   size_t work_bytes, id_info* info, void* stream);
 
 /* Kernel-class tracing. id_trace_enable(capacity > 0) creates `capacity`
  * CUDA event pairs; while enabled, every launch of the traced kernel classes

@@ -41,7 +41,7 @@ _DTYPES = {torch.float64: ID_F64, torch.float32: ID_F32}
 
 class IdOpts(ctypes.Structure):
     _fields_ = [("nb", ctypes.c_int32), ("refine", ctypes.c_int32), ("engine", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 5)]
+                ("zsolve", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
 
 
 class IdInfo(ctypes.Structure):
@@ -93,6 +93,9 @@ _SIG = {
     "id_batched_problem_workspace_size": (ctypes.c_size_t, [ctypes.c_int, _I64, _I64, _I64]),
     "id_decompose_batched": (ctypes.c_int, [_P, _I64, ctypes.c_int, _P, ctypes.c_size_t, _P, _P]),
     "id_sampled_workspace_size": (ctypes.c_size_t, [ctypes.c_int, _I64, _I64, _I64, _I64, _P]),
+    "id_reconstruct_workspace_size": (ctypes.c_size_t, [ctypes.c_int, _I64, _I64, _I64, ctypes.c_int32]),
+    "id_reconstruct": (ctypes.c_int, [_P, ctypes.c_int, _I64, _I64, _I64, _I64, _P, _P, _I64, ctypes.c_int32, _P, _I64,
+                                      _P, ctypes.c_size_t, _P, _P]),
     "id_decompose_sampled": (ctypes.c_int, [_P, ctypes.c_int, _I64, _I64, _I64, _P, _I64, _I64, _P, _P, _P, _I64, _P,
                                             ctypes.c_size_t, _P, _P]),
     "id_refine_workspace_size": (ctypes.c_size_t, [ctypes.c_int, _I64, _I64, _I64]),
@@ -129,11 +132,12 @@ def exported_symbols():
     return list(_SIG)
 
 
-def _opts(nb: int, refine: bool = True, engine: int = 0):
+def _opts(nb: int, refine: bool = True, engine: int = 0, zsolve: int = 0):
     o = IdOpts()
     o.nb = int(nb)
     o.refine = 0 if refine else -1
     o.engine = int(engine)
+    o.zsolve = int(zsolve)
     return o
 
 
@@ -161,8 +165,8 @@ class Workspace:
     buf: torch.Tensor
 
     @staticmethod
-    def for_problem(dtype, m, n, k, nb=0, device="cuda", host_io=False):
-        o = _opts(nb)
+    def for_problem(dtype, m, n, k, nb=0, device="cuda", host_io=False, normal_eq=False):
+        o = _opts(nb, zsolve=1 if normal_eq else 0)
         if host_io:
             nbytes = int(lib().id_decompose_host_workspace_size(_DTYPES[dtype], m, n, k, ctypes.byref(o)))
         else:
@@ -172,7 +176,7 @@ class Workspace:
         return Workspace(torch.empty(nbytes, dtype=torch.uint8, device=device))
 
 
-def id_decompose(A: torch.Tensor, k: int, *, nb: int = 0, engine: int = ENGINE_AUTO,
+def id_decompose(A: torch.Tensor, k: int, *, nb: int = 0, engine: int = ENGINE_AUTO, normal_eq: bool = False,
                  workspace: Workspace | None = None, out: tuple | None = None, sync: bool = True):
     """Rank-k ID of a CUDA matrix A (m x n, row-major, float32/float64).
 
@@ -181,20 +185,22 @@ def id_decompose(A: torch.Tensor, k: int, *, nb: int = 0, engine: int = ENGINE_A
     With sync=False nothing waits for the GPU (usable inside CUDA-graph capture);
     read the status later with ``read_info(workspace)``. engine: ENGINE_AUTO
     (small problems on one thread-block cluster, others on the persistent grid),
-    ENGINE_GRID or ENGINE_CLUSTER.
+    ENGINE_GRID or ENGINE_CLUSTER. normal_eq: Z from the paper's normal
+    equations R_k^T R_k Z = C^T A (column IDs, grid engine) instead of the back
+    substitution with R.
     """
     _check_cuda_matrix(A, "A")
     m, n = A.shape
     nz = max(m, n)
     dev = A.device
     if workspace is None:
-        workspace = Workspace.for_problem(A.dtype, m, n, k, nb, dev)
+        workspace = Workspace.for_problem(A.dtype, m, n, k, nb, dev, normal_eq=normal_eq)
     if out is None:
         J = torch.empty(k, dtype=torch.int32, device=dev)
         Z = torch.empty(k, nz, dtype=A.dtype, device=dev)
     else:
         J, Z = out
-    o = _opts(nb, engine=engine)
+    o = _opts(nb, engine=engine, zsolve=1 if normal_eq else 0)
     info = IdInfo()
     with torch.cuda.device(dev):
         rc = lib().id_decompose(A.data_ptr(), _DTYPES[A.dtype], m, n, A.stride(0), k, ctypes.byref(o),
@@ -328,6 +334,32 @@ def id_decompose_sampled(A: torch.Tensor, idx, k: int, *, nb: int = 0, workspace
     if rc in _CALL_ERRORS:
         raise IdError(rc, "id_decompose_sampled")
     return J, Z, (info.as_dict() if sync else None)
+
+
+def id_reconstruct(A: torch.Tensor, J: torch.Tensor, Z: torch.Tensor, *, transposed: bool = False,
+                   out: torch.Tensor | None = None, workspace: Workspace | None = None, sync: bool = True):
+    """The ID's approximation of A: A[:, J] @ Z (column ID), or Z.T @ A[J, :]
+    (row ID of an m > n matrix, transposed=True). Returns (approx, info)."""
+    _check_cuda_matrix(A, "A")
+    _check_cuda_matrix(Z, "Z")
+    m, n = A.shape
+    k = J.numel()
+    dev = A.device
+    dt = _DTYPES[A.dtype]
+    if workspace is None:
+        nbytes = int(lib().id_reconstruct_workspace_size(dt, m, n, k, 1 if transposed else 0))
+        if nbytes == 0:
+            raise IdError(ID_EINVAL, "id_reconstruct_workspace_size")
+        workspace = Workspace(torch.empty(nbytes, dtype=torch.uint8, device=dev))
+    Out = torch.empty(m, n, dtype=A.dtype, device=dev) if out is None else out
+    info = IdInfo()
+    with torch.cuda.device(dev):
+        rc = lib().id_reconstruct(A.data_ptr(), dt, m, n, A.stride(0), k, J.data_ptr(), Z.data_ptr(), Z.stride(0),
+                                  1 if transposed else 0, Out.data_ptr(), Out.stride(0), workspace.buf.data_ptr(),
+                                  workspace.buf.numel(), ctypes.byref(info) if sync else None, _stream(dev))
+    if rc in _CALL_ERRORS or (sync and info.status == ID_EINVAL):
+        raise IdError(ID_EINVAL if rc == 0 else rc, "id_reconstruct")
+    return Out, (info.as_dict() if sync else None)
 
 
 def id_refine(A: torch.Tensor, J: torch.Tensor, Z: torch.Tensor, *, workspace: Workspace | None = None,

@@ -131,13 +131,16 @@ int read_info(const void* work, id_info* info, cudaStream_t s) {
     return info->status;
 }
 
+// The normal-equation route to Z (opts->zsolve = 1): column IDs on the grid engine.
+int zsolve_of(const id_opts* opts) { return opts ? opts->zsolve : 0; }
+
 // Engine choice: the cluster kernel when asked for, or by default when the
 // problem fits it (the persistent grid kernel pays grid-wide barriers and L2
 // round trips every step, which dominate small problems).
 template <typename T>
 bool use_cluster(int64_t m, int64_t n, int64_t k, const id_opts* opts) {
     const int eng = opts ? opts->engine : 0;
-    if (eng == 1) return false;
+    if (eng == 1 || zsolve_of(opts) == 1) return false;
     // FP64 arithmetic runs at 2 lanes per clock per SM on this GPU: by default an
     // FP64 problem takes the cluster only when a 16-CTA cluster can hold it
     // (200 x 400, k = 20: 361 us on 16 CTAs, 539 us on 8, 524 us on the grid).
@@ -149,6 +152,8 @@ bool use_cluster(int64_t m, int64_t n, int64_t k, const id_opts* opts) {
 bool engine_ok(id_dtype dt, int64_t m, int64_t n, int64_t k, const id_opts* opts) {
     const int eng = opts ? opts->engine : 0;
     if (eng < 0 || eng > 2) return false;
+    const int zs = zsolve_of(opts);
+    if (zs < 0 || zs > 1 || (zs == 1 && (m > n || eng == 2))) return false;
     if (eng == 2) return (dt == ID_F64 ? cluster_size<double>(m, n, k) : cluster_size<float>(m, n, k)) > 0;
     return true;
 }
@@ -160,7 +165,8 @@ int decompose_impl(const void* A, int64_t m, int64_t n, int64_t lda, int64_t k, 
     const int mx = (int)(trans ? n : m), nx = (int)(trans ? m : n);
     const id_dtype dt = sizeof(T) == 8 ? ID_F64 : ID_F32;
     const Layout L = make_layout(dt, mx, nx, (int)k, opts, true, true);
-    if (work_bytes < L.total) return ID_ENOMEM;
+    const bool zs = zsolve_of(opts) == 1;
+    if (work_bytes < L.total + (zs ? sampled_z_bytes(m, n, k) : 0)) return ID_ENOMEM;
     if (configure_once()) return ID_ECUDA;
     char* base = static_cast<char*>(work);
     if (use_cluster<T>(m, n, k, opts)) {
@@ -175,6 +181,14 @@ int decompose_impl(const void* A, int64_t m, int64_t n, int64_t lda, int64_t k, 
     if (cudaMemsetAsync(dinfo, 0, sizeof(DevInfo), s) != cudaSuccess) return ID_ECUDA;
     if (copy_in<T>(A, lda, trans, P, s) != cudaSuccess) return ID_ECUDA;
     if (cpqr_run<T>(P, s) != cudaSuccess) return ID_ECUDA;
+    if (zs) {   // the paper's route: J = P_k, then R_k^T R_k Z = C^T A against A (m <= n here)
+        if (finalize_info(P.st, dinfo, (int)k, 0, P.nb, s) != cudaSuccess) return ID_ECUDA;
+        if (sample_map_j(P.perm, nullptr, (int)k, J, s) != cudaSuccess) return ID_ECUDA;
+        const int rc = sampled_z_run<T>(A, m, n, lda, (int)k, J, P.W, P.ldw, Z, ldz, base + L.total, dinfo, s);
+        if (rc != ID_OK) return rc;
+        if (info) return read_info(work, info, s);
+        return ID_OK;
+    }
     double* Tm = reinterpret_cast<double*>(base + L.T);
     const int ldt = nx - (int)k > 0 ? nx - (int)k : 1;
     if (solve_run<T>(P.W, P.ldw, (int)k, nx, Tm, ldt, s) != cudaSuccess) return ID_ECUDA;
@@ -231,8 +245,10 @@ size_t id_cpqr_workspace_size(id_dtype dtype, int64_t m, int64_t n, int64_t ldx,
 
 size_t id_workspace_size(id_dtype dtype, int64_t m, int64_t n, int64_t k, const id_opts* opts) {
     if ((dtype != ID_F64 && dtype != ID_F32) || !sizes_ok(m, n, k)) return 0;
+    const int zs = zsolve_of(opts);
+    if (zs < 0 || zs > 1 || (zs == 1 && m > n)) return 0;
     const int mx = (int)(m > n ? n : m), nx = (int)(m > n ? m : n);
-    return make_layout(dtype, mx, nx, (int)k, opts, true, true).total;
+    return make_layout(dtype, mx, nx, (int)k, opts, true, true).total + (zs ? sampled_z_bytes(m, n, k) : 0);
 }
 
 int id_decompose(const void* A, id_dtype dtype, int64_t m, int64_t n, int64_t lda, int64_t k, const id_opts* opts,
@@ -245,6 +261,7 @@ int id_decompose(const void* A, id_dtype dtype, int64_t m, int64_t n, int64_t ld
     if (!aligned(work, 256)) return ID_EINVAL;
     if (opts && opts->nb < 0) return ID_EINVAL;
     if (!engine_ok(dtype, m, n, k, opts)) return ID_EINVAL;
+    if (zsolve_of(opts) == 1 && (lda > INT32_MAX || ldz > INT32_MAX)) return ID_EINVAL;   // the FP64 GEMMs' ints
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (dtype == ID_F64) return decompose_impl<double>(A, m, n, lda, k, opts, J, Z, ldz, work, work_bytes, info, s);
     return decompose_impl<float>(A, m, n, lda, k, opts, J, Z, ldz, work, work_bytes, info, s);
@@ -513,11 +530,40 @@ int id_info_read(const void* work, id_info* info, void* stream) {
 
 int64_t id_launch_count(id_dtype dtype, int64_t m, int64_t n, int64_t k, const id_opts* opts) {
     if ((dtype != ID_F64 && dtype != ID_F32) || !sizes_ok(m, n, k) || !engine_ok(dtype, m, n, k, opts)) return -1;
+    if (zsolve_of(opts) == 1) return -1;   // not counted: the launches depend on k and include cuBLAS
     const bool cl = dtype == ID_F64 ? use_cluster<double>(m, n, k, opts) : use_cluster<float>(m, n, k, opts);
     if (cl) return 2;   // the cluster kernel and its statistics kernel
     const int64_t nx = m > n ? m : n;
     // copy-in, persistent CPQR, back substitution (when n > k), Z scatter, status
     return 4 + (nx > k ? 1 : 0);
+}
+
+size_t id_reconstruct_workspace_size(id_dtype dtype, int64_t m, int64_t n, int64_t k, int32_t transposed) {
+    if (dtype != ID_F64 && dtype != ID_F32) return 0;
+    if (m < 1 || n < 1 || k < 1 || k > (transposed ? m : n) || m > INT32_MAX || n > INT32_MAX) return 0;
+    if (transposed != 0 && transposed != 1) return 0;
+    return align_up(sizeof(DevInfo)) + reconstruct_bytes(m, n, k, transposed, dtype == ID_F64 ? 8 : 4);
+}
+
+int id_reconstruct(const void* A, id_dtype dtype, int64_t m, int64_t n, int64_t lda, int64_t k, const int32_t* J,
+                   const void* Z, int64_t ldz, int32_t transposed, void* Out, int64_t ldo, void* work,
+                   size_t work_bytes, id_info* info, void* stream) {
+    if (!A || !J || !Z || !Out || !work) return ID_EINVAL;
+    const size_t need = id_reconstruct_workspace_size(dtype, m, n, k, transposed);
+    if (need == 0) return ID_EINVAL;
+    const int64_t zw = transposed ? m : n;
+    if (lda < n || ldo < n || ldz < zw || lda > INT32_MAX || ldo > INT32_MAX || ldz > INT32_MAX) return ID_EINVAL;
+    if (!aligned(work, 256)) return ID_EINVAL;
+    if (work_bytes < need) return ID_ENOMEM;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    DevInfo* dinfo = reinterpret_cast<DevInfo*>(work);
+    void* rws = static_cast<char*>(work) + align_up(sizeof(DevInfo));
+    const int rc = dtype == ID_F64
+                       ? reconstruct_run<double>(A, m, n, lda, (int)k, J, Z, ldz, transposed, Out, ldo, rws, dinfo, s)
+                       : reconstruct_run<float>(A, m, n, lda, (int)k, J, Z, ldz, transposed, Out, ldo, rws, dinfo, s);
+    if (rc != ID_OK) return rc;
+    if (info) return read_info(work, info, s);
+    return ID_OK;
 }
 
 int id_trace_enable(int capacity) { return trace_enable(capacity) == 0 ? ID_OK : ID_ECUDA; }

@@ -78,6 +78,11 @@ cudaError_t sample_gather_run(const void* A, int64_t lda, int m, const int32_t* 
                               cudaStream_t s);
 cudaError_t sample_map_j(const int* perm, const int32_t* idx, int k, int32_t* J, cudaStream_t s);
 size_t sampled_z_bytes(int64_t m, int64_t n, int64_t k);
+// The ID's approximation A[:, J] Z (rows = 0) or Z^T A[J, :] (rows = 1), refine.cu.
+size_t reconstruct_bytes(int64_t m, int64_t n, int64_t k, int rows, size_t elem);
+template <typename T>
+int reconstruct_run(const void* A, int64_t m, int64_t n, int64_t lda, int k, const int32_t* J, const void* Z,
+                    int64_t ldz, int rows, void* Out, int64_t ldo, void* ws, DevInfo* dinfo, cudaStream_t s);
 template <typename T>
 int sampled_z_run(const void* A, int64_t m, int64_t n, int64_t lda, int k, const int32_t* J, const void* W, int ldw,
                   void* Z, int64_t ldz, void* ws, DevInfo* dinfo, cudaStream_t s);

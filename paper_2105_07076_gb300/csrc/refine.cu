@@ -448,8 +448,10 @@ __global__ void k_gather_sample(const T* __restrict__ A, int64_t lda, int m, con
     }
 }
 
+// J = idx[perm[0:k]] (idx == nullptr: J = perm[0:k], the pivots themselves)
 __global__ void k_map_j(const int* __restrict__ perm, const int32_t* __restrict__ idx, int k, int32_t* J) {
-    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < k; l += gridDim.x * blockDim.x) J[l] = idx[perm[l]];
+    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < k; l += gridDim.x * blockDim.x)
+        J[l] = idx ? idx[perm[l]] : perm[l];
 }
 
 template <typename T>
@@ -733,6 +735,88 @@ int backward_run(const float* A, int64_t m, int64_t n, int64_t lda, int k, const
     trace_end(tr, s);
     return cudaGetLastError() == cudaSuccess ? ID_OK : ID_ECUDA;
 }
+
+// ------------------------------------------------------ reconstruction C Z --
+// S = A[:, J] (m x k row-major) or, for a row ID, S = A[J, :] (k x n
+// row-major). An index outside its range sets flag[0] = 2 and gathers zeros.
+template <typename T>
+__global__ void k_gather_skel(const T* __restrict__ A, int64_t lda, int m, int n, int k, const int32_t* __restrict__ J,
+                              int rows, T* __restrict__ S, int* flag) {
+    const int64_t total = rows ? (int64_t)k * n : (int64_t)m * k;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        if (rows) {
+            const int c = (int)(e / n), l = (int)(e % n);
+            const int r = J[c];
+            const bool ok = r >= 0 && r < m;
+            if (!ok && l == 0) flag[0] = 2;
+            S[e] = ok ? A[(int64_t)r * lda + l] : T(0);
+        } else {
+            const int64_t i = e / k;
+            const int c = (int)(e % k);
+            const int l = J[c];
+            const bool ok = l >= 0 && l < n;
+            if (!ok && i == 0) flag[0] = 2;
+            S[e] = ok ? A[i * lda + l] : T(0);
+        }
+    }
+}
+
+__global__ void k_recon_finalize(DevInfo* info, const int* flag) {
+    id_info r = {};
+    r.status = flag[0] == 2 ? ID_EINVAL : ID_OK;
+    info->info = r;
+}
+
+size_t reconstruct_bytes(int64_t m, int64_t n, int64_t k, int rows, size_t s) {
+    return al(16) + al(s * (size_t)k * (size_t)(rows ? n : m)) + kCublasWs;
+}
+
+template <typename T>
+int reconstruct_run(const void* Av, int64_t m, int64_t n, int64_t lda, int k, const int32_t* J, const void* Zv,
+                    int64_t ldz, int rows, void* Outv, int64_t ldo, void* ws, DevInfo* dinfo, cudaStream_t s) {
+    char* base = static_cast<char*>(ws);
+    int* flag = reinterpret_cast<int*>(base);
+    T* S = reinterpret_cast<T*>(base + al(16));
+    char* cws = base + al(16) + al(sizeof(T) * (size_t)k * (size_t)(rows ? n : m));
+    cublasHandle_t h = cublas_handle();
+    if (!h) return ID_ECUDA;
+    std::lock_guard<std::mutex> lk(g_cb_mu);
+    if (cublasSetStream(h, s) != CUBLAS_STATUS_SUCCESS) return ID_ECUDA;
+    if (cublasSetWorkspace(h, cws, kCublasWs) != CUBLAS_STATUS_SUCCESS) return ID_ECUDA;
+    if (cudaMemsetAsync(flag, 0, 16, s) != cudaSuccess) return ID_ECUDA;
+    const T* A = static_cast<const T*>(Av);
+    k_gather_skel<T><<<grid_for(rows ? (int64_t)k * n : m * k), kRThreads, 0, s>>>(A, lda, (int)m, (int)n, k, J, rows,
+                                                                                  S, flag);
+    // Column-major views of the row-major arrays. Column ID: Out^T (n x m) =
+    // Z^T (n x k, ld ldz) S^T (k x m, ld k). Row ID: Out^T (n x m) = S^T (n x k,
+    // ld n) Z (k x m), Z^T being the column-major (m x k, ld ldz) view.
+    const int M = (int)n, N = (int)m;
+    bool ok;
+    if (sizeof(T) == 8) {
+        const double one = 1.0, zero = 0.0;
+        const double* Z = static_cast<const double*>(Zv);
+        const double* Sd = reinterpret_cast<const double*>(S);
+        double* Out = static_cast<double*>(Outv);
+        ok = (rows ? cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_T, M, N, k, &one, Sd, (int)n, Z, (int)ldz, &zero, Out,
+                                 (int)ldo)
+                   : cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, M, N, k, &one, Z, (int)ldz, Sd, k, &zero, Out,
+                                 (int)ldo)) == CUBLAS_STATUS_SUCCESS;
+    } else {
+        const float* Z = static_cast<const float*>(Zv);
+        const float* Sf = reinterpret_cast<const float*>(S);
+        float* Out = static_cast<float*>(Outv);
+        ok = rows ? sgemm(h, CUBLAS_OP_N, CUBLAS_OP_T, M, N, k, 1.0f, Sf, (int)n, Z, (int)ldz, 0.0f, Out, (int)ldo)
+                  : sgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, M, N, k, 1.0f, Z, (int)ldz, Sf, k, 0.0f, Out, (int)ldo);
+    }
+    if (!ok) return ID_ECUDA;
+    k_recon_finalize<<<1, 1, 0, s>>>(dinfo, flag);
+    return cudaGetLastError() == cudaSuccess ? ID_OK : ID_ECUDA;
+}
+
+template int reconstruct_run<double>(const void*, int64_t, int64_t, int64_t, int, const int32_t*, const void*, int64_t,
+                                     int, void*, int64_t, void*, DevInfo*, cudaStream_t);
+template int reconstruct_run<float>(const void*, int64_t, int64_t, int64_t, int, const int32_t*, const void*, int64_t,
+                                    int, void*, int64_t, void*, DevInfo*, cudaStream_t);
 
 // ------------------------------------------------ column-sampling Optim RID --
 struct SampLayout {

@@ -147,6 +147,45 @@ def test_sampled_rules(gbid):
     assert call([0, 1, 2, 3], work_bytes=64) == gbid.ID_ENOMEM
 
 
+def test_normal_equation_route_rules(gbid):
+    """opts.zsolve = 1 (the paper's normal-equation Z): column IDs on the grid engine only."""
+    L = gbid.lib()
+    fake = ctypes.c_void_p(256)
+    base = L.id_workspace_size(0, 300, 700, 40, None)
+    ne = gbid._opts(0, zsolve=1)
+    assert L.id_workspace_size(0, 300, 700, 40, ctypes.byref(ne)) > base
+    assert L.id_workspace_size(0, 700, 300, 40, ctypes.byref(ne)) == 0       # a row ID
+    bad = gbid._opts(0, zsolve=2)
+    assert L.id_workspace_size(0, 300, 700, 40, ctypes.byref(bad)) == 0
+    cl = gbid._opts(0, engine=gbid.ENGINE_CLUSTER, zsolve=1)
+    assert L.id_decompose(fake, 0, 200, 400, 400, 20, ctypes.byref(cl), fake, fake, 400, fake, 1 << 30, None,
+                          None) == gbid.ID_EINVAL
+    assert L.id_decompose(fake, 0, 400, 200, 200, 20, ctypes.byref(ne), fake, fake, 400, fake, 1 << 30, None,
+                          None) == gbid.ID_EINVAL
+    assert L.id_launch_count(0, 300, 700, 40, ctypes.byref(ne)) == -1
+
+
+def test_reconstruct_rules(gbid):
+    L = gbid.lib()
+    fake = ctypes.c_void_p(256)
+    assert L.id_reconstruct_workspace_size(0, 300, 700, 40, 0) >= 300 * 40 * 8
+    assert L.id_reconstruct_workspace_size(1, 700, 300, 40, 1) >= 40 * 300 * 4
+    assert L.id_reconstruct_workspace_size(0, 300, 700, 701, 0) == 0        # k > n
+    assert L.id_reconstruct_workspace_size(0, 30, 700, 31, 1) == 0          # k > m for a row ID
+    assert L.id_reconstruct_workspace_size(0, 300, 700, 40, 2) == 0
+    assert L.id_reconstruct_workspace_size(2, 300, 700, 40, 0) == 0
+
+    def call(lda=700, ldz=700, ldo=700, tr=0, work_bytes=1 << 30, A=fake):
+        return L.id_reconstruct(A, 0, 300, 700, lda, 40, fake, fake, ldz, tr, fake, ldo, fake, work_bytes, None, None)
+
+    assert call(A=None) == gbid.ID_EINVAL
+    assert call(lda=699) == gbid.ID_EINVAL
+    assert call(ldo=699) == gbid.ID_EINVAL
+    assert call(ldz=699) == gbid.ID_EINVAL
+    assert call(tr=1, ldz=299) == gbid.ID_EINVAL      # a row ID's Z is k x m
+    assert call(work_bytes=64) == gbid.ID_ENOMEM
+
+
 def test_batched_workspace_rules(gbid):
     L = gbid.lib()
     assert L.id_batched_problem_workspace_size(1, 100, 300, 20) >= 100 * 300 * 4 + 300 * 4
