@@ -24,6 +24,8 @@ Interpolative Decomposition", arXiv 2105.07076):
   pivots and R_11, R_12 do not depend on later steps.
 * Sec. 2.2: the least-squares target min ||A - C Z||_F for a fixed skeleton set,
   used by the randomized variant (``ls_interp``) and by the refinement of T.
+* Sec. 1.2 footnote: the two-sided ID X^T A[I, J] Z, built from a column ID and
+  a row ID of its skeleton (``two_sided_interp_decomp``).
 
 Readings where the paper is silent (each listed again in the design doc):
 * pivot = column of largest residual 2-norm over the not-yet-chosen columns;
@@ -281,6 +283,45 @@ def sampled_interp_decomp(A: np.ndarray, idx: np.ndarray, k: int):
     R = np.triu(f["F"][:k, :k])
     Z = normal_equation_z(A, J, R)
     return J, Z, {"perm": f["perm"], "R": R, "rank": f["rank"], "gap": f["gap"]}
+
+
+def two_sided_interp_decomp(A: np.ndarray, k: int):
+    """Two-sided ID A ~= X^T A[I, J] Z, the variant of Cheng et al. that the
+    footnote of Sec. 1.2 names.
+
+    m <= n: the column ID (J, Z) of A (Sec. 2.1), then a row ID (I, X) of the
+    skeleton C = A[:, J] (the Sec. 2 footnote's m > n route on an m x k
+    matrix). m > n: the roles swap, a row ID (I, X) of A, then the column ID
+    (J, Z) of R = A[I, :]. A rank-k m x k (k x n) skeleton has an exact k-row
+    (k-column) ID, so in exact arithmetic the second stage adds no error:
+    X^T C[I, :] = C. A stage whose matrix is already k x k keeps every row
+    (column): the identity. Returns (I, J, X, Z); X is k x m, Z is k x n.
+    """
+    A = np.asarray(A, dtype=np.float64)
+    m, n = A.shape
+    if not (1 <= k <= min(m, n)):
+        raise ValueError("need 1 <= k <= min(m, n)")
+    if m <= n:
+        J, Z, _ = interp_decomp(A, k)
+        C = A[:, J]
+        if m == k:
+            I, X = np.arange(k), np.eye(k)
+        else:
+            I, X, _ = interp_decomp(C, k)          # m > k: a row ID of C
+    else:
+        I, X, _ = interp_decomp(A, k)              # m > n: a row ID of A
+        R = A[I, :]
+        if n == k:
+            J, Z = np.arange(k), np.eye(k)
+        else:
+            J, Z, _ = interp_decomp(R, k)          # k < n: a column ID of R
+    return I, J, X, Z
+
+
+def two_sided_reconstruct(A: np.ndarray, I: np.ndarray, J: np.ndarray, X: np.ndarray, Z: np.ndarray) -> np.ndarray:
+    """X^T A[I, J] Z."""
+    A = np.asarray(A, dtype=np.float64)
+    return X.T @ A[np.ix_(I, J)] @ Z
 
 
 def randomized_interp_decomp(A: np.ndarray, omega: np.ndarray, k: int):

@@ -332,6 +332,47 @@ def test_sampled_rid_properties():
         orc.sampled_interp_decomp(A, np.array([1, 1, 2]), 2)
 
 
+# ---------------------------------------------------------------- two-sided ---
+@pytest.mark.parametrize("m,n", [(60, 140), (140, 60), (80, 80)])
+def test_two_sided_exact_rank(m, n):
+    """Rank k exactly: X^T A[I, J] Z reproduces A."""
+    k = 12
+    s = np.where(np.arange(min(m, n)) < k, np.exp(-np.arange(min(m, n)) / 4.0), 0.0)
+    A = synth.lowrank(m, n, s, 8).numpy()
+    I, J, X, Z = orc.two_sided_interp_decomp(A, k)
+    assert X.shape == (k, m) and Z.shape == (k, n)
+    err = np.linalg.norm(A - orc.two_sided_reconstruct(A, I, J, X, Z)) / np.linalg.norm(A)
+    assert err <= 1e-12
+
+
+@pytest.mark.parametrize("m,n", [(60, 140), (140, 60)])
+def test_two_sided_error_is_the_one_sided_error(m, n):
+    """The second stage is exact in exact arithmetic, so the two-sided error
+    equals the first stage's ID error; X[:, I] and Z[:, J] are identities."""
+    k = 15
+    A = synth.lowrank(m, n, np.exp(-np.arange(min(m, n)) / 6.0), 9).numpy()
+    I, J, X, Z = orc.two_sided_interp_decomp(A, k)
+    assert np.array_equal(X[:, I], np.eye(k)) and np.array_equal(Z[:, J], np.eye(k))
+    e2 = np.linalg.norm(A - orc.two_sided_reconstruct(A, I, J, X, Z)) / np.linalg.norm(A)
+    if m <= n:
+        e1 = orc.rel_error(A, J, Z)
+    else:
+        e1 = orc.rel_error(A, I, X, transposed=True)
+    assert abs(e2 - e1) <= 1e-10 * e1
+    # never below the Eckart-Young floor
+    assert e2 >= np.sqrt(np.sum(np.exp(-np.arange(k, min(m, n)) / 3.0)) / np.sum(np.exp(-np.arange(min(m, n)) / 3.0))) * (1 - 1e-9)
+
+
+def test_two_sided_transpose_symmetry():
+    """The two-sided ID of A^T is that of A with the roles of (I, X) and (J, Z) swapped."""
+    k = 10
+    A = synth.lowrank(50, 120, np.exp(-np.arange(50) / 5.0), 10).numpy()
+    I, J, X, Z = orc.two_sided_interp_decomp(A, k)
+    It, Jt, Xt, Zt = orc.two_sided_interp_decomp(A.T.copy(), k)
+    assert np.array_equal(It, J) and np.array_equal(Jt, I)
+    assert np.allclose(Xt, Z, atol=1e-12) and np.allclose(Zt, X, atol=1e-12)
+
+
 # ----------------------------------------------------------------- gradient ---
 def test_gradient_matches_central_differences():
     rng = np.random.default_rng(17)
