@@ -15,8 +15,9 @@ in one persistent launch; and under "latency", back-to-back 200 x 400 FP64
 IDs at k = 20; and under "differentiable", 256 IDs of 512 x 1024 at k = 64
 forward (batched) and backward; and under "sampled", the paper's
 column-sampling Optim RID of the headline matrices (p = 307 sampled columns),
-and under "listing", the paper's listing outputs of the same matrices (Z from
-the normal equations, approx = C @ Z)
+under "listing", the paper's listing outputs of the same matrices (Z from
+the normal equations, approx = C @ Z), and under "two_sided", the two-sided ID
+of the same matrices and the row ID of the 8192 x 4096 transpose
 (--only randomized / batched / latency / differentiable runs that workload
 alone; --only id skips them; --only sampled keeps the ID and the sampled RID).
 
@@ -437,6 +438,55 @@ def listing_block(gbid, dev, steps, mats):
     return out
 
 
+def two_sided_block(gbid, dev, steps, mats):
+    """The two-sided ID X^T A[I, J] Z (Sec. 1.2 footnote) of the headline
+    matrices, and the row ID at scale: the 8192 x 4096 transpose of the FP64
+    matrix (the m > n route), whose pivots and Z must equal the column ID's."""
+    import torch
+
+    out = {"workload": f"two_sided_{M}x{N}_k{K_RANK}; row_id_{N}x{M}_k{K_RANK}"}
+    s = torch.cuda.current_stream()
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        ev = []
+        for _ in range(steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            fn()
+            e1.record(s)
+            ev.append((e0, e1))
+        torch.cuda.synchronize()
+        return statistics.mean(a.elapsed_time(b) for a, b in ev)
+
+    for name, A in mats.items():
+        ws = gbid.two_sided_workspace(A.dtype, M, N, K_RANK, device=dev)
+        I = torch.empty(K_RANK, dtype=torch.int32, device=dev)
+        J = torch.empty(K_RANK, dtype=torch.int32, device=dev)
+        X = torch.empty(K_RANK, M, dtype=A.dtype, device=dev)
+        Z = torch.empty(K_RANK, N, dtype=A.dtype, device=dev)
+        ms = timed(lambda: gbid.id_decompose_two_sided(A, K_RANK, workspace=ws, out=(I, J, X, Z), sync=False))
+        _, _, _, _, infos = gbid.id_decompose_two_sided(A, K_RANK, workspace=ws, out=(I, J, X, Z))
+        A64 = A.double()
+        approx = X.double().T @ A64[I.long()][:, J.long()] @ Z.double()
+        err = (torch.linalg.norm(A64 - approx) / torch.linalg.norm(A64)).item()
+        out[name] = {"ms_per_step": ms, "value": 1000.0 / ms, "unit": UNIT, "rel_err": err,
+                     "status": [i["status_name"] for i in infos]}
+    At = mats["f64"].T.contiguous()
+    ws = gbid.Workspace.for_problem(At.dtype, N, M, K_RANK, device=dev)
+    Jr = torch.empty(K_RANK, dtype=torch.int32, device=dev)
+    Zr = torch.empty(K_RANK, N, dtype=At.dtype, device=dev)
+    ms = timed(lambda: gbid.id_decompose(At, K_RANK, workspace=ws, out=(Jr, Zr), sync=False))
+    info = gbid.read_info(ws)
+    out["row_id_f64"] = {"ms_per_step": ms, "value": 1000.0 / ms, "unit": UNIT, "status": info["status_name"],
+                         "transposed": info["transposed"]}
+    del At
+    return out
+
+
 BATCH_COUNT = 4096
 
 
@@ -707,6 +757,8 @@ def run_gbid(args):
         if args.only in ("all", "sampled") else None
     lst = listing_block(gbid, dev, max(3, min(args.steps, 10)), {n: r["A"] for n, r in results.items()}) \
         if args.only in ("all", "sampled") else None
+    two = two_sided_block(gbid, dev, max(3, min(args.steps, 10)), {n: r["A"] for n, r in results.items()}) \
+        if args.only in ("all", "sampled") else None
     rid = randomized_block(gbid, dev, max(2, min(args.steps, 5))) if args.only == "all" else None
     bat = batched_block(gbid, dev, max(3, min(args.steps, 10))) if args.only == "all" else None
     lat = latency_block(gbid, dev, args.steps) if args.only == "all" else None
@@ -746,6 +798,7 @@ def run_gbid(args):
         "randomized": rid,
         "sampled": samp,
         "listing": lst,
+        "two_sided": two,
         "batched": bat,
         "latency": lat,
         "differentiable": dif,

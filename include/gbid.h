@@ -359,6 +359,26 @@ int id_reconstruct(const void* A, id_dtype dtype, int64_t m, int64_t n, int64_t 
                    const void* Z, int64_t ldz, int32_t transposed, void* Out, int64_t ldo, void* work,
                    size_t work_bytes, id_info* info, void* stream);
 
+/* id_decompose_two_sided -- rank-k two-sided ID A ~= X^T A[I, J] Z, the
+ * variant (Cheng et al.) that the footnote of Sec. 1.2 names. For m <= n:
+ * the column ID (J, Z) of A (Sec. 2.1), then the row ID (I, X) of the
+ * skeleton C = A[:, J] (the m > n route of the Sec. 2 footnote on an m x k
+ * matrix). For m > n the roles swap: the row ID (I, X) of A, then the
+ * column ID (J, Z) of R = A[I, :]. A stage on a k x k matrix keeps all rows
+ * (columns): the identity. In exact arithmetic the second stage adds no
+ * error (X^T C[I, :] = C for a rank-k C).
+ *   A    [in]  m x n row-major, lda >= n, dtype (not modified).
+ *   I    [out] k row indices; X [out] k x m row-major (ldx >= m), X[:, I] = I.
+ *   J    [out] k column indices; Z [out] k x n row-major (ldz >= n), Z[:, J] = I.
+ *   opts       stage 1's options (nb, engine; zsolve must be 0); stage 2 uses defaults.
+ *   work [in]  id_two_sided_workspace_size() bytes, 256-byte aligned.
+ *   info [out] HOST array of TWO id_info (stage 1, then stage 2), or NULL.
+ * Returns as id_decompose; with info, the first non-OK stage status. */
+size_t id_two_sided_workspace_size(id_dtype dtype, int64_t m, int64_t n, int64_t k, const id_opts* opts);
+int id_decompose_two_sided(const void* A, id_dtype dtype, int64_t m, int64_t n, int64_t lda, int64_t k,
+                           const id_opts* opts, int32_t* I, int32_t* J, void* X, int64_t ldx, void* Z, int64_t ldz,
+                           void* work, size_t work_bytes, id_info* info, void* stream);
+
 /* Kernel-class tracing. id_trace_enable(capacity > 0) creates `capacity`
  * CUDA event pairs; while enabled, every launch of the traced kernel classes
  * (until the pairs are used up) is bracketed by an event pair recorded on the

@@ -94,6 +94,9 @@ _SIG = {
     "id_decompose_batched": (ctypes.c_int, [_P, _I64, ctypes.c_int, _P, ctypes.c_size_t, _P, _P]),
     "id_sampled_workspace_size": (ctypes.c_size_t, [ctypes.c_int, _I64, _I64, _I64, _I64, _P]),
     "id_reconstruct_workspace_size": (ctypes.c_size_t, [ctypes.c_int, _I64, _I64, _I64, ctypes.c_int32]),
+    "id_two_sided_workspace_size": (ctypes.c_size_t, [ctypes.c_int, _I64, _I64, _I64, _P]),
+    "id_decompose_two_sided": (ctypes.c_int, [_P, ctypes.c_int, _I64, _I64, _I64, _I64, _P, _P, _P, _P, _I64, _P, _I64,
+                                              _P, ctypes.c_size_t, _P, _P]),
     "id_reconstruct": (ctypes.c_int, [_P, ctypes.c_int, _I64, _I64, _I64, _I64, _P, _P, _I64, ctypes.c_int32, _P, _I64,
                                       _P, ctypes.c_size_t, _P, _P]),
     "id_decompose_sampled": (ctypes.c_int, [_P, ctypes.c_int, _I64, _I64, _I64, _P, _I64, _I64, _P, _P, _P, _I64, _P,
@@ -334,6 +337,44 @@ def id_decompose_sampled(A: torch.Tensor, idx, k: int, *, nb: int = 0, workspace
     if rc in _CALL_ERRORS:
         raise IdError(rc, "id_decompose_sampled")
     return J, Z, (info.as_dict() if sync else None)
+
+
+def two_sided_workspace(dtype: torch.dtype, m: int, n: int, k: int, *, nb: int = 0, device=None) -> Workspace:
+    o = _opts(nb)
+    nbytes = int(lib().id_two_sided_workspace_size(_DTYPES[dtype], m, n, k, ctypes.byref(o)))
+    if nbytes == 0:
+        raise IdError(ID_EINVAL, "id_two_sided_workspace_size")
+    return Workspace(torch.empty(nbytes, dtype=torch.uint8, device=device))
+
+
+def id_decompose_two_sided(A: torch.Tensor, k: int, *, nb: int = 0, workspace: Workspace | None = None,
+                           out: tuple | None = None, sync: bool = True):
+    """Rank-k two-sided ID A ~= X.T @ A[I][:, J] @ Z (the variant the paper's
+    Sec. 1.2 footnote names): a column ID then a row ID of its skeleton (the
+    roles swap for m > n). Returns (I, J, X, Z, infos) with X (k, m), Z (k, n)
+    and infos a pair of dicts (stage 1, stage 2) when sync."""
+    _check_cuda_matrix(A, "A")
+    m, n = A.shape
+    dev = A.device
+    if workspace is None:
+        workspace = two_sided_workspace(A.dtype, m, n, k, nb=nb, device=dev)
+    if out is None:
+        I = torch.empty(k, dtype=torch.int32, device=dev)
+        J = torch.empty(k, dtype=torch.int32, device=dev)
+        X = torch.empty(k, m, dtype=A.dtype, device=dev)
+        Z = torch.empty(k, n, dtype=A.dtype, device=dev)
+    else:
+        I, J, X, Z = out
+    o = _opts(nb)
+    infos = (IdInfo * 2)()
+    with torch.cuda.device(dev):
+        rc = lib().id_decompose_two_sided(A.data_ptr(), _DTYPES[A.dtype], m, n, A.stride(0), k, ctypes.byref(o),
+                                          I.data_ptr(), J.data_ptr(), X.data_ptr(), X.stride(0), Z.data_ptr(),
+                                          Z.stride(0), workspace.buf.data_ptr(), workspace.buf.numel(),
+                                          infos if sync else None, _stream(dev))
+    if rc in _CALL_ERRORS:
+        raise IdError(rc, "id_decompose_two_sided")
+    return I, J, X, Z, ((infos[0].as_dict(), infos[1].as_dict()) if sync else None)
 
 
 def id_reconstruct(A: torch.Tensor, J: torch.Tensor, Z: torch.Tensor, *, transposed: bool = False,

@@ -566,6 +566,87 @@ int id_reconstruct(const void* A, id_dtype dtype, int64_t m, int64_t n, int64_t 
     return ID_OK;
 }
 
+// Two-sided ID: stage 1 on A (a column ID for m <= n, a row ID for m > n),
+// then the other ID of the skeleton S (m x k, or k x n). Regions: stage 1's
+// workspace, S, a flag word, stage 2's workspace.
+namespace {
+struct TwoSided {
+    size_t ws1, S, flag, ws2, total;
+    int64_t sm, sn;   // S is sm x sn row-major
+    bool second;      // stage 2 runs an ID (S is not k x k)
+};
+bool two_sided_layout(id_dtype dt, int64_t m, int64_t n, int64_t k, const id_opts* opts, TwoSided* L) {
+    const size_t w1 = id_workspace_size(dt, m, n, k, opts);
+    if (!w1) return false;
+    L->sm = m <= n ? m : k;
+    L->sn = m <= n ? k : n;
+    L->second = m <= n ? m > k : n > k;
+    const size_t w2 = L->second ? id_workspace_size(dt, L->sm, L->sn, k, nullptr) : align_up(sizeof(DevInfo));
+    if (!w2) return false;
+    const size_t s = dt == ID_F64 ? 8 : 4;
+    L->ws1 = 0;
+    L->S = align_up(w1);
+    L->flag = L->S + align_up(s * (size_t)L->sm * L->sn);
+    L->ws2 = L->flag + align_up(16);
+    L->total = L->ws2 + align_up(w2);
+    return true;
+}
+}  // namespace
+
+size_t id_two_sided_workspace_size(id_dtype dtype, int64_t m, int64_t n, int64_t k, const id_opts* opts) {
+    if (dtype != ID_F64 && dtype != ID_F32) return 0;
+    if (zsolve_of(opts) != 0) return 0;
+    TwoSided L;
+    return two_sided_layout(dtype, m, n, k, opts, &L) ? L.total : 0;
+}
+
+int id_decompose_two_sided(const void* A, id_dtype dtype, int64_t m, int64_t n, int64_t lda, int64_t k,
+                           const id_opts* opts, int32_t* I, int32_t* J, void* X, int64_t ldx, void* Z, int64_t ldz,
+                           void* work, size_t work_bytes, id_info* info, void* stream) {
+    if (!A || !I || !J || !X || !Z || !work) return ID_EINVAL;
+    const size_t need = id_two_sided_workspace_size(dtype, m, n, k, opts);
+    if (need == 0) return ID_EINVAL;
+    if (lda < n || ldx < m || ldz < n || !aligned(work, 256)) return ID_EINVAL;
+    if (opts && opts->nb < 0) return ID_EINVAL;
+    if (!engine_ok(dtype, m, n, k, opts)) return ID_EINVAL;
+    if (work_bytes < need) return ID_ENOMEM;
+    TwoSided L;
+    two_sided_layout(dtype, m, n, k, opts, &L);
+    char* base = static_cast<char*>(work);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const bool f64 = dtype == ID_F64;
+    const bool cols_first = m <= n;
+    // stage 1: the column ID (J, Z) of A, or for m > n its row ID (I, X)
+    int rc = id_decompose(A, dtype, m, n, lda, k, opts, cols_first ? J : I, cols_first ? Z : X, cols_first ? ldz : ldx,
+                          base + L.ws1, L.S, nullptr, stream);
+    if (rc != ID_OK) return rc;
+    // the skeleton: C = A[:, J] (m x k) or R = A[I, :] (k x n)
+    int* flag = reinterpret_cast<int*>(base + L.flag);
+    if (cudaMemsetAsync(flag, 0, 16, s) != cudaSuccess) return ID_ECUDA;
+    if ((f64 ? gather_skeleton<double>(A, lda, m, n, (int)k, cols_first ? J : I, cols_first ? 0 : 1, base + L.S, flag, s)
+             : gather_skeleton<float>(A, lda, m, n, (int)k, cols_first ? J : I, cols_first ? 0 : 1, base + L.S, flag,
+                                      s)) != cudaSuccess)
+        return ID_ECUDA;
+    // stage 2: the row ID (I, X) of C, or the column ID (J, Z) of R
+    int32_t* idx2 = cols_first ? I : J;
+    void* Z2 = cols_first ? X : Z;
+    const int64_t ld2 = cols_first ? ldx : ldz;
+    if (L.second) {
+        rc = id_decompose(base + L.S, dtype, L.sm, L.sn, L.sn, k, nullptr, idx2, Z2, ld2, base + L.ws2,
+                          L.total - L.ws2, nullptr, stream);
+        if (rc != ID_OK) return rc;
+    } else {
+        DevInfo* d2 = reinterpret_cast<DevInfo*>(base + L.ws2);
+        if ((f64 ? identity_id<double>(idx2, Z2, ld2, (int)k, d2, s) : identity_id<float>(idx2, Z2, ld2, (int)k, d2, s)) !=
+            cudaSuccess)
+            return ID_ECUDA;
+    }
+    if (!info) return ID_OK;
+    const int s1 = read_info(base + L.ws1, &info[0], s);
+    const int s2 = read_info(base + L.ws2, &info[1], s);
+    return s1 != ID_OK ? s1 : s2;
+}
+
 int id_trace_enable(int capacity) { return trace_enable(capacity) == 0 ? ID_OK : ID_ECUDA; }
 
 int id_trace_read(double* ms, int64_t* launches, int nkinds) {

@@ -78,6 +78,13 @@ cudaError_t sample_gather_run(const void* A, int64_t lda, int m, const int32_t* 
                               cudaStream_t s);
 cudaError_t sample_map_j(const int* perm, const int32_t* idx, int k, int32_t* J, cudaStream_t s);
 size_t sampled_z_bytes(int64_t m, int64_t n, int64_t k);
+// Two-sided ID pieces (refine.cu): S = A[:, idx] (rows = 0) or A[idx, :]
+// (rows = 1); the ID of a k x k matrix (idx = 0..k-1, Z = I).
+template <typename T>
+cudaError_t gather_skeleton(const void* A, int64_t lda, int64_t m, int64_t n, int k, const int32_t* idx, int rows,
+                            void* S, int* flag, cudaStream_t s);
+template <typename T>
+cudaError_t identity_id(int32_t* idx, void* Zx, int64_t ldz, int k, DevInfo* info, cudaStream_t s);
 // The ID's approximation A[:, J] Z (rows = 0) or Z^T A[J, :] (rows = 1), refine.cu.
 size_t reconstruct_bytes(int64_t m, int64_t n, int64_t k, int rows, size_t elem);
 template <typename T>

@@ -761,6 +761,44 @@ __global__ void k_gather_skel(const T* __restrict__ A, int64_t lda, int m, int n
     }
 }
 
+template <typename T>
+cudaError_t gather_skeleton(const void* A, int64_t lda, int64_t m, int64_t n, int k, const int32_t* idx, int rows,
+                            void* S, int* flag, cudaStream_t s) {
+    k_gather_skel<T><<<grid_for(rows ? (int64_t)k * n : m * k), kRThreads, 0, s>>>(
+        static_cast<const T*>(A), lda, (int)m, (int)n, k, idx, rows, static_cast<T*>(S), flag);
+    return cudaGetLastError();
+}
+template cudaError_t gather_skeleton<double>(const void*, int64_t, int64_t, int64_t, int, const int32_t*, int, void*,
+                                             int*, cudaStream_t);
+template cudaError_t gather_skeleton<float>(const void*, int64_t, int64_t, int64_t, int, const int32_t*, int, void*,
+                                            int*, cudaStream_t);
+
+// An ID of a k x k matrix keeps everything: idx = 0..k-1, Zx = I (k x k, ld ldz);
+// info: status ID_OK, rank k, Z statistics of the identity.
+template <typename T>
+__global__ void k_identity_id(int32_t* idx, T* Zx, int64_t ldz, int k, DevInfo* info) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < k * k; e += gridDim.x * blockDim.x) {
+        const int r = e / k, c = e % k;
+        Zx[(int64_t)r * ldz + c] = r == c ? T(1) : T(0);
+        if (r == 0) idx[c] = c;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        id_info z = {};
+        z.rank = k;
+        z.max_abs_z = 1.0;
+        z.engine = 1;
+        info->info = z;
+    }
+}
+
+template <typename T>
+cudaError_t identity_id(int32_t* idx, void* Zx, int64_t ldz, int k, DevInfo* info, cudaStream_t s) {
+    k_identity_id<T><<<grid_for((int64_t)k * k), kRThreads, 0, s>>>(idx, static_cast<T*>(Zx), ldz, k, info);
+    return cudaGetLastError();
+}
+template cudaError_t identity_id<double>(int32_t*, void*, int64_t, int, DevInfo*, cudaStream_t);
+template cudaError_t identity_id<float>(int32_t*, void*, int64_t, int, DevInfo*, cudaStream_t);
+
 __global__ void k_recon_finalize(DevInfo* info, const int* flag) {
     id_info r = {};
     r.status = flag[0] == 2 ? ID_EINVAL : ID_OK;

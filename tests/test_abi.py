@@ -186,6 +186,27 @@ def test_reconstruct_rules(gbid):
     assert call(work_bytes=64) == gbid.ID_ENOMEM
 
 
+def test_two_sided_rules(gbid):
+    L = gbid.lib()
+    fake = ctypes.c_void_p(256)
+    one = L.id_workspace_size(0, 300, 700, 40, None)
+    assert L.id_two_sided_workspace_size(0, 300, 700, 40, None) > one + 300 * 40 * 8
+    assert L.id_two_sided_workspace_size(1, 700, 300, 40, None) > 0
+    assert L.id_two_sided_workspace_size(0, 40, 700, 40, None) > 0          # k = m: the second stage is trivial
+    assert L.id_two_sided_workspace_size(0, 300, 700, 301, None) == 0
+    ne = gbid._opts(0, zsolve=1)
+    assert L.id_two_sided_workspace_size(0, 300, 700, 40, ctypes.byref(ne)) == 0
+
+    def call(ldx=300, ldz=700, lda=700, work_bytes=1 << 30):
+        return L.id_decompose_two_sided(fake, 0, 300, 700, lda, 40, None, fake, fake, fake, ldx, fake, ldz, fake,
+                                        work_bytes, None, None)
+
+    assert call(ldx=299) == gbid.ID_EINVAL     # X is k x m
+    assert call(ldz=699) == gbid.ID_EINVAL     # Z is k x n
+    assert call(lda=699) == gbid.ID_EINVAL
+    assert call(work_bytes=1024) == gbid.ID_ENOMEM
+
+
 def test_batched_workspace_rules(gbid):
     L = gbid.lib()
     assert L.id_batched_problem_workspace_size(1, 100, 300, 20) >= 100 * 300 * 4 + 300 * 4

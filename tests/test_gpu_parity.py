@@ -313,6 +313,18 @@ def test_full_size_4096x8192_k256(gbid, c2_inputs, dtype):
     assert tail * (1 - 1e-6) <= err <= 3.0 * tail, (err, tail)
 
 
+def test_full_size_row_id_of_the_transpose(gbid, c2_inputs):
+    """The m > n route at full size: the row ID of the 8192 x 4096 transpose runs
+    the same CPQR on the same working matrix, so J and Z equal the column ID's."""
+    if gbid.engine == 2:
+        pytest.skip("too large for one cluster: the grid kernel, as in the other run")
+    A, _ = c2_inputs
+    J, Z, info = gbid.id_decompose(A, 256)
+    Jt, Zt, info_t = gbid.id_decompose(A.T.contiguous(), 256)
+    assert info_t["transposed"] == 1 and info_t["status"] == gbid.ID_OK
+    assert torch.equal(J, Jt) and torch.equal(Z, Zt)
+
+
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
 def test_full_size_exact_rank_256(gbid, c2_inputs, dtype):
     if gbid.engine == 2:
