@@ -285,6 +285,16 @@ def sampled_interp_decomp(A: np.ndarray, idx: np.ndarray, k: int):
     return J, Z, {"perm": f["perm"], "R": R, "rank": f["rank"], "gap": f["gap"]}
 
 
+def csr_to_dense(rowptr: np.ndarray, colind: np.ndarray, values: np.ndarray, m: int, n: int) -> np.ndarray:
+    """The dense m x n matrix of a CSR triple (row i holds colind/values[rowptr[i]:rowptr[i+1]]);
+    duplicate entries are summed. The sparse-input ID is interp_decomp of this matrix."""
+    A = np.zeros((m, n), dtype=np.float64)
+    for i in range(m):
+        for q in range(int(rowptr[i]), int(rowptr[i + 1])):
+            A[i, int(colind[q])] += float(values[q])
+    return A
+
+
 def two_sided_interp_decomp(A: np.ndarray, k: int):
     """Two-sided ID A ~= X^T A[I, J] Z, the variant of Cheng et al. that the
     footnote of Sec. 1.2 names.

@@ -173,6 +173,31 @@ def batched_uneven(count: int, seed: int, *, m_range=(32, 256), k_range=(8, 64),
     return out
 
 
+def sparse_powerlaw_csr(m: int, n: int, density: float, seed: int, *, alpha: float = 1.2):
+    """Seeded sparse m x n matrix in CSR form with a power-law column degree
+    distribution (column l gets a share proportional to (1 + r_l)^-alpha of the
+    density * m * n nonzeros, r a random permutation; capped at m), rows drawn
+    uniformly per column, values U(0, 1) (non-negative, like the paper's
+    sparse and Boolean data). Returns (rowptr int64 (m+1), colind int32,
+    values float64), rows sorted, column indices sorted within a row."""
+    rng = np.random.default_rng(seed)
+    w = (1.0 + rng.permutation(n)) ** -alpha
+    deg = np.minimum(rng.multinomial(int(density * m * n), w / w.sum()), m)
+    rows, cols = [], []
+    for l in np.flatnonzero(deg):
+        r = rng.choice(m, size=int(deg[l]), replace=False)
+        rows.append(r)
+        cols.append(np.full(r.size, l))
+    rows = np.concatenate(rows) if rows else np.zeros(0, np.int64)
+    cols = np.concatenate(cols) if cols else np.zeros(0, np.int64)
+    order = np.lexsort((cols, rows))
+    rows, cols = rows[order], cols[order]
+    vals = rng.random(rows.size)
+    rowptr = np.zeros(m + 1, dtype=np.int64)
+    np.add.at(rowptr, rows + 1, 1)
+    return np.cumsum(rowptr), cols.astype(np.int32), vals
+
+
 # name -> (m, n, k, spectrum kind, seed)
 WORKLOADS = {
     "id_200x400_k20_f64": dict(m=200, n=400, k=20, spec="pow2_half", seed=1),

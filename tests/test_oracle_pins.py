@@ -332,6 +332,32 @@ def test_sampled_rid_properties():
         orc.sampled_interp_decomp(A, np.array([1, 1, 2]), 2)
 
 
+# ------------------------------------------------------------- sparse input ---
+def test_csr_to_dense_matches_the_library_routine():
+    """The oracle's CSR densification against scipy.sparse (duplicates summed)."""
+    sp = pytest.importorskip("scipy.sparse")
+    rowptr, colind, vals = synth.sparse_powerlaw_csr(40, 90, 0.08, 3)
+    # plant a duplicate entry in row 5 and an empty row 7
+    A = orc.csr_to_dense(rowptr, colind, vals, 40, 90)
+    B = sp.csr_matrix((vals, colind, rowptr), shape=(40, 90)).toarray()
+    assert np.array_equal(A, B)
+    r = np.array([0, 2, 2, 3], dtype=np.int64)
+    c = np.array([4, 4, 1], dtype=np.int32)
+    v = np.array([1.5, 2.0, -1.0])
+    D = orc.csr_to_dense(r, c, v, 3, 6)
+    assert D[0, 4] == 3.5 and D[2, 1] == -1.0 and np.count_nonzero(D) == 2
+    assert np.array_equal(D, sp.csr_matrix((v, c, r), shape=(3, 6)).toarray())
+
+
+def test_sparse_generator_shape():
+    rowptr, colind, vals = synth.sparse_powerlaw_csr(300, 800, 0.02, 5)
+    assert rowptr[0] == 0 and rowptr[-1] == colind.size == vals.size
+    assert np.all(np.diff(rowptr) >= 0) and colind.min() >= 0 and colind.max() < 800
+    assert 0.6 * 0.02 * 300 * 800 <= colind.size <= 0.02 * 300 * 800    # the heaviest columns are capped at m
+    deg = np.bincount(colind, minlength=800)
+    assert deg.max() > 10 * max(1, np.median(deg))          # heavy-tailed column degrees
+
+
 # ---------------------------------------------------------------- two-sided ---
 @pytest.mark.parametrize("m,n", [(60, 140), (140, 60), (80, 80)])
 def test_two_sided_exact_rank(m, n):
