@@ -16,8 +16,9 @@ IDs at k = 20; and under "differentiable", 256 IDs of 512 x 1024 at k = 64
 forward (batched) and backward; and under "sampled", the paper's
 column-sampling Optim RID of the headline matrices (p = 307 sampled columns),
 under "listing", the paper's listing outputs of the same matrices (Z from
-the normal equations, approx = C @ Z), and under "two_sided", the two-sided ID
-of the same matrices and the row ID of the 8192 x 4096 transpose
+the normal equations, approx = C @ Z), under "two_sided", the two-sided ID
+of the same matrices and the row ID of the 8192 x 4096 transpose, and under
+"sparse", the ID of a 4096 x 8192 CSR matrix with 1% power-law nonzeros
 (--only randomized / batched / latency / differentiable runs that workload
 alone; --only id skips them; --only sampled keeps the ID and the sampled RID).
 
@@ -487,6 +488,45 @@ def two_sided_block(gbid, dev, steps, mats):
     return out
 
 
+def sparse_block(gbid, dev, steps):
+    """Sparse input (CSR) at the headline size: 4096 x 8192, 1% nonzeros with
+    power-law column degrees, U(0,1) values (seed 6), k = 256, FP64; ms per ID
+    from device-resident CSR arrays, and the dense ID of the same matrix."""
+    import numpy as np
+    import torch
+
+    import synth
+
+    rowptr, colind, vals = synth.sparse_powerlaw_csr(M, N, 0.01, 6)
+    r = torch.as_tensor(rowptr, device=dev)
+    c = torch.as_tensor(colind, device=dev)
+    v = torch.as_tensor(vals, dtype=torch.float64, device=dev)
+    ws = gbid.csr_workspace(torch.float64, M, N, K_RANK, device=dev)
+    J = torch.empty(K_RANK, dtype=torch.int32, device=dev)
+    Z = torch.empty(K_RANK, N, dtype=torch.float64, device=dev)
+    for _ in range(3):
+        gbid.id_decompose_csr(r, c, v, (M, N), K_RANK, workspace=ws, out=(J, Z), sync=False)
+    torch.cuda.synchronize()
+    s = torch.cuda.current_stream()
+    ev = []
+    for _ in range(steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        gbid.id_decompose_csr(r, c, v, (M, N), K_RANK, workspace=ws, out=(J, Z), sync=False)
+        e1.record(s)
+        ev.append((e0, e1))
+    torch.cuda.synchronize()
+    ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    info = gbid.read_info(ws)
+    A = torch.zeros(M, N, dtype=torch.float64, device=dev)
+    rows = torch.repeat_interleave(torch.arange(M, device=dev), torch.diff(r))
+    A.index_put_((rows, c.long()), v, accumulate=True)
+    err = rel_error_gpu(A, J, Z)
+    return {"workload": f"csr_{M}x{N}_density0.01_k{K_RANK}_f64", "nnz": int(vals.size), "ms_per_step": ms,
+            "value": 1000.0 / ms, "unit": UNIT, "status": info["status_name"], "rel_err": err}
+
+
 BATCH_COUNT = 4096
 
 
@@ -759,6 +799,7 @@ def run_gbid(args):
         if args.only in ("all", "sampled") else None
     two = two_sided_block(gbid, dev, max(3, min(args.steps, 10)), {n: r["A"] for n, r in results.items()}) \
         if args.only in ("all", "sampled") else None
+    spa = sparse_block(gbid, dev, max(3, min(args.steps, 10))) if args.only in ("all", "sampled") else None
     rid = randomized_block(gbid, dev, max(2, min(args.steps, 5))) if args.only == "all" else None
     bat = batched_block(gbid, dev, max(3, min(args.steps, 10))) if args.only == "all" else None
     lat = latency_block(gbid, dev, args.steps) if args.only == "all" else None
@@ -799,6 +840,7 @@ def run_gbid(args):
         "sampled": samp,
         "listing": lst,
         "two_sided": two,
+        "sparse": spa,
         "batched": bat,
         "latency": lat,
         "differentiable": dif,

@@ -359,6 +359,25 @@ int id_reconstruct(const void* A, id_dtype dtype, int64_t m, int64_t n, int64_t 
                    const void* Z, int64_t ldz, int32_t transposed, void* Out, int64_t ldo, void* work,
                    size_t work_bytes, id_info* info, void* stream);
 
+/* id_decompose_csr -- rank-k ID (as id_decompose) of a sparse A given in CSR
+ * form, for inputs such as the sparse matrices of the paper's experiments
+ * (Sec. 3): the skeleton C = A[:, J] keeps A's sparsity (Sec. 1.2). A is
+ * formed directly in the dense working layout (no dense copy of A), then the
+ * same CPQR, back substitution and Z assembly run on the grid engine.
+ *   rowptr [in] m + 1 int64 offsets (device), nondecreasing, rowptr[m] <= nnz.
+ *   colind [in] nnz int32 column indices in [0, n) (device); values [in] nnz
+ *               entries of dtype (device). Duplicate (row, column) entries
+ *               are summed, in an unspecified order.
+ *   J, Z   [out] as for id_decompose (m > n gives a row ID).
+ *   work   [in]  id_csr_workspace_size() bytes, 256-byte aligned.
+ *   opts   nb as for id_decompose; engine 2 or zsolve != 0 is ID_EINVAL.
+ * A malformed rowptr or column index is found on the device: the status
+ * (through info) is ID_EINVAL and J, Z are unspecified. */
+size_t id_csr_workspace_size(id_dtype dtype, int64_t m, int64_t n, int64_t k, const id_opts* opts);
+int id_decompose_csr(const int64_t* rowptr, const int32_t* colind, const void* values, id_dtype dtype, int64_t m,
+                     int64_t n, int64_t nnz, int64_t k, const id_opts* opts, int32_t* J, void* Z, int64_t ldz,
+                     void* work, size_t work_bytes, id_info* info, void* stream);
+
 /* id_decompose_two_sided -- rank-k two-sided ID A ~= X^T A[I, J] Z, the
  * variant (Cheng et al.) that the footnote of Sec. 1.2 names. For m <= n:
  * the column ID (J, Z) of A (Sec. 2.1), then the row ID (I, X) of the

@@ -95,6 +95,9 @@ _SIG = {
     "id_sampled_workspace_size": (ctypes.c_size_t, [ctypes.c_int, _I64, _I64, _I64, _I64, _P]),
     "id_reconstruct_workspace_size": (ctypes.c_size_t, [ctypes.c_int, _I64, _I64, _I64, ctypes.c_int32]),
     "id_two_sided_workspace_size": (ctypes.c_size_t, [ctypes.c_int, _I64, _I64, _I64, _P]),
+    "id_csr_workspace_size": (ctypes.c_size_t, [ctypes.c_int, _I64, _I64, _I64, _P]),
+    "id_decompose_csr": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _I64, _I64, _I64, _I64, _P, _P, _P, _I64, _P,
+                                        ctypes.c_size_t, _P, _P]),
     "id_decompose_two_sided": (ctypes.c_int, [_P, ctypes.c_int, _I64, _I64, _I64, _I64, _P, _P, _P, _P, _I64, _P, _I64,
                                               _P, ctypes.c_size_t, _P, _P]),
     "id_reconstruct": (ctypes.c_int, [_P, ctypes.c_int, _I64, _I64, _I64, _I64, _P, _P, _I64, ctypes.c_int32, _P, _I64,
@@ -336,6 +339,47 @@ def id_decompose_sampled(A: torch.Tensor, idx, k: int, *, nb: int = 0, workspace
                                         ctypes.byref(info) if sync else None, _stream(dev))
     if rc in _CALL_ERRORS:
         raise IdError(rc, "id_decompose_sampled")
+    return J, Z, (info.as_dict() if sync else None)
+
+
+def csr_workspace(dtype: torch.dtype, m: int, n: int, k: int, *, nb: int = 0, device=None) -> Workspace:
+    o = _opts(nb)
+    nbytes = int(lib().id_csr_workspace_size(_DTYPES[dtype], m, n, k, ctypes.byref(o)))
+    if nbytes == 0:
+        raise IdError(ID_EINVAL, "id_csr_workspace_size")
+    return Workspace(torch.empty(nbytes, dtype=torch.uint8, device=device))
+
+
+def id_decompose_csr(rowptr: torch.Tensor, colind: torch.Tensor, values: torch.Tensor, shape, k: int, *,
+                     nb: int = 0, workspace: Workspace | None = None, out: tuple | None = None, sync: bool = True):
+    """Rank-k ID of a sparse CUDA matrix in CSR form (rowptr int64 (m+1),
+    colind int32, values float32/float64, all on the GPU). Same outputs as
+    id_decompose; the skeleton A[:, J] keeps A's sparsity."""
+    m, n = (int(shape[0]), int(shape[1]))
+    if not (rowptr.is_cuda and colind.is_cuda and values.is_cuda):
+        raise ValueError("rowptr, colind and values must be CUDA tensors (no CPU fallback)")
+    if rowptr.dtype != torch.int64 or colind.dtype != torch.int32 or values.dtype not in _DTYPES:
+        raise ValueError("rowptr int64, colind int32, values float32/float64")
+    if rowptr.numel() != m + 1 or colind.numel() != values.numel():
+        raise ValueError("rowptr must have m + 1 entries and colind as many as values")
+    dev = values.device
+    if workspace is None:
+        workspace = csr_workspace(values.dtype, m, n, k, nb=nb, device=dev)
+    nz = max(m, n)
+    if out is None:
+        J = torch.empty(k, dtype=torch.int32, device=dev)
+        Z = torch.empty(k, nz, dtype=values.dtype, device=dev)
+    else:
+        J, Z = out
+    o = _opts(nb)
+    info = IdInfo()
+    with torch.cuda.device(dev):
+        rc = lib().id_decompose_csr(rowptr.data_ptr(), colind.data_ptr(), values.data_ptr(), _DTYPES[values.dtype], m,
+                                    n, values.numel(), k, ctypes.byref(o), J.data_ptr(), Z.data_ptr(), Z.stride(0),
+                                    workspace.buf.data_ptr(), workspace.buf.numel(),
+                                    ctypes.byref(info) if sync else None, _stream(dev))
+    if rc in _CALL_ERRORS:
+        raise IdError(rc, "id_decompose_csr")
     return J, Z, (info.as_dict() if sync else None)
 
 

@@ -231,6 +231,35 @@ size_t rid_bytes(int64_t m, int64_t n, int64_t l, int64_t k, const id_opts* opts
     return base + (rid_refine(opts) ? refine_bytes(m, n, k) : 0);
 }
 
+// Sparse (CSR) input: the matrix is formed in the working layout directly,
+// then the grid-engine path of decompose_impl.
+template <typename T>
+int decompose_csr_impl(const int64_t* rowptr, const int32_t* colind, const void* vals, int64_t m, int64_t n,
+                       int64_t nnz, int64_t k, const id_opts* opts, int32_t* J, void* Z, int64_t ldz, void* work,
+                       size_t work_bytes, id_info* info, cudaStream_t s) {
+    const int trans = m > n ? 1 : 0;
+    const int mx = (int)(trans ? n : m), nx = (int)(trans ? m : n);
+    const id_dtype dt = sizeof(T) == 8 ? ID_F64 : ID_F32;
+    const Layout L = make_layout(dt, mx, nx, (int)k, opts, true, true);
+    if (work_bytes < L.total + align_up(16)) return ID_ENOMEM;
+    if (configure_once()) return ID_ECUDA;
+    char* base = static_cast<char*>(work);
+    CpqrPlan P = make_plan(L, base, nullptr, nullptr, nullptr, (int)k, m, n);
+    DevInfo* dinfo = reinterpret_cast<DevInfo*>(base + L.info);
+    int* flag = reinterpret_cast<int*>(base + L.total);
+    if (cudaMemsetAsync(dinfo, 0, sizeof(DevInfo), s) != cudaSuccess) return ID_ECUDA;
+    if (cudaMemsetAsync(flag, 0, 16, s) != cudaSuccess) return ID_ECUDA;
+    if (csr_in<T>(rowptr, colind, vals, m, n, nnz, trans, P, flag, s) != cudaSuccess) return ID_ECUDA;
+    if (cpqr_run<T>(P, s) != cudaSuccess) return ID_ECUDA;
+    double* Tm = reinterpret_cast<double*>(base + L.T);
+    const int ldt = nx - (int)k > 0 ? nx - (int)k : 1;
+    if (solve_run<T>(P.W, P.ldw, (int)k, nx, Tm, ldt, s) != cudaSuccess) return ID_ECUDA;
+    if (scatter_z<T>(P.perm, Tm, ldt, (int)k, nx, Z, ldz, J, dinfo, s) != cudaSuccess) return ID_ECUDA;
+    if (finalize_info(P.st, dinfo, (int)k, trans, P.nb, s, flag) != cudaSuccess) return ID_ECUDA;
+    if (info) return read_info(work, info, s);
+    return ID_OK;
+}
+
 }  // namespace
 }  // namespace gbid
 
@@ -564,6 +593,28 @@ int id_reconstruct(const void* A, id_dtype dtype, int64_t m, int64_t n, int64_t 
     if (rc != ID_OK) return rc;
     if (info) return read_info(work, info, s);
     return ID_OK;
+}
+
+size_t id_csr_workspace_size(id_dtype dtype, int64_t m, int64_t n, int64_t k, const id_opts* opts) {
+    if (opts && (opts->engine == 2 || opts->zsolve != 0)) return 0;
+    const size_t w = id_workspace_size(dtype, m, n, k, opts);
+    return w ? w + align_up(16) : 0;
+}
+
+int id_decompose_csr(const int64_t* rowptr, const int32_t* colind, const void* values, id_dtype dtype, int64_t m,
+                     int64_t n, int64_t nnz, int64_t k, const id_opts* opts, int32_t* J, void* Z, int64_t ldz,
+                     void* work, size_t work_bytes, id_info* info, void* stream) {
+    if (!rowptr || !J || !Z || !work || nnz < 0 || (nnz > 0 && (!colind || !values))) return ID_EINVAL;
+    const size_t need = id_csr_workspace_size(dtype, m, n, k, opts);
+    if (need == 0) return ID_EINVAL;
+    if (ldz < (m > n ? m : n) || !aligned(work, 256)) return ID_EINVAL;
+    if (opts && opts->nb < 0) return ID_EINVAL;
+    if (work_bytes < need) return ID_ENOMEM;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (dtype == ID_F64)
+        return decompose_csr_impl<double>(rowptr, colind, values, m, n, nnz, k, opts, J, Z, ldz, work, work_bytes,
+                                          info, s);
+    return decompose_csr_impl<float>(rowptr, colind, values, m, n, nnz, k, opts, J, Z, ldz, work, work_bytes, info, s);
 }
 
 // Two-sided ID: stage 1 on A (a column ID for m <= n, a row ID for m > n),

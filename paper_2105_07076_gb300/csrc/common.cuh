@@ -12,7 +12,7 @@ constexpr int kWarp = 32;
 constexpr int kMaxParts = 2048;     // argmax partial slots per producer kernel
 
 // Device-side status bits collected during a decomposition.
-enum : int { kStatNonFinite = 1, kStatTimeout = 2, kStatOverflow = 4 };
+enum : int { kStatNonFinite = 1, kStatTimeout = 2, kStatOverflow = 4, kStatBadInput = 8 };
 
 // One candidate of the pivot search: residual norm, original index, position.
 struct __align__(16) ArgMax {

@@ -113,6 +113,33 @@ __global__ void __launch_bounds__(256) k_copy_in(const T* __restrict__ A, int64_
     }
 }
 
+// CSR A (m x n: rowptr[m + 1], colind, values) into the working matrix,
+// X = A (trans = 0: W[l * ldw + i]) or X = A^T (trans = 1: W[i * ldw + l]).
+// W is zero on entry. One warp per row; duplicate entries are summed (in an
+// unspecified order). A decreasing or out-of-range rowptr, or a column index
+// outside [0, n), sets kStatBadInput and the entry is skipped.
+template <typename T>
+__global__ void __launch_bounds__(256) k_csr_in(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
+                                                const T* __restrict__ vals, int m, int n, int64_t nnz, int trans,
+                                                T* W, int ldw, int* status) {
+    const int lane = threadIdx.x % kWarp;
+    for (int i = blockIdx.x * (blockDim.x / kWarp) + threadIdx.x / kWarp; i < m; i += gridDim.x * (blockDim.x / kWarp)) {
+        const int64_t b = rowptr[i], e = rowptr[i + 1];
+        if (b < 0 || e < b || e > nnz) {
+            if (lane == 0) atomicOr(status, kStatBadInput);
+            continue;
+        }
+        for (int64_t q = b + lane; q < e; q += kWarp) {
+            const int l = colind[q];
+            if (l < 0 || l >= n) {
+                atomicOr(status, kStatBadInput);
+                continue;
+            }
+            atomicAdd(trans ? W + (int64_t)i * ldw + l : W + (int64_t)l * ldw + i, vals[q]);
+        }
+    }
+}
+
 // Zero rows m..ldw-1 of every column (id_cpqr path, user-provided X).
 template <typename T>
 __global__ void k_zero_pad(T* W, int ldw, int m, int n) {
@@ -1347,6 +1374,17 @@ cudaError_t copy_in(const void* A, int64_t lda, int trans, const CpqrPlan& P, cu
 }
 
 template <typename T>
+cudaError_t csr_in(const int64_t* rowptr, const int32_t* colind, const void* vals, int64_t m, int64_t n, int64_t nnz,
+                   int trans, const CpqrPlan& P, int* status, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(P.W, 0, sizeof(T) * (size_t)P.ldw * P.n, s);
+    if (e != cudaSuccess) return e;
+    const int blocks = (int)std::min<int64_t>(ceil_div(m, kThreads / kWarp), 4096);
+    k_csr_in<T><<<blocks, kThreads, 0, s>>>(rowptr, colind, static_cast<const T*>(vals), (int)m, (int)n, nnz, trans,
+                                            static_cast<T*>(P.W), P.ldw, status);
+    return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t zero_pad(const CpqrPlan& P, cudaStream_t s) {
     if (P.ldw == P.m) return cudaSuccess;
     k_zero_pad<T><<<304, 256, 0, s>>>(static_cast<T*>(P.W), P.ldw, P.m, P.n);
@@ -1433,6 +1471,10 @@ template int cpqr_grid<double>(int);
 template int cpqr_grid<float>(int);
 template cudaError_t copy_in<double>(const void*, int64_t, int, const CpqrPlan&, cudaStream_t);
 template cudaError_t copy_in<float>(const void*, int64_t, int, const CpqrPlan&, cudaStream_t);
+template cudaError_t csr_in<double>(const int64_t*, const int32_t*, const void*, int64_t, int64_t, int64_t, int,
+                                    const CpqrPlan&, int*, cudaStream_t);
+template cudaError_t csr_in<float>(const int64_t*, const int32_t*, const void*, int64_t, int64_t, int64_t, int,
+                                   const CpqrPlan&, int*, cudaStream_t);
 template cudaError_t zero_pad<double>(const CpqrPlan&, cudaStream_t);
 template cudaError_t zero_pad<float>(const CpqrPlan&, cudaStream_t);
 template cudaError_t cpqr_run<double>(const CpqrPlan&, cudaStream_t);

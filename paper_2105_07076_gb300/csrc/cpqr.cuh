@@ -37,6 +37,10 @@ inline size_t sync_bytes(int k) { return 64 + 4 * (size_t)k; }
 template <typename T> cudaError_t cpqr_configure();
 template <typename T> cudaError_t copy_in(const void* A, int64_t lda, int trans, const CpqrPlan& P, cudaStream_t s);
 template <typename T> cudaError_t zero_pad(const CpqrPlan& P, cudaStream_t s);
+// CSR input into the (zeroed) working matrix; bad input sets kStatBadInput in *status.
+template <typename T>
+cudaError_t csr_in(const int64_t* rowptr, const int32_t* colind, const void* vals, int64_t m, int64_t n, int64_t nnz,
+                   int trans, const CpqrPlan& P, int* status, cudaStream_t s);
 template <typename T> cudaError_t cpqr_run(const CpqrPlan& P, cudaStream_t s);
 template <typename T> int cpqr_grid(int m);   // CTAs of the cooperative launch (0: cannot launch)
 

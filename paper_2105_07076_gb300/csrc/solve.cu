@@ -229,7 +229,8 @@ __global__ void k_finalize(const State* st, DevInfo* info, int k, int transposed
     r.engine = 1;
     r.n_gt2 = (int64_t)info->n_gt2;
     r.max_abs_z = __longlong_as_double((long long)info->max_abs_z_bits);
-    if (status & kStatNonFinite) r.status = ID_ENONFINITE;
+    if (status & kStatBadInput) r.status = ID_EINVAL;
+    else if (status & kStatNonFinite) r.status = ID_ENONFINITE;
     else if (status & kStatTimeout) r.status = ID_ETIMEOUT;
     else if (st->rank < k) r.status = ID_RANK_DEFICIENT;
     else r.status = ID_OK;

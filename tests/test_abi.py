@@ -207,6 +207,26 @@ def test_two_sided_rules(gbid):
     assert call(work_bytes=1024) == gbid.ID_ENOMEM
 
 
+def test_csr_rules(gbid):
+    L = gbid.lib()
+    fake = ctypes.c_void_p(256)
+    assert L.id_csr_workspace_size(0, 300, 700, 40, None) > L.id_workspace_size(0, 300, 700, 40, None)
+    assert L.id_csr_workspace_size(0, 300, 700, 301, None) == 0
+    cl = gbid._opts(0, engine=gbid.ENGINE_CLUSTER)
+    assert L.id_csr_workspace_size(0, 200, 400, 20, ctypes.byref(cl)) == 0
+    ne = gbid._opts(0, zsolve=1)
+    assert L.id_csr_workspace_size(0, 200, 400, 20, ctypes.byref(ne)) == 0
+
+    def call(nnz=100, ldz=700, colind=fake, work_bytes=1 << 30):
+        return L.id_decompose_csr(fake, colind, fake, 0, 300, 700, nnz, 40, None, fake, fake, ldz, fake, work_bytes,
+                                  None, None)
+
+    assert call(nnz=-1) == gbid.ID_EINVAL
+    assert call(colind=None) == gbid.ID_EINVAL
+    assert call(ldz=699) == gbid.ID_EINVAL
+    assert call(work_bytes=1024) == gbid.ID_ENOMEM
+
+
 def test_batched_workspace_rules(gbid):
     L = gbid.lib()
     assert L.id_batched_problem_workspace_size(1, 100, 300, 20) >= 100 * 300 * 4 + 300 * 4
