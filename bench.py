@@ -534,7 +534,8 @@ def differentiable_block(gbid, dev, steps):
     """The differentiable form: 256 FP32 matrices 512 x 1024, s_i = (1+i)^-2,
     k = 64 (seed 5): forward by one batched launch, then dL/dA for
     L = <G, Z> (G ~ N(0,1), seed 5) by id_backward per matrix, the 256 backward
-    calls replayed from one CUDA graph (stream-ordered, one shared workspace)."""
+    calls spread over 16 streams (one workspace each) and replayed from one
+    CUDA graph."""
     import torch
 
     import synth
@@ -546,13 +547,11 @@ def differentiable_block(gbid, dev, steps):
     g = torch.Generator(device=dev).manual_seed(5)
     Gs = [torch.randn(k, n, generator=g, device=dev) for _ in range(nb)]
     plan = gbid.BatchedPlan(mats, [k] * nb)
-    nbytes = int(gbid.lib().id_backward_workspace_size(gbid.ID_F32, m, n, k))
-    ws = gbid.Workspace(torch.empty(nbytes, dtype=torch.uint8, device=dev))
+    bplan = gbid.BackwardPlan(m, n, k, streams=16, device=dev)
     dAs = [torch.empty(m, n, device=dev) for _ in range(nb)]
 
     def backward_all():
-        for A, J, Z, G, dA in zip(mats, plan.J, plan.Z, Gs, dAs):
-            gbid.id_backward(A, J, Z, G, workspace=ws, out=dA, sync=False)
+        bplan.run(mats, plan.J, plan.Z, Gs, dAs)
 
     plan.run()
     backward_all()

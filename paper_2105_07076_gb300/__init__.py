@@ -502,6 +502,33 @@ def id_backward(A: torch.Tensor, J: torch.Tensor, Z: torch.Tensor, dZ: torch.Ten
     return dA, (info.as_dict() if sync else None)
 
 
+class BackwardPlan:
+    """dL/dA for many IDs of one size (FP32, m <= n), spread over ``streams``
+    CUDA streams so that the problems' small kernels overlap; each stream has
+    its own workspace. ``run`` forks from the current stream and joins back
+    into it, so it can be captured in a CUDA graph and replayed."""
+
+    def __init__(self, m: int, n: int, k: int, *, streams: int = 16, device="cuda"):
+        nbytes = int(lib().id_backward_workspace_size(ID_F32, m, n, k))
+        if nbytes == 0:
+            raise IdError(ID_EINVAL, "id_backward_workspace_size")
+        self.shape = (m, n, k)
+        self.streams = [torch.cuda.Stream(device=device) for _ in range(max(1, int(streams)))]
+        self.workspaces = [Workspace(torch.empty(nbytes, dtype=torch.uint8, device=device)) for _ in self.streams]
+
+    def run(self, As, Js, Zs, dZs, dAs):
+        cur = torch.cuda.current_stream()
+        for st in self.streams:
+            st.wait_stream(cur)
+        for b, (A, J, Z, dZ, dA) in enumerate(zip(As, Js, Zs, dZs, dAs)):
+            q = b % len(self.streams)
+            with torch.cuda.stream(self.streams[q]):
+                id_backward(A, J, Z, dZ, workspace=self.workspaces[q], out=dA, sync=False)
+        for st in self.streams:
+            cur.wait_stream(st)
+        return dAs
+
+
 class IdFunction(torch.autograd.Function):
     """Z = ID(A) with the skeleton frozen after the forward pass (FP32 CUDA, m <= n):
     forward runs id_decompose, backward id_backward."""
