@@ -272,6 +272,36 @@ def test_host_buffers_entry_point(gbid):
     assert torch.equal(J, Jd.cpu()) and torch.equal(Z, Zd.cpu())
 
 
+# ------------------------------------------------------------ size limits ---
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_widest_matrix(gbid, dtype):
+    """n = 2048 * 256 = 524288 columns, the largest the grid kernel takes (one
+    GEMV CTA owns at most 256 of them): pivots replayed by the oracle, Z
+    against the oracle's least-squares Z on sampled columns."""
+    if gbid.engine == 2:
+        pytest.skip("too large for one cluster")
+    m, n, k = 48, 524288, 12
+    A = synth.lowrank(m, n, synth.spectrum("exp64", m), 77, device="cuda").to(dtype)
+    J, Z, info = gbid.id_decompose(A, k)
+    assert info["status"] == gbid.ID_OK
+    Ah = A.double().cpu().numpy()
+    Jg = J.cpu().numpy().astype(np.int64)
+    ok, worst = orc.verify_pivots(Ah, Jg, tol_piv(dtype, m))
+    assert ok, worst.max()
+    Zg = Z.double().cpu().numpy()
+    assert np.array_equal(Zg[:, Jg], np.eye(k))
+    cols = np.random.default_rng(1).choice(np.setdiff1d(np.arange(n), Jg), 64, replace=False)
+    Zs, *_ = np.linalg.lstsq(Ah[:, Jg], Ah[:, cols], rcond=None)
+    cond = np.linalg.cond(Ah[:, Jg])
+    bar = TOL_Z[dtype] if dtype == torch.float64 else max(TOL_Z[dtype], 2 * cond * 2.0 ** -24)
+    assert np.linalg.norm(Zg[:, cols] - Zs) / np.linalg.norm(Zs) <= bar
+
+
+def test_one_past_the_widest_matrix_is_refused(gbid):
+    with pytest.raises(gbid.IdError):
+        gbid.Workspace.for_problem(torch.float32, 16, 2048 * 256 + 1, 4)
+
+
 # ---------------------------------------------- full size, sampled checks ---
 @pytest.fixture(scope="module")
 def c2_inputs():
