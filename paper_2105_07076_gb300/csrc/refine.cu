@@ -10,8 +10,8 @@
 //      diagonal factorisation, a forward substitution for the panel row, a
 //      tiled rank-32 update of the trailing upper triangle). A non-positive
 //      pivot (rank(C) < k) sets a flag and Z is left unchanged.
-//   4. U^{-1} by the library's blocked back substitution (R11 = U, R12 = I),
-//      rounded to FP32.
+//   4. U^{-1} in FP64 by a blocked inverse (32 x 32 diagonal blocks by back
+//      substitution, merged with FP64 GEMMs), rounded to FP32.
 //   5. Over column blocks of 4096: R_b = A_b - C Z_b, H_b = C^T R_b as
 //      FP32-accurate GEMMs (cuBLAS, FP32 compute emulated on the BF16 tensor
 //      cores where that is faster). Columns of J give R_b = 0 exactly
@@ -220,16 +220,6 @@ __global__ void __launch_bounds__(256) k_ctb(const float* __restrict__ C, const 
             const int i = i0 + ty * 4 + a, j = j0 + tx * 4 + b;
             if (i < k && j < n) B[(int64_t)i * n + j] = (double)hi[a][b] + (double)lo[a][b];
         }
-}
-
-// Wa = [G | I] column-major with leading dimension k; G's upper triangle is
-// written by k_gram_sum, so only the identity half is set here.
-__global__ void k_identity_half(double* Wa, int k) {
-    const int64_t total = (int64_t)k * k;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        const int c = (int)(e / k), r = (int)(e % k);
-        Wa[(int64_t)(k + c) * k + r] = r == c ? 1.0 : 0.0;
-    }
 }
 
 // Diagonal block (b <= 32) at p0: D = U_D^T U_D in place. 256 threads: per
@@ -519,18 +509,86 @@ __global__ void k_sampled_finalize(DevInfo* info, const int* flag) {
     info->info = r;
 }
 
+// ------------------------------------------------ triangular inverse U^{-1} --
+// Blocked: the kTriLeaf x kTriLeaf diagonal blocks are inverted by back
+// substitution (one CTA per block, one thread per column), then neighbouring
+// blocks merge, [A B; 0 C]^{-1} = [A^{-1}  -A^{-1} B C^{-1}; 0  C^{-1}], with two
+// FP64 GEMMs per merge, so the work spreads over the GPU instead of a few
+// column blocks of one solve.
+constexpr int kTriLeaf = 32;
+
+__global__ void __launch_bounds__(kTriLeaf) k_tri_inv_leaf(const double* __restrict__ U, int k,
+                                                          double* __restrict__ Uinv) {
+    __shared__ double Us[kTriLeaf][kTriLeaf + 1];
+    __shared__ double Xs[kTriLeaf][kTriLeaf + 1];
+    const int o = blockIdx.x * kTriLeaf, b = min(kTriLeaf, k - o), c = threadIdx.x;
+    for (int r = 0; r < b; ++r) Us[r][c] = (c < b && r <= c) ? U[(int64_t)(o + c) * k + o + r] : 0.0;
+    __syncthreads();
+    if (c < b) {
+        // U_blk x = e_c by back substitution; x_r = 0 for r > c
+        for (int r = b - 1; r >= 0; --r) {
+            if (r > c) {
+                Xs[r][c] = 0.0;
+                continue;
+            }
+            double acc = r == c ? 1.0 : 0.0;
+            for (int j = r + 1; j <= c; ++j) acc -= Us[r][j] * Xs[j][c];
+            Xs[r][c] = acc / Us[r][r];
+        }
+        for (int r = 0; r < b; ++r) Uinv[(int64_t)(o + c) * k + o + r] = Xs[r][c];
+    }
+}
+
+// out (row-major k x k) = the transpose of in (column-major k x k): the same matrix, row-major.
+__global__ void k_cm_to_rm(const double* __restrict__ in, int k, double* __restrict__ out) {
+    const int64_t total = (int64_t)k * k;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e / k), c = (int)(e % k);
+        out[e] = in[(int64_t)c * k + i];
+    }
+}
+
+// U: upper triangle of a column-major k x k array (ld k; below the diagonal
+// unused). Uinv_cm (k x k, column-major) and tmp ((k/2 + kTriLeaf)^2 doubles)
+// are scratch; Uinv_rm receives U^{-1} row-major. The caller holds the cuBLAS
+// handle's lock with its stream set.
+cudaError_t tri_inverse(const double* U, int k, double* Uinv_cm, double* tmp, double* Uinv_rm, cublasHandle_t h,
+                        cudaStream_t s) {
+    if (cudaMemsetAsync(Uinv_cm, 0, sizeof(double) * (size_t)k * k, s) != cudaSuccess) return cudaErrorUnknown;
+    const int nleaf = ceil_div(k, kTriLeaf);
+    k_tri_inv_leaf<<<nleaf, kTriLeaf, 0, s>>>(U, k, Uinv_cm);
+    // merge blocks of width w into blocks of width 2w, bottom-up
+    const double one = 1.0, zero = 0.0, mone = -1.0;
+    for (int w = kTriLeaf; w < k; w *= 2) {
+        for (int o1 = 0; o1 + w < k; o1 += 2 * w) {
+            const int b1 = w, o2 = o1 + w, b2 = min(w, k - o2);
+            // tmp (b1 x b2, ld b1) = A^{-1} B
+            if (cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, b1, b2, b1, &one, Uinv_cm + o1 + (int64_t)o1 * k, k,
+                            U + o1 + (int64_t)o2 * k, k, &zero, tmp, b1) != CUBLAS_STATUS_SUCCESS)
+                return cudaErrorUnknown;
+            // U^{-1}(o1, o2) = -tmp C^{-1}
+            if (cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, b1, b2, b2, &mone, tmp, b1, Uinv_cm + o2 + (int64_t)o2 * k,
+                            k, &zero, Uinv_cm + o1 + (int64_t)o2 * k, k) != CUBLAS_STATUS_SUCCESS)
+                return cudaErrorUnknown;
+        }
+    }
+    k_cm_to_rm<<<grid_for((int64_t)k * k), kRThreads, 0, s>>>(Uinv_cm, k, Uinv_rm);
+    return cudaGetLastError();
+}
+
 // Steps 1-4 shared by the refinement and the backward pass: C = A[:, J],
 // G = C^T C (double-float), G = U^T U (FP64, flag[0] = 1 if not positive
-// definite), U^{-1} in FP64 (row-major k x k).
+// definite), U^{-1} in FP64 (row-major k x k) by the blocked inverse (Gp and
+// Wa's second half are its scratch).
 void factor_skeleton(const float* A, int64_t m, int64_t n, int64_t lda, int k, const int32_t* J, float* C32,
-                     double* Gp, double* Wa, double* Uinv64, double* gdiag, int* flag, cudaStream_t s) {
+                     double* Gp, double* Wa, double* Uinv64, double* gdiag, int* flag, cublasHandle_t h,
+                     cudaStream_t s) {
     k_check_j<<<1, kRThreads, 0, s>>>(J, k, n, flag);
     k_gather<<<grid_for(m * k), kRThreads, 0, s>>>(A, lda, (int)m, k, n, J, C32);
     const int nt = ceil_div(k, kGT);
     const int rows_per = (int)round_up(ceil_div(m, kGramSplit), kGK);
     k_gram<<<dim3(nt, nt, kGramSplit), 256, 0, s>>>(C32, (int)m, k, rows_per, Gp);
     k_gram_sum<<<grid_for((int64_t)k * k), kRThreads, 0, s>>>(Gp, kGramSplit, k, Wa, gdiag);
-    k_identity_half<<<grid_for((int64_t)k * k), kRThreads, 0, s>>>(Wa, k);
     for (int p0 = 0; p0 < k; p0 += kCholB) {
         const int b = k - p0 < kCholB ? k - p0 : kCholB;
         k_chol_diag<<<1, 256, 0, s>>>(Wa, k, p0, b, gdiag, flag);
@@ -541,7 +599,7 @@ void factor_skeleton(const float* A, int64_t m, int64_t n, int64_t lda, int k, c
             k_chol_update<<<dim3(nt2, nt2), kRThreads, 0, s>>>(Wa, k, p0, b, k);
         }
     }
-    solve_run<double>(Wa, k, k, 2 * k, Uinv64, k, s);
+    tri_inverse(Wa, k, Wa + (size_t)k * k, Gp, Uinv64, h, s);
 }
 
 }  // namespace
@@ -599,7 +657,7 @@ int refine_run(const float* A, int64_t m, int64_t n, int64_t lda, int k, const i
     if (cublasSetWorkspace(h, base + L.cws, kCublasWs) != CUBLAS_STATUS_SUCCESS) return ID_ECUDA;
     if (cudaMemsetAsync(flag, 0, 16, s) != cudaSuccess) return ID_ECUDA;
     const int tr = trace_begin(TraceKind::kRefine, s);
-    factor_skeleton(A, m, n, lda, k, J, C32, Gp, Wa, Uinv64, reinterpret_cast<double*>(base + L.gdiag), flag, s);
+    factor_skeleton(A, m, n, lda, k, J, C32, Gp, Wa, Uinv64, reinterpret_cast<double*>(base + L.gdiag), flag, h, s);
     if (cudaGetLastError() != cudaSuccess) return ID_ECUDA;
     k_to_f32<<<grid_for((int64_t)k * k), kRThreads, 0, s>>>(Uinv64, Uinv32, (int64_t)k * k);
     // 5. H = C^T (A - C Z), by column blocks. Column-major views: A row-major
@@ -696,7 +754,7 @@ int backward_run(const float* A, int64_t m, int64_t n, int64_t lda, int k, const
     if (cudaMemsetAsync(flag, 0, 16, s) != cudaSuccess) return ID_ECUDA;
     if (cudaMemsetAsync(mask, 0, (size_t)n, s) != cudaSuccess) return ID_ECUDA;
     const int tr = trace_begin(TraceKind::kRefine, s);
-    factor_skeleton(A, m, n, lda, k, J, C32, Gp, Wa, Uinv64, reinterpret_cast<double*>(base + L.gdiag), flag, s);
+    factor_skeleton(A, m, n, lda, k, J, C32, Gp, Wa, Uinv64, reinterpret_cast<double*>(base + L.gdiag), flag, h, s);
     k_mask_j<<<1, kRThreads, 0, s>>>(J, k, n, mask);
     dim3 g2(ceil_div(n, kRThreads) < 1024 ? ceil_div(n, kRThreads) : 1024, k);
     k_gz<<<g2, kRThreads, 0, s>>>(dZ, lddz, k, (int)n, mask, G64);
@@ -931,7 +989,9 @@ int sampled_z_run(const void* Av, int64_t m, int64_t n, int64_t lda, int k, cons
     if (sizeof(T) == 8) {
         const double* A64 = reinterpret_cast<const double*>(Av);
         k_rk_identity<T><<<grid_for((int64_t)2 * k * k), kRThreads, 0, s>>>(static_cast<const T*>(W), ldw, k, Wa);
-        if (solve_run<double>(Wa, k, k, 2 * k, Uinv64, k, s) != cudaSuccess) return ID_ECUDA;
+        if (tri_inverse(Wa, k, Wa + (size_t)k * k, reinterpret_cast<double*>(base + L.Gp), Uinv64, h, s) !=
+            cudaSuccess)
+            return ID_ECUDA;
         k_gather_f64<T><<<grid_for(m * k), kRThreads, 0, s>>>(A, lda, (int)m, k, J, C64);
         // B = C^T A: B^T (n x k) = A^T (n x m) C (m x k); row-major arrays read as column-major transposes
         if (cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_T, (int)n, k, (int)m, &one, A64, (int)lda, C64, k, &zero, B64,
@@ -941,7 +1001,7 @@ int sampled_z_run(const void* Av, int64_t m, int64_t n, int64_t lda, int k, cons
         float* C32 = reinterpret_cast<float*>(base + L.C32);
         factor_skeleton(reinterpret_cast<const float*>(A), m, n, lda, k, J, C32,
                         reinterpret_cast<double*>(base + L.Gp), Wa, Uinv64, reinterpret_cast<double*>(base + L.gdiag),
-                        flag, s);
+                        flag, h, s);
         k_ctb<<<dim3(ceil_div(n, kGT), ceil_div(k, kGT)), 256, 0, s>>>(C32, reinterpret_cast<const float*>(A), lda,
                                                                        (int)m, k, (int)n, B64);
     }
