@@ -26,6 +26,8 @@ Interpolative Decomposition", arXiv 2105.07076):
   used by the randomized variant (``ls_interp``) and by the refinement of T.
 * Sec. 1.2 footnote: the two-sided ID X^T A[I, J] Z, built from a column ID and
   a row ID of its skeleton (``two_sided_interp_decomp``).
+* Sec. 3 (sparse test matrices): a CSR input is the dense matrix of its
+  entries, duplicates summed (``csr_to_dense``); its ID is interp_decomp's.
 
 Readings where the paper is silent (each listed again in the design doc):
 * pivot = column of largest residual 2-norm over the not-yet-chosen columns;
