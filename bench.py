@@ -151,6 +151,24 @@ def dist_setup():
     return world, rank, local
 
 
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The largest of the ranks' values (the slowest rank's time): an all-reduce MAX."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.item()
+
+
+def aggregate_rate(ms_slowest: float, world: int) -> float:
+    """Whole-job IDs/s of independent replicas: every rank decomposes one matrix
+    per step and the job's step lasts as long as its slowest rank's."""
+    return world * 1000.0 / ms_slowest
+
+
 def make_input(device, dtype):
     import torch
 
@@ -759,11 +777,7 @@ def run_gbid(args):
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
-        mean_ms = statistics.mean(ms)
-        t = torch.tensor([mean_ms], device=dev)
-        if world > 1:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        mean_ms = t.item()
+        mean_ms = max_over_ranks(statistics.mean(ms), world, dev)
         err = rel_error_gpu(A, J, Z)
         cp_ms, cp_n = tr.get("cpqr", (0.0, 0))
         cp_avg = cp_ms / cp_n if cp_n else float("nan")
@@ -782,15 +796,12 @@ def run_gbid(args):
                     "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured"
                     else "fallback"}
         eff = (flops_cpqr(M, N, K_RANK) + flops_solve(N, K_RANK)) / (mean_ms * 1e-3) / 1e12
-        results[name] = {"ms_per_step": mean_ms, "value": world * 1000.0 / mean_ms, "eff_tflops": eff,
+        results[name] = {"ms_per_step": mean_ms, "value": aggregate_rate(mean_ms, world), "eff_tflops": eff,
                          "rel_err": err, "status": info["status_name"], "roofline": roof,
                          "solve_ms": (tr.get("solve", (0.0, 1))[0] / max(tr.get("solve", (0, 1))[1], 1)),
                          "launches_per_step": gbid.launch_count(dt, M, N, K_RANK), "A": A}
     e2e_v, h2d, d2h = e2e_rate(gbid, results["f64"]["A"], max(2, min(args.steps, 5)))
-    if world > 1:
-        t = torch.tensor([1.0 / e2e_v], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_v = world / t.item()
+    e2e_v = aggregate_rate(max_over_ranks(1000.0 / e2e_v, world, dev), world)
 
     samp = sampled_block(gbid, dev, max(3, min(args.steps, 10)), {n: r["A"] for n, r in results.items()}) \
         if args.only in ("all", "sampled") else None
