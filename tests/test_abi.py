@@ -53,6 +53,18 @@ def test_workspace_size_rules(gbid):
     assert L.id_workspace_size(0, 10, 20, 11, None) == 0     # k > min(m, n)
     assert L.id_workspace_size(7, 10, 20, 5, None) == 0      # bad dtype
     assert L.id_cpqr_workspace_size(0, 10, 20, 12, 5, None) == 0   # ldx not a multiple of 8
+    # empty matrices have no ID
+    assert L.id_workspace_size(0, 0, 20, 1, None) == 0
+    assert L.id_workspace_size(0, 10, 0, 1, None) == 0
+    assert L.id_sampled_workspace_size(0, 10, 20, 0, 0, None) == 0
+    assert L.id_two_sided_workspace_size(1, 0, 0, 1, None) == 0
+    assert L.id_csr_workspace_size(0, 0, 20, 1, None) == 0
+    assert L.id_reconstruct_workspace_size(0, 10, 20, 0, 0) == 0
+    # the size limits: k <= 16384, the long side <= 2048 * 256, the short side <= 65536
+    assert L.id_workspace_size(1, 16, 2048 * 256, 8, None) > 0
+    assert L.id_workspace_size(1, 16, 2048 * 256 + 1, 8, None) == 0
+    assert L.id_workspace_size(1, 65537, 65537, 8, None) == 0
+    assert L.id_workspace_size(1, 20000, 20000, 16385, None) == 0
 
 
 def test_argument_errors_return_before_any_launch(gbid):
