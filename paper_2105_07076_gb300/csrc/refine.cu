@@ -22,6 +22,7 @@
 // cuBLAS runs only the plain GEMMs of step 5 and 6; it gets its workspace
 // from the caller's, so nothing is allocated per call (one handle per device
 // is created on first use).
+#include <cublasLt.h>
 #include <cublas_v2.h>
 #include <cuda_runtime.h>
 #include <float.h>
@@ -619,6 +620,51 @@ cublasHandle_t cublas_handle() {
     return h;
 }
 
+std::map<int, cublasLtHandle_t> g_lt;
+std::mutex g_lt_mu;   // its own lock: callers may already hold g_cb_mu
+
+cublasLtHandle_t lt_handle() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    std::lock_guard<std::mutex> lk(g_lt_mu);
+    auto it = g_lt.find(dev);
+    if (it != g_lt.end()) return it->second;
+    cublasLtHandle_t h = nullptr;
+    if (cublasLtCreate(&h) != CUBLAS_STATUS_SUCCESS) return nullptr;
+    g_lt[dev] = h;
+    return h;
+}
+
+// D = alpha A B + beta C with C and D separate (column-major, no transposes;
+// A M x K, B K x N, C and D M x N), FP32 compute emulated on the BF16 tensor
+// cores. False when cuBLASLt does not take it; the caller then falls back.
+bool sgemm_dc(cublasLtHandle_t lt, int M, int N, int K, float alpha, const float* A, int lda, const float* B, int ldb,
+              float beta, const float* C, int ldc, float* D, int ldd, void* ws, size_t ws_bytes, cudaStream_t s) {
+    if (!lt) return false;
+    cublasLtMatmulDesc_t op = nullptr;
+    cublasLtMatrixLayout_t la = nullptr, lb = nullptr, lc = nullptr, ld = nullptr;
+    cublasLtMatmulPreference_t pref = nullptr;
+    const cublasStatus_t S = CUBLAS_STATUS_SUCCESS;
+    bool ok = cublasLtMatmulDescCreate(&op, CUBLAS_COMPUTE_32F_EMULATED_16BFX9, CUDA_R_32F) == S &&
+              cublasLtMatrixLayoutCreate(&la, CUDA_R_32F, M, K, lda) == S &&
+              cublasLtMatrixLayoutCreate(&lb, CUDA_R_32F, K, N, ldb) == S &&
+              cublasLtMatrixLayoutCreate(&lc, CUDA_R_32F, M, N, ldc) == S &&
+              cublasLtMatrixLayoutCreate(&ld, CUDA_R_32F, M, N, ldd) == S && cublasLtMatmulPreferenceCreate(&pref) == S &&
+              cublasLtMatmulPreferenceSetAttribute(pref, CUBLASLT_MATMUL_PREF_MAX_WORKSPACE_BYTES, &ws_bytes,
+                                                   sizeof(ws_bytes)) == S;
+    cublasLtMatmulHeuristicResult_t res;
+    int nres = 0;
+    ok = ok && cublasLtMatmulAlgoGetHeuristic(lt, op, la, lb, lc, ld, pref, 1, &res, &nres) == S && nres > 0;
+    ok = ok && cublasLtMatmul(lt, op, &alpha, A, la, B, lb, &beta, C, lc, D, ld, &res.algo, ws, ws_bytes, s) == S;
+    if (pref) cublasLtMatmulPreferenceDestroy(pref);
+    if (ld) cublasLtMatrixLayoutDestroy(ld);
+    if (lc) cublasLtMatrixLayoutDestroy(lc);
+    if (lb) cublasLtMatrixLayoutDestroy(lb);
+    if (la) cublasLtMatrixLayoutDestroy(la);
+    if (op) cublasLtMatmulDescDestroy(op);
+    return ok;
+}
+
 // FP32-accurate GEMM (column-major arguments as cuBLAS takes them).
 bool sgemm(cublasHandle_t h, cublasOperation_t ta, cublasOperation_t tb, int M, int N, int K, float alpha,
            const float* A, int lda, const float* B, int ldb, float beta, float* C, int ldc) {
@@ -662,14 +708,19 @@ int refine_run(const float* A, int64_t m, int64_t n, int64_t lda, int k, const i
     k_to_f32<<<grid_for((int64_t)k * k), kRThreads, 0, s>>>(Uinv64, Uinv32, (int64_t)k * k);
     // 5. H = C^T (A - C Z), by column blocks. Column-major views: A row-major
     //    m x n is A^T (n x m, ld lda); Z is Z^T (n x k, ld ldz); C is C^T (k x m, ld k).
+    cublasLtHandle_t lt = lt_handle();
     for (int64_t b0 = 0; b0 < n; b0 += kResCols) {
         const int nb = (int)(n - b0 < kResCols ? n - b0 : kResCols);
-        if (cudaMemcpy2DAsync(Rb, (size_t)nb * 4, A + b0, (size_t)lda * 4, (size_t)nb * 4, (size_t)m,
-                              cudaMemcpyDeviceToDevice, s) != cudaSuccess)
-            return ID_ECUDA;
-        // R_b^T (nb x m) -= Z_b^T (nb x k) C^T (k x m)
-        if (!sgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, nb, (int)m, k, -1.0f, Z + b0, (int)ldz, C32, k, 1.0f, Rb, nb))
-            return ID_ECUDA;
+        // R_b^T (nb x m) = A_b^T - Z_b^T (nb x k) C^T (k x m): straight from A when cuBLASLt takes the
+        // separate input C, else a copy of A_b and an in-place GEMM
+        if (!sgemm_dc(lt, nb, (int)m, k, -1.0f, Z + b0, (int)ldz, C32, k, 1.0f, A + b0, (int)lda, Rb, nb,
+                      base + L.cws, kCublasWs, s)) {
+            if (cudaMemcpy2DAsync(Rb, (size_t)nb * 4, A + b0, (size_t)lda * 4, (size_t)nb * 4, (size_t)m,
+                                  cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+                return ID_ECUDA;
+            if (!sgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, nb, (int)m, k, -1.0f, Z + b0, (int)ldz, C32, k, 1.0f, Rb, nb))
+                return ID_ECUDA;
+        }
         // H_b^T (nb x k) = R_b^T (nb x m) C (m x k)
         if (!sgemm(h, CUBLAS_OP_N, CUBLAS_OP_T, nb, k, (int)m, 1.0f, Rb, nb, C32, k, 0.0f, H + b0, (int)n))
             return ID_ECUDA;
@@ -772,13 +823,17 @@ int backward_run(const float* A, int64_t m, int64_t n, int64_t lda, int k, const
     if (!sgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, (int)n, (int)m, k, 1.0f, W32, (int)n, C32, k, 0.0f, dA, (int)ldda))
         return ID_ECUDA;
     // dC = sum_b R_b W_b^T: dC^T (k x m, ld k) += W_b (k x nb) R_b^T (nb x m)
+    cublasLtHandle_t lt = lt_handle();
     for (int64_t b0 = 0; b0 < n; b0 += kResCols) {
         const int nb = (int)(n - b0 < kResCols ? n - b0 : kResCols);
-        if (cudaMemcpy2DAsync(Rb, (size_t)nb * 4, A + b0, (size_t)lda * 4, (size_t)nb * 4, (size_t)m,
-                              cudaMemcpyDeviceToDevice, s) != cudaSuccess)
-            return ID_ECUDA;
-        if (!sgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, nb, (int)m, k, -1.0f, Z + b0, (int)ldz, C32, k, 1.0f, Rb, nb))
-            return ID_ECUDA;
+        if (!sgemm_dc(lt, nb, (int)m, k, -1.0f, Z + b0, (int)ldz, C32, k, 1.0f, A + b0, (int)lda, Rb, nb,
+                      base + L.cws, kCublasWs, s)) {
+            if (cudaMemcpy2DAsync(Rb, (size_t)nb * 4, A + b0, (size_t)lda * 4, (size_t)nb * 4, (size_t)m,
+                                  cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+                return ID_ECUDA;
+            if (!sgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, nb, (int)m, k, -1.0f, Z + b0, (int)ldz, C32, k, 1.0f, Rb, nb))
+                return ID_ECUDA;
+        }
         if (!sgemm(h, CUBLAS_OP_T, CUBLAS_OP_N, k, (int)m, nb, 1.0f, W32 + b0, (int)n, Rb, nb, b0 == 0 ? 0.0f : 1.0f,
                    dC, k))
             return ID_ECUDA;
