@@ -635,19 +635,24 @@ cublasLtHandle_t lt_handle() {
     return h;
 }
 
-// D = alpha A B + beta C with C and D separate (column-major, no transposes;
-// A M x K, B K x N, C and D M x N), FP32 compute emulated on the BF16 tensor
-// cores. False when cuBLASLt does not take it; the caller then falls back.
-bool sgemm_dc(cublasLtHandle_t lt, int M, int N, int K, float alpha, const float* A, int lda, const float* B, int ldb,
-              float beta, const float* C, int ldc, float* D, int ldd, void* ws, size_t ws_bytes, cudaStream_t s) {
+// D = alpha op(A) op(B) + beta C, C and D may be separate (column-major;
+// op(A) M x K, op(B) K x N, C and D M x N), FP32 compute emulated on the BF16
+// tensor cores, through cuBLASLt with an explicit workspace. False when
+// cuBLASLt does not take it; the caller then falls back.
+bool sgemm_lt(cublasLtHandle_t lt, cublasOperation_t ta, cublasOperation_t tb, int M, int N, int K, float alpha,
+              const float* A, int lda, const float* B, int ldb, float beta, const float* C, int ldc, float* D, int ldd,
+              void* ws, size_t ws_bytes, cudaStream_t s) {
     if (!lt) return false;
     cublasLtMatmulDesc_t op = nullptr;
     cublasLtMatrixLayout_t la = nullptr, lb = nullptr, lc = nullptr, ld = nullptr;
     cublasLtMatmulPreference_t pref = nullptr;
     const cublasStatus_t S = CUBLAS_STATUS_SUCCESS;
+    const bool tA = ta == CUBLAS_OP_T, tB = tb == CUBLAS_OP_T;
     bool ok = cublasLtMatmulDescCreate(&op, CUBLAS_COMPUTE_32F_EMULATED_16BFX9, CUDA_R_32F) == S &&
-              cublasLtMatrixLayoutCreate(&la, CUDA_R_32F, M, K, lda) == S &&
-              cublasLtMatrixLayoutCreate(&lb, CUDA_R_32F, K, N, ldb) == S &&
+              cublasLtMatmulDescSetAttribute(op, CUBLASLT_MATMUL_DESC_TRANSA, &ta, sizeof(ta)) == S &&
+              cublasLtMatmulDescSetAttribute(op, CUBLASLT_MATMUL_DESC_TRANSB, &tb, sizeof(tb)) == S &&
+              cublasLtMatrixLayoutCreate(&la, CUDA_R_32F, tA ? K : M, tA ? M : K, lda) == S &&
+              cublasLtMatrixLayoutCreate(&lb, CUDA_R_32F, tB ? N : K, tB ? K : N, ldb) == S &&
               cublasLtMatrixLayoutCreate(&lc, CUDA_R_32F, M, N, ldc) == S &&
               cublasLtMatrixLayoutCreate(&ld, CUDA_R_32F, M, N, ldd) == S && cublasLtMatmulPreferenceCreate(&pref) == S &&
               cublasLtMatmulPreferenceSetAttribute(pref, CUBLASLT_MATMUL_PREF_MAX_WORKSPACE_BYTES, &ws_bytes,
@@ -713,7 +718,7 @@ int refine_run(const float* A, int64_t m, int64_t n, int64_t lda, int k, const i
         const int nb = (int)(n - b0 < kResCols ? n - b0 : kResCols);
         // R_b^T (nb x m) = A_b^T - Z_b^T (nb x k) C^T (k x m): straight from A when cuBLASLt takes the
         // separate input C, else a copy of A_b and an in-place GEMM
-        if (!sgemm_dc(lt, nb, (int)m, k, -1.0f, Z + b0, (int)ldz, C32, k, 1.0f, A + b0, (int)lda, Rb, nb,
+        if (!sgemm_lt(lt, CUBLAS_OP_N, CUBLAS_OP_N, nb, (int)m, k, -1.0f, Z + b0, (int)ldz, C32, k, 1.0f, A + b0, (int)lda, Rb, nb,
                       base + L.cws, kCublasWs, s)) {
             if (cudaMemcpy2DAsync(Rb, (size_t)nb * 4, A + b0, (size_t)lda * 4, (size_t)nb * 4, (size_t)m,
                                   cudaMemcpyDeviceToDevice, s) != cudaSuccess)
@@ -826,7 +831,7 @@ int backward_run(const float* A, int64_t m, int64_t n, int64_t lda, int k, const
     cublasLtHandle_t lt = lt_handle();
     for (int64_t b0 = 0; b0 < n; b0 += kResCols) {
         const int nb = (int)(n - b0 < kResCols ? n - b0 : kResCols);
-        if (!sgemm_dc(lt, nb, (int)m, k, -1.0f, Z + b0, (int)ldz, C32, k, 1.0f, A + b0, (int)lda, Rb, nb,
+        if (!sgemm_lt(lt, CUBLAS_OP_N, CUBLAS_OP_N, nb, (int)m, k, -1.0f, Z + b0, (int)ldz, C32, k, 1.0f, A + b0, (int)lda, Rb, nb,
                       base + L.cws, kCublasWs, s)) {
             if (cudaMemcpy2DAsync(Rb, (size_t)nb * 4, A + b0, (size_t)lda * 4, (size_t)nb * 4, (size_t)m,
                                   cudaMemcpyDeviceToDevice, s) != cudaSuccess)
