@@ -232,18 +232,20 @@ __global__ void __launch_bounds__(256) k_ctb(const float* __restrict__ C, const 
 __global__ void __launch_bounds__(256) k_chol_diag(double* G, int ld, int p0, int b, const double* gdiag,
                                                    int* flag) {
     __shared__ double D[kCholB][kCholB + 1];
+    __shared__ double gd[kCholB];   // the block's original diagonal, loaded once (not per step)
     __shared__ double rj_s;
     const int t = threadIdx.x;
     for (int e = t; e < kCholB * kCholB; e += blockDim.x) {
         const int r = e / kCholB, c = e % kCholB;
         D[r][c] = (c < b && r <= c) ? G[(int64_t)(p0 + c) * ld + p0 + r] : 0.0;
     }
+    if (t < b) gd[t] = gdiag[p0 + t];
     __syncthreads();
     for (int j = 0; j < b; ++j) {
         if (t == 0) {
             const double d = D[j][j];
             double u = 1.0;
-            if (!(d > 64.0 * DBL_EPSILON * gdiag[p0 + j]) || !isfinite(d)) {
+            if (!(d > 64.0 * DBL_EPSILON * gd[j]) || !isfinite(d)) {
                 if (flag[0] == 0) flag[0] = 1;
             } else {
                 u = sqrt(d);
