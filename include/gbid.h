@@ -96,7 +96,14 @@ typedef struct {
     int32_t nb;           /* panel width actually used                            */
     int32_t refined;      /* 1 when a least-squares refinement was applied to Z   */
     int32_t engine;       /* 1 persistent grid CPQR, 2 cluster, 3 batched kernel  */
-    int32_t reserved[3];
+    int32_t reserved0;
+    /* ||A - C Z||_F / ||A||_F of a deterministic ID, from the CPQR's residual
+     * column norms: with Z P = [I R11^{-1} R12] the residual is Q2 R22
+     * (Sec. 2.1), whose Frobenius norm is that of the columns left after k
+     * steps. Filled by id_decompose on the grid engine and by id_decompose_csr
+     * (relative accuracy about that of the norm downdate, ~1e-6); 0 for an ID
+     * of a k x k matrix; -1 where it is not computed. */
+    double  err_est;
 } id_info;
 
 /* Bytes of device workspace id_decompose needs for this problem (k <= 16384).

@@ -48,13 +48,14 @@ class IdInfo(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("rank", ctypes.c_int32), ("transposed", ctypes.c_int32),
                 ("n_recompute", ctypes.c_int32), ("n_gt2", ctypes.c_int64), ("max_abs_z", ctypes.c_double),
                 ("r00", ctypes.c_double), ("nb", ctypes.c_int32), ("refined", ctypes.c_int32),
-                ("engine", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("engine", ctypes.c_int32), ("reserved0", ctypes.c_int32), ("err_est", ctypes.c_double)]
 
     def as_dict(self):
         return {"status": self.status, "status_name": STATUS_NAMES.get(self.status, str(self.status)),
                 "rank": self.rank, "transposed": bool(self.transposed), "n_recompute": self.n_recompute,
                 "n_gt2": self.n_gt2, "max_abs_z": self.max_abs_z, "r00": self.r00, "nb": self.nb,
-                "refined": bool(self.refined), "engine": ENGINE_NAMES.get(self.engine, self.engine)}
+                "refined": bool(self.refined), "engine": ENGINE_NAMES.get(self.engine, self.engine),
+                "err_est": self.err_est}
 
 
 # Return codes that mean the call itself failed; device-detected conditions

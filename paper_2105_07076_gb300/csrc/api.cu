@@ -183,6 +183,7 @@ int decompose_impl(const void* A, int64_t m, int64_t n, int64_t lda, int64_t k, 
     if (cpqr_run<T>(P, s) != cudaSuccess) return ID_ECUDA;
     if (zs) {   // the paper's route: J = P_k, then R_k^T R_k Z = C^T A against A (m <= n here)
         if (finalize_info(P.st, dinfo, (int)k, 0, P.nb, s) != cudaSuccess) return ID_ECUDA;
+        if (error_estimate(P.vn1, (int)k, nx, P.st, dinfo, s) != cudaSuccess) return ID_ECUDA;
         if (sample_map_j(P.perm, nullptr, (int)k, J, s) != cudaSuccess) return ID_ECUDA;
         const int rc = sampled_z_run<T>(A, m, n, lda, (int)k, J, P.W, P.ldw, Z, ldz, base + L.total, dinfo, s);
         if (rc != ID_OK) return rc;
@@ -194,6 +195,7 @@ int decompose_impl(const void* A, int64_t m, int64_t n, int64_t lda, int64_t k, 
     if (solve_run<T>(P.W, P.ldw, (int)k, nx, Tm, ldt, s) != cudaSuccess) return ID_ECUDA;
     if (scatter_z<T>(P.perm, Tm, ldt, (int)k, nx, Z, ldz, J, dinfo, s) != cudaSuccess) return ID_ECUDA;
     if (finalize_info(P.st, dinfo, (int)k, trans, P.nb, s) != cudaSuccess) return ID_ECUDA;
+    if (error_estimate(P.vn1, (int)k, nx, P.st, dinfo, s) != cudaSuccess) return ID_ECUDA;
     if (info) return read_info(work, info, s);
     return ID_OK;
 }
@@ -256,6 +258,7 @@ int decompose_csr_impl(const int64_t* rowptr, const int32_t* colind, const void*
     if (solve_run<T>(P.W, P.ldw, (int)k, nx, Tm, ldt, s) != cudaSuccess) return ID_ECUDA;
     if (scatter_z<T>(P.perm, Tm, ldt, (int)k, nx, Z, ldz, J, dinfo, s) != cudaSuccess) return ID_ECUDA;
     if (finalize_info(P.st, dinfo, (int)k, trans, P.nb, s, flag) != cudaSuccess) return ID_ECUDA;
+    if (error_estimate(P.vn1, (int)k, nx, P.st, dinfo, s) != cudaSuccess) return ID_ECUDA;
     if (info) return read_info(work, info, s);
     return ID_OK;
 }
@@ -563,8 +566,8 @@ int64_t id_launch_count(id_dtype dtype, int64_t m, int64_t n, int64_t k, const i
     const bool cl = dtype == ID_F64 ? use_cluster<double>(m, n, k, opts) : use_cluster<float>(m, n, k, opts);
     if (cl) return 2;   // the cluster kernel and its statistics kernel
     const int64_t nx = m > n ? m : n;
-    // copy-in, persistent CPQR, back substitution (when n > k), Z scatter, status
-    return 4 + (nx > k ? 1 : 0);
+    // copy-in, persistent CPQR, back substitution (when n > k), Z scatter, status, error estimate
+    return 5 + (nx > k ? 1 : 0);
 }
 
 size_t id_reconstruct_workspace_size(id_dtype dtype, int64_t m, int64_t n, int64_t k, int32_t transposed) {

@@ -253,6 +253,7 @@ __global__ void __launch_bounds__(kBThreads, 3) k_id_batched(const id_problem* _
             if (t == 0) {
                 id_info r = {};
                 r.status = ID_EINVAL;
+                r.err_est = -1.0;
                 infos[b] = r;
             }
             continue;
@@ -495,6 +496,7 @@ __global__ void __launch_bounds__(kBThreads, 3) k_id_batched(const id_problem* _
             r.r00 = r00;
             r.nb = 1;
             r.engine = 3;
+            r.err_est = -1.0;
             infos[b] = r;
         }
     }

@@ -416,6 +416,7 @@ __global__ void __launch_bounds__(kCThreads, 1) k_id_cluster(const T* __restrict
         res.r00 = r00;
         res.nb = 0;
         res.engine = 2;
+        res.err_est = -1.0;
         dinfo->info = res;
     }
 }

@@ -66,6 +66,7 @@ struct State {
     double scale;       // 1 / (x_0 - beta): scales x into v with v_0 = 1
     double r00;         // |R_00|
     double rank_tol;    // sqrt(max(m, n)) * eps(working precision)
+    double fro2;        // ||X||_F^2 from the initial column norms
 };
 
 // Device copy of id_info kept in the workspace.

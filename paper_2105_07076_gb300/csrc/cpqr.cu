@@ -413,6 +413,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
             st->rank_tol = P.rank_tol;
         }
         ArgMax best = empty_argmax();
+        double fro = 0.0;   // this thread's share of ||X||_F^2 (lane 0 of each warp)
         for (int l = blockIdx.x * NW + w; l < n; l += G * NW) {
             const T* col = W + (int64_t)l * ldw;
             double s = 0.0;
@@ -421,6 +422,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
                 s = fma(x, x, s);
             }
             s = warp_sum(s);
+            if (lane == 0) fro += s;
             if (lane == 0) {
                 const double nu = sqrt(s);
                 P.vn1[l] = nu;
@@ -436,6 +438,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
         }
         best = block_argmax(best);
         if (t == 0) P.part[blockIdx.x] = best;
+        fro = block_sum(fro);
+        if (t == 0) atomicAdd(&st->fro2, fro);
     }
     grid_sync(P.bar, epoch, st);
 

@@ -60,6 +60,8 @@ int sketch_run(const float* A, int64_t m, int64_t n, int64_t lda, const uint16_t
                int64_t ldy, int* status, cudaStream_t s);
 cudaError_t finalize_info(const State* st, DevInfo* info, int k, int transposed, int nb, cudaStream_t s,
                           const int* extra_status = nullptr);
+// info->err_est from the CPQR's residual column norms (after finalize_info).
+cudaError_t error_estimate(const double* vn1, int k, int n, const State* st, DevInfo* info, cudaStream_t s);
 
 // One least-squares refinement of Z against A (refine.cu). Returns an id_status;
 // updates info->info.refined and the Z statistics.

@@ -388,6 +388,7 @@ __global__ void k_info_init(DevInfo* d, int k) {
     DevInfo z = {};
     z.info.status = ID_OK;
     z.info.rank = k;
+    z.info.err_est = -1.0;
     *d = z;
 }
 
@@ -907,6 +908,7 @@ __global__ void k_identity_id(int32_t* idx, T* Zx, int64_t ldz, int k, DevInfo* 
         z.rank = k;
         z.max_abs_z = 1.0;
         z.engine = 1;
+        z.err_est = 0.0;   // an ID of a k x k matrix is exact
         info->info = z;
     }
 }
@@ -922,6 +924,7 @@ template cudaError_t identity_id<float>(int32_t*, void*, int64_t, int, DevInfo*,
 __global__ void k_recon_finalize(DevInfo* info, const int* flag) {
     id_info r = {};
     r.status = flag[0] == 2 ? ID_EINVAL : ID_OK;
+    r.err_est = -1.0;
     info->info = r;
 }
 

@@ -227,6 +227,7 @@ __global__ void k_finalize(const State* st, DevInfo* info, int k, int transposed
     r.transposed = transposed;
     r.nb = nb;
     r.engine = 1;
+    r.err_est = -1.0;
     r.n_gt2 = (int64_t)info->n_gt2;
     r.max_abs_z = __longlong_as_double((long long)info->max_abs_z_bits);
     if (status & kStatBadInput) r.status = ID_EINVAL;
@@ -240,6 +241,28 @@ __global__ void k_finalize(const State* st, DevInfo* info, int k, int transposed
 cudaError_t finalize_info(const State* st, DevInfo* info, int k, int transposed, int nb, cudaStream_t s,
                           const int* extra_status) {
     k_finalize<<<1, 1, 0, s>>>(st, info, k, transposed, nb, extra_status);
+    return cudaGetLastError();
+}
+
+// err_est = sqrt(sum of the residual column norms^2 over positions k..n-1) / ||X||_F.
+__global__ void __launch_bounds__(256) k_err_est(const double* __restrict__ vn1, int k, int n, const State* st,
+                                                 DevInfo* info) {
+    double s = 0.0;
+    for (int l = k + threadIdx.x; l < n; l += blockDim.x) s = fma(vn1[l], vn1[l], s);
+    __shared__ double red[8];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int w = 0; w < 8; ++w) tot += red[w];
+        const double f = st->fro2;
+        info->info.err_est = f > 0.0 ? sqrt(tot / f) : 0.0;
+    }
+}
+
+cudaError_t error_estimate(const double* vn1, int k, int n, const State* st, DevInfo* info, cudaStream_t s) {
+    k_err_est<<<1, 256, 0, s>>>(vn1, k, n, st, info);
     return cudaGetLastError();
 }
 

@@ -111,7 +111,7 @@ def test_engine_option(gbid):
     assert L.id_launch_count(0, 200, 400, 20, ctypes.byref(cl)) == 2
     assert L.id_launch_count(0, 4096, 8192, 256, ctypes.byref(cl)) == -1
     grid = gbid._opts(0, engine=gbid.ENGINE_GRID)
-    assert L.id_launch_count(0, 200, 400, 20, ctypes.byref(grid)) == 5
+    assert L.id_launch_count(0, 200, 400, 20, ctypes.byref(grid)) == 6
     assert L.id_launch_count(1, 200, 400, 20, None) == 2          # FP32: the default takes the cluster
 
 

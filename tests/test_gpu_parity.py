@@ -272,6 +272,25 @@ def test_host_buffers_entry_point(gbid):
     assert torch.equal(J, Jd.cpu()) and torch.equal(Z, Zd.cpu())
 
 
+# ------------------------------------------------------------ error estimate ---
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("m,n,k,spec", [(300, 700, 40, "poly1.5"), (700, 300, 40, "exp64"), (128, 2000, 64, "poly2")])
+def test_error_estimate(gbid, dtype, m, n, k, spec):
+    """info["err_est"] (grid engine) is ||A - C Z||_F / ||A||_F from the residual column
+    norms: it matches the oracle's error of the GPU's own ID to the accuracy of
+    the norm downdate."""
+    A = synth.lowrank(m, n, synth.spectrum(spec, min(m, n)), 19, dtype=dtype).cuda()
+    J, Z, info = gbid.id_decompose(A, k, engine=gbid.ENGINE_GRID)
+    Ah = A.double().cpu().numpy()
+    tr = m > n
+    err = orc.rel_error(Ah, J.cpu().numpy().astype(np.int64), Z[:, :max(m, n)].double().cpu().numpy(), transposed=tr)
+    assert info["err_est"] == pytest.approx(err, rel=1e-3 if dtype == torch.float64 else 1e-2)
+    if gbid.engine != 2:
+        _, _, ic = gbid.id_decompose(synth.lowrank(200, 400, synth.spectrum("pow2_half", 200), 1).cuda(), 20,
+                                     engine=gbid.ENGINE_CLUSTER)
+        assert ic["err_est"] == -1.0        # not computed by the cluster engine
+
+
 # ------------------------------------------------------------ size limits ---
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
 def test_widest_matrix(gbid, dtype):
@@ -341,6 +360,7 @@ def test_full_size_4096x8192_k256(gbid, c2_inputs, dtype):
     err = np.linalg.norm(Ah - C @ Zg) / np.linalg.norm(Ah)
     tail = synth.tail_bound(synth.spectrum("exp64", 4096), k)
     assert tail * (1 - 1e-6) <= err <= 3.0 * tail, (err, tail)
+    assert info["err_est"] == pytest.approx(err, rel=1e-3)
 
 
 def test_full_size_row_id_of_the_transpose(gbid, c2_inputs):
