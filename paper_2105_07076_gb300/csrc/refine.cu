@@ -584,9 +584,9 @@ cudaError_t tri_inverse(const double* U, int k, double* Uinv_cm, double* tmp, do
 // G = C^T C (double-float), G = U^T U (FP64, flag[0] = 1 if not positive
 // definite), U^{-1} in FP64 (row-major k x k) by the blocked inverse (Gp and
 // Wa's second half are its scratch).
-void factor_skeleton(const float* A, int64_t m, int64_t n, int64_t lda, int k, const int32_t* J, float* C32,
-                     double* Gp, double* Wa, double* Uinv64, double* gdiag, int* flag, cublasHandle_t h,
-                     cudaStream_t s) {
+cudaError_t factor_skeleton(const float* A, int64_t m, int64_t n, int64_t lda, int k, const int32_t* J, float* C32,
+                            double* Gp, double* Wa, double* Uinv64, double* gdiag, int* flag, cublasHandle_t h,
+                            cudaStream_t s) {
     k_check_j<<<1, kRThreads, 0, s>>>(J, k, n, flag);
     k_gather<<<grid_for(m * k), kRThreads, 0, s>>>(A, lda, (int)m, k, n, J, C32);
     const int nt = ceil_div(k, kGT);
@@ -603,7 +603,9 @@ void factor_skeleton(const float* A, int64_t m, int64_t n, int64_t lda, int k, c
             k_chol_update<<<dim3(nt2, nt2), kRThreads, 0, s>>>(Wa, k, p0, b, k);
         }
     }
-    tri_inverse(Wa, k, Wa + (size_t)k * k, Gp, Uinv64, h, s);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return tri_inverse(Wa, k, Wa + (size_t)k * k, Gp, Uinv64, h, s);
 }
 
 }  // namespace
@@ -711,8 +713,9 @@ int refine_run(const float* A, int64_t m, int64_t n, int64_t lda, int k, const i
     if (cublasSetWorkspace(h, base + L.cws, kCublasWs) != CUBLAS_STATUS_SUCCESS) return ID_ECUDA;
     if (cudaMemsetAsync(flag, 0, 16, s) != cudaSuccess) return ID_ECUDA;
     const int tr = trace_begin(TraceKind::kRefine, s);
-    factor_skeleton(A, m, n, lda, k, J, C32, Gp, Wa, Uinv64, reinterpret_cast<double*>(base + L.gdiag), flag, h, s);
-    if (cudaGetLastError() != cudaSuccess) return ID_ECUDA;
+    if (factor_skeleton(A, m, n, lda, k, J, C32, Gp, Wa, Uinv64, reinterpret_cast<double*>(base + L.gdiag), flag, h,
+                        s) != cudaSuccess)
+        return ID_ECUDA;
     k_to_f32<<<grid_for((int64_t)k * k), kRThreads, 0, s>>>(Uinv64, Uinv32, (int64_t)k * k);
     // 5. H = C^T (A - C Z), by column blocks. Column-major views: A row-major
     //    m x n is A^T (n x m, ld lda); Z is Z^T (n x k, ld ldz); C is C^T (k x m, ld k).
@@ -813,7 +816,9 @@ int backward_run(const float* A, int64_t m, int64_t n, int64_t lda, int k, const
     if (cudaMemsetAsync(flag, 0, 16, s) != cudaSuccess) return ID_ECUDA;
     if (cudaMemsetAsync(mask, 0, (size_t)n, s) != cudaSuccess) return ID_ECUDA;
     const int tr = trace_begin(TraceKind::kRefine, s);
-    factor_skeleton(A, m, n, lda, k, J, C32, Gp, Wa, Uinv64, reinterpret_cast<double*>(base + L.gdiag), flag, h, s);
+    if (factor_skeleton(A, m, n, lda, k, J, C32, Gp, Wa, Uinv64, reinterpret_cast<double*>(base + L.gdiag), flag, h,
+                        s) != cudaSuccess)
+        return ID_ECUDA;
     k_mask_j<<<1, kRThreads, 0, s>>>(J, k, n, mask);
     dim3 g2(ceil_div(n, kRThreads) < 1024 ? ceil_div(n, kRThreads) : 1024, k);
     k_gz<<<g2, kRThreads, 0, s>>>(dZ, lddz, k, (int)n, mask, G64);
@@ -1064,9 +1069,10 @@ int sampled_z_run(const void* Av, int64_t m, int64_t n, int64_t lda, int k, cons
             return ID_ECUDA;
     } else {
         float* C32 = reinterpret_cast<float*>(base + L.C32);
-        factor_skeleton(reinterpret_cast<const float*>(A), m, n, lda, k, J, C32,
-                        reinterpret_cast<double*>(base + L.Gp), Wa, Uinv64, reinterpret_cast<double*>(base + L.gdiag),
-                        flag, h, s);
+        if (factor_skeleton(reinterpret_cast<const float*>(A), m, n, lda, k, J, C32,
+                            reinterpret_cast<double*>(base + L.Gp), Wa, Uinv64,
+                            reinterpret_cast<double*>(base + L.gdiag), flag, h, s) != cudaSuccess)
+            return ID_ECUDA;
         k_ctb<<<dim3(ceil_div(n, kGT), ceil_div(k, kGT)), 256, 0, s>>>(C32, reinterpret_cast<const float*>(A), lda,
                                                                        (int)m, k, (int)n, B64);
     }
