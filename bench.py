@@ -431,8 +431,7 @@ def listing_block(gbid, dev, steps, mats):
         J = torch.empty(K_RANK, dtype=torch.int32, device=dev)
         Z = torch.empty(K_RANK, N, dtype=A.dtype, device=dev)
         approx = torch.empty(M, N, dtype=A.dtype, device=dev)
-        rws = gbid.Workspace(torch.empty(gbid.lib().id_reconstruct_workspace_size(gbid._DTYPES[A.dtype], M, N, K_RANK, 0),
-                                         dtype=torch.uint8, device=dev))
+        rws = gbid.reconstruct_workspace(A.dtype, M, N, K_RANK, device=dev)
         for _ in range(3):
             gbid.id_decompose(A, K_RANK, normal_eq=True, workspace=ws, out=(J, Z), sync=False)
             gbid.id_reconstruct(A, J, Z, out=approx, workspace=rws, sync=False)

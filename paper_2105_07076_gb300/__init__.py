@@ -422,6 +422,14 @@ def id_decompose_two_sided(A: torch.Tensor, k: int, *, nb: int = 0, workspace: W
     return I, J, X, Z, ((infos[0].as_dict(), infos[1].as_dict()) if sync else None)
 
 
+def reconstruct_workspace(dtype: torch.dtype, m: int, n: int, k: int, *, transposed: bool = False,
+                          device=None) -> Workspace:
+    nbytes = int(lib().id_reconstruct_workspace_size(_DTYPES[dtype], m, n, k, 1 if transposed else 0))
+    if nbytes == 0:
+        raise IdError(ID_EINVAL, "id_reconstruct_workspace_size")
+    return Workspace(torch.empty(nbytes, dtype=torch.uint8, device=device))
+
+
 def id_reconstruct(A: torch.Tensor, J: torch.Tensor, Z: torch.Tensor, *, transposed: bool = False,
                    out: torch.Tensor | None = None, workspace: Workspace | None = None, sync: bool = True):
     """The ID's approximation of A: A[:, J] @ Z (column ID), or Z.T @ A[J, :]
@@ -433,10 +441,7 @@ def id_reconstruct(A: torch.Tensor, J: torch.Tensor, Z: torch.Tensor, *, transpo
     dev = A.device
     dt = _DTYPES[A.dtype]
     if workspace is None:
-        nbytes = int(lib().id_reconstruct_workspace_size(dt, m, n, k, 1 if transposed else 0))
-        if nbytes == 0:
-            raise IdError(ID_EINVAL, "id_reconstruct_workspace_size")
-        workspace = Workspace(torch.empty(nbytes, dtype=torch.uint8, device=dev))
+        workspace = reconstruct_workspace(A.dtype, m, n, k, transposed=transposed, device=dev)
     Out = torch.empty(m, n, dtype=A.dtype, device=dev) if out is None else out
     info = IdInfo()
     with torch.cuda.device(dev):
