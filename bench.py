@@ -84,7 +84,7 @@ def load_peaks():
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_cpqr launch on this
 # workload, from the ncu capture summarised in profiles/ (bytes per launch).
 # Set to None whenever k_cpqr changes until it is captured again.
-NCU_TRAFFIC = {"f64": 49.64e9, "f32": 11.95e9}
+NCU_TRAFFIC = {"f64": 49.62e9, "f32": 11.95e9}
 
 # FP64 ALU peak: 152 SMs x 2 FP64 FMA per clock x 2 flops x 2.07 GHz (a DFMA
 # microbenchmark on this GPU measured 1.196 TFLOP/s).
