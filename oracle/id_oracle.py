@@ -29,7 +29,7 @@ Interpolative Decomposition", arXiv 2105.07076):
 * Sec. 3 (sparse test matrices): a CSR input is the dense matrix of its
   entries, duplicates summed (``csr_to_dense``); its ID is interp_decomp's.
 
-Readings where the paper is silent (each listed again in the design doc):
+Readings where the paper is silent:
 * pivot = column of largest residual 2-norm over the not-yet-chosen columns;
   exact ties go to the smallest ORIGINAL column index;
 * Householder sign: beta = -sign(x_0) ||x|| with sign(0) = +1, reflector
