@@ -244,14 +244,15 @@ __global__ void __launch_bounds__(256) k_chol_diag(double* G, int ld, int p0, in
     for (int j = 0; j < b; ++j) {
         if (t == 0) {
             const double d = D[j][j];
-            double u = 1.0;
+            double u = 1.0, ru = 1.0;
             if (!(d > 64.0 * DBL_EPSILON * gd[j]) || !isfinite(d)) {
                 if (flag[0] == 0) flag[0] = 1;
             } else {
-                u = sqrt(d);
+                ru = rsqrt(d);   // one reciprocal square root instead of a square root and a division:
+                u = d * ru;      // FP64 runs at 2 lanes per clock per SM, so this chain sets the pace
             }
             D[j][j] = u;
-            rj_s = 1.0 / u;
+            rj_s = ru;
         }
         __syncthreads();
         if (t > j && t < b) D[j][t] *= rj_s;
