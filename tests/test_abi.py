@@ -256,3 +256,24 @@ def test_binding_refuses_cpu_tensors(gbid):
 
     with pytest.raises(ValueError):
         gbid.id_decompose(torch.zeros(4, 8, dtype=torch.float64), 2)
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    """Without the built library the binding raises; there is no CPU fallback."""
+    import subprocess
+    import sys
+
+    code = (
+        "import sys; sys.path.insert(0, %r)\n"
+        "import paper_2105_07076_gb300 as g\n"
+        "g.LIB_PATH = %r\n"
+        "g._lib = None\n"
+        "try:\n"
+        "    g.lib()\n"
+        "except RuntimeError as e:\n"
+        "    print('raised', e)\n"
+        "else:\n"
+        "    print('loaded')\n"
+    ) % (ROOT, str(tmp_path / "libgbid.so"))
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=120)
+    assert "raised" in out.stdout, out.stdout + out.stderr
