@@ -182,6 +182,17 @@ int id_cpqr(void* X, id_dtype dtype, int64_t m, int64_t n, int64_t ldx, int64_t 
             const id_opts* opts, int32_t* perm, double* tau,
             void* work, size_t work_bytes, id_info* info, void* stream);
 
+/* id_cpqr_residual_norms -- after id_cpqr with the same arguments and work:
+ * out[i] (n doubles, device) = the residual 2-norm of the column at position
+ * i >= k after the k steps, ||X(k:m, i)|| of the updated matrix (the norms the
+ * pivot rule compares, kept in FP64 by the CPQR's downdate with exact
+ * recomputes); out[i] for i < k is the residual norm column i had when step i
+ * chose it (|R_ii| in exact arithmetic). The root sum of squares over i >= k
+ * is ||R22||_F, the ID's residual (Sec. 2.1). A stream-ordered copy from the
+ * workspace; returns ID_EINVAL for bad arguments. */
+int id_cpqr_residual_norms(const void* work, id_dtype dtype, int64_t m, int64_t n, int64_t ldx, int64_t k,
+                           const id_opts* opts, double* out, void* stream);
+
 /* id_solve -- T = R11^{-1} R12 by blocked back substitution (Sec. 2.1,
  * equivalent to the normal equations R_k^T R_k Z = C^T A of Eq. final_eq).
  *

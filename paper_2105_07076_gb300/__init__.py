@@ -111,6 +111,7 @@ _SIG = {
                                    ctypes.c_size_t, _P, _P]),
     "id_refine": (ctypes.c_int, [_P, ctypes.c_int, _I64, _I64, _I64, _I64, _P, _P, _I64, _P, ctypes.c_size_t, _P, _P]),
     "id_launch_count": (ctypes.c_int64, [ctypes.c_int, _I64, _I64, _I64, _P]),
+    "id_cpqr_residual_norms": (ctypes.c_int, [_P, ctypes.c_int, _I64, _I64, _I64, _I64, _P, _P, _P]),
     "id_trace_enable": (ctypes.c_int, [ctypes.c_int]),
     "id_trace_read": (ctypes.c_int, [_P, _P, ctypes.c_int]),
     "id_version": (ctypes.c_char_p, []),
@@ -591,12 +592,13 @@ def id_decompose_host(A: torch.Tensor, k: int, *, nb: int = 0, engine: int = ENG
     return J, Z, info.as_dict()
 
 
-def id_cpqr(Xcm: torch.Tensor, m: int, k: int, *, nb: int = 0, workspace: torch.Tensor | None = None):
+def id_cpqr(Xcm: torch.Tensor, m: int, k: int, *, nb: int = 0, workspace: torch.Tensor | None = None,
+            residual_norms: bool = False):
     """k-step CPQR in place of a column-major m x n matrix.
 
     ``Xcm`` is a CUDA tensor of shape (n, ldx): row l holds column l of X (so
-    X = Xcm[:, :m].T), ldx >= m a multiple of 8. Returns (perm, tau, info).
-    """
+    X = Xcm[:, :m].T), ldx >= m a multiple of 8. Returns (perm, tau, info), and
+    with residual_norms=True also the n residual column norms (FP64, by position)."""
     if not Xcm.is_cuda or Xcm.dtype not in _DTYPES or Xcm.dim() != 2 or Xcm.stride(1) != 1:
         raise ValueError("Xcm must be a 2-D contiguous CUDA float32/float64 tensor")
     n, ldx = Xcm.shape[0], Xcm.stride(0)
@@ -616,7 +618,15 @@ def id_cpqr(Xcm: torch.Tensor, m: int, k: int, *, nb: int = 0, workspace: torch.
                            _stream(dev))
     if rc in _CALL_ERRORS:
         raise IdError(rc, "id_cpqr")
-    return perm, tau, info.as_dict()
+    if not residual_norms:
+        return perm, tau, info.as_dict()
+    nu = torch.empty(n, dtype=torch.float64, device=dev)
+    with torch.cuda.device(dev):
+        rc = lib().id_cpqr_residual_norms(workspace.data_ptr(), _DTYPES[Xcm.dtype], m, n, ldx, k, ctypes.byref(o),
+                                          nu.data_ptr(), _stream(dev))
+    if rc != ID_OK:
+        raise IdError(rc, "id_cpqr_residual_norms")
+    return perm, tau, info.as_dict(), nu
 
 
 def id_solve(Xcm: torch.Tensor, k: int) -> torch.Tensor:

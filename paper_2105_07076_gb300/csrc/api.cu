@@ -350,6 +350,18 @@ int id_cpqr(void* X, id_dtype dtype, int64_t m, int64_t n, int64_t ldx, int64_t 
     return cpqr_impl<float>(X, m, n, ldx, k, opts, perm, tau, work, work_bytes, info, s);
 }
 
+int id_cpqr_residual_norms(const void* work, id_dtype dtype, int64_t m, int64_t n, int64_t ldx, int64_t k,
+                           const id_opts* opts, double* out, void* stream) {
+    if (!work || !out) return ID_EINVAL;
+    if (id_cpqr_workspace_size(dtype, m, n, ldx, k, opts) == 0) return ID_EINVAL;
+    const Layout L = make_layout(dtype, (int)m, (int)n, (int)k, opts, false, false, (int)ldx);
+    const char* base = static_cast<const char*>(work);
+    return cudaMemcpyAsync(out, base + L.vn1, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice,
+                           static_cast<cudaStream_t>(stream)) == cudaSuccess
+               ? ID_OK
+               : ID_ECUDA;
+}
+
 int id_solve(const void* X, id_dtype dtype, int64_t n, int64_t ldx, int64_t k, double* T, int64_t ldt, void* stream) {
     if (!X || !T) return ID_EINVAL;
     if (dtype != ID_F64 && dtype != ID_F32) return ID_EINVAL;

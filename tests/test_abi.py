@@ -89,6 +89,11 @@ def test_argument_errors_return_before_any_launch(gbid):
     # id_cpqr: m > n and bad ldx
     assert L.id_cpqr(fake, 0, 30, 20, 32, 5, None, fake, fake, ws, 1 << 20, None, None) == gbid.ID_EINVAL
     assert L.id_cpqr(fake, 0, 10, 20, 12, 5, None, fake, fake, ws, 1 << 20, None, None) == gbid.ID_EINVAL
+    # id_cpqr_residual_norms: NULL workspace or output, m > n, bad ldx
+    assert L.id_cpqr_residual_norms(None, 0, 10, 20, 16, 5, None, fake, None) == gbid.ID_EINVAL
+    assert L.id_cpqr_residual_norms(ws, 0, 10, 20, 16, 5, None, None, None) == gbid.ID_EINVAL
+    assert L.id_cpqr_residual_norms(ws, 0, 30, 20, 32, 5, None, fake, None) == gbid.ID_EINVAL
+    assert L.id_cpqr_residual_norms(ws, 0, 10, 20, 12, 5, None, fake, None) == gbid.ID_EINVAL
     # id_solve: k > n
     assert L.id_solve(fake, 0, 5, 8, 6, fake, 1, None) == gbid.ID_EINVAL
     # id_decompose_batched: count < 0, NULL descriptors, bad dtype, small queue scratch; count 0 is a no-op

@@ -227,9 +227,14 @@ def test_cpqr_and_solve_entry_points(gbid, dtype):
     Xcm = torch.zeros(n, ldx, dtype=dtype)
     Xcm[:, :m] = torch.as_tensor(A.T).to(dtype)
     Xd = Xcm.cuda()
-    perm, tau, info = gbid.id_cpqr(Xd, m, k)
+    perm, tau, info, nu = gbid.id_cpqr(Xd, m, k, residual_norms=True)
     A_exact = torch.as_tensor(A).to(dtype).double().numpy()
     f = orc.cpqr(A_exact, k)
+    # residual column norms after k steps (the oracle's updated trailing block), and the winning norms
+    res_o = np.linalg.norm(f["F"][k:, k:], axis=0)
+    nug = nu.cpu().numpy()
+    assert np.allclose(nug[k:], res_o, rtol=1e-6 if dtype == torch.float64 else 1e-3, atol=1e-12 * res_o.max())
+    assert np.allclose(nug[:k], f["nu"], rtol=1e-6 if dtype == torch.float64 else 1e-3)
     pg = perm.cpu().numpy()
     assert np.array_equal(pg[:k], f["perm"][:k])
     assert sorted(pg.tolist()) == list(range(n))
