@@ -563,7 +563,7 @@ def differentiable_block(gbid, dev, steps):
             for b in range(nb)]
     g = torch.Generator(device=dev).manual_seed(5)
     Gs = [torch.randn(k, n, generator=g, device=dev) for _ in range(nb)]
-    plan = gbid.BatchedPlan(mats, [k] * nb)
+    plan = gbid.BatchedPlan(mats, [k] * nb, autotune=True)     # tile shape tuned here, before timing
     bplan = gbid.BackwardPlan(m, n, k, streams=16, device=dev)
     dAs = [torch.empty(m, n, device=dev) for _ in range(nb)]
 
@@ -607,7 +607,8 @@ def differentiable_block(gbid, dev, steps):
     ok = sum(1 for i in infos if i["status_name"] == "ID_OK")
     return {"workload": "diff_256x512x1024_k64_f32", "fwd_ms": fwd, "bwd_ms": bwd,
             "value": nb * 1000.0 / (fwd + bwd), "unit": "IDs/s (forward + backward)",
-            "bwd_graph": graph is not None, "statuses_ok": ok}
+            "bwd_graph": graph is not None, "statuses_ok": ok,
+            "fwd_tuned_instance": gbid.batched_configs(torch.float32)[plan.config]}
 
 
 def latency_block(gbid, dev, steps):
@@ -695,7 +696,7 @@ def batched_block(gbid, dev, steps):
     probs = synth.batched_uneven(BATCH_COUNT, 4, dtype=torch.float32, device=dev)
     mats = [p["A"] for p in probs]
     ks = [p["k"] for p in probs]
-    plan = gbid.BatchedPlan(mats, ks)
+    plan = gbid.BatchedPlan(mats, ks, autotune=True)            # tile shape tuned here, before timing
     for _ in range(3):
         plan.run()
     torch.cuda.synchronize()
@@ -728,6 +729,8 @@ def batched_block(gbid, dev, steps):
     return {"workload": f"batched_{BATCH_COUNT}_uneven_f32", "ms_per_launch": ms,
             "value": BATCH_COUNT * 1000.0 / ms, "unit": UNIT, "eff_tflops": flops / (ms * 1e-3) / 1e12,
             "launches_per_step": 1, "statuses": statuses,
+            "tuner": {"chosen": gbid.batched_configs(torch.float32)[plan.config],
+                      "ms_per_instance": [round(x, 3) for x in plan.tune_ms]},
             "err_over_tail": {"median": statistics.median(ratios), "max": max(ratios)}}
 
 

@@ -351,6 +351,44 @@ size_t id_batched_problem_workspace_size(id_dtype dtype, int64_t m, int64_t n, i
 int id_decompose_batched(const id_problem* problems, int64_t count, id_dtype dtype, void* batch_work,
                          size_t batch_work_bytes, id_info* infos, void* stream);
 
+/* Tile shapes of the batched kernel and their tuner. The kernel is built in
+ * several instances; each performs the same floating-point operations in the
+ * same order on every element, so all of them return bit-identical J, Z and
+ * id_info (up to the sign of zero entries) and differ only in speed.
+ *
+ * id_batched_config_count -- number of instances for dtype (0: bad dtype).
+ * id_batched_config_get   -- *out = instance `index` (0 is the default that
+ *                            id_decompose_batched uses); ID_EINVAL for a bad
+ *                            dtype, index or NULL out.
+ * id_decompose_batched_with -- id_decompose_batched with instance `config`
+ *                            (same arguments and rules; ID_EINVAL for a bad
+ *                            config index). Enqueues only; graph-capturable.
+ * id_batched_autotune     -- times every instance on this batch: per instance
+ *                            one untimed launch, then `reps` (1..1000) launches
+ *                            between two events on `stream`; ms_out (HOST,
+ *                            config_count floats, or NULL) receives the mean
+ *                            ms per launch and *best (HOST) the fastest index.
+ *                            WAITS for the stream (not capturable). J, Z and
+ *                            infos then hold the batch's results (any
+ *                            instance's: they are identical). Returns ID_OK,
+ *                            ID_EINVAL (as above, or best NULL, reps out of
+ *                            range), ID_ENOMEM or ID_ECUDA. count == 0: *best
+ *                            = 0, nothing launched. */
+typedef struct {
+    int32_t threads;        /* threads per CTA                                      */
+    int32_t cols_per_warp;  /* trailing columns a warp updates per pass             */
+    int32_t rows_per_lane;  /* rows a lane holds per pass: column segments of up to
+                               32 x this rows stay in registers (64 x this with half
+                               the columns), longer ones take two passes             */
+    int32_t ctas_per_sm;    /* resident CTAs per SM the register budget is cut for  */
+} id_batched_config;
+int id_batched_config_count(id_dtype dtype);
+int id_batched_config_get(id_dtype dtype, int index, id_batched_config* out);
+int id_decompose_batched_with(const id_problem* problems, int64_t count, id_dtype dtype, void* batch_work,
+                              size_t batch_work_bytes, id_info* infos, int config, void* stream);
+int id_batched_autotune(const id_problem* problems, int64_t count, id_dtype dtype, void* batch_work,
+                        size_t batch_work_bytes, id_info* infos, int reps, float* ms_out, int* best, void* stream);
+
 /* id_info_read -- copy the device-side status of the last call that used
  * `work` to *info (host) and wait for `stream`. Returns info->status. */
 int id_info_read(const void* work, id_info* info, void* stream);

@@ -93,6 +93,11 @@ _SIG = {
                                                _I64, _P, ctypes.c_size_t, _P, _P]),
     "id_batched_problem_workspace_size": (ctypes.c_size_t, [ctypes.c_int, _I64, _I64, _I64]),
     "id_decompose_batched": (ctypes.c_int, [_P, _I64, ctypes.c_int, _P, ctypes.c_size_t, _P, _P]),
+    "id_batched_config_count": (ctypes.c_int, [ctypes.c_int]),
+    "id_batched_config_get": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P]),
+    "id_decompose_batched_with": (ctypes.c_int, [_P, _I64, ctypes.c_int, _P, ctypes.c_size_t, _P, ctypes.c_int, _P]),
+    "id_batched_autotune": (ctypes.c_int, [_P, _I64, ctypes.c_int, _P, ctypes.c_size_t, _P, ctypes.c_int, _P, _P,
+                                           _P]),
     "id_sampled_workspace_size": (ctypes.c_size_t, [ctypes.c_int, _I64, _I64, _I64, _I64, _P]),
     "id_reconstruct_workspace_size": (ctypes.c_size_t, [ctypes.c_int, _I64, _I64, _I64, ctypes.c_int32]),
     "id_two_sided_workspace_size": (ctypes.c_size_t, [ctypes.c_int, _I64, _I64, _I64, _P]),
@@ -681,15 +686,52 @@ class IdProblem(ctypes.Structure):
                 ("work", ctypes.c_void_p)]
 
 
+class IdBatchedConfig(ctypes.Structure):
+    _fields_ = [("threads", ctypes.c_int32), ("cols_per_warp", ctypes.c_int32), ("rows_per_lane", ctypes.c_int32),
+                ("ctas_per_sm", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {f: int(getattr(self, f)) for f, _ in self._fields_}
+
+
+def batched_configs(dtype=torch.float32) -> list:
+    """The batched kernel's instances (tile shapes) for dtype, index 0 the default."""
+    dt = _DTYPES[dtype]
+    out = []
+    for i in range(int(lib().id_batched_config_count(dt))):
+        c = IdBatchedConfig()
+        rc = lib().id_batched_config_get(dt, i, ctypes.byref(c))
+        if rc != ID_OK:
+            raise IdError(rc, "id_batched_config_get")
+        out.append(c.as_dict())
+    return out
+
+
+def _shape_signature(dtype, device, mats, ks) -> tuple:
+    """Key of the tuner's choice: dtype, device and the multiset of (m, n, k)."""
+    return (str(dtype), str(device), tuple(sorted((int(A.shape[0]), int(A.shape[1]), int(k)) for A, k in zip(mats, ks))))
+
+
+_TUNED: dict = {}
+
+
 class BatchedPlan:
     """Descriptors, outputs and scratch of id_decompose_batched for a fixed list
     of CUDA matrices (one dtype, one device). ``run()`` enqueues one memset and
     one kernel and never waits or allocates, so it can be captured in a CUDA
     graph and replayed. Problems are queued largest first (k m n descending) so
     that the persistent CTAs finish together; outputs keep the caller's order.
+
+    ``config`` picks the kernel instance (an index into batched_configs());
+    ``autotune=True`` instead times every instance on this batch
+    (id_batched_autotune, which waits for the device) and keeps the fastest.
+    The choice is remembered per (dtype, device, multiset of shapes), so a
+    later plan over the same shapes reuses it without timing again. All
+    instances give bit-identical results; ``tune_ms`` holds the timings.
     """
 
-    def __init__(self, mats: list, ks: list):
+    def __init__(self, mats: list, ks: list, *, config: int | None = None, autotune: bool = False,
+                 tune_reps: int = 3):
         if len(mats) != len(ks):
             raise ValueError("one k per matrix")
         if not mats:
@@ -726,17 +768,40 @@ class BatchedPlan:
         self.desc = raw.to(dev)
         self.infos = torch.zeros(len(order) * ctypes.sizeof(IdInfo), dtype=torch.uint8, device=dev)
         self.batch_work = torch.zeros(BATCHED_WORK_BYTES, dtype=torch.uint8, device=dev)
+        self.tune_ms = None
+        self.config = 0 if config is None else int(config)
+        if config is None and autotune:
+            key = _shape_signature(dt, dev, self.mats, self.ks)
+            if key in _TUNED:
+                self.config, self.tune_ms = _TUNED[key]
+            else:
+                self.config, self.tune_ms = self.autotune(tune_reps)
+                _TUNED[key] = (self.config, self.tune_ms)
+
+    def autotune(self, reps: int = 3):
+        """Time every kernel instance on this batch; returns (best index, ms per instance).
+        Leaves the batch's results in J, Z and the infos."""
+        ncfg = int(lib().id_batched_config_count(_DTYPES[self.dtype]))
+        ms = (ctypes.c_float * ncfg)()
+        best = ctypes.c_int(-1)
+        with torch.cuda.device(self.device):
+            rc = lib().id_batched_autotune(self.desc.data_ptr(), len(self.order), _DTYPES[self.dtype],
+                                           self.batch_work.data_ptr(), self.batch_work.numel(), self.infos.data_ptr(),
+                                           int(reps), ms, ctypes.byref(best), _stream(self.device))
+        if rc != ID_OK:
+            raise IdError(rc, "id_batched_autotune")
+        return int(best.value), [float(x) for x in ms]
 
     def __len__(self):
         return len(self.mats)
 
     def run(self):
         with torch.cuda.device(self.device):
-            rc = lib().id_decompose_batched(self.desc.data_ptr(), len(self.order), _DTYPES[self.dtype],
-                                            self.batch_work.data_ptr(), self.batch_work.numel(),
-                                            self.infos.data_ptr(), _stream(self.device))
+            rc = lib().id_decompose_batched_with(self.desc.data_ptr(), len(self.order), _DTYPES[self.dtype],
+                                                 self.batch_work.data_ptr(), self.batch_work.numel(),
+                                                 self.infos.data_ptr(), self.config, _stream(self.device))
         if rc in _CALL_ERRORS:
-            raise IdError(rc, "id_decompose_batched")
+            raise IdError(rc, "id_decompose_batched_with")
 
     def read_infos(self) -> list:
         """Per-problem info dicts in the caller's order (waits for the device)."""
@@ -748,10 +813,12 @@ class BatchedPlan:
         return out
 
 
-def id_decompose_batched(mats: list, ks: list, *, sync: bool = True):
+def id_decompose_batched(mats: list, ks: list, *, sync: bool = True, config: int | None = None,
+                         autotune: bool = False):
     """Rank-k_i IDs of the CUDA matrices mats[i] in one launch. Returns (Js, Zs, infos, plan);
-    infos is None when sync is False (read them later with plan.read_infos())."""
-    plan = BatchedPlan(mats, ks)
+    infos is None when sync is False (read them later with plan.read_infos()). ``config`` and
+    ``autotune`` choose the kernel instance as in BatchedPlan."""
+    plan = BatchedPlan(mats, ks, config=config, autotune=autotune)
     plan.run()
     return plan.J, plan.Z, (plan.read_infos() if sync else None), plan
 

@@ -21,6 +21,15 @@
 // Per-problem status (argument check, non-finite input, numerical rank) goes
 // to that problem's id_info. Nothing waits on another CTA: the only shared
 // state is the queue counter.
+//
+// The kernel is instantiated for several tile shapes (threads per CTA,
+// trailing columns per warp, rows a lane holds per pass, resident CTAs per
+// SM). Every instance performs the same operations in the same order on
+// every element: a lane always sums its rows j + lane + 32q in increasing q,
+// the warp and block reductions are fixed butterflies or exact comparisons,
+// and one warp solves each column of T. So all instances give bit-identical
+// J, Z and id_info, and id_batched_autotune may time them on the caller's
+// batch and keep the fastest.
 #include <cuda_runtime.h>
 #include <float.h>
 #include <math.h>
@@ -35,9 +44,8 @@
 namespace gbid {
 namespace {
 
-constexpr int kBThreads = 256;
-constexpr int kBWarps = kBThreads / kWarp;
-constexpr int kBRows = 8;                    // rows per lane per pass (256-row chunks)
+constexpr int kBMaxWarps = 16;               // up to 512 threads per CTA
+constexpr int kBRows = 8;                    // rows per lane per pass of the reflector (256-row chunks)
 constexpr int kBCopy = 16;                   // loads in flight per thread in the copy-in
 constexpr int kBMaxK = ID_BATCHED_MAX_K;
 constexpr int kBMaxM = ID_BATCHED_MAX_MIN_DIM;
@@ -57,26 +65,29 @@ __host__ __device__ inline BLayout b_layout(int s, int64_t mx, int64_t nx) {
     return L;
 }
 
+template <int NW>
 __device__ ArgMax b_block_argmax(ArgMax a, ArgMax* red) {
     a = warp_argmax(a);
     const int w = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
     __syncthreads();
     if (lane == 0) red[w] = a;
     __syncthreads();
-    a = lane < kBWarps ? red[lane] : empty_argmax();
+    a = lane < NW ? red[lane] : empty_argmax();
     return warp_argmax(a);
 }
 
+template <int NW>
 __device__ double b_block_sum(double v, double* red) {
     v = warp_sum(v);
     const int w = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
     __syncthreads();
     if (lane == 0) red[w] = v;
     __syncthreads();
-    v = lane < kBWarps ? red[lane] : 0.0;
+    v = lane < NW ? red[lane] : 0.0;
     return warp_sum(v);
 }
 
+template <int NW>
 __device__ double b_block_max(double v, double* red) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -84,7 +95,7 @@ __device__ double b_block_max(double v, double* red) {
     __syncthreads();
     if (lane == 0) red[w] = v;
     __syncthreads();
-    v = lane < kBWarps ? red[lane] : 0.0;
+    v = lane < NW ? red[lane] : 0.0;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
@@ -224,16 +235,21 @@ __device__ void b_update_group(T* W, int ldw, const int* perm, int mx, int nx, i
     }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kBThreads, 3) k_id_batched(const id_problem* __restrict__ probs, int count,
-                                                        unsigned* queue, id_info* __restrict__ infos) {
-    constexpr int CG = sizeof(T) == 4 ? 4 : 2;          // trailing columns per warp and pass
+// TH threads per CTA, CG trailing columns per warp and pass, R rows per lane
+// per pass (column segments of up to 32 R rows stay in registers), MINB the
+// resident CTAs per SM the register budget is cut for.
+template <typename T, int TH, int CG, int R, int MINB>
+__global__ void __launch_bounds__(TH, MINB) k_id_batched(const id_problem* __restrict__ probs, int count,
+                                                      unsigned* queue, id_info* __restrict__ infos) {
+    constexpr int kBThreads = TH;
+    constexpr int kBWarps = TH / kWarp;
+    static_assert(TH % kWarp == 0 && kBWarps <= kBMaxWarps, "threads per CTA");
     const double eps = sizeof(T) == 8 ? DBL_EPSILON : (double)FLT_EPSILON;
     __shared__ T v_s[kBMaxM];
     __shared__ double r11[kBMaxK][kBMaxK + 1];
     __shared__ double rinv[kBMaxK];
-    __shared__ ArgMax red_a[kBWarps];
-    __shared__ double red_d[kBWarps];
+    __shared__ ArgMax red_a[kBMaxWarps];
+    __shared__ double red_d[kBMaxWarps];
     __shared__ double sc[2];
     __shared__ int s_b;
     const int t = threadIdx.x, lane = t % kWarp, w = t / kWarp;
@@ -324,7 +340,7 @@ __global__ void __launch_bounds__(kBThreads, 3) k_id_batched(const id_problem* _
             }
         }
         nonfinite = __syncthreads_or(nonfinite);
-        best = b_block_argmax(best, red_a);
+        best = b_block_argmax<kBWarps>(best, red_a);
         T ysc = T(1);
         if (best.val > 0.0) {
             int e2;
@@ -390,18 +406,18 @@ __global__ void __launch_bounds__(kBThreads, 3) k_id_batched(const id_problem* _
             if (rank == k && (r00 == 0.0 || fabs(beta) <= rank_tol * r00)) rank = j;
             const T tauT = (T)sc[1];
             // the last step still updates: it writes row k-1 of R12. Column segments
-            // of up to 256 rows stay in registers CG columns at a time, up to 512
+            // of up to 32 R rows stay in registers CG columns at a time, up to 64 R
             // rows CG / 2 columns at a time; longer ones take two passes.
             Cand<T> bw = cand_empty<T>();
-            if (mx - j > kWarp * kBRows && mx - j <= 2 * kWarp * kBRows) {
-                constexpr int CG2 = CG / 2;
+            if (mx - j > kWarp * R && mx - j <= 2 * kWarp * R) {
+                constexpr int CG2 = CG > 1 ? CG / 2 : 1;
                 for (int pos0 = j + 1 + w * CG2; pos0 < nx; pos0 += kBWarps * CG2)
-                    b_update_group<T, CG2, 2 * kBRows>(W, ldw, perm, mx, nx, j, pos0, tauT, ysc, v_s, bw);
+                    b_update_group<T, CG2, 2 * R>(W, ldw, perm, mx, nx, j, pos0, tauT, ysc, v_s, bw);
             } else {
                 for (int pos0 = j + 1 + w * CG; pos0 < nx; pos0 += kBWarps * CG)
-                    b_update_group<T, CG, kBRows>(W, ldw, perm, mx, nx, j, pos0, tauT, ysc, v_s, bw);
+                    b_update_group<T, CG, R>(W, ldw, perm, mx, nx, j, pos0, tauT, ysc, v_s, bw);
             }
-            best = b_block_argmax(cand_to_argmax(bw), red_a);   // its barriers also order this step's writes
+            best = b_block_argmax<kBWarps>(cand_to_argmax(bw), red_a);   // its barriers also order this step's writes
         }
 
         // 3. T = R11^{-1} R12 (FP64), Z, J
@@ -483,8 +499,8 @@ __global__ void __launch_bounds__(kBThreads, 3) k_id_batched(const id_problem* _
             Z[(int64_t)i * ldz + perm[l]] = i == l ? T(1) : T(0);
         }
         for (int l = t; l < k; l += kBThreads) pr.J[l] = perm[l];
-        const double zmax_b = b_block_max((double)zmax, red_d);
-        const double gt2_b = b_block_sum((double)gt2, red_d);
+        const double zmax_b = b_block_max<kBWarps>((double)zmax, red_d);
+        const double gt2_b = b_block_sum<kBWarps>((double)gt2, red_d);
         if (t == 0) {
             id_info r = {};
             r.status = nonfinite ? ID_ENONFINITE : (rank < k ? ID_RANK_DEFICIENT : ID_OK);
@@ -502,13 +518,42 @@ __global__ void __launch_bounds__(kBThreads, 3) k_id_batched(const id_problem* _
     }
 }
 
+// The instances the tuner chooses from, one table per element type: {threads,
+// columns per warp, rows per lane, CTAs per SM}. Entry 0 is the default.
+using BatchedFn = void (*)(const id_problem*, int, unsigned*, id_info*);
+struct BConfig {
+    id_batched_config c;
+    BatchedFn fn;
+};
+
+#define GBID_BCFG(T, TH, CG, R, MB) {{TH, CG, R, MB}, &k_id_batched<T, TH, CG, R, MB>}
+const BConfig kBCfg32[] = {
+    GBID_BCFG(float, 256, 4, 8, 3), GBID_BCFG(float, 256, 2, 8, 3), GBID_BCFG(float, 256, 8, 4, 3),
+    GBID_BCFG(float, 256, 4, 4, 3), GBID_BCFG(float, 128, 4, 8, 5), GBID_BCFG(float, 256, 4, 8, 2),
+    GBID_BCFG(float, 512, 4, 8, 1),
+};
+const BConfig kBCfg64[] = {
+    GBID_BCFG(double, 256, 2, 8, 3), GBID_BCFG(double, 256, 1, 8, 3), GBID_BCFG(double, 256, 4, 4, 3),
+    GBID_BCFG(double, 256, 2, 4, 3), GBID_BCFG(double, 128, 2, 8, 5), GBID_BCFG(double, 256, 2, 8, 2),
+    GBID_BCFG(double, 512, 2, 8, 1),
+};
+#undef GBID_BCFG
+constexpr int kBNumCfg = (int)(sizeof(kBCfg32) / sizeof(kBCfg32[0]));
+static_assert(kBNumCfg == (int)(sizeof(kBCfg64) / sizeof(kBCfg64[0])), "one table size");
+
+inline const BConfig* b_table(id_dtype dtype) {
+    return dtype == ID_F64 ? kBCfg64 : dtype == ID_F32 ? kBCfg32 : nullptr;
+}
+
 int g_bnsm = 0;
-int g_bocc[2] = {0, 0};
+int g_bocc[2][kBNumCfg] = {};
 std::mutex g_bmu;
 
-template <typename T>
-int batched_grid(int count) {
-    const int slot = sizeof(T) == 8 ? 0 : 1;
+// Grid of one instance: the resident capacity (SMs x CTAs per SM that the
+// occupancy calculator gives for it), or the problem count if smaller.
+int batched_grid(id_dtype dtype, int cfg, int count) {
+    const int slot = dtype == ID_F64 ? 0 : 1;
+    const BConfig& b = b_table(dtype)[cfg];
     {
         std::lock_guard<std::mutex> lk(g_bmu);
         if (g_bnsm == 0) {
@@ -516,10 +561,34 @@ int batched_grid(int count) {
             cudaGetDevice(&dev);
             cudaDeviceGetAttribute(&g_bnsm, cudaDevAttrMultiProcessorCount, dev);
         }
-        if (g_bocc[slot] == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_bocc[slot], k_id_batched<T>, kBThreads, 0);
+        if (g_bocc[slot][cfg] == 0)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_bocc[slot][cfg], b.fn, b.c.threads, 0);
     }
-    const int cap = g_bnsm * (g_bocc[slot] > 0 ? g_bocc[slot] : 1);
+    const int cap = g_bnsm * (g_bocc[slot][cfg] > 0 ? g_bocc[slot][cfg] : 1);
     return count < cap ? count : cap;
+}
+
+int check_batched(const id_problem* problems, int64_t count, id_dtype dtype, void* batch_work,
+                  size_t batch_work_bytes, id_info* infos, int config) {
+    if (!b_table(dtype)) return ID_EINVAL;
+    if (count < 0 || count > INT32_MAX) return ID_EINVAL;
+    if (config < 0 || config >= kBNumCfg) return ID_EINVAL;
+    if (count == 0) return ID_OK;
+    if (!problems || !batch_work || !infos) return ID_EINVAL;
+    if (batch_work_bytes < ID_BATCHED_WORK_BYTES) return ID_ENOMEM;
+    return ID_OK;
+}
+
+// One memset (the queue counter) and one launch; arguments already checked.
+int launch_batched(const id_problem* problems, int count, id_dtype dtype, unsigned* queue, id_info* infos,
+                   int config, cudaStream_t s) {
+    if (cudaMemsetAsync(queue, 0, sizeof(unsigned), s) != cudaSuccess) return ID_ECUDA;
+    const BConfig& b = b_table(dtype)[config];
+    const int g = batched_grid(dtype, config, count);
+    const int tr = trace_begin(TraceKind::kBatched, s);
+    b.fn<<<g, b.c.threads, 0, s>>>(problems, count, queue, infos);
+    trace_end(tr, s);
+    return cudaGetLastError() == cudaSuccess ? ID_OK : ID_ECUDA;
 }
 
 }  // namespace
@@ -534,24 +603,68 @@ extern "C" size_t id_batched_problem_workspace_size(id_dtype dtype, int64_t m, i
     return b_layout(dtype == ID_F64 ? 8 : 4, mn, mx).total;
 }
 
+extern "C" int id_batched_config_count(id_dtype dtype) { return b_table(dtype) ? kBNumCfg : 0; }
+
+extern "C" int id_batched_config_get(id_dtype dtype, int index, id_batched_config* out) {
+    if (!b_table(dtype) || !out || index < 0 || index >= kBNumCfg) return ID_EINVAL;
+    *out = b_table(dtype)[index].c;
+    return ID_OK;
+}
+
+extern "C" int id_decompose_batched_with(const id_problem* problems, int64_t count, id_dtype dtype, void* batch_work,
+                                         size_t batch_work_bytes, id_info* infos, int config, void* stream) {
+    const int rc = check_batched(problems, count, dtype, batch_work, batch_work_bytes, infos, config);
+    if (rc != ID_OK || count == 0) return rc;
+    return launch_batched(problems, (int)count, dtype, static_cast<unsigned*>(batch_work), infos, config,
+                          static_cast<cudaStream_t>(stream));
+}
+
 extern "C" int id_decompose_batched(const id_problem* problems, int64_t count, id_dtype dtype, void* batch_work,
                                     size_t batch_work_bytes, id_info* infos, void* stream) {
-    if (dtype != ID_F64 && dtype != ID_F32) return ID_EINVAL;
-    if (count < 0 || count > INT32_MAX) return ID_EINVAL;
-    if (count == 0) return ID_OK;
-    if (!problems || !batch_work || !infos) return ID_EINVAL;
-    if (batch_work_bytes < ID_BATCHED_WORK_BYTES) return ID_ENOMEM;
+    return id_decompose_batched_with(problems, count, dtype, batch_work, batch_work_bytes, infos, 0, stream);
+}
+
+extern "C" int id_batched_autotune(const id_problem* problems, int64_t count, id_dtype dtype, void* batch_work,
+                                   size_t batch_work_bytes, id_info* infos, int reps, float* ms_out, int* best,
+                                   void* stream) {
+    if (!best || reps < 1 || reps > 1000) return ID_EINVAL;
+    const int rc = check_batched(problems, count, dtype, batch_work, batch_work_bytes, infos, 0);
+    if (rc != ID_OK) return rc;
+    if (count == 0) {
+        *best = 0;
+        if (ms_out)
+            for (int c = 0; c < kBNumCfg; ++c) ms_out[c] = 0.0f;
+        return ID_OK;
+    }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     unsigned* queue = static_cast<unsigned*>(batch_work);
-    if (cudaMemsetAsync(queue, 0, sizeof(unsigned), s) != cudaSuccess) return ID_ECUDA;
-    const int tr = trace_begin(TraceKind::kBatched, s);
-    if (dtype == ID_F64) {
-        const int g = batched_grid<double>((int)count);
-        k_id_batched<double><<<g, kBThreads, 0, s>>>(problems, (int)count, queue, infos);
-    } else {
-        const int g = batched_grid<float>((int)count);
-        k_id_batched<float><<<g, kBThreads, 0, s>>>(problems, (int)count, queue, infos);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return ID_ECUDA;
     }
-    trace_end(tr, s);
-    return cudaGetLastError() == cudaSuccess ? ID_OK : ID_ECUDA;
+    int status = ID_OK, arg = 0;
+    float best_ms = 0.0f;
+    for (int c = 0; c < kBNumCfg && status == ID_OK; ++c) {
+        // one untimed launch (first-use costs, the problems' scratch paged in), then reps timed back to back
+        status = launch_batched(problems, (int)count, dtype, queue, infos, c, s);
+        if (status == ID_OK && cudaEventRecord(e0, s) != cudaSuccess) status = ID_ECUDA;
+        for (int r = 0; r < reps && status == ID_OK; ++r)
+            status = launch_batched(problems, (int)count, dtype, queue, infos, c, s);
+        if (status == ID_OK && cudaEventRecord(e1, s) != cudaSuccess) status = ID_ECUDA;
+        float ms = 0.0f;
+        if (status == ID_OK && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+            status = ID_ECUDA;
+        if (status != ID_OK) break;
+        ms /= (float)reps;
+        if (ms_out) ms_out[c] = ms;
+        if (c == 0 || ms < best_ms) {
+            best_ms = ms;
+            arg = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (status == ID_OK) *best = arg;
+    return status;
 }

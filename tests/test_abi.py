@@ -8,6 +8,7 @@ import os
 import re
 
 import pytest
+import torch
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -102,6 +103,47 @@ def test_argument_errors_return_before_any_launch(gbid):
     assert L.id_decompose_batched(fake, 3, 9, fake, 256, fake, None) == gbid.ID_EINVAL
     assert L.id_decompose_batched(fake, 3, 1, fake, 16, fake, None) == gbid.ID_ENOMEM
     assert L.id_decompose_batched(None, 0, 1, None, 0, None, None) == gbid.ID_OK
+
+
+def test_batched_instances_and_tuner_rules(gbid):
+    """The batched kernel's instance table and the tuner's argument checks
+    (nothing here reaches the device)."""
+    L = gbid.lib()
+    fake = ctypes.c_void_p(256)
+    n32, n64 = L.id_batched_config_count(1), L.id_batched_config_count(0)
+    assert n32 >= 2 and n64 >= 2 and L.id_batched_config_count(5) == 0
+    for dt, cnt in ((0, n64), (1, n32)):
+        seen = set()
+        for i in range(cnt):
+            c = gbid.IdBatchedConfig()
+            assert L.id_batched_config_get(dt, i, ctypes.byref(c)) == gbid.ID_OK
+            d = c.as_dict()
+            assert d["threads"] % 32 == 0 and 32 <= d["threads"] <= 512
+            assert d["cols_per_warp"] >= 1 and d["rows_per_lane"] >= 1 and d["ctas_per_sm"] >= 1
+            # 32-bit registers per CTA within the SM's 65536 at the stated residency
+            assert d["threads"] * d["ctas_per_sm"] <= 2048
+            seen.add(tuple(d.values()))
+        assert len(seen) == cnt                                  # no instance twice
+        c = gbid.IdBatchedConfig()
+        assert L.id_batched_config_get(dt, cnt, ctypes.byref(c)) == gbid.ID_EINVAL
+        assert L.id_batched_config_get(dt, -1, ctypes.byref(c)) == gbid.ID_EINVAL
+        assert L.id_batched_config_get(dt, 0, None) == gbid.ID_EINVAL
+    assert gbid.batched_configs(torch.float32)[0] == {"threads": 256, "cols_per_warp": 4, "rows_per_lane": 8,
+                                                      "ctas_per_sm": 3}
+    assert L.id_batched_config_get(7, 0, ctypes.byref(gbid.IdBatchedConfig())) == gbid.ID_EINVAL
+    # id_decompose_batched_with: the config index is checked first; count 0 is a no-op
+    assert L.id_decompose_batched_with(fake, 3, 1, fake, 256, fake, n32, None) == gbid.ID_EINVAL
+    assert L.id_decompose_batched_with(fake, 3, 1, fake, 256, fake, -1, None) == gbid.ID_EINVAL
+    assert L.id_decompose_batched_with(fake, 3, 1, fake, 16, fake, 1, None) == gbid.ID_ENOMEM
+    assert L.id_decompose_batched_with(None, 0, 1, None, 0, None, 1, None) == gbid.ID_OK
+    # id_batched_autotune: NULL best, reps out of range; an empty batch picks 0 and launches nothing
+    best = ctypes.c_int(-7)
+    ms = (ctypes.c_float * n32)(*([1.0] * n32))
+    assert L.id_batched_autotune(fake, 3, 1, fake, 256, fake, 3, ms, None, None) == gbid.ID_EINVAL
+    assert L.id_batched_autotune(fake, 3, 1, fake, 256, fake, 0, ms, ctypes.byref(best), None) == gbid.ID_EINVAL
+    assert L.id_batched_autotune(fake, 3, 9, fake, 256, fake, 3, ms, ctypes.byref(best), None) == gbid.ID_EINVAL
+    assert L.id_batched_autotune(None, 0, 1, None, 0, None, 3, ms, ctypes.byref(best), None) == gbid.ID_OK
+    assert best.value == 0 and list(ms) == [0.0] * n32
 
 
 def test_engine_option(gbid):

@@ -167,3 +167,75 @@ def test_batched_full_workload_4096(gbid):
             assert err >= synth.tail_bound(s, k) * (1 - 1e-4) - 1e-6, (i, err)
     for i in range(0, 4096, 512):
         _check_problem(mats[i], ks[i], Js[i], Zs[i], infos[i], torch.float32)
+
+
+def _path_batch(dtype, seed):
+    """Shapes whose column segments take every path of every kernel instance
+    (a segment of up to 32 R rows in registers, up to 64 R with half the
+    columns, longer in two passes, for R = 4 and 8), both routes (m > n takes
+    the transpose), k up to the maximum, and an all-zero matrix."""
+    shapes = [(20, 50, 7), (100, 260, 30), (130, 131, 64), (200, 700, 40), (256, 300, 64), (300, 620, 33),
+              (520, 600, 64), (700, 900, 50), (1024, 1100, 16), (900, 300, 25), (640, 129, 64), (33, 1000, 8)]
+    mats, ks = [], []
+    for i, (m, n, k) in enumerate(shapes):
+        d = min(m, n)
+        A = synth.lowrank(m, n, synth.spectrum("exp8m", d, m=d), seed + i).to(dtype)
+        mats.append(A.cuda())
+        ks.append(k)
+    mats.append(torch.zeros(40, 90, dtype=dtype, device="cuda"))
+    ks.append(10)
+    return mats, ks
+
+
+def _same(a, b):
+    """Equal values, NaN where the other has NaN (Z past the numerical rank of a
+    rank-deficient problem is 0/0)."""
+    return torch.equal(a.isnan(), b.isnan()) and torch.equal(a.nan_to_num(0.0), b.nan_to_num(0.0))
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+def test_every_instance_gives_identical_results(gbid, dtype):
+    """The kernel's instances (tile shapes the tuner picks from) perform the
+    same operations in the same order: J, Z and id_info agree exactly with the
+    default instance, which itself passes the oracle checks."""
+    mats, ks = _path_batch(dtype, 21)
+    cfgs = gbid.batched_configs(dtype)
+    assert len(cfgs) >= 2
+    base = gbid.BatchedPlan(mats, ks, config=0)
+    base.run()
+    infos0 = base.read_infos()
+    for A, k, J, Z, info in zip(mats, ks, base.J, base.Z, infos0):
+        assert info["status"] in (gbid.ID_OK, gbid.ID_RANK_DEFICIENT), info
+        if torch.count_nonzero(A).item():
+            _check_problem(A, k, J, Z, info, dtype)
+    assert infos0[-1]["status"] == gbid.ID_RANK_DEFICIENT and infos0[-1]["rank"] == 0
+    for c in range(1, len(cfgs)):
+        plan = gbid.BatchedPlan(mats, ks, config=c)
+        plan.run()
+        infos = plan.read_infos()
+        for i in range(len(mats)):
+            assert torch.equal(plan.J[i], base.J[i]), (cfgs[c], i)
+            assert _same(plan.Z[i], base.Z[i]), (cfgs[c], i)
+            assert infos[i] == infos0[i], (cfgs[c], i)
+
+
+def test_autotune_picks_the_fastest_instance(gbid):
+    """id_batched_autotune times every instance on the batch, returns the
+    fastest and leaves the batch's results; a later plan over the same shapes
+    reuses the choice."""
+    mats, ks = _mixed_batch(torch.float32, 64, 17)
+    ref = gbid.BatchedPlan(mats, ks, config=0)
+    ref.run()
+    plan = gbid.BatchedPlan(mats, ks, autotune=True, tune_reps=2)
+    ms = plan.tune_ms
+    assert len(ms) == len(gbid.batched_configs(torch.float32)) and min(ms) > 0
+    assert plan.config == int(np.argmin(ms))
+    torch.cuda.synchronize()
+    for i in range(len(mats)):
+        assert torch.equal(plan.J[i], ref.J[i]) and _same(plan.Z[i], ref.Z[i])
+    again = gbid.BatchedPlan(mats, ks, autotune=True)
+    assert again.config == plan.config and again.tune_ms is plan.tune_ms
+    again.run()
+    torch.cuda.synchronize()
+    for i in range(len(mats)):
+        assert _same(again.Z[i], ref.Z[i])
