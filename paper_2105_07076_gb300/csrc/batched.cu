@@ -52,6 +52,12 @@ constexpr int kBMaxM = ID_BATCHED_MAX_MIN_DIM;
 
 __host__ __device__ inline size_t b_align(size_t x) { return (x + 255) & ~size_t(255); }
 
+// R11 (upper triangular, k <= kBMaxK) packed by columns in shared memory:
+// entry (r, i), r <= i, at i (i + 1) / 2 + r. Lanes reading one column take
+// consecutive words.
+constexpr int kBR11 = kBMaxK * (kBMaxK + 1) / 2;
+__device__ __forceinline__ int rp(int r, int i) { return i * (i + 1) / 2 + r; }
+
 struct BLayout {
     size_t perm, total;
     int ldw;
@@ -246,7 +252,7 @@ __global__ void __launch_bounds__(TH, MINB) k_id_batched(const id_problem* __res
     static_assert(TH % kWarp == 0 && kBWarps <= kBMaxWarps, "threads per CTA");
     const double eps = sizeof(T) == 8 ? DBL_EPSILON : (double)FLT_EPSILON;
     __shared__ T v_s[kBMaxM];
-    __shared__ double r11[kBMaxK][kBMaxK + 1];
+    __shared__ double r11[kBR11];
     __shared__ double rinv[kBMaxK];
     __shared__ ArgMax red_a[kBMaxWarps];
     __shared__ double red_d[kBMaxWarps];
@@ -431,17 +437,17 @@ __global__ void __launch_bounds__(TH, MINB) k_id_batched(const id_problem* __res
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const int e = e0 + u * kBThreads;
-                if (e < k * k) r11[e / k][e % k] = v[u];
+                if (e < k * k && e / k <= e % k) r11[rp(e / k, e % k)] = v[u];
             }
         }
         __syncthreads();
-        for (int i = t; i < k; i += kBThreads) rinv[i] = 1.0 / r11[i][i];
+        for (int i = t; i < k; i += kBThreads) rinv[i] = 1.0 / r11[rp(i, i)];
         __syncthreads();
         // R(r, i) / R(i, i) above the diagonal: the substitution then needs one
         // FMA per step, b_r -= (R(r,i) / R(i,i)) b_i, and one scaling at the end
         for (int e = t; e < k * k; e += kBThreads) {
             const int r = e / k, i = e % k;
-            if (r < i) r11[r][i] *= rinv[i];
+            if (r < i) r11[rp(r, i)] *= rinv[i];
         }
         __syncthreads();
         T* Z = static_cast<T*>(pr.Z);
@@ -469,8 +475,8 @@ __global__ void __launch_bounds__(TH, MINB) k_id_batched(const id_problem* __res
 #pragma unroll
                 for (int qq = 0; qq < 4; ++qq) {
                     const double bi = __shfl_sync(0xffffffffu, sl ? x[qq][1] : x[qq][0], own);
-                    if (lane < i) x[qq][0] = fma(-r11[lane][i], bi, x[qq][0]);
-                    if (two && lane + kWarp < i) x[qq][1] = fma(-r11[lane + kWarp][i], bi, x[qq][1]);
+                    if (lane < i) x[qq][0] = fma(-r11[rp(lane, i)], bi, x[qq][0]);
+                    if (two && lane + kWarp < i) x[qq][1] = fma(-r11[rp(lane + kWarp, i)], bi, x[qq][1]);
                 }
             }
 #pragma unroll
@@ -530,12 +536,12 @@ struct BConfig {
 const BConfig kBCfg32[] = {
     GBID_BCFG(float, 256, 4, 8, 3), GBID_BCFG(float, 256, 2, 8, 3), GBID_BCFG(float, 256, 8, 4, 3),
     GBID_BCFG(float, 256, 4, 4, 3), GBID_BCFG(float, 128, 4, 8, 5), GBID_BCFG(float, 256, 4, 8, 2),
-    GBID_BCFG(float, 512, 4, 8, 1),
+    GBID_BCFG(float, 512, 4, 8, 1), GBID_BCFG(float, 128, 4, 8, 6), GBID_BCFG(float, 128, 2, 8, 8),
 };
 const BConfig kBCfg64[] = {
     GBID_BCFG(double, 256, 2, 8, 3), GBID_BCFG(double, 256, 1, 8, 3), GBID_BCFG(double, 256, 4, 4, 3),
     GBID_BCFG(double, 256, 2, 4, 3), GBID_BCFG(double, 128, 2, 8, 5), GBID_BCFG(double, 256, 2, 8, 2),
-    GBID_BCFG(double, 512, 2, 8, 1),
+    GBID_BCFG(double, 512, 2, 8, 1), GBID_BCFG(double, 128, 2, 8, 6), GBID_BCFG(double, 128, 1, 8, 8),
 };
 #undef GBID_BCFG
 constexpr int kBNumCfg = (int)(sizeof(kBCfg32) / sizeof(kBCfg32[0]));
