@@ -771,16 +771,17 @@ class BatchedPlan:
         self.tune_ms = None
         self.config = 0 if config is None else int(config)
         if config is None and autotune:
-            key = _shape_signature(dt, dev, self.mats, self.ks)
-            if key in _TUNED:
-                self.config, self.tune_ms = _TUNED[key]
+            cached = _TUNED.get(_shape_signature(dt, dev, self.mats, self.ks))
+            if cached is not None:
+                self.config, self.tune_ms = cached
             else:
-                self.config, self.tune_ms = self.autotune(tune_reps)
-                _TUNED[key] = (self.config, self.tune_ms)
+                self.autotune(tune_reps)
 
     def autotune(self, reps: int = 3):
-        """Time every kernel instance on this batch; returns (best index, ms per instance).
-        Leaves the batch's results in J, Z and the infos."""
+        """Time every kernel instance on this batch, make the fastest this plan's
+        instance and remember it for these shapes; returns (best index, ms per
+        instance). Waits for the device; leaves the batch's results in J, Z and
+        the infos."""
         ncfg = int(lib().id_batched_config_count(_DTYPES[self.dtype]))
         ms = (ctypes.c_float * ncfg)()
         best = ctypes.c_int(-1)
@@ -790,7 +791,9 @@ class BatchedPlan:
                                            int(reps), ms, ctypes.byref(best), _stream(self.device))
         if rc != ID_OK:
             raise IdError(rc, "id_batched_autotune")
-        return int(best.value), [float(x) for x in ms]
+        self.config, self.tune_ms = int(best.value), [float(x) for x in ms]
+        _TUNED[_shape_signature(self.dtype, self.device, self.mats, self.ks)] = (self.config, self.tune_ms)
+        return self.config, self.tune_ms
 
     def __len__(self):
         return len(self.mats)
