@@ -318,7 +318,9 @@ int id_backward(const void* A, id_dtype dtype, int64_t m, int64_t n, int64_t lda
  * many small IDs (a hierarchical compression) has no batched form in the
  * paper itself; the arithmetic per matrix is that of id_decompose:
  * Householder CPQR stopped after k pivots (residual norms taken exactly every
- * step, ties to the smallest original index), T = R11^{-1} R12 in FP64.
+ * step, ties to the smallest original index), T = R11^{-1} R12 by back
+ * substitution in FP64 (FP64 data) or in double-float arithmetic of about 48
+ * significant bits (FP32 data).
  *
  *   problems   [in]  DEVICE array of `count` id_problem descriptors, read by
  *                    the kernel (so the call can be captured in a CUDA graph

@@ -15,9 +15,11 @@
 //      a downdate would; squares of y / 2^e, 2^e near the largest column
 //      norm, summed in the working precision) for the next pivot's argmax
 //      (ties: smallest original column index).
-//   3. T = R11^{-1} R12 by back substitution in FP64 (R11 staged in shared
-//      memory; a warp solves four right-hand sides at a time, lane = row),
-//      written straight into Z through perm; Z[:, J] = I, J = perm[0:k].
+//   3. T = R11^{-1} R12 by back substitution (R11 staged in shared memory;
+//      a warp solves four right-hand sides at a time, lane = row), in FP64
+//      for FP64 data and in double-float arithmetic (about 48 bits, on the
+//      FP32 pipe) for FP32 data, written straight into Z through perm;
+//      Z[:, J] = I, J = perm[0:k].
 // Per-problem status (argument check, non-finite input, numerical rank) goes
 // to that problem's id_info. Nothing waits on another CTA: the only shared
 // state is the queue counter.
@@ -57,6 +59,24 @@ __host__ __device__ inline size_t b_align(size_t x) { return (x + 255) & ~size_t
 // consecutive words.
 constexpr int kBR11 = kBMaxK * (kBMaxK + 1) / 2;
 __device__ __forceinline__ int rp(int r, int i) { return i * (i + 1) / 2 + r; }
+
+// x <- x - r b on unevaluated float pairs (hi + lo), about 48 significant
+// bits: r b by Dekker's product (the FMA gives hi's rounding error exactly),
+// the difference by Knuth's TwoSum, renormalised by Dekker's FastTwoSum. The
+// _rn intrinsics keep the compiler from contracting the error-free steps.
+__device__ __forceinline__ void df_sub_mul(float& xh, float& xl, float rh, float rl, float bh, float bl) {
+    const float p = __fmul_rn(rh, bh);
+    float pe = __fmaf_rn(rh, bh, -p);
+    pe = __fmaf_rn(rh, bl, pe);
+    pe = __fmaf_rn(rl, bh, pe);
+    const float s = __fsub_rn(xh, p);
+    const float v = __fsub_rn(s, xh);
+    float e = __fadd_rn(__fsub_rn(xh, __fsub_rn(s, v)), __fsub_rn(-p, v));
+    e = __fadd_rn(e, __fsub_rn(xl, pe));
+    const float nh = __fadd_rn(s, e);
+    xl = __fsub_rn(e, __fsub_rn(nh, s));
+    xh = nh;
+}
 
 struct BLayout {
     size_t perm, total;
@@ -444,10 +464,22 @@ __global__ void __launch_bounds__(TH, MINB) k_id_batched(const id_problem* __res
         for (int i = t; i < k; i += kBThreads) rinv[i] = 1.0 / r11[rp(i, i)];
         __syncthreads();
         // R(r, i) / R(i, i) above the diagonal: the substitution then needs one
-        // FMA per step, b_r -= (R(r,i) / R(i,i)) b_i, and one scaling at the end
+        // FMA per step, b_r -= (R(r,i) / R(i,i)) b_i, and one scaling at the end.
+        // FP32 data: the ratio is kept as a float pair in the same slot, and the
+        // substitution runs in double-float arithmetic on the FP32 pipe (about
+        // 48 bits, far below the FP32 data's own rounding; the FP64 pipe does
+        // one warp instruction per 16 clocks per SM on this GPU).
         for (int e = t; e < k * k; e += kBThreads) {
             const int r = e / k, i = e % k;
-            if (r < i) r11[rp(r, i)] *= rinv[i];
+            if (r < i) {
+                const double d = r11[rp(r, i)] * rinv[i];
+                if constexpr (sizeof(T) == 4) {
+                    const float hi = (float)d;
+                    reinterpret_cast<float2*>(r11)[rp(r, i)] = make_float2(hi, (float)(d - (double)hi));
+                } else {
+                    r11[rp(r, i)] = d;
+                }
+            }
         }
         __syncthreads();
         T* Z = static_cast<T*>(pr.Z);
@@ -455,7 +487,7 @@ __global__ void __launch_bounds__(TH, MINB) k_id_batched(const id_problem* __res
         T zmax = T(1);                  // the identity block holds ones
         float gt2 = 0.0f;
         for (int l0 = k + 4 * w; l0 < nx; l0 += 4 * kBWarps) {
-            double x[4][2];
+            T xv[4][2];
             int colq[4];
 #pragma unroll
             for (int qq = 0; qq < 4; ++qq) {
@@ -464,19 +496,51 @@ __global__ void __launch_bounds__(TH, MINB) k_id_batched(const id_problem* __res
 #pragma unroll
                 for (int s = 0; s < 2; ++s) {
                     const int i = lane + kWarp * s;
-                    x[qq][s] = (colq[qq] >= 0 && i < k) ? (double)W[(int64_t)colq[qq] * ldw + i] : 0.0;
+                    xv[qq][s] = (colq[qq] >= 0 && i < k) ? W[(int64_t)colq[qq] * ldw + i] : T(0);
                 }
             }
             // b_i (final once rows > i are applied) is broadcast; rows below 32
             // only when k > 32; x = b / diag(R) at the end
             const bool two = k > kWarp;
-            for (int i = k - 1; i >= 0; --i) {
-                const int own = i % kWarp, sl = i / kWarp;
+            double x[4][2];
+            if constexpr (sizeof(T) == 4) {
+                float xl[4][2];
 #pragma unroll
-                for (int qq = 0; qq < 4; ++qq) {
-                    const double bi = __shfl_sync(0xffffffffu, sl ? x[qq][1] : x[qq][0], own);
-                    if (lane < i) x[qq][0] = fma(-r11[rp(lane, i)], bi, x[qq][0]);
-                    if (two && lane + kWarp < i) x[qq][1] = fma(-r11[rp(lane + kWarp, i)], bi, x[qq][1]);
+                for (int qq = 0; qq < 4; ++qq) xl[qq][0] = xl[qq][1] = 0.0f;
+                const float2* r11f = reinterpret_cast<const float2*>(r11);
+                for (int i = k - 1; i >= 0; --i) {
+                    const int own = i % kWarp, sl = i / kWarp;
+#pragma unroll
+                    for (int qq = 0; qq < 4; ++qq) {
+                        const float bh = __shfl_sync(0xffffffffu, sl ? xv[qq][1] : xv[qq][0], own);
+                        const float bl = __shfl_sync(0xffffffffu, sl ? xl[qq][1] : xl[qq][0], own);
+                        if (lane < i) {
+                            const float2 r = r11f[rp(lane, i)];
+                            df_sub_mul(xv[qq][0], xl[qq][0], r.x, r.y, bh, bl);
+                        }
+                        if (two && lane + kWarp < i) {
+                            const float2 r = r11f[rp(lane + kWarp, i)];
+                            df_sub_mul(xv[qq][1], xl[qq][1], r.x, r.y, bh, bl);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int qq = 0; qq < 4; ++qq)
+#pragma unroll
+                    for (int s = 0; s < 2; ++s) x[qq][s] = (double)xv[qq][s] + (double)xl[qq][s];
+            } else {
+#pragma unroll
+                for (int qq = 0; qq < 4; ++qq)
+#pragma unroll
+                    for (int s = 0; s < 2; ++s) x[qq][s] = (double)xv[qq][s];
+                for (int i = k - 1; i >= 0; --i) {
+                    const int own = i % kWarp, sl = i / kWarp;
+#pragma unroll
+                    for (int qq = 0; qq < 4; ++qq) {
+                        const double bi = __shfl_sync(0xffffffffu, sl ? x[qq][1] : x[qq][0], own);
+                        if (lane < i) x[qq][0] = fma(-r11[rp(lane, i)], bi, x[qq][0]);
+                        if (two && lane + kWarp < i) x[qq][1] = fma(-r11[rp(lane + kWarp, i)], bi, x[qq][1]);
+                    }
                 }
             }
 #pragma unroll
