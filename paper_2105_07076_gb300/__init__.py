@@ -714,6 +714,71 @@ def _shape_signature(dtype, device, mats, ks) -> tuple:
 
 _TUNED: dict = {}
 
+# The tuner's choices can also persist across processes: set GBID_TUNE_CACHE
+# to a JSON file path. Entries are keyed by the element type, the GPU's name,
+# the library's instance table and a digest of the batch's shapes, so a
+# rebuilt library with other instances, or another GPU model, never reuses a
+# stale choice. Without the variable nothing is read or written.
+TUNE_CACHE_ENV = "GBID_TUNE_CACHE"
+
+
+def tune_cache_key(dtype_name: str, device_name: str, configs: list, shapes: list) -> str:
+    """Key of a persisted tuning: dtype, GPU name, instance table, shape multiset."""
+    import hashlib
+    import json
+
+    body = json.dumps({"configs": configs, "shapes": sorted([int(a), int(b), int(c)] for a, b, c in shapes)},
+                      sort_keys=True)
+    return f"{dtype_name}|{device_name}|{hashlib.sha256(body.encode()).hexdigest()[:32]}"
+
+
+def tune_cache_get(path: str, key: str):
+    """(config index, ms per instance) stored under key in the JSON file, or None
+    (missing or unreadable file, missing key, malformed entry)."""
+    import json
+
+    try:
+        with open(path) as f:
+            entry = json.load(f).get(key)
+        if entry is None:
+            return None
+        return int(entry["config"]), [float(x) for x in entry["ms"]]
+    except (OSError, ValueError, TypeError, KeyError, AttributeError):
+        return None
+
+
+def tune_cache_put(path: str, key: str, config: int, ms: list) -> None:
+    """Store one tuning in the JSON file (read, update, write to a temporary file
+    and rename, so a reader never sees a half-written file)."""
+    import json
+    import tempfile
+
+    data = {}
+    try:
+        with open(path) as f:
+            loaded = json.load(f)
+        if isinstance(loaded, dict):
+            data = loaded
+    except (OSError, ValueError):
+        pass
+    data[key] = {"config": int(config), "ms": [float(x) for x in ms]}
+    d = os.path.dirname(os.path.abspath(path))
+    fd, tmp = tempfile.mkstemp(dir=d, prefix=".gbid_tune_", suffix=".json")
+    try:
+        with os.fdopen(fd, "w") as f:
+            json.dump(data, f, sort_keys=True)
+        os.replace(tmp, path)
+    except BaseException:
+        if os.path.exists(tmp):
+            os.unlink(tmp)
+        raise
+
+
+def _persisted_key(plan) -> str:
+    shapes = [(A.shape[0], A.shape[1], k) for A, k in zip(plan.mats, plan.ks)]
+    return tune_cache_key(str(plan.dtype), torch.cuda.get_device_name(plan.device), batched_configs(plan.dtype),
+                          shapes)
+
 
 class BatchedPlan:
     """Descriptors, outputs and scratch of id_decompose_batched for a fixed list
@@ -726,8 +791,9 @@ class BatchedPlan:
     ``autotune=True`` instead times every instance on this batch
     (id_batched_autotune, which waits for the device) and keeps the fastest.
     The choice is remembered per (dtype, device, multiset of shapes), so a
-    later plan over the same shapes reuses it without timing again. All
-    instances give bit-identical results; ``tune_ms`` holds the timings.
+    later plan over the same shapes reuses it without timing again, and, when
+    GBID_TUNE_CACHE names a JSON file, across processes too. All instances
+    give bit-identical results; ``tune_ms`` holds the timings.
     """
 
     def __init__(self, mats: list, ks: list, *, config: int | None = None, autotune: bool = False,
@@ -772,6 +838,13 @@ class BatchedPlan:
         self.config = 0 if config is None else int(config)
         if config is None and autotune:
             cached = _TUNED.get(_shape_signature(dt, dev, self.mats, self.ks))
+            path = os.environ.get(TUNE_CACHE_ENV)
+            if cached is None and path:
+                cached = tune_cache_get(path, _persisted_key(self))
+                if cached is not None and not 0 <= cached[0] < len(cached[1]):
+                    cached = None
+                if cached is not None:
+                    _TUNED[_shape_signature(dt, dev, self.mats, self.ks)] = cached
             if cached is not None:
                 self.config, self.tune_ms = cached
             else:
@@ -793,6 +866,9 @@ class BatchedPlan:
             raise IdError(rc, "id_batched_autotune")
         self.config, self.tune_ms = int(best.value), [float(x) for x in ms]
         _TUNED[_shape_signature(self.dtype, self.device, self.mats, self.ks)] = (self.config, self.tune_ms)
+        path = os.environ.get(TUNE_CACHE_ENV)
+        if path:
+            tune_cache_put(path, _persisted_key(self), self.config, self.tune_ms)
         return self.config, self.tune_ms
 
     def __len__(self):

@@ -324,3 +324,34 @@ def test_missing_library_fails_loudly(tmp_path):
     ) % (ROOT, str(tmp_path / "libgbid.so"))
     out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=120)
     assert "raised" in out.stdout, out.stdout + out.stderr
+
+
+def test_tuning_cache_file(gbid, tmp_path):
+    """The persisted tuner choices: keys separate dtype, GPU model, instance
+    table and shape multiset (in any order); the file round-trips, keeps other
+    entries, survives a malformed file, and leaves no temporary files."""
+    cfgs = [{"threads": 256}, {"threads": 128}]
+    shapes = [(40, 90, 8), (100, 30, 12)]
+    key = gbid.tune_cache_key("torch.float32", "GPU X", cfgs, shapes)
+    assert key == gbid.tune_cache_key("torch.float32", "GPU X", cfgs, list(reversed(shapes)))
+    others = [gbid.tune_cache_key("torch.float64", "GPU X", cfgs, shapes),
+              gbid.tune_cache_key("torch.float32", "GPU Y", cfgs, shapes),
+              gbid.tune_cache_key("torch.float32", "GPU X", cfgs[:1], shapes),
+              gbid.tune_cache_key("torch.float32", "GPU X", cfgs, shapes[:1])]
+    assert len(set(others + [key])) == 5
+    path = str(tmp_path / "tune.json")
+    assert gbid.tune_cache_get(path, key) is None                    # no file yet
+    gbid.tune_cache_put(path, key, 1, [2.5, 1.5])
+    gbid.tune_cache_put(path, others[0], 0, [3.0, 4.0])
+    assert gbid.tune_cache_get(path, key) == (1, [2.5, 1.5])
+    assert gbid.tune_cache_get(path, others[0]) == (0, [3.0, 4.0])
+    assert gbid.tune_cache_get(path, others[1]) is None
+    assert sorted(os.listdir(tmp_path)) == ["tune.json"]
+    with open(path, "w") as f:
+        f.write("{not json")
+    assert gbid.tune_cache_get(path, key) is None
+    gbid.tune_cache_put(path, key, 1, [2.5, 1.5])                    # a malformed file is replaced
+    assert gbid.tune_cache_get(path, key) == (1, [2.5, 1.5])
+    with open(path, "w") as f:
+        f.write('{"%s": {"config": "x"}}' % key)
+    assert gbid.tune_cache_get(path, key) is None
