@@ -36,7 +36,6 @@ import os
 import statistics
 import subprocess
 import sys
-import tempfile
 import threading
 import time
 
@@ -48,6 +47,7 @@ WORKLOAD = "id_4096x8192_k256"
 METRIC = "IDs/s and effective TFLOP/s at stated rel. Frobenius error vs FP64 plain ID"
 UNIT = "IDs/s"
 REF_SAMPLE_STEPS = 4           # pivot steps per --impl reference step
+BATCHED_CPU_SAMPLE = 1024      # problems of the uneven batch the oracle decomposes for its CPU baseline
 
 
 def flops_cpqr(m, n, k):
@@ -180,14 +180,14 @@ def make_input(device, dtype):
 
 # ---------------------------------------------------------------- oracle CPU --
 ORACLE_SNIPPET = r"""
-import sys, time, json
+import io, sys, time, json
 import numpy as np
 sys.path.insert(0, sys.argv[1])
 from oracle import id_oracle as orc
-A = np.load(sys.argv[2])
-s = int(sys.argv[3])
-reps = int(sys.argv[4])
-full = sys.argv[5] == "full"
+A = np.load(io.BytesIO(sys.stdin.buffer.read()))
+s = int(sys.argv[2])
+reps = int(sys.argv[3])
+full = sys.argv[4] == "full"
 out = []
 for _ in range(reps):
     t0 = time.perf_counter()
@@ -200,21 +200,72 @@ print(json.dumps(out))
 """
 
 
+ONE_THREAD = {"OMP_NUM_THREADS": "1", "OPENBLAS_NUM_THREADS": "1", "MKL_NUM_THREADS": "1"}
+
+
+def _npy_bytes(save, *args, **kw) -> bytes:
+    import io
+
+    buf = io.BytesIO()
+    save(buf, *args, **kw)
+    return buf.getvalue()
+
+
 def time_oracle(A_cpu_np, steps, reps, full=False):
     """Seconds per call of the oracle (its first `steps` pivot steps, or a whole rank-`steps` ID
-    when `full`), single-threaded, in a fresh process."""
+    when `full`), single-threaded, in a fresh process (the matrix goes through its stdin)."""
     import numpy as np
 
-    with tempfile.TemporaryDirectory() as d:
-        path = os.path.join(d, "A.npy")
-        np.save(path, A_cpu_np)
-        env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-        r = subprocess.run([sys.executable, "-c", ORACLE_SNIPPET, ROOT, path, str(steps), str(reps),
-                            "full" if full else "steps"],
-                           capture_output=True, text=True, env=env, timeout=1800)
-        if r.returncode != 0:
-            raise RuntimeError(r.stderr[-2000:])
-        return json.loads(r.stdout.strip().splitlines()[-1])
+    r = subprocess.run([sys.executable, "-c", ORACLE_SNIPPET, ROOT, str(steps), str(reps),
+                        "full" if full else "steps"],
+                       input=_npy_bytes(np.save, A_cpu_np), capture_output=True, env=dict(os.environ, **ONE_THREAD),
+                       timeout=1800)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr.decode(errors="replace")[-2000:])
+    return json.loads(r.stdout.decode().strip().splitlines()[-1])
+
+
+MANY_SNIPPET = r"""
+import io, sys, time, json
+import numpy as np
+sys.path.insert(0, sys.argv[1])
+from oracle import id_oracle as orc
+d = np.load(io.BytesIO(sys.stdin.buffer.read()))
+ks = d["ks"]
+t0 = time.perf_counter()
+for i in range(len(ks)):
+    orc.interp_decomp(d["A%d" % i], int(ks[i]))
+print(json.dumps(time.perf_counter() - t0))
+"""
+
+
+def time_oracle_many(mats, ks, workers):
+    """Seconds for the oracle's complete IDs of the FP64 numpy matrices `mats`
+    on `workers` single-threaded processes that run at the same time, worker w
+    taking matrices w, w + workers, ...: the largest of their compute times
+    (process start and data transfer excluded)."""
+    import numpy as np
+
+    procs = []
+    for w in range(min(workers, len(mats))):
+        idx = list(range(w, len(mats), workers))
+        payload = _npy_bytes(np.savez, ks=np.array([ks[i] for i in idx], dtype=np.int64),
+                             **{f"A{j}": mats[i] for j, i in enumerate(idx)})
+        p = subprocess.Popen([sys.executable, "-c", MANY_SNIPPET, ROOT], stdin=subprocess.PIPE,
+                             stdout=subprocess.PIPE, stderr=subprocess.STDOUT, env=dict(os.environ, **ONE_THREAD))
+        procs.append((p, payload))
+    # each worker reads all of its input before it starts computing, so writing
+    # the inputs one after the other still lets the workers overlap
+    for p, payload in procs:
+        p.stdin.write(payload)
+        p.stdin.close()
+    secs = []
+    for p, _ in procs:
+        out = p.stdout.read().decode(errors="replace")
+        if p.wait(timeout=1800) != 0:
+            raise RuntimeError(out[-2000:])
+        secs.append(float(json.loads(out.strip().splitlines()[-1])))
+    return max(secs)
 
 
 def oracle_ids_per_s(sample_seconds, steps):
@@ -684,11 +735,13 @@ def latency_block(gbid, dev, steps):
             "note": "trailing-GEMV bytes s*sum_j (m-j)(n-j) over the best per-ID time (A stays in L2)"}
 
 
-def batched_block(gbid, dev, steps):
+def batched_block(gbid, dev, steps, cpu_sample=0):
     """The batched form: 4096 FP32 matrices, m ~ U[32, 256], n ~ U[m, 4m],
     k ~ U[8, 64], s_i = exp(-8 i / m), 10% non-negative sparse (seed 4), all
     decomposed by one persistent launch. The inputs plus scratch (about 1.7 GB)
-    exceed L2, so no flush is needed between launches."""
+    exceed L2, so no flush is needed between launches. With cpu_sample > 0 the
+    oracle decomposes the first cpu_sample problems on the host, on one core
+    and on every core (one single-threaded process per core)."""
     import torch
 
     import synth
@@ -726,12 +779,25 @@ def batched_block(gbid, dev, steps):
     statuses = {}
     for i in infos:
         statuses[i["status_name"]] = statuses.get(i["status_name"], 0) + 1
+    cpu = None
+    if cpu_sample > 0:
+        sample = [p["A"].double().cpu().numpy() for p in probs[:cpu_sample]]
+        ks_s = ks[:cpu_sample]
+        cores = os.cpu_count() or 1
+        t1 = time_oracle_many(sample, ks_s, 1)
+        tp = time_oracle_many(sample, ks_s, cores)
+        what = (f"complete IDs of the first {len(sample)} of the {BATCH_COUNT} problems (FP32 values in FP64) "
+                f"by the oracle, numpy")
+        cpu = {"value": len(sample) / t1, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{what}, one thread ({t1:.1f} s)",
+               "all_cores": {"value": len(sample) / tp, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{what}, {cores} single-threaded processes ({tp:.1f} s)"}}
     return {"workload": f"batched_{BATCH_COUNT}_uneven_f32", "ms_per_launch": ms,
             "value": BATCH_COUNT * 1000.0 / ms, "unit": UNIT, "eff_tflops": flops / (ms * 1e-3) / 1e12,
             "launches_per_step": 1, "statuses": statuses,
             "tuner": {"chosen": gbid.batched_configs(torch.float32)[plan.config],
                       "ms_per_instance": [round(x, 3) for x in plan.tune_ms]},
-            "err_over_tail": {"median": statistics.median(ratios), "max": max(ratios)}}
+            "err_over_tail": {"median": statistics.median(ratios), "max": max(ratios)}, "cpu_baseline": cpu}
 
 
 def run_gbid(args):
@@ -757,7 +823,8 @@ def run_gbid(args):
         elif args.only == "differentiable":
             side = differentiable_block(gbid, dev, args.steps)
         else:
-            side = batched_block(gbid, dev, max(3, min(args.steps, 10)))
+            side = batched_block(gbid, dev, max(3, min(args.steps, 10)),
+                                 BATCHED_CPU_SAMPLE if rank == 0 and world == 1 and not args.no_cpu_baseline else 0)
         if rank == 0:
             print(json.dumps(dict(side, n_gpus=world, steps=args.steps, warmup=args.warmup)), flush=True)
         return 0
@@ -813,7 +880,9 @@ def run_gbid(args):
         if args.only in ("all", "sampled") else None
     spa = sparse_block(gbid, dev, max(3, min(args.steps, 10))) if args.only in ("all", "sampled") else None
     rid = randomized_block(gbid, dev, max(2, min(args.steps, 5))) if args.only == "all" else None
-    bat = batched_block(gbid, dev, max(3, min(args.steps, 10))) if args.only == "all" else None
+    bat = batched_block(gbid, dev, max(3, min(args.steps, 10)),
+                        BATCHED_CPU_SAMPLE if rank == 0 and world == 1 and not args.no_cpu_baseline else 0) \
+        if args.only == "all" else None
     lat = latency_block(gbid, dev, args.steps) if args.only == "all" else None
     dif = differentiable_block(gbid, dev, args.steps) if args.only == "all" else None
 

@@ -41,3 +41,23 @@ def test_reference_other_ranks_exit_quietly():
     r = _run({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"}, timeout=120)
     assert r.returncode == 0, r.stderr[-2000:]
     assert not [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+
+
+def test_oracle_timer_over_worker_processes():
+    """The batched CPU baseline's timer: every worker runs its share of the
+    oracle IDs and reports its compute time; a failing worker raises."""
+    import numpy as np
+    import pytest
+
+    sys.path.insert(0, ROOT)
+    import bench
+
+    rng = np.random.default_rng(0)
+    mats = [rng.standard_normal((20 + 3 * i, 50)) for i in range(6)]
+    ks = [5] * 6
+    t1 = bench.time_oracle_many(mats, ks, 1)
+    t3 = bench.time_oracle_many(mats, ks, 3)
+    assert t1 > 0 and t3 > 0
+    assert bench.time_oracle_many(mats[:2], ks[:2], 8) > 0          # more workers than matrices
+    with pytest.raises(RuntimeError):
+        bench.time_oracle_many([rng.standard_normal((10, 20))], [11], 1)   # k > min(m, n): the oracle refuses
