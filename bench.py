@@ -783,7 +783,7 @@ def batched_block(gbid, dev, steps, cpu_sample=0):
     if cpu_sample > 0:
         sample = [p["A"].double().cpu().numpy() for p in probs[:cpu_sample]]
         ks_s = ks[:cpu_sample]
-        cores = os.cpu_count() or 1
+        cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
         t1 = time_oracle_many(sample, ks_s, 1)
         tp = time_oracle_many(sample, ks_s, cores)
         what = (f"complete IDs of the first {len(sample)} of the {BATCH_COUNT} problems (FP32 values in FP64) "
