@@ -48,6 +48,7 @@ METRIC = "IDs/s and effective TFLOP/s at stated rel. Frobenius error vs FP64 pla
 UNIT = "IDs/s"
 REF_SAMPLE_STEPS = 4           # pivot steps per --impl reference step
 BATCHED_CPU_SAMPLE = 1024      # problems of the uneven batch the oracle decomposes for its CPU baseline
+DIFF_CPU_SAMPLE = 64           # forward + gradient problems of the differentiable workload for its CPU baseline
 
 
 def flops_cpqr(m, n, k):
@@ -232,15 +233,22 @@ sys.path.insert(0, sys.argv[1])
 from oracle import id_oracle as orc
 d = np.load(io.BytesIO(sys.stdin.buffer.read()))
 ks = d["ks"]
+grad = sys.argv[2] == "grad"
 t0 = time.perf_counter()
 for i in range(len(ks)):
-    orc.interp_decomp(d["A%d" % i], int(ks[i]))
+    A = d["A%d" % i]
+    J, Z, _ = orc.interp_decomp(A, int(ks[i]))
+    if grad:
+        J = np.asarray(J, dtype=np.int64)
+        perm = np.concatenate([J, np.setdiff1d(np.arange(A.shape[1]), J)])
+        orc.id_grad(A, J, perm, d["G%d" % i])
 print(json.dumps(time.perf_counter() - t0))
 """
 
 
-def time_oracle_many(mats, ks, workers):
+def time_oracle_many(mats, ks, workers, grads=None):
     """Seconds for the oracle's complete IDs of the FP64 numpy matrices `mats`
+    (and, with `grads`, the gradient of <grads[i], Z> with the skeleton frozen)
     on `workers` single-threaded processes that run at the same time, worker w
     taking matrices w, w + workers, ...: the largest of their compute times
     (process start and data transfer excluded)."""
@@ -249,9 +257,12 @@ def time_oracle_many(mats, ks, workers):
     procs = []
     for w in range(min(workers, len(mats))):
         idx = list(range(w, len(mats), workers))
-        payload = _npy_bytes(np.savez, ks=np.array([ks[i] for i in idx], dtype=np.int64),
-                             **{f"A{j}": mats[i] for j, i in enumerate(idx)})
-        p = subprocess.Popen([sys.executable, "-c", MANY_SNIPPET, ROOT], stdin=subprocess.PIPE,
+        arrays = {f"A{j}": mats[i] for j, i in enumerate(idx)}
+        if grads is not None:
+            arrays.update({f"G{j}": grads[i] for j, i in enumerate(idx)})
+        payload = _npy_bytes(np.savez, ks=np.array([ks[i] for i in idx], dtype=np.int64), **arrays)
+        p = subprocess.Popen([sys.executable, "-c", MANY_SNIPPET, ROOT, "grad" if grads is not None else "id"],
+                             stdin=subprocess.PIPE,
                              stdout=subprocess.PIPE, stderr=subprocess.STDOUT, env=dict(os.environ, **ONE_THREAD))
         procs.append((p, payload))
     # each worker reads all of its input before it starts computing, so writing
@@ -598,7 +609,7 @@ def sparse_block(gbid, dev, steps):
 BATCH_COUNT = 4096
 
 
-def differentiable_block(gbid, dev, steps):
+def differentiable_block(gbid, dev, steps, cpu_sample=0):
     """The differentiable form: 256 FP32 matrices 512 x 1024, s_i = (1+i)^-2,
     k = 64 (seed 5): forward by one batched launch, then dL/dA for
     L = <G, Z> (G ~ N(0,1), seed 5) by id_backward per matrix, the 256 backward
@@ -656,7 +667,20 @@ def differentiable_block(gbid, dev, steps):
     bwd = statistics.mean(b.elapsed_time(c) for _, b, c in ev)
     infos = plan.read_infos()
     ok = sum(1 for i in infos if i["status_name"] == "ID_OK")
-    return {"workload": "diff_256x512x1024_k64_f32", "fwd_ms": fwd, "bwd_ms": bwd,
+    cpu = None
+    if cpu_sample > 0:
+        sample = [A.double().cpu().numpy() for A in mats[:cpu_sample]]
+        grads = [G.double().cpu().numpy() for G in Gs[:cpu_sample]]
+        cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+        t1 = time_oracle_many(sample, [k] * len(sample), 1, grads=grads)
+        tp = time_oracle_many(sample, [k] * len(sample), cores, grads=grads)
+        what = (f"forward ID and gradient of the first {len(sample)} of the {nb} problems (FP32 values in FP64) by "
+                f"the oracle, numpy")
+        cpu = {"value": len(sample) / t1, "unit": "IDs/s (forward + backward)", "cores": 1, "kind": "oracle",
+               "sample": f"{what}, one thread ({t1:.1f} s)",
+               "all_cores": {"value": len(sample) / tp, "unit": "IDs/s (forward + backward)", "cores": cores,
+                             "kind": "oracle", "sample": f"{what}, {cores} single-threaded processes ({tp:.1f} s)"}}
+    return {"workload": "diff_256x512x1024_k64_f32", "fwd_ms": fwd, "bwd_ms": bwd, "cpu_baseline": cpu,
             "value": nb * 1000.0 / (fwd + bwd), "unit": "IDs/s (forward + backward)",
             "bwd_graph": graph is not None, "statuses_ok": ok,
             "fwd_tuned_instance": gbid.batched_configs(torch.float32)[plan.config]}
@@ -821,7 +845,8 @@ def run_gbid(args):
         elif args.only == "latency":
             side = latency_block(gbid, dev, args.steps)
         elif args.only == "differentiable":
-            side = differentiable_block(gbid, dev, args.steps)
+            side = differentiable_block(gbid, dev, args.steps,
+                                        DIFF_CPU_SAMPLE if rank == 0 and world == 1 and not args.no_cpu_baseline else 0)
         else:
             side = batched_block(gbid, dev, max(3, min(args.steps, 10)),
                                  BATCHED_CPU_SAMPLE if rank == 0 and world == 1 and not args.no_cpu_baseline else 0)
@@ -884,7 +909,9 @@ def run_gbid(args):
                         BATCHED_CPU_SAMPLE if rank == 0 and world == 1 and not args.no_cpu_baseline else 0) \
         if args.only == "all" else None
     lat = latency_block(gbid, dev, args.steps) if args.only == "all" else None
-    dif = differentiable_block(gbid, dev, args.steps) if args.only == "all" else None
+    dif = differentiable_block(gbid, dev, args.steps,
+                               DIFF_CPU_SAMPLE if rank == 0 and world == 1 and not args.no_cpu_baseline else 0) \
+        if args.only == "all" else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

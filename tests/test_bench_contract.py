@@ -59,5 +59,7 @@ def test_oracle_timer_over_worker_processes():
     t3 = bench.time_oracle_many(mats, ks, 3)
     assert t1 > 0 and t3 > 0
     assert bench.time_oracle_many(mats[:2], ks[:2], 8) > 0          # more workers than matrices
+    grads = [rng.standard_normal((5, 50)) for _ in range(6)]           # forward ID plus gradient per matrix
+    assert bench.time_oracle_many(mats, ks, 2, grads=grads) > 0
     with pytest.raises(RuntimeError):
         bench.time_oracle_many([rng.standard_normal((10, 20))], [11], 1)   # k > min(m, n): the oracle refuses
