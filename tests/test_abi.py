@@ -355,3 +355,48 @@ def test_tuning_cache_file(gbid, tmp_path):
     with open(path, "w") as f:
         f.write('{"%s": {"config": "x"}}' % key)
     assert gbid.tune_cache_get(path, key) is None
+
+
+C_PROGRAM = r"""
+#include <stdio.h>
+#include "gbid.h"
+
+#define CHECK(c) do { if (!(c)) { printf("failed: %s\n", #c); return 1; } } while (0)
+
+int main(void) {
+    id_opts o = {0};
+    CHECK(id_workspace_size(ID_F64, 100, 300, 20, &o) > 0);
+    CHECK(id_workspace_size(ID_F64, 100, 300, 20, NULL) == id_workspace_size(ID_F64, 100, 300, 20, &o));
+    CHECK(id_workspace_size(ID_F32, 100, 300, 101, NULL) == 0);          /* k > min(m, n) */
+    CHECK(id_batched_problem_workspace_size(ID_F32, 100, 300, 20) > 0);
+    CHECK(id_batched_config_count(ID_F32) >= 2);
+    id_batched_config c;
+    CHECK(id_batched_config_get(ID_F32, 0, &c) == ID_OK && c.threads % 32 == 0);
+    CHECK(id_decompose(NULL, ID_F64, 100, 300, 300, 20, NULL, NULL, NULL, 300, NULL, 0, NULL, NULL) == ID_EINVAL);
+    CHECK(id_launch_count(ID_F64, 100, 300, 400, NULL) == -1);
+    printf("ok\n");
+    return 0;
+}
+"""
+
+
+def test_header_is_plain_c_and_callable_from_c(gbid, tmp_path):
+    """include/gbid.h compiles as strict C99, and a C program linked against
+    the library calls it (host-only entry points: sizes, the instance table,
+    argument errors)."""
+    import shutil
+    import subprocess
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "use_gbid.c"
+    src.write_text(C_PROGRAM)
+    exe = tmp_path / "use_gbid"
+    libdir = os.path.dirname(gbid.LIB_PATH)
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I" + os.path.join(ROOT, "include"),
+                        str(src), "-L" + libdir, "-lgbid", "-Wl,-rpath," + libdir, "-o", str(exe)],
+                       capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0 and r.stdout.strip() == "ok", r.stdout + r.stderr
