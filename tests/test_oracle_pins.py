@@ -428,15 +428,15 @@ def _golden_rows():
         for line in f:
             if line.startswith("#") or not line.strip():
                 continue
-            name, m, n, k, e_id, e_svd, zmax = line.split()
-            rows.append((name, int(m), int(n), int(k), float(e_id), float(e_svd), float(zmax)))
+            name, m, n, k, e_id, e_svd, zmax, e_rid = line.split()
+            rows.append((name, int(m), int(n), int(k), float(e_id), float(e_svd), float(zmax), float(e_rid)))
     return rows
 
 
 @pytest.mark.slow
 @pytest.mark.parametrize("row", _golden_rows(), ids=lambda r: r[0])
 def test_paper_table_statistics(row):
-    name, m, n, k, e_id, e_svd, zmax = row
+    name, m, n, k, e_id, e_svd, zmax, e_rid = row
     A = synth.paper_dataset(name, seed=2021)
     J, Z, info = orc.interp_decomp(A, k)
     err = orc.rel_error(A, J, Z)
@@ -444,3 +444,8 @@ def test_paper_table_statistics(row):
     assert info["max_abs_z"] <= zmax + 1e-9
     sv = np.linalg.svd(A, compute_uv=False)
     assert synth.tail_bound(sv, k) == pytest.approx(e_svd, abs=0.005)
+    # the column-sampling Optim RID (Sec. 2.2) with the paper's oversampling p = k + floor(0.2 k)
+    p = k + int(0.2 * k)
+    idx = np.random.default_rng(2021).choice(n, size=p, replace=False)
+    Jr, Zr = orc.sampled_interp_decomp(A, idx, k)[:2]
+    assert orc.rel_error(A, np.asarray(Jr), Zr) == pytest.approx(e_rid, abs=0.005)
