@@ -428,15 +428,16 @@ def _golden_rows():
         for line in f:
             if line.startswith("#") or not line.strip():
                 continue
-            name, m, n, k, e_id, e_svd, zmax, e_rid = line.split()
-            rows.append((name, int(m), int(n), int(k), float(e_id), float(e_svd), float(zmax), float(e_rid)))
+            name, m, n, k, e_id, e_svd, zmax, e_rid, zmax_rid = line.split()
+            rows.append((name, int(m), int(n), int(k), float(e_id), float(e_svd), float(zmax), float(e_rid),
+                         float(zmax_rid)))
     return rows
 
 
 @pytest.mark.slow
 @pytest.mark.parametrize("row", _golden_rows(), ids=lambda r: r[0])
 def test_paper_table_statistics(row):
-    name, m, n, k, e_id, e_svd, zmax, e_rid = row
+    name, m, n, k, e_id, e_svd, zmax, e_rid, zmax_rid = row
     A = synth.paper_dataset(name, seed=2021)
     J, Z, info = orc.interp_decomp(A, k)
     err = orc.rel_error(A, J, Z)
@@ -449,3 +450,4 @@ def test_paper_table_statistics(row):
     idx = np.random.default_rng(2021).choice(n, size=p, replace=False)
     Jr, Zr = orc.sampled_interp_decomp(A, idx, k)[:2]
     assert orc.rel_error(A, np.asarray(Jr), Zr) == pytest.approx(e_rid, abs=0.005)
+    assert np.abs(Zr).max() <= zmax_rid + 1e-9
