@@ -824,6 +824,18 @@ def batched_block(gbid, dev, steps, cpu_sample=0):
             "err_over_tail": {"median": statistics.median(ratios), "max": max(ratios)}, "cpu_baseline": cpu}
 
 
+def guarded(name, fn, *a):
+    """fn(*a), or {"error": ...} with the traceback on stderr if it raises."""
+    import traceback
+
+    try:
+        return fn(*a)
+    except Exception as exc:                      # noqa: BLE001 - reported in the JSON line
+        traceback.print_exc()
+        print(f"side workload {name} failed: {exc!r}", file=sys.stderr, flush=True)
+        return {"workload": name, "error": repr(exc)[:500]}
+
+
 def run_gbid(args):
     import torch
     import torch.distributed as dist
@@ -897,29 +909,32 @@ def run_gbid(args):
     e2e_v, h2d, d2h = e2e_rate(gbid, results["f64"]["A"], max(2, min(args.steps, 5)))
     e2e_v = aggregate_rate(max_over_ranks(1000.0 / e2e_v, world, dev), world)
 
-    samp = sampled_block(gbid, dev, max(3, min(args.steps, 10)), {n: r["A"] for n, r in results.items()}) \
-        if args.only in ("all", "sampled") else None
-    lst = listing_block(gbid, dev, max(3, min(args.steps, 10)), {n: r["A"] for n, r in results.items()}) \
-        if args.only in ("all", "sampled") else None
-    two = two_sided_block(gbid, dev, max(3, min(args.steps, 10)), {n: r["A"] for n, r in results.items()}) \
-        if args.only in ("all", "sampled") else None
-    spa = sparse_block(gbid, dev, max(3, min(args.steps, 10))) if args.only in ("all", "sampled") else None
-    rid = randomized_block(gbid, dev, max(2, min(args.steps, 5))) if args.only == "all" else None
-    bat = batched_block(gbid, dev, max(3, min(args.steps, 10)),
-                        BATCHED_CPU_SAMPLE if rank == 0 and world == 1 and not args.no_cpu_baseline else 0) \
-        if args.only == "all" else None
-    lat = latency_block(gbid, dev, args.steps) if args.only == "all" else None
-    dif = differentiable_block(gbid, dev, args.steps,
-                               DIFF_CPU_SAMPLE if rank == 0 and world == 1 and not args.no_cpu_baseline else 0) \
-        if args.only == "all" else None
+    # the side workloads: a failure in one is reported in the line, not fatal to the headline numbers above
+    mats = {n: r["A"] for n, r in results.items()}
+    side_steps = max(3, min(args.steps, 10))
+    cpu_ok = rank == 0 and world == 1 and not args.no_cpu_baseline
+    with_sampled = args.only in ("all", "sampled")
+    with_all = args.only == "all"
+    samp = guarded("sampled", sampled_block, gbid, dev, side_steps, mats) if with_sampled else None
+    lst = guarded("listing", listing_block, gbid, dev, side_steps, mats) if with_sampled else None
+    two = guarded("two_sided", two_sided_block, gbid, dev, side_steps, mats) if with_sampled else None
+    spa = guarded("sparse", sparse_block, gbid, dev, side_steps) if with_sampled else None
+    rid = guarded("randomized", randomized_block, gbid, dev, max(2, min(args.steps, 5))) if with_all else None
+    bat = guarded("batched", batched_block, gbid, dev, side_steps, BATCHED_CPU_SAMPLE if cpu_ok else 0) \
+        if with_all else None
+    lat = guarded("latency", latency_block, gbid, dev, args.steps) if with_all else None
+    dif = guarded("differentiable", differentiable_block, gbid, dev, args.steps, DIFF_CPU_SAMPLE if cpu_ok else 0) \
+        if with_all else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        A_np = results["f64"]["A"].cpu().numpy()
-        secs = time_oracle(A_np, K_RANK, 1, full=True)
-        cpu = {"value": 1.0 / secs[0], "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"one complete rank-{K_RANK} ID of the same 4096 x 8192 FP64 matrix by the oracle "
-                         f"({secs[0]:.1f} s, numpy, one thread)"}
+        def one_oracle_id():
+            secs = time_oracle(results["f64"]["A"].cpu().numpy(), K_RANK, 1, full=True)
+            return {"value": 1.0 / secs[0], "unit": UNIT, "cores": 1, "kind": "oracle",
+                    "sample": f"one complete rank-{K_RANK} ID of the same 4096 x 8192 FP64 matrix by the oracle "
+                              f"({secs[0]:.1f} s, numpy, one thread)"}
+
+        cpu = guarded("cpu_baseline", one_oracle_id)
     if world > 1 and dist.is_initialized():
         dist.barrier()
     if rank != 0:

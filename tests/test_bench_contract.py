@@ -63,3 +63,17 @@ def test_oracle_timer_over_worker_processes():
     assert bench.time_oracle_many(mats, ks, 2, grads=grads) > 0
     with pytest.raises(RuntimeError):
         bench.time_oracle_many([rng.standard_normal((10, 20))], [11], 1)   # k > min(m, n): the oracle refuses
+
+
+def test_a_failing_side_workload_is_reported_not_fatal(capsys):
+    sys.path.insert(0, ROOT)
+    import bench
+
+    assert bench.guarded("ok", lambda a, b: a + b, 2, 3) == 5
+
+    def boom():
+        raise ValueError("no device")
+
+    out = bench.guarded("side", boom)
+    assert out["workload"] == "side" and "no device" in out["error"]
+    assert "side workload side failed" in capsys.readouterr().err
