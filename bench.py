@@ -9,9 +9,10 @@ the same matrix is measured in the same run and reported beside it.
 
 The line also carries, under "randomized", the randomized ID of a 16384 x
 32768 FP32 matrix (s_i = (1+i)^-1.5, k = 512): BF16 Gaussian sketch on the
-tensor cores, CPQR of the 522 x 32768 sketch, FP64 solve; and under
-"batched", 4096 uneven FP32 IDs (m ~ U[32, 256], n ~ U[m, 4m], k ~ U[8, 64])
-in one persistent launch; and under "latency", back-to-back 200 x 400 FP64
+tensor cores, CPQR of the 522 x 32768 sketch, the sketch's T in FP32, one
+least-squares refinement of Z against A; and under "batched", 4096 uneven
+FP32 IDs (m ~ U[32, 256], n ~ U[m, 4m], k ~ U[8, 64]) in one persistent
+launch, its tile shape picked by the library's tuner; and under "latency", back-to-back 200 x 400 FP64
 IDs at k = 20; and under "differentiable", 256 IDs of 512 x 1024 at k = 64
 forward (batched) and backward; and under "sampled", the paper's
 column-sampling Optim RID of the headline matrices (p = 307 sampled columns),
