@@ -438,7 +438,7 @@ def randomized_block(gbid, dev, steps):
     del A, C
     return {"workload": f"rid_{RM}x{RN}_k{RK}_l{RL}", "ms_per_step": ms, "value": 1000.0 / ms, "unit": UNIT,
             "kernel_ms": per, "rel_err": err, "tail_bound": tail, "status": info["status_name"],
-            "dtype": "bf16 sketch (FP32 accumulate), f32 CPQR, f64 solve, one least-squares refinement "
+            "dtype": "bf16 sketch (FP32 accumulate), f32 CPQR, f32 solve of the sketch's T, one least-squares refinement "
                      "(double-float Gram, f64 Cholesky, f32-accurate GEMMs)",
             "sketch_roofline": {"bound": "tensor", "achieved": sk_tflops, "peak": bf16, "unit": "TFLOP/s",
                                 "frac": sk_tflops / bf16, "peak_source": src}}
