@@ -35,7 +35,9 @@
  *     is non-NULL). No entry point aborts or traps.
  *   - Precision: ID_F64 computes in FP64 throughout. ID_F32 stores and
  *     updates the matrix in FP32, keeps the residual column norms and their
- *     downdate in FP64, and solves T = R11^{-1} R12 in FP64.
+ *     downdate in FP64, and solves T = R11^{-1} R12 in FP64, except where an
+ *     entry point states otherwise (the batched form's double-float solve,
+ *     the randomized ID's FP32 solve that only seeds its refinement).
  */
 #ifndef GBID_H
 #define GBID_H
@@ -224,11 +226,11 @@ int id_sketch(const void* A, id_dtype dtype, int64_t m, int64_t n, int64_t lda, 
 
 /* id_decompose_randomized -- randomized rank-k ID of A (m x n, m <= n) from a
  * Gaussian sketch: Y = Omega A (id_sketch, tensor cores), k steps of column-
- * pivoted QR of Y (FP32 matrix, FP64 residual norms), T = R11^{-1} R12 of Y's R
- * in FP64, Z = [I T] P^T. The skeleton J indexes columns of A. By default
- * (opts->refine = 0) Z is then refined once against A (id_refine): the
- * least-squares Z for J that Sec. 2.2 asks for; opts->refine = -1 keeps the
- * sketch's Z (T then comes from Y's R in FP64 instead of FP32).
+ * pivoted QR of Y (FP32 matrix, FP64 residual norms), T = R11^{-1} R12 of Y's R,
+ * Z = [I T] P^T. The skeleton J indexes columns of A. By default
+ * (opts->refine = 0) T is solved in FP32 and Z is then refined once against A
+ * (id_refine): the least-squares Z for J that Sec. 2.2 asks for.
+ * opts->refine = -1 keeps the sketch's Z, with T solved in FP64.
  *
  *   A      [in]  m x n FP32 row-major, n <= lda < 2^31, lda a multiple of 4, 16-byte aligned.
  *   Omega  [in]  l x m BF16 row-major, ldo >= m, ldo a multiple of 8, 16-byte
