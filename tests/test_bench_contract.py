@@ -77,3 +77,23 @@ def test_a_failing_side_workload_is_reported_not_fatal(capsys):
     out = bench.guarded("side", boom)
     assert out["workload"] == "side" and "no device" in out["error"]
     assert "side workload side failed" in capsys.readouterr().err
+
+
+def test_algorithmic_units_match_the_stated_figures():
+    """The roofline's work units: the flop convention 4 (m-j)(n-j) per step plus
+    k^2 (n-k), the algorithmic bytes s sum (m-j)(n-j) + s m n, and the FP64
+    operations the left-looking form executes, at 4096 x 8192, k = 256."""
+    import pytest
+
+    sys.path.insert(0, ROOT)
+    import bench
+
+    assert bench.flops_cpqr(4096, 8192, 256) == pytest.approx(3.28e10, rel=2e-3)
+    assert bench.flops_solve(8192, 256) == pytest.approx(5.2e8, rel=1e-2)
+    assert bench.bytes_cpqr(4096, 8192, 256, 8) == pytest.approx(65.8e9, rel=2e-3)
+    assert bench.bytes_cpqr(4096, 8192, 256, 4) == pytest.approx(32.9e9, rel=2e-3)
+    assert bench.fp64_flops_executed(4096, 8192, 256) == pytest.approx(1.79e10, rel=3e-3)
+    # closed forms of the sums on a small case
+    m, n, k = 7, 11, 5
+    assert bench.flops_cpqr(m, n, k) == sum(4 * (m - j) * (n - j) for j in range(k))
+    assert bench.bytes_cpqr(m, n, k, 8) == 8 * (sum((m - j) * (n - j) for j in range(k)) + m * n)
