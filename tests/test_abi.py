@@ -400,3 +400,23 @@ def test_header_is_plain_c_and_callable_from_c(gbid, tmp_path):
     assert r.returncode == 0, r.stderr
     r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
     assert r.returncode == 0 and r.stdout.strip() == "ok", r.stdout + r.stderr
+
+
+def test_cpu_tensors_are_refused_not_computed(gbid):
+    """No CPU fallback: every device-side entry point of the binding rejects a
+    CPU tensor before any work."""
+    A = torch.randn(10, 20, dtype=torch.float64)
+    J = torch.arange(5, dtype=torch.int32)
+    calls = [
+        lambda: gbid.id_decompose(A, 5),
+        lambda: gbid.id_decompose_randomized(A.float(), torch.randn(8, 10).to(torch.bfloat16), 5),
+        lambda: gbid.id_decompose_batched([A], [5]),
+        lambda: gbid.id_refine(A.float(), J, torch.zeros(5, 20)),
+        lambda: gbid.id_decompose_two_sided(A, 5),
+        lambda: gbid.id_decompose_sampled(A, list(range(8)), 5),
+        lambda: gbid.id_reconstruct(A, J, torch.zeros(5, 20, dtype=torch.float64)),
+        lambda: gbid.IdFunction.apply(A, 5),
+    ]
+    for call in calls:
+        with pytest.raises(ValueError, match="CUDA"):
+            call()
