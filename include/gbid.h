@@ -397,6 +397,18 @@ int id_batched_autotune(const id_problem* problems, int64_t count, id_dtype dtyp
  * `work` to *info (host) and wait for `stream`. Returns info->status. */
 int id_info_read(const void* work, id_info* info, void* stream);
 
+/* id_selftest_bounded_wait -- runs the library's bounded device wait (the
+ * primitive behind every grid barrier of the CPQR kernel) on a counter that
+ * nothing increments: the wait must give up after its poll limit (2^22
+ * polls, a few seconds) and report a timeout instead of hanging, leaving the
+ * context usable. work: DEVICE scratch of ID_SELFTEST_WORK_BYTES, 256-byte
+ * aligned. *status (HOST) receives ID_ETIMEOUT when the wait gave up as
+ * designed (ID_OK would mean it did not). WAITS for the stream. Returns
+ * ID_OK, ID_EINVAL (NULL pointer, small or misaligned work) or ID_ECUDA.
+ * Failure detection of the library's own making; the paper has none. */
+#define ID_SELFTEST_WORK_BYTES 4096
+int id_selftest_bounded_wait(void* work, size_t work_bytes, int* status, void* stream);
+
 /* Number of kernel launches one id_decompose call enqueues for this problem
  * (memsets excluded). Returns -1 for invalid arguments. */
 int64_t id_launch_count(id_dtype dtype, int64_t m, int64_t n, int64_t k, const id_opts* opts);

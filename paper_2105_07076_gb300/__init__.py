@@ -117,6 +117,7 @@ _SIG = {
     "id_refine": (ctypes.c_int, [_P, ctypes.c_int, _I64, _I64, _I64, _I64, _P, _P, _I64, _P, ctypes.c_size_t, _P, _P]),
     "id_launch_count": (ctypes.c_int64, [ctypes.c_int, _I64, _I64, _I64, _P]),
     "id_cpqr_residual_norms": (ctypes.c_int, [_P, ctypes.c_int, _I64, _I64, _I64, _I64, _P, _P, _P]),
+    "id_selftest_bounded_wait": (ctypes.c_int, [_P, ctypes.c_size_t, _P, _P]),
     "id_trace_enable": (ctypes.c_int, [ctypes.c_int]),
     "id_trace_read": (ctypes.c_int, [_P, _P, ctypes.c_int]),
     "id_version": (ctypes.c_char_p, []),
@@ -646,6 +647,23 @@ def id_solve(Xcm: torch.Tensor, k: int) -> torch.Tensor:
     if rc < 0:
         raise IdError(rc, "id_solve")
     return T[:, : n - k]
+
+
+SELFTEST_WORK_BYTES = 4096    # ID_SELFTEST_WORK_BYTES
+
+
+def selftest_bounded_wait(device=None) -> int:
+    """Run the library's bounded device wait on a counter nothing increments
+    (id_selftest_bounded_wait). Returns ID_ETIMEOUT when the wait gave up as
+    designed; waits for the device (a few seconds)."""
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    work = torch.empty(SELFTEST_WORK_BYTES, dtype=torch.uint8, device=dev)
+    status = ctypes.c_int(1)
+    with torch.cuda.device(dev):
+        rc = lib().id_selftest_bounded_wait(work.data_ptr(), work.numel(), ctypes.byref(status), _stream(dev))
+    if rc != ID_OK:
+        raise IdError(rc, "id_selftest_bounded_wait")
+    return int(status.value)
 
 
 def launch_count(dtype: torch.dtype, m: int, n: int, k: int, nb: int = 0, engine: int = ENGINE_AUTO) -> int:

@@ -188,6 +188,14 @@ __device__ bool wait_geq(const unsigned* p, unsigned target, State* st) {
     return true;
 }
 
+// Self-test of the bounded wait: thread 0 waits on a counter that nothing
+// increments, so the wait gives up after kSpinLimit polls and records
+// kStatTimeout, the path every barrier of k_cpqr takes when a CTA never
+// arrives. One CTA, no other waiter: the kernel always ends.
+__global__ void k_selftest_wait(const unsigned* counter, State* st) {
+    if (threadIdx.x == 0) wait_geq(counter, 1u, st);
+}
+
 __device__ void grid_sync(unsigned* bar, unsigned& epoch, State* st) {
     __syncthreads();
     ++epoch;
@@ -1485,3 +1493,20 @@ template cudaError_t cpqr_run<double>(const CpqrPlan&, cudaStream_t);
 template cudaError_t cpqr_run<float>(const CpqrPlan&, cudaStream_t);
 
 }  // namespace gbid
+
+extern "C" int id_selftest_bounded_wait(void* work, size_t work_bytes, int* status, void* stream) {
+    static_assert(256 + sizeof(gbid::State) <= ID_SELFTEST_WORK_BYTES, "self-test scratch");
+    if (!work || !status || work_bytes < ID_SELFTEST_WORK_BYTES || (reinterpret_cast<uintptr_t>(work) & 255))
+        return ID_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cudaMemsetAsync(work, 0, ID_SELFTEST_WORK_BYTES, s) != cudaSuccess) return ID_ECUDA;
+    const unsigned* counter = static_cast<const unsigned*>(work);
+    gbid::State* st = reinterpret_cast<gbid::State*>(static_cast<char*>(work) + 256);
+    gbid::k_selftest_wait<<<1, 32, 0, s>>>(counter, st);
+    if (cudaGetLastError() != cudaSuccess) return ID_ECUDA;
+    int bits = 0;
+    if (cudaMemcpyAsync(&bits, &st->status, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return ID_ECUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return ID_ECUDA;
+    *status = (bits & gbid::kStatTimeout) ? ID_ETIMEOUT : ID_OK;
+    return ID_OK;
+}

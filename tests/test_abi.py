@@ -420,3 +420,15 @@ def test_cpu_tensors_are_refused_not_computed(gbid):
     for call in calls:
         with pytest.raises(ValueError, match="CUDA"):
             call()
+
+
+def test_bounded_wait_selftest_argument_rules(gbid):
+    """id_selftest_bounded_wait checks its scratch before any CUDA work."""
+    L = gbid.lib()
+    st = ctypes.c_int(7)
+    assert L.id_selftest_bounded_wait(None, 4096, ctypes.byref(st), None) == gbid.ID_EINVAL
+    assert L.id_selftest_bounded_wait(ctypes.c_void_p(4096), 4095, ctypes.byref(st), None) == gbid.ID_EINVAL
+    assert L.id_selftest_bounded_wait(ctypes.c_void_p(4096 + 16), 4096, ctypes.byref(st), None) == gbid.ID_EINVAL
+    assert L.id_selftest_bounded_wait(ctypes.c_void_p(4096), 4096, None, None) == gbid.ID_EINVAL
+    assert st.value == 7
+    assert gbid.SELFTEST_WORK_BYTES == 4096

@@ -1,4 +1,7 @@
-"""Tall working matrices: the k_cpqr configurations that only a large m reaches.
+"""GPU cases written but not yet run on a GB300: they run only with
+GBID_STAGED_TESTS=1 in the environment until a run has shown them green.
+
+Tall working matrices: the k_cpqr configurations that only a large m reaches.
 
 Beyond about 13 400 FP64 rows (27 900 FP32) the reflector's shared-memory
 copy leaves room for one CTA per SM instead of two; beyond about 25 000 FP64
@@ -8,9 +11,14 @@ matrix with graded column scales and checks the pivots by the oracle's greedy
 replay and Z against the oracle's Z for the GPU's pivots (the same bars as the
 other parity tests).
 
-Each case moves several GB through the oracle on the host, so the module runs
-only with GBID_TALL_TESTS=1 in the environment.
+Each tall case moves several GB through the oracle on the host.
+
+The bounded wait: the library's wait primitive (behind every grid barrier of
+the CPQR kernel), run on a counter that nothing increments, must give up and
+report ID_ETIMEOUT, and the context must stay usable afterwards.
 """
+import time
+
 import math
 import os
 
@@ -21,8 +29,8 @@ import torch
 from oracle import id_oracle as orc
 
 pytestmark = [pytest.mark.gpu,
-              pytest.mark.skipif(os.environ.get("GBID_TALL_TESTS") != "1",
-                                 reason="tall-matrix cases run with GBID_TALL_TESTS=1")]
+              pytest.mark.skipif(os.environ.get("GBID_STAGED_TESTS") != "1",
+                                 reason="staged GPU cases run with GBID_STAGED_TESTS=1")]
 
 U32 = 2.0 ** -24
 
@@ -58,3 +66,13 @@ def test_tall_working_matrix(gbid, dtype, m, n, k):
     Zo = orc.interp_decomp(Ah, k, pivots=Jg)[1]
     bar = 1e-10 if dtype == torch.float64 else max(1e-4, 2 * np.linalg.cond(Ah[:, Jg]) * U32)
     assert np.linalg.norm(Zg - Zo) / np.linalg.norm(Zo) <= bar
+
+
+def test_bounded_wait_gives_up_and_the_context_survives(gbid):
+    t0 = time.monotonic()
+    assert gbid.selftest_bounded_wait() == gbid.ID_ETIMEOUT
+    assert time.monotonic() - t0 < 60.0
+    A = torch.randn(40, 90, dtype=torch.float64, device="cuda")
+    J, Z, info = gbid.id_decompose(A, 8)
+    assert info["status"] == gbid.ID_OK
+    assert torch.equal(Z[torch.arange(8, device="cuda"), J.long()], torch.ones(8, dtype=torch.float64, device="cuda"))
