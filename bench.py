@@ -825,6 +825,66 @@ def batched_block(gbid, dev, steps, cpu_sample=0):
             "err_over_tail": {"median": statistics.median(ratios), "max": max(ratios)}, "cpu_baseline": cpu}
 
 
+def compare_block(gbid, dev, steps):
+    """The mixed-precision and batched forms beside the plain FP64 ID at the
+    same reconstruction error: the randomized ID of the 16384 x 32768 FP32
+    matrix against the FP64 ID of the same matrix (promoted), and the FP32
+    batched launch against the FP64 batched launch of the same 4096 problems.
+    Only with --only compare: the FP64 ID at 16384 rows takes the one-CTA-per-SM
+    configuration of the CPQR kernel."""
+    import torch
+
+    import synth
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        s = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(reps):
+            out = fn()
+        e1.record(s)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps, out
+
+    out = {"workload": "same-error comparisons"}
+    A = synth.lowrank(RM, RN, synth.spectrum("poly1.5", RM), 3, device=dev, dtype=torch.float32,
+                      gen_dtype=torch.float32)
+    om = synth.gaussian_sketch_bf16(RL, RM, seed=33, device=dev)
+    ms_r, (J, Z, _) = timed(lambda: gbid.id_decompose_randomized(A, om, RK, sync=False), max(2, steps))
+    err_r = rel_error_gpu(A, J, Z)
+    A64 = A.double()
+    del J, Z
+    ms_d, (J, Z, info) = timed(lambda: gbid.id_decompose(A64, RK, sync=False), 2)
+    err_d = rel_error_gpu(A64, J, Z)
+    out["randomized_vs_fp64"] = {"matrix": f"{RM}x{RN} k={RK}", "randomized_ms": ms_r, "randomized_rel_err": err_r,
+                                 "fp64_ms": ms_d, "fp64_rel_err": err_d, "speedup": ms_d / ms_r}
+    del A, A64, J, Z
+    torch.cuda.empty_cache()
+    probs = synth.batched_uneven(BATCH_COUNT, 4, dtype=torch.float32, device=dev)
+    res = {}
+    for name, dt in (("f32", torch.float32), ("f64", torch.float64)):
+        mats = [p["A"].to(dt) for p in probs]
+        plan = gbid.BatchedPlan(mats, [p["k"] for p in probs], autotune=True)
+        ms, _ = timed(plan.run, steps)
+        ratios = []
+        for p, A_, J_, Z_ in zip(probs, mats, plan.J, plan.Z):
+            if p["kind"] == "lowrank":
+                A_64 = A_.double()
+                ratios.append((torch.linalg.norm(A_64 - A_64[:, J_.long()] @ Z_.double()) /
+                               torch.linalg.norm(A_64)).item())
+        res[name] = {"ms_per_launch": ms, "IDs_per_s": BATCH_COUNT * 1000.0 / ms,
+                     "median_rel_err": statistics.median(ratios), "instance": batched_configs_of(gbid, dt, plan)}
+    res["speedup_f32_over_f64"] = res["f64"]["ms_per_launch"] / res["f32"]["ms_per_launch"]
+    out["batched_f32_vs_f64"] = res
+    return out
+
+
+def batched_configs_of(gbid, dt, plan):
+    return gbid.batched_configs(dt)[plan.config]
+
+
 def guarded(name, fn, *a):
     """fn(*a), or {"error": ...} with the traceback on stderr if it raises."""
     import traceback
@@ -852,8 +912,10 @@ def run_gbid(args):
     import paper_2105_07076_gb300 as gbid
 
     dev = torch.device("cuda", local)
-    if args.only in ("randomized", "batched", "latency", "differentiable"):  # one side workload alone
-        if args.only == "randomized":
+    if args.only in ("randomized", "batched", "latency", "differentiable", "compare"):  # one side workload alone
+        if args.only == "compare":
+            side = compare_block(gbid, dev, max(3, min(args.steps, 10)))
+        elif args.only == "randomized":
             side = randomized_block(gbid, dev, max(2, min(args.steps, 5)))
         elif args.only == "latency":
             side = latency_block(gbid, dev, args.steps)
@@ -982,10 +1044,12 @@ def main():
     ap.add_argument("--impl", default="gbid", choices=["gbid", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only", default="all",
-                    choices=["all", "id", "sampled", "randomized", "batched", "latency", "differentiable"],
+                    choices=["all", "id", "sampled", "randomized", "batched", "latency", "differentiable",
+                             "compare"],
                     help="id: the 4096 x 8192 ID alone; sampled: the ID, the column-sampling RID and the paper's "
                          "listing outputs (normal-equation Z, C @ Z) of the same matrices; randomized / batched / "
-                         "latency / differentiable: that side workload alone")
+                         "latency / differentiable: that side workload alone; compare: the randomized and "
+                         "batched forms beside the FP64 ID of the same inputs (not part of the default run)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
