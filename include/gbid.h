@@ -150,9 +150,13 @@ int id_decompose_host(const void* A_host, id_dtype dtype, int64_t m, int64_t n, 
  * which every GPU that loads the library keeps until the process exits. The
  * paper has no counterpart; this is a deployment convenience.
  *
- *   Arguments as for id_decompose, minus work/work_bytes.
+ *   Arguments as for id_decompose, minus work/work_bytes. `info` must be
+ *   NULL when the call is enqueued into a stream that is being captured (a
+ *   non-NULL info makes the call wait for the stream, which capture forbids).
  *   Returns ID_ENOMEM, before enqueuing anything, when
- *   id_workspace_size(dtype, m, n, k, opts) > ID_NOALLOC_SCRATCH_BYTES.
+ *   id_workspace_size(dtype, m, n, k, opts) > ID_NOALLOC_SCRATCH_BYTES, and
+ *   ID_EINVAL when opts->zsolve != 0 (that route's library GEMMs create a
+ *   handle, and allocate, on first use).
  *   The first call on a device looks up the array's device address (with that
  *   device current); make that first call before any stream capture.
  *   All calls share the one array: calls that may overlap on the GPU (other

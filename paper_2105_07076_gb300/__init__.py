@@ -228,9 +228,12 @@ def id_decompose(A: torch.Tensor, k: int, *, nb: int = 0, engine: int = ENGINE_A
 NOALLOC_SCRATCH_BYTES = 32 << 20   # ID_NOALLOC_SCRATCH_BYTES in gbid.h
 
 
-def id_decompose_noalloc(A: torch.Tensor, k: int, *, nb: int = 0, out: tuple | None = None):
+def id_decompose_noalloc(A: torch.Tensor, k: int, *, nb: int = 0, out: tuple | None = None, sync: bool = True):
     """The ID with the library's fixed scratch instead of a workspace, for callers that
-    cannot allocate device memory (only J and Z are allocated here, unless ``out`` is given)."""
+    cannot allocate device memory (only J and Z are allocated here, unless ``out`` is given).
+
+    sync=False passes no info pointer, so nothing waits for the stream (the form to use
+    while the stream is being captured); the third result is then None."""
     _check_cuda_matrix(A, "A")
     m, n = A.shape
     dev = A.device
@@ -243,10 +246,11 @@ def id_decompose_noalloc(A: torch.Tensor, k: int, *, nb: int = 0, out: tuple | N
     info = IdInfo()
     with torch.cuda.device(dev):
         rc = lib().id_decompose_noalloc(A.data_ptr(), _DTYPES[A.dtype], m, n, A.stride(0), k, ctypes.byref(o),
-                                        J.data_ptr(), Z.data_ptr(), Z.stride(0), ctypes.byref(info), _stream(dev))
+                                        J.data_ptr(), Z.data_ptr(), Z.stride(0),
+                                        ctypes.byref(info) if sync else None, _stream(dev))
     if rc in _CALL_ERRORS:
         raise IdError(rc, "id_decompose_noalloc")
-    return J, Z, info.as_dict()
+    return J, Z, (info.as_dict() if sync else None)
 
 
 def id_sketch(A: torch.Tensor, omega: torch.Tensor, *, out: torch.Tensor | None = None, sync: bool = True):

@@ -1,6 +1,7 @@
 // C ABI of the ID library: argument checks, workspace layout, launch order.
 #include <cuda_runtime.h>
 
+#include <mutex>
 #include <vector>
 #include <stdint.h>
 #include <string.h>
@@ -113,14 +114,22 @@ bool sizes_ok(int64_t m, int64_t n, int64_t k) {
     return true;
 }
 
+// Kernel attributes (the opt-in to large dynamic shared memory) belong to each
+// device's context, so they are set once per device index.
+constexpr int kMaxDevices = 64;
+std::mutex g_conf_mu;
+bool g_conf_done[kMaxDevices] = {};
+
 int configure_once() {
-    static int done = 0;   // per process; attributes apply to every device the kernels run on
-    if (done) return 0;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return -1;
+    std::lock_guard<std::mutex> lk(g_conf_mu);
+    if (g_conf_done[dev]) return 0;
     if (cpqr_configure<double>() != cudaSuccess) return -1;
     if (cpqr_configure<float>() != cudaSuccess) return -1;
     if (solve_configure() != cudaSuccess) return -1;
     if (sketch_configure() != cudaSuccess) return -1;
-    done = 1;
+    g_conf_done[dev] = true;
     return 0;
 }
 

@@ -428,15 +428,25 @@ __global__ void k_cluster_stats(DevInfo* d) {
     d->info = r;
 }
 
+// Kernel attributes belong to each device's context: the flags are kept per
+// device index (and per dtype).
+constexpr int kCMaxDevices = 64;
 std::mutex g_cmu;
-bool g_cconf[2] = {false, false};
-bool g_c16[2] = {false, false};   // a 16-CTA cluster with the largest shared memory is schedulable
+bool g_cconf[kCMaxDevices][2] = {};
+bool g_c16[kCMaxDevices][2] = {};   // a 16-CTA cluster with the largest shared memory is schedulable
+
+int cluster_dev() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kCMaxDevices) return 0;
+    return dev;
+}
 
 template <typename T>
 cudaError_t cluster_configure() {
     std::lock_guard<std::mutex> lk(g_cmu);
     const int slot = sizeof(T) == 8 ? 0 : 1;
-    if (g_cconf[slot]) return cudaSuccess;
+    const int dev = cluster_dev();
+    if (g_cconf[dev][slot]) return cudaSuccess;
     cudaError_t e = cudaFuncSetAttribute(k_id_cluster<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCSmemMax);
     if (e != cudaSuccess) return e;
     if (cudaFuncSetAttribute(k_id_cluster<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
@@ -453,10 +463,10 @@ cudaError_t cluster_configure() {
         cfg.numAttrs = 1;
         int nclusters = 0;
         if (cudaOccupancyMaxActiveClusters(&nclusters, k_id_cluster<T>, &cfg) == cudaSuccess && nclusters > 0)
-            g_c16[slot] = true;
+            g_c16[dev][slot] = true;
         cudaGetLastError();   // a refused query leaves no error behind
     }
-    g_cconf[slot] = true;
+    g_cconf[dev][slot] = true;
     return cudaSuccess;
 }
 
@@ -469,7 +479,7 @@ int cluster_size(int64_t m, int64_t n, int64_t k) {
     if (k > kCMaxK || mx > kCMaxRows || nx > 8192) return 0;
     cluster_configure<T>();   // (on a machine without a GPU this fails and the portable cap holds)
     cudaGetLastError();
-    const int cap = g_c16[sizeof(T) == 8 ? 0 : 1] ? 16 : 8;
+    const int cap = g_c16[cluster_dev()][sizeof(T) == 8 ? 0 : 1] ? 16 : 8;
     // at least ceil(n_x / 64) CTAs (per-step work per CTA) and at least what
     // fits; FP64 takes the widest cluster (its arithmetic runs at 2 lanes per
     // clock per SM, so every SM counts)
