@@ -280,8 +280,9 @@ int id_decompose_sampled(const void* A, id_dtype dtype, int64_t m, int64_t n, in
  * problem is linear), which is the Z Sec. 2.2 asks for.
  * Arithmetic: C^T C in FP64 (products of FP32 values are exact in FP64) and
  * its Cholesky factor U in FP64; U^{-1} in FP64, applied in FP32; the
- * residual A - C Z and C^T times it as FP32-accurate GEMMs (cuBLAS, FP32
- * compute emulated on the BF16 tensor cores where that is faster).
+ * residual A - C Z and C^T times it as FP32-accurate 3xTF32 products on the
+ * tensor cores (the library's own tcgen05 kernel, see id_gemm), by column
+ * blocks of A whose residual stays in L2.
  *   A     [in]     m x n FP32 row-major, n <= lda < 2^31, m <= n (a column ID).
  *   J     [in]     k skeleton columns (distinct, in [0, n)).
  *   Z     [in,out] k x n FP32 row-major, n <= ldz < 2^31; Z[:, J] = I on entry.
@@ -426,14 +427,33 @@ int64_t id_launch_count(id_dtype dtype, int64_t m, int64_t n, int64_t k, const i
  *   Z    [in]  k x n (k x m when transposed) row-major, ldz >= that width, < 2^31.
  *   Out  [out] m x n row-major, n <= ldo < 2^31.
  *   work [in]  id_reconstruct_workspace_size() bytes, 256-byte aligned.
- * The skeleton is gathered, then one GEMM: FP64 data in FP64, FP32 data in
- * FP32-accurate products (cuBLAS, FP32 compute emulated on the BF16 tensor
- * cores). info (HOST or NULL): status ID_EINVAL if a J entry is out of range
+ * The skeleton is gathered, then one product (id_gemm's): FP64 data in
+ * FP64, FP32 data in FP32-accurate 3xTF32 products on the tensor cores. info (HOST or NULL): status ID_EINVAL if a J entry is out of range
  * (Out is then unspecified), else ID_OK. */
 size_t id_reconstruct_workspace_size(id_dtype dtype, int64_t m, int64_t n, int64_t k, int32_t transposed);
 int id_reconstruct(const void* A, id_dtype dtype, int64_t m, int64_t n, int64_t lda, int64_t k, const int32_t* J,
                    const void* Z, int64_t ldz, int32_t transposed, void* Out, int64_t ldo, void* work,
                    size_t work_bytes, id_info* info, void* stream);
+
+/* id_gemm -- C = alpha op(A) op(B) + beta C for row-major DEVICE matrices,
+ * op(X) = X (flag 0) or X^T (flag 1): the matrix product behind the
+ * refinement (the least-squares Z of Sec. 2.2), the gradient and
+ * id_reconstruct (Listing 1's approx = C @ Z), exposed for callers and tests.
+ *   ID_F64: FP64 arithmetic on the FP64 pipe.
+ *   ID_F32: FP32-accurate products on the tensor cores by the 3xTF32 split
+ *           (x = hi + lo, hi rounded to TF32; lo_a hi_b + hi_a lo_b +
+ *           hi_a hi_b accumulated in FP32 in tensor memory): an entry's
+ *           error is about 2^-21 of sum_k |a_ik| |b_kj| (FP32 itself: 2^-24
+ *           per operation).
+ *   M, N, K in [1, 2^31); lda, ldb, ldc at least the row widths they hold
+ *   (op(A) is M x K, op(B) K x N, C M x N). beta = 0: C is not read.
+ *   work [in] id_gemm_workspace_size() bytes, 256-byte aligned.
+ *   info (HOST or NULL): non-NULL waits and returns ID_ETIMEOUT if a bounded
+ *   device wait of the tensor-core kernel expired, else ID_OK. */
+size_t id_gemm_workspace_size(id_dtype dtype, int64_t M, int64_t N, int64_t K);
+int id_gemm(id_dtype dtype, int32_t ta, int32_t tb, int64_t M, int64_t N, int64_t K, double alpha, const void* A,
+            int64_t lda, const void* B, int64_t ldb, double beta, void* C, int64_t ldc, void* work, size_t work_bytes,
+            id_info* info, void* stream);
 
 /* id_decompose_csr -- rank-k ID (as id_decompose) of a sparse A given in CSR
  * form, for inputs such as the sparse matrices of the paper's experiments

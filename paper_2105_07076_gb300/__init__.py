@@ -121,6 +121,9 @@ _SIG = {
     "id_trace_enable": (ctypes.c_int, [ctypes.c_int]),
     "id_trace_read": (ctypes.c_int, [_P, _P, ctypes.c_int]),
     "id_version": (ctypes.c_char_p, []),
+    "id_gemm_workspace_size": (ctypes.c_size_t, [ctypes.c_int, _I64, _I64, _I64]),
+    "id_gemm": (ctypes.c_int, [ctypes.c_int, ctypes.c_int32, ctypes.c_int32, _I64, _I64, _I64, ctypes.c_double, _P, _I64,
+                               _P, _I64, ctypes.c_double, _P, _I64, _P, ctypes.c_size_t, _P, _P]),
 }
 
 TRACE_KINDS = ("cpqr", "solve", "sketch", "copy_in", "scatter", "batched", "refine", "sampled_z")
@@ -462,6 +465,37 @@ def id_reconstruct(A: torch.Tensor, J: torch.Tensor, Z: torch.Tensor, *, transpo
     if rc in _CALL_ERRORS or (sync and info.status == ID_EINVAL):
         raise IdError(ID_EINVAL if rc == 0 else rc, "id_reconstruct")
     return Out, (info.as_dict() if sync else None)
+
+
+def gemm(A: torch.Tensor, B: torch.Tensor, *, ta: bool = False, tb: bool = False, alpha: float = 1.0,
+         beta: float = 0.0, out: torch.Tensor | None = None, sync: bool = True):
+    """out = alpha op(A) op(B) + beta out for row-major CUDA matrices of one dtype, op(X) = X or X.T:
+    FP64 on the FP64 pipe, FP32 as FP32-accurate 3xTF32 products on the tensor cores. Returns (out, info)."""
+    _check_cuda_matrix(A, "A")
+    _check_cuda_matrix(B, "B")
+    if A.dtype != B.dtype:
+        raise ValueError("A and B must have one dtype")
+    M, K = (A.shape[1], A.shape[0]) if ta else (A.shape[0], A.shape[1])
+    K2, N = (B.shape[1], B.shape[0]) if tb else (B.shape[0], B.shape[1])
+    if K != K2:
+        raise ValueError("inner dimensions differ")
+    dev = A.device
+    dt = _DTYPES[A.dtype]
+    if out is None:
+        out = torch.zeros(M, N, dtype=A.dtype, device=dev)
+    _check_cuda_matrix(out, "out")
+    nbytes = int(lib().id_gemm_workspace_size(dt, M, N, K))
+    if nbytes == 0:
+        raise IdError(ID_EINVAL, "id_gemm_workspace_size")
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    info = IdInfo()
+    with torch.cuda.device(dev):
+        rc = lib().id_gemm(dt, 1 if ta else 0, 1 if tb else 0, M, N, K, float(alpha), A.data_ptr(), A.stride(0),
+                           B.data_ptr(), B.stride(0), float(beta), out.data_ptr(), out.stride(0), ws.data_ptr(),
+                           ws.numel(), ctypes.byref(info) if sync else None, _stream(dev))
+    if rc in _CALL_ERRORS:
+        raise IdError(rc, "id_gemm")
+    return out, (info.as_dict() if sync else None)
 
 
 def id_refine(A: torch.Tensor, J: torch.Tensor, Z: torch.Tensor, *, workspace: Workspace | None = None,

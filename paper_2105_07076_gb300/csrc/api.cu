@@ -8,6 +8,7 @@
 
 #include "common.cuh"
 #include "cpqr.cuh"
+#include "gemm.cuh"
 #include "gbid.h"
 #include "trace.cuh"
 
@@ -129,6 +130,7 @@ int configure_once() {
     if (cpqr_configure<float>() != cudaSuccess) return -1;
     if (solve_configure() != cudaSuccess) return -1;
     if (sketch_configure() != cudaSuccess) return -1;
+    if (gemm_configure() != cudaSuccess) return -1;
     g_conf_done[dev] = true;
     return 0;
 }
@@ -583,7 +585,7 @@ int id_info_read(const void* work, id_info* info, void* stream) {
 
 int64_t id_launch_count(id_dtype dtype, int64_t m, int64_t n, int64_t k, const id_opts* opts) {
     if ((dtype != ID_F64 && dtype != ID_F32) || !sizes_ok(m, n, k) || !engine_ok(dtype, m, n, k, opts)) return -1;
-    if (zsolve_of(opts) == 1) return -1;   // not counted: the launches depend on k and include cuBLAS
+    if (zsolve_of(opts) == 1) return -1;   // not counted: the launches of the blocked inverse depend on k
     const bool cl = dtype == ID_F64 ? use_cluster<double>(m, n, k, opts) : use_cluster<float>(m, n, k, opts);
     if (cl) return 2;   // the cluster kernel and its statistics kernel
     const int64_t nx = m > n ? m : n;
@@ -615,6 +617,45 @@ int id_reconstruct(const void* A, id_dtype dtype, int64_t m, int64_t n, int64_t 
                        ? reconstruct_run<double>(A, m, n, lda, (int)k, J, Z, ldz, transposed, Out, ldo, rws, dinfo, s)
                        : reconstruct_run<float>(A, m, n, lda, (int)k, J, Z, ldz, transposed, Out, ldo, rws, dinfo, s);
     if (rc != ID_OK) return rc;
+    if (info) return read_info(work, info, s);
+    return ID_OK;
+}
+
+size_t id_gemm_workspace_size(id_dtype dtype, int64_t M, int64_t N, int64_t K) {
+    if (dtype != ID_F64 && dtype != ID_F32) return 0;
+    if (M < 1 || N < 1 || K < 1 || M > INT32_MAX || N > INT32_MAX || K > INT32_MAX - 16) return 0;
+    const size_t head = align_up(sizeof(DevInfo)) + kAlign;
+    return head + (dtype == ID_F32 ? gemm_f32_bytes((int)M, (int)N, (int)K) : 0);
+}
+
+int id_gemm(id_dtype dtype, int32_t ta, int32_t tb, int64_t M, int64_t N, int64_t K, double alpha, const void* A,
+            int64_t lda, const void* B, int64_t ldb, double beta, void* C, int64_t ldc, void* work, size_t work_bytes,
+            id_info* info, void* stream) {
+    if (!A || !B || !C || !work || (ta != 0 && ta != 1) || (tb != 0 && tb != 1)) return ID_EINVAL;
+    const size_t need = id_gemm_workspace_size(dtype, M, N, K);
+    if (need == 0) return ID_EINVAL;
+    // row widths: op(A) M x K is stored M x K (ta = 0) or K x M; likewise B, C
+    if (lda < (ta ? M : K) || ldb < (tb ? K : N) || ldc < N) return ID_EINVAL;
+    if (!aligned(work, 256)) return ID_EINVAL;
+    if (work_bytes < need) return ID_ENOMEM;
+    if (configure_once()) return ID_ECUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    char* base = static_cast<char*>(work);
+    DevInfo* dinfo = reinterpret_cast<DevInfo*>(base);
+    int* status = reinterpret_cast<int*>(base + align_up(sizeof(DevInfo)));
+    if (cudaMemsetAsync(base, 0, align_up(sizeof(DevInfo)) + kAlign, s) != cudaSuccess) return ID_ECUDA;
+    int rc = ID_OK;
+    if (dtype == ID_F64) {
+        if (dgemm(ta, tb, (int)M, (int)N, (int)K, alpha, static_cast<const double*>(A), lda,
+                  static_cast<const double*>(B), ldb, beta, static_cast<double*>(C), ldc, s) != cudaSuccess)
+            return ID_ECUDA;
+    } else {
+        rc = gemm_f32(ta, tb, (int)M, (int)N, (int)K, (float)alpha, static_cast<const float*>(A), lda,
+                      static_cast<const float*>(B), ldb, (float)beta, static_cast<float*>(C), ldc,
+                      base + align_up(sizeof(DevInfo)) + kAlign, status, s);
+        if (rc != ID_OK) return rc;
+    }
+    if (gemm_status_to_info(status, dinfo, s) != cudaSuccess) return ID_ECUDA;
     if (info) return read_info(work, info, s);
     return ID_OK;
 }

@@ -11,46 +11,65 @@
 //      tiled rank-32 update of the trailing upper triangle). A non-positive
 //      pivot (rank(C) < k) sets a flag and Z is left unchanged.
 //   4. U^{-1} in FP64 by a blocked inverse (32 x 32 diagonal blocks by back
-//      substitution, merged with FP64 GEMMs), rounded to FP32.
-//   5. Over column blocks of 4096: R_b = A_b - C Z_b, H_b = C^T R_b as
-//      FP32-accurate GEMMs (cuBLAS, FP32 compute emulated on the BF16 tensor
-//      cores where that is faster). Columns of J give R_b = 0 exactly
-//      (Z[:, J] = I), so they receive no update.
-//   6. D = U^{-1} (U^{-T} H) (FP32 GEMMs; the correction needs relative
-//      accuracy cond(U) u_32 only), Z += D, Z[:, J] = I restored, Z
-//      statistics recomputed.
-// cuBLAS runs only the plain GEMMs of step 5 and 6; it gets its workspace
-// from the caller's, so nothing is allocated per call (one handle per device
-// is created on first use).
-#include <cublasLt.h>
-#include <cublas_v2.h>
+//      substitution, merged with FP64 products).
+//   5. Over column blocks of A small enough that the block's residual stays in
+//      L2: R_b^T = A_b^T - Z_b^T C^T and H_b^T = R_b^T C, FP32-accurate
+//      3xTF32 products on the tensor cores (gemm.cu). The first writes R_b^T
+//      already split into the operand form of the second; the second runs
+//      split-K over the m rows, its slices summed in FP64 by k_reduce_split.
+//      Columns of J give R_b = 0 exactly (Z[:, J] = I), so they receive no
+//      update.
+//   6. Y^T = H^T U^{-1}, then Z += (Y^T U^{-T})^T in the last product's
+//      epilogue (the correction needs relative accuracy cond(U) u_32 only),
+//      Z[:, J] = I restored, Z statistics recomputed.
+// Every product runs in the library's own kernels; nothing is allocated.
 #include <cuda_runtime.h>
 #include <float.h>
 #include <math.h>
 
-#include <map>
-#include <mutex>
-
 #include "common.cuh"
 #include "cpqr.cuh"
 #include "gbid.h"
+#include "gemm.cuh"
 #include "trace.cuh"
-#include "blas.cuh"
 
 namespace gbid {
 namespace {
 
 constexpr int kRThreads = 256;
 constexpr int kCholB = 32;
-constexpr int64_t kResCols = 4096;
-constexpr size_t kCublasWs = 32u << 20;
+constexpr int kTargetCtas = 152;   // split-K slices are sized to about one wave of CTAs
+constexpr int kGramSplit = 16;     // row chunks of the Gram matrix
 
 size_t al(size_t x) { return (x + 255) / 256 * 256; }
 
-constexpr int kGramSplit = 16;   // row chunks of the Gram matrix
+
+// Column block of the refinement's residual: R_b^T (nb x mp, hi and lo) is
+// kept near 64 MB so that it stays in L2 between its two products.
+int ref_block(int64_t m, int64_t n) {
+    const int64_t mp = kpad16(m);
+    int64_t nb = (64ll << 20) / (8 * mp) / 128 * 128;
+    if (nb < 128) nb = 128;
+    if (nb > 8192) nb = 8192;
+    const int64_t n128 = (n + 127) / 128 * 128;
+    return (int)(nb < n128 ? nb : n128);
+}
+
+// Split-K slices of H_b^T = R_b^T C (nb x k output tiles, K = mp).
+int ref_splits(int nb, int k, int64_t mp) {
+    const int tiles = ((nb + 127) / 128) * ((k + gemm_bn(k) - 1) / gemm_bn(k));
+    int sp = kTargetCtas / tiles;
+    const int kb = (int)(mp / 16);
+    if (sp < 1) sp = 1;
+    if (sp > kb) sp = kb;
+    const int per = (kb + sp - 1) / sp;
+    return (kb + per - 1) / per;
+}
 
 struct RefLayout {
-    size_t flag, C32, Wa, Gp, gdiag, Uinv64, Uinv32, Rb, H, Y1, cws, total;
+    size_t flag, C32, Wa, Gp, gdiag, Uinv64, Ch, Cl, Cth, Ctl, Uth, Utl, Uh, Ul, Zth, Ztl, Rth, Rtl, Part, Hth, Htl,
+        Yth, Ytl, total;
+    int nb, splits;
 };
 
 RefLayout ref_layout(int64_t m, int64_t n, int64_t k) {
@@ -61,17 +80,32 @@ RefLayout ref_layout(int64_t m, int64_t n, int64_t k) {
         off = al(off + b);
         return o;
     };
+    const size_t kp = (size_t)kpad16(k), mp = (size_t)kpad16(m);
+    L.nb = ref_block(m, n);
+    L.splits = ref_splits(L.nb, (int)k, (int64_t)mp);
     L.flag = take(16);
     L.C32 = take(4 * (size_t)m * k);
     L.Wa = take(8 * (size_t)k * 2 * k);
     L.Gp = take(8 * (size_t)kGramSplit * k * k);
     L.gdiag = take(8 * (size_t)k);
     L.Uinv64 = take(8 * (size_t)k * k);
-    L.Uinv32 = take(4 * (size_t)k * k);
-    L.Rb = take(4 * (size_t)m * (size_t)(n < kResCols ? n : kResCols));
-    L.H = take(4 * (size_t)k * n);
-    L.Y1 = take(4 * (size_t)k * n);
-    L.cws = take(kCublasWs);
+    L.Ch = take(4 * (size_t)m * kp);
+    L.Cl = take(4 * (size_t)m * kp);
+    L.Cth = take(4 * (size_t)k * mp);
+    L.Ctl = take(4 * (size_t)k * mp);
+    L.Uth = take(4 * (size_t)k * kp);
+    L.Utl = take(4 * (size_t)k * kp);
+    L.Uh = take(4 * (size_t)k * kp);
+    L.Ul = take(4 * (size_t)k * kp);
+    L.Zth = take(4 * (size_t)L.nb * kp);
+    L.Ztl = take(4 * (size_t)L.nb * kp);
+    L.Rth = take(4 * (size_t)L.nb * mp);
+    L.Rtl = take(4 * (size_t)L.nb * mp);
+    L.Part = take(4 * (size_t)L.splits * L.nb * k);
+    L.Hth = take(4 * (size_t)n * kp);
+    L.Htl = take(4 * (size_t)n * kp);
+    L.Yth = take(4 * (size_t)n * kp);
+    L.Ytl = take(4 * (size_t)n * kp);
     L.total = off;
     return L;
 }
@@ -330,15 +364,6 @@ __global__ void k_to_f32(const double* __restrict__ x, float* __restrict__ y, in
         y[e] = (float)x[e];
 }
 
-// Z += D (k x n, D row-major with leading dimension n) when the factorisation
-// succeeded; then Z[:, J] = I again and the Z statistics of the result.
-__global__ void k_apply(float* Z, int64_t ldz, const float* __restrict__ D, int k, int n, const int* flag) {
-    if (flag[0]) return;
-    const int i = blockIdx.y;
-    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < n; l += gridDim.x * blockDim.x)
-        Z[(int64_t)i * ldz + l] += D[(int64_t)i * n + l];
-}
-
 __global__ void k_restore_identity(float* Z, int64_t ldz, const int32_t* J, int k, const int* flag) {
     if (flag[0]) return;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < k * k; e += gridDim.x * blockDim.x) {
@@ -374,10 +399,16 @@ __global__ void k_reset_stats(DevInfo* info, const int* flag) {
     info->max_abs_z_bits = 0;
 }
 
+// flag[0]: 1 = C^T C not positive definite, 2 = a J entry outside [0, n);
+// flag[1]: kStat* bits of the products (kStatTimeout: a bounded wait expired).
 __global__ void k_ref_finalize(DevInfo* info, const int* flag) {
     id_info r = info->info;
     r.refined = flag[0] ? 0 : 1;
     if (flag[0] == 2) r.status = ID_EINVAL;
+    if (flag[1] & kStatTimeout) {
+        r.status = ID_ETIMEOUT;
+        r.refined = 0;
+    }
     if (!flag[0]) {
         r.n_gt2 = (int64_t)info->n_gt2;
         r.max_abs_z = __longlong_as_double((long long)info->max_abs_z_bits);
@@ -428,6 +459,7 @@ __global__ void k_bwd_finalize(DevInfo* info, const int* flag) {
     id_info r = info->info;
     if (flag[0] == 2) r.status = ID_EINVAL;
     else if (flag[0] == 1) r.status = ID_RANK_DEFICIENT;
+    if (flag[1] & kStatTimeout) r.status = ID_ETIMEOUT;
     info->info = r;
 }
 
@@ -555,26 +587,25 @@ __global__ void k_cm_to_rm(const double* __restrict__ in, int k, double* __restr
 
 // U: upper triangle of a column-major k x k array (ld k; below the diagonal
 // unused). Uinv_cm (k x k, column-major) and tmp ((k/2 + kTriLeaf)^2 doubles)
-// are scratch; Uinv_rm receives U^{-1} row-major. The caller holds the cuBLAS
-// handle's lock with its stream set.
-cudaError_t tri_inverse(const double* U, int k, double* Uinv_cm, double* tmp, double* Uinv_rm, cublasHandle_t h,
-                        cudaStream_t s) {
+// are scratch; Uinv_rm receives U^{-1} row-major. The merges run the
+// row-major FP64 product on the transposes (a column-major block read
+// row-major is the block's transpose).
+cudaError_t tri_inverse(const double* U, int k, double* Uinv_cm, double* tmp, double* Uinv_rm, cudaStream_t s) {
     if (cudaMemsetAsync(Uinv_cm, 0, sizeof(double) * (size_t)k * k, s) != cudaSuccess) return cudaErrorUnknown;
     const int nleaf = ceil_div(k, kTriLeaf);
     k_tri_inv_leaf<<<nleaf, kTriLeaf, 0, s>>>(U, k, Uinv_cm);
     // merge blocks of width w into blocks of width 2w, bottom-up
-    const double one = 1.0, zero = 0.0, mone = -1.0;
     for (int w = kTriLeaf; w < k; w *= 2) {
         for (int o1 = 0; o1 + w < k; o1 += 2 * w) {
             const int b1 = w, o2 = o1 + w, b2 = min(w, k - o2);
-            // tmp (b1 x b2, ld b1) = A^{-1} B
-            if (cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, b1, b2, b1, &one, Uinv_cm + o1 + (int64_t)o1 * k, k,
-                            U + o1 + (int64_t)o2 * k, k, &zero, tmp, b1) != CUBLAS_STATUS_SUCCESS)
-                return cudaErrorUnknown;
-            // U^{-1}(o1, o2) = -tmp C^{-1}
-            if (cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, b1, b2, b2, &mone, tmp, b1, Uinv_cm + o2 + (int64_t)o2 * k,
-                            k, &zero, Uinv_cm + o1 + (int64_t)o2 * k, k) != CUBLAS_STATUS_SUCCESS)
-                return cudaErrorUnknown;
+            // tmp (b1 x b2, column-major ld b1) = A^{-1} B, formed as tmp^T = B^T A^{-T}
+            cudaError_t e = dgemm(0, 0, b2, b1, b1, 1.0, U + o1 + (int64_t)o2 * k, k, Uinv_cm + o1 + (int64_t)o1 * k,
+                                  k, 0.0, tmp, b1, s);
+            if (e != cudaSuccess) return e;
+            // U^{-1}(o1, o2) = -tmp C^{-1}, formed as its transpose -C^{-T} tmp^T
+            e = dgemm(0, 0, b2, b1, b2, -1.0, Uinv_cm + o2 + (int64_t)o2 * k, k, tmp, b1, 0.0,
+                      Uinv_cm + o1 + (int64_t)o2 * k, k, s);
+            if (e != cudaSuccess) return e;
         }
     }
     k_cm_to_rm<<<grid_for((int64_t)k * k), kRThreads, 0, s>>>(Uinv_cm, k, Uinv_rm);
@@ -586,8 +617,7 @@ cudaError_t tri_inverse(const double* U, int k, double* Uinv_cm, double* tmp, do
 // definite), U^{-1} in FP64 (row-major k x k) by the blocked inverse (Gp and
 // Wa's second half are its scratch).
 cudaError_t factor_skeleton(const float* A, int64_t m, int64_t n, int64_t lda, int k, const int32_t* J, float* C32,
-                            double* Gp, double* Wa, double* Uinv64, double* gdiag, int* flag, cublasHandle_t h,
-                            cudaStream_t s) {
+                            double* Gp, double* Wa, double* Uinv64, double* gdiag, int* flag, cudaStream_t s) {
     k_check_j<<<1, kRThreads, 0, s>>>(J, k, n, flag);
     k_gather<<<grid_for(m * k), kRThreads, 0, s>>>(A, lda, (int)m, k, n, J, C32);
     const int nt = ceil_div(k, kGT);
@@ -606,86 +636,29 @@ cudaError_t factor_skeleton(const float* A, int64_t m, int64_t n, int64_t lda, i
     }
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    return tri_inverse(Wa, k, Wa + (size_t)k * k, Gp, Uinv64, h, s);
+    return tri_inverse(Wa, k, Wa + (size_t)k * k, Gp, Uinv64, s);
+}
+
+// H^T rows of one column block from the split-K slices of R_b^T C:
+// H(l, q) = sum_z P[z][l][q], summed in FP64, rounded to FP32 and split into
+// the operand form (columns k..kp-1 zero).
+__global__ void k_reduce_split(const float* __restrict__ P, int splits, int nb, int k, int kp, float* __restrict__ hi,
+                               float* __restrict__ lo) {
+    const int64_t total = (int64_t)nb * kp;
+    const int64_t slice = (int64_t)nb * k;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int l = (int)(e / kp), q = (int)(e % kp);
+        double acc = 0.0;
+        if (q < k)
+            for (int z = 0; z < splits; ++z) acc += (double)P[z * slice + (int64_t)l * k + q];
+        const float x = (float)acc;
+        const float h = tf32_hi(x);
+        hi[e] = h;
+        lo[e] = x - h;
+    }
 }
 
 }  // namespace
-
-std::mutex g_cb_mu;
-std::map<int, cublasHandle_t> g_cb;
-
-cublasHandle_t cublas_handle() {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
-    std::lock_guard<std::mutex> lk(g_cb_mu);
-    auto it = g_cb.find(dev);
-    if (it != g_cb.end()) return it->second;
-    cublasHandle_t h = nullptr;
-    if (cublasCreate(&h) != CUBLAS_STATUS_SUCCESS) return nullptr;
-    g_cb[dev] = h;
-    return h;
-}
-
-std::map<int, cublasLtHandle_t> g_lt;
-std::mutex g_lt_mu;   // its own lock: callers may already hold g_cb_mu
-
-cublasLtHandle_t lt_handle() {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
-    std::lock_guard<std::mutex> lk(g_lt_mu);
-    auto it = g_lt.find(dev);
-    if (it != g_lt.end()) return it->second;
-    cublasLtHandle_t h = nullptr;
-    if (cublasLtCreate(&h) != CUBLAS_STATUS_SUCCESS) return nullptr;
-    g_lt[dev] = h;
-    return h;
-}
-
-// D = alpha op(A) op(B) + beta C, C and D may be separate (column-major;
-// op(A) M x K, op(B) K x N, C and D M x N), FP32 compute emulated on the BF16
-// tensor cores, through cuBLASLt with an explicit workspace. False when
-// cuBLASLt does not take it; the caller then falls back.
-bool sgemm_lt(cublasLtHandle_t lt, cublasOperation_t ta, cublasOperation_t tb, int M, int N, int K, float alpha,
-              const float* A, int lda, const float* B, int ldb, float beta, const float* C, int ldc, float* D, int ldd,
-              void* ws, size_t ws_bytes, cudaStream_t s) {
-    if (!lt) return false;
-    cublasLtMatmulDesc_t op = nullptr;
-    cublasLtMatrixLayout_t la = nullptr, lb = nullptr, lc = nullptr, ld = nullptr;
-    cublasLtMatmulPreference_t pref = nullptr;
-    const cublasStatus_t S = CUBLAS_STATUS_SUCCESS;
-    const bool tA = ta == CUBLAS_OP_T, tB = tb == CUBLAS_OP_T;
-    bool ok = cublasLtMatmulDescCreate(&op, CUBLAS_COMPUTE_32F_EMULATED_16BFX9, CUDA_R_32F) == S &&
-              cublasLtMatmulDescSetAttribute(op, CUBLASLT_MATMUL_DESC_TRANSA, &ta, sizeof(ta)) == S &&
-              cublasLtMatmulDescSetAttribute(op, CUBLASLT_MATMUL_DESC_TRANSB, &tb, sizeof(tb)) == S &&
-              cublasLtMatrixLayoutCreate(&la, CUDA_R_32F, tA ? K : M, tA ? M : K, lda) == S &&
-              cublasLtMatrixLayoutCreate(&lb, CUDA_R_32F, tB ? N : K, tB ? K : N, ldb) == S &&
-              cublasLtMatrixLayoutCreate(&lc, CUDA_R_32F, M, N, ldc) == S &&
-              cublasLtMatrixLayoutCreate(&ld, CUDA_R_32F, M, N, ldd) == S && cublasLtMatmulPreferenceCreate(&pref) == S &&
-              cublasLtMatmulPreferenceSetAttribute(pref, CUBLASLT_MATMUL_PREF_MAX_WORKSPACE_BYTES, &ws_bytes,
-                                                   sizeof(ws_bytes)) == S;
-    cublasLtMatmulHeuristicResult_t res;
-    int nres = 0;
-    ok = ok && cublasLtMatmulAlgoGetHeuristic(lt, op, la, lb, lc, ld, pref, 1, &res, &nres) == S && nres > 0;
-    ok = ok && cublasLtMatmul(lt, op, &alpha, A, la, B, lb, &beta, C, lc, D, ld, &res.algo, ws, ws_bytes, s) == S;
-    if (pref) cublasLtMatmulPreferenceDestroy(pref);
-    if (ld) cublasLtMatrixLayoutDestroy(ld);
-    if (lc) cublasLtMatrixLayoutDestroy(lc);
-    if (lb) cublasLtMatrixLayoutDestroy(lb);
-    if (la) cublasLtMatrixLayoutDestroy(la);
-    if (op) cublasLtMatmulDescDestroy(op);
-    return ok;
-}
-
-// FP32-accurate GEMM (column-major arguments as cuBLAS takes them).
-bool sgemm(cublasHandle_t h, cublasOperation_t ta, cublasOperation_t tb, int M, int N, int K, float alpha,
-           const float* A, int lda, const float* B, int ldb, float beta, float* C, int ldc) {
-    cublasStatus_t st = cublasGemmEx(h, ta, tb, M, N, K, &alpha, A, CUDA_R_32F, lda, B, CUDA_R_32F, ldb, &beta, C,
-                                     CUDA_R_32F, ldc, CUBLAS_COMPUTE_32F_EMULATED_16BFX9, CUBLAS_GEMM_DEFAULT);
-    if (st == CUBLAS_STATUS_SUCCESS) return true;
-    st = cublasGemmEx(h, ta, tb, M, N, K, &alpha, A, CUDA_R_32F, lda, B, CUDA_R_32F, ldb, &beta, C, CUDA_R_32F, ldc,
-                      CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT);
-    return st == CUBLAS_STATUS_SUCCESS;
-}
 
 size_t refine_bytes(int64_t m, int64_t n, int64_t k) { return ref_layout(m, n, k).total; }
 
@@ -698,53 +671,75 @@ int refine_run(const float* A, int64_t m, int64_t n, int64_t lda, int k, const i
                void* ws, DevInfo* dinfo, cudaStream_t s) {
     const RefLayout L = ref_layout(m, n, k);
     char* base = static_cast<char*>(ws);
+    auto fp = [&](size_t o) { return reinterpret_cast<float*>(base + o); };
     int* flag = reinterpret_cast<int*>(base + L.flag);
-    float* C32 = reinterpret_cast<float*>(base + L.C32);
+    int* gst = flag + 1;   // status bits of the products
+    float* C32 = fp(L.C32);
     double* Gp = reinterpret_cast<double*>(base + L.Gp);
     double* Wa = reinterpret_cast<double*>(base + L.Wa);
     double* Uinv64 = reinterpret_cast<double*>(base + L.Uinv64);
-    float* Uinv32 = reinterpret_cast<float*>(base + L.Uinv32);
-    float* Rb = reinterpret_cast<float*>(base + L.Rb);
-    float* H = reinterpret_cast<float*>(base + L.H);
-    float* Y1 = reinterpret_cast<float*>(base + L.Y1);
-    cublasHandle_t h = cublas_handle();
-    if (!h) return ID_ECUDA;
-    std::lock_guard<std::mutex> lk(g_cb_mu);   // one stream/workspace binding of the handle at a time
-    if (cublasSetStream(h, s) != CUBLAS_STATUS_SUCCESS) return ID_ECUDA;
-    if (cublasSetWorkspace(h, base + L.cws, kCublasWs) != CUBLAS_STATUS_SUCCESS) return ID_ECUDA;
+    const int kp = (int)kpad16(k), mp = (int)kpad16(m);
     if (cudaMemsetAsync(flag, 0, 16, s) != cudaSuccess) return ID_ECUDA;
     const int tr = trace_begin(TraceKind::kRefine, s);
-    if (factor_skeleton(A, m, n, lda, k, J, C32, Gp, Wa, Uinv64, reinterpret_cast<double*>(base + L.gdiag), flag, h,
-                        s) != cudaSuccess)
+    if (factor_skeleton(A, m, n, lda, k, J, C32, Gp, Wa, Uinv64, reinterpret_cast<double*>(base + L.gdiag), flag, s) !=
+        cudaSuccess)
         return ID_ECUDA;
-    k_to_f32<<<grid_for((int64_t)k * k), kRThreads, 0, s>>>(Uinv64, Uinv32, (int64_t)k * k);
-    // 5. H = C^T (A - C Z), by column blocks. Column-major views: A row-major
-    //    m x n is A^T (n x m, ld lda); Z is Z^T (n x k, ld ldz); C is C^T (k x m, ld k).
-    cublasLtHandle_t lt = lt_handle();
-    for (int64_t b0 = 0; b0 < n; b0 += kResCols) {
-        const int nb = (int)(n - b0 < kResCols ? n - b0 : kResCols);
-        // R_b^T (nb x m) = A_b^T - Z_b^T (nb x k) C^T (k x m): straight from A when cuBLASLt takes the
-        // separate input C, else a copy of A_b and an in-place GEMM
-        if (!sgemm_lt(lt, CUBLAS_OP_N, CUBLAS_OP_N, nb, (int)m, k, -1.0f, Z + b0, (int)ldz, C32, k, 1.0f, A + b0, (int)lda, Rb, nb,
-                      base + L.cws, kCublasWs, s)) {
-            if (cudaMemcpy2DAsync(Rb, (size_t)nb * 4, A + b0, (size_t)lda * 4, (size_t)nb * 4, (size_t)m,
-                                  cudaMemcpyDeviceToDevice, s) != cudaSuccess)
-                return ID_ECUDA;
-            if (!sgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, nb, (int)m, k, -1.0f, Z + b0, (int)ldz, C32, k, 1.0f, Rb, nb))
-                return ID_ECUDA;
-        }
-        // H_b^T (nb x k) = R_b^T (nb x m) C (m x k)
-        if (!sgemm(h, CUBLAS_OP_N, CUBLAS_OP_T, nb, k, (int)m, 1.0f, Rb, nb, C32, k, 0.0f, H + b0, (int)n))
-            return ID_ECUDA;
+    // operands: C (m x kp), C^T (k x mp), (U^{-1})^T and U^{-1} (k x kp)
+    if (split_tf32<float>(C32, k, 0, (int)m, k, kp, fp(L.Ch), fp(L.Cl), kp, s) != cudaSuccess) return ID_ECUDA;
+    if (split_tf32<float>(C32, k, 1, k, (int)m, mp, fp(L.Cth), fp(L.Ctl), mp, s) != cudaSuccess) return ID_ECUDA;
+    if (split_tf32<double>(Uinv64, k, 1, k, k, kp, fp(L.Uth), fp(L.Utl), kp, s) != cudaSuccess) return ID_ECUDA;
+    if (split_tf32<double>(Uinv64, k, 0, k, k, kp, fp(L.Uh), fp(L.Ul), kp, s) != cudaSuccess) return ID_ECUDA;
+    const TfOperand opC{fp(L.Ch), fp(L.Cl), kp, (int)m};
+    const TfOperand opCt{fp(L.Cth), fp(L.Ctl), mp, k};
+    // 5. H^T = (A - C Z)^T C by column blocks of A
+    for (int64_t b0 = 0; b0 < n; b0 += L.nb) {
+        const int nbb = (int)(n - b0 < L.nb ? n - b0 : L.nb);
+        if (split_tf32<float>(Z + b0, ldz, 1, nbb, k, kp, fp(L.Zth), fp(L.Ztl), kp, s) != cudaSuccess) return ID_ECUDA;
+        // R_b^T (nbb x mp) = A_b^T - Z_b^T C^T, written in operand form; columns m..mp-1 are zero
+        TfEpilogue e1;
+        e1.alpha = -1.0f;
+        e1.beta = 1.0f;
+        e1.cin = A + b0;
+        e1.ldc = lda;
+        e1.cin_trans = 1;
+        e1.cin_cols = (int)m;
+        e1.d = fp(L.Rth);
+        e1.d_lo = fp(L.Rtl);
+        e1.ldd = mp;
+        int rc = gemm_tf32x3(TfOperand{fp(L.Zth), fp(L.Ztl), kp, nbb}, opC, nbb, mp, kp, 1, e1, gst, s);
+        if (rc != ID_OK) return rc;
+        // split-K slices of H_b^T = R_b^T C (nbb x k), then their FP64 sum in operand form
+        TfEpilogue e2;
+        e2.d = fp(L.Part);
+        e2.ldd = k;
+        e2.z_stride = (int64_t)nbb * k;
+        rc = gemm_tf32x3(TfOperand{fp(L.Rth), fp(L.Rtl), mp, nbb}, opCt, nbb, k, mp, L.splits, e2, gst, s);
+        if (rc != ID_OK) return rc;
+        k_reduce_split<<<grid_for((int64_t)nbb * kp), kRThreads, 0, s>>>(fp(L.Part), L.splits, nbb, k, kp,
+                                                                          fp(L.Hth) + b0 * kp, fp(L.Htl) + b0 * kp);
     }
-    // 6. Y1 = U^{-T} H, D = U^{-1} Y1 (into H). Uinv32 row-major k x k is the
-    //    column-major (U^{-1})^T.  Y1^T (n x k) = H^T U^{-1};  D^T = Y1^T U^{-T}.
-    if (!sgemm(h, CUBLAS_OP_N, CUBLAS_OP_T, (int)n, k, k, 1.0f, H, (int)n, Uinv32, k, 0.0f, Y1, (int)n))
-        return ID_ECUDA;
-    if (!sgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, (int)n, k, k, 1.0f, Y1, (int)n, Uinv32, k, 0.0f, H, (int)n))
-        return ID_ECUDA;
+    // 6. Y^T = H^T U^{-1} (B(q, p) = U^{-1}(p, q)); Z += (Y^T U^{-T})^T in the epilogue (B(q, p) = U^{-1}(q, p))
+    TfEpilogue e3;
+    e3.d = fp(L.Yth);
+    e3.d_lo = fp(L.Ytl);
+    e3.ldd = kp;
+    int rc = gemm_tf32x3(TfOperand{fp(L.Hth), fp(L.Htl), kp, (int)n}, TfOperand{fp(L.Uth), fp(L.Utl), kp, k}, (int)n,
+                         kp, kp, 1, e3, gst, s);
+    if (rc != ID_OK) return rc;
+    TfEpilogue e4;
+    e4.alpha = 1.0f;
+    e4.beta = 1.0f;
+    e4.cin = Z;
+    e4.ldc = ldz;
+    e4.cin_trans = 1;
+    e4.d = Z;
+    e4.ldd = ldz;
+    e4.d_trans = 1;
+    e4.skip = flag;   // no update when C^T C is singular or J is invalid
+    rc = gemm_tf32x3(TfOperand{fp(L.Yth), fp(L.Ytl), kp, (int)n}, TfOperand{fp(L.Uh), fp(L.Ul), kp, k}, (int)n, k,
+                     kp, 1, e4, gst, s);
+    if (rc != ID_OK) return rc;
     dim3 g2(ceil_div(n, kRThreads) < 1024 ? ceil_div(n, kRThreads) : 1024, k);
-    k_apply<<<g2, kRThreads, 0, s>>>(Z, ldz, H, k, (int)n, flag);
     k_restore_identity<<<grid_for((int64_t)k * k), kRThreads, 0, s>>>(Z, ldz, J, k, flag);
     k_reset_stats<<<1, 1, 0, s>>>(dinfo, flag);
     k_zstats<<<g2, kRThreads, 0, s>>>(Z, ldz, k, (int)n, flag, dinfo);
@@ -754,7 +749,7 @@ int refine_run(const float* A, int64_t m, int64_t n, int64_t lda, int k, const i
 }
 
 struct BwdLayout {
-    size_t flag, mask, C32, Gp, gdiag, Wa, Uinv64, G64, Y64, W32, Rb, dC, M1, cws, total;
+    size_t flag, mask, C32, Gp, gdiag, Wa, Uinv64, G64, Y64, W32, R, dC, M1, gws, total;
 };
 
 static BwdLayout bwd_layout(int64_t m, int64_t n, int64_t k) {
@@ -775,10 +770,15 @@ static BwdLayout bwd_layout(int64_t m, int64_t n, int64_t k) {
     L.G64 = take(8 * (size_t)k * n);
     L.Y64 = take(8 * (size_t)k * n);
     L.W32 = take(4 * (size_t)k * n);
-    L.Rb = take(4 * (size_t)m * (size_t)(n < kResCols ? n : kResCols));
+    L.R = take(4 * (size_t)m * n);
     L.dC = take(4 * (size_t)m * k);
     L.M1 = take(4 * (size_t)k * k);
-    L.cws = take(kCublasWs);
+    // operand scratch of the largest of the five FP32 products
+    size_t g = gemm_f32_bytes((int)m, (int)n, (int)k);
+    const size_t g2 = gemm_f32_bytes((int)m, (int)k, (int)n), g3 = gemm_f32_bytes((int)k, (int)k, (int)n);
+    if (g2 > g) g = g2;
+    if (g3 > g) g = g3;
+    L.gws = take(g);
     L.total = off;
     return L;
 }
@@ -790,14 +790,16 @@ size_t backward_bytes(int64_t m, int64_t n, int64_t k) { return bwd_layout(m, n,
 //   dA[:, rest] = C W,   dA[:, J] = (B - C T) W^T - C W T^T.
 // In full-width form (W zero on J, R = A - C Z zero on J):
 //   dA = C W (all columns, zero on J), dC = R W^T - C (W Z^T), dA[:, J] = dC.
-// W is formed in FP64 (U^{-1} applied twice with DGEMM: the gradient carries
-// cond(C)^2); the products with C, R and Z are FP32-accurate GEMMs.
+// W is formed in FP64 (U^{-1} applied twice: the gradient carries
+// cond(C)^2); the products with C, R and Z are FP32-accurate 3xTF32
+// products on the tensor cores.
 int backward_run(const float* A, int64_t m, int64_t n, int64_t lda, int k, const int32_t* J, const float* Z,
                  int64_t ldz, const float* dZ, int64_t lddz, float* dA, int64_t ldda, void* ws, DevInfo* dinfo,
                  cudaStream_t s) {
     const BwdLayout L = bwd_layout(m, n, k);
     char* base = static_cast<char*>(ws);
     int* flag = reinterpret_cast<int*>(base + L.flag);
+    int* gst = flag + 1;
     unsigned char* mask = reinterpret_cast<unsigned char*>(base + L.mask);
     float* C32 = reinterpret_cast<float*>(base + L.C32);
     double* Gp = reinterpret_cast<double*>(base + L.Gp);
@@ -806,58 +808,35 @@ int backward_run(const float* A, int64_t m, int64_t n, int64_t lda, int k, const
     double* G64 = reinterpret_cast<double*>(base + L.G64);
     double* Y64 = reinterpret_cast<double*>(base + L.Y64);
     float* W32 = reinterpret_cast<float*>(base + L.W32);
-    float* Rb = reinterpret_cast<float*>(base + L.Rb);
+    float* R = reinterpret_cast<float*>(base + L.R);
     float* dC = reinterpret_cast<float*>(base + L.dC);
     float* M1 = reinterpret_cast<float*>(base + L.M1);
-    cublasHandle_t h = cublas_handle();
-    if (!h) return ID_ECUDA;
-    std::lock_guard<std::mutex> lk(g_cb_mu);
-    if (cublasSetStream(h, s) != CUBLAS_STATUS_SUCCESS) return ID_ECUDA;
-    if (cublasSetWorkspace(h, base + L.cws, kCublasWs) != CUBLAS_STATUS_SUCCESS) return ID_ECUDA;
+    void* gws = base + L.gws;
+    const int M = (int)m, N = (int)n;
     if (cudaMemsetAsync(flag, 0, 16, s) != cudaSuccess) return ID_ECUDA;
     if (cudaMemsetAsync(mask, 0, (size_t)n, s) != cudaSuccess) return ID_ECUDA;
     const int tr = trace_begin(TraceKind::kRefine, s);
-    if (factor_skeleton(A, m, n, lda, k, J, C32, Gp, Wa, Uinv64, reinterpret_cast<double*>(base + L.gdiag), flag, h,
-                        s) != cudaSuccess)
+    if (factor_skeleton(A, m, n, lda, k, J, C32, Gp, Wa, Uinv64, reinterpret_cast<double*>(base + L.gdiag), flag, s) !=
+        cudaSuccess)
         return ID_ECUDA;
     k_mask_j<<<1, kRThreads, 0, s>>>(J, k, n, mask);
     dim3 g2(ceil_div(n, kRThreads) < 1024 ? ceil_div(n, kRThreads) : 1024, k);
-    k_gz<<<g2, kRThreads, 0, s>>>(dZ, lddz, k, (int)n, mask, G64);
-    // W = U^{-1} U^{-T} G (FP64). Row-major k x n matrices are column-major n x k
-    // (ld n); Uinv64 row-major is the column-major (U^{-1})^T.
-    const double one = 1.0, zero = 0.0;
-    if (cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_T, (int)n, k, k, &one, G64, (int)n, Uinv64, k, &zero, Y64, (int)n) !=
-        CUBLAS_STATUS_SUCCESS)
-        return ID_ECUDA;
-    if (cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, (int)n, k, k, &one, Y64, (int)n, Uinv64, k, &zero, G64, (int)n) !=
-        CUBLAS_STATUS_SUCCESS)
-        return ID_ECUDA;
+    k_gz<<<g2, kRThreads, 0, s>>>(dZ, lddz, k, N, mask, G64);
+    // W = U^{-1} (U^{-T} G) in FP64 (Uinv64 is U^{-1} row-major)
+    if (dgemm(1, 0, k, N, k, 1.0, Uinv64, k, G64, n, 0.0, Y64, n, s) != cudaSuccess) return ID_ECUDA;
+    if (dgemm(0, 0, k, N, k, 1.0, Uinv64, k, Y64, n, 0.0, G64, n, s) != cudaSuccess) return ID_ECUDA;
     k_to_f32<<<grid_for((int64_t)k * n), kRThreads, 0, s>>>(G64, W32, (int64_t)k * n);
-    // dA = C W: dA^T (n x m, ld ldda) = W^T (n x k) C^T (k x m)
-    if (!sgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, (int)n, (int)m, k, 1.0f, W32, (int)n, C32, k, 0.0f, dA, (int)ldda))
-        return ID_ECUDA;
-    // dC = sum_b R_b W_b^T: dC^T (k x m, ld k) += W_b (k x nb) R_b^T (nb x m)
-    cublasLtHandle_t lt = lt_handle();
-    for (int64_t b0 = 0; b0 < n; b0 += kResCols) {
-        const int nb = (int)(n - b0 < kResCols ? n - b0 : kResCols);
-        if (!sgemm_lt(lt, CUBLAS_OP_N, CUBLAS_OP_N, nb, (int)m, k, -1.0f, Z + b0, (int)ldz, C32, k, 1.0f, A + b0, (int)lda, Rb, nb,
-                      base + L.cws, kCublasWs, s)) {
-            if (cudaMemcpy2DAsync(Rb, (size_t)nb * 4, A + b0, (size_t)lda * 4, (size_t)nb * 4, (size_t)m,
-                                  cudaMemcpyDeviceToDevice, s) != cudaSuccess)
-                return ID_ECUDA;
-            if (!sgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, nb, (int)m, k, -1.0f, Z + b0, (int)ldz, C32, k, 1.0f, Rb, nb))
-                return ID_ECUDA;
-        }
-        if (!sgemm(h, CUBLAS_OP_T, CUBLAS_OP_N, k, (int)m, nb, 1.0f, W32 + b0, (int)n, Rb, nb, b0 == 0 ? 0.0f : 1.0f,
-                   dC, k))
-            return ID_ECUDA;
-    }
-    // M1 = W Z^T (k x k; the buffer read row-major is M1): M1^T = Z W^T
-    if (!sgemm(h, CUBLAS_OP_T, CUBLAS_OP_N, k, k, (int)n, 1.0f, Z, (int)ldz, W32, (int)n, 0.0f, M1, k))
-        return ID_ECUDA;
-    // dC -= C M1: dC^T (k x m) -= M1^T (k x k) C^T (k x m)
-    if (!sgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, k, (int)m, k, -1.0f, M1, k, C32, k, 1.0f, dC, k)) return ID_ECUDA;
-    k_scatter_dc<<<grid_for(m * k), kRThreads, 0, s>>>(dC, (int)m, k, J, n, dA, ldda);
+    int rc;
+    // dA = C W (m x n)
+    if ((rc = gemm_f32(0, 0, M, N, k, 1.0f, C32, k, W32, n, 0.0f, dA, ldda, gws, gst, s)) != ID_OK) return rc;
+    // R = A - C Z (m x n)
+    if ((rc = gemm_f32_ex(0, 0, M, N, k, -1.0f, C32, k, Z, ldz, 1.0f, A, lda, R, n, gws, gst, s)) != ID_OK) return rc;
+    // dC = R W^T (m x k)
+    if ((rc = gemm_f32(0, 1, M, k, N, 1.0f, R, n, W32, n, 0.0f, dC, k, gws, gst, s)) != ID_OK) return rc;
+    // M1 = W Z^T (k x k), then dC -= C M1
+    if ((rc = gemm_f32(0, 1, k, k, N, 1.0f, W32, n, Z, ldz, 0.0f, M1, k, gws, gst, s)) != ID_OK) return rc;
+    if ((rc = gemm_f32(0, 0, M, k, k, -1.0f, C32, k, M1, k, 1.0f, dC, k, gws, gst, s)) != ID_OK) return rc;
+    k_scatter_dc<<<grid_for(m * k), kRThreads, 0, s>>>(dC, M, k, J, n, dA, ldda);
     k_bwd_finalize<<<1, 1, 0, s>>>(dinfo, flag);
     trace_end(tr, s);
     return cudaGetLastError() == cudaSuccess ? ID_OK : ID_ECUDA;
@@ -929,13 +908,13 @@ template cudaError_t identity_id<float>(int32_t*, void*, int64_t, int, DevInfo*,
 
 __global__ void k_recon_finalize(DevInfo* info, const int* flag) {
     id_info r = {};
-    r.status = flag[0] == 2 ? ID_EINVAL : ID_OK;
+    r.status = flag[0] == 2 ? ID_EINVAL : ((flag[1] & kStatTimeout) ? ID_ETIMEOUT : ID_OK);
     r.err_est = -1.0;
     info->info = r;
 }
 
 size_t reconstruct_bytes(int64_t m, int64_t n, int64_t k, int rows, size_t s) {
-    return al(16) + al(s * (size_t)k * (size_t)(rows ? n : m)) + kCublasWs;
+    return al(16) + al(s * (size_t)k * (size_t)(rows ? n : m)) + (s == 4 ? gemm_f32_bytes((int)m, (int)n, (int)k) : 0);
 }
 
 template <typename T>
@@ -944,38 +923,28 @@ int reconstruct_run(const void* Av, int64_t m, int64_t n, int64_t lda, int k, co
     char* base = static_cast<char*>(ws);
     int* flag = reinterpret_cast<int*>(base);
     T* S = reinterpret_cast<T*>(base + al(16));
-    char* cws = base + al(16) + al(sizeof(T) * (size_t)k * (size_t)(rows ? n : m));
-    cublasHandle_t h = cublas_handle();
-    if (!h) return ID_ECUDA;
-    std::lock_guard<std::mutex> lk(g_cb_mu);
-    if (cublasSetStream(h, s) != CUBLAS_STATUS_SUCCESS) return ID_ECUDA;
-    if (cublasSetWorkspace(h, cws, kCublasWs) != CUBLAS_STATUS_SUCCESS) return ID_ECUDA;
+    char* gws = base + al(16) + al(sizeof(T) * (size_t)k * (size_t)(rows ? n : m));
     if (cudaMemsetAsync(flag, 0, 16, s) != cudaSuccess) return ID_ECUDA;
     const T* A = static_cast<const T*>(Av);
     k_gather_skel<T><<<grid_for(rows ? (int64_t)k * n : m * k), kRThreads, 0, s>>>(A, lda, (int)m, (int)n, k, J, rows,
                                                                                   S, flag);
-    // Column-major views of the row-major arrays. Column ID: Out^T (n x m) =
-    // Z^T (n x k, ld ldz) S^T (k x m, ld k). Row ID: Out^T (n x m) = S^T (n x k,
-    // ld n) Z (k x m), Z^T being the column-major (m x k, ld ldz) view.
-    const int M = (int)n, N = (int)m;
-    bool ok;
+    // Column ID: Out (m x n) = S (m x k) Z (k x n). Row ID: Out = Z^T (m x k; Z is k x m) S (k x n).
+    const int M = (int)m, N = (int)n;
     if (sizeof(T) == 8) {
-        const double one = 1.0, zero = 0.0;
         const double* Z = static_cast<const double*>(Zv);
         const double* Sd = reinterpret_cast<const double*>(S);
         double* Out = static_cast<double*>(Outv);
-        ok = (rows ? cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_T, M, N, k, &one, Sd, (int)n, Z, (int)ldz, &zero, Out,
-                                 (int)ldo)
-                   : cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, M, N, k, &one, Z, (int)ldz, Sd, k, &zero, Out,
-                                 (int)ldo)) == CUBLAS_STATUS_SUCCESS;
+        const cudaError_t e = rows ? dgemm(1, 0, M, N, k, 1.0, Z, ldz, Sd, n, 0.0, Out, ldo, s)
+                                   : dgemm(0, 0, M, N, k, 1.0, Sd, k, Z, ldz, 0.0, Out, ldo, s);
+        if (e != cudaSuccess) return ID_ECUDA;
     } else {
         const float* Z = static_cast<const float*>(Zv);
         const float* Sf = reinterpret_cast<const float*>(S);
         float* Out = static_cast<float*>(Outv);
-        ok = rows ? sgemm(h, CUBLAS_OP_N, CUBLAS_OP_T, M, N, k, 1.0f, Sf, (int)n, Z, (int)ldz, 0.0f, Out, (int)ldo)
-                  : sgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, M, N, k, 1.0f, Z, (int)ldz, Sf, k, 0.0f, Out, (int)ldo);
+        const int rc = rows ? gemm_f32(1, 0, M, N, k, 1.0f, Z, ldz, Sf, n, 0.0f, Out, ldo, gws, flag + 1, s)
+                            : gemm_f32(0, 0, M, N, k, 1.0f, Sf, k, Z, ldz, 0.0f, Out, ldo, gws, flag + 1, s);
+        if (rc != ID_OK) return rc;
     }
-    if (!ok) return ID_ECUDA;
     k_recon_finalize<<<1, 1, 0, s>>>(dinfo, flag);
     return cudaGetLastError() == cudaSuccess ? ID_OK : ID_ECUDA;
 }
@@ -987,7 +956,7 @@ template int reconstruct_run<float>(const void*, int64_t, int64_t, int64_t, int,
 
 // ------------------------------------------------ column-sampling Optim RID --
 struct SampLayout {
-    size_t flag, C32, Gp, gdiag, Wa, Uinv64, M64, C64, B64, Z64, cws, total;
+    size_t flag, C32, Gp, gdiag, Wa, Uinv64, M64, C64, B64, Z64, total;
 };
 
 static SampLayout samp_layout(int64_t m, int64_t n, int64_t k) {
@@ -1008,7 +977,6 @@ static SampLayout samp_layout(int64_t m, int64_t n, int64_t k) {
     L.C64 = take(8 * (size_t)m * k);
     L.B64 = take(8 * (size_t)k * n);
     L.Z64 = take(8 * (size_t)k * n);
-    L.cws = take(kCublasWs);
     L.total = off;
     return L;
 }
@@ -1029,12 +997,13 @@ cudaError_t sample_map_j(const int* perm, const int32_t* idx, int k, int32_t* J,
 }
 
 // Z of Optim RID: R_k^T R_k Z = C^T A in FP64. FP64 data: R_k is the CPQR's own
-// factor (the paper's route) and B = C^T A is a DGEMM. FP32 data: the CPQR's
-// R_k carries FP32 rounding, which the normal equations would square, so U with
-// U^T U = C^T C is formed from C itself (exact products, double-float sums,
-// FP64 Cholesky) -- the same matrix in exact arithmetic -- and B = C^T A comes
-// from k_ctb (exact products, double-float sums). Then M = U^{-1} U^{-T} and
-// Z = M B in FP64; Z[:, J] is set to the identity it equals in exact arithmetic.
+// factor (the paper's route) and B = C^T A is an FP64 product. FP32 data: the
+// CPQR's R_k carries FP32 rounding, which the normal equations would square,
+// so U with U^T U = C^T C is formed from C itself (exact products,
+// double-float sums, FP64 Cholesky) -- the same matrix in exact arithmetic --
+// and B = C^T A comes from k_ctb (exact products, double-float sums). Then
+// M = U^{-1} U^{-T} and Z = M B in FP64; Z[:, J] is set to the identity it
+// equals in exact arithmetic.
 template <typename T>
 int sampled_z_run(const void* Av, int64_t m, int64_t n, int64_t lda, int k, const int32_t* J, const void* W, int ldw,
                   void* Zv, int64_t ldz, void* ws, DevInfo* dinfo, cudaStream_t s) {
@@ -1049,48 +1018,35 @@ int sampled_z_run(const void* Av, int64_t m, int64_t n, int64_t lda, int k, cons
     double* C64 = reinterpret_cast<double*>(base + L.C64);
     double* B64 = reinterpret_cast<double*>(base + L.B64);
     double* Z64 = reinterpret_cast<double*>(base + L.Z64);
-    cublasHandle_t h = cublas_handle();
-    if (!h) return ID_ECUDA;
-    std::lock_guard<std::mutex> lk(g_cb_mu);
-    if (cublasSetStream(h, s) != CUBLAS_STATUS_SUCCESS) return ID_ECUDA;
-    if (cublasSetWorkspace(h, base + L.cws, kCublasWs) != CUBLAS_STATUS_SUCCESS) return ID_ECUDA;
+    const int N = (int)n;
     if (cudaMemsetAsync(flag, 0, 16, s) != cudaSuccess) return ID_ECUDA;
     const int tr = trace_begin(TraceKind::kSampledZ, s);
-    const double one = 1.0, zero = 0.0;
     if (sizeof(T) == 8) {
         const double* A64 = reinterpret_cast<const double*>(Av);
         k_rk_identity<T><<<grid_for((int64_t)2 * k * k), kRThreads, 0, s>>>(static_cast<const T*>(W), ldw, k, Wa);
-        if (tri_inverse(Wa, k, Wa + (size_t)k * k, reinterpret_cast<double*>(base + L.Gp), Uinv64, h, s) !=
-            cudaSuccess)
+        if (tri_inverse(Wa, k, Wa + (size_t)k * k, reinterpret_cast<double*>(base + L.Gp), Uinv64, s) != cudaSuccess)
             return ID_ECUDA;
         k_gather_f64<T><<<grid_for(m * k), kRThreads, 0, s>>>(A, lda, (int)m, k, J, C64);
-        // B = C^T A: B^T (n x k) = A^T (n x m) C (m x k); row-major arrays read as column-major transposes
-        if (cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_T, (int)n, k, (int)m, &one, A64, (int)lda, C64, k, &zero, B64,
-                        (int)n) != CUBLAS_STATUS_SUCCESS)
-            return ID_ECUDA;
+        // B = C^T A (k x n)
+        if (dgemm(1, 0, k, N, (int)m, 1.0, C64, k, A64, lda, 0.0, B64, n, s) != cudaSuccess) return ID_ECUDA;
     } else {
         float* C32 = reinterpret_cast<float*>(base + L.C32);
         if (factor_skeleton(reinterpret_cast<const float*>(A), m, n, lda, k, J, C32,
                             reinterpret_cast<double*>(base + L.Gp), Wa, Uinv64,
-                            reinterpret_cast<double*>(base + L.gdiag), flag, h, s) != cudaSuccess)
+                            reinterpret_cast<double*>(base + L.gdiag), flag, s) != cudaSuccess)
             return ID_ECUDA;
         k_ctb<<<dim3(ceil_div(n, kGT), ceil_div(k, kGT)), 256, 0, s>>>(C32, reinterpret_cast<const float*>(A), lda,
-                                                                       (int)m, k, (int)n, B64);
+                                                                       (int)m, k, N, B64);
     }
-    // M = U^{-1} U^{-T} (= (C^T C)^{-1}); Uinv64 row-major reads as U^{-T} column-major
-    if (cublasDgemm(h, CUBLAS_OP_T, CUBLAS_OP_N, k, k, k, &one, Uinv64, k, Uinv64, k, &zero, M64, k) !=
-        CUBLAS_STATUS_SUCCESS)
-        return ID_ECUDA;
-    // Z = M B: Z^T (n x k) = B^T M^T
+    // M = U^{-1} U^{-T} (= (C^T C)^{-1}), then Z = M B (k x n)
+    if (dgemm(0, 1, k, k, k, 1.0, Uinv64, k, Uinv64, k, 0.0, M64, k, s) != cudaSuccess) return ID_ECUDA;
     double* Zd = sizeof(T) == 8 ? reinterpret_cast<double*>(Zv) : Z64;
-    const int ldzd = sizeof(T) == 8 ? (int)ldz : (int)n;
-    if (cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_T, (int)n, k, k, &one, B64, (int)n, M64, k, &zero, Zd, ldzd) !=
-        CUBLAS_STATUS_SUCCESS)
-        return ID_ECUDA;
+    const int64_t ldzd = sizeof(T) == 8 ? ldz : n;
+    if (dgemm(0, 0, k, N, k, 1.0, M64, k, B64, n, 0.0, Zd, ldzd, s) != cudaSuccess) return ID_ECUDA;
     dim3 g2(ceil_div(n, kRThreads) < 1024 ? ceil_div(n, kRThreads) : 1024, k);
-    if (sizeof(T) == 4) k_z_from64<T><<<g2, kRThreads, 0, s>>>(Z64, k, (int)n, Z, ldz);
+    if (sizeof(T) == 4) k_z_from64<T><<<g2, kRThreads, 0, s>>>(Z64, k, N, Z, ldz);
     k_identity_at_j<T><<<grid_for((int64_t)k * k), kRThreads, 0, s>>>(Z, ldz, J, k);
-    k_zstats_t<T><<<g2, kRThreads, 0, s>>>(Z, ldz, k, (int)n, dinfo);
+    k_zstats_t<T><<<g2, kRThreads, 0, s>>>(Z, ldz, k, N, dinfo);
     k_sampled_finalize<<<1, 1, 0, s>>>(dinfo, flag);
     trace_end(tr, s);
     return cudaGetLastError() == cudaSuccess ? ID_OK : ID_ECUDA;
