@@ -154,9 +154,9 @@ int id_decompose_host(const void* A_host, id_dtype dtype, int64_t m, int64_t n, 
  *   NULL when the call is enqueued into a stream that is being captured (a
  *   non-NULL info makes the call wait for the stream, which capture forbids).
  *   Returns ID_ENOMEM, before enqueuing anything, when
- *   id_workspace_size(dtype, m, n, k, opts) > ID_NOALLOC_SCRATCH_BYTES, and
- *   ID_EINVAL when opts->zsolve != 0 (that route's library GEMMs create a
- *   handle, and allocate, on first use).
+ *   id_workspace_size(dtype, m, n, k, opts) > ID_NOALLOC_SCRATCH_BYTES.
+ *   Every option of id_decompose is taken (the normal-equation route's
+ *   products are the library's own kernels and allocate nothing).
  *   The first call on a device looks up the array's device address (with that
  *   device current); make that first call before any stream capture.
  *   All calls share the one array: calls that may overlap on the GPU (other

@@ -42,9 +42,6 @@ int scratch_for_current_device(void** out) {
 extern "C" int id_decompose_noalloc(const void* A, id_dtype dtype, int64_t m, int64_t n, int64_t lda, int64_t k,
                                     const id_opts* opts, int32_t* J, void* Z, int64_t ldz, id_info* info,
                                     void* stream) {
-    // The normal-equation route (zsolve = 1) runs library GEMMs that create a
-    // handle, and so allocate, on first use: refused here.
-    if (opts && opts->zsolve != 0) return ID_EINVAL;
     const size_t need = id_workspace_size(dtype, m, n, k, opts);
     if (need == 0) return ID_EINVAL;
     if (need > (size_t)ID_NOALLOC_SCRATCH_BYTES) return ID_ENOMEM;   // problem too large for the fixed scratch

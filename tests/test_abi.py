@@ -433,11 +433,3 @@ def test_bounded_wait_selftest_argument_rules(gbid):
     assert st.value == 7
     assert gbid.SELFTEST_WORK_BYTES == 4096
 
-
-def test_noalloc_refuses_the_normal_equation_route(gbid):
-    # the zsolve = 1 route would reach library GEMMs that allocate on first use;
-    # the no-allocation entry point refuses it before anything is enqueued
-    fake = ctypes.c_void_p(256)
-    o = gbid._opts(0, zsolve=1)
-    rc = gbid.lib().id_decompose_noalloc(fake, gbid.ID_F64, 10, 20, 20, 5, ctypes.byref(o), fake, fake, 20, None, None)
-    assert rc == gbid.ID_EINVAL
