@@ -417,6 +417,9 @@ int id_selftest_bounded_wait(void* work, size_t work_bytes, int* status, void* s
 /* Number of kernel launches one id_decompose call enqueues for this problem
  * (memsets excluded). Returns -1 for invalid arguments. */
 int64_t id_launch_count(id_dtype dtype, int64_t m, int64_t n, int64_t k, const id_opts* opts);
+/* The same for one id_decompose_randomized call (sketch, CPQR of the l x n
+ * sketch, solve, Z, and the refinement unless opts->refine < 0). */
+int64_t id_rid_launch_count(int64_t m, int64_t n, int64_t l, int64_t k, const id_opts* opts);
 
 /* id_reconstruct -- the ID's approximation of A (the `approx = C @ Z` that
  * the paper's listings return with the skeleton and Z, Sec. 2.1):

@@ -86,6 +86,9 @@ def cpqr(X: np.ndarray, k: int, pivots=None):
       perm   n int64: perm[i] = original index of the column now at position i;
       tau    k FP64 reflector scalars;
       nu     k FP64: the winning residual norm at each step (= |R_jj|);
+      top    k FP64: the largest residual norm at each step (= nu unless the
+             pivots are forced; 1 - nu / top is then the forced choice's
+             shortfall against the greedy rule, as verify_pivots reports it);
       gap    k FP64: relative gap (nu_max - nu_second) / nu_max at each step;
       rank   numerical rank found within the k steps (k if none is small).
     """
@@ -96,6 +99,7 @@ def cpqr(X: np.ndarray, k: int, pivots=None):
     perm = np.arange(n, dtype=np.int64)
     tau = np.zeros(k)
     nu_win = np.zeros(k)
+    nu_top = np.zeros(k)
     gap = np.full(k, np.inf)
     for j in range(k):
         B = F[j:, j:]
@@ -111,6 +115,7 @@ def cpqr(X: np.ndarray, k: int, pivots=None):
             second = rest.max()
             gap[j] = (top - second) / top if top > 0 else 0.0
         nu_win[j] = nu[p - j]
+        nu_top[j] = top
         if p != j:
             F[:, [j, p]] = F[:, [p, j]]
             perm[[j, p]] = perm[[p, j]]
@@ -128,7 +133,7 @@ def cpqr(X: np.ndarray, k: int, pivots=None):
         if d[0] == 0.0 or d[j] <= thresh:
             rank = j
             break
-    return {"F": F, "perm": perm, "tau": tau, "nu": nu_win, "gap": gap, "rank": rank}
+    return {"F": F, "perm": perm, "tau": tau, "nu": nu_win, "top": nu_top, "gap": gap, "rank": rank}
 
 
 def back_substitute(R11: np.ndarray, R12: np.ndarray) -> np.ndarray:
@@ -171,6 +176,7 @@ def interp_decomp(A: np.ndarray, k: int, pivots=None):
         "R": R,
         "tau": f["tau"],
         "nu": f["nu"],
+        "top": f["top"],
         "gap": f["gap"],
         "rank": f["rank"],
         "n_gt2": int(np.count_nonzero(np.abs(Z) > 2.0)),

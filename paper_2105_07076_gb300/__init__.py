@@ -116,6 +116,7 @@ _SIG = {
                                    ctypes.c_size_t, _P, _P]),
     "id_refine": (ctypes.c_int, [_P, ctypes.c_int, _I64, _I64, _I64, _I64, _P, _P, _I64, _P, ctypes.c_size_t, _P, _P]),
     "id_launch_count": (ctypes.c_int64, [ctypes.c_int, _I64, _I64, _I64, _P]),
+    "id_rid_launch_count": (ctypes.c_int64, [_I64, _I64, _I64, _I64, _P]),
     "id_cpqr_residual_norms": (ctypes.c_int, [_P, ctypes.c_int, _I64, _I64, _I64, _I64, _P, _P, _P]),
     "id_selftest_bounded_wait": (ctypes.c_int, [_P, ctypes.c_size_t, _P, _P]),
     "id_trace_enable": (ctypes.c_int, [ctypes.c_int]),
@@ -709,6 +710,12 @@ def launch_count(dtype: torch.dtype, m: int, n: int, k: int, nb: int = 0, engine
     engine cannot take the problem)."""
     o = _opts(nb, engine=engine)
     return int(lib().id_launch_count(_DTYPES[dtype], m, n, k, ctypes.byref(o)))
+
+
+def rid_launch_count(m: int, n: int, l: int, k: int, nb: int = 0, refine: bool = True) -> int:
+    """Kernel launches one id_decompose_randomized call enqueues (as the library counts them)."""
+    o = _opts(nb, refine)
+    return int(lib().id_rid_launch_count(m, n, l, k, ctypes.byref(o)))
 
 
 def trace_enable(capacity: int = 4096) -> None:

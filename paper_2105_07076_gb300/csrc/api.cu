@@ -43,7 +43,7 @@ int pick_nb(id_dtype dt, int m, int n, int k, const id_opts* opts) {
 }
 
 struct Layout {
-    size_t info, state, W, F, xbuf, ssq, sync, vn1, vn2, perm, tau, part3, aux, T, total;
+    size_t info, state, W, F, xbuf, ssq, sync, vn1, vn2, perm, tau, part3, aux, T, wy, total;
     int m, n, ldw, nb, ldf;
 };
 
@@ -74,6 +74,8 @@ Layout make_layout(id_dtype dt, int m, int n, int k, const id_opts* opts, bool w
     L.part3 = take(sizeof(ArgMax) * kMaxParts);
     L.aux = take(s * kMaxPanel);
     L.T = with_t ? take(8 * (size_t)k * (n - k > 0 ? n - k : 1)) : 0;
+    // FP32 panels narrower than k: operand scratch of the tensor-core WY update
+    L.wy = (dt == ID_F32 && L.nb < k) ? take(wy_bytes(m, n, L.nb)) : 0;
     L.total = off;
     return L;
 }
@@ -100,7 +102,20 @@ CpqrPlan make_plan(const Layout& L, char* base, void* W, int32_t* perm, double* 
     P.part3 = reinterpret_cast<ArgMax*>(base + L.part3);
     P.aux = base + L.aux;
     P.st = reinterpret_cast<State*>(base + L.state);
+    P.wy_ws = L.wy ? base + L.wy : nullptr;
     return P;
+}
+
+// Kernel launches of cpqr_run on an m x n working matrix: one persistent
+// launch, or for FP32 panels narrower than k one launch per panel with the
+// tensor-core WY update (two operand splits and the product) between panels
+// while rows remain below the panel.
+int64_t cpqr_launch_count(id_dtype dt, int64_t m, int64_t n, int64_t k, const id_opts* opts) {
+    const int nb = pick_nb(dt, (int)m, (int)n, (int)k, opts);
+    int64_t c = 1;
+    if (dt == ID_F32 && nb < k)
+        for (int64_t je = nb; je < k; je += nb) c += 1 + (m > je ? 3 : 0);
+    return c;
 }
 
 bool sizes_ok(int64_t m, int64_t n, int64_t k) {
@@ -583,14 +598,21 @@ int id_info_read(const void* work, id_info* info, void* stream) {
     return read_info(work, info, static_cast<cudaStream_t>(stream));
 }
 
+int64_t id_rid_launch_count(int64_t m, int64_t n, int64_t l, int64_t k, const id_opts* opts) {
+    if (id_rid_workspace_size(m, n, l, k, opts) == 0) return -1;
+    // sketch, copy-in, CPQR of the sketch, solve (when n > k), Z scatter, status, refinement
+    return 4 + cpqr_launch_count(ID_F32, l, n, k, opts) + (n > k ? 1 : 0) +
+           (rid_refine(opts) ? refine_launch_count(m, n, k) : 0);
+}
+
 int64_t id_launch_count(id_dtype dtype, int64_t m, int64_t n, int64_t k, const id_opts* opts) {
     if ((dtype != ID_F64 && dtype != ID_F32) || !sizes_ok(m, n, k) || !engine_ok(dtype, m, n, k, opts)) return -1;
     if (zsolve_of(opts) == 1) return -1;   // not counted: the launches of the blocked inverse depend on k
     const bool cl = dtype == ID_F64 ? use_cluster<double>(m, n, k, opts) : use_cluster<float>(m, n, k, opts);
     if (cl) return 2;   // the cluster kernel and its statistics kernel
-    const int64_t nx = m > n ? m : n;
-    // copy-in, persistent CPQR, back substitution (when n > k), Z scatter, status, error estimate
-    return 5 + (nx > k ? 1 : 0);
+    const int64_t nx = m > n ? m : n, mx = m > n ? n : m;
+    // copy-in, CPQR, back substitution (when n > k), Z scatter, status, error estimate
+    return 4 + cpqr_launch_count(dtype, mx, nx, k, opts) + (nx > k ? 1 : 0);
 }
 
 size_t id_reconstruct_workspace_size(id_dtype dtype, int64_t m, int64_t n, int64_t k, int32_t transposed) {

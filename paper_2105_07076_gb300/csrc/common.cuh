@@ -76,6 +76,39 @@ struct DevInfo {
     unsigned long long max_abs_z_bits;
 };
 
+// Z statistics of Definition 1 (count of |Z_ij| > 2, largest |Z_ij|): the
+// block's partial counts and maxima (amax >= 0, +inf for a NaN) are reduced in
+// shared memory and committed with one atomic of each per block. Every thread
+// of the block must call it.
+__device__ __forceinline__ void zstats_commit(unsigned long long gt2, double amax, DevInfo* info) {
+    __shared__ unsigned long long s_gt2[32];
+    __shared__ double s_amax[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        gt2 += __shfl_xor_sync(0xffffffffu, gt2, o);
+        amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    }
+    const int w = threadIdx.x / kWarp, lane = threadIdx.x % kWarp, nw = (blockDim.x + kWarp - 1) / kWarp;
+    if (lane == 0) {
+        s_gt2[w] = gt2;
+        s_amax[w] = amax;
+    }
+    __syncthreads();
+    if (w == 0) {
+        gt2 = lane < nw ? s_gt2[lane] : 0ull;
+        amax = lane < nw ? s_amax[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            gt2 += __shfl_xor_sync(0xffffffffu, gt2, o);
+            amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+        }
+        if (lane == 0) {
+            if (gt2) atomicAdd(&info->n_gt2, gt2);
+            atomicMax(&info->max_abs_z_bits, (unsigned long long)__double_as_longlong(amax));
+        }
+    }
+}
+
 inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 

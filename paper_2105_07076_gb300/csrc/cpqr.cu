@@ -22,6 +22,7 @@
 
 #include "common.cuh"
 #include "cpqr.cuh"
+#include "gemm.cuh"
 #include "trace.cuh"
 
 namespace gbid {
@@ -276,6 +277,8 @@ struct KParams {
     double rank_tol;
     int rows_per_cta; // row chunk of the pivot-column phase (multiple of 32)
     int short_mode;   // short matrices with panels of at most 32: one grid barrier per step
+    int j_begin, j_end;   // the pivot steps of this launch (one panel when the WY update runs outside)
+    int wy_outside;       // 1: no phase C; the compact-WY update runs as its own launch between panels
 };
 
 // WY tile: W(i, l) -= sum_{c < nbw} V(i, c) F(l, c), 64 x 64 tile at (i0, l0).
@@ -414,8 +417,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
     unsigned epoch = 0;
     const uint64_t pol_last = l2_policy(true), pol_first = l2_policy(false);
 
-    // ---- column norms, perm, first argmax partials
-    {
+    // ---- column norms, perm, first argmax partials (the first launch only)
+    if (P.j_begin == 0) {
         if (blockIdx.x == 0 && t == 0) {
             st->rank = P.k;
             st->rank_tol = P.rank_tol;
@@ -448,15 +451,15 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
         if (t == 0) P.part[blockIdx.x] = best;
         fro = block_sum(fro);
         if (t == 0) atomicAdd(&st->fro2, fro);
+        grid_sync(P.bar, epoch, st);
     }
-    grid_sync(P.bar, epoch, st);
 
     const int RC = P.rows_per_cta;
     const int r0 = blockIdx.x * RC;
     const int r1 = min(r0 + RC, m);
-    double r00 = 0.0;   // |R_00| (thread 0)
+    double r00 = P.j_begin > 0 ? ld(&st->r00) : 0.0;   // |R_00| (thread 0; set at step 0)
 
-    for (int j = 0; j < P.k; ++j) {
+    for (int j = P.j_begin; j < P.j_end; ++j) {
         if (timed_out(st)) break;
         const int j0 = j / P.nb * P.nb;
         const int jj = j - j0;
@@ -1325,7 +1328,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
         grid_sync(P.bar, epoch, st);
 
         // ---- C: compact-WY trailing update at the end of a panel
-        if (j + 1 < P.k && jj == P.nb - 1 && m > j + 1) {
+        if (!P.wy_outside && j + 1 < P.k && jj == P.nb - 1 && m > j + 1) {
             const int je = j + 1;
             const int tm = (m - je + 63) / 64, tn = (n - je + 63) / 64;
             for (int tile = blockIdx.x; tile < tm * tn; tile += G)
@@ -1416,6 +1419,46 @@ int cpqr_grid(int m) {
     return std::min(kMaxParts, g_nsm * occ);
 }
 
+static size_t al256(size_t x) { return (x + 255) / 256 * 256; }
+
+size_t wy_bytes(int m, int n, int nb) {
+    const size_t kp = (size_t)kpad16(nb);
+    return 2 * al256(4 * (size_t)m * kp) + 2 * al256(4 * (size_t)n * kp);
+}
+
+// The compact-WY update after the panel of steps j0..je-1 (FP32 data):
+// W(je:m, je:n) -= V F^T with V = W(je:m, j0:je) (the panel's reflectors below
+// its diagonal block) and F = F(je:n, 0:je-j0), as a 3xTF32 product on the
+// tensor cores whose epilogue updates W in place (column-major, so the
+// accumulator's lanes run along the rows of W and the stores coalesce).
+static int wy_update_f32(const CpqrPlan& P, int j0, int je, cudaStream_t s) {
+    const int M = P.m - je, N = P.n - je, nbw = je - j0, kp = (int)kpad16(nbw);
+    if (M < 1 || N < 1) return ID_OK;
+    char* w = static_cast<char*>(P.wy_ws);
+    float* ah = reinterpret_cast<float*>(w);
+    float* alo = reinterpret_cast<float*>(w + al256(4 * (size_t)P.m * kp));
+    float* bh = reinterpret_cast<float*>(w + 2 * al256(4 * (size_t)P.m * kp));
+    float* blo = reinterpret_cast<float*>(w + 2 * al256(4 * (size_t)P.m * kp) + al256(4 * (size_t)P.n * kp));
+    float* W = static_cast<float*>(P.W);
+    const float* F = static_cast<const float*>(P.F);
+    // V (M x nbw): V(r, c) = W[(j0 + c) * ldw + je + r], the transposed read of the panel's columns
+    if (split_tf32<float>(W + (int64_t)j0 * P.ldw + je, P.ldw, 1, M, nbw, kp, ah, alo, kp, s) != cudaSuccess)
+        return ID_ECUDA;
+    // F rows je..n-1 (N x nbw), row-major with leading dimension ldf
+    if (split_tf32<float>(F + (int64_t)je * P.ldf, P.ldf, 0, N, nbw, kp, bh, blo, kp, s) != cudaSuccess)
+        return ID_ECUDA;
+    TfEpilogue ep;
+    ep.alpha = -1.0f;
+    ep.beta = 1.0f;
+    ep.cin = W + (int64_t)je * P.ldw + je;   // W(je + r, je + c) at [c * ldw + r]
+    ep.ldc = P.ldw;
+    ep.cin_trans = 1;
+    ep.d = W + (int64_t)je * P.ldw + je;
+    ep.ldd = P.ldw;
+    ep.d_trans = 1;
+    return gemm_tf32x3(TfOperand{ah, alo, kp, M}, TfOperand{bh, blo, kp, N}, M, N, kp, 1, ep, &P.st->status, s);
+}
+
 template <typename T>
 cudaError_t cpqr_run(const CpqrPlan& P, cudaStream_t s) {
     const double eps = sizeof(T) == 8 ? DBL_EPSILON : (double)FLT_EPSILON;
@@ -1429,7 +1472,6 @@ cudaError_t cpqr_run(const CpqrPlan& P, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(P.st, 0, sizeof(State), s);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(P.sync, 0, sync_bytes(P.k), s);
-    if (e != cudaSuccess) return e;
     if (e != cudaSuccess) return e;
 
     KParams K;
@@ -1468,12 +1510,23 @@ cudaError_t cpqr_run(const CpqrPlan& P, cudaStream_t s) {
     attr.val.cooperative = 1;
     cfg.attrs = &attr;
     cfg.numAttrs = 1;
+    // FP32 panels narrower than k: the WY update runs on the tensor cores
+    // between per-panel launches of k_cpqr (which then skips its phase C).
+    K.wy_outside = (sizeof(T) == 4 && P.nb < P.k && P.wy_ws != nullptr) ? 1 : 0;
+    const int step = K.wy_outside ? P.nb : P.k;
     const int tr = trace_begin(TraceKind::kCpqr, s);
-    if (short_rows<T>(P.m)) e = cudaLaunchKernelEx(&cfg, k_cpqr<T, true, true>, K);
-    else if (pl.smem_v) e = cudaLaunchKernelEx(&cfg, k_cpqr<T, true, false>, K);
-    else e = cudaLaunchKernelEx(&cfg, k_cpqr<T, false, false>, K);
+    for (int j0 = 0; j0 < P.k; j0 += step) {
+        K.j_begin = j0;
+        K.j_end = j0 + step < P.k ? j0 + step : P.k;
+        if (j0 > 0 && (e = cudaMemsetAsync(K.bar, 0, 64, s)) != cudaSuccess) return e;   // fresh barrier epochs
+        if (short_rows<T>(P.m)) e = cudaLaunchKernelEx(&cfg, k_cpqr<T, true, true>, K);
+        else if (pl.smem_v) e = cudaLaunchKernelEx(&cfg, k_cpqr<T, true, false>, K);
+        else e = cudaLaunchKernelEx(&cfg, k_cpqr<T, false, false>, K);
+        if (e != cudaSuccess) return e;
+        if (K.wy_outside && K.j_end < P.k && P.m > K.j_end && wy_update_f32(P, j0, K.j_end, s) != ID_OK)
+            return cudaErrorLaunchFailure;
+    }
     trace_end(tr, s);
-    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

@@ -28,7 +28,13 @@ struct CpqrPlan {
     ArgMax* part3;            // kMaxParts argmax partials of the previous step
     void* aux;                // kMaxPanel (T)
     State* st;
+    void* wy_ws;              // FP32 with nb < k: wy_bytes(m, n, nb) of operand scratch for the
+                              // tensor-core compact-WY update between panels (nullptr: in-kernel update)
 };
+
+// Operand scratch of the FP32 compact-WY update W_trail -= V F^T (3xTF32 on
+// the tensor cores): V and F in split operand form.
+size_t wy_bytes(int m, int n, int nb);
 
 // Bytes of the zero-initialised synchronisation area of one CPQR: a 64-byte
 // grid-barrier slot and k per-step aux counters.
@@ -66,6 +72,7 @@ cudaError_t error_estimate(const double* vn1, int k, int n, const State* st, Dev
 // One least-squares refinement of Z against A (refine.cu). Returns an id_status;
 // updates info->info.refined and the Z statistics.
 size_t refine_bytes(int64_t m, int64_t n, int64_t k);
+int64_t refine_launch_count(int64_t m, int64_t n, int64_t k);
 cudaError_t refine_info_init(DevInfo* dinfo, int k, cudaStream_t s);   // status ID_OK, rank k, statistics zero
 int refine_run(const float* A, int64_t m, int64_t n, int64_t lda, int k, const int32_t* J, float* Z, int64_t ldz,
                void* ws, DevInfo* dinfo, cudaStream_t s);

@@ -35,9 +35,11 @@ constexpr int kGBK = 16;                            // K per stage: 16 FP32 = 64
 constexpr unsigned long long kGSpin = 1ull << 24;
 constexpr size_t kGSmemMax = 200 * 1024;
 
-template <int BN> struct GemmShape {
+// CPS CTAs per SM share its shared memory (and tensor memory): with two, one
+// CTA's epilogue overlaps the other's main loop.
+template <int BN, int CPS> struct GemmShape {
     static constexpr int kStage = 2 * 128 * 64 + 2 * BN * 64;   // A hi/lo + B hi/lo, bytes (multiple of 1024)
-    static constexpr int kStages0 = (int)((kGSmemMax - 1024) / kStage);
+    static constexpr int kStages0 = (int)((kGSmemMax / CPS - 1024) / kStage);
     static constexpr int kStages = kStages0 > 8 ? 8 : kStages0;
     static constexpr size_t kSmem = (size_t)kStages * kStage + 1024;
 };
@@ -48,12 +50,12 @@ struct GParams {
     int* status;
 };
 
-template <int BN>
-__global__ void __launch_bounds__(kGThreads, 1) k_gemm_tf32x3(const __grid_constant__ CUtensorMap tAh,
+template <int BN, int CPS>
+__global__ void __launch_bounds__(kGThreads, CPS) k_gemm_tf32x3(const __grid_constant__ CUtensorMap tAh,
                                                               const __grid_constant__ CUtensorMap tAl,
                                                               const __grid_constant__ CUtensorMap tBh,
                                                               const __grid_constant__ CUtensorMap tBl, GParams P) {
-    using Sh = GemmShape<BN>;
+    using Sh = GemmShape<BN, CPS>;
     constexpr int NS = Sh::kStages;
     extern __shared__ __align__(1024) unsigned char g_raw[];
     __shared__ __align__(8) uint64_t full[NS];
@@ -305,6 +307,37 @@ __global__ void __launch_bounds__(256) k_dgemm(int M, int N, int K, double alpha
     }
 }
 
+// Batched small FP64 products, C_z = alpha A_z B_z + beta C_z (row-major, no
+// transposes): 16 x 16 output tiles, one output per thread, so that even a
+// few small products spread over the GPU (the FP64 pipe issues about two
+// fused multiply-adds per clock per SM, so a product needs every SM).
+__global__ void __launch_bounds__(256) k_dgemm16(int M, int N, int K, double alpha, const double* __restrict__ A,
+                                                 int64_t lda, int64_t sa, const double* __restrict__ B, int64_t ldb,
+                                                 int64_t sb, double beta, double* __restrict__ C, int64_t ldc,
+                                                 int64_t sc) {
+    __shared__ double As[16][17], Bs[16][17];
+    const int z = blockIdx.z;
+    A += z * sa;
+    B += z * sb;
+    C += z * sc;
+    const int m0 = blockIdx.y * 16, n0 = blockIdx.x * 16;
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    double acc = 0.0;
+    for (int k0 = 0; k0 < K; k0 += 16) {
+        __syncthreads();
+        As[ty][tx] = (m0 + ty < M && k0 + tx < K) ? A[(int64_t)(m0 + ty) * lda + k0 + tx] : 0.0;
+        Bs[ty][tx] = (k0 + ty < K && n0 + tx < N) ? B[(int64_t)(k0 + ty) * ldb + n0 + tx] : 0.0;
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) acc = fma(As[ty][kk], Bs[kk][tx], acc);
+    }
+    const int i = m0 + ty, j = n0 + tx;
+    if (i < M && j < N) {
+        double* c = C + (int64_t)i * ldc + j;
+        *c = beta != 0.0 ? fma(alpha, acc, beta * *c) : alpha * acc;
+    }
+}
+
 // ------------------------------------------------------------------- host --
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
@@ -338,7 +371,7 @@ bool operand_map(CUtensorMap* map, const float* ptr, int64_t kp, int rows, int64
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int BN>
+template <int BN, int CPS>
 int launch_tf32x3(const TfOperand& A, const TfOperand& B, int M, int N, int K, int splits, const TfEpilogue& ep,
                   int* status, cudaStream_t s) {
     CUtensorMap tAh, tAl, tBh, tBl;
@@ -359,9 +392,11 @@ int launch_tf32x3(const TfOperand& A, const TfOperand& B, int M, int N, int K, i
     P.status = status;
     dim3 grid((N + BN - 1) / BN, (M + 127) / 128, splits);
     if (grid.y > 65535) return ID_EINVAL;
-    k_gemm_tf32x3<BN><<<grid, kGThreads, GemmShape<BN>::kSmem, s>>>(tAh, tAl, tBh, tBl, P);
+    k_gemm_tf32x3<BN, CPS><<<grid, kGThreads, GemmShape<BN, CPS>::kSmem, s>>>(tAh, tAl, tBh, tBl, P);
     return cudaGetLastError() == cudaSuccess ? ID_OK : ID_ECUDA;
 }
+
+int g_nsm_gemm = 148;   // SMs of the device (set by gemm_configure)
 
 size_t al256(size_t x) { return (x + 255) / 256 * 256; }
 
@@ -374,16 +409,23 @@ __global__ void k_gemm_status(const int* status, DevInfo* info) {
 
 }  // namespace
 
+template <int BN, int CPS>
+cudaError_t configure_one() {
+    return cudaFuncSetAttribute(k_gemm_tf32x3<BN, CPS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)GemmShape<BN, CPS>::kSmem);
+}
+
 cudaError_t gemm_configure() {
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k_gemm_tf32x3<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)GemmShape<64>::kSmem)) != cudaSuccess)
+    if ((e = configure_one<64, 1>()) != cudaSuccess || (e = configure_one<128, 1>()) != cudaSuccess ||
+        (e = configure_one<256, 1>()) != cudaSuccess || (e = configure_one<64, 2>()) != cudaSuccess ||
+        (e = configure_one<128, 2>()) != cudaSuccess || (e = configure_one<256, 2>()) != cudaSuccess)
         return e;
-    if ((e = cudaFuncSetAttribute(k_gemm_tf32x3<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)GemmShape<128>::kSmem)) != cudaSuccess)
-        return e;
-    return cudaFuncSetAttribute(k_gemm_tf32x3<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)GemmShape<256>::kSmem);
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && nsm > 0)
+        g_nsm_gemm = nsm;
+    return cudaSuccess;
 }
 
 template <typename S>
@@ -411,9 +453,19 @@ int gemm_tf32x3(const TfOperand& A, const TfOperand& B, int M, int N, int K, int
     if (M < 1 || N < 1) return ID_OK;
     if (K < kGBK || K % kGBK != 0 || !ep.d || !status) return ID_EINVAL;
     const int bn = gemm_bn(N);
-    if (bn == 64) return launch_tf32x3<64>(A, B, M, N, K, splits, ep, status, s);
-    if (bn == 128) return launch_tf32x3<128>(A, B, M, N, K, splits, ep, status, s);
-    return launch_tf32x3<256>(A, B, M, N, K, splits, ep, status, s);
+    // Two CTAs per SM (one's epilogue overlapping the other's main loop) when
+    // the grid fills more than one CTA per SM; a grid of at most one wave
+    // keeps one CTA per SM and its deeper pipeline.
+    const int kb = K / kGBK, sp = splits < 1 ? 1 : (splits > kb ? kb : splits);
+    const int64_t ctas = (int64_t)((N + bn - 1) / bn) * ((M + 127) / 128) * sp;
+    if (ctas > g_nsm_gemm) {
+        if (bn == 64) return launch_tf32x3<64, 2>(A, B, M, N, K, splits, ep, status, s);
+        if (bn == 128) return launch_tf32x3<128, 2>(A, B, M, N, K, splits, ep, status, s);
+        return launch_tf32x3<256, 2>(A, B, M, N, K, splits, ep, status, s);
+    }
+    if (bn == 64) return launch_tf32x3<64, 1>(A, B, M, N, K, splits, ep, status, s);
+    if (bn == 128) return launch_tf32x3<128, 1>(A, B, M, N, K, splits, ep, status, s);
+    return launch_tf32x3<256, 1>(A, B, M, N, K, splits, ep, status, s);
 }
 
 cudaError_t dgemm(int ta, int tb, int M, int N, int K, double alpha, const double* A, int64_t lda, const double* B,
@@ -430,6 +482,16 @@ cudaError_t dgemm(int ta, int tb, int M, int N, int K, double alpha, const doubl
 
 cudaError_t gemm_status_to_info(const int* status, DevInfo* info, cudaStream_t s) {
     k_gemm_status<<<1, 1, 0, s>>>(status, info);
+    return cudaGetLastError();
+}
+
+cudaError_t dgemm_batched(int M, int N, int K, double alpha, const double* A, int64_t lda, int64_t sa,
+                          const double* B, int64_t ldb, int64_t sb, double beta, double* C, int64_t ldc, int64_t sc,
+                          int batch, cudaStream_t s) {
+    if (M < 1 || N < 1 || batch < 1) return cudaSuccess;
+    dim3 grid((N + 15) / 16, (M + 15) / 16, batch);
+    if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidValue;
+    k_dgemm16<<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, sa, B, ldb, sb, beta, C, ldc, sc);
     return cudaGetLastError();
 }
 

@@ -66,6 +66,13 @@ cudaError_t gemm_configure();
 cudaError_t dgemm(int ta, int tb, int M, int N, int K, double alpha, const double* A, int64_t lda, const double* B,
                   int64_t ldb, double beta, double* C, int64_t ldc, cudaStream_t s);
 
+// batch row-major FP64 products C_z = alpha A_z B_z + beta C_z with
+// X_z = X + z * sx (no transposes), on 16 x 16 tiles: small products that
+// still spread over every SM.
+cudaError_t dgemm_batched(int M, int N, int K, double alpha, const double* A, int64_t lda, int64_t sa,
+                          const double* B, int64_t ldb, int64_t sb, double beta, double* C, int64_t ldc, int64_t sc,
+                          int batch, cudaStream_t s);
+
 // Row-major FP32-accurate product through the tensor cores, same semantics as
 // dgemm (FP32 data). ws: scratch of gemm_f32_bytes(M, N, K) bytes.
 size_t gemm_f32_bytes(int M, int N, int K);

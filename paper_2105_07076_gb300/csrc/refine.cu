@@ -376,21 +376,13 @@ __global__ void k_zstats(const float* Z, int64_t ldz, int k, int n, const int* f
     if (flag[0]) return;
     const int i = blockIdx.y;
     unsigned long long gt2 = 0;
-    double amax = 0.0;
+    float amax = 0.0f;
     for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < n; l += gridDim.x * blockDim.x) {
-        const double a = fabs((double)Z[(int64_t)i * ldz + l]);
-        gt2 += a > 2.0 ? 1ull : 0ull;
-        amax = a == a ? fmax(amax, a) : INFINITY;
+        const float a = fabsf(Z[(int64_t)i * ldz + l]);
+        gt2 += a > 2.0f ? 1ull : 0ull;
+        amax = a == a ? fmaxf(amax, a) : INFINITY;
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        gt2 += __shfl_xor_sync(0xffffffffu, gt2, o);
-        amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
-    }
-    if (threadIdx.x % kWarp == 0) {
-        if (gt2) atomicAdd(&info->n_gt2, gt2);
-        atomicMax(&info->max_abs_z_bits, (unsigned long long)__double_as_longlong(amax));
-    }
+    zstats_commit(gt2, (double)amax, info);
 }
 
 __global__ void k_reset_stats(DevInfo* info, const int* flag) {
@@ -521,21 +513,14 @@ template <typename T>
 __global__ void k_zstats_t(const T* Z, int64_t ldz, int k, int n, DevInfo* info) {
     const int i = blockIdx.y;
     unsigned long long gt2 = 0;
-    double amax = 0.0;
+    T amax = T(0);
     for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < n; l += gridDim.x * blockDim.x) {
-        const double a = fabs((double)Z[(int64_t)i * ldz + l]);
-        gt2 += a > 2.0 ? 1ull : 0ull;
-        amax = a == a ? fmax(amax, a) : INFINITY;
+        T a = Z[(int64_t)i * ldz + l];
+        a = a < T(0) ? -a : a;
+        gt2 += a > T(2) ? 1ull : 0ull;
+        amax = a == a ? (a > amax ? a : amax) : T(INFINITY);
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        gt2 += __shfl_xor_sync(0xffffffffu, gt2, o);
-        amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
-    }
-    if (threadIdx.x % kWarp == 0) {
-        if (gt2) atomicAdd(&info->n_gt2, gt2);
-        atomicMax(&info->max_abs_z_bits, (unsigned long long)__double_as_longlong(amax));
-    }
+    zstats_commit(gt2, (double)amax, info);
 }
 
 __global__ void k_sampled_finalize(DevInfo* info, const int* flag) {
@@ -594,17 +579,27 @@ cudaError_t tri_inverse(const double* U, int k, double* Uinv_cm, double* tmp, do
     if (cudaMemsetAsync(Uinv_cm, 0, sizeof(double) * (size_t)k * k, s) != cudaSuccess) return cudaErrorUnknown;
     const int nleaf = ceil_div(k, kTriLeaf);
     k_tri_inv_leaf<<<nleaf, kTriLeaf, 0, s>>>(U, k, Uinv_cm);
-    // merge blocks of width w into blocks of width 2w, bottom-up
+    // merge blocks of width w into blocks of width 2w, bottom-up; the merges of
+    // one level with b2 = w run as one batched launch per product (pair p at
+    // o1 = 2 w p; its tmp at tmp + p w^2), a ragged last pair on its own
     for (int w = kTriLeaf; w < k; w *= 2) {
-        for (int o1 = 0; o1 + w < k; o1 += 2 * w) {
-            const int b1 = w, o2 = o1 + w, b2 = min(w, k - o2);
+        const int full = (k / w) / 2;           // pairs with b2 = w
+        const bool ragged = (k / w) % 2 == 1 && k % w != 0;   // a last pair with 0 < b2 < w
+        for (int part = 0; part < 2; ++part) {
+            const int batch = part == 0 ? full : (ragged ? 1 : 0);
+            if (batch == 0) continue;
+            const int o1 = part == 0 ? 0 : 2 * w * full;
+            const int b1 = w, o2 = o1 + w, b2 = part == 0 ? w : k - o2;
+            const int64_t stride = (int64_t)2 * w * (k + 1);   // pair p+1 is 2w rows and 2w columns further
+            double* tp = tmp + (part == 0 ? 0 : (int64_t)full * w * w);
             // tmp (b1 x b2, column-major ld b1) = A^{-1} B, formed as tmp^T = B^T A^{-T}
-            cudaError_t e = dgemm(0, 0, b2, b1, b1, 1.0, U + o1 + (int64_t)o2 * k, k, Uinv_cm + o1 + (int64_t)o1 * k,
-                                  k, 0.0, tmp, b1, s);
+            cudaError_t e = dgemm_batched(b2, b1, b1, 1.0, U + o1 + (int64_t)o2 * k, k, stride,
+                                          Uinv_cm + o1 + (int64_t)o1 * k, k, stride, 0.0, tp, b1, (int64_t)w * w,
+                                          batch, s);
             if (e != cudaSuccess) return e;
             // U^{-1}(o1, o2) = -tmp C^{-1}, formed as its transpose -C^{-T} tmp^T
-            e = dgemm(0, 0, b2, b1, b2, -1.0, Uinv_cm + o2 + (int64_t)o2 * k, k, tmp, b1, 0.0,
-                      Uinv_cm + o1 + (int64_t)o2 * k, k, s);
+            e = dgemm_batched(b2, b1, b2, -1.0, Uinv_cm + o2 + (int64_t)o2 * k, k, stride, tp, b1, (int64_t)w * w,
+                              0.0, Uinv_cm + o1 + (int64_t)o2 * k, k, stride, batch, s);
             if (e != cudaSuccess) return e;
         }
     }
@@ -640,18 +635,32 @@ cudaError_t factor_skeleton(const float* A, int64_t m, int64_t n, int64_t lda, i
 }
 
 // H^T rows of one column block from the split-K slices of R_b^T C:
-// H(l, q) = sum_z P[z][l][q], summed in FP64, rounded to FP32 and split into
-// the operand form (columns k..kp-1 zero).
+// H(l, q) = sum_z P[z][l][q], summed in double-float on the FP32 pipe (TwoSum
+// of the running sum, the rounding errors collected in a second float),
+// rounded to FP32 and split into the operand form (columns k..kp-1 zero).
 __global__ void k_reduce_split(const float* __restrict__ P, int splits, int nb, int k, int kp, float* __restrict__ hi,
                                float* __restrict__ lo) {
     const int64_t total = (int64_t)nb * kp;
     const int64_t slice = (int64_t)nb * k;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         const int l = (int)(e / kp), q = (int)(e % kp);
-        double acc = 0.0;
+        float sh = 0.0f, sl = 0.0f;
         if (q < k)
-            for (int z = 0; z < splits; ++z) acc += (double)P[z * slice + (int64_t)l * k + q];
-        const float x = (float)acc;
+            for (int z0 = 0; z0 < splits; z0 += 8) {
+                float xs[8];   // eight slices' loads in flight before the dependent sums
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    xs[u] = z0 + u < splits ? P[(z0 + u) * slice + (int64_t)l * k + q] : 0.0f;
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const float x = xs[u];
+                    const float t = __fadd_rn(sh, x);
+                    const float bp = __fsub_rn(t, sh);
+                    sl = __fadd_rn(sl, __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bp)), __fsub_rn(x, bp)));
+                    sh = t;
+                }
+            }
+        const float x = __fadd_rn(sh, sl);
         const float h = tf32_hi(x);
         hi[e] = h;
         lo[e] = x - h;
@@ -661,6 +670,26 @@ __global__ void k_reduce_split(const float* __restrict__ P, int splits, int nb, 
 }  // namespace
 
 size_t refine_bytes(int64_t m, int64_t n, int64_t k) { return ref_layout(m, n, k).total; }
+
+// Kernel launches of refine_run for this problem (memsets excluded); the
+// count follows the launch sites of factor_skeleton, tri_inverse and
+// refine_run one for one.
+int64_t refine_launch_count(int64_t m, int64_t n, int64_t k) {
+    int64_t c = 4;   // k_check_j, k_gather, k_gram, k_gram_sum
+    for (int64_t p0 = 0; p0 < k; p0 += kCholB) c += 1 + (k - p0 - kCholB > 0 ? 2 : 0);
+    c += 2;          // the inverse's leaves and the final layout change
+    for (int64_t w = kTriLeaf; w < k; w *= 2) {
+        const bool full = (k / w) / 2 > 0, ragged = (k / w) % 2 == 1 && k % w != 0;
+        c += (full ? 2 : 0) + (ragged ? 2 : 0);
+    }
+    const RefLayout L = ref_layout(m, n, k);
+    c += 4;                                     // the operand splits of C, C^T, U^{-T}, U^{-1}
+    c += 4 * ((n + L.nb - 1) / L.nb);           // per column block: Z_b split, R_b^T, the split-K slices, their sum
+    c += 2 + 4;                                 // Y^T and the Z update; identity, reset, statistics, status
+    return c;
+}
+
+
 
 cudaError_t refine_info_init(DevInfo* dinfo, int k, cudaStream_t s) {
     k_info_init<<<1, 1, 0, s>>>(dinfo, k);
@@ -739,7 +768,7 @@ int refine_run(const float* A, int64_t m, int64_t n, int64_t lda, int k, const i
     rc = gemm_tf32x3(TfOperand{fp(L.Yth), fp(L.Ytl), kp, (int)n}, TfOperand{fp(L.Uh), fp(L.Ul), kp, k}, (int)n, k,
                      kp, 1, e4, gst, s);
     if (rc != ID_OK) return rc;
-    dim3 g2(ceil_div(n, kRThreads) < 1024 ? ceil_div(n, kRThreads) : 1024, k);
+    dim3 g2(ceil_div(n, kRThreads * 8), k);
     k_restore_identity<<<grid_for((int64_t)k * k), kRThreads, 0, s>>>(Z, ldz, J, k, flag);
     k_reset_stats<<<1, 1, 0, s>>>(dinfo, flag);
     k_zstats<<<g2, kRThreads, 0, s>>>(Z, ldz, k, (int)n, flag, dinfo);
@@ -1044,9 +1073,10 @@ int sampled_z_run(const void* Av, int64_t m, int64_t n, int64_t lda, int k, cons
     const int64_t ldzd = sizeof(T) == 8 ? ldz : n;
     if (dgemm(0, 0, k, N, k, 1.0, M64, k, B64, n, 0.0, Zd, ldzd, s) != cudaSuccess) return ID_ECUDA;
     dim3 g2(ceil_div(n, kRThreads) < 1024 ? ceil_div(n, kRThreads) : 1024, k);
+    dim3 g8(ceil_div(n, kRThreads * 8), k);
     if (sizeof(T) == 4) k_z_from64<T><<<g2, kRThreads, 0, s>>>(Z64, k, N, Z, ldz);
     k_identity_at_j<T><<<grid_for((int64_t)k * k), kRThreads, 0, s>>>(Z, ldz, J, k);
-    k_zstats_t<T><<<g2, kRThreads, 0, s>>>(Z, ldz, k, N, dinfo);
+    k_zstats_t<T><<<g8, kRThreads, 0, s>>>(Z, ldz, k, N, dinfo);
     k_sampled_finalize<<<1, 1, 0, s>>>(dinfo, flag);
     trace_end(tr, s);
     return cudaGetLastError() == cudaSuccess ? ID_OK : ID_ECUDA;

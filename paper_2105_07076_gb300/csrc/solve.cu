@@ -187,33 +187,24 @@ __global__ void __launch_bounds__(256) k_scatter_z(const int* __restrict__ perm,
                                                    int k, int n, T* __restrict__ Z, int64_t ldz, int32_t* J,
                                                    DevInfo* info) {
     const int i = blockIdx.y;
-    const int l = blockIdx.x * blockDim.x + threadIdx.x;
     unsigned long long gt2 = 0;
-    double amax = 0.0;
-    if (l < n) {
+    T amax = T(0);   // statistics of the stored values, in their precision
+    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < n; l += gridDim.x * blockDim.x) {
         const int col = perm[l];
-        const double val = l < k ? (l == i ? 1.0 : 0.0) : Tm[(int64_t)i * ldt + (l - k)];
-        Z[(int64_t)i * ldz + col] = (T)val;
-        const double a = fabs(val);
-        gt2 = a > 2.0 ? 1ull : 0ull;
-        amax = a == a ? a : INFINITY;
+        const T val = l < k ? (l == i ? T(1) : T(0)) : (T)Tm[(int64_t)i * ldt + (l - k)];
+        Z[(int64_t)i * ldz + col] = val;
+        const T a = val < T(0) ? -val : val;
+        gt2 += a > T(2) ? 1ull : 0ull;
+        amax = a == a ? (a > amax ? a : amax) : T(INFINITY);
         if (i == 0 && l < k) J[l] = col;
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        gt2 += __shfl_xor_sync(0xffffffffu, gt2, o);
-        amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
-    }
-    if (threadIdx.x % kWarp == 0) {
-        if (gt2) atomicAdd(&info->n_gt2, gt2);
-        atomicMax(&info->max_abs_z_bits, (unsigned long long)__double_as_longlong(amax));
-    }
+    zstats_commit(gt2, (double)amax, info);
 }
 
 template <typename T>
 cudaError_t scatter_z(const int* perm, const double* Tm, int ldt, int k, int n, void* Z, int64_t ldz, int32_t* J,
                       DevInfo* info, cudaStream_t s) {
-    dim3 grid(ceil_div(n, 256), k);
+    dim3 grid(ceil_div(n, 256 * 8) > 0 ? ceil_div(n, 256 * 8) : 1, k);   // 8 columns per thread
     k_scatter_z<T><<<grid, 256, 0, s>>>(perm, Tm, ldt, k, n, static_cast<T*>(Z), ldz, J, info);
     return cudaGetLastError();
 }

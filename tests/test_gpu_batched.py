@@ -148,13 +148,19 @@ def test_batched_nonfinite_and_zero_matrix(gbid):
 
 
 def test_batched_full_workload_4096(gbid):
-    """4096 FP32 problems, m ~ U[32, 256], n ~ U[m, 4m], k ~ U[8, 64], 10% sparse:
-    every problem's identity block and status; oracle checks on a sample; the
-    reconstruction error of every low-rank problem above its Eckart-Young floor."""
+    """4096 FP32 problems, m ~ U[32, 256], n ~ U[m, 4m], k ~ U[8, 64], 10% sparse,
+    every problem checked against the oracle (a forced-pivot oracle ID each, in
+    a pool of worker processes): status, identity block, the greedy replay up
+    to the numerical rank, Z against the oracle's Z for the GPU's pivots, the Z
+    statistics, and the reconstruction error of every low-rank problem above
+    its Eckart-Young floor."""
+    from oracle_jobs import cores, forced_id, oracle_pool
+
     probs = synth.batched_uneven(4096, 4, dtype=torch.float32, device="cuda")
     mats = [p["A"] for p in probs]
     ks = [p["k"] for p in probs]
     Js, Zs, infos, plan = gbid.id_decompose_batched(mats, ks)
+    host = []
     for i, (p, J, Z, info) in enumerate(zip(probs, Js, Zs, infos)):
         assert info["status"] in (gbid.ID_OK, gbid.ID_RANK_DEFICIENT), (i, info)
         k = p["k"]
@@ -165,8 +171,25 @@ def test_batched_full_workload_4096(gbid):
             s = synth.spectrum("exp8m", min(p["m"], p["n"]), m=p["m"])
             # the floor of the FP64 matrix, less the FP32 rounding of the input
             assert err >= synth.tail_bound(s, k) * (1 - 1e-4) - 1e-6, (i, err)
-    for i in range(0, 4096, 512):
-        _check_problem(mats[i], ks[i], Js[i], Zs[i], infos[i], torch.float32)
+        host.append((p["A"].double().cpu().numpy(), k, J.cpu().numpy().astype(np.int64), Z.double().cpu().numpy()))
+    with oracle_pool(cores(), 1) as ex:
+        res = list(ex.map(forced_id, [h[0] for h in host], [h[1] for h in host], [h[2] for h in host], chunksize=32))
+    n_z = 0
+    for i, ((Ah, k, Jg, Zg), o, info) in enumerate(zip(host, res, infos)):
+        m, n = Ah.shape
+        assert info["transposed"] == (m > n)
+        assert len(set(Jg.tolist())) == k
+        assert np.count_nonzero(Zg[:, Jg]) == k
+        r = min(o["rank"], info["rank"])
+        tol = 64 * U32 * math.sqrt(min(m, n))
+        assert np.all(o["short"][:r] <= tol), (i, float(o["short"][:r].max()))
+        if o["rank"] == k and info["status"] == gbid.ID_OK:
+            bar = max(1e-4, 2 * o["cond"] * U32)
+            assert np.linalg.norm(Zg - o["Z"]) / np.linalg.norm(o["Z"]) <= bar, (i, o["cond"])
+            assert info["max_abs_z"] == pytest.approx(np.abs(Zg).max(), rel=1e-12)
+            assert info["n_gt2"] == int(np.count_nonzero(np.abs(Zg) > 2.0))
+            n_z += 1
+    assert n_z >= 4000, n_z   # the rank-deficient (sparse) problems are the only ones without a Z check
 
 
 def _path_batch(dtype, seed):

@@ -335,37 +335,46 @@ def c2_inputs():
     return A, Ar
 
 
-@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
-def test_full_size_4096x8192_k256(gbid, c2_inputs, dtype):
-    """Same launch configuration as the bench; sampled oracle checks."""
+def test_full_size_4096x8192_k256(gbid, c2_inputs):
+    """The bench's workload in its launch configuration, checked completely:
+    FP64 and FP32, every one of the 256 pivots replayed by the oracle's greedy
+    rule and the whole Z against the oracle's Z for the GPU's pivots (both from
+    one forced-pivot oracle pass per dtype, the two passes in parallel)."""
     if gbid.engine == 2:
         pytest.skip("too large for one cluster: the grid kernel, as in the other run")
+    import warnings
+
+    from oracle_jobs import cores, forced_id, oracle_pool
+
     A64, _ = c2_inputs
-    A = A64.to(dtype)
     k = 256
-    J, Z, info = gbid.id_decompose(A, k)
-    assert info["status"] == gbid.ID_OK and info["rank"] == k
-    Ah = A.double().cpu().numpy()
-    Jg = J.cpu().numpy().astype(np.int64)
-    Zg = Z.double().cpu().numpy()
-    assert len(set(Jg.tolist())) == k
-    assert np.array_equal(Zg[:, Jg], np.eye(k))
-    # first 6 pivots replayed by the oracle's exact greedy rule
-    ok, worst = orc.verify_pivots(Ah, Jg[:6], tol_piv(dtype, 4096))
-    assert ok, worst
-    # 24 sampled columns of Z against the oracle's least-squares Z for J_gpu
-    rng = np.random.default_rng(0)
-    rest = np.setdiff1d(np.arange(8192), Jg)
-    cols = rng.choice(rest, 24, replace=False)
-    C = Ah[:, Jg]
-    Zs, *_ = np.linalg.lstsq(C, Ah[:, cols], rcond=None)
-    rel = np.linalg.norm(Zg[:, cols] - Zs) / np.linalg.norm(Zs)
-    assert rel <= TOL_Z[dtype], rel
-    # error between the Eckart-Young floor and a small multiple of it
-    err = np.linalg.norm(Ah - C @ Zg) / np.linalg.norm(Ah)
+    runs = {}
+    for dtype in (torch.float64, torch.float32):
+        A = A64.to(dtype)
+        J, Z, info = gbid.id_decompose(A, k)
+        assert info["status"] == gbid.ID_OK and info["rank"] == k, info
+        runs[dtype] = (A.double().cpu().numpy(), J.cpu().numpy().astype(np.int64), Z.double().cpu().numpy(), info)
+    with oracle_pool(2, max(1, cores() // 2)) as ex:
+        futs = {dt: ex.submit(forced_id, r[0], k, r[1]) for dt, r in runs.items()}
+        res = {dt: f.result() for dt, f in futs.items()}
     tail = synth.tail_bound(synth.spectrum("exp64", 4096), k)
-    assert tail * (1 - 1e-6) <= err <= 3.0 * tail, (err, tail)
-    assert info["err_est"] == pytest.approx(err, rel=1e-3)
+    for dtype, (Ah, Jg, Zg, info) in runs.items():
+        o = res[dtype]
+        tp = tol_piv(dtype, 4096)
+        assert len(set(Jg.tolist())) == k
+        assert np.array_equal(Zg[:, Jg], np.eye(k))
+        assert o["rank"] == k
+        assert np.all(o["short"] <= tp), (dtype, int(np.argmax(o["short"])), float(o["short"].max()))
+        rel = np.linalg.norm(Zg - o["Z"]) / np.linalg.norm(o["Z"])
+        assert rel <= TOL_Z[dtype], (dtype, rel)
+        err = orc.rel_error(Ah, Jg, Zg)
+        assert tail * (1 - 1e-6) <= err <= 3.0 * tail, (err, tail)
+        assert info["err_est"] == pytest.approx(err, rel=1e-3)
+        if dtype == torch.float32:
+            # steps the FP32 margin (64 u_32 sqrt(m)) accepts that the 1e-6 bar would not
+            n_loose = int(np.count_nonzero(o["short"] > 1e-6))
+            warnings.warn(f"FP32 4096x8192 k=256: {n_loose} of {k} pivot steps fall short of the greedy maximum by "
+                          f"more than 1e-6 (largest {o['short'].max():.2e}, FP32 margin {tp:.2e})")
 
 
 def test_full_size_row_id_of_the_transpose(gbid, c2_inputs):

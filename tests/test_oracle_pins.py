@@ -268,6 +268,22 @@ def test_verify_pivots_accepts_own_and_rejects_planted_swap():
     assert not ok2 and worst2[3] > 1e-6
 
 
+def test_forced_pivot_shortfall_equals_the_replay():
+    """cpqr's largest residual norm per step: equal to the winner's on a free
+    run, and with forced pivots 1 - nu / top is the replay's shortfall (the
+    planted swap shows from the swapped step on; an independent replay computes it)."""
+    s = synth.spectrum("pow2_half", 100)
+    A = _lowrank_np(100, 200, s, 12)
+    J, _, info = orc.interp_decomp(A, 15)
+    assert np.array_equal(info["top"], info["nu"])
+    bad = J.copy()
+    bad[[3, 4]] = bad[[4, 3]]
+    _, _, ib = orc.interp_decomp(A, 15, pivots=bad)
+    _, worst = orc.verify_pivots(A, bad, 1e-6)
+    assert np.allclose(1.0 - ib["nu"] / ib["top"], worst, rtol=0, atol=1e-13)
+    assert worst[3] > 1e-6 and np.all(worst[:3] <= 1e-12)
+
+
 def test_forced_pivots_reproduce_free_run():
     rng = np.random.default_rng(13)
     A = rng.standard_normal((30, 45))
