@@ -1,32 +1,36 @@
-"""Throughput of the GB300 interpolative decomposition on the 4096 x 8192, k = 256 workload.
+"""Throughput of the GB300 interpolative decomposition on its headline workload.
 
-One step = one rank-256 ID (column-pivoted QR stopped after 256 pivots,
-back substitution, Z assembly) of a 4096 x 8192 matrix A = U diag(s) V^T with
-Haar U, V and s_i = exp(-i/64). The headline is the FP64 ID; the FP32 ID of
-the same matrix is measured in the same run and reported beside it.
+One step = one randomized rank-512 ID of a 16384 x 32768 FP32 matrix
+A = U diag(s) V^T (Haar U, V, s_i = (1+i)^-1.5): the Gaussian sketch
+Y = Omega A (Omega 522 x 16384, N(0,1) rounded to BF16) on the tensor cores,
+k = 512 steps of column-pivoted QR of Y (FP32 matrix, FP64 norm downdate,
+the compact-WY update on the tensor cores), the sketch's T, and one
+least-squares refinement of Z against A (3xTF32 products on the tensor
+cores). Inputs stay resident in HBM; A (2.15 GB) exceeds L2, so no flush is
+needed between steps. The line carries the roofline of the dominant kernel
+in SURVEY-convention units, the end-to-end rate with host buffers, the
+oracle's rate on a bounded sample (cpu_baseline), and, under "compare", the
+plain FP64 GPU ID of the same matrix and the FP64 batched launch beside the
+mixed-precision and FP32 batched forms at their reconstruction errors.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gbid|reference]
 
-The line also carries, under "randomized", the randomized ID of a 16384 x
-32768 FP32 matrix (s_i = (1+i)^-1.5, k = 512): BF16 Gaussian sketch on the
-tensor cores, CPQR of the 522 x 32768 sketch, the sketch's T in FP32, one
-least-squares refinement of Z against A; and under "batched", 4096 uneven
-FP32 IDs (m ~ U[32, 256], n ~ U[m, 4m], k ~ U[8, 64]) in one persistent
-launch, its tile shape picked by the library's tuner; and under "latency", back-to-back 200 x 400 FP64
-IDs at k = 20; and under "differentiable", 256 IDs of 512 x 1024 at k = 64
-forward (batched) and backward; and under "sampled", the paper's
-column-sampling Optim RID of the headline matrices (p = 307 sampled columns),
-under "listing", the paper's listing outputs of the same matrices (Z from
-the normal equations, approx = C @ Z), under "two_sided", the two-sided ID
-of the same matrices and the row ID of the 8192 x 4096 transpose, and under
-"sparse", the ID of a 4096 x 8192 CSR matrix with 1% power-law nonzeros
-(--only randomized / batched / latency / differentiable runs that workload
-alone; --only id skips them; --only sampled keeps the ID and the sampled RID).
+Side workloads in the same line: "deterministic" (the 4096 x 8192, k = 256 ID
+in FP64 and FP32, s_i = exp(-i/64)), "batched" (4096 uneven FP32 IDs in one
+persistent launch, tile shape picked by the library's tuner), "latency"
+(back-to-back 200 x 400 FP64 IDs, k = 20), "differentiable" (256 IDs of
+512 x 1024 at k = 64, forward and backward), "sampled" (the paper's
+column-sampling Optim RID of the 4096 x 8192 matrices), "listing" (Z from the
+normal equations, approx = C @ Z), "two_sided" and "sparse" (a 4096 x 8192
+CSR matrix). --only randomized runs the headline alone; --only id the
+headline and the deterministic block; --only batched / latency /
+differentiable / compare one side workload alone.
 
 Multi-GPU (N > 1, launched by torchrun): every rank decomposes its own copy
 (independent replicas, no collective on the data path); value = total IDs/s.
---impl reference times the FP64 CPU oracle on a bounded sample of the same
-workload (rank 0 only) and prints the same JSON line with "impl": "reference".
+--impl reference times the FP64 CPU oracle on a bounded sample of the
+headline workload (rank 0 only) and prints the same JSON line with
+"impl": "reference".
 """
 from __future__ import annotations
 
@@ -45,9 +49,12 @@ sys.path.insert(0, ROOT)
 
 M, N, K_RANK = 4096, 8192, 256
 WORKLOAD = "id_4096x8192_k256"
+# the headline: the randomized ID of a 16384 x 32768 FP32 matrix, k = 512, l = k + 10
+RM, RN, RK, RL = 16384, 32768, 512, 522
+RWORKLOAD = f"rid_{RM}x{RN}_k{RK}_l{RL}"
+RID_CPU_COLS = 1024            # columns of A in one oracle sample of the headline workload
 METRIC = "IDs/s and effective TFLOP/s at stated rel. Frobenius error vs FP64 plain ID"
 UNIT = "IDs/s"
-REF_SAMPLE_STEPS = 4           # pivot steps per --impl reference step
 BATCHED_CPU_SAMPLE = 1024      # problems of the uneven batch the oracle decomposes for its CPU baseline
 DIFF_CPU_SAMPLE = 64           # forward + gradient problems of the differentiable workload for its CPU baseline
 
@@ -280,34 +287,28 @@ def time_oracle_many(mats, ks, workers, grads=None):
     return max(secs)
 
 
-def oracle_ids_per_s(sample_seconds, steps):
-    """Full-ID rate extrapolated from `steps` pivot steps by the CPQR flop count."""
-    scale = flops_cpqr(M, N, K_RANK) / flops_cpqr(M, N, steps)
-    return 1.0 / (sample_seconds * scale)
-
-
 def run_reference(args):
+    """The oracle, as it stands, on the host cores: each step is one oracle
+    randomized ID of the headline matrix's first RID_CPU_COLS columns (same
+    Omega and k), and the rate is scaled to the whole matrix by the column ratio.
+    Rank 0 alone runs and prints; the other ranks exit without work."""
     world, rank, local = dist_setup()
     if rank != 0:
         return 0
-    import numpy as np
     import torch
 
     dev = "cuda" if torch.cuda.is_available() else "cpu"
-    A = make_input(dev, torch.float64).cpu().numpy()
-    total = args.warmup + args.steps
-    secs = time_oracle(A, REF_SAMPLE_STEPS, total)[args.warmup:]
+    A, om = rid_inputs(dev)
+    secs = rid_oracle_seconds(A, om, args.warmup + args.steps)[args.warmup:]
     per = statistics.mean(secs)
-    value = oracle_ids_per_s(per, REF_SAMPLE_STEPS)
-    sample = (f"first {REF_SAMPLE_STEPS} of {K_RANK} pivot steps of the FP64 oracle per step, "
-              f"extrapolated to a full ID by the CPQR flop count")
+    value = rid_oracle_rate(per)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3 * flops_cpqr(M, N, K_RANK) /
-        flops_cpqr(M, N, REF_SAMPLE_STEPS), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "m": M, "n": N, "k": K_RANK, "spectrum": "s_i = exp(-i/64)"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": rid_config(max(world, args.gpus)),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": RID_SAMPLE + f"; ms_per_step is one sample ({per:.2f} s)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -380,14 +381,27 @@ def e2e_rate(gbid, A, steps):
     return 1000.0 / ms, h2d, d2h
 
 
-# Randomized ID workload reported beside the headline: 16384 x 32768 FP32,
-# s_i = (1+i)^-1.5, k = 512, Omega 522 x 16384 (N(0,1) rounded to BF16).
-RM, RN, RK, RL = 16384, 32768, 512, 522
 
 
-def randomized_block(gbid, dev, steps):
-    """ms per randomized ID (sketch, CPQR of Y, solve, Z), its kernels, and the
-    error on A. A (2.1 GB) exceeds L2, so no flush is needed between IDs."""
+def rid_config(world):
+    return {"workload": RWORKLOAD, "m": RM, "n": RN, "k": RK, "l": RL, "spectrum": "s_i = (1+i)^-1.5",
+            "inputs": "A = U diag(s) V^T with Haar U, V (seed 3), FP32; Omega N(0,1) rounded to BF16 (seed 33)",
+            "form": "randomized ID: BF16 sketch on the tensor cores, FP32 CPQR of the sketch with FP64 norms and "
+                    "tensor-core WY updates, one least-squares refinement of Z against A (3xTF32 tensor-core products)",
+            "parallelism": f"replicas x{world}",
+            "l2": "no flush: A (2.15 GB) exceeds L2 (129 MB) and is read in full every step"}
+
+
+def rid_flops():
+    """The flop convention of one randomized ID (sketch, CPQR of Y, solve, refinement)."""
+    f_sketch = 2.0 * RL * RM * RN
+    f_cpqr = flops_cpqr(RL, RN, RK)
+    f_solve = flops_solve(RN, RK)
+    f_refine = 2.0 * RM * RK * (RN - RK) + 4.0 * RM * RK * RK + 2.0 * RK * RK * (RN - RK)
+    return {"sketch": f_sketch, "cpqr": f_cpqr, "solve": f_solve, "refine": f_refine}
+
+
+def rid_inputs(dev):
     import torch
 
     import synth
@@ -395,53 +409,179 @@ def randomized_block(gbid, dev, steps):
     A = synth.lowrank(RM, RN, synth.spectrum("poly1.5", RM), 3, device=dev, dtype=torch.float32,
                       gen_dtype=torch.float32)
     om = synth.gaussian_sketch_bf16(RL, RM, seed=33, device=dev)
+    return A, om
+
+
+def rid_time(gbid, A, om, steps, warmup, world, local):
+    """Per-step device times (ms) of the randomized ID on resident inputs, the
+    per-stage kernel times of the library's trace, the clocks during the timed
+    region, and the last step's J, Z and status."""
+    import torch
+    import torch.distributed as dist
+
+    dev = A.device
     ws = gbid.rid_workspace(RM, RN, RL, RK, device=dev)
     J = torch.empty(RK, dtype=torch.int32, device=dev)
     Z = torch.empty(RK, RN, dtype=torch.float32, device=dev)
-    for _ in range(3):
+    for _ in range(warmup):
         gbid.id_decompose_randomized(A, om, RK, workspace=ws, out=(J, Z), sync=False)
     torch.cuda.synchronize()
-    gbid.trace_enable(8 * steps + 8)
+    if world > 1:
+        dist.barrier()
+    gbid.trace_enable(64 * steps + 64)
     s = torch.cuda.current_stream()
     ev = []
-    for _ in range(steps):
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(s)
-        gbid.id_decompose_randomized(A, om, RK, workspace=ws, out=(J, Z), sync=False)
-        e1.record(s)
-        ev.append((e0, e1))
-    torch.cuda.synchronize()
-    ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    with ClockSampler(local) as cs:
+        for _ in range(steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            gbid.id_decompose_randomized(A, om, RK, workspace=ws, out=(J, Z), sync=False)
+            e1.record(s)
+            ev.append((e0, e1))
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = [a.elapsed_time(b) for a, b in ev]
     tr = gbid.trace_read()
     gbid.trace_enable(0)
-    info = gbid.read_info(ws)
     per = {k: v[0] / v[1] for k, v in tr.items() if v[1]}
-    with torch.no_grad():
-        torch.backends.cuda.matmul.allow_tf32 = False
-        C = A[:, J.long()]
-        num = den = 0.0
-        for c0 in range(0, RN, 4096):          # FP32 products, FP64 sums, 4096 columns at a time
-            Ac = A[:, c0:c0 + 4096]
-            num += torch.sum((Ac - C @ Z[:, c0:c0 + 4096]).double() ** 2).item()
-            den += torch.sum(Ac.double() ** 2).item()
-        err = math.sqrt(num / den)
-    tail = synth.tail_bound(synth.spectrum("poly1.5", RM), RK)
-    sk = per.get("sketch", float("nan"))
-    sk_tflops = 2.0 * RL * RM * RN / (sk * 1e-3) / 1e12
+    return ms, per, cs.summary(), gbid.read_info(ws), J, Z
+
+
+def rid_error(A, J, Z):
+    """||A - A[:, J] Z||_F / ||A||_F in FP64 sums, 4096 columns at a time."""
+    import torch
+
+    C = A[:, J.long()].double()
+    num = den = 0.0
+    for c0 in range(0, A.shape[1], 4096):
+        Ac = A[:, c0:c0 + 4096].double()
+        num += torch.sum((Ac - C @ Z[:, c0:c0 + 4096].double()) ** 2).item()
+        den += torch.sum(Ac ** 2).item()
+    return math.sqrt(num / den)
+
+
+def rid_rooflines(per, hbm_peak, peak_src):
+    """Per-stage rooflines in the SURVEY's units: the CPQR of the sketch against
+    HBM (its algorithmic bytes, the trailing block read once per pivot step),
+    the sketch and the refinement against the tensor peak of their input type."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             bf16 = float(json.load(f)["bf16_tflops"])
-        src = "measured burst bf16 (MEASURED_PEAKS.json)"
+        bsrc = "of measured: MEASURED_PEAKS.json bf16_tflops (burst)"
     except Exception:
-        bf16, src = 1900.0, "fallback"
-    del A, C
-    return {"workload": f"rid_{RM}x{RN}_k{RK}_l{RL}", "ms_per_step": ms, "value": 1000.0 / ms, "unit": UNIT,
-            "kernel_ms": per, "rel_err": err, "tail_bound": tail, "status": info["status_name"],
-            "dtype": "bf16 sketch (FP32 accumulate), f32 CPQR, f32 solve of the sketch's T, one least-squares refinement "
-                     "(double-float Gram, f64 Cholesky, f32-accurate GEMMs)",
-            "sketch_roofline": {"bound": "tensor", "achieved": sk_tflops, "peak": bf16, "unit": "TFLOP/s",
-                                "frac": sk_tflops / bf16, "peak_source": src}}
+        bf16, bsrc = 1900.0, "of fallback"
+    tf32 = bf16 * 1.1 / 2.25          # nominal dense TF32 / BF16 ratio
+    fl = rid_flops()
+    out = {}
+    cp = per.get("cpqr")
+    if cp:
+        b = bytes_cpqr(RL, RN, RK, 4)
+        ach = b / (cp * 1e-3) / 1e9
+        out["cpqr"] = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
+                       "traffic": None, "kernel": "k_cpqr<float> per panel + tensor-core WY updates (522 x 32768 sketch)",
+                       "kernel_ms": cp, "algorithmic_bytes": b,
+                       "peak_source": f"of {peak_src}: MEASURED_PEAKS.json hbm_gbs" if peak_src == "measured"
+                       else "of fallback",
+                       "note": "the 68 MB sketch stays in L2; its trailing reads are counted against HBM"}
+    sk = per.get("sketch")
+    if sk:
+        ach = fl["sketch"] / (sk * 1e-3) / 1e12
+        out["sketch"] = {"bound": "tensor", "achieved": ach, "peak": bf16, "unit": "TFLOP/s", "frac": ach / bf16,
+                         "traffic": None, "kernel": "k_sketch (BF16 tcgen05)", "kernel_ms": sk, "peak_source": bsrc}
+    rf = per.get("refine")
+    if rf:
+        executed = 3.0 * 2.0 * 2.0 * RM * RK * RN      # C Z and C^T R, three TF32 products each
+        ach = executed / (rf * 1e-3) / 1e12
+        out["refine"] = {"bound": "tensor", "achieved": ach, "peak": tf32, "unit": "TFLOP/s", "frac": ach / tf32,
+                         "traffic": None, "kernel": "k_gemm_tf32x3 (3xTF32 tcgen05) + skeleton factorisation",
+                         "kernel_ms": rf, "convention_tflops": fl["refine"] / (rf * 1e-3) / 1e12,
+                         "peak_source": bsrc + " x the nominal TF32/BF16 ratio 1.1/2.25",
+                         "note": "achieved counts the executed 3xTF32 products of the residual and C^T R"}
+    dom = max(out, key=lambda k: out[k]["kernel_ms"]) if out else None
+    return out, dom
+
+
+def rid_e2e(gbid, A, om, steps):
+    """IDs/s through the public call with host buffers: every step copies A and
+    Omega from pinned host memory, runs the randomized ID and copies J and Z back."""
+    import torch
+
+    Ah = A.cpu().pin_memory()
+    Oh = om.cpu().pin_memory()
+    Ad = torch.empty_like(A)
+    Od = torch.empty_like(om)
+    ws = gbid.rid_workspace(RM, RN, RL, RK, device=A.device)
+    J = torch.empty(RK, dtype=torch.int32, device=A.device)
+    Z = torch.empty(RK, RN, dtype=torch.float32, device=A.device)
+    Jh = torch.empty(RK, dtype=torch.int32, pin_memory=True)
+    Zh = torch.empty(RK, RN, dtype=torch.float32, pin_memory=True)
+
+    def step():
+        Ad.copy_(Ah, non_blocking=True)
+        Od.copy_(Oh, non_blocking=True)
+        gbid.id_decompose_randomized(Ad, Od, RK, workspace=ws, out=(J, Z), sync=False)
+        Jh.copy_(J, non_blocking=True)
+        Zh.copy_(Z, non_blocking=True)
+
+    step()
+    torch.cuda.synchronize()
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(steps):
+        step()
+    e1.record(s)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    h2d = Ah.numel() * 4 + Oh.numel() * 2
+    d2h = Jh.numel() * 4 + Zh.numel() * 4
+    del Ah, Oh, Ad, Od, ws
+    return 1000.0 / ms, h2d, d2h
+
+
+RID_ORACLE_SNIPPET = r"""
+import io, sys, time, json
+import numpy as np
+sys.path.insert(0, sys.argv[1])
+from oracle import id_oracle as orc
+d = np.load(io.BytesIO(sys.stdin.buffer.read()))
+k, reps = int(sys.argv[2]), int(sys.argv[3])
+out = []
+for _ in range(reps):
+    t0 = time.perf_counter()
+    orc.randomized_interp_decomp(d["A"], d["om"], k)
+    out.append(time.perf_counter() - t0)
+print(json.dumps(out))
+"""
+
+
+def rid_oracle_seconds(A, om, reps):
+    """Seconds per oracle randomized ID (sketch, CPQR of Y, refinement, FP64) of the
+    first RID_CPU_COLS columns of A with the same Omega and k, single-threaded, in a
+    fresh process (the sample goes through its stdin)."""
+    import numpy as np
+
+    Ah = A[:, :RID_CPU_COLS].double().cpu().numpy()
+    Oh = om.double().cpu().numpy()
+    r = subprocess.run([sys.executable, "-c", RID_ORACLE_SNIPPET, ROOT, str(RK), str(reps)],
+                       input=_npy_bytes(np.savez, A=Ah, om=Oh), capture_output=True,
+                       env=dict(os.environ, **ONE_THREAD), timeout=3600)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr.decode(errors="replace")[-2000:])
+    return json.loads(r.stdout.decode().strip().splitlines()[-1])
+
+
+def rid_oracle_rate(secs):
+    """IDs/s of the whole workload from the sample: every stage's work grows
+    linearly with the number of columns (the sketch, the refinement, and the
+    CPQR of Y for n >> k), so one ID takes RN / RID_CPU_COLS samples' time."""
+    return RID_CPU_COLS / (RN * secs)
+
+
+RID_SAMPLE = (f"oracle randomized ID (FP64, numpy, one thread) of the first {RID_CPU_COLS} of the {RN} columns of the "
+              f"same A with the same Omega and k = {RK}, scaled to all columns by the column ratio")
 
 
 def sampled_block(gbid, dev, steps, mats):
@@ -826,12 +966,12 @@ def batched_block(gbid, dev, steps, cpu_sample=0):
 
 
 def compare_block(gbid, dev, steps):
-    """The mixed-precision and batched forms beside the plain FP64 ID at the
-    same reconstruction error: the randomized ID of the 16384 x 32768 FP32
-    matrix against the FP64 ID of the same matrix (promoted), and the FP32
-    batched launch against the FP64 batched launch of the same 4096 problems.
-    Only with --only compare: the FP64 ID at 16384 rows takes the one-CTA-per-SM
-    configuration of the CPQR kernel."""
+    """The mixed-precision and batched forms beside the plain FP64 GPU ID at
+    their reconstruction errors: the randomized ID of the 16384 x 32768 FP32
+    matrix against the deterministic FP64 ID of the same matrix (promoted; the
+    FP64 CPQR at 16384 rows runs k_cpqr's one-CTA-per-SM configuration, which
+    the tall-matrix parity tests cover), and the FP32 batched launch against the
+    FP64 batched launch of the same 4096 problems."""
     import torch
 
     import synth
@@ -849,18 +989,22 @@ def compare_block(gbid, dev, steps):
         return e0.elapsed_time(e1) / reps, out
 
     out = {"workload": "same-error comparisons"}
-    A = synth.lowrank(RM, RN, synth.spectrum("poly1.5", RM), 3, device=dev, dtype=torch.float32,
-                      gen_dtype=torch.float32)
-    om = synth.gaussian_sketch_bf16(RL, RM, seed=33, device=dev)
-    ms_r, (J, Z, _) = timed(lambda: gbid.id_decompose_randomized(A, om, RK, sync=False), max(2, steps))
-    err_r = rel_error_gpu(A, J, Z)
+    A, om = rid_inputs(dev)
+    ws = gbid.rid_workspace(RM, RN, RL, RK, device=dev)
+    ms_r, (J, Z, _) = timed(lambda: gbid.id_decompose_randomized(A, om, RK, workspace=ws, sync=False), max(2, steps))
+    err_r = rid_error(A, J, Z)
+    del ws, J, Z
     A64 = A.double()
-    del J, Z
-    ms_d, (J, Z, info) = timed(lambda: gbid.id_decompose(A64, RK, sync=False), 2)
-    err_d = rel_error_gpu(A64, J, Z)
+    ws64 = gbid.Workspace.for_problem(torch.float64, RM, RN, RK, device=dev)
+    ms_d, (J, Z, _) = timed(lambda: gbid.id_decompose(A64, RK, workspace=ws64, sync=False), 2)
+    info = gbid.read_info(ws64)
+    err_d = rid_error(A64, J, Z)
     out["randomized_vs_fp64"] = {"matrix": f"{RM}x{RN} k={RK}", "randomized_ms": ms_r, "randomized_rel_err": err_r,
-                                 "fp64_ms": ms_d, "fp64_rel_err": err_d, "speedup": ms_d / ms_r}
-    del A, A64, J, Z
+                                 "randomized_ids_per_s": 1000.0 / ms_r, "fp64_ms": ms_d, "fp64_rel_err": err_d,
+                                 "fp64_ids_per_s": 1000.0 / ms_d, "fp64_status": info["status_name"],
+                                 "speedup": ms_d / ms_r, "err_ratio": err_r / err_d,
+                                 "tail_bound": synth.tail_bound(synth.spectrum("poly1.5", RM), RK)}
+    del A, A64, J, Z, ws64
     torch.cuda.empty_cache()
     probs = synth.batched_uneven(BATCH_COUNT, 4, dtype=torch.float32, device=dev)
     res = {}
@@ -897,6 +1041,62 @@ def guarded(name, fn, *a):
         return {"workload": name, "error": repr(exc)[:500]}
 
 
+def deterministic_block(gbid, dev, args, world, hbm_peak, peak_src, cpu_ok):
+    """The deterministic ID of the 4096 x 8192 matrix (s_i = exp(-i/64), k = 256)
+    in FP64 and FP32: per-step device times with L2 flushed between steps, the
+    error, rooflines of k_cpqr in the SURVEY's units (algorithmic bytes against
+    HBM; FP64 also the flop convention and the executed FP64 operations against
+    the FP64 peak), the end-to-end rate through the host-buffer entry point and
+    one complete oracle ID of the FP64 matrix on one core. Returns (block, matrices)."""
+    import torch
+
+    flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)   # 256 MB > L2
+    res = {}
+    mats = {}
+    for name, dt in (("f64", torch.float64), ("f32", torch.float32)):
+        A = make_input(dev, dt)
+        ms, tr, info, J, Z = time_gpu(gbid, A, args.steps, args.warmup, flush)
+        mean_ms = max_over_ranks(statistics.mean(ms), world, dev)
+        cp_ms, cp_n = tr.get("cpqr", (0.0, 0))
+        cp = cp_ms / cp_n if cp_n else float("nan")
+        s = A.element_size()
+        b = bytes_cpqr(M, N, K_RANK, s)
+        ach = b / (cp * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
+                "traffic": NCU_TRAFFIC[name], "kernel": f"k_cpqr<{'double' if s == 8 else 'float'}>", "kernel_ms": cp,
+                "algorithmic_bytes": b,
+                "peak_source": "of measured: MEASURED_PEAKS.json hbm_gbs" if peak_src == "measured" else "of fallback"}
+        if s == 8:
+            conv = flops_cpqr(M, N, K_RANK) / (cp * 1e-3) / 1e12
+            exe = fp64_flops_executed(M, N, K_RANK) / (cp * 1e-3) / 1e12
+            roof["fp64"] = {"bound": "alu", "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                            "convention_achieved": conv, "convention_frac": conv / FP64_PEAK_TFLOPS,
+                            "executed_achieved": exe, "executed_frac": exe / FP64_PEAK_TFLOPS,
+                            "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (a DFMA probe: 1.196)",
+                            "note": "the convention counts 4 (m-j)(n-j) per step; the left-looking form executes fewer"}
+        eff = (flops_cpqr(M, N, K_RANK) + flops_solve(N, K_RANK)) / (mean_ms * 1e-3) / 1e12
+        res[name] = {"ms_per_step": mean_ms, "value": aggregate_rate(mean_ms, world), "unit": UNIT, "eff_tflops": eff,
+                     "rel_err": rel_error_gpu(A, J, Z), "status": info["status_name"], "roofline": roof,
+                     "launches_per_step": gbid.launch_count(dt, M, N, K_RANK)}
+        mats[name] = A
+    del flush
+    e2e_v, h2d, d2h = e2e_rate(gbid, mats["f64"], max(2, min(args.steps, 5)))
+    res["f64"]["e2e"] = {"value": aggregate_rate(max_over_ranks(1000.0 / e2e_v, world, dev), world), "unit": UNIT,
+                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+    res["f32"]["speedup_vs_f64"] = res["f32"]["value"] / res["f64"]["value"]
+    res["tail_bound"] = __import__("synth").tail_bound(__import__("synth").spectrum("exp64", M), K_RANK)
+    res["workload"] = WORKLOAD
+    if cpu_ok:
+        def one_oracle_id():
+            secs = time_oracle(mats["f64"].cpu().numpy(), K_RANK, 1, full=True)
+            return {"value": 1.0 / secs[0], "unit": UNIT, "cores": 1, "kind": "oracle",
+                    "sample": f"one complete rank-{K_RANK} ID of the same 4096 x 8192 FP64 matrix by the oracle "
+                              f"({secs[0]:.1f} s, numpy, one thread)"}
+
+        res["cpu_baseline"] = guarded("cpu_baseline", one_oracle_id)
+    return res, mats
+
+
 def run_gbid(args):
     import torch
     import torch.distributed as dist
@@ -910,119 +1110,92 @@ def run_gbid(args):
 
     ge.build()
     import paper_2105_07076_gb300 as gbid
+    import synth
 
     dev = torch.device("cuda", local)
-    if args.only in ("randomized", "batched", "latency", "differentiable", "compare"):  # one side workload alone
+    cpu_ok = rank == 0 and world == 1 and not args.no_cpu_baseline
+    if args.only in ("batched", "latency", "differentiable", "compare"):  # one side workload alone
         if args.only == "compare":
             side = compare_block(gbid, dev, max(3, min(args.steps, 10)))
-        elif args.only == "randomized":
-            side = randomized_block(gbid, dev, max(2, min(args.steps, 5)))
         elif args.only == "latency":
             side = latency_block(gbid, dev, args.steps)
         elif args.only == "differentiable":
-            side = differentiable_block(gbid, dev, args.steps,
-                                        DIFF_CPU_SAMPLE if rank == 0 and world == 1 and not args.no_cpu_baseline else 0)
+            side = differentiable_block(gbid, dev, args.steps, DIFF_CPU_SAMPLE if cpu_ok else 0)
         else:
-            side = batched_block(gbid, dev, max(3, min(args.steps, 10)),
-                                 BATCHED_CPU_SAMPLE if rank == 0 and world == 1 and not args.no_cpu_baseline else 0)
+            side = batched_block(gbid, dev, max(3, min(args.steps, 10)), BATCHED_CPU_SAMPLE if cpu_ok else 0)
         if rank == 0:
             print(json.dumps(dict(side, n_gpus=world, steps=args.steps, warmup=args.warmup)), flush=True)
         return 0
     hbm_peak, peak_src = load_peaks()
-    flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)   # 256 MB > L2
-    results = {}
-    clocks = None
-    for name, dt in (("f64", torch.float64), ("f32", torch.float32)):
-        A = make_input(dev, dt)
-        if world > 1:
-            dist.barrier()
-        torch.cuda.synchronize()
-        if name == "f64":
-            with ClockSampler(local) as cs:
-                ms, tr, info, J, Z = time_gpu(gbid, A, args.steps, args.warmup, flush)
-            clocks = cs.summary()
-        else:
-            ms, tr, info, J, Z = time_gpu(gbid, A, args.steps, args.warmup, flush)
-        torch.cuda.synchronize()
-        if world > 1:
-            dist.barrier()
-        mean_ms = max_over_ranks(statistics.mean(ms), world, dev)
-        err = rel_error_gpu(A, J, Z)
-        cp_ms, cp_n = tr.get("cpqr", (0.0, 0))
-        cp_avg = cp_ms / cp_n if cp_n else float("nan")
-        s = A.element_size()
-        if name == "f64":
-            achieved = fp64_flops_executed(M, N, K_RANK) / (cp_avg * 1e-3) / 1e12
-            roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": achieved / FP64_PEAK_TFLOPS, "traffic": NCU_TRAFFIC["f64"], "kernel": "k_cpqr<double>",
-                    "kernel_ms": cp_avg,
-                    "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (DFMA probe: 1.196)"}
-        else:
-            achieved = bytes_cpqr(M, N, K_RANK, s) / (cp_avg * 1e-3) / 1e9
-            roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                    "frac": achieved / hbm_peak, "traffic": NCU_TRAFFIC["f32"], "kernel": "k_cpqr<float>",
-                    "kernel_ms": cp_avg,
-                    "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured"
-                    else "fallback"}
-        eff = (flops_cpqr(M, N, K_RANK) + flops_solve(N, K_RANK)) / (mean_ms * 1e-3) / 1e12
-        results[name] = {"ms_per_step": mean_ms, "value": aggregate_rate(mean_ms, world), "eff_tflops": eff,
-                         "rel_err": err, "status": info["status_name"], "roofline": roof,
-                         "solve_ms": (tr.get("solve", (0.0, 1))[0] / max(tr.get("solve", (0, 1))[1], 1)),
-                         "launches_per_step": gbid.launch_count(dt, M, N, K_RANK), "A": A}
-    e2e_v, h2d, d2h = e2e_rate(gbid, results["f64"]["A"], max(2, min(args.steps, 5)))
-    e2e_v = aggregate_rate(max_over_ranks(1000.0 / e2e_v, world, dev), world)
 
-    # the side workloads: a failure in one is reported in the line, not fatal to the headline numbers above
-    mats = {n: r["A"] for n, r in results.items()}
+    # ---- the headline: the randomized ID of the 16384 x 32768 matrix
+    A, om = rid_inputs(dev)
+    ms, per, clocks, info, J, Z = rid_time(gbid, A, om, args.steps, args.warmup, world, local)
+    mean_ms = max_over_ranks(statistics.mean(ms), world, dev)
+    err = rid_error(A, J, Z)
+    kernels, dom = rid_rooflines(per, hbm_peak, peak_src)
+    fl = rid_flops()
+    eff = sum(fl.values()) / (mean_ms * 1e-3) / 1e12
+    e2e_v, h2d, d2h = rid_e2e(gbid, A, om, max(2, min(args.steps, 5)))
+    e2e_v = aggregate_rate(max_over_ranks(1000.0 / e2e_v, world, dev), world)
+    cpu = None
+    if cpu_ok:
+        def oracle_sample():
+            secs = rid_oracle_seconds(A, om, 2)
+            return {"value": rid_oracle_rate(statistics.mean(secs)), "unit": UNIT, "cores": 1, "kind": "oracle",
+                    "sample": RID_SAMPLE + f" ({statistics.mean(secs):.1f} s per sample, 2 samples)"}
+
+        cpu = guarded("cpu_baseline", oracle_sample)
+    tail = synth.tail_bound(synth.spectrum("poly1.5", RM), RK)
+    del A, om, J, Z
+    torch.cuda.empty_cache()
+
+    # ---- side workloads: a failure in one is reported in the line, not fatal to the headline
     side_steps = max(3, min(args.steps, 10))
-    cpu_ok = rank == 0 and world == 1 and not args.no_cpu_baseline
+    with_det = args.only in ("all", "id", "sampled")
     with_sampled = args.only in ("all", "sampled")
     with_all = args.only == "all"
-    samp = guarded("sampled", sampled_block, gbid, dev, side_steps, mats) if with_sampled else None
-    lst = guarded("listing", listing_block, gbid, dev, side_steps, mats) if with_sampled else None
-    two = guarded("two_sided", two_sided_block, gbid, dev, side_steps, mats) if with_sampled else None
+    det, mats = None, None
+    if with_det:
+        try:
+            det, mats = deterministic_block(gbid, dev, args, world, hbm_peak, peak_src, cpu_ok)
+        except Exception as exc:                  # noqa: BLE001 - reported in the JSON line
+            import traceback
+
+            traceback.print_exc()
+            det = {"workload": WORKLOAD, "error": repr(exc)[:500]}
+    samp = guarded("sampled", sampled_block, gbid, dev, side_steps, mats) if with_sampled and mats else None
+    lst = guarded("listing", listing_block, gbid, dev, side_steps, mats) if with_sampled and mats else None
+    two = guarded("two_sided", two_sided_block, gbid, dev, side_steps, mats) if with_sampled and mats else None
     spa = guarded("sparse", sparse_block, gbid, dev, side_steps) if with_sampled else None
-    rid = guarded("randomized", randomized_block, gbid, dev, max(2, min(args.steps, 5))) if with_all else None
+    mats = None
+    torch.cuda.empty_cache()
     bat = guarded("batched", batched_block, gbid, dev, side_steps, BATCHED_CPU_SAMPLE if cpu_ok else 0) \
         if with_all else None
     lat = guarded("latency", latency_block, gbid, dev, args.steps) if with_all else None
     dif = guarded("differentiable", differentiable_block, gbid, dev, args.steps, DIFF_CPU_SAMPLE if cpu_ok else 0) \
         if with_all else None
-
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        def one_oracle_id():
-            secs = time_oracle(results["f64"]["A"].cpu().numpy(), K_RANK, 1, full=True)
-            return {"value": 1.0 / secs[0], "unit": UNIT, "cores": 1, "kind": "oracle",
-                    "sample": f"one complete rank-{K_RANK} ID of the same 4096 x 8192 FP64 matrix by the oracle "
-                              f"({secs[0]:.1f} s, numpy, one thread)"}
-
-        cpu = guarded("cpu_baseline", one_oracle_id)
+    cmp = guarded("compare", compare_block, gbid, dev, side_steps) if with_all else None
     if world > 1 and dist.is_initialized():
         dist.barrier()
     if rank != 0:
         return 0
-    import synth
-
-    tail = synth.tail_bound(synth.spectrum("exp64", M), K_RANK)
-    r64, r32 = results["f64"], results["f32"]
     line = {
-        "metric": METRIC, "value": r64["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": r64["ms_per_step"], "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "m": M, "n": N, "k": K_RANK, "spectrum": "s_i = exp(-i/64)",
-                   "inputs": "A = U diag(s) V^T, Haar U, V (seed 2)", "parallelism": f"replicas x{world}",
-                   "l2": "256 MB buffer written between timed steps (A + working copy also exceed L2)"},
-        "eff_tflops": r64["eff_tflops"], "rel_err": r64["rel_err"], "tail_bound": tail, "status": r64["status"],
-        "roofline": r64["roofline"],
+        "metric": METRIC, "value": aggregate_rate(mean_ms, world), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean_ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "precision": "BF16 sketch (FP32 accumulation), FP32 CPQR with FP64 norms, FP32 solve of the sketch's T, "
+                     "3xTF32 refinement products, FP64 Gram factor",
+        "data": "synthetic", "config": rid_config(max(world, args.gpus)),
+        "eff_tflops": eff, "flops_convention": fl, "rel_err": err, "tail_bound": tail, "status": info["status_name"],
+        "roofline": dict(kernels[dom], stage=dom) if dom else None,
+        "kernels": kernels, "kernel_ms": per,
         "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": r64["launches_per_step"] * args.steps,
+        "gpu_launches": gbid.rid_launch_count(RM, RN, RL, RK) * args.steps,
         "clocks": clocks,
-        "f32": {"value": r32["value"], "unit": UNIT, "ms_per_step": r32["ms_per_step"], "eff_tflops": r32["eff_tflops"],
-                "rel_err": r32["rel_err"], "status": r32["status"], "roofline": r32["roofline"],
-                "speedup_vs_f64": r32["value"] / r64["value"]},
-        "solve_ms": {"f64": r64["solve_ms"], "f32": r32["solve_ms"]},
-        "randomized": rid,
+        "cpu_baseline": cpu,
+        "compare": cmp,
+        "deterministic": det,
         "sampled": samp,
         "listing": lst,
         "two_sided": two,
@@ -1030,7 +1203,6 @@ def run_gbid(args):
         "batched": bat,
         "latency": lat,
         "differentiable": dif,
-        "cpu_baseline": cpu,
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -1044,12 +1216,10 @@ def main():
     ap.add_argument("--impl", default="gbid", choices=["gbid", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only", default="all",
-                    choices=["all", "id", "sampled", "randomized", "batched", "latency", "differentiable",
-                             "compare"],
-                    help="id: the 4096 x 8192 ID alone; sampled: the ID, the column-sampling RID and the paper's "
-                         "listing outputs (normal-equation Z, C @ Z) of the same matrices; randomized / batched / "
-                         "latency / differentiable: that side workload alone; compare: the randomized and "
-                         "batched forms beside the FP64 ID of the same inputs (not part of the default run)")
+                    choices=["all", "randomized", "id", "sampled", "batched", "latency", "differentiable", "compare"],
+                    help="randomized: the headline alone; id: the headline and the 4096 x 8192 deterministic ID; "
+                         "sampled: those and the column-sampling RID, the listing outputs, the two-sided ID and the "
+                         "sparse ID; batched / latency / differentiable / compare: that side workload alone")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

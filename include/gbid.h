@@ -411,6 +411,17 @@ int id_info_read(const void* work, id_info* info, void* stream);
  * designed (ID_OK would mean it did not). WAITS for the stream. Returns
  * ID_OK, ID_EINVAL (NULL pointer, small or misaligned work) or ID_ECUDA.
  * Failure detection of the library's own making; the paper has none. */
+/* id_cpqr_timeline -- a diagnostic of the persistent CPQR kernel: while set
+ * (steps > 0), every CPQR launch has its first CTA stamp the GPU's nanosecond
+ * timer at the phase boundaries of each pivot step j < steps into
+ * buf[8 j + q] (DEVICE memory the caller owns, 8 * steps int64):
+ *   q = 0 step start, 1 pivot known, 2 pivot column and its norm formed,
+ *   3 reflector and aux ready (the trailing product starts), 4 trailing
+ *   product done, 5 after the step's last grid barrier; 6 and 7 unused.
+ * id_cpqr_timeline(NULL, 0) switches it off. Not thread-safe; the paper has
+ * no counterpart. Returns ID_OK or ID_EINVAL. */
+int id_cpqr_timeline(long long* buf, int steps);
+
 #define ID_SELFTEST_WORK_BYTES 4096
 int id_selftest_bounded_wait(void* work, size_t work_bytes, int* status, void* stream);
 

@@ -117,6 +117,7 @@ _SIG = {
     "id_refine": (ctypes.c_int, [_P, ctypes.c_int, _I64, _I64, _I64, _I64, _P, _P, _I64, _P, ctypes.c_size_t, _P, _P]),
     "id_launch_count": (ctypes.c_int64, [ctypes.c_int, _I64, _I64, _I64, _P]),
     "id_rid_launch_count": (ctypes.c_int64, [_I64, _I64, _I64, _I64, _P]),
+    "id_cpqr_timeline": (ctypes.c_int, [_P, ctypes.c_int]),
     "id_cpqr_residual_norms": (ctypes.c_int, [_P, ctypes.c_int, _I64, _I64, _I64, _I64, _P, _P, _P]),
     "id_selftest_bounded_wait": (ctypes.c_int, [_P, ctypes.c_size_t, _P, _P]),
     "id_trace_enable": (ctypes.c_int, [ctypes.c_int]),
@@ -716,6 +717,19 @@ def rid_launch_count(m: int, n: int, l: int, k: int, nb: int = 0, refine: bool =
     """Kernel launches one id_decompose_randomized call enqueues (as the library counts them)."""
     o = _opts(nb, refine)
     return int(lib().id_rid_launch_count(m, n, l, k, ctypes.byref(o)))
+
+
+def cpqr_timeline(buf: torch.Tensor | None) -> None:
+    """Stamp the CPQR kernel's phase boundaries of each pivot step into buf (CUDA int64,
+    8 entries per step; None switches the diagnostic off). See id_cpqr_timeline."""
+    if buf is None:
+        rc = lib().id_cpqr_timeline(None, 0)
+    else:
+        if not buf.is_cuda or buf.dtype != torch.int64 or not buf.is_contiguous():
+            raise ValueError("buf must be a contiguous CUDA int64 tensor")
+        rc = lib().id_cpqr_timeline(buf.data_ptr(), buf.numel() // 8)
+    if rc != ID_OK:
+        raise IdError(rc, "id_cpqr_timeline")
 
 
 def trace_enable(capacity: int = 4096) -> None:

@@ -279,7 +279,23 @@ struct KParams {
     int short_mode;   // short matrices with panels of at most 32: one grid barrier per step
     int j_begin, j_end;   // the pivot steps of this launch (one panel when the WY update runs outside)
     int wy_outside;       // 1: no phase C; the compact-WY update runs as its own launch between panels
+    long long* tl;        // step timeline (diagnostic, usually null): kTlSlots %globaltimer stamps per step
+    int tl_steps;         // steps the timeline holds
 };
+
+// Step timeline: CTA 0, thread 0 stamps %globaltimer at the phase boundaries
+// of every step j < tl_steps into tl[j * kTlSlots + q]:
+//   0 step start, 1 pivot known, 2 pivot column and its norm formed,
+//   3 reflector and aux ready (trailing product starts), 4 trailing product
+//   done, 5 after the step's last grid barrier (6, 7 unused).
+constexpr int kTlSlots = 8;
+__device__ __forceinline__ void tl_stamp(const KParams& P, int j, int q) {
+    if (P.tl != nullptr && blockIdx.x == 0 && threadIdx.x == 0 && j < P.tl_steps) {
+        long long t;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        P.tl[(int64_t)j * kTlSlots + q] = t;
+    }
+}
 
 // WY tile: W(i, l) -= sum_{c < nbw} V(i, c) F(l, c), 64 x 64 tile at (i0, l0).
 template <typename T>
@@ -461,6 +477,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
 
     for (int j = P.j_begin; j < P.j_end; ++j) {
         if (timed_out(st)) break;
+        tl_stamp(P, j, 0);
         const int j0 = j / P.nb * P.nb;
         const int jj = j - j0;
 
@@ -489,6 +506,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
             }
             best = block_argmax(best);
             p = best.pos >= j ? best.pos : j;
+            tl_stamp(P, j, 1);
             if (blockIdx.x == 0 && p != j) {
                 if (t == 0) {
                     const double a = ld(P.vn1 + j), b = ld(P.vn1 + p);
@@ -529,6 +547,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
                 }
             }
             const double S = block_sum(sq);   // synchronises: x0_s and v_s are visible after it
+            tl_stamp(P, j, 2);
             if (t == 0) {
                 const double x0 = (double)x0_s;
                 const double alpha = sqrt(fma(x0, x0, S));
@@ -610,6 +629,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
         }
         best = block_argmax(best);
         p = best.pos >= j ? best.pos : j;
+        tl_stamp(P, j, 1);
         if (blockIdx.x == 0 && p != j) {
             if (t == 0) {
                 const double a = ld(P.vn1 + j), b = ld(P.vn1 + p);
@@ -695,6 +715,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
             if (lane == 0) P.ssq[blockIdx.x] = ssq;
         }
         grid_sync(P.bar, epoch, st);
+        tl_stamp(P, j, 2);
 
         // ---- B: reflector scalars (same arithmetic in every CTA), this CTA's
         // aux entry and the trailing product's operands, from one round of loads.
@@ -801,6 +822,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
         const T scaleT = (T)scale;
 
         // ---- B3: trailing product over this CTA's column range
+        tl_stamp(P, j, 3);
         if (j + 1 < n) {
             const T tauT = (T)tau;
             const int ncols = n - j - 1;
@@ -1322,10 +1344,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
             }
             if (nbat > 0) flush();   // only reached after a timed-out wait
             }
+            tl_stamp(P, j, 4);
             bestc = block_argmax(bestc);
             if (t == 0) P.part[blockIdx.x] = bestc;
         }
         grid_sync(P.bar, epoch, st);
+        tl_stamp(P, j, 5);
 
         // ---- C: compact-WY trailing update at the end of a panel
         if (!P.wy_outside && j + 1 < P.k && jj == P.nb - 1 && m > j + 1) {
@@ -1365,6 +1389,8 @@ static SmemPlan cpqr_smem(int m) {
 }
 
 static int g_nsm = 0;
+static long long* g_tl = nullptr;   // step timeline of the next CPQR runs (diagnostic)
+static int g_tl_steps = 0;
 
 
 template <typename T>
@@ -1499,6 +1525,8 @@ cudaError_t cpqr_run(const CpqrPlan& P, cudaStream_t s) {
     K.rank_tol = sqrt((double)(P.m_user > P.n_user ? P.m_user : P.n_user)) * eps;
     K.rows_per_cta = (int)round_up(ceil_div(P.m, G), kWarp);
     K.short_mode = short_rows<T>(P.m) && P.nb <= kWarp ? 1 : 0;
+    K.tl = g_tl;
+    K.tl_steps = g_tl_steps;
 
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(G);
@@ -1546,6 +1574,13 @@ template cudaError_t cpqr_run<double>(const CpqrPlan&, cudaStream_t);
 template cudaError_t cpqr_run<float>(const CpqrPlan&, cudaStream_t);
 
 }  // namespace gbid
+
+extern "C" int id_cpqr_timeline(long long* buf, int steps) {
+    if (steps < 0 || (steps > 0 && !buf)) return ID_EINVAL;
+    gbid::g_tl = steps > 0 ? buf : nullptr;
+    gbid::g_tl_steps = steps;
+    return ID_OK;
+}
 
 extern "C" int id_selftest_bounded_wait(void* work, size_t work_bytes, int* status, void* stream) {
     static_assert(256 + sizeof(gbid::State) <= ID_SELFTEST_WORK_BYTES, "self-test scratch");

@@ -129,13 +129,32 @@ __global__ void __launch_bounds__(kGThreads, CPS) k_gemm_tf32x3(const __grid_con
         __syncwarp();
     } else {
         // ---- epilogue (warps 2..5): accumulators -> alpha acc + beta cin -> d
+        const TfEpilogue& E = P.ep;
+        const int q4 = w % 4;   // this warp's TMEM lane quarter
+        const int i = m0 + q4 * 32 + lane;
+        if (E.cin != nullptr) {
+            // the addend does not depend on the products: its lines go to L2
+            // while the main loop runs (two prefetches cover a misaligned span)
+            const int i0w = m0 + q4 * 32, i1w = min(i0w + 31, P.M - 1);
+            const int jlim = min(P.N, E.cin_cols);
+            if (E.cin_trans) {
+                for (int jj = lane; jj < BN && n0 + jj < jlim && i0w < P.M; jj += 32) {
+                    const float* row = E.cin + (int64_t)(n0 + jj) * E.ldc;
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(row + i0w));
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(row + i1w));
+                }
+            } else if (i < P.M) {
+                const float* row = E.cin + (int64_t)i * E.ldc;
+                for (int c0 = 0; c0 < BN && n0 + c0 < jlim; c0 += 32) {
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(row + n0 + c0));
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(row + min(n0 + c0 + 31, jlim - 1)));
+                }
+            }
+        }
         const bool ok = tc::mb_wait(&accf, 0u, abrt, kGSpin);
         tc::fence_after();
-        const TfEpilogue& E = P.ep;
         const bool skip = E.skip != nullptr && *E.skip != 0;
         if (ok && !skip) {
-            const int q4 = w % 4;   // this warp's TMEM lane quarter
-            const int i = m0 + q4 * 32 + lane;
             const int64_t zoff = (int64_t)z * E.z_stride;
             float* d = E.d + zoff;
             float* dl = E.d_lo ? E.d_lo + zoff : nullptr;
@@ -149,13 +168,31 @@ __global__ void __launch_bounds__(kGThreads, CPS) k_gemm_tf32x3(const __grid_con
                 const int j0 = n0 + c0;
                 if (j0 >= P.N) continue;
                 float v[32];
+                const int jlim = min(P.N, E.cin_cols);
+                if (E.cin != nullptr && !E.cin_trans && j0 + 32 <= jlim && (E.ldc & 3) == 0 &&
+                    (reinterpret_cast<uintptr_t>(E.cin) & 15) == 0) {
+                    // a row segment of the addend: eight 16-byte loads
+                    const float4* c4 = reinterpret_cast<const float4*>(E.cin + (int64_t)i * E.ldc + j0);
+                    float4 cv[8];
 #pragma unroll
-                for (int u = 0; u < 32; ++u) {
-                    const int j = j0 + u;
-                    float x = E.alpha * __uint_as_float(r[u]);
-                    if (E.cin != nullptr && j < P.N && j < E.cin_cols)
-                        x = fmaf(E.beta, E.cin_trans ? E.cin[(int64_t)j * E.ldc + i] : E.cin[(int64_t)i * E.ldc + j], x);
-                    v[u] = x;
+                    for (int u = 0; u < 8; ++u) cv[u] = c4[u];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        v[4 * u] = fmaf(E.beta, cv[u].x, E.alpha * __uint_as_float(r[4 * u]));
+                        v[4 * u + 1] = fmaf(E.beta, cv[u].y, E.alpha * __uint_as_float(r[4 * u + 1]));
+                        v[4 * u + 2] = fmaf(E.beta, cv[u].z, E.alpha * __uint_as_float(r[4 * u + 2]));
+                        v[4 * u + 3] = fmaf(E.beta, cv[u].w, E.alpha * __uint_as_float(r[4 * u + 3]));
+                    }
+                } else {
+#pragma unroll
+                    for (int u = 0; u < 32; ++u) {
+                        const int j = j0 + u;
+                        float x = E.alpha * __uint_as_float(r[u]);
+                        if (E.cin != nullptr && j < jlim)
+                            x = fmaf(E.beta, E.cin_trans ? E.cin[(int64_t)j * E.ldc + i] : E.cin[(int64_t)i * E.ldc + j],
+                                     x);
+                        v[u] = x;
+                    }
                 }
                 if (vec && j0 + 32 <= P.N) {
                     float4* dh4 = reinterpret_cast<float4*>(d + (int64_t)i * E.ldd + j0);

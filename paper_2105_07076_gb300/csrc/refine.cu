@@ -720,22 +720,27 @@ int refine_run(const float* A, int64_t m, int64_t n, int64_t lda, int k, const i
     if (split_tf32<double>(Uinv64, k, 0, k, k, kp, fp(L.Uh), fp(L.Ul), kp, s) != cudaSuccess) return ID_ECUDA;
     const TfOperand opC{fp(L.Ch), fp(L.Cl), kp, (int)m};
     const TfOperand opCt{fp(L.Cth), fp(L.Ctl), mp, k};
+    // columns m..mp-1 of R_b^T stay zero (the products write columns < m only)
+    if (mp > m && (cudaMemsetAsync(fp(L.Rth), 0, 4 * (size_t)L.nb * mp, s) != cudaSuccess ||
+                   cudaMemsetAsync(fp(L.Rtl), 0, 4 * (size_t)L.nb * mp, s) != cudaSuccess))
+        return ID_ECUDA;
     // 5. H^T = (A - C Z)^T C by column blocks of A
     for (int64_t b0 = 0; b0 < n; b0 += L.nb) {
         const int nbb = (int)(n - b0 < L.nb ? n - b0 : L.nb);
         if (split_tf32<float>(Z + b0, ldz, 1, nbb, k, kp, fp(L.Zth), fp(L.Ztl), kp, s) != cudaSuccess) return ID_ECUDA;
-        // R_b^T (nbb x mp) = A_b^T - Z_b^T C^T, written in operand form; columns m..mp-1 are zero
+        // R_b = A_b - C Z_b (m x nbb, the accumulator's lanes along the rows of A, so that
+        // the reads of A and the transposed stores of R_b^T (nbb x mp, operand form) coalesce)
         TfEpilogue e1;
         e1.alpha = -1.0f;
         e1.beta = 1.0f;
         e1.cin = A + b0;
         e1.ldc = lda;
-        e1.cin_trans = 1;
-        e1.cin_cols = (int)m;
+        e1.cin_cols = nbb;
         e1.d = fp(L.Rth);
         e1.d_lo = fp(L.Rtl);
         e1.ldd = mp;
-        int rc = gemm_tf32x3(TfOperand{fp(L.Zth), fp(L.Ztl), kp, nbb}, opC, nbb, mp, kp, 1, e1, gst, s);
+        e1.d_trans = 1;
+        int rc = gemm_tf32x3(opC, TfOperand{fp(L.Zth), fp(L.Ztl), kp, nbb}, (int)m, nbb, kp, 1, e1, gst, s);
         if (rc != ID_OK) return rc;
         // split-K slices of H_b^T = R_b^T C (nbb x k), then their FP64 sum in operand form
         TfEpilogue e2;

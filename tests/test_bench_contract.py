@@ -16,10 +16,24 @@ def _run(env_extra, timeout=600):
                           stdin=subprocess.DEVNULL)
 
 
-def test_reference_line_has_the_contract_keys():
-    r = _run({"RANK": "0", "WORLD_SIZE": "1", "LOCAL_RANK": "0"})
-    assert r.returncode == 0, r.stderr[-2000:]
-    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+def test_reference_line_has_the_contract_keys(monkeypatch, capsys):
+    """run_reference on a shrunken copy of the headline workload (the full
+    16384 x 32768 inputs are generated on the GPU machine): one JSON line with the
+    contract's keys, the GPU arm's config dict, and a rate that is the
+    sample's scaled by the column ratio."""
+    import argparse
+
+    sys.path.insert(0, ROOT)
+    import bench
+
+    for name, val in (("RM", 256), ("RN", 1024), ("RK", 32), ("RL", 42), ("RID_CPU_COLS", 128)):
+        monkeypatch.setattr(bench, name, val)
+    monkeypatch.setattr(bench, "RWORKLOAD", "rid_256x1024_k32_l42")
+    for k, v in (("RANK", "0"), ("WORLD_SIZE", "1"), ("LOCAL_RANK", "0")):
+        monkeypatch.setenv(k, v)
+    args = argparse.Namespace(gpus=1, steps=1, warmup=3, impl="reference", no_cpu_baseline=False, only="all")
+    assert bench.run_reference(args) == 0
+    lines = [ln for ln in capsys.readouterr().out.splitlines() if ln.startswith("{")]
     assert len(lines) == 1
     d = json.loads(lines[0])
     assert d["impl"] == "reference"
@@ -27,14 +41,14 @@ def test_reference_line_has_the_contract_keys():
         assert key in d, key
     assert d["value"] > 0 and d["n_gpus"] == 1 and d["steps"] == 1 and d["warmup"] == 3
     assert d["higher_is_better"] is True and d["vs_baseline"] is None and d["dtype"] == "f64"
-    assert d["config"]["workload"] and "model" not in d["config"]
+    assert d["config"] == bench.rid_config(1) and "model" not in d["config"]
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     e = d["e2e"]
     assert e["value"] == d["value"] and e["unit"] == d["unit"]
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
-    # ms per extrapolated full ID agrees with the rate
-    assert abs(1000.0 / d["ms_per_step"] - d["value"]) <= 1e-9 * d["value"] + 1e-12
+    # ms_per_step is one sample; the rate scales it by the column ratio
+    assert abs(bench.rid_oracle_rate(d["ms_per_step"] / 1000.0) - d["value"]) <= 1e-9 * d["value"]
 
 
 def test_reference_other_ranks_exit_quietly():
@@ -97,3 +111,25 @@ def test_algorithmic_units_match_the_stated_figures():
     m, n, k = 7, 11, 5
     assert bench.flops_cpqr(m, n, k) == sum(4 * (m - j) * (n - j) for j in range(k))
     assert bench.bytes_cpqr(m, n, k, 8) == 8 * (sum((m - j) * (n - j) for j in range(k)) + m * n)
+
+
+def test_headline_units_match_the_stated_figures():
+    """The headline's work units at 16384 x 32768, k = 512, l = 522: sketch
+    2 l m n = 5.6e11, CPQR of the sketch 1.78e10, solve 8.5e9, refinement
+    2mk(n-k) + 4mk^2 + 2k^2(n-k) = 5.75e11 flop; the sketch CPQR's algorithmic
+    bytes 4 sum (l-j)(n-j) + 4 l n = 17.9 GB."""
+    import pytest
+
+    sys.path.insert(0, ROOT)
+    import bench
+
+    f = bench.rid_flops()
+    assert f["sketch"] == pytest.approx(5.6e11, rel=1e-2)
+    assert f["cpqr"] == pytest.approx(1.78e10, rel=1e-2)
+    assert f["solve"] == pytest.approx(8.5e9, rel=1e-2)
+    # 2mk(n-k) = 5.4e11 is the convention's leading term; 4mk^2 + 2k^2(n-k) add 3.4e10
+    assert f["refine"] == pytest.approx(2.0 * 16384 * 512 * (32768 - 512) + 4.0 * 16384 * 512 ** 2
+                                        + 2.0 * 512 ** 2 * (32768 - 512))
+    assert 2.0 * 16384 * 512 * (32768 - 512) == pytest.approx(5.4e11, rel=1e-2)
+    assert bench.bytes_cpqr(522, 32768, 512, 4) == pytest.approx(17.9e9, rel=1e-2)
+    assert bench.rid_oracle_rate(1.0) == pytest.approx(bench.RID_CPU_COLS / bench.RN)

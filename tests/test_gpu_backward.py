@@ -109,3 +109,44 @@ def test_backward_plan_matches_single_calls(gbid):
     graph.replay()
     torch.cuda.synchronize()
     assert all(torch.equal(a, b) for a, b in zip(dAs, ref))
+
+
+def test_backward_matches_central_differences_512x1024(gbid):
+    """The differentiable workload's shape (512 x 1024, s_i = (1+i)^-2, k = 64,
+    L = <G, Z> with G ~ N(0,1)): the GPU gradient against FP64 central
+    differences with step 1e-6 of L(A) = <G, Z(A)>, Z(A) the oracle's
+    least-squares Z for the frozen skeleton (Sec. 2.1), on 64 sampled entries,
+    half of them in skeleton columns. The bar is the Frobenius test's,
+    max(1e-4, 8 sqrt(n) cond(C) u_32), relative to the sample's largest entry;
+    the differences' own error (h^2 truncation and eps/h rounding) is far below it."""
+    m, n, k = 512, 1024, 64
+    A = synth.lowrank(m, n, synth.spectrum("poly2", m), 5, dtype=torch.float32).cuda()
+    J, Z, info = gbid.id_decompose(A, k)
+    assert info["status"] == gbid.ID_OK
+    g = torch.Generator(device="cuda").manual_seed(5)
+    G = torch.randn(k, n, generator=g, device="cuda")
+    dA, binfo = gbid.id_backward(A, J, Z, G)
+    assert binfo["status"] == gbid.ID_OK
+    Ah = A.double().cpu().numpy()
+    Jg = J.cpu().numpy().astype(np.int64)
+    Gh = G.double().cpu().numpy()
+    rest = np.setdiff1d(np.arange(n), Jg)
+    rng = np.random.default_rng(11)
+    cols = np.concatenate([rng.choice(Jg, 32), rng.choice(rest, 32)])
+    rows = rng.integers(0, m, 64)
+    h = 1e-6
+
+    def loss(X):
+        return float(np.sum(Gh * orc.ls_interp(X, Jg)))
+
+    fd = np.empty(64)
+    for s, (i, j) in enumerate(zip(rows, cols)):
+        Xp = Ah.copy()
+        Xp[i, j] += h
+        Xm = Ah.copy()
+        Xm[i, j] -= h
+        fd[s] = (loss(Xp) - loss(Xm)) / (2 * h)
+    got = dA.double().cpu().numpy()[rows, cols]
+    cond = np.linalg.cond(Ah[:, Jg])
+    bar = max(1e-4, 8 * math.sqrt(n) * cond * U32)
+    assert np.max(np.abs(got - fd)) <= bar * np.max(np.abs(fd)), (np.max(np.abs(got - fd)) / np.max(np.abs(fd)), bar)
