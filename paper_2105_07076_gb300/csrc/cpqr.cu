@@ -32,22 +32,6 @@ constexpr size_t kCpqrSmemMax = 200 * 1024;  // dynamic shared memory (v cached 
 
 template <typename T> struct Vec;
 
-// Four consecutive entries (16-byte aligned), L2-coherent loads.
-__device__ __forceinline__ void ld4(const float* p, float (&o)[4]) {
-    const float4 v = __ldcg(reinterpret_cast<const float4*>(p));
-    o[0] = v.x;
-    o[1] = v.y;
-    o[2] = v.z;
-    o[3] = v.w;
-}
-__device__ __forceinline__ void ld4(const double* p, double (&o)[4]) {
-    const double2 a = __ldcg(reinterpret_cast<const double2*>(p));
-    const double2 b = __ldcg(reinterpret_cast<const double2*>(p) + 1);
-    o[0] = a.x;
-    o[1] = a.y;
-    o[2] = b.x;
-    o[3] = b.y;
-}
 template <> struct Vec<double> { using type = double2; static constexpr int n = 2; };
 template <> struct Vec<float> { using type = float4; static constexpr int n = 4; };
 
@@ -377,7 +361,6 @@ __device__ void wy_tile(T* W, int ldw, int m, int n, int i0, int l0, int j0, int
 }
 
 constexpr int kFRegs = 8;   // panel entries per lane held in registers (panels up to 256 wide)
-constexpr int kPrepCols = 512;   // short mode: columns per CTA whose panel products are formed up front
 // reflector entries per thread prefetched ahead of the pivot argmax (panels up to 8 * kPre wide)
 template <typename T> constexpr int pre_entries() { return sizeof(T) == 4 ? 32 : 16; }
 
@@ -426,7 +409,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
     T* v_s = fco + kMaxPanel + 4;                      // 16-byte aligned
     const int ldv = (P.m + Vec<T>::n - 1) / Vec<T>::n * Vec<T>::n + 8;   // v_s length; the panel copy follows
     T* vpan_s = v_s + ldv;                             // short mode: the panel's reflectors, ldv per column
-    T* pre_s = vpan_s + kWarp * ldv;                   // short mode: 2 x kPrepCols panel products of the range
     __shared__ T wy_s[16 * 64 + 16 * 65];              // WY-update tiles
     __shared__ T red[NW][kWarp];
     __shared__ double sc[4];
@@ -1160,35 +1142,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
                     }
                 }
             } else {
-            // Short mode: the panel products s1(l) = F(l, :) aux and s2(l) = F(l, :) V(j, :)^T
-            // of every column of this CTA's range in one pass (a thread per column, its F
-            // row in 16-byte loads), so a pair round below reduces only its two dot
-            // products; the moved column's F row goes to row p here as well.
-            const bool prep = pair && shortm && c_cnt <= kPrepCols;
-            if (prep) {
-                for (int q = t; q < c_cnt; q += kThreads) {
-                    const int l = j + 1 + c_lo + q;
-                    const bool moved = l == p && p != j;
-                    const T* frow = F + (int64_t)(moved ? j : l) * ldf;
-                    T a1 = T(0), a2 = T(0);
-                    for (int c0 = 0; c0 < jj; c0 += 4) {
-                        T f4[4];
-                        ld4(frow + c0, f4);
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            const int c = c0 + e;
-                            if (c < jj) {
-                                a1 += f4[e] * aux_s[c];
-                                a2 += f4[e] * vrow_s[c];
-                                if (moved) F[(int64_t)p * ldf + c] = f4[e];
-                            }
-                        }
-                    }
-                    pre_s[q] = a1;
-                    pre_s[kPrepCols + q] = a2;
-                }
-                __syncthreads();
-            }
             int idx = 0;
             if (lane == 0) idx = atomicAdd(ctr, pair ? 2 : 1);
             idx = __shfl_sync(0xffffffffu, idx, 0);
@@ -1217,8 +1170,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
                         b_nu2 = ld(P.vn2 + l1);
                         b_orig = ld(P.perm + l1);
                     }
-                    const T f0 = !prep && lane < jj ? ld(F + (int64_t)(mv0 ? j : l0) * ldf + lane) : T(0);
-                    const T f1 = !prep && has1 && lane < jj ? ld(F + (int64_t)(mv1 ? j : l1) * ldf + lane) : T(0);
+                    const T f0 = lane < jj ? ld(F + (int64_t)(mv0 ? j : l0) * ldf + lane) : T(0);
+                    const T f1 = (has1 && lane < jj) ? ld(F + (int64_t)(mv1 ? j : l1) * ldf + lane) : T(0);
                     const T* cp0 = W + (int64_t)l0 * ldw;
                     const T* cp1 = W + (int64_t)l1 * ldw;
                     V xv[8];
@@ -1261,28 +1214,20 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
                         aux_ready = true;
                     }
                     T s10 = T(0), s20 = T(0), s11 = T(0), s21 = T(0);
-                    if (prep) {
-                        const int q0 = l0 - (j + 1 + c_lo), q1 = l1 - (j + 1 + c_lo);
-                        s10 = pre_s[q0];
-                        s20 = pre_s[kPrepCols + q0];
-                        s11 = pre_s[q1];
-                        s21 = pre_s[kPrepCols + q1];
-                    } else {
-                        if (lane < jj) {
-                            s10 = f0 * auxr[0];
-                            s20 = f0 * vrow_s[lane];
-                            s11 = f1 * auxr[0];
-                            s21 = f1 * vrow_s[lane];
-                            if (mv0) F[(int64_t)p * ldf + lane] = f0;
-                            if (mv1) F[(int64_t)p * ldf + lane] = f1;
-                        }
-                        s10 = warp_sum(s10);
-                        s20 = warp_sum(s20);
-                        s11 = warp_sum(s11);
-                        s21 = warp_sum(s21);
+                    if (lane < jj) {
+                        s10 = f0 * auxr[0];
+                        s20 = f0 * vrow_s[lane];
+                        s11 = f1 * auxr[0];
+                        s21 = f1 * vrow_s[lane];
+                        if (mv0) F[(int64_t)p * ldf + lane] = f0;
+                        if (mv1) F[(int64_t)p * ldf + lane] = f1;
                     }
                     a0 = warp_sum(a0);
                     a1 = warp_sum(a1);
+                    s10 = warp_sum(s10);
+                    s20 = warp_sum(s20);
+                    s11 = warp_sum(s11);
+                    s21 = warp_sum(s21);
                     if (exact_norms) {
                         q0 = warp_sum(q0);
                         q1 = warp_sum(q1);
@@ -1451,7 +1396,7 @@ static SmemPlan cpqr_smem(int m) {
     pl.smem_v = fixed + vbytes <= kCpqrSmemMax;
     pl.bytes = fixed + (pl.smem_v ? vbytes : 0);
     // short matrices keep a copy of the panel's reflectors (up to 32 columns of v's length)
-    if (short_rows<T>(m)) pl.bytes += (size_t)kWarp * vbytes + 2 * sizeof(T) * kPrepCols;
+    if (short_rows<T>(m)) pl.bytes += (size_t)kWarp * vbytes;
     return pl;
 }
 
