@@ -408,7 +408,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
     T* fco = vrow_s + kMaxPanel + 4;
     T* v_s = fco + kMaxPanel + 4;                      // 16-byte aligned
     const int ldv = (P.m + Vec<T>::n - 1) / Vec<T>::n * Vec<T>::n + 8;   // v_s length; the panel copy follows
-    T* vpan_s = v_s + ldv;                             // short mode: the panel's reflectors, ldv per column
+    T* vpan_s = v_s + ldv;                             // short mode: the panel's reflectors, ldp per column
+    const int ldp = ldv + 1;                           // odd: a warp reading 32 panel columns hits 32 banks
     __shared__ T wy_s[16 * 64 + 16 * 65];              // WY-update tiles
     __shared__ T red[NW][kWarp];
     __shared__ double sc[4];
@@ -417,6 +418,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
     __shared__ double nu_s[2][kWarp], nu2_s[2][kWarp];   // slab-form epilogue operands
     __shared__ int orig_s[2][kWarp];
     __shared__ int abort_s;
+    __shared__ int stop_s;         // short mode: the step's timeout flag as thread 0 read it
     __shared__ T aux_s[kWarp];     // short mode: aux of the current step
     __shared__ T x0_s;
 
@@ -477,12 +479,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
     double r00 = P.j_begin > 0 ? ld(&st->r00) : 0.0;   // |R_00| (thread 0; set at step 0)
 
     for (int j = P.j_begin; j < P.j_end; ++j) {
-        if (timed_out(st)) break;
+        const bool shortm = kShort && P.short_mode;
+        // (short mode tests the timeout flag once its first loads are in flight)
+        if (!shortm && timed_out(st)) break;
         tl_stamp(P, j, 0);
         const int j0 = j / P.nb * P.nb;
         const int jj = j - j0;
 
-        const bool shortm = kShort && P.short_mode;
         const int j_al = j & ~(VN - 1);
         const int m_pad = (m + VN - 1) / VN * VN;
         int p = j;
@@ -505,9 +508,33 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
                 const ArgMax c = ld_argmax(P.part + e);
                 if (better(c, best)) best = c;
             }
-            best = block_argmax(best);
+            if (t == 0) stop_s = timed_out(st) ? 1 : 0;   // one read, shared: the block breaks together
+            best = block_argmax(best);                      // (its barriers publish stop_s)
+            if (stop_s) break;
             p = best.pos >= j ? best.pos : j;
             tl_stamp(P, j, 1);
+            // The CTA whose trailing range holds position p (CTA 0 when p = j) swaps
+            // columns j and p below; its swap of their norms and original indices
+            // loads them now, off its critical path (nobody else writes them this step).
+            const int ncols = n - j - 1;
+            int owner = 0;
+            if (p != j) {
+                const int q = p - j - 1, per = ncols / G, rem = ncols % G;
+                owner = q < rem * (per + 1) ? q / (per + 1) : rem + (q - rem * (per + 1)) / per;
+            }
+            double sw_a = 0.0, sw_b = 0.0;   // vn1 (thread 0), vn2 (thread 32), perm (thread 64) of j and p
+            if ((int)blockIdx.x == owner && p != j) {
+                if (t == 0) {
+                    sw_a = ld(P.vn1 + j);
+                    sw_b = ld(P.vn1 + p);
+                } else if (t == 32) {
+                    sw_a = ld(P.vn2 + j);
+                    sw_b = ld(P.vn2 + p);
+                } else if (t == 64) {
+                    sw_a = (double)ld(P.perm + j);
+                    sw_b = (double)ld(P.perm + p);
+                }
+            }
 #pragma unroll
             for (int u = 0; u < kSR; ++u) {
                 const int i = t + u * kThreads;
@@ -524,7 +551,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
                     T x = T(0);
                     if (i >= j && i < m) {
                         T acc = T(0);
-                        for (int c = 0; c < jj; ++c) acc += vpan_s[c * ldv + i] * fco[c];
+                        for (int c = 0; c < jj; ++c) acc += vpan_s[c * ldp + i] * fco[c];
                         x = wp_r[u] - acc;
                     }
                     if (i == j) x0_s = x;
@@ -544,8 +571,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
                 double beta = 0.0, tau = 0.0, scale = 0.0;
                 if (alpha != 0.0) {
                     beta = x0 >= 0.0 ? -alpha : alpha;
-                    tau = (beta - x0) / beta;
-                    scale = 1.0 / (x0 - beta);
+                    // tau = (beta - x0) / beta and scale = 1 / (x0 - beta) from one FP64
+                    // division (|x0 - beta| = |x0| + alpha, never zero; FP32 data keep
+                    // beta (x0 - beta) ~ alpha^2 inside FP64's range)
+                    const double d = x0 - beta;
+                    const double inv = 1.0 / (beta * d);
+                    tau = -d * d * inv;
+                    scale = beta * inv;
                 }
                 sc[0] = beta;
                 sc[1] = tau;
@@ -563,44 +595,48 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
             }
             __syncthreads();
             const T tauT = (T)sc[1], scaleT = (T)sc[2];
-            // aux(c) = -tau (scale V(j+1:m, c)^T x(j+1:m) + V(j, c)), one warp per entry
-            for (int c = w; c < jj; c += NW) {
+            // aux(c) = -tau (scale V(j+1:m, c)^T x(j+1:m) + V(j, c)): thread t takes panel
+            // column c = t % 32 over row chunk t / 32 (the panel copy's odd leading dimension
+            // keeps a warp's 32 columns in distinct banks), the chunks' partials meet in
+            // shared memory
+            {
+                const int c = t % kWarp, ch = t / kWarp;
+                const int rows = m - (j + 1);
+                const int per = rows > 0 ? (rows + NW - 1) / NW : 0;
+                const int i0 = j + 1 + ch * per, i1 = min(m, i0 + per);
                 T a = T(0);
-                for (int i = j + 1 + lane; i < m; i += kWarp) a += vpan_s[c * ldv + i] * v_s[i - j_al];
-                a = warp_sum(a);
-                if (lane == 0) aux_s[c] = -tauT * (scaleT * a + vpan_s[c * ldv + j]);
+                if (c < jj)
+                    for (int i = i0; i < i1; ++i) a += vpan_s[c * ldp + i] * v_s[i - j_al];
+                red[ch][c] = a;
             }
-            for (int c = t; c < jj; c += kThreads) vrow_s[c] = vpan_s[c * ldv + j];
+            __syncthreads();
+            if (t < jj) {
+                T sum = T(0);
+#pragma unroll
+                for (int g = 0; g < NW; ++g) sum += red[g][t];
+                aux_s[t] = -tauT * (scaleT * sum + vpan_s[t * ldp + j]);
+                vrow_s[t] = vpan_s[t * ldp + j];
+            }
             __syncthreads();   // the panel copy's column jj is rewritten next
             for (int i = t; i < ldv; i += kThreads)
-                vpan_s[jj * ldv + i] = (i > j && i < m) ? v_s[i - j_al] * scaleT : T(0);
-            // The columns j and p: the CTA whose trailing range holds position p
-            // (CTA 0 when p = j) swaps them, and their norms and original indices,
-            // so its own product reads the new column p; it first waits until every
-            // CTA has read the old columns (phase A above), and nobody else reads
+                vpan_s[jj * ldp + i] = (i > j && i < m) ? v_s[i - j_al] * scaleT : T(0);
+            // The columns j and p: the owner swaps them, and their norms and original
+            // indices, so its own product reads the new column p; it first waits until
+            // every CTA has read the old columns (phase A above), and nobody else reads
             // either column, or position p's norms, during the rest of the step.
-            const int ncols = n - j - 1;
-            int owner = 0;
-            if (p != j) {
-                const int q = p - j - 1, per = ncols / G, rem = ncols % G;
-                owner = q < rem * (per + 1) ? q / (per + 1) : rem + (q - rem * (per + 1)) / per;
-            }
             if ((int)blockIdx.x == owner) {
                 if (t == 0) wait_geq(P.auxcnt + j, (unsigned)G, st);
                 __syncthreads();
                 if (p != j) {
                     if (t == 0) {
-                        const double a = ld(P.vn1 + j), b = ld(P.vn1 + p);
-                        P.vn1[j] = b;
-                        P.vn1[p] = a;
+                        P.vn1[j] = sw_b;
+                        P.vn1[p] = sw_a;
                     } else if (t == 32) {
-                        const double a = ld(P.vn2 + j), b = ld(P.vn2 + p);
-                        P.vn2[j] = b;
-                        P.vn2[p] = a;
+                        P.vn2[j] = sw_b;
+                        P.vn2[p] = sw_a;
                     } else if (t == 64) {
-                        const int a = ld(P.perm + j), b = ld(P.perm + p);
-                        P.perm[j] = b;
-                        P.perm[p] = a;
+                        P.perm[j] = (int)sw_b;
+                        P.perm[p] = (int)sw_a;
                     }
                 }
                 const T betaT = (T)sc[0];
@@ -1222,31 +1258,49 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
                         if (mv0) F[(int64_t)p * ldf + lane] = f0;
                         if (mv1) F[(int64_t)p * ldf + lane] = f1;
                     }
-                    a0 = warp_sum(a0);
-                    a1 = warp_sum(a1);
-                    s10 = warp_sum(s10);
-                    s20 = warp_sum(s20);
-                    s11 = warp_sum(s11);
-                    s21 = warp_sum(s21);
-                    if (exact_norms) {
-                        q0 = warp_sum(q0);
-                        q1 = warp_sum(q1);
+                    // The eight warp sums (the two dot products, the two columns' panel
+                    // products, the two squared norms) as one transposed butterfly: after
+                    // three halving exchanges each lane holds one partial of one of the
+                    // eight, whose last two levels finish it, and the two batch lanes
+                    // then fetch theirs (13 shuffles instead of 40).
+                    T v8[8] = {a0, a1, s10, s20, s11, s21, q0, q1};
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const bool hi = (lane & 16) != 0;
+                        const T send = hi ? v8[q] : v8[q + 4];
+                        const T keep = hi ? v8[q + 4] : v8[q];
+                        v8[q] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
                     }
-                    if (lane == s0) {
-                        const T f = tauT * (scaleT * a0 + wjl0) + s10;
-                        b_f = f;
-                        b_r = wjl0 - s20 - f;
-                        b_sq = q0;
-                        F[(int64_t)l0 * ldf + jj] = f;
-                        W[(int64_t)l0 * ldw + j] = b_r;
+#pragma unroll
+                    for (int q = 0; q < 2; ++q) {
+                        const bool hi = (lane & 8) != 0;
+                        const T send = hi ? v8[q] : v8[q + 2];
+                        const T keep = hi ? v8[q + 2] : v8[q];
+                        v8[q] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
                     }
-                    if (has1 && lane == s1i) {
-                        const T f = tauT * (scaleT * a1 + wjl1) + s11;
+                    {
+                        const bool hi = (lane & 4) != 0;
+                        const T send = hi ? v8[0] : v8[1];
+                        const T keep = hi ? v8[1] : v8[0];
+                        v8[0] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+                    }
+                    v8[0] += __shfl_xor_sync(0xffffffffu, v8[0], 2);
+                    v8[0] += __shfl_xor_sync(0xffffffffu, v8[0], 1);
+                    // sum k now sits on lane 16 (k >> 2 & 1) + 8 (k >> 1 & 1) + 4 (k & 1)
+                    const bool second = has1 && lane == s1i;
+                    const T ga = __shfl_sync(0xffffffffu, v8[0], second ? 4 : 0);     // a0 | a1
+                    const T gs1 = __shfl_sync(0xffffffffu, v8[0], second ? 16 : 8);   // s10 | s11
+                    const T gs2 = __shfl_sync(0xffffffffu, v8[0], second ? 20 : 12);  // s20 | s21
+                    const T gq = __shfl_sync(0xffffffffu, v8[0], second ? 28 : 24);   // q0 | q1
+                    if (lane == s0 || second) {
+                        const int lc = second ? l1 : l0;
+                        const T wjl = second ? wjl1 : wjl0;
+                        const T f = tauT * (scaleT * ga + wjl) + gs1;
                         b_f = f;
-                        b_r = wjl1 - s21 - f;
-                        b_sq = q1;
-                        F[(int64_t)l1 * ldf + jj] = f;
-                        W[(int64_t)l1 * ldw + j] = b_r;
+                        b_r = wjl - gs2 - f;
+                        b_sq = gq;
+                        F[(int64_t)lc * ldf + jj] = f;
+                        W[(int64_t)lc * ldw + j] = b_r;
                     }
                     nbat += has1 ? 2 : 1;
                     idx = __shfl_sync(0xffffffffu, nidx, 0);
@@ -1396,7 +1450,7 @@ static SmemPlan cpqr_smem(int m) {
     pl.smem_v = fixed + vbytes <= kCpqrSmemMax;
     pl.bytes = fixed + (pl.smem_v ? vbytes : 0);
     // short matrices keep a copy of the panel's reflectors (up to 32 columns of v's length)
-    if (short_rows<T>(m)) pl.bytes += (size_t)kWarp * vbytes;
+    if (short_rows<T>(m)) pl.bytes += (size_t)kWarp * (vbytes + sizeof(T));   // leading dimension ldv + 1
     return pl;
 }
 

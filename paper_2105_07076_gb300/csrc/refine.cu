@@ -97,8 +97,8 @@ RefLayout ref_layout(int64_t m, int64_t n, int64_t k) {
     L.Utl = take(4 * (size_t)k * kp);
     L.Uh = take(4 * (size_t)k * kp);
     L.Ul = take(4 * (size_t)k * kp);
-    L.Zth = take(4 * (size_t)L.nb * kp);
-    L.Ztl = take(4 * (size_t)L.nb * kp);
+    L.Zth = take(4 * (size_t)n * kp);
+    L.Ztl = take(4 * (size_t)n * kp);
     L.Rth = take(4 * (size_t)L.nb * mp);
     L.Rtl = take(4 * (size_t)L.nb * mp);
     L.Part = take(4 * (size_t)L.splits * L.nb * k);
@@ -683,8 +683,8 @@ int64_t refine_launch_count(int64_t m, int64_t n, int64_t k) {
         c += (full ? 2 : 0) + (ragged ? 2 : 0);
     }
     const RefLayout L = ref_layout(m, n, k);
-    c += 4;                                     // the operand splits of C, C^T, U^{-T}, U^{-1}
-    c += 4 * ((n + L.nb - 1) / L.nb);           // per column block: Z_b split, R_b^T, the split-K slices, their sum
+    c += 5;                                     // the operand splits of C, C^T, U^{-T}, U^{-1}, Z^T
+    c += 3 * ((n + L.nb - 1) / L.nb);           // per column block: R_b^T, the split-K slices, their sum
     c += 2 + 4;                                 // Y^T and the Z update; identity, reset, statistics, status
     return c;
 }
@@ -724,10 +724,11 @@ int refine_run(const float* A, int64_t m, int64_t n, int64_t lda, int k, const i
     if (mp > m && (cudaMemsetAsync(fp(L.Rth), 0, 4 * (size_t)L.nb * mp, s) != cudaSuccess ||
                    cudaMemsetAsync(fp(L.Rtl), 0, 4 * (size_t)L.nb * mp, s) != cudaSuccess))
         return ID_ECUDA;
+    // Z^T (n x kp) in operand form, once for all column blocks
+    if (split_tf32<float>(Z, ldz, 1, (int)n, k, kp, fp(L.Zth), fp(L.Ztl), kp, s) != cudaSuccess) return ID_ECUDA;
     // 5. H^T = (A - C Z)^T C by column blocks of A
     for (int64_t b0 = 0; b0 < n; b0 += L.nb) {
         const int nbb = (int)(n - b0 < L.nb ? n - b0 : L.nb);
-        if (split_tf32<float>(Z + b0, ldz, 1, nbb, k, kp, fp(L.Zth), fp(L.Ztl), kp, s) != cudaSuccess) return ID_ECUDA;
         // R_b = A_b - C Z_b (m x nbb, the accumulator's lanes along the rows of A, so that
         // the reads of A and the transposed stores of R_b^T (nbb x mp, operand form) coalesce)
         TfEpilogue e1;
@@ -740,7 +741,8 @@ int refine_run(const float* A, int64_t m, int64_t n, int64_t lda, int k, const i
         e1.d_lo = fp(L.Rtl);
         e1.ldd = mp;
         e1.d_trans = 1;
-        int rc = gemm_tf32x3(opC, TfOperand{fp(L.Zth), fp(L.Ztl), kp, nbb}, (int)m, nbb, kp, 1, e1, gst, s);
+        int rc = gemm_tf32x3(opC, TfOperand{fp(L.Zth) + b0 * kp, fp(L.Ztl) + b0 * kp, kp, nbb}, (int)m, nbb, kp, 1, e1,
+                             gst, s);
         if (rc != ID_OK) return rc;
         // split-K slices of H_b^T = R_b^T C (nbb x k), then their FP64 sum in operand form
         TfEpilogue e2;
