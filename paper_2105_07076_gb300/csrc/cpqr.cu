@@ -1521,8 +1521,10 @@ size_t wy_bytes(int m, int n, int nb) {
 // The compact-WY update after the panel of steps j0..je-1 (FP32 data):
 // W(je:m, je:n) -= V F^T with V = W(je:m, j0:je) (the panel's reflectors below
 // its diagonal block) and F = F(je:n, 0:je-j0), as a 3xTF32 product on the
-// tensor cores whose epilogue updates W in place (column-major, so the
-// accumulator's lanes run along the rows of W and the stores coalesce).
+// tensor cores whose epilogue updates W in place. The product is formed as
+// (W - V F^T)^T = W^T - F V^T: the accumulator's lanes run along the columns of
+// the column-major W, so each thread reads and writes 128-byte segments of a
+// column with 16-byte accesses.
 static int wy_update_f32(const CpqrPlan& P, int j0, int je, cudaStream_t s) {
     const int M = P.m - je, N = P.n - je, nbw = je - j0, kp = (int)kpad16(nbw);
     if (M < 1 || N < 1) return ID_OK;
@@ -1542,13 +1544,11 @@ static int wy_update_f32(const CpqrPlan& P, int j0, int je, cudaStream_t s) {
     TfEpilogue ep;
     ep.alpha = -1.0f;
     ep.beta = 1.0f;
-    ep.cin = W + (int64_t)je * P.ldw + je;   // W(je + r, je + c) at [c * ldw + r]
+    ep.cin = W + (int64_t)je * P.ldw + je;   // (column c, row r) of the block at [c * ldw + r]
     ep.ldc = P.ldw;
-    ep.cin_trans = 1;
     ep.d = W + (int64_t)je * P.ldw + je;
     ep.ldd = P.ldw;
-    ep.d_trans = 1;
-    return gemm_tf32x3(TfOperand{ah, alo, kp, M}, TfOperand{bh, blo, kp, N}, M, N, kp, 1, ep, &P.st->status, s);
+    return gemm_tf32x3(TfOperand{bh, blo, kp, N}, TfOperand{ah, alo, kp, M}, N, M, kp, 1, ep, &P.st->status, s);
 }
 
 template <typename T>

@@ -8,13 +8,14 @@
 // Per K block of kBK = 32 (one 64-byte swizzle row of BF16):
 //   warp 0 (lane 0)  TMA: Omega block MB x (128 x 32) BF16, 64B-swizzled,
 //                    and the FP32 A tile 32 x BN (no swizzle), one mbarrier;
-//   warps 2-5        convert the FP32 tile to BF16 (round to nearest even)
+//   warps 2-9        convert the FP32 tile to BF16 (round to nearest even)
 //                    and write it K-major, 64B-swizzled: the B operand;
 //   warp 1 (lane 0)  tcgen05.mma kind::f16 (BF16 x BF16 -> FP32 in TMEM),
 //                    M = 128, N = BN, K = 16, twice per 128-row block; the
 //                    stage is released by tcgen05.commit.
-// Epilogue: warps 2-5 read the accumulators with tcgen05.ld (each warp its
-// 32-lane quarter of TMEM) and store Y. kStages stages are in flight.
+// Epilogue: warps 2-9 read the accumulators with tcgen05.ld (each warp its
+// 32-lane quarter of TMEM, two warps per quarter splitting the 32-column
+// chunks) and store Y. kStages stages are in flight.
 // Every mbarrier wait is bounded; on expiry the kernel records a timeout,
 // stops issuing, waits (bounded) for work already issued and frees its TMEM.
 #include <cuda.h>
@@ -32,7 +33,8 @@
 namespace gbid {
 namespace {
 
-constexpr int kSkThreads = 192;     // 6 warps
+constexpr int kSkThreads = 320;     // 10 warps: TMA, MMA, eight converter / epilogue warps
+constexpr int kConvWarps = 8;
 constexpr int kBK = 32;             // K per stage: 32 BF16 = 64 bytes = one SW64 row
 constexpr int kStages = 3;
 constexpr int kMaxMB = 5;           // l <= 640
@@ -174,7 +176,7 @@ __global__ void __launch_bounds__(kSkThreads, 1) k_sketch(const __grid_constant_
         abort_flag = 0;
         for (int s = 0; s < kStages; ++s) {
             mb_init(&full[s], 1);
-            mb_init(&conv[s], 4);
+            mb_init(&conv[s], kConvWarps);
             mb_init(&empty[s], 1);
         }
         mb_init(&accf, 1);
@@ -228,14 +230,14 @@ __global__ void __launch_bounds__(kSkThreads, 1) k_sketch(const __grid_constant_
         }
         __syncwarp();
     } else {
-        // ---- converters (warps 2..5): FP32 tile -> BF16, K-major, 64-byte swizzle
-        const int ct = t - 64;   // 0..127
+        // ---- converters (warps 2..9): FP32 tile -> BF16, K-major, 64-byte swizzle
+        const int ct = t - 64;   // 0..32 * kConvWarps - 1
         for (int kb = 0; kb < KB; ++kb) {
             const int s = kb % kStages;
             if (!mb_wait(&full[s], (kb / kStages) & 1u, abrt)) break;
             const float* af = af_tile(s);
             unsigned char* bc = bc_tile(s);
-            for (int u = ct; u < BN * 4; u += 128) {
+            for (int u = ct; u < BN * 4; u += 32 * kConvWarps) {
                 const int r = u % BN, kc = u / BN;   // row r of the operand (column n0 + r of A), K chunk kc
                 uint32_t packed[4];
 #pragma unroll
@@ -257,19 +259,28 @@ __global__ void __launch_bounds__(kSkThreads, 1) k_sketch(const __grid_constant_
         const bool ok = mb_wait(&accf, 0u, abrt);
         tc_fence_after();
         if (ok) {
-            const int q4 = w % 4;   // this warp's TMEM lane quarter
+            const int q4 = w % 4;          // this warp's TMEM lane quarter
+            const int half = (w - 2) / 4;  // the two warps of a quarter take alternate 32-column chunks
             for (int mb = 0; mb < MB; ++mb) {
                 const int row = mb * 128 + q4 * 32 + lane;
-                for (int c0 = 0; c0 < BN; c0 += 32) {
+                for (int c0 = 32 * half; c0 < BN; c0 += 64) {
                     uint32_t r[32];
                     TMEM_LD_X32(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(mb * BN + c0), r);
                     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
                     if (row < P.M) {
                         float* yrow = P.Y + (int64_t)row * P.ldy + n0 + c0;
                         const int lim = min(32, P.N - (n0 + c0));
+                        if (lim == 32 && (P.ldy & 3) == 0 && (reinterpret_cast<uintptr_t>(P.Y) & 15) == 0) {
+                            float4* y4 = reinterpret_cast<float4*>(yrow);   // eight 16-byte stores
 #pragma unroll
-                        for (int i = 0; i < 32; ++i)
-                            if (i < lim) yrow[i] = __uint_as_float(r[i]);
+                            for (int q = 0; q < 8; ++q)
+                                y4[q] = make_float4(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1]),
+                                                    __uint_as_float(r[4 * q + 2]), __uint_as_float(r[4 * q + 3]));
+                        } else {
+#pragma unroll
+                            for (int i = 0; i < 32; ++i)
+                                if (i < lim) yrow[i] = __uint_as_float(r[i]);
+                        }
                     }
                 }
             }
