@@ -194,8 +194,9 @@ int id_cpqr(void* X, id_dtype dtype, int64_t m, int64_t n, int64_t ldx, int64_t 
  * pivot rule compares, kept in FP64 by the CPQR's downdate with exact
  * recomputes); out[i] for i < k is the residual norm column i had when step i
  * chose it (|R_ii| in exact arithmetic). The root sum of squares over i >= k
- * is ||R22||_F, the ID's residual (Sec. 2.1). A stream-ordered copy from the
- * workspace; returns ID_EINVAL for bad arguments. */
+ * is ||R22||_F, the ID's residual (Sec. 2.1). One stream-ordered kernel (the
+ * workspace keeps the squared norms; out gets their square roots); returns
+ * ID_EINVAL for bad arguments. */
 int id_cpqr_residual_norms(const void* work, id_dtype dtype, int64_t m, int64_t n, int64_t ldx, int64_t k,
                            const id_opts* opts, double* out, void* stream);
 

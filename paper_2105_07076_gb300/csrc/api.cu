@@ -382,8 +382,8 @@ int id_cpqr_residual_norms(const void* work, id_dtype dtype, int64_t m, int64_t 
     if (id_cpqr_workspace_size(dtype, m, n, ldx, k, opts) == 0) return ID_EINVAL;
     const Layout L = make_layout(dtype, (int)m, (int)n, (int)k, opts, false, false, (int)ldx);
     const char* base = static_cast<const char*>(work);
-    return cudaMemcpyAsync(out, base + L.vn1, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice,
-                           static_cast<cudaStream_t>(stream)) == cudaSuccess
+    return norms_from_squares(reinterpret_cast<const double*>(base + L.vn1), out, (int)n,
+                              static_cast<cudaStream_t>(stream)) == cudaSuccess
                ? ID_OK
                : ID_ECUDA;
 }

@@ -23,8 +23,13 @@ struct __align__(16) ArgMax {
 
 // Total order used for pivot selection: larger norm wins, equal norms go to
 // the smaller ORIGINAL column index. An empty slot has val = -1.
+// Every val is -1 or a non-negative double other than -0 (a norm, a squared
+// norm, or a sum of squares): on that set the bit patterns read as signed
+// 64-bit integers order exactly as the values, so the comparison runs on the
+// integer pipe instead of the FP64 pipe.
 __device__ __forceinline__ bool better(const ArgMax& a, const ArgMax& b) {
-    return a.val > b.val || (a.val == b.val && a.orig < b.orig);
+    const long long av = __double_as_longlong(a.val), bv = __double_as_longlong(b.val);
+    return av > bv || (av == bv && a.orig < b.orig);
 }
 
 __device__ __forceinline__ ArgMax empty_argmax() {

@@ -14,6 +14,11 @@
 // The norm downdate follows Drmac & Bujanovic (LAPACK Working Note 176): the
 // downdated estimate nu_l * sqrt(1 - (r_l / nu_l)^2) is replaced by an exact
 // recompute once (nu_new / nu_last_exact)^2 falls below sqrt(eps_64).
+// The residual norms are kept SQUARED in FP64 (vn1: the current estimate,
+// vn2: the recompute threshold sqrt(eps) times the last exact value): the
+// downdate is then nu^2 <- nu^2 - r^2 (one FMA), the argmax over squared norms
+// picks the same column as over norms, and no square root, division or
+// threshold product is taken on the step's critical path.
 #include <cuda_runtime.h>
 #include <float.h>
 #include <math.h>
@@ -70,6 +75,75 @@ __device__ double block_sum(double v) {
     __syncthreads();
     v = lane < nw ? red[lane] : 0.0;
     return warp_sum(v);
+}
+
+// Double-float (hi + lo, FP32 pair) arithmetic on the FP32 pipe: this GPU
+// issues FP64 at a small fraction of its FP32 rate, so the short steps'
+// sums of squares carry about 44 bits in FP32 pairs instead (Knuth's TwoSum
+// for the additions, an FMA for the exact error of each square).
+struct F2 {
+    float hi, lo;
+};
+__device__ __forceinline__ F2 f2_add(F2 a, F2 b) {
+    const float s = a.hi + b.hi;
+    const float bb = s - a.hi;
+    float e = (a.hi - (s - bb)) + (b.hi - bb);
+    e += a.lo + b.lo;
+    F2 r;
+    r.hi = s + e;
+    r.lo = e - (r.hi - s);
+    return r;
+}
+__device__ __forceinline__ F2 f2_sq(float x) {   // x^2 exactly
+    F2 r;
+    r.hi = x * x;
+    r.lo = fmaf(x, x, -r.hi);
+    return r;
+}
+__device__ __forceinline__ F2 warp_sum_f2(F2 v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        F2 u;
+        u.hi = __shfl_xor_sync(0xffffffffu, v.hi, o);
+        u.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
+        v = f2_add(v, u);
+    }
+    return v;
+}
+// Comparisons of doubles in [0, inf] on the integer pipe (their bit patterns
+// order as the values).
+__device__ __forceinline__ bool dle(double a, double b) {
+    return __double_as_longlong(a) <= __double_as_longlong(b);
+}
+// A downdated squared norm clamped to [0, inf]: below zero (cancellation) and
+// NaN give 0.
+__device__ __forceinline__ double clamp_sq(double t) {
+    const long long b = __double_as_longlong(t);
+    return (b > 0 && b <= 0x7FF0000000000000LL) ? t : 0.0;
+}
+// 2^-(e/2) for a squared norm 2^e (FP64), clamped to FP32's normal range: the
+// power-of-two scale that brings a column of that norm near 1 before its
+// entries are squared in FP32.
+__device__ __forceinline__ float sq_scale(double nu2) {
+    const long long b = __double_as_longlong(nu2);
+    if (b <= 0 || b >= 0x7FF0000000000000LL) return 1.0f;
+    int k = -((int)((b >> 52) & 0x7ff) - 1023) / 2;
+    k = k < -126 ? -126 : (k > 126 ? 126 : k);
+    return __int_as_float((k + 127) << 23);
+}
+
+// Deterministic block sum of FP32 pairs; the result is valid in every thread.
+__device__ F2 block_sum_f2(F2 v) {
+    __shared__ F2 red_f2[32];
+    v = warp_sum_f2(v);
+    const int w = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
+    const int nw = blockDim.x / kWarp;
+    __syncthreads();
+    if (lane == 0) red_f2[w] = v;
+    __syncthreads();
+    if (lane < nw) v = red_f2[lane];
+    else v.hi = v.lo = 0.0f;
+    return warp_sum_f2(v);
 }
 
 // Deterministic block sum in the working precision.
@@ -384,7 +458,7 @@ struct SmemPlan {
 //     on odd steps (the tail of one sweep is still in L2 when the next starts):
 //       g = W(j:m, l)^T v,  F(l, jj) = tau g + F(l, 0:jj) aux,
 //       R(j, l) = W(j, l) - F(l, 0:jj) V(j, 0:jj)^T - F(l, jj),
-//     and the FP64 norm downdate nu_l <- nu_l sqrt(1 - (R(j,l)/nu_l)^2),
+//     and the FP64 norm downdate nu_l^2 <- nu_l^2 - R(j,l)^2,
 //     replaced by an exact recompute when (nu_new / nu_exact)^2 <= sqrt(eps)
 //     of the working precision (Drmac & Bujanovic, LAPACK Working Note 176);
 //     at a panel's first step the norms are reset exactly from the product's
@@ -400,6 +474,7 @@ struct SmemPlan {
 // compiles the two-columns-per-round mode of the trailing product.
 template <typename T, bool kSmemV, bool kShort>
 __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
+    static_assert(!kShort || sizeof(T) == 4, "the short instance is FP32 only (launched in short mode only)");
     using V = typename Vec<T>::type;
     constexpr int VN = Vec<T>::n;
     constexpr int NW = kThreads / kWarp;
@@ -413,6 +488,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
     __shared__ T wy_s[16 * 64 + 16 * 65];              // WY-update tiles
     __shared__ T red[NW][kWarp];
     __shared__ double sc[4];
+    __shared__ float scf[4];       // beta, tau, scale rounded to FP32
     __shared__ double red2[NW];
     __shared__ int qctr;   // column queue of this CTA
     __shared__ double nu_s[2][kWarp], nu2_s[2][kWarp];   // slab-form epilogue operands
@@ -454,13 +530,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
             s = warp_sum(s);
             if (lane == 0) fro += s;
             if (lane == 0) {
-                const double nu = sqrt(s);
-                P.vn1[l] = nu;
-                P.vn2[l] = nu;
+                P.vn1[l] = s;   // squared norms
+                P.vn2[l] = tol3z * s;
                 P.perm[l] = l;
                 if (!isfinite(s)) atomicOr(&st->status, kStatNonFinite);
                 ArgMax c;
-                c.val = isfinite(nu) ? nu : -1.0;
+                c.val = isfinite(s) ? s : -1.0;
                 c.orig = l;
                 c.pos = l;
                 if (better(c, best)) best = c;
@@ -512,6 +587,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
             best = block_argmax(best);                      // (its barriers publish stop_s)
             if (stop_s) break;
             p = best.pos >= j ? best.pos : j;
+            // power-of-two scale for the FP32 squares of the pivot column (its
+            // squared norm is the winning value)
+            const float sig = sq_scale(best.val);
             tl_stamp(P, j, 1);
             // The CTA whose trailing range holds position p (CTA 0 when p = j) swaps
             // columns j and p below; its swap of their norms and original indices
@@ -542,8 +620,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
             }
             for (int c = t; c < jj; c += kThreads) fco[c] = ld(F + (int64_t)p * ldf + c);
             __syncthreads();
-            // x(i) = W(i, p) - sum_c V(i, c) F(p, c) on rows j..m-1; v_s = x below row j
-            double sq = 0.0;
+            // x(i) = W(i, p) - sum_c V(i, c) F(p, c) on rows j..m-1; v_s = x below row j.
+            // ||x(j+1:m)||^2 is summed in FP32 pairs (the instance is FP32 only).
+            F2 sq{0.0f, 0.0f};
 #pragma unroll
             for (int u = 0; u < kSR; ++u) {
                 const int i = t + u * kThreads;
@@ -556,33 +635,39 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
                     }
                     if (i == j) x0_s = x;
                     v_s[i - j_al] = i > j ? x : T(0);
-                    if (i > j) sq = fma((double)x, (double)x, sq);
+                    if (i > j) sq = f2_add(sq, f2_sq((float)x * sig));
                 }
             }
-            const double S = block_sum(sq);   // synchronises: x0_s and v_s are visible after it
+            const F2 S = block_sum_f2(sq);   // synchronises: x0_s and v_s are visible after it
             tl_stamp(P, j, 2);
             // This CTA has read columns j and p and F(p, :); the CTA that rewrites
             // them (below) waits for every CTA's signal (the step's counter, unused
             // otherwise in this mode), so the reads are never overtaken.
             if (t == 0) red_release_add(P.auxcnt + j, 1u);
             if (t == 0) {
-                const double x0 = (double)x0_s;
-                const double alpha = sqrt(fma(x0, x0, S));
-                double beta = 0.0, tau = 0.0, scale = 0.0;
-                if (alpha != 0.0) {
-                    beta = x0 >= 0.0 ? -alpha : alpha;
-                    // tau = (beta - x0) / beta and scale = 1 / (x0 - beta) from one FP64
-                    // division (|x0 - beta| = |x0| + alpha, never zero; FP32 data keep
-                    // beta (x0 - beta) ~ alpha^2 inside FP64's range)
-                    const double d = x0 - beta;
-                    const double inv = 1.0 / (beta * d);
-                    tau = -d * d * inv;
-                    scale = beta * inv;
+                // The reflector's scalars in FP32 (the working precision of this
+                // instance): alpha = sqrt(x0^2 + S) from the pair sum with one Newton
+                // correction, tau = (beta - x0) / beta and scale = 1 / (x0 - beta) as
+                // rounded FP32 divisions (|x0 - beta| = |x0| + alpha, never zero).
+                const float x0 = (float)x0_s;
+                const F2 a2 = f2_add(f2_sq(x0 * sig), S);   // (scaled by sig^2)
+                float alpha = sqrtf(a2.hi);
+                if (alpha > 0.0f) alpha += (fmaf(-alpha, alpha, a2.hi) + a2.lo) / (2.0f * alpha);
+                alpha = alpha / sig;   // exact: a power of two
+                float beta = 0.0f, tau = 0.0f, scale = 0.0f;
+                if (alpha != 0.0f) {
+                    beta = x0 >= 0.0f ? -alpha : alpha;
+                    const float d = x0 - beta;
+                    tau = __fdiv_rn(-d, beta);
+                    scale = __fdiv_rn(1.0f, d);
                 }
+                scf[0] = beta;
+                scf[1] = tau;
+                scf[2] = scale;
                 sc[0] = beta;
                 sc[1] = tau;
                 sc[2] = scale;
-                if (j == 0) r00 = fabs(beta);
+                if (j == 0) r00 = fabs((double)beta);
                 if (blockIdx.x == 0) {
                     st->beta = beta;
                     st->tau = tau;
@@ -594,7 +679,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
                 qctr = 0;
             }
             __syncthreads();
-            const T tauT = (T)sc[1], scaleT = (T)sc[2];
+            const T tauT = scf[1], scaleT = scf[2];
             // aux(c) = -tau (scale V(j+1:m, c)^T x(j+1:m) + V(j, c)): thread t takes panel
             // column c = t % 32 over row chunk t / 32 (the panel copy's odd leading dimension
             // keeps a warp's 32 columns in distinct banks), the chunks' partials meet in
@@ -639,7 +724,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
                         P.perm[p] = (int)sw_a;
                     }
                 }
-                const T betaT = (T)sc[0];
+                const T betaT = scf[0];
 #pragma unroll
                 for (int u = 0; u < kSR; ++u) {
                     const int i = t + u * kThreads;
@@ -821,6 +906,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
                 sc[0] = beta;
                 sc[1] = tau;
                 sc[2] = scale;
+                scf[0] = (float)beta;
+                scf[1] = (float)tau;
+                scf[2] = (float)scale;
                 if (j == 0) r00 = fabs(beta);     // |R_00|, identical in every CTA
                 if (blockIdx.x == 0) {
                     st->beta = beta;
@@ -840,7 +928,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
             __syncthreads();
         }
         {
-            const T scaleT = (T)sc[2];
+            const T scaleT = sizeof(T) == 4 ? (T)scf[2] : (T)sc[2];
             // v on this CTA's rows into W(:, j) (reflector storage, v_j = 1 implicit)
             for (int r = max(r0, j) + t; r < r1; r += kThreads)
                 W[(int64_t)j * ldw + r] = r == j ? (T)sc[0] : ld(xbuf + r) * scaleT;
@@ -863,13 +951,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
         // is formed elementwise; the products with v below use
         // v^T y = scale * x(j+1:m)^T y(j+1:m) + y_j, so no per-element scaling
         // (and no FP64 conversion in FP32) is needed on the hot loops.
-        const double tau = sc[1], scale = sc[2];
-        const T scaleT = (T)scale;
+        // (FP32 reads the scalars' FP32 copies: no per-thread FP64 conversion)
+        const T scaleT = sizeof(T) == 4 ? (T)scf[2] : (T)sc[2];
 
         // ---- B3: trailing product over this CTA's column range
         tl_stamp(P, j, 3);
         if (j + 1 < n) {
-            const T tauT = (T)tau;
+            const T tauT = sizeof(T) == 4 ? (T)scf[1] : (T)sc[1];
             const int ncols = n - j - 1;
             // Each CTA owns a contiguous, balanced range of trailing columns (so
             // every SM gets the same work) and its warps share it through a
@@ -883,7 +971,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
             int* ctr = &qctr;
             ArgMax bestc = empty_argmax();
             bool aux_ready = false;
-            T auxr[kFRegs];                  // aux[lane + 32 q], loaded once the counter says it is complete
+            // (the kShort instance runs panels of at most 32: one register per lane)
+            constexpr int kFR = kShort ? 1 : kFRegs;
+            T auxr[kFR];                     // aux[lane + 32 q], loaded once the counter says it is complete
             // Epilogues are batched: lane q owns the q-th finished column of the
             // current batch, so the FP64 downdate of 32 columns is one pass of
             // full-warp FP64 instructions instead of 32 single-lane ones.
@@ -897,10 +987,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
             const bool exact_norms = jj == 0;
             auto flush = [&]() {
                 int flagged = 0;
-                // The downdate in divide-free form (FP64 division and square root are
-                // long instruction sequences on this GPU's FP64 pipe):
-                //   nu_new^2 = (nu - |r|)(nu + |r|), one square root per column, and
-                //   the recompute test (nu_new / nu_exact)^2 <= sqrt(eps) multiplied out.
+                // The downdate on squared norms, without division or square root
+                // (long instruction sequences on this GPU's FP64 pipe):
+                //   nu_new^2 = nu^2 - r^2 (one FMA), and the recompute test
+                //   (nu_new / nu_exact)^2 <= sqrt(eps) multiplied out.
                 if (lane < nbat && exact_norms) {
                     ArgMax cnd;
                     cnd.orig = b_orig;
@@ -914,9 +1004,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
                         if (t2 <= tol3z * S) {
                             flagged = 1;
                         } else {
-                            cnd.val = sqrt(t2);
-                            P.vn1[b_l] = cnd.val;
-                            P.vn2[b_l] = cnd.val;
+                            cnd.val = t2;
+                            P.vn1[b_l] = t2;
+                            P.vn2[b_l] = tol3z * t2;
                         }
                     }
                     if (!flagged && better(cnd, bestc)) bestc = cnd;
@@ -925,15 +1015,15 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
                     cnd.orig = b_orig;
                     cnd.pos = b_l;
                     cnd.val = 0.0;
-                    if (b_nu != 0.0) {
-                        const double ra = fabs((double)b_r);
-                        double t2 = (b_nu - ra) * (b_nu + ra);
-                        t2 = t2 > 0.0 ? t2 : 0.0;
-                        if (t2 <= tol3z * b_nu2 * b_nu2) {
+                    if (__double_as_longlong(b_nu) != 0) {
+                        // b_nu: squared norm; b_nu2: its recompute threshold
+                        const double ra = (double)b_r;
+                        const double t2 = clamp_sq(fma(-ra, ra, b_nu));
+                        if (dle(t2, b_nu2)) {
                             flagged = 1;
                         } else {
-                            cnd.val = sqrt(t2);
-                            P.vn1[b_l] = cnd.val;
+                            cnd.val = t2;
+                            P.vn1[b_l] = t2;
                         }
                     }
                     if (!flagged && better(cnd, bestc)) bestc = cnd;
@@ -958,11 +1048,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
                     }
                     sacc = warp_sum(sacc);
                     if (lane == src) {
-                        const double nv = sqrt(sacc);
-                        P.vn1[l] = nv;
-                        P.vn2[l] = nv;
+                        P.vn1[l] = sacc;
+                        P.vn2[l] = tol3z * sacc;
                         ArgMax cnd;
-                        cnd.val = nv;
+                        cnd.val = sacc;
                         cnd.orig = b_orig;
                         cnd.pos = l;
                         if (better(cnd, bestc)) bestc = cnd;
@@ -1127,19 +1216,17 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
                             cnd.orig = orig_s[pb][lane];
                             cnd.pos = l;
                             cnd.val = 0.0;
-                            const double nu = nu_s[pb][lane];
+                            const double nu = nu_s[pb][lane];   // squared norms
                             if (nu != 0.0) {
-                                // nu_new^2 = (nu - |r|)(nu + |r|); recompute when it falls to
-                                // sqrt(eps) of the last exact norm squared
-                                const double ra = fabs((double)r);
-                                double t2 = (nu - ra) * (nu + ra);
-                                t2 = t2 > 0.0 ? t2 : 0.0;
-                                const double nu2 = nu2_s[pb][lane];
-                                if (t2 <= tol3z * nu2 * nu2) {
+                                // nu_new^2 = nu^2 - r^2; recompute when it falls to
+                                // sqrt(eps) of the last exact squared norm
+                                const double ra = (double)r;
+                                const double t2 = clamp_sq(fma(-ra, ra, nu));
+                                if (dle(t2, nu2_s[pb][lane])) {   // (the recompute threshold)
                                     flagged = 1;
                                 } else {
-                                    cnd.val = sqrt(t2);
-                                    P.vn1[l] = cnd.val;
+                                    cnd.val = t2;
+                                    P.vn1[l] = t2;
                                 }
                             }
                             if (!flagged && better(cnd, bestc)) bestc = cnd;
@@ -1164,11 +1251,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
                             }
                             sacc = warp_sum(sacc);
                             if (lane == src) {
-                                const double nv = sqrt(sacc);
-                                P.vn1[lr] = nv;
-                                P.vn2[lr] = nv;
+                                P.vn1[lr] = sacc;
+                                P.vn2[lr] = tol3z * sacc;
                                 ArgMax cnd;
-                                cnd.val = nv;
+                                cnd.val = sacc;
                                 cnd.orig = origr;
                                 cnd.pos = lr;
                                 if (better(cnd, bestc)) bestc = cnd;
@@ -1321,26 +1407,28 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
                     b_nu2 = ld(P.vn2 + l);
                     b_orig = ld(P.perm + l);
                 }
-                T fr[kFRegs];
+                T fr[kFR];
 #pragma unroll
-                for (int q = 0; q < kFRegs; ++q) {
+                for (int q = 0; q < kFR; ++q) {
                     const int c = lane + q * kWarp;
                     fr[q] = c < jj ? ld(frow + c) : T(0);
                 }
-                // g = W(j_al:m_pad, l)^T v, eight 16-byte loads per lane in flight
+                // g = W(j_al:m_pad, l)^T v, eight 16-byte loads per lane in flight (five in
+                // the kShort instance: its columns have at most 5 S rows, one pass)
+                constexpr int kGU = kShort ? 5 : 8;
                 const T* col = W + (int64_t)l * ldw;
                 const uint64_t pol = 2 * idx >= c_cnt ? pol_last : pol_first;
                 T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0), sq = T(0);
-                for (int i0 = j_al + lane * VN; i0 < m_pad; i0 += 8 * S) {
-                    V xv[8];
+                for (int i0 = j_al + lane * VN; i0 < m_pad; i0 += kGU * S) {
+                    V xv[kGU];
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) {
+                    for (int u = 0; u < kGU; ++u) {
                         const int i = i0 + u * S;
                         if (i < m_pad) xv[u] = ld_hint(reinterpret_cast<const V*>(col + i), pol);
                     }
                     if (exact_norms) {
 #pragma unroll
-                        for (int u = 0; u < 8; ++u) {
+                        for (int u = 0; u < kGU; ++u) {
                             const int i = i0 + u * S;
                             if (i < m_pad) {
                                 const T* xe = reinterpret_cast<const T*>(&xv[u]);
@@ -1351,7 +1439,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
                         }
                     }
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) {
+                    for (int u = 0; u < kGU; ++u) {
                         const int i = i0 + u * S;
                         if (i < m_pad) {
                             const V yv = kSmemV ? *reinterpret_cast<const V*>(v_s + (i - j_al))
@@ -1369,7 +1457,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
                     ok = __shfl_sync(0xffffffffu, ok, 0);
                     if (!ok) break;
 #pragma unroll
-                    for (int q = 0; q < kFRegs; ++q) {
+                    for (int q = 0; q < kFR; ++q) {
                         const int c = lane + q * kWarp;
                         auxr[q] = c < jj ? (shortm ? aux_s[c < kWarp ? c : 0] : ld(aux + c)) : T(0);
                     }
@@ -1377,7 +1465,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
                 }
                 T s1 = T(0), s2 = T(0);
 #pragma unroll
-                for (int q = 0; q < kFRegs; ++q) {
+                for (int q = 0; q < kFR; ++q) {
                     const int c = lane + q * kWarp;
                     if (c < jj) {
                         if (moved) F[(int64_t)p * ldf + c] = fr[q];
@@ -1385,7 +1473,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
                         s2 += fr[q] * vrow_s[c];
                     }
                 }
-                for (int c = lane + kFRegs * kWarp; c < jj; c += kWarp) {   // panels wider than kFRegs * 32
+                for (int c = lane + kFR * kWarp; c < jj; c += kWarp) {   // panels wider than kFR * 32
                     const T fv = ld(frow + c);
                     if (moved) F[(int64_t)p * ldf + c] = fv;
                     s1 += fv * ld(aux + c);   // (never in short mode: its panels are at most 32 wide)
@@ -1437,11 +1525,17 @@ template <typename T>
 static bool short_rows(int m) {
     return sizeof(T) == 4 && m <= 5 * kWarp * Vec<T>::n;
 }
+// The kShort instance runs only in short mode (panels of at most 32), so its
+// panel products fit one register per lane.
+template <typename T>
+static bool use_short(int m, int nb) {
+    return short_rows<T>(m) && nb <= kWarp;
+}
 
 // Shared-memory bytes of k_cpqr for m working rows; v is cached in shared
 // memory when it fits in kCpqrSmemMax.
 template <typename T>
-static SmemPlan cpqr_smem(int m) {
+static SmemPlan cpqr_smem(int m, int nb) {
     const int vn = Vec<T>::n;
     const size_t m_pad = (size_t)(m + vn - 1) / vn * vn;
     const size_t fixed = sizeof(T) * 2 * ((size_t)kMaxPanel + 4);
@@ -1450,7 +1544,7 @@ static SmemPlan cpqr_smem(int m) {
     pl.smem_v = fixed + vbytes <= kCpqrSmemMax;
     pl.bytes = fixed + (pl.smem_v ? vbytes : 0);
     // short matrices keep a copy of the panel's reflectors (up to 32 columns of v's length)
-    if (short_rows<T>(m)) pl.bytes += (size_t)kWarp * (vbytes + sizeof(T));   // leading dimension ldv + 1
+    if (use_short<T>(m, nb)) pl.bytes += (size_t)kWarp * (vbytes + sizeof(T));   // leading dimension ldv + 1
     return pl;
 }
 
@@ -1464,7 +1558,8 @@ cudaError_t cpqr_configure() {
     cudaError_t e = cudaFuncSetAttribute(k_cpqr<T, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kCpqrSmemMax);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_cpqr<T, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCpqrSmemMax);
+    e = cudaFuncSetAttribute(k_cpqr<float, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kCpqrSmemMax);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_cpqr<T, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCpqrSmemMax);
     if (e != cudaSuccess) return e;
@@ -1499,11 +1594,11 @@ cudaError_t zero_pad(const CpqrPlan& P, cudaStream_t s) {
 }
 
 template <typename T>
-int cpqr_grid(int m) {
-    const SmemPlan pl = cpqr_smem<T>(m);
+int cpqr_grid(int m, int nb) {
+    const SmemPlan pl = cpqr_smem<T>(m, nb);
     int occ = 0;
-    if (short_rows<T>(m))
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cpqr<T, true, true>, kThreads, pl.bytes);
+    if (use_short<T>(m, nb))
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cpqr<float, true, true>, kThreads, pl.bytes);
     else if (pl.smem_v)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cpqr<T, true, false>, kThreads, pl.bytes);
     else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cpqr<T, false, false>, kThreads, pl.bytes);
@@ -1554,11 +1649,11 @@ static int wy_update_f32(const CpqrPlan& P, int j0, int je, cudaStream_t s) {
 template <typename T>
 cudaError_t cpqr_run(const CpqrPlan& P, cudaStream_t s) {
     const double eps = sizeof(T) == 8 ? DBL_EPSILON : (double)FLT_EPSILON;
-    const SmemPlan pl = cpqr_smem<T>(P.m);
+    const SmemPlan pl = cpqr_smem<T>(P.m, P.nb);
     // The full resident grid even for small problems: a 16-CTA grid measured
     // slower on a 200 x 400 ID (608 against 504 us), the per-step latencies
     // (L2 round trips, barriers) dominating either way.
-    const int G = cpqr_grid<T>(P.m);
+    const int G = cpqr_grid<T>(P.m, P.nb);
     if (G < 1) return cudaErrorInvalidConfiguration;
 
     cudaError_t e = cudaMemsetAsync(P.st, 0, sizeof(State), s);
@@ -1590,7 +1685,7 @@ cudaError_t cpqr_run(const CpqrPlan& P, cudaStream_t s) {
     // numerical rank: |R_jj| <= sqrt(max(m, n)) eps |R_00| (rounding-noise level of a residual)
     K.rank_tol = sqrt((double)(P.m_user > P.n_user ? P.m_user : P.n_user)) * eps;
     K.rows_per_cta = (int)round_up(ceil_div(P.m, G), kWarp);
-    K.short_mode = short_rows<T>(P.m) && P.nb <= kWarp ? 1 : 0;
+    K.short_mode = use_short<T>(P.m, P.nb) ? 1 : 0;
     K.tl = g_tl;
     K.tl_steps = g_tl_steps;
 
@@ -1613,7 +1708,7 @@ cudaError_t cpqr_run(const CpqrPlan& P, cudaStream_t s) {
         K.j_begin = j0;
         K.j_end = j0 + step < P.k ? j0 + step : P.k;
         if (j0 > 0 && (e = cudaMemsetAsync(K.bar, 0, 64, s)) != cudaSuccess) return e;   // fresh barrier epochs
-        if (short_rows<T>(P.m)) e = cudaLaunchKernelEx(&cfg, k_cpqr<T, true, true>, K);
+        if (use_short<T>(P.m, P.nb)) e = cudaLaunchKernelEx(&cfg, k_cpqr<float, true, true>, K);
         else if (pl.smem_v) e = cudaLaunchKernelEx(&cfg, k_cpqr<T, true, false>, K);
         else e = cudaLaunchKernelEx(&cfg, k_cpqr<T, false, false>, K);
         if (e != cudaSuccess) return e;
@@ -1626,8 +1721,8 @@ cudaError_t cpqr_run(const CpqrPlan& P, cudaStream_t s) {
 
 template cudaError_t cpqr_configure<double>();
 template cudaError_t cpqr_configure<float>();
-template int cpqr_grid<double>(int);
-template int cpqr_grid<float>(int);
+template int cpqr_grid<double>(int, int);
+template int cpqr_grid<float>(int, int);
 template cudaError_t copy_in<double>(const void*, int64_t, int, const CpqrPlan&, cudaStream_t);
 template cudaError_t copy_in<float>(const void*, int64_t, int, const CpqrPlan&, cudaStream_t);
 template cudaError_t csr_in<double>(const int64_t*, const int32_t*, const void*, int64_t, int64_t, int64_t, int,

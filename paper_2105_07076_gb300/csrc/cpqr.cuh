@@ -68,6 +68,8 @@ cudaError_t finalize_info(const State* st, DevInfo* info, int k, int transposed,
                           const int* extra_status = nullptr);
 // info->err_est from the CPQR's residual column norms (after finalize_info).
 cudaError_t error_estimate(const double* vn1, int k, int n, const State* st, DevInfo* info, cudaStream_t s);
+// out[0:n] = the residual norms from the CPQR workspace's squared norms vn1.
+cudaError_t norms_from_squares(const double* vn1, double* out, int n, cudaStream_t s);
 
 // One least-squares refinement of Z against A (refine.cu). Returns an id_status;
 // updates info->info.refined and the Z statistics.

@@ -7,6 +7,8 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "cpqr.cuh"
 #include "trace.cuh"
@@ -235,11 +237,12 @@ cudaError_t finalize_info(const State* st, DevInfo* info, int k, int transposed,
     return cudaGetLastError();
 }
 
-// err_est = sqrt(sum of the residual column norms^2 over positions k..n-1) / ||X||_F.
+// err_est = sqrt(sum of the residual column norms^2 over positions k..n-1) / ||X||_F
+// (vn1 holds the squared norms).
 __global__ void __launch_bounds__(256) k_err_est(const double* __restrict__ vn1, int k, int n, const State* st,
                                                  DevInfo* info) {
     double s = 0.0;
-    for (int l = k + threadIdx.x; l < n; l += blockDim.x) s = fma(vn1[l], vn1[l], s);
+    for (int l = k + threadIdx.x; l < n; l += blockDim.x) s += vn1[l];
     __shared__ double red[8];
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = s;
@@ -254,6 +257,18 @@ __global__ void __launch_bounds__(256) k_err_est(const double* __restrict__ vn1,
 
 cudaError_t error_estimate(const double* vn1, int k, int n, const State* st, DevInfo* info, cudaStream_t s) {
     k_err_est<<<1, 256, 0, s>>>(vn1, k, n, st, info);
+    return cudaGetLastError();
+}
+
+// out[l] = sqrt(vn1[l]): the residual norms from the CPQR's squared norms.
+__global__ void __launch_bounds__(256) k_norms_from_squares(const double* __restrict__ vn1, double* __restrict__ out,
+                                                            int n) {
+    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < n; l += gridDim.x * blockDim.x) out[l] = sqrt(vn1[l]);
+}
+
+cudaError_t norms_from_squares(const double* vn1, double* out, int n, cudaStream_t s) {
+    const int grid = std::min((n + 255) / 256, 1024);
+    k_norms_from_squares<<<grid, 256, 0, s>>>(vn1, out, n);
     return cudaGetLastError();
 }
 
