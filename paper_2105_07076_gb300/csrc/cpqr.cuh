@@ -48,7 +48,7 @@ template <typename T>
 cudaError_t csr_in(const int64_t* rowptr, const int32_t* colind, const void* vals, int64_t m, int64_t n, int64_t nnz,
                    int trans, const CpqrPlan& P, int* status, cudaStream_t s);
 template <typename T> cudaError_t cpqr_run(const CpqrPlan& P, cudaStream_t s);
-template <typename T> int cpqr_grid(int m);   // CTAs of the cooperative launch (0: cannot launch)
+template <typename T> int cpqr_grid(int m, int nb);   // CTAs of the cooperative launch (0: cannot launch)
 
 // Back substitution T = R11^{-1} R12 (FP64) and Z assembly.
 // T = R11^{-1} R12 (FP64 arithmetic; FP32 when fp32_arith and T = float, for a
