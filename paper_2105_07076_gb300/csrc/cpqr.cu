@@ -209,11 +209,9 @@ struct SmemPlan {
 //  C. every nb steps (nb < k): compact-WY update W_trail -= V F^T. -- barrier
 // Every wait (grid barrier, aux counter) is bounded and ends the kernel early
 // with kStatTimeout instead of hanging.
-// kShort: the instance for matrices of at most 5 * 32 * VN rows, which also
-// compiles the two-columns-per-round mode of the trailing product.
-template <typename T, bool kSmemV, bool kShort>
+// (Short FP32 matrices with panels of at most 32 run on k_cpqr_short instead.)
+template <typename T, bool kSmemV>
 __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
-    static_assert(!kShort || sizeof(T) == 4, "the short instance is FP32 only (launched in short mode only)");
     using V = typename Vec<T>::type;
     constexpr int VN = Vec<T>::n;
     constexpr int NW = kThreads / kWarp;
@@ -221,9 +219,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
     T* vrow_s = reinterpret_cast<T*>(smem_raw);
     T* fco = vrow_s + kMaxPanel + 4;
     T* v_s = fco + kMaxPanel + 4;                      // 16-byte aligned
-    const int ldv = (P.m + Vec<T>::n - 1) / Vec<T>::n * Vec<T>::n + 8;   // v_s length; the panel copy follows
-    T* vpan_s = v_s + ldv;                             // short mode: the panel's reflectors, ldp per column
-    const int ldp = ldv + 1;                           // odd: a warp reading 32 panel columns hits 32 banks
     __shared__ T wy_s[16 * 64 + 16 * 65];              // WY-update tiles
     __shared__ T red[NW][kWarp];
     __shared__ double sc[4];
@@ -233,9 +228,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
     __shared__ double nu_s[2][kWarp], nu2_s[2][kWarp];   // slab-form epilogue operands
     __shared__ int orig_s[2][kWarp];
     __shared__ int abort_s;
-    __shared__ int stop_s;         // short mode: the step's timeout flag as thread 0 read it
-    __shared__ T aux_s[kWarp];     // short mode: aux of the current step
-    __shared__ T x0_s;
 
     T* W = static_cast<T*>(P.W);
     T* F = static_cast<T*>(P.F);
@@ -293,9 +285,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
     double r00 = P.j_begin > 0 ? ld(&st->r00) : 0.0;   // |R_00| (thread 0; set at step 0)
 
     for (int j = P.j_begin; j < P.j_end; ++j) {
-        const bool shortm = kShort && P.short_mode;
-        // (short mode tests the timeout flag once its first loads are in flight)
-        if (!shortm && timed_out(st)) break;
+        if (timed_out(st)) break;
         tl_stamp(P, j, 0);
         const int j0 = j / P.nb * P.nb;
         const int jj = j - j0;
@@ -303,179 +293,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
         const int j_al = j & ~(VN - 1);
         const int m_pad = (m + VN - 1) / VN * VN;
         int p = j;
-        if (shortm) {
-            // ---- A+B for short matrices (panels of at most 32): every CTA forms the
-            // pivot column, the reflector and aux itself from its shared-memory copy
-            // of the panel's reflectors, so the step needs one grid barrier instead
-            // of two, and no aux counter. The arithmetic is the same in every CTA.
-            // Rows t + 256 u of W(:, j) go out first (they do not depend on the pivot):
-            // the CTA that writes the columns j and p then needs no further round trip.
-            constexpr int kSR = (5 * kWarp * VN + kThreads - 1) / kThreads;   // rows per thread (m <= 5 * 32 * VN)
-            T wj_r[kSR], wp_r[kSR];
-#pragma unroll
-            for (int u = 0; u < kSR; ++u) {
-                const int i = t + u * kThreads;
-                wj_r[u] = i < m ? ld(W + (int64_t)j * ldw + i) : T(0);
-            }
-            ArgMax best = empty_argmax();
-            for (int e = t; e < G; e += kThreads) {
-                const ArgMax c = ld_argmax(P.part + e);
-                if (better(c, best)) best = c;
-            }
-            if (t == 0) stop_s = timed_out(st) ? 1 : 0;   // one read, shared: the block breaks together
-            best = block_argmax(best);                      // (its barriers publish stop_s)
-            if (stop_s) break;
-            p = best.pos >= j ? best.pos : j;
-            // power-of-two scale for the FP32 squares of the pivot column (its
-            // squared norm is the winning value)
-            const float sig = sq_scale(best.val);
-            tl_stamp(P, j, 1);
-            // The CTA whose trailing range holds position p (CTA 0 when p = j) swaps
-            // columns j and p below; its swap of their norms and original indices
-            // loads them now, off its critical path (nobody else writes them this step).
-            const int ncols = n - j - 1;
-            int owner = 0;
-            if (p != j) {
-                const int q = p - j - 1, per = ncols / G, rem = ncols % G;
-                owner = q < rem * (per + 1) ? q / (per + 1) : rem + (q - rem * (per + 1)) / per;
-            }
-            double sw_a = 0.0, sw_b = 0.0;   // vn1 (thread 0), vn2 (thread 32), perm (thread 64) of j and p
-            if ((int)blockIdx.x == owner && p != j) {
-                if (t == 0) {
-                    sw_a = ld(P.vn1 + j);
-                    sw_b = ld(P.vn1 + p);
-                } else if (t == 32) {
-                    sw_a = ld(P.vn2 + j);
-                    sw_b = ld(P.vn2 + p);
-                } else if (t == 64) {
-                    sw_a = (double)ld(P.perm + j);
-                    sw_b = (double)ld(P.perm + p);
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < kSR; ++u) {
-                const int i = t + u * kThreads;
-                wp_r[u] = i < m ? ld(W + (int64_t)p * ldw + i) : T(0);
-            }
-            for (int c = t; c < jj; c += kThreads) fco[c] = ld(F + (int64_t)p * ldf + c);
-            __syncthreads();
-            // x(i) = W(i, p) - sum_c V(i, c) F(p, c) on rows j..m-1; v_s = x below row j.
-            // ||x(j+1:m)||^2 is summed in FP32 pairs (the instance is FP32 only).
-            F2 sq{0.0f, 0.0f};
-#pragma unroll
-            for (int u = 0; u < kSR; ++u) {
-                const int i = t + u * kThreads;
-                if (i >= j_al && i < m_pad) {
-                    T x = T(0);
-                    if (i >= j && i < m) {
-                        T acc = T(0);
-                        for (int c = 0; c < jj; ++c) acc += vpan_s[c * ldp + i] * fco[c];
-                        x = wp_r[u] - acc;
-                    }
-                    if (i == j) x0_s = x;
-                    v_s[i - j_al] = i > j ? x : T(0);
-                    if (i > j) sq = f2_add(sq, f2_sq((float)x * sig));
-                }
-            }
-            const F2 S = block_sum_f2(sq);   // synchronises: x0_s and v_s are visible after it
-            tl_stamp(P, j, 2);
-            // This CTA has read columns j and p and F(p, :); the CTA that rewrites
-            // them (below) waits for every CTA's signal (the step's counter, unused
-            // otherwise in this mode), so the reads are never overtaken.
-            if (t == 0) red_release_add(P.auxcnt + j, 1u);
-            if (t == 0) {
-                // The reflector's scalars in FP32 (the working precision of this
-                // instance): alpha = sqrt(x0^2 + S) from the pair sum with one Newton
-                // correction, tau = (beta - x0) / beta and scale = 1 / (x0 - beta) as
-                // rounded FP32 divisions (|x0 - beta| = |x0| + alpha, never zero).
-                const float x0 = (float)x0_s;
-                const F2 a2 = f2_add(f2_sq(x0 * sig), S);   // (scaled by sig^2)
-                float alpha = sqrtf(a2.hi);
-                if (alpha > 0.0f) alpha += (fmaf(-alpha, alpha, a2.hi) + a2.lo) / (2.0f * alpha);
-                alpha = alpha / sig;   // exact: a power of two
-                float beta = 0.0f, tau = 0.0f, scale = 0.0f;
-                if (alpha != 0.0f) {
-                    beta = x0 >= 0.0f ? -alpha : alpha;
-                    const float d = x0 - beta;
-                    tau = __fdiv_rn(-d, beta);
-                    scale = __fdiv_rn(1.0f, d);
-                }
-                scf[0] = beta;
-                scf[1] = tau;
-                scf[2] = scale;
-                sc[0] = beta;
-                sc[1] = tau;
-                sc[2] = scale;
-                if (j == 0) r00 = fabs((double)beta);
-                if (blockIdx.x == 0) {
-                    st->beta = beta;
-                    st->tau = tau;
-                    P.tau[j] = tau;
-                    if (j == 0) st->r00 = r00;
-                    if (r00 == 0.0 || fabs(beta) <= P.rank_tol * r00) atomicMin(&st->rank, j);
-                    if (!isfinite(beta)) atomicOr(&st->status, kStatNonFinite);
-                }
-                qctr = 0;
-            }
-            __syncthreads();
-            const T tauT = scf[1], scaleT = scf[2];
-            // aux(c) = -tau (scale V(j+1:m, c)^T x(j+1:m) + V(j, c)): thread t takes panel
-            // column c = t % 32 over row chunk t / 32 (the panel copy's odd leading dimension
-            // keeps a warp's 32 columns in distinct banks), the chunks' partials meet in
-            // shared memory
-            {
-                const int c = t % kWarp, ch = t / kWarp;
-                const int rows = m - (j + 1);
-                const int per = rows > 0 ? (rows + NW - 1) / NW : 0;
-                const int i0 = j + 1 + ch * per, i1 = min(m, i0 + per);
-                T a = T(0);
-                if (c < jj)
-                    for (int i = i0; i < i1; ++i) a += vpan_s[c * ldp + i] * v_s[i - j_al];
-                red[ch][c] = a;
-            }
-            __syncthreads();
-            if (t < jj) {
-                T sum = T(0);
-#pragma unroll
-                for (int g = 0; g < NW; ++g) sum += red[g][t];
-                aux_s[t] = -tauT * (scaleT * sum + vpan_s[t * ldp + j]);
-                vrow_s[t] = vpan_s[t * ldp + j];
-            }
-            __syncthreads();   // the panel copy's column jj is rewritten next
-            for (int i = t; i < ldv; i += kThreads)
-                vpan_s[jj * ldp + i] = (i > j && i < m) ? v_s[i - j_al] * scaleT : T(0);
-            // The columns j and p: the owner swaps them, and their norms and original
-            // indices, so its own product reads the new column p; it first waits until
-            // every CTA has read the old columns (phase A above), and nobody else reads
-            // either column, or position p's norms, during the rest of the step.
-            if ((int)blockIdx.x == owner) {
-                if (t == 0) wait_geq(P.auxcnt + j, (unsigned)G, st);
-                __syncthreads();
-                if (p != j) {
-                    if (t == 0) {
-                        P.vn1[j] = sw_b;
-                        P.vn1[p] = sw_a;
-                    } else if (t == 32) {
-                        P.vn2[j] = sw_b;
-                        P.vn2[p] = sw_a;
-                    } else if (t == 64) {
-                        P.perm[j] = (int)sw_b;
-                        P.perm[p] = (int)sw_a;
-                    }
-                }
-                const T betaT = scf[0];
-#pragma unroll
-                for (int u = 0; u < kSR; ++u) {
-                    const int i = t + u * kThreads;
-                    if (i < m) {
-                        if (p != j) W[(int64_t)p * ldw + i] = wj_r[u];   // the old column j moves to p
-                        if (i >= j || p != j)
-                            W[(int64_t)j * ldw + i] = i < j ? wp_r[u] : (i == j ? betaT : v_s[i - j_al] * scaleT);
-                    }
-                }
-            }
-            __syncthreads();
-        } else {
+        {
         // ---- A: pivot, swap, lazy update of the pivot column
         // The panel's reflector entries on this CTA's first row tile do not
         // depend on the pivot: their loads are issued before the argmax
@@ -710,8 +528,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
             int* ctr = &qctr;
             ArgMax bestc = empty_argmax();
             bool aux_ready = false;
-            // (the kShort instance runs panels of at most 32: one register per lane)
-            constexpr int kFR = kShort ? 1 : kFRegs;
+            constexpr int kFR = kFRegs;
             T auxr[kFR];                     // aux[lane + 32 q], loaded once the counter says it is complete
             // Epilogues are batched: lane q owns the q-th finished column of the
             // current batch, so the FP64 downdate of 32 columns is one pass of
@@ -781,7 +598,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
                         T y = ld(col + i);
                         for (int c = 0; c < jj; ++c) y -= ld(W + (int64_t)(j0 + c) * ldw + i) * ld(frow + c);
                         // the current reflector (other CTAs may still be writing it to W(:, j))
-                        const T vi = (shortm ? v_s[i - j_al] : ld(xbuf + i)) * scaleT;
+                        const T vi = ld(xbuf + i) * scaleT;
                         y -= vi * f;
                         sacc = fma((double)y, (double)y, sacc);
                     }
@@ -799,11 +616,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
                 }
                 nbat = 0;
             };
-            // Short columns (at most 4 vector loads per lane) and a panel no wider
-            // than a warp: each warp takes two columns per round of loads, so one
-            // L2 round trip serves both (the sketch of a randomized ID has ~520 rows).
-            constexpr int S = kWarp * VN;
-            const bool pair = kShort && (m_pad - j_al) <= 4 * S && jj <= kWarp;
+            constexpr int S = kWarp * VN;   // rows per vector load of a warp
             if (sizeof(T) == 8 && !exact_norms) {
                 // FP64: balanced row-slab form. Warp w takes the same row slab of every
                 // column of a group of GC columns (GC accumulators per lane), so the
@@ -1004,134 +817,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
                 }
             } else {
             int idx = 0;
-            if (lane == 0) idx = atomicAdd(ctr, pair ? 2 : 1);
+            if (lane == 0) idx = atomicAdd(ctr, 1);
             idx = __shfl_sync(0xffffffffu, idx, 0);
             while (idx < c_cnt) {
-                if (pair) {
-                    const int idx1 = idx + 1;
-                    const bool has1 = idx1 < c_cnt;
-                    const int l0 = j + 1 + c_lo + (rev ? c_cnt - 1 - idx : idx);
-                    const int l1 = has1 ? j + 1 + c_lo + (rev ? c_cnt - 1 - idx1 : idx1) : l0;
-                    int nidx = 0;
-                    if (lane == 0) nidx = atomicAdd(ctr, 2);
-                    const bool mv0 = l0 == p && p != j, mv1 = has1 && l1 == p && p != j;
-                    const int s0 = nbat, s1i = nbat + 1;
-                    T wjl0 = T(0), wjl1 = T(0);
-                    if (lane == s0) {
-                        b_l = l0;
-                        wjl0 = ld(W + (int64_t)l0 * ldw + j);
-                        b_nu = ld(P.vn1 + l0);
-                        b_nu2 = ld(P.vn2 + l0);
-                        b_orig = ld(P.perm + l0);
-                    }
-                    if (has1 && lane == s1i) {
-                        b_l = l1;
-                        wjl1 = ld(W + (int64_t)l1 * ldw + j);
-                        b_nu = ld(P.vn1 + l1);
-                        b_nu2 = ld(P.vn2 + l1);
-                        b_orig = ld(P.perm + l1);
-                    }
-                    const T f0 = lane < jj ? ld(F + (int64_t)(mv0 ? j : l0) * ldf + lane) : T(0);
-                    const T f1 = (has1 && lane < jj) ? ld(F + (int64_t)(mv1 ? j : l1) * ldf + lane) : T(0);
-                    const T* cp0 = W + (int64_t)l0 * ldw;
-                    const T* cp1 = W + (int64_t)l1 * ldw;
-                    V xv[8];
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const int i = j_al + lane * VN + u * S;
-                        if (i < m_pad) {
-                            xv[u] = ld_hint(reinterpret_cast<const V*>(cp0 + i), 2 * idx >= c_cnt ? pol_last : pol_first);
-                            if (has1)
-                                xv[4 + u] = ld_hint(reinterpret_cast<const V*>(cp1 + i), 2 * idx1 >= c_cnt ? pol_last : pol_first);
-                        }
-                    }
-                    T a0 = T(0), a1 = T(0), q0 = T(0), q1 = T(0);
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const int i = j_al + lane * VN + u * S;
-                        if (i < m_pad) {
-                            const V yv = kSmemV ? *reinterpret_cast<const V*>(v_s + (i - j_al))
-                                                : x_at<T, V, VN>(xbuf, i, j, m);
-                            a0 = dot_vec(xv[u], yv, a0);
-                            if (has1) a1 = dot_vec(xv[4 + u], yv, a1);
-                            if (exact_norms) {
-                                const T* x0e = reinterpret_cast<const T*>(&xv[u]);
-                                const T* x1e = reinterpret_cast<const T*>(&xv[4 + u]);
-#pragma unroll
-                                for (int q = 0; q < VN; ++q)
-                                    if (i + q >= j) {
-                                        q0 = fma(x0e[q], x0e[q], q0);
-                                        if (has1) q1 = fma(x1e[q], x1e[q], q1);
-                                    }
-                            }
-                        }
-                    }
-                    if (!aux_ready) {
-                        int ok = 1;
-                        if (lane == 0 && !shortm) ok = wait_geq(P.auxcnt + j, (unsigned)jj, st) ? 1 : 0;
-                        ok = __shfl_sync(0xffffffffu, ok, 0);
-                        if (!ok) break;
-                        auxr[0] = lane < jj ? (shortm ? aux_s[lane] : ld(aux + lane)) : T(0);
-                        aux_ready = true;
-                    }
-                    T s10 = T(0), s20 = T(0), s11 = T(0), s21 = T(0);
-                    if (lane < jj) {
-                        s10 = f0 * auxr[0];
-                        s20 = f0 * vrow_s[lane];
-                        s11 = f1 * auxr[0];
-                        s21 = f1 * vrow_s[lane];
-                        if (mv0) F[(int64_t)p * ldf + lane] = f0;
-                        if (mv1) F[(int64_t)p * ldf + lane] = f1;
-                    }
-                    // The eight warp sums (the two dot products, the two columns' panel
-                    // products, the two squared norms) as one transposed butterfly: after
-                    // three halving exchanges each lane holds one partial of one of the
-                    // eight, whose last two levels finish it, and the two batch lanes
-                    // then fetch theirs (13 shuffles instead of 40).
-                    T v8[8] = {a0, a1, s10, s20, s11, s21, q0, q1};
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const bool hi = (lane & 16) != 0;
-                        const T send = hi ? v8[q] : v8[q + 4];
-                        const T keep = hi ? v8[q + 4] : v8[q];
-                        v8[q] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-                    }
-#pragma unroll
-                    for (int q = 0; q < 2; ++q) {
-                        const bool hi = (lane & 8) != 0;
-                        const T send = hi ? v8[q] : v8[q + 2];
-                        const T keep = hi ? v8[q + 2] : v8[q];
-                        v8[q] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
-                    }
-                    {
-                        const bool hi = (lane & 4) != 0;
-                        const T send = hi ? v8[0] : v8[1];
-                        const T keep = hi ? v8[1] : v8[0];
-                        v8[0] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
-                    }
-                    v8[0] += __shfl_xor_sync(0xffffffffu, v8[0], 2);
-                    v8[0] += __shfl_xor_sync(0xffffffffu, v8[0], 1);
-                    // sum k now sits on lane 16 (k >> 2 & 1) + 8 (k >> 1 & 1) + 4 (k & 1)
-                    const bool second = has1 && lane == s1i;
-                    const T ga = __shfl_sync(0xffffffffu, v8[0], second ? 4 : 0);     // a0 | a1
-                    const T gs1 = __shfl_sync(0xffffffffu, v8[0], second ? 16 : 8);   // s10 | s11
-                    const T gs2 = __shfl_sync(0xffffffffu, v8[0], second ? 20 : 12);  // s20 | s21
-                    const T gq = __shfl_sync(0xffffffffu, v8[0], second ? 28 : 24);   // q0 | q1
-                    if (lane == s0 || second) {
-                        const int lc = second ? l1 : l0;
-                        const T wjl = second ? wjl1 : wjl0;
-                        const T f = tauT * (scaleT * ga + wjl) + gs1;
-                        b_f = f;
-                        b_r = wjl - gs2 - f;
-                        b_sq = gq;
-                        F[(int64_t)lc * ldf + jj] = f;
-                        W[(int64_t)lc * ldw + j] = b_r;
-                    }
-                    nbat += has1 ? 2 : 1;
-                    idx = __shfl_sync(0xffffffffu, nidx, 0);
-                    if (nbat >= kWarp - 1 || idx >= c_cnt) flush();
-                    continue;
-                }
                 const int l = j + 1 + c_lo + (rev ? c_cnt - 1 - idx : idx);
                 int nidx = 0;
                 if (lane == 0) nidx = atomicAdd(ctr, 1);   // next column, in flight meanwhile
@@ -1152,9 +840,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
                     const int c = lane + q * kWarp;
                     fr[q] = c < jj ? ld(frow + c) : T(0);
                 }
-                // g = W(j_al:m_pad, l)^T v, eight 16-byte loads per lane in flight (five in
-                // the kShort instance: its columns have at most 5 S rows, one pass)
-                constexpr int kGU = kShort ? 5 : 8;
+                // g = W(j_al:m_pad, l)^T v, eight 16-byte loads per lane in flight
+                constexpr int kGU = 8;
                 const T* col = W + (int64_t)l * ldw;
                 const uint64_t pol = 2 * idx >= c_cnt ? pol_last : pol_first;
                 T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0), sq = T(0);
@@ -1192,13 +879,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
                 }
                 if (!aux_ready) {
                     int ok = 1;
-                    if (lane == 0 && !shortm) ok = wait_geq(P.auxcnt + j, (unsigned)jj, st) ? 1 : 0;
+                    if (lane == 0) ok = wait_geq(P.auxcnt + j, (unsigned)jj, st) ? 1 : 0;
                     ok = __shfl_sync(0xffffffffu, ok, 0);
                     if (!ok) break;
 #pragma unroll
                     for (int q = 0; q < kFR; ++q) {
                         const int c = lane + q * kWarp;
-                        auxr[q] = c < jj ? (shortm ? aux_s[c < kWarp ? c : 0] : ld(aux + c)) : T(0);
+                        auxr[q] = c < jj ? ld(aux + c) : T(0);
                     }
                     aux_ready = true;
                 }
@@ -1215,7 +902,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
                 for (int c = lane + kFR * kWarp; c < jj; c += kWarp) {   // panels wider than kFR * 32
                     const T fv = ld(frow + c);
                     if (moved) F[(int64_t)p * ldf + c] = fv;
-                    s1 += fv * ld(aux + c);   // (never in short mode: its panels are at most 32 wide)
+                    s1 += fv * ld(aux + c);
                     s2 += fv * vrow_s[c];
                 }
                 const T gx = warp_sum((a0 + a1) + (a2 + a3));   // x(j+1:m)^T W(j+1:m, l)
@@ -1257,18 +944,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
 }
 
 // ------------------------------------------------------------------- host --
-// Matrices short enough for the kShort instance (v always fits in shared memory).
-// FP32 only: the FP64 instance spills and measured slower on a 200 x 400 ID
-// (550 against 504 us).
-template <typename T>
-static bool short_rows(int m) {
-    return sizeof(T) == 4 && m <= 5 * kWarp * Vec<T>::n;
-}
-// Short FP32 matrices with panels of at most 32 run on the dedicated
-// short-matrix kernel (cpqr_short.cu), one launch per panel.
+// Short FP32 matrices (at most 640 rows) with panels of at most 32 run on the
+// short-matrix kernel (cpqr_short.cu), one launch per panel. FP32 only: it
+// keeps the panel's reflectors and the staged columns in shared memory.
 template <typename T>
 static bool use_short(int m, int nb) {
-    return short_rows<T>(m) && cpqr_short_rows(m) && nb <= kWarp;
+    return sizeof(T) == 4 && cpqr_short_rows(m) && nb <= kWarp;
 }
 
 // Shared-memory bytes of k_cpqr for m working rows; v is cached in shared
@@ -1293,11 +974,11 @@ static int g_tl_steps = 0;
 
 template <typename T>
 cudaError_t cpqr_configure() {
-    cudaError_t e = cudaFuncSetAttribute(k_cpqr<T, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_cpqr<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kCpqrSmemMax);
     if (e != cudaSuccess) return e;
     if (sizeof(T) == 4 && (e = cpqr_short_configure()) != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_cpqr<T, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCpqrSmemMax);
+    e = cudaFuncSetAttribute(k_cpqr<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCpqrSmemMax);
     if (e != cudaSuccess) return e;
     int dev = 0;
     cudaGetDevice(&dev);
@@ -1335,8 +1016,8 @@ int cpqr_grid(int m, int nb) {
     if (use_short<T>(m, nb)) return cpqr_short_grid();
     int occ = 0;
     if (pl.smem_v)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cpqr<T, true, false>, kThreads, pl.bytes);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cpqr<T, false, false>, kThreads, pl.bytes);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cpqr<T, true>, kThreads, pl.bytes);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cpqr<T, false>, kThreads, pl.bytes);
     if (occ < 1) return 0;
     return std::min(kMaxParts, g_nsm * occ);
 }
@@ -1420,7 +1101,6 @@ cudaError_t cpqr_run(const CpqrPlan& P, cudaStream_t s) {
     // numerical rank: |R_jj| <= sqrt(max(m, n)) eps |R_00| (rounding-noise level of a residual)
     K.rank_tol = sqrt((double)(P.m_user > P.n_user ? P.m_user : P.n_user)) * eps;
     K.rows_per_cta = (int)round_up(ceil_div(P.m, G), kWarp);
-    K.short_mode = use_short<T>(P.m, P.nb) ? 1 : 0;
     K.tl = g_tl;
     K.tl_steps = g_tl_steps;
 
@@ -1447,8 +1127,8 @@ cudaError_t cpqr_run(const CpqrPlan& P, cudaStream_t s) {
         K.j_end = j0 + step < P.k ? j0 + step : P.k;
         if (j0 > 0 && (e = cudaMemsetAsync(K.bar, 0, 64, s)) != cudaSuccess) return e;   // fresh barrier epochs
         if (shortk) e = cpqr_short_launch(K, G, s);
-        else if (pl.smem_v) e = cudaLaunchKernelEx(&cfg, k_cpqr<T, true, false>, K);
-        else e = cudaLaunchKernelEx(&cfg, k_cpqr<T, false, false>, K);
+        else if (pl.smem_v) e = cudaLaunchKernelEx(&cfg, k_cpqr<T, true>, K);
+        else e = cudaLaunchKernelEx(&cfg, k_cpqr<T, false>, K);
         if (e != cudaSuccess) return e;
         if (K.wy_outside && K.j_end < P.k && P.m > K.j_end && wy_update_f32(P, j0, K.j_end, s) != ID_OK)
             return cudaErrorLaunchFailure;

@@ -173,14 +173,15 @@ static __device__ bool wait_geq(const unsigned* p, unsigned target, State* st) {
     return true;
 }
 
+// The block barrier orders the CTA's writes before thread 0's release, and
+// thread 0's acquire before the other threads' reads; release and acquire at
+// gpu scope carry the order between CTAs, so no separate fence is needed.
 static __device__ void grid_sync(unsigned* bar, unsigned& epoch, State* st) {
     __syncthreads();
     ++epoch;
     if (threadIdx.x == 0) {
-        __threadfence();
         red_release_add(bar, 1u);
         wait_geq(bar, epoch * gridDim.x, st);
-        __threadfence();
     }
     __syncthreads();
 }
@@ -252,7 +253,6 @@ struct KParams {
     State* st;
     double rank_tol;
     int rows_per_cta; // row chunk of the pivot-column phase (multiple of 32)
-    int short_mode;   // short matrices with panels of at most 32: one grid barrier per step
     int j_begin, j_end;   // the pivot steps of this launch (one panel when the WY update runs outside)
     int wy_outside;       // 1: no phase C; the compact-WY update runs as its own launch between panels
     long long* tl;        // step timeline (diagnostic, usually null): kTlSlots %globaltimer stamps per step

@@ -17,17 +17,17 @@
 //      R(j, l) = W(j, l) - F(l, 0:jj) V(j, 0:jj)^T - F(l, jj), the FP64
 //      downdate of the squared norm (exact recompute on cancellation) and the
 //      CTA's argmax partial.                                 -- grid barrier
-// During a step the trailing columns do not change except at positions j and
-// p, so each warp copies its next D column pairs (rows j..m with their F rows,
-// squared norms and original indices) from L2 into shared memory with
-// cp.async as soon as the step starts: the copies overlap phases A and B, and
-// the product reads shared memory. Position p, rewritten by the swap, takes
-// its data from the owner's shared copy of the old column j instead.
+// The trailing product is latency-bound (one L2 round trip per column group
+// and warp): a group of TPC threads takes one column (TPC = 16, 8, 4 or 2,
+// picked each step so that a thread holds at most 12 vector loads of its
+// column), so a warp keeps 32 / TPC columns in flight per round, and each
+// column costs log2(TPC) shuffle levels instead of a full warp reduction.
 #include <cuda_runtime.h>
 #include <float.h>
 #include <math.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "common.cuh"
 #include "cpqr.cuh"
@@ -43,45 +43,18 @@ constexpr int kSMaxRows = 640;                          // the short-matrix boun
 constexpr int kSUnits = kSMaxRows / (kWarp * 4);        // 16-byte chunks per lane and column
 constexpr int kSRows = (kSMaxRows + kSThreads - 1) / kSThreads;   // rows per thread in phase A
 constexpr int kSPanel = 32;                             // widest panel
-constexpr int kSMaxD = 8;                               // column-pair slots per warp, at most
-constexpr int kSScal = 12;                              // slot tail: vn1, vn2 and perm 16-byte chunks
 
 // Shared-memory layout of one panel launch (floats; every region 16-byte aligned).
 struct SLayout {
-    int r0;    // first staged row: the panel's first step rounded down to a multiple of 4
-    int len;   // staged rows per column: m_pad - r0
+    int r0;    // first row kept: the panel's first step rounded down to a multiple of 4
+    int len;   // rows kept per column: m_pad - r0
     int ldp;   // panel copy leading dimension (len + 1: odd, so 32 panel columns hit 32 banks)
-    int cs;    // column slot: len rows, the F row (32), the norm and index chunks (12)
-    int D;     // column-pair slots per warp
-    int perm16;   // perm is staged too (16-byte aligned, n a multiple of 4: no chunk runs past its end)
 };
 
 struct SParams {
     KParams K;
     SLayout L;
 };
-
-__device__ __forceinline__ void cp16(float* sdst, const float* gsrc) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(sdst);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gsrc) : "memory");
-}
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N> __device__ __forceinline__ void cp_wait() {
-    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
-// Wait until at most n of this thread's newest copy groups are still pending.
-__device__ __forceinline__ void cp_wait_n(int n) {
-    switch (n) {
-        case 0: cp_wait<0>(); break;
-        case 1: cp_wait<1>(); break;
-        case 2: cp_wait<2>(); break;
-        case 3: cp_wait<3>(); break;
-        case 4: cp_wait<4>(); break;
-        case 5: cp_wait<5>(); break;
-        case 6: cp_wait<6>(); break;
-        default: cp_wait<7>(); break;
-    }
-}
 
 }  // namespace
 
@@ -107,13 +80,13 @@ __global__ void __launch_bounds__(kSThreads, 1) k_cpqr_short(const __grid_consta
     float* fj_s = fco + kSPanel;                   // 32: F(j, 0:jj), the row that moves to position p
     float* vrow_s = fj_s + kSPanel;                // 32: V(j, 0:jj)
     float* aux_s = vrow_s + kSPanel;               // 32: aux
-    float* my_slots = aux_s + kSPanel + (size_t)w * L.D * 2 * L.cs;   // this warp's D pair slots
     __shared__ float red[kSWarps][kWarp];
     __shared__ float scf[4];       // beta, tau, scale
     __shared__ double swd[2];      // the old position j's vn1, vn2 (the column that moves to p)
     __shared__ int swi;            // its original index
     __shared__ float x0_s;
     __shared__ int stop_s;
+    const uint64_t pol_last = l2_policy(true), pol_first = l2_policy(false);
 
     // ---- squared column norms, perm, first argmax partials (the first panel only).
     // Each warp takes whole columns; the squares are summed in FP32 pairs after a
@@ -167,21 +140,20 @@ __global__ void __launch_bounds__(kSThreads, 1) k_cpqr_short(const __grid_consta
     }
 
     const int j0 = P.j_begin;   // one panel per launch
-    double r00 = j0 > 0 ? ld(&st->r00) : 0.0;   // |R_00| (thread 0)
+    double r00 = j0 > 0 ? ld(&st->r00) : 0.0;   // |R_00| (kept by thread 31, which forms the reflectors)
     for (int j = j0; j < P.j_end; ++j) {
         tl_stamp(P, j, 0);
         const int jj = j - j0;
         const int j_al = j & ~3;
         const int rows = m_pad - j_al;   // staged rows of this step (<= len)
         // this CTA's trailing positions: a contiguous, balanced range, swept in
-        // alternating directions; warp w takes the column pairs w, w + 16, ...
+        // alternating directions (the columns read last in one step are read first
+        // in the next, while they are still in L2)
         const int ncols = n - j - 1;
         const int per = ncols > 0 ? ncols / G : 0, rem = ncols > 0 ? ncols % G : 0;
         const int c_lo = (int)blockIdx.x * per + min((int)blockIdx.x, rem);
         const int c_cnt = ncols > 0 ? per + ((int)blockIdx.x < rem ? 1 : 0) : 0;
         const bool rev = (j & 1) != 0;
-        const int npairs = (c_cnt + 1) / 2;
-        const int my_pairs = npairs > w ? (npairs - w + kSWarps - 1) / kSWarps : 0;
         auto pos_of = [&](int qc) { return j + 1 + c_lo + (rev ? c_cnt - 1 - qc : qc); };
 
         // ---- A. the argmax partials and column j's rows go out first
@@ -194,38 +166,6 @@ __global__ void __launch_bounds__(kSThreads, 1) k_cpqr_short(const __grid_consta
             wj_r[u] = i < m ? ld(W + (int64_t)j * ldw + i) : 0.0f;
         }
         if (t == 0) stop_s = timed_out(st) ? 1 : 0;   // one read, shared: the block breaks together
-        // then this warp's first D column pairs into its slots (one copy group per pair):
-        // the rows j_al..m_pad of each column, its F row (the first jj entries), and the
-        // 16-byte chunks holding its squared norm, recompute threshold and original index
-        auto issue = [&](int r) {
-            const int q = w + r * kSWarps;
-            float* sl = my_slots + (size_t)(r % L.D) * 2 * L.cs;
-#pragma unroll
-            for (int s2 = 0; s2 < 2; ++s2) {
-                const int qc = 2 * q + s2;
-                if (qc < c_cnt) {
-                    const int l = pos_of(qc);
-                    const float* src = W + (int64_t)l * ldw + j_al;
-                    float* dst = sl + s2 * L.cs;
-#pragma unroll
-                    for (int u = 0; u < kSUnits; ++u) {
-                        const int o = lane * 4 + u * 128;
-                        if (o < rows) cp16(dst + o, src + o);
-                    }
-                    const int e = lane - 16 * s2;   // lanes 16 s2 .. 16 s2 + 10 copy the tail
-                    if (e >= 0 && e < 8 && 4 * e < jj) cp16(dst + L.len + 4 * e, F + (int64_t)l * ldf + 4 * e);
-                    else if (e == 8) cp16(dst + L.len + 32, reinterpret_cast<const float*>(P.vn1 + (l & ~1)));
-                    else if (e == 9) cp16(dst + L.len + 36, reinterpret_cast<const float*>(P.vn2 + (l & ~1)));
-                    else if (e == 10 && L.perm16)
-                        cp16(dst + L.len + 40, reinterpret_cast<const float*>(P.perm + (l & ~3)));
-                }
-            }
-            cp_commit();
-        };
-        const int npre = min(L.D, my_pairs);
-        for (int r = 0; r < npre; ++r) issue(r);
-        int issued = npre;
-
         best = block_argmax(best);   // (its barriers publish stop_s)
         if (stop_s) break;
         const int p = best.pos >= j ? best.pos : j;
@@ -292,11 +232,27 @@ __global__ void __launch_bounds__(kSThreads, 1) k_cpqr_short(const __grid_consta
         // This CTA has read columns j and p and F(p, :): the owner's swap below
         // waits for every CTA's signal, so these reads are never overtaken.
         if (t == 0) red_release_add(P.auxcnt + j, 1u);
+        // Lane 31 of every warp has no aux work (panel columns number at most 31 before
+        // the current one): the owner's wait for every CTA's reads runs on thread 511
+        // and the reflector's scalars on thread 31, alongside the aux dots.
+        if (is_owner && t == kSThreads - 1) wait_geq(P.auxcnt + j, (unsigned)G, st);
 
-        // ---- B. reflector: alpha = sqrt(x0^2 + S) from the pair sum with one Newton
+        // ---- B. aux(c) = -tau (scale V(j+1:m, c)^T x(j+1:m) + V(j, c)): thread t takes
+        // panel column c = t % 32 over row chunk t / 32; the chunks meet in shared memory
+        {
+            const int c = t % kWarp, ch = t / kWarp;
+            const int nr = m - (j + 1);
+            const int per_r = nr > 0 ? (nr + kSWarps - 1) / kSWarps : 0;
+            const int i0 = j + 1 + ch * per_r, i1 = min(m, i0 + per_r);
+            float a = 0.0f;
+            if (c < jj)
+                for (int i = i0; i < i1; ++i) a += vpan[c * L.ldp + (i - L.r0)] * v_s[i - j_al];
+            red[ch][c] = a;
+        }
+        // The reflector: alpha = sqrt(x0^2 + S) from the pair sum with one Newton
         // correction, tau = (beta - x0) / beta and scale = 1 / (x0 - beta) as rounded
-        // FP32 divisions (|x0 - beta| = |x0| + alpha, never zero)
-        if (t == 0) {
+        // FP32 divisions (|x0 - beta| = |x0| + alpha, never zero).
+        if (t == kWarp - 1) {
             const float x0 = x0_s;
             const F2 a2 = f2_add(f2_sq(x0 * sig), S);   // (scaled by sig^2)
             float alpha = sqrtf(a2.hi);
@@ -324,19 +280,6 @@ __global__ void __launch_bounds__(kSThreads, 1) k_cpqr_short(const __grid_consta
         }
         __syncthreads();
         const float tauf = scf[1], scalef = scf[2];
-        // aux(c) = -tau (scale V(j+1:m, c)^T x(j+1:m) + V(j, c)): thread t takes panel
-        // column c = t % 32 over row chunk t / 32; the chunks meet in shared memory
-        {
-            const int c = t % kWarp, ch = t / kWarp;
-            const int nr = m - (j + 1);
-            const int per_r = nr > 0 ? (nr + kSWarps - 1) / kSWarps : 0;
-            const int i0 = j + 1 + ch * per_r, i1 = min(m, i0 + per_r);
-            float a = 0.0f;
-            if (c < jj)
-                for (int i = i0; i < i1; ++i) a += vpan[c * L.ldp + (i - L.r0)] * v_s[i - j_al];
-            red[ch][c] = a;
-        }
-        __syncthreads();
         if (t < jj) {
             float sum = 0.0f;
 #pragma unroll
@@ -348,12 +291,11 @@ __global__ void __launch_bounds__(kSThreads, 1) k_cpqr_short(const __grid_consta
         __syncthreads();   // the panel copy's column jj is written next
         for (int i = L.r0 + t; i < L.r0 + L.len; i += kSThreads)
             vpan[jj * L.ldp + (i - L.r0)] = (i > j && i < m) ? v_s[i - j_al] * scalef : 0.0f;
-        // The owner swaps columns j and p, their norms and original indices, once
-        // every CTA has read the old columns (phase A); nobody else reads either
-        // column, or position p's norms, during the rest of the step.
+        // The owner swaps columns j and p, their norms and original indices (every CTA
+        // has read the old columns: thread 511's wait ended before the barrier above);
+        // nobody else reads either column, or position p's norms, during the rest of
+        // the step.
         if (is_owner) {
-            if (t == 0) wait_geq(P.auxcnt + j, (unsigned)G, st);
-            __syncthreads();
             if (p != j) {
                 if (t == 0) {
                     P.vn1[j] = sw_b;
@@ -384,24 +326,30 @@ __global__ void __launch_bounds__(kSThreads, 1) k_cpqr_short(const __grid_consta
         tl_stamp(P, j, 3);
 
         // ---- C. trailing product from the staged slots. Epilogues are batched:
-        // lane q owns the q-th finished column of the batch, so the FP64 downdate
-        // of up to 32 columns is one pass of full-warp instructions.
+        // lane q keeps the q-th finished column's sums, so F(l, jj), R(j, l) and the
+        // FP64 downdate of up to 32 columns take one pass of full-warp instructions.
         ArgMax bestc = empty_argmax();
         const bool exact_norms = jj == 0;   // W(j:m, l) is exact at a panel's first step
         int nbat = 0;
         int b_l = -1, b_orig = 0;
-        float b_r = 0.0f, b_f = 0.0f, b_sq = 0.0f;
+        float b_ga = 0.0f, b_s1 = 0.0f, b_s2 = 0.0f, b_sq = 0.0f, b_wj = 0.0f;
         double b_nu = 0.0, b_nu2 = 0.0;
         auto flush = [&]() {
-            // nu_new^2 = nu^2 - r^2 (one FMA); recompute when it falls to the
+            // f = tau (scale g + W(j, l)) + F(l, :) aux, R(j, l) = W(j, l) - F(l, :) V(j, :)^T - f;
+            // nu_new^2 = nu^2 - r^2 (one FMA), recomputed when it falls to the
             // threshold sqrt(eps) nu_exact^2 kept in vn2
             int flagged = 0;
+            float f = 0.0f;
             if (lane < nbat) {
+                f = tauf * (scalef * b_ga + b_wj) + b_s1;
+                const float r = b_wj - b_s2 - f;
+                F[(int64_t)b_l * ldf + jj] = f;
+                W[(int64_t)b_l * ldw + j] = r;
                 ArgMax cnd;
                 cnd.orig = b_orig;
                 cnd.pos = b_l;
                 cnd.val = 0.0;
-                const double ra = (double)b_r;
+                const double ra = (double)r;
                 if (exact_norms) {
                     const double S2 = (double)b_sq;   // ||W(j:m, l)||^2 from the product
                     if (S2 > 0.0) {
@@ -431,7 +379,7 @@ __global__ void __launch_bounds__(kSThreads, 1) k_cpqr_short(const __grid_consta
                 const int src = __ffs(fm) - 1;
                 fm &= fm - 1;
                 const int l = __shfl_sync(0xffffffffu, b_l, src);
-                const float f = __shfl_sync(0xffffffffu, b_f, src);
+                const float fl = __shfl_sync(0xffffffffu, f, src);
                 const int orr = __shfl_sync(0xffffffffu, b_orig, src);
                 const float* frow = F + (int64_t)((l == p && p != j) ? j : l) * ldf;
                 const float* col = W + (int64_t)l * ldw;
@@ -439,7 +387,7 @@ __global__ void __launch_bounds__(kSThreads, 1) k_cpqr_short(const __grid_consta
                 for (int i = j + 1 + lane; i < m; i += kWarp) {
                     float y = ld(col + i);
                     for (int c = 0; c < jj; ++c) y -= vpan[c * L.ldp + (i - L.r0)] * ld(frow + c);
-                    y -= v_s[i - j_al] * scalef * f;
+                    y -= v_s[i - j_al] * scalef * fl;
                     sacc = fma((double)y, (double)y, sacc);
                 }
                 sacc = warp_sum(sacc);
@@ -456,114 +404,119 @@ __global__ void __launch_bounds__(kSThreads, 1) k_cpqr_short(const __grid_consta
             }
             nbat = 0;
         };
-        const float* wjs_al = wj_s + (j_al - L.r0);   // the moved column's staged rows
-        for (int r = 0; r < my_pairs; ++r) {
-            cp_wait_n(issued - r - 1);
-            __syncwarp();   // every lane's copies of this pair have landed
-            const int q = w + r * kSWarps;
-            const int qc0 = 2 * q;
-            const bool has1 = qc0 + 1 < c_cnt;
-            const int l0 = pos_of(qc0), l1 = has1 ? pos_of(qc0 + 1) : l0;
-            const float* sl = my_slots + (size_t)(r % L.D) * 2 * L.cs;
-            const bool mv0 = l0 == p && p != j, mv1 = has1 && l1 == p && p != j;
-            const float* d0 = mv0 ? wjs_al : sl;
-            const float* d1 = mv1 ? wjs_al : sl + L.cs;
-            const float f0 = lane < jj ? (mv0 ? fj_s[lane] : sl[L.len + lane]) : 0.0f;
-            const float f1 = (has1 && lane < jj) ? (mv1 ? fj_s[lane] : sl[L.cs + L.len + lane]) : 0.0f;
-            // g = x(j+1:m)^T W(j+1:m, l) (x is zero at rows <= j) and, at a panel's
-            // first step, ||W(j:m, l)||^2
-            float a0 = 0.0f, a1 = 0.0f, q0 = 0.0f, q1 = 0.0f;
+        const float* wjs_al = wj_s + (j_al - L.r0);   // the moved column's rows j_al..
+        // One round: a group of TPC lanes per column, NC = 32 / TPC columns per warp;
+        // thread `part` of a group holds rows j_al + 4 part + 4 TPC k (k < NL) of its
+        // column and entries 4 (part + TPC e) .. + 3 of its F row.
+        auto sweep = [&](auto tpc_c) {
+            constexpr int TPC = decltype(tpc_c)::value;
+            constexpr int NC = kWarp / TPC;
+            constexpr int NL = TPC == 16 ? 10 : 12;             // rows <= 4 TPC NL
+            constexpr int NF = (kSPanel / 4 + TPC - 1) / TPC;   // F-row chunks per thread
+            const int cg = lane / TPC, part = lane % TPC;
+            const int ngroups = (c_cnt + NC - 1) / NC;
+            for (int gi = w; gi < ngroups; gi += kSWarps) {
+                const int qc = gi * NC + cg;
+                const bool has = qc < c_cnt;
+                const int l = has ? pos_of(qc) : j;
+                const bool mv = has && l == p && p != j;
+                // the round's columns go to batch lanes nbat .. nbat + NC - 1, which load
+                // their squared norms, thresholds and original indices now (for the flush)
+                const int ncol = min(NC, c_cnt - gi * NC);
+                const bool mine = lane >= nbat && lane < nbat + ncol;
+                if (mine) {
+                    const int lb = pos_of(gi * NC + lane - nbat);
+                    const bool bmv = lb == p && p != j;
+                    b_l = lb;
+                    b_nu = bmv ? swd[0] : ld(P.vn1 + lb);
+                    b_nu2 = bmv ? swd[1] : ld(P.vn2 + lb);
+                    b_orig = bmv ? swi : ld(P.perm + lb);
+                }
+                const uint64_t pol = 2 * qc >= c_cnt ? pol_last : pol_first;
+                const float* colp = W + (int64_t)l * ldw + j_al;
+                float4 xv[NL];
 #pragma unroll
-            for (int u = 0; u < kSUnits; ++u) {
-                const int o = lane * 4 + u * 128;
-                if (o < rows) {
-                    const float4 yv = *reinterpret_cast<const float4*>(v_s + o);
-                    const float4 x0v = *reinterpret_cast<const float4*>(d0 + o);
-                    a0 = dot_vec(x0v, yv, a0);
-                    float4 x1v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-                    if (has1) {
-                        x1v = *reinterpret_cast<const float4*>(d1 + o);
-                        a1 = dot_vec(x1v, yv, a1);
+                for (int k = 0; k < NL; ++k) {
+                    const int o = 4 * part + 4 * TPC * k;
+                    xv[k] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                    if (has && o < rows)
+                        xv[k] = mv ? *reinterpret_cast<const float4*>(wjs_al + o)
+                                   : ld_hint(reinterpret_cast<const float4*>(colp + o), pol);
+                }
+                float4 fv[NF];
+#pragma unroll
+                for (int e = 0; e < NF; ++e) {
+                    const int cb = 4 * (part + TPC * e);
+                    fv[e] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                    if (has && cb < jj)
+                        fv[e] = mv ? *reinterpret_cast<const float4*>(fj_s + cb)
+                                   : __ldcg(reinterpret_cast<const float4*>(F + (int64_t)l * ldf + cb));
+                }
+                // g = x(j+1:m)^T W(j+1:m, l) (x is zero at rows <= j); at a panel's first
+                // step also ||W(j:m, l)||^2
+                float a = 0.0f, qn = 0.0f;
+#pragma unroll
+                for (int k = 0; k < NL; ++k) {
+                    const int o = 4 * part + 4 * TPC * k;
+                    if (o < rows) {
+                        const float4 yv = *reinterpret_cast<const float4*>(v_s + o);
+                        a = dot_vec(xv[k], yv, a);
+                        if (exact_norms) {
+                            const float* xe = reinterpret_cast<const float*>(&xv[k]);
+#pragma unroll
+                            for (int z = 0; z < 4; ++z)
+                                if (j_al + o + z >= j) qn = fmaf(xe[z], xe[z], qn);
+                        }
                     }
-                    if (exact_norms) {
-                        const float* x0e = reinterpret_cast<const float*>(&x0v);
-                        const float* x1e = reinterpret_cast<const float*>(&x1v);
+                }
+                // F(l, 0:jj) aux and F(l, 0:jj) V(j, 0:jj)^T (entries past jj masked)
+                float s1 = 0.0f, s2 = 0.0f;
 #pragma unroll
-                        for (int e = 0; e < 4; ++e)
-                            if (j_al + o + e >= j) {
-                                q0 = fmaf(x0e[e], x0e[e], q0);
-                                q1 = fmaf(x1e[e], x1e[e], q1);
+                for (int e = 0; e < NF; ++e) {
+                    const int cb = 4 * (part + TPC * e);
+                    if (cb < jj) {
+                        const float* fe = reinterpret_cast<const float*>(&fv[e]);
+#pragma unroll
+                        for (int z = 0; z < 4; ++z)
+                            if (cb + z < jj) {
+                                s1 = fmaf(fe[z], aux_s[cb + z], s1);
+                                s2 = fmaf(fe[z], vrow_s[cb + z], s2);
+                                if (mv) F[(int64_t)p * ldf + cb + z] = fe[z];   // column p carries the old F(j, :)
                             }
                     }
                 }
-            }
-            float s10 = 0.0f, s20 = 0.0f, s11 = 0.0f, s21 = 0.0f;
-            if (lane < jj) {
-                const float ax = aux_s[lane], vr = vrow_s[lane];
-                s10 = f0 * ax;
-                s20 = f0 * vr;
-                s11 = f1 * ax;
-                s21 = f1 * vr;
-                if (mv0 || mv1) F[(int64_t)p * ldf + lane] = fj_s[lane];   // column p carries the old F(j, :)
-            }
-            // The eight warp sums as one transposed butterfly: after three halving
-            // exchanges each lane holds one partial of one of the eight, whose last
-            // two levels finish it; the two batch lanes then fetch theirs.
-            float v8[8] = {a0, a1, s10, s20, s11, s21, q0, q1};
+                // W(j, l) sits in the group's first chunk (rows j_al .. j_al + 3)
+                const int zj = j - j_al;
+                const float wj_own = zj == 0 ? xv[0].x : (zj == 1 ? xv[0].y : (zj == 2 ? xv[0].z : xv[0].w));
 #pragma unroll
-            for (int qq = 0; qq < 4; ++qq) {
-                const bool hi = (lane & 16) != 0;
-                const float send = hi ? v8[qq] : v8[qq + 4];
-                const float keep = hi ? v8[qq + 4] : v8[qq];
-                v8[qq] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+                for (int o2 = 1; o2 < TPC; o2 <<= 1) {
+                    a += __shfl_xor_sync(0xffffffffu, a, o2);
+                    s1 += __shfl_xor_sync(0xffffffffu, s1, o2);
+                    s2 += __shfl_xor_sync(0xffffffffu, s2, o2);
+                    if (exact_norms) qn += __shfl_xor_sync(0xffffffffu, qn, o2);
+                }
+                const int src = mine ? (lane - nbat) * TPC : 0;
+                const float ga = __shfl_sync(0xffffffffu, a, src);
+                const float gs1 = __shfl_sync(0xffffffffu, s1, src);
+                const float gs2 = __shfl_sync(0xffffffffu, s2, src);
+                const float gq = __shfl_sync(0xffffffffu, qn, src);
+                const float gwj = __shfl_sync(0xffffffffu, wj_own, src);
+                if (mine) {
+                    b_ga = ga;
+                    b_s1 = gs1;
+                    b_s2 = gs2;
+                    b_sq = gq;
+                    b_wj = gwj;
+                }
+                nbat += ncol;
+                if (nbat > kWarp - NC) flush();
             }
-#pragma unroll
-            for (int qq = 0; qq < 2; ++qq) {
-                const bool hi = (lane & 8) != 0;
-                const float send = hi ? v8[qq] : v8[qq + 2];
-                const float keep = hi ? v8[qq + 2] : v8[qq];
-                v8[qq] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
-            }
-            {
-                const bool hi = (lane & 4) != 0;
-                const float send = hi ? v8[0] : v8[1];
-                const float keep = hi ? v8[1] : v8[0];
-                v8[0] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
-            }
-            v8[0] += __shfl_xor_sync(0xffffffffu, v8[0], 2);
-            v8[0] += __shfl_xor_sync(0xffffffffu, v8[0], 1);
-            // sum k now sits on lane 16 (k >> 2 & 1) + 8 (k >> 1 & 1) + 4 (k & 1)
-            const int s0 = nbat, s1i = nbat + 1;
-            const bool second = has1 && lane == s1i;
-            const float ga = __shfl_sync(0xffffffffu, v8[0], second ? 4 : 0);     // a0 | a1
-            const float gs1 = __shfl_sync(0xffffffffu, v8[0], second ? 16 : 8);   // s10 | s11
-            const float gs2 = __shfl_sync(0xffffffffu, v8[0], second ? 20 : 12);  // s20 | s21
-            const float gq = __shfl_sync(0xffffffffu, v8[0], second ? 28 : 24);   // q0 | q1
-            if (lane == s0 || second) {
-                const int lc = second ? l1 : l0;
-                const bool mv = second ? mv1 : mv0;
-                const float* dd = second ? d1 : d0;
-                const float* tail = (second ? sl + L.cs : sl) + L.len + 32;
-                const float wjl = dd[j - j_al];                 // W(j, l)
-                b_l = lc;
-                b_nu = mv ? swd[0] : reinterpret_cast<const double*>(tail)[lc & 1];
-                b_nu2 = mv ? swd[1] : reinterpret_cast<const double*>(tail + 4)[lc & 1];
-                b_orig = mv ? swi : (L.perm16 ? reinterpret_cast<const int*>(tail + 8)[lc & 3] : ld(P.perm + lc));
-                const float f = tauf * (scalef * ga + wjl) + gs1;   // tau v^T W(j:m, l) + F(l, :) aux
-                b_f = f;
-                b_r = wjl - gs2 - f;                                // R(j, l)
-                b_sq = gq;
-                F[(int64_t)lc * ldf + jj] = f;
-                W[(int64_t)lc * ldw + j] = b_r;
-            }
-            nbat += has1 ? 2 : 1;
-            __syncwarp();   // every lane is done with this slot: refill it
-            if (issued < my_pairs) {
-                issue(issued);
-                ++issued;
-            }
-            if (nbat >= kWarp - 1) flush();
-        }
+        };
+        // threads per column: the fewest that keep a thread at 12 vector loads or fewer
+        if (rows > 384) sweep(std::integral_constant<int, 16>{});
+        else if (rows > 192) sweep(std::integral_constant<int, 8>{});
+        else if (rows > 96) sweep(std::integral_constant<int, 4>{});
+        else sweep(std::integral_constant<int, 2>{});
         if (nbat > 0) flush();
         tl_stamp(P, j, 4);
         bestc = block_argmax(bestc);
@@ -571,32 +524,24 @@ __global__ void __launch_bounds__(kSThreads, 1) k_cpqr_short(const __grid_consta
         grid_sync(P.bar, epoch, st);
         tl_stamp(P, j, 5);
     }
-    cp_wait<0>();   // (only after an early stop can copies still be in flight)
 }
 
 // ------------------------------------------------------------------- host --
 namespace {
 
-int g_short_budget = 0;   // dynamic shared memory available to k_cpqr_short (bytes)
 int g_short_nsm = 0;
 
 SLayout short_layout(int m, int j0) {
     SLayout L;
-    L.perm16 = 0;
     const int m_pad = (m + 3) & ~3;
     L.r0 = j0 & ~3;
     L.len = m_pad - L.r0;
     L.ldp = L.len + 1;
-    L.cs = L.len + 32 + kSScal;
-    const size_t fixed = sizeof(float) * ((size_t)kSPanel * L.ldp + (L.len + 8) + L.len + 4 * kSPanel);
-    const size_t pair = sizeof(float) * 2 * (size_t)L.cs * kSWarps;
-    L.D = (size_t)g_short_budget > fixed ? (int)std::min<size_t>(kSMaxD, ((size_t)g_short_budget - fixed) / pair) : 0;
     return L;
 }
 
 size_t short_bytes(const SLayout& L) {
-    return sizeof(float) * ((size_t)kSPanel * L.ldp + (L.len + 8) + L.len + 4 * kSPanel +
-                            (size_t)kSWarps * L.D * 2 * L.cs);
+    return sizeof(float) * ((size_t)kSPanel * L.ldp + (L.len + 8) + L.len + 4 * kSPanel);
 }
 
 }  // namespace
@@ -605,21 +550,17 @@ cudaError_t cpqr_short_configure() {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    int optin = 0;
-    if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&g_short_nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    cudaFuncAttributes fa;
-    if ((e = cudaFuncGetAttributes(&fa, k_cpqr_short)) != cudaSuccess) return e;
-    g_short_budget = optin - (int)fa.sharedSizeBytes;
-    return cudaFuncSetAttribute(k_cpqr_short, cudaFuncAttributeMaxDynamicSharedMemorySize, g_short_budget);
+    const SLayout L = short_layout(kSMaxRows, 0);   // the largest layout (the first panel at 640 rows)
+    return cudaFuncSetAttribute(k_cpqr_short, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)short_bytes(L));
 }
 
 bool cpqr_short_rows(int m) { return m >= 1 && m <= kSMaxRows; }
 
 int cpqr_short_grid() {
-    // every panel's layout fits one CTA per SM: the widest (m = 640, the first panel) is checked
+    // one CTA per SM for every panel's layout: the largest is checked
     const SLayout L = short_layout(kSMaxRows, 0);
-    if (L.D < 1 || g_short_nsm < 1 || g_short_nsm > kSThreads) return 0;
+    if (g_short_nsm < 1 || g_short_nsm > kSThreads) return 0;
     int occ = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cpqr_short, kSThreads, short_bytes(L)) != cudaSuccess ||
         occ < 1)
@@ -631,8 +572,8 @@ cudaError_t cpqr_short_launch(const KParams& K, int grid, cudaStream_t s) {
     SParams SP;
     SP.K = K;
     SP.L = short_layout(K.m, K.j_begin);
-    SP.L.perm16 = (reinterpret_cast<uintptr_t>(K.perm) % 16 == 0 && K.n % 4 == 0) ? 1 : 0;
-    if (SP.L.D < 1 || grid < 1 || grid > kSThreads || K.j_end - K.j_begin > kSPanel) return cudaErrorInvalidConfiguration;
+    if (grid < 1 || grid > kSThreads || K.j_end - K.j_begin > kSPanel || !cpqr_short_rows(K.m))
+        return cudaErrorInvalidConfiguration;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(kSThreads);
