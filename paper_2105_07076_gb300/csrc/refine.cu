@@ -27,6 +27,8 @@
 #include <float.h>
 #include <math.h>
 
+#include <mutex>
+
 #include "common.cuh"
 #include "cpqr.cuh"
 #include "gbid.h"
@@ -611,10 +613,9 @@ cudaError_t tri_inverse(const double* U, int k, double* Uinv_cm, double* tmp, do
 // G = C^T C (double-float), G = U^T U (FP64, flag[0] = 1 if not positive
 // definite), U^{-1} in FP64 (row-major k x k) by the blocked inverse (Gp and
 // Wa's second half are its scratch).
-cudaError_t factor_skeleton(const float* A, int64_t m, int64_t n, int64_t lda, int k, const int32_t* J, float* C32,
-                            double* Gp, double* Wa, double* Uinv64, double* gdiag, int* flag, cudaStream_t s) {
-    k_check_j<<<1, kRThreads, 0, s>>>(J, k, n, flag);
-    k_gather<<<grid_for(m * k), kRThreads, 0, s>>>(A, lda, (int)m, k, n, J, C32);
+// C^T C = U^T U (FP64 Cholesky of the double-float Gram) and U^{-1}, from C32.
+static cudaError_t factor_gram(int64_t m, int k, const float* C32, double* Gp, double* Wa, double* Uinv64,
+                               double* gdiag, int* flag, cudaStream_t s) {
     const int nt = ceil_div(k, kGT);
     const int rows_per = (int)round_up(ceil_div(m, kGramSplit), kGK);
     k_gram<<<dim3(nt, nt, kGramSplit), 256, 0, s>>>(C32, (int)m, k, rows_per, Gp);
@@ -632,6 +633,46 @@ cudaError_t factor_skeleton(const float* A, int64_t m, int64_t n, int64_t lda, i
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     return tri_inverse(Wa, k, Wa + (size_t)k * k, Gp, Uinv64, s);
+}
+
+cudaError_t factor_skeleton(const float* A, int64_t m, int64_t n, int64_t lda, int k, const int32_t* J, float* C32,
+                            double* Gp, double* Wa, double* Uinv64, double* gdiag, int* flag, cudaStream_t s) {
+    k_check_j<<<1, kRThreads, 0, s>>>(J, k, n, flag);
+    k_gather<<<grid_for(m * k), kRThreads, 0, s>>>(A, lda, (int)m, k, n, J, C32);
+    return factor_gram(m, k, C32, Gp, Wa, Uinv64, gdiag, flag, s);
+}
+
+// A side stream per device for work that overlaps the main stream inside one
+// call (the Gram factor of the refinement beside its residual products), with
+// the fork and join events. The enqueue of one fork/join pair holds the mutex,
+// so concurrent calls never interleave their records and waits on the shared
+// events; a stream under capture takes the sequential order instead.
+struct SideStream {
+    std::mutex mu;
+    cudaStream_t s2 = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+    bool ok = false, tried = false;
+};
+static SideStream g_side[64];
+
+static SideStream* side_stream(cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return nullptr;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    SideStream* ss = &g_side[dev];
+    ss->mu.lock();
+    if (!ss->tried) {
+        ss->tried = true;
+        ss->ok = cudaStreamCreateWithFlags(&ss->s2, cudaStreamNonBlocking) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&ss->fork, cudaEventDisableTiming) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&ss->join, cudaEventDisableTiming) == cudaSuccess;
+    }
+    if (!ss->ok) {
+        ss->mu.unlock();
+        return nullptr;
+    }
+    return ss;   // locked: the caller unlocks after enqueueing its join
 }
 
 // H^T rows of one column block from the split-K slices of R_b^T C:
@@ -710,22 +751,41 @@ int refine_run(const float* A, int64_t m, int64_t n, int64_t lda, int k, const i
     const int kp = (int)kpad16(k), mp = (int)kpad16(m);
     if (cudaMemsetAsync(flag, 0, 16, s) != cudaSuccess) return ID_ECUDA;
     const int tr = trace_begin(TraceKind::kRefine, s);
-    if (factor_skeleton(A, m, n, lda, k, J, C32, Gp, Wa, Uinv64, reinterpret_cast<double*>(base + L.gdiag), flag, s) !=
-        cudaSuccess)
+    k_check_j<<<1, kRThreads, 0, s>>>(J, k, n, flag);
+    k_gather<<<grid_for(m * k), kRThreads, 0, s>>>(A, lda, (int)m, k, n, J, C32);
+    // The Gram factor (C^T C = U^T U, U^{-1} and its operand forms) is needed only by the
+    // last two products: it runs on a side stream beside the residual products when the
+    // caller's stream is not being captured (a chain of small latency-bound launches).
+    SideStream* ss = side_stream(s);
+    cudaStream_t sg = ss ? ss->s2 : s;
+    if (ss && (cudaEventRecord(ss->fork, s) != cudaSuccess || cudaStreamWaitEvent(sg, ss->fork, 0) != cudaSuccess)) {
+        ss->mu.unlock();
         return ID_ECUDA;
-    // operands: C (m x kp), C^T (k x mp), (U^{-1})^T and U^{-1} (k x kp)
-    if (split_tf32<float>(C32, k, 0, (int)m, k, kp, fp(L.Ch), fp(L.Cl), kp, s) != cudaSuccess) return ID_ECUDA;
-    if (split_tf32<float>(C32, k, 1, k, (int)m, mp, fp(L.Cth), fp(L.Ctl), mp, s) != cudaSuccess) return ID_ECUDA;
-    if (split_tf32<double>(Uinv64, k, 1, k, k, kp, fp(L.Uth), fp(L.Utl), kp, s) != cudaSuccess) return ID_ECUDA;
-    if (split_tf32<double>(Uinv64, k, 0, k, k, kp, fp(L.Uh), fp(L.Ul), kp, s) != cudaSuccess) return ID_ECUDA;
+    }
+    bool gram_ok = factor_gram(m, k, C32, Gp, Wa, Uinv64, reinterpret_cast<double*>(base + L.gdiag), flag, sg) ==
+                       cudaSuccess &&
+                   split_tf32<double>(Uinv64, k, 1, k, k, kp, fp(L.Uth), fp(L.Utl), kp, sg) == cudaSuccess &&
+                   split_tf32<double>(Uinv64, k, 0, k, k, kp, fp(L.Uh), fp(L.Ul), kp, sg) == cudaSuccess;
+    if (ss) gram_ok = gram_ok && cudaEventRecord(ss->join, sg) == cudaSuccess;   // (waited on after the loop)
+    if (!gram_ok) {
+        if (ss) ss->mu.unlock();
+        return ID_ECUDA;
+    }
+    // operands: C (m x kp), C^T (k x mp)
+    auto fail = [&](int rc) {
+        if (ss) ss->mu.unlock();
+        return rc;
+    };
+    if (split_tf32<float>(C32, k, 0, (int)m, k, kp, fp(L.Ch), fp(L.Cl), kp, s) != cudaSuccess) return fail(ID_ECUDA);
+    if (split_tf32<float>(C32, k, 1, k, (int)m, mp, fp(L.Cth), fp(L.Ctl), mp, s) != cudaSuccess) return fail(ID_ECUDA);
     const TfOperand opC{fp(L.Ch), fp(L.Cl), kp, (int)m};
     const TfOperand opCt{fp(L.Cth), fp(L.Ctl), mp, k};
     // columns m..mp-1 of R_b^T stay zero (the products write columns < m only)
     if (mp > m && (cudaMemsetAsync(fp(L.Rth), 0, 4 * (size_t)L.nb * mp, s) != cudaSuccess ||
                    cudaMemsetAsync(fp(L.Rtl), 0, 4 * (size_t)L.nb * mp, s) != cudaSuccess))
-        return ID_ECUDA;
+        return fail(ID_ECUDA);
     // Z^T (n x kp) in operand form, once for all column blocks
-    if (split_tf32<float>(Z, ldz, 1, (int)n, k, kp, fp(L.Zth), fp(L.Ztl), kp, s) != cudaSuccess) return ID_ECUDA;
+    if (split_tf32<float>(Z, ldz, 1, (int)n, k, kp, fp(L.Zth), fp(L.Ztl), kp, s) != cudaSuccess) return fail(ID_ECUDA);
     // 5. H^T = (A - C Z)^T C by column blocks of A
     for (int64_t b0 = 0; b0 < n; b0 += L.nb) {
         const int nbb = (int)(n - b0 < L.nb ? n - b0 : L.nb);
@@ -743,16 +803,22 @@ int refine_run(const float* A, int64_t m, int64_t n, int64_t lda, int k, const i
         e1.d_trans = 1;
         int rc = gemm_tf32x3(opC, TfOperand{fp(L.Zth) + b0 * kp, fp(L.Ztl) + b0 * kp, kp, nbb}, (int)m, nbb, kp, 1, e1,
                              gst, s);
-        if (rc != ID_OK) return rc;
+        if (rc != ID_OK) return fail(rc);
         // split-K slices of H_b^T = R_b^T C (nbb x k), then their FP64 sum in operand form
         TfEpilogue e2;
         e2.d = fp(L.Part);
         e2.ldd = k;
         e2.z_stride = (int64_t)nbb * k;
         rc = gemm_tf32x3(TfOperand{fp(L.Rth), fp(L.Rtl), mp, nbb}, opCt, nbb, k, mp, L.splits, e2, gst, s);
-        if (rc != ID_OK) return rc;
+        if (rc != ID_OK) return fail(rc);
         k_reduce_split<<<grid_for((int64_t)nbb * kp), kRThreads, 0, s>>>(fp(L.Part), L.splits, nbb, k, kp,
                                                                           fp(L.Hth) + b0 * kp, fp(L.Htl) + b0 * kp);
+    }
+    // join: the products below need U^{-1}
+    if (ss) {
+        const bool jw = cudaStreamWaitEvent(s, ss->join, 0) == cudaSuccess;
+        ss->mu.unlock();
+        if (!jw) return ID_ECUDA;
     }
     // 6. Y^T = H^T U^{-1} (B(q, p) = U^{-1}(p, q)); Z += (Y^T U^{-T})^T in the epilogue (B(q, p) = U^{-1}(q, p))
     TfEpilogue e3;
