@@ -221,11 +221,19 @@ int id_solve(const void* X, id_dtype dtype, int64_t n, int64_t ldx, int64_t k,
  *   Omega  [in]  l x m BF16 row-major (uint16 bit patterns), ldo >= m, ldo a
  *                multiple of 8, 16-byte aligned; 1 <= l <= 640.
  *   Y      [out] l x n FP32 row-major, ldy >= n.
- *   work   [in]  id_sketch_workspace_size() bytes of device scratch, 256-byte aligned.
+ *   work   [in]  id_sketch_workspace_size() bytes of device scratch, 256-byte aligned;
+ *                with id_sketch_scratch_size(n, l) bytes more, a short last wave of
+ *                column tiles is split along m (the sum of the slices taken in slice
+ *                order), as id_decompose_randomized does: then Y is bit-identical to
+ *                the sketch inside id_decompose_randomized on the same device.
  *   dtype must be ID_F32. info / stream as for id_decompose.
  * Returns ID_OK, ID_EINVAL (sizes, strides, alignment), ID_ENOMEM, ID_ECUDA,
  * or ID_ETIMEOUT (through info) if a bounded device wait expired. */
 size_t id_sketch_workspace_size(void);
+/* Extra workspace bytes for the split of the last wave (0: no split for these sizes
+ * on the current device; the library must have been initialised on it, e.g. by an
+ * earlier call, for the device's SM count to be known). */
+size_t id_sketch_scratch_size(int64_t n, int64_t l);
 int id_sketch(const void* A, id_dtype dtype, int64_t m, int64_t n, int64_t lda, const uint16_t* Omega_bf16, int64_t l,
               int64_t ldo, float* Y, int64_t ldy, void* work, size_t work_bytes, id_info* info, void* stream);
 

@@ -86,6 +86,7 @@ _SIG = {
     "id_info_read": (ctypes.c_int, [_P, _P, _P]),
     "id_decompose_noalloc": (ctypes.c_int, [_P, ctypes.c_int, _I64, _I64, _I64, _I64, _P, _P, _P, _I64, _P, _P]),
     "id_sketch_workspace_size": (ctypes.c_size_t, []),
+    "id_sketch_scratch_size": (ctypes.c_size_t, [ctypes.c_int64, ctypes.c_int64]),
     "id_sketch": (ctypes.c_int, [_P, ctypes.c_int, _I64, _I64, _I64, _P, _I64, _I64, _P, _I64, _P, ctypes.c_size_t, _P,
                                  _P]),
     "id_rid_workspace_size": (ctypes.c_size_t, [_I64, _I64, _I64, _I64, _P]),
@@ -272,7 +273,10 @@ def id_sketch(A: torch.Tensor, omega: torch.Tensor, *, out: torch.Tensor | None 
         raise ValueError("omega must have A.shape[0] columns")
     dev = A.device
     Y = out if out is not None else torch.empty(l, n, dtype=torch.float32, device=dev)
-    work = torch.empty(int(lib().id_sketch_workspace_size()), dtype=torch.uint8, device=dev)
+    with torch.cuda.device(dev):
+        # with the scratch of the last wave's split: Y is bit-identical to the randomized ID's sketch
+        nbytes = int(lib().id_sketch_workspace_size()) + int(lib().id_sketch_scratch_size(n, l))
+    work = torch.empty(nbytes, dtype=torch.uint8, device=dev)
     info = IdInfo()
     with torch.cuda.device(dev):
         rc = lib().id_sketch(A.data_ptr(), ID_F32, m, n, A.stride(0), omega.data_ptr(), l, omega.stride(0),

@@ -113,6 +113,7 @@ CpqrPlan make_plan(const Layout& L, char* base, void* W, int32_t* perm, double* 
 int64_t cpqr_launch_count(id_dtype dt, int64_t m, int64_t n, int64_t k, const id_opts* opts) {
     const int nb = pick_nb(dt, (int)m, (int)n, (int)k, opts);
     int64_t c = 1;
+    if (dt == ID_F32 && cpqr_short_rows((int)m) && nb <= 32) return c;   // one launch, the WY update inside
     if (dt == ID_F32 && nb < k)
         for (int64_t je = nb; je < k; je += nb) c += 1 + (m > je ? 3 : 0);
     return c;
@@ -402,6 +403,12 @@ int id_solve(const void* X, id_dtype dtype, int64_t n, int64_t ldx, int64_t k, d
 
 size_t id_sketch_workspace_size(void) { return 1024; }
 
+size_t id_sketch_scratch_size(int64_t n, int64_t l) {
+    if (n < 1 || l < 1 || l > 640 || n > ((int64_t)1 << 31) - 1) return 0;
+    if (configure_once()) return 0;
+    return sketch_scratch_bytes(n, l);
+}
+
 size_t id_rid_workspace_size(int64_t m, int64_t n, int64_t l, int64_t k, const id_opts* opts) {
     if (m < 1 || n < 1 || k < 1 || l < k || l > 640 || l > m || m > n || !sizes_ok(l, n, k)) return 0;
     return rid_bytes(m, n, l, k, opts, nullptr);
@@ -431,11 +438,13 @@ int id_decompose_randomized(const void* A, id_dtype dtype, int64_t m, int64_t n,
     DevInfo* dinfo = reinterpret_cast<DevInfo*>(base + L.info);
     if (cudaMemsetAsync(dinfo, 0, sizeof(DevInfo), s) != cudaSuccess) return ID_ECUDA;
     if (cudaMemsetAsync(sk_status, 0, sizeof(int), s) != cudaSuccess) return ID_ECUDA;
-    // 1. Y = Omega A (tensor cores)
-    int rc = sketch_run(static_cast<const float*>(A), m, n, lda, Omega_bf16, l, ldo, Y, ldy, sk_status, s);
+    // 1. Y = Omega A (tensor cores); the CPQR's working matrix, not yet in use, is the
+    // scratch of the sketch's K-split last wave
+    CpqrPlan P = make_plan(L, base, nullptr, nullptr, nullptr, (int)k, l, n);
+    int rc = sketch_run(static_cast<const float*>(A), m, n, lda, Omega_bf16, l, ldo, Y, ldy, sk_status, s,
+                        static_cast<float*>(P.W), sizeof(float) * (size_t)P.ldw * (size_t)n);
     if (rc != ID_OK) return rc;
     // 2. k-step CPQR of Y (FP32 matrix, FP64 norms), 3. T = R11^{-1} R12 of Y in FP64, 4. Z
-    CpqrPlan P = make_plan(L, base, nullptr, nullptr, nullptr, (int)k, l, n);
     if (copy_in<float>(Y, ldy, 0, P, s) != cudaSuccess) return ID_ECUDA;
     if (cpqr_run<float>(P, s) != cudaSuccess) return ID_ECUDA;
     double* Tm = reinterpret_cast<double*>(base + L.T);
@@ -586,7 +595,12 @@ int id_sketch(const void* A, id_dtype dtype, int64_t m, int64_t n, int64_t lda, 
     DevInfo* dinfo = reinterpret_cast<DevInfo*>(base);
     State* st = reinterpret_cast<State*>(base + align_up(sizeof(DevInfo)));
     if (cudaMemsetAsync(work, 0, id_sketch_workspace_size(), s) != cudaSuccess) return ID_ECUDA;
-    const int rc = sketch_run(static_cast<const float*>(A), m, n, lda, Omega_bf16, l, ldo, Y, ldy, &st->status, s);
+    // the split of a short last wave, when the caller's workspace has room for it
+    float* scratch = work_bytes >= id_sketch_workspace_size() + sketch_scratch_bytes(n, l)
+                         ? reinterpret_cast<float*>(base + id_sketch_workspace_size())
+                         : nullptr;
+    const int rc = sketch_run(static_cast<const float*>(A), m, n, lda, Omega_bf16, l, ldo, Y, ldy, &st->status, s,
+                              scratch, work_bytes - id_sketch_workspace_size());
     if (rc != ID_OK) return rc;
     if (finalize_info(st, dinfo, 0, 0, 0, s) != cudaSuccess) return ID_ECUDA;
     if (info) return read_info(work, info, s);
@@ -600,8 +614,10 @@ int id_info_read(const void* work, id_info* info, void* stream) {
 
 int64_t id_rid_launch_count(int64_t m, int64_t n, int64_t l, int64_t k, const id_opts* opts) {
     if (id_rid_workspace_size(m, n, l, k, opts) == 0) return -1;
-    // sketch, copy-in, CPQR of the sketch, solve (when n > k), Z scatter, status, refinement
-    return 4 + cpqr_launch_count(ID_F32, l, n, k, opts) + (n > k ? 1 : 0) +
+    // sketch (and the sum of its K-split last wave), copy-in, CPQR of the sketch, solve (when
+    // n > k), Z scatter, status, refinement
+    const size_t w_bytes = sizeof(float) * (size_t)round_up(l, 8) * (size_t)n;
+    return 3 + sketch_launch_count(n, l, w_bytes) + cpqr_launch_count(ID_F32, l, n, k, opts) + (n > k ? 1 : 0) +
            (rid_refine(opts) ? refine_launch_count(m, n, k) : 0);
 }
 

@@ -945,7 +945,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_cpqr(KParams P) {
 
 // ------------------------------------------------------------------- host --
 // Short FP32 matrices (at most 640 rows) with panels of at most 32 run on the
-// short-matrix kernel (cpqr_short.cu), one launch per panel. FP32 only: it
+// short-matrix kernel (cpqr_short.cu), one launch for all panels. FP32 only: it
 // keeps the panel's reflectors and the staged columns in shared memory.
 template <typename T>
 static bool use_short(int m, int nb) {
@@ -1118,16 +1118,22 @@ cudaError_t cpqr_run(const CpqrPlan& P, cudaStream_t s) {
     // between per-panel launches of k_cpqr (which then skips its phase C).
     K.wy_outside = (sizeof(T) == 4 && P.nb < P.k && P.wy_ws != nullptr) ? 1 : 0;
     const int step = K.wy_outside ? P.nb : P.k;
-    // the short-matrix kernel takes one panel per launch
-    const bool shortk = use_short<T>(P.m, P.nb) && step <= kWarp;
-    if (use_short<T>(P.m, P.nb) && !shortk) return cudaErrorInvalidConfiguration;
+    // the short-matrix kernel runs every panel in one launch (its WY update inside)
+    const bool shortk = use_short<T>(P.m, P.nb);
     const int tr = trace_begin(TraceKind::kCpqr, s);
+    if (shortk) {
+        K.j_begin = 0;
+        K.j_end = P.k;
+        e = cpqr_short_launch(K, G, s);
+        if (e != cudaSuccess) return e;
+        trace_end(tr, s);
+        return cudaGetLastError();
+    }
     for (int j0 = 0; j0 < P.k; j0 += step) {
         K.j_begin = j0;
         K.j_end = j0 + step < P.k ? j0 + step : P.k;
         if (j0 > 0 && (e = cudaMemsetAsync(K.bar, 0, 64, s)) != cudaSuccess) return e;   // fresh barrier epochs
-        if (shortk) e = cpqr_short_launch(K, G, s);
-        else if (pl.smem_v) e = cudaLaunchKernelEx(&cfg, k_cpqr<T, true>, K);
+        if (pl.smem_v) e = cudaLaunchKernelEx(&cfg, k_cpqr<T, true>, K);
         else e = cudaLaunchKernelEx(&cfg, k_cpqr<T, false>, K);
         if (e != cudaSuccess) return e;
         if (K.wy_outside && K.j_end < P.k && P.m > K.j_end && wy_update_f32(P, j0, K.j_end, s) != ID_OK)

@@ -49,6 +49,7 @@ cudaError_t csr_in(const int64_t* rowptr, const int32_t* colind, const void* val
                    int trans, const CpqrPlan& P, int* status, cudaStream_t s);
 template <typename T> cudaError_t cpqr_run(const CpqrPlan& P, cudaStream_t s);
 template <typename T> int cpqr_grid(int m, int nb);   // CTAs of the cooperative launch (0: cannot launch)
+bool cpqr_short_rows(int m);   // FP32 matrices with this many rows (and panels of at most 32) take the short kernel
 
 // Back substitution T = R11^{-1} R12 (FP64) and Z assembly.
 // T = R11^{-1} R12 (FP64 arithmetic; FP32 when fp32_arith and T = float, for a
@@ -62,8 +63,12 @@ cudaError_t solve_configure();
 
 // Y = Omega A on tcgen05 tensor cores (sketch.cu). Returns an id_status.
 cudaError_t sketch_configure();
+// scratch (optional, 16-byte aligned): room for the K slices of a short last
+// wave of column tiles (sketch_scratch_bytes); without it no tile is split.
 int sketch_run(const float* A, int64_t m, int64_t n, int64_t lda, const uint16_t* Om, int64_t l, int64_t ldo, float* Y,
-               int64_t ldy, int* status, cudaStream_t s);
+               int64_t ldy, int* status, cudaStream_t s, float* scratch = nullptr, size_t scratch_bytes = 0);
+size_t sketch_scratch_bytes(int64_t n, int64_t l);
+int sketch_launch_count(int64_t n, int64_t l, size_t scratch_bytes);
 cudaError_t finalize_info(const State* st, DevInfo* info, int k, int transposed, int nb, cudaStream_t s,
                           const int* extra_status = nullptr);
 // info->err_est from the CPQR's residual column norms (after finalize_info).

@@ -274,11 +274,12 @@ __device__ __forceinline__ void tl_stamp(const KParams& P, int j, int q) {
 }
 
 // The short-matrix CPQR kernel (cpqr_short.cu): FP32, at most 640 rows,
-// panels of at most 32 pivots, one cooperative launch per panel.
+// panels of at most 32 pivots, one cooperative launch (the compact-WY
+// update between panels inside the kernel).
 cudaError_t cpqr_short_configure();
 bool cpqr_short_rows(int m);
 int cpqr_short_grid();   // CTAs of its cooperative launch (0: cannot launch)
-// Steps K.j_begin .. K.j_end - 1 (one panel; phase 0 when j_begin = 0).
+// Steps K.j_begin .. K.j_end - 1 (phase 0 when j_begin = 0; K.j_begin a multiple of K.nb).
 cudaError_t cpqr_short_launch(const KParams& K, int grid, cudaStream_t s);
 
 }  // namespace gbid

@@ -2,8 +2,8 @@
 // rows, panels of at most 32 pivots), for sm_103a: the CPQR of the sketch
 // Y = Omega A of a randomized ID (Sec. 2.1 applied to Y as in Sec. 2.2).
 //
-// One persistent cooperative launch per panel, one CTA of 512 threads per SM,
-// one grid barrier per pivot step. Step j (jj = j - j0 inside the panel):
+// One persistent cooperative launch for all k steps, one CTA of 512 threads per
+// SM, one grid barrier per pivot step. Step j (jj = j - j0 inside its panel):
 //   A. every CTA reads the previous step's argmax partials (largest squared
 //      residual norm, ties to the smallest original index) and forms the pivot
 //      column x = W(j:m, p) - V(j:m, 0:jj) F(p, 0:jj)^T from its shared-memory
@@ -17,6 +17,9 @@
 //      R(j, l) = W(j, l) - F(l, 0:jj) V(j, 0:jj)^T - F(l, jj), the FP64
 //      downdate of the squared norm (exact recompute on cancellation) and the
 //      CTA's argmax partial.                                 -- grid barrier
+//   D. at a panel's last step, the compact-WY update of the trailing columns,
+//      W(je:m, l) -= V(je:m, :) F(l, :)^T, each CTA on its share of the
+//      columns from its panel copy and the F rows.           -- grid barrier
 // The trailing product is latency-bound (one L2 round trip per column group
 // and warp): a group of TPC threads takes one column (TPC = 16, 8, 4 or 2,
 // picked each step so that a thread holds at most 12 vector loads of its
@@ -43,6 +46,7 @@ constexpr int kSMaxRows = 640;                          // the short-matrix boun
 constexpr int kSUnits = kSMaxRows / (kWarp * 4);        // 16-byte chunks per lane and column
 constexpr int kSRows = (kSMaxRows + kSThreads - 1) / kSThreads;   // rows per thread in phase A
 constexpr int kSPanel = 32;                             // widest panel
+constexpr int kSWyCols = 256;                           // columns per chunk of the in-kernel WY update
 
 // Shared-memory layout of one panel launch (floats; every region 16-byte aligned).
 struct SLayout {
@@ -80,6 +84,7 @@ __global__ void __launch_bounds__(kSThreads, 1) k_cpqr_short(const __grid_consta
     float* fj_s = fco + kSPanel;                   // 32: F(j, 0:jj), the row that moves to position p
     float* vrow_s = fj_s + kSPanel;                // 32: V(j, 0:jj)
     float* aux_s = vrow_s + kSPanel;               // 32: aux
+    float* ftile = aux_s + kSPanel;                // kSWyCols x 32: F rows of the WY update's columns
     __shared__ float red[kSWarps][kWarp];
     __shared__ float scf[4];       // beta, tau, scale
     __shared__ double swd[2];      // the old position j's vn1, vn2 (the column that moves to p)
@@ -139,10 +144,10 @@ __global__ void __launch_bounds__(kSThreads, 1) k_cpqr_short(const __grid_consta
         grid_sync(P.bar, epoch, st);
     }
 
-    const int j0 = P.j_begin;   // one panel per launch
-    double r00 = j0 > 0 ? ld(&st->r00) : 0.0;   // |R_00| (kept by thread 31, which forms the reflectors)
-    for (int j = j0; j < P.j_end; ++j) {
+    double r00 = P.j_begin > 0 ? ld(&st->r00) : 0.0;   // |R_00| (kept by thread 31, which forms the reflectors)
+    for (int j = P.j_begin; j < P.j_end; ++j) {
         tl_stamp(P, j, 0);
+        const int j0 = j / P.nb * P.nb;   // the panel's first step
         const int jj = j - j0;
         const int j_al = j & ~3;
         const int rows = m_pad - j_al;   // staged rows of this step (<= len)
@@ -523,6 +528,55 @@ __global__ void __launch_bounds__(kSThreads, 1) k_cpqr_short(const __grid_consta
         if (t == 0) P.part[blockIdx.x] = bestc;
         grid_sync(P.bar, epoch, st);
         tl_stamp(P, j, 5);
+
+        // ---- compact-WY update at a panel's end: W(je:m, l) -= V(je:m, 0:nb) F(l, 0:nb)^T for
+        // every trailing column l (this CTA's balanced share), from the panel copy and the
+        // panel's F rows. Lane = row (coalesced reads and writes of W), the row's V(i, :) in
+        // registers, each column's F row broadcast from shared memory: FMA-bound.
+        if (jj == P.nb - 1 && j + 1 < P.j_end && j + 1 < m) {
+            const int je = j + 1;
+            const int nw = n - je;
+            const int perw = nw / G, remw = nw % G;
+            const int w_lo = je + (int)blockIdx.x * perw + min((int)blockIdx.x, remw);
+            const int w_cnt = perw + ((int)blockIdx.x < remw ? 1 : 0);
+            const int nrc = (m - je + kWarp - 1) / kWarp;   // row chunks of 32
+            const int cs = max(1, kSWarps / nrc);          // column splits (every warp busy)
+            for (int cb = 0; cb < w_cnt; cb += kSWyCols) {
+                const int cn = min(kSWyCols, w_cnt - cb);
+                __syncthreads();   // the previous chunk's F rows are no longer read
+                for (int e = t; e < cn * kSPanel; e += kSThreads) {
+                    const int q = e / kSPanel, c = e % kSPanel;
+                    ftile[e] = c <= jj ? ld(F + (int64_t)(w_lo + cb + q) * ldf + c) : 0.0f;
+                }
+                __syncthreads();
+                for (int task = w; task < nrc * cs; task += kSWarps) {
+                    const int rc = task % nrc, cq = task / nrc;
+                    const int i = je + rc * kWarp + lane;
+                    const bool row_ok = i < m;
+                    float vr[kSPanel];
+#pragma unroll
+                    for (int c = 0; c < kSPanel; ++c) vr[c] = (row_ok && c <= jj) ? vpan[c * L.ldp + (i - L.r0)] : 0.0f;
+                    const int q0 = cq * cn / cs, q1 = (cq + 1) * cn / cs;
+                    for (int q = q0; q < q1; ++q) {
+                        const float4* f4 = reinterpret_cast<const float4*>(ftile + q * kSPanel);
+                        float acc = 0.0f;
+#pragma unroll
+                        for (int u = 0; u < kSPanel / 4; ++u) {
+                            const float4 f = f4[u];
+                            acc = fmaf(vr[4 * u], f.x, acc);
+                            acc = fmaf(vr[4 * u + 1], f.y, acc);
+                            acc = fmaf(vr[4 * u + 2], f.z, acc);
+                            acc = fmaf(vr[4 * u + 3], f.w, acc);
+                        }
+                        if (row_ok) {
+                            float* wp = W + (int64_t)(w_lo + cb + q) * ldw + i;
+                            *wp = ld(wp) - acc;
+                        }
+                    }
+                }
+            }
+            grid_sync(P.bar, epoch, st);   // the next panel reads the updated columns
+        }
     }
 }
 
@@ -541,7 +595,7 @@ SLayout short_layout(int m, int j0) {
 }
 
 size_t short_bytes(const SLayout& L) {
-    return sizeof(float) * ((size_t)kSPanel * L.ldp + (L.len + 8) + L.len + 4 * kSPanel);
+    return sizeof(float) * ((size_t)kSPanel * L.ldp + (L.len + 8) + L.len + 4 * kSPanel + (size_t)kSWyCols * kSPanel);
 }
 
 }  // namespace
@@ -572,7 +626,7 @@ cudaError_t cpqr_short_launch(const KParams& K, int grid, cudaStream_t s) {
     SParams SP;
     SP.K = K;
     SP.L = short_layout(K.m, K.j_begin);
-    if (grid < 1 || grid > kSThreads || K.j_end - K.j_begin > kSPanel || !cpqr_short_rows(K.m))
+    if (grid < 1 || grid > kSThreads || K.nb < 1 || K.nb > kSPanel || !cpqr_short_rows(K.m))
         return cudaErrorInvalidConfiguration;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);

@@ -16,6 +16,10 @@
 // Epilogue: warps 2-9 read the accumulators with tcgen05.ld (each warp its
 // 32-lane quarter of TMEM, two warps per quarter splitting the 32-column
 // chunks) and store Y. kStages stages are in flight.
+// One CTA fits an SM, so the column tiles run in waves of #SMs CTAs. When the
+// last wave would be short, its tiles are split along K into `parts` slices
+// (one more CTA each) so that it fills the SMs; the slices' accumulators go
+// to a scratch buffer and k_sketch_tail sums them in slice order.
 // Every mbarrier wait is bounded; on expiry the kernel records a timeout,
 // stops issuing, waits (bounded) for work already issued and frees its TMEM.
 #include <cuda.h>
@@ -23,6 +27,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "common.cuh"
@@ -136,6 +141,10 @@ struct SkParams {
     float* Y;
     int64_t ldy;
     int* status;
+    int n_full;       // CTAs 0 .. n_full - 1 take whole column tiles
+    int parts;        // the later CTAs take K slices of the remaining tiles
+    int kb_part;      // K blocks per slice
+    float* scratch;   // slice (t, p) of tail tile t: M x BN floats at ((t parts + p) M) BN
 };
 
 // Dynamic shared memory, 1024-byte aligned: per stage, MB Omega blocks
@@ -160,8 +169,17 @@ __global__ void __launch_bounds__(kSkThreads, 1) k_sketch(const __grid_constant_
 
     const int t = threadIdx.x, w = t / 32, lane = t % 32;
     const int MB = P.MB, BN = P.BN;
-    const int n0 = blockIdx.x * BN;
-    const int KB = (P.K + kBK - 1) / kBK;
+    const int KB_all = (P.K + kBK - 1) / kBK;
+    int tile = blockIdx.x, part = -1, kb_lo = 0, kb_hi = KB_all;
+    if ((int)blockIdx.x >= P.n_full) {
+        const int q = blockIdx.x - P.n_full;
+        tile = P.n_full + q / P.parts;
+        part = q % P.parts;
+        kb_lo = part * P.kb_part;
+        kb_hi = min(KB_all, kb_lo + P.kb_part);
+    }
+    const int n0 = tile * BN;
+    const int KB = kb_hi - kb_lo;   // this CTA's K blocks (>= 1: the host sizes the slices)
     const size_t SB = sk_stage_bytes(MB, BN);
     unsigned char* base = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(sk_raw) + 1023) & ~static_cast<uintptr_t>(1023));
@@ -202,8 +220,9 @@ __global__ void __launch_bounds__(kSkThreads, 1) k_sketch(const __grid_constant_
                 const unsigned use = kb / kStages;
                 if (use > 0 && !mb_wait(&empty[s], (use - 1) & 1u, abrt)) break;
                 mb_expect_tx(&full[s], bytes);
-                for (int mb = 0; mb < MB; ++mb) tma_load_2d(om_tile(s, mb), &tm_om, kb * kBK, mb * 128, &full[s]);
-                tma_load_2d(af_tile(s), &tm_a, n0, kb * kBK, &full[s]);
+                const int kx = (kb_lo + kb) * kBK;
+                for (int mb = 0; mb < MB; ++mb) tma_load_2d(om_tile(s, mb), &tm_om, kx, mb * 128, &full[s]);
+                tma_load_2d(af_tile(s), &tm_a, n0, kx, &full[s]);
             }
         }
         __syncwarp();
@@ -267,7 +286,15 @@ __global__ void __launch_bounds__(kSkThreads, 1) k_sketch(const __grid_constant_
                     uint32_t r[32];
                     TMEM_LD_X32(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(mb * BN + c0), r);
                     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                    if (row < P.M) {
+                    if (row < P.M && part >= 0) {
+                        // a K slice: the whole 32-column chunk to the scratch (16-byte stores)
+                        float4* y4 = reinterpret_cast<float4*>(
+                            P.scratch + ((int64_t)((tile - P.n_full) * P.parts + part) * P.M + row) * BN + c0);
+#pragma unroll
+                        for (int q = 0; q < 8; ++q)
+                            y4[q] = make_float4(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1]),
+                                                __uint_as_float(r[4 * q + 2]), __uint_as_float(r[4 * q + 3]));
+                    } else if (row < P.M) {
                         float* yrow = P.Y + (int64_t)row * P.ldy + n0 + c0;
                         const int lim = min(32, P.N - (n0 + c0));
                         if (lim == 32 && (P.ldy & 3) == 0 && (reinterpret_cast<uintptr_t>(P.Y) & 15) == 0) {
@@ -300,6 +327,24 @@ __global__ void __launch_bounds__(kSkThreads, 1) k_sketch(const __grid_constant_
     if (w == 0) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+    }
+}
+
+// Y(row, n0 + c) of the split tail tiles: the sum of their K slices in slice order.
+__global__ void __launch_bounds__(256) k_sketch_tail(const float* __restrict__ scratch, int n_full, int ntail,
+                                                     int parts, int M, int N, int BN, float* __restrict__ Y,
+                                                     int64_t ldy) {
+    const int64_t total = (int64_t)ntail * M * BN;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(e % BN);
+        const int64_t rt = e / BN;
+        const int row = (int)(rt % M), ti = (int)(rt / M);
+        const int col = (n_full + ti) * BN + c;
+        if (col >= N) continue;
+        float v = 0.0f;
+        for (int p = 0; p < parts; ++p) v += scratch[((int64_t)(ti * parts + p) * M + row) * BN + c];
+        Y[(int64_t)row * ldy + col] = v;
     }
 }
 
@@ -345,13 +390,48 @@ int sketch_bn(int MB) {
 
 }  // namespace
 
+namespace {
+int g_sk_nsm = 0;   // SMs of the device (set by sketch_configure)
+
+// The tail split of n columns: slices per tail tile (1: no split) and whole tiles.
+void sketch_split(int64_t n, int BN, int* n_full, int* parts, int* ntail) {
+    const int tiles = (int)((n + BN - 1) / BN);
+    *n_full = tiles;
+    *parts = 1;
+    *ntail = 0;
+    if (g_sk_nsm < 1) return;
+    const int tail = tiles % g_sk_nsm;
+    if (tail == 0 || tiles < g_sk_nsm) return;
+    const int p = std::min(8, g_sk_nsm / tail);
+    if (p < 2) return;
+    *n_full = tiles - tail;
+    *parts = p;
+    *ntail = tail;
+}
+}  // namespace
+
 cudaError_t sketch_configure() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&g_sk_nsm, cudaDevAttrMultiProcessorCount, dev);
     return cudaFuncSetAttribute(k_sketch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSkSmemMax);
+}
+
+size_t sketch_scratch_bytes(int64_t n, int64_t l) {
+    const int MB = (int)((l + 127) / 128);
+    if (MB < 1 || MB > kMaxMB) return 0;
+    int n_full, parts, ntail;
+    sketch_split(n, sketch_bn(MB), &n_full, &parts, &ntail);
+    return (size_t)ntail * parts * (size_t)l * sketch_bn(MB) * sizeof(float);
+}
+
+int sketch_launch_count(int64_t n, int64_t l, size_t scratch_bytes) {
+    const size_t need = sketch_scratch_bytes(n, l);
+    return 1 + (need > 0 && scratch_bytes >= need ? 1 : 0);
 }
 
 // Y (l x n, ldy) = Omega (l x m BF16, ldo) * A (m x n FP32, lda). Returns an id_status.
 int sketch_run(const float* A, int64_t m, int64_t n, int64_t lda, const uint16_t* Om, int64_t l, int64_t ldo, float* Y,
-               int64_t ldy, int* status, cudaStream_t s) {
+               int64_t ldy, int* status, cudaStream_t s, float* scratch, size_t scratch_bytes) {
     const int MB = (int)((l + 127) / 128);
     if (MB < 1 || MB > kMaxMB) return ID_EINVAL;
     const int BN = sketch_bn(MB);
@@ -371,11 +451,31 @@ int sketch_run(const float* A, int64_t m, int64_t n, int64_t lda, const uint16_t
     P.Y = Y;
     P.ldy = ldy;
     P.status = status;
+    int n_full, parts, ntail;
+    sketch_split(n, BN, &n_full, &parts, &ntail);
+    const int KB = (int)((m + kBK - 1) / kBK);
+    const size_t need = (size_t)ntail * parts * (size_t)l * BN * sizeof(float);
+    if (ntail == 0 || scratch == nullptr || scratch_bytes < need || (reinterpret_cast<uintptr_t>(scratch) & 15) ||
+        KB < parts) {
+        n_full = (int)((n + BN - 1) / BN);   // no split: every CTA a whole tile
+        parts = 1;
+        ntail = 0;
+    }
+    P.kb_part = (KB + parts - 1) / parts;
+    parts = (KB + P.kb_part - 1) / P.kb_part;   // every slice non-empty
+    P.n_full = n_full;
+    P.parts = parts;
+    P.scratch = scratch;
     const size_t smem = (size_t)kStages * sk_stage_bytes(MB, BN) + 1024;
     if (smem > kSkSmemMax) return ID_EINVAL;
-    const int grid = (int)((n + BN - 1) / BN);
+    const int grid = n_full + ntail * parts;
     const int tr = trace_begin(TraceKind::kSketch, s);
     k_sketch<<<grid, kSkThreads, smem, s>>>(tm_om, tm_a, P);
+    if (ntail > 0) {
+        const int64_t tot = (int64_t)ntail * l * BN;
+        k_sketch_tail<<<(int)std::min<int64_t>((tot + 255) / 256, 4096), 256, 0, s>>>(scratch, n_full, ntail, parts,
+                                                                                    (int)l, (int)n, BN, Y, ldy);
+    }
     trace_end(tr, s);
     return cudaGetLastError() == cudaSuccess ? ID_OK : ID_ECUDA;
 }
