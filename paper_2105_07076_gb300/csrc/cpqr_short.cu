@@ -47,6 +47,7 @@ constexpr int kSUnits = kSMaxRows / (kWarp * 4);        // 16-byte chunks per la
 constexpr int kSRows = (kSMaxRows + kSThreads - 1) / kSThreads;   // rows per thread in phase A
 constexpr int kSPanel = 32;                             // widest panel
 constexpr int kSWyCols = 256;                           // columns per chunk of the in-kernel WY update
+constexpr int kSWyBatch = 16;                           // WY columns whose W loads are in flight together
 
 // Shared-memory layout of one panel launch (floats; every region 16-byte aligned).
 struct SLayout {
@@ -540,7 +541,6 @@ __global__ void __launch_bounds__(kSThreads, 1) k_cpqr_short(const __grid_consta
             const int w_lo = je + (int)blockIdx.x * perw + min((int)blockIdx.x, remw);
             const int w_cnt = perw + ((int)blockIdx.x < remw ? 1 : 0);
             const int nrc = (m - je + kWarp - 1) / kWarp;   // row chunks of 32
-            const int cs = max(1, kSWarps / nrc);          // column splits (every warp busy)
             for (int cb = 0; cb < w_cnt; cb += kSWyCols) {
                 const int cn = min(kSWyCols, w_cnt - cb);
                 __syncthreads();   // the previous chunk's F rows are no longer read
@@ -549,6 +549,8 @@ __global__ void __launch_bounds__(kSThreads, 1) k_cpqr_short(const __grid_consta
                     ftile[e] = c <= jj ? ld(F + (int64_t)(w_lo + cb + q) * ldf + c) : 0.0f;
                 }
                 __syncthreads();
+                // column splits: about four tasks per warp, of at least kSWyBatch columns each
+                const int cs = max(1, min(cn / kSWyBatch, (4 * kSWarps + nrc - 1) / nrc));
                 for (int task = w; task < nrc * cs; task += kSWarps) {
                     const int rc = task % nrc, cq = task / nrc;
                     const int i = je + rc * kWarp + lane;
@@ -557,20 +559,27 @@ __global__ void __launch_bounds__(kSThreads, 1) k_cpqr_short(const __grid_consta
 #pragma unroll
                     for (int c = 0; c < kSPanel; ++c) vr[c] = (row_ok && c <= jj) ? vpan[c * L.ldp + (i - L.r0)] : 0.0f;
                     const int q0 = cq * cn / cs, q1 = (cq + 1) * cn / cs;
-                    for (int q = q0; q < q1; ++q) {
-                        const float4* f4 = reinterpret_cast<const float4*>(ftile + q * kSPanel);
-                        float acc = 0.0f;
+                    // kSWyBatch columns per L2 round trip: their W(i, l) loads go out together
+                    for (int qb = q0; qb < q1; qb += kSWyBatch) {
+                        float wv[kSWyBatch];
 #pragma unroll
-                        for (int u = 0; u < kSPanel / 4; ++u) {
-                            const float4 f = f4[u];
-                            acc = fmaf(vr[4 * u], f.x, acc);
-                            acc = fmaf(vr[4 * u + 1], f.y, acc);
-                            acc = fmaf(vr[4 * u + 2], f.z, acc);
-                            acc = fmaf(vr[4 * u + 3], f.w, acc);
-                        }
-                        if (row_ok) {
-                            float* wp = W + (int64_t)(w_lo + cb + q) * ldw + i;
-                            *wp = ld(wp) - acc;
+                        for (int u = 0; u < kSWyBatch; ++u)
+                            wv[u] = (row_ok && qb + u < q1) ? ld(W + (int64_t)(w_lo + cb + qb + u) * ldw + i) : 0.0f;
+#pragma unroll
+                        for (int u = 0; u < kSWyBatch; ++u) {
+                            if (qb + u < q1) {
+                                const float4* f4 = reinterpret_cast<const float4*>(ftile + (qb + u) * kSPanel);
+                                float acc = 0.0f;
+#pragma unroll
+                                for (int e = 0; e < kSPanel / 4; ++e) {
+                                    const float4 f = f4[e];
+                                    acc = fmaf(vr[4 * e], f.x, acc);
+                                    acc = fmaf(vr[4 * e + 1], f.y, acc);
+                                    acc = fmaf(vr[4 * e + 2], f.z, acc);
+                                    acc = fmaf(vr[4 * e + 3], f.w, acc);
+                                }
+                                if (row_ok) W[(int64_t)(w_lo + cb + qb + u) * ldw + i] = wv[u] - acc;
+                            }
                         }
                     }
                 }

@@ -132,6 +132,7 @@ def test_lowrank_200x400_k20_f32(gbid):
     ((333, 517), 37, 0), ((333, 517), 37, 5), ((333, 517), 37, 16),
     ((37, 1000), 10, 0), ((1, 7), 1, 0), ((5, 9), 5, 0), ((64, 96), 64, 0), ((48, 48), 48, 7),
     ((517, 333), 29, 0), ((1000, 37), 12, 4), ((257, 1031), 64, 32),
+    ((700, 1500), 100, 16),   # FP32: more rows than the short kernel takes, so the tensor-core WY update
 ])
 def test_shapes(gbid, dtype, shape, k, nb):
     rng = np.random.default_rng(hash((shape, k, nb)) % 2**32)
