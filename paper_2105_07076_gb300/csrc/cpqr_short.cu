@@ -35,6 +35,8 @@
 #include "common.cuh"
 #include "cpqr.cuh"
 #include "cpqr_dev.cuh"
+#include "gemm.cuh"
+#include "tc.cuh"
 
 namespace gbid {
 
@@ -46,8 +48,14 @@ constexpr int kSMaxRows = 640;                          // the short-matrix boun
 constexpr int kSUnits = kSMaxRows / (kWarp * 4);        // 16-byte chunks per lane and column
 constexpr int kSRows = (kSMaxRows + kSThreads - 1) / kSThreads;   // rows per thread in phase A
 constexpr int kSPanel = 32;                             // widest panel
-constexpr int kSWyCols = 256;                           // columns per chunk of the in-kernel WY update
-constexpr int kSWyBatch = 16;                           // WY columns whose W loads are in flight together
+// In-kernel compact-WY update on the tensor cores: per CTA, tiles of 128 columns
+// (the MMA's M, operand A = their F rows) by 256 rows (its N, operand B = the
+// panel's V rows), K = the panel width (two 16-wide K blocks), 3xTF32 into a
+// 256-column tensor-memory accumulator.
+constexpr int kWyM = 128, kWyN = 256;
+constexpr int kWyTileA = kWyM * 64, kWyTileB = kWyN * 64;   // bytes of one 64-byte-swizzled K16 tile
+constexpr int kWyBytes = 4 * kWyTileA + 4 * kWyTileB;       // A and B: hi and lo, two K16 blocks each
+constexpr unsigned long long kWySpin = 1ull << 24;
 
 // Shared-memory layout of one panel launch (floats; every region 16-byte aligned).
 struct SLayout {
@@ -85,14 +93,32 @@ __global__ void __launch_bounds__(kSThreads, 1) k_cpqr_short(const __grid_consta
     float* fj_s = fco + kSPanel;                   // 32: F(j, 0:jj), the row that moves to position p
     float* vrow_s = fj_s + kSPanel;                // 32: V(j, 0:jj)
     float* aux_s = vrow_s + kSPanel;               // 32: aux
-    float* ftile = aux_s + kSPanel;                // kSWyCols x 32: F rows of the WY update's columns
+    // the WY update's operand tiles (1024-byte aligned for the 64-byte swizzle)
+    unsigned char* wy_ops = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(aux_s + kSPanel) + 1023) & ~static_cast<uintptr_t>(1023));
     __shared__ float red[kSWarps][kWarp];
     __shared__ float scf[4];       // beta, tau, scale
     __shared__ double swd[2];      // the old position j's vn1, vn2 (the column that moves to p)
     __shared__ int swi;            // its original index
     __shared__ float x0_s;
     __shared__ int stop_s;
+    __shared__ __align__(8) uint64_t wy_bar;   // completion of the WY update's MMAs
+    __shared__ uint32_t wy_tmem;               // its tensor-memory accumulator
+    __shared__ int wy_abort;                   // a bounded wait on wy_bar gave up
     const uint64_t pol_last = l2_policy(true), pol_first = l2_policy(false);
+    const bool wy_on = P.nb < P.j_end - P.j_begin;   // more than one panel: WY updates between them
+    if (wy_on) {
+        if (t == 0) {
+            wy_abort = 0;
+            tc::mb_init(&wy_bar, 1);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        if (w == 0) tc::tmem_alloc(&wy_tmem, kWyN);
+        tc::fence_before();
+        __syncthreads();
+        tc::fence_after();
+    }
+    unsigned wy_phase = 0;   // parity of wy_bar's next completion
 
     // ---- squared column norms, perm, first argmax partials (the first panel only).
     // Each warp takes whole columns; the squares are summed in FP32 pairs after a
@@ -530,62 +556,116 @@ __global__ void __launch_bounds__(kSThreads, 1) k_cpqr_short(const __grid_consta
         grid_sync(P.bar, epoch, st);
         tl_stamp(P, j, 5);
 
-        // ---- compact-WY update at a panel's end: W(je:m, l) -= V(je:m, 0:nb) F(l, 0:nb)^T for
-        // every trailing column l (this CTA's balanced share), from the panel copy and the
-        // panel's F rows. Lane = row (coalesced reads and writes of W), the row's V(i, :) in
-        // registers, each column's F row broadcast from shared memory: FMA-bound.
-        if (jj == P.nb - 1 && j + 1 < P.j_end && j + 1 < m) {
+        // ---- compact-WY update at a panel's end on the tensor cores:
+        // W(je:m, l) -= V(je:m, 0:nb) F(l, 0:nb)^T for this CTA's balanced share of the trailing
+        // columns, as D(i, l) = sum_c V(i, c) F(l, c) (3xTF32: the operands split into TF32 hi and
+        // lo parts and written in the 64-byte-swizzled K-major layout the MMA reads; A = 128 rows
+        // of the panel's reflectors, B = 256 columns' F rows) and an epilogue that subtracts D from
+        // W (TMEM lane = row i, so a warp's accesses to one column coalesce).
+        if (wy_on && jj == P.nb - 1 && j + 1 < P.j_end && j + 1 < m) {
             const int je = j + 1;
             const int nw = n - je;
             const int perw = nw / G, remw = nw % G;
             const int w_lo = je + (int)blockIdx.x * perw + min((int)blockIdx.x, remw);
             const int w_cnt = perw + ((int)blockIdx.x < remw ? 1 : 0);
-            const int nrc = (m - je + kWarp - 1) / kWarp;   // row chunks of 32
-            for (int cb = 0; cb < w_cnt; cb += kSWyCols) {
-                const int cn = min(kSWyCols, w_cnt - cb);
-                __syncthreads();   // the previous chunk's F rows are no longer read
-                for (int e = t; e < cn * kSPanel; e += kSThreads) {
-                    const int q = e / kSPanel, c = e % kSPanel;
-                    ftile[e] = c <= jj ? ld(F + (int64_t)(w_lo + cb + q) * ldf + c) : 0.0f;
+            const int nrow = m - je;
+            const uint32_t idesc = tc::idesc_tf32(kWyM, kWyN);
+            // element (r, c) of a K16 tile at r * 64 + ((c / 4) ^ ((r >> 1) & 3)) * 16 + (c % 4) * 4
+            auto put = [&](unsigned char* tile_hi, unsigned char* tile_lo, int r, int c, float x) {
+                const int off = r * 64 + (((c >> 2) ^ ((r >> 1) & 3)) << 4) + ((c & 3) << 2);
+                const float h = tf32_hi(x);
+                *reinterpret_cast<float*>(tile_hi + off) = h;
+                *reinterpret_cast<float*>(tile_lo + off) = x - h;
+            };
+            unsigned char* a_hi = wy_ops;                      // [kt][128 x 64 B]: V rows
+            unsigned char* a_lo = wy_ops + 2 * kWyTileA;
+            unsigned char* b_hi = wy_ops + 4 * kWyTileA;       // [kt][256 x 64 B]: F rows
+            unsigned char* b_lo = b_hi + 2 * kWyTileB;
+            for (int nt = 0; nt < w_cnt; nt += kWyN) {
+                const int ncnt = min(kWyN, w_cnt - nt);
+                // B: the F rows of columns w_lo + nt .. (entries past the panel zero)
+                for (int e = t; e < kWyN * kSPanel; e += kSThreads) {
+                    const int r = e / kSPanel, c = e % kSPanel;
+                    const float x = (r < ncnt && c <= jj) ? ld(F + (int64_t)(w_lo + nt + r) * ldf + c) : 0.0f;
+                    put(b_hi + (c >> 4) * kWyTileB, b_lo + (c >> 4) * kWyTileB, r, c & 15, x);
                 }
-                __syncthreads();
-                // column splits: about four tasks per warp, of at least kSWyBatch columns each
-                const int cs = max(1, min(cn / kSWyBatch, (4 * kSWarps + nrc - 1) / nrc));
-                for (int task = w; task < nrc * cs; task += kSWarps) {
-                    const int rc = task % nrc, cq = task / nrc;
-                    const int i = je + rc * kWarp + lane;
-                    const bool row_ok = i < m;
-                    float vr[kSPanel];
+                for (int mt = 0; mt < nrow; mt += kWyM) {
+                    const int mcnt = min(kWyM, nrow - mt);
+                    // A: rows je + mt .. of the panel's reflectors (from the panel copy)
+                    for (int e = t; e < kWyM * kSPanel; e += kSThreads) {
+                        const int r = e / kSPanel, c = e % kSPanel;
+                        const float x = (r < mcnt && c <= jj) ? vpan[c * L.ldp + (je + mt + r - L.r0)] : 0.0f;
+                        put(a_hi + (c >> 4) * kWyTileA, a_lo + (c >> 4) * kWyTileA, r, c & 15, x);
+                    }
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic writes -> MMA reads
+                    tc::fence_before();
+                    __syncthreads();   // (also: the previous tile's accumulator reads are done)
+                    tc::fence_after();
+                    if (t == 0) {
 #pragma unroll
-                    for (int c = 0; c < kSPanel; ++c) vr[c] = (row_ok && c <= jj) ? vpan[c * L.ldp + (i - L.r0)] : 0.0f;
-                    const int q0 = cq * cn / cs, q1 = (cq + 1) * cn / cs;
-                    // kSWyBatch columns per L2 round trip: their W(i, l) loads go out together
-                    for (int qb = q0; qb < q1; qb += kSWyBatch) {
-                        float wv[kSWyBatch];
+                        for (int kt = 0; kt < 2; ++kt)
 #pragma unroll
-                        for (int u = 0; u < kSWyBatch; ++u)
-                            wv[u] = (row_ok && qb + u < q1) ? ld(W + (int64_t)(w_lo + cb + qb + u) * ldw + i) : 0.0f;
+                            for (int kk = 0; kk < 2; ++kk) {
+                                const unsigned o = kk * 32;   // 8 TF32 = 32 bytes along the swizzled row
+                                const unsigned ah = tc::su32(a_hi + kt * kWyTileA) + o,
+                                               al = tc::su32(a_lo + kt * kWyTileA) + o;
+                                const unsigned bh = tc::su32(b_hi + kt * kWyTileB) + o,
+                                               bl = tc::su32(b_lo + kt * kWyTileB) + o;
+                                tc::umma_tf32(wy_tmem, tc::sdesc_sw64(al), tc::sdesc_sw64(bh), idesc,
+                                              (kt | kk) ? 1u : 0u);
+                                tc::umma_tf32(wy_tmem, tc::sdesc_sw64(ah), tc::sdesc_sw64(bl), idesc, 1u);
+                                tc::umma_tf32(wy_tmem, tc::sdesc_sw64(ah), tc::sdesc_sw64(bh), idesc, 1u);
+                            }
+                        tc::umma_commit(&wy_bar);
+                    }
+                    int ok = 1;
+                    if (lane == 0) ok = tc::mb_wait(&wy_bar, wy_phase, &wy_abort, kWySpin) ? 1 : 0;
+                    ok = __shfl_sync(0xffffffffu, ok, 0);
+                    wy_phase ^= 1u;
+                    tc::fence_after();
+                    if (!ok) {
+                        if (t == 0) atomicOr(&st->status, kStatTimeout);
+                    } else {
+                        // epilogue: warp w reads TMEM lane quarter w % 4 (32 rows of W), the four warps
+                        // of a quarter take alternate 32-column chunks; lane = row, so each column's
+                        // read-modify-write is one coalesced 128-byte access per warp
+                        const int q4 = w % 4, part4 = w / 4;
+                        const int r = q4 * 32 + lane;   // A row: W row je + mt + r
+                        const bool row_ok = r < mcnt;
+                        float* wrow = W + (int64_t)(w_lo + nt) * ldw + je + mt + r;
+                        for (int c0 = part4 * 32; c0 < kWyN; c0 += 128) {
+                            uint32_t v[32];
+                            TMEM_LD_X32(wy_tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)c0, v);
+                            tc::tmem_wait_ld();
+                            if (c0 < ncnt) {
+                                float x[32];
 #pragma unroll
-                        for (int u = 0; u < kSWyBatch; ++u) {
-                            if (qb + u < q1) {
-                                const float4* f4 = reinterpret_cast<const float4*>(ftile + (qb + u) * kSPanel);
-                                float acc = 0.0f;
+                                for (int u = 0; u < 32; ++u)
+                                    x[u] = (row_ok && c0 + u < ncnt) ? ld(wrow + (int64_t)(c0 + u) * ldw) : 0.0f;
 #pragma unroll
-                                for (int e = 0; e < kSPanel / 4; ++e) {
-                                    const float4 f = f4[e];
-                                    acc = fmaf(vr[4 * e], f.x, acc);
-                                    acc = fmaf(vr[4 * e + 1], f.y, acc);
-                                    acc = fmaf(vr[4 * e + 2], f.z, acc);
-                                    acc = fmaf(vr[4 * e + 3], f.w, acc);
-                                }
-                                if (row_ok) W[(int64_t)(w_lo + cb + qb + u) * ldw + i] = wv[u] - acc;
+                                for (int u = 0; u < 32; ++u)
+                                    if (row_ok && c0 + u < ncnt) wrow[(int64_t)(c0 + u) * ldw] = x[u] - __uint_as_float(v[u]);
                             }
                         }
                     }
+                    tc::fence_before();
+                    __syncthreads();   // the operand tiles and the accumulator are free again
+                    tc::fence_after();
                 }
             }
             grid_sync(P.bar, epoch, st);   // the next panel reads the updated columns
         }
+    }
+    if (wy_on) {
+        // (after a wait that gave up, an MMA may still run: wait again, bounded, before the free)
+        if (t == 0 && wy_abort) {
+            unsigned long long spins = 0;
+            while (!tc::mb_test(&wy_bar, wy_phase ^ 1u) && ++spins < kWySpin) __nanosleep(64);
+        }
+        tc::fence_before();
+        __syncthreads();
+        tc::fence_after();
+        if (w == 0) tc::tmem_dealloc(wy_tmem, kWyN);
     }
 }
 
@@ -604,7 +684,7 @@ SLayout short_layout(int m, int j0) {
 }
 
 size_t short_bytes(const SLayout& L) {
-    return sizeof(float) * ((size_t)kSPanel * L.ldp + (L.len + 8) + L.len + 4 * kSPanel + (size_t)kSWyCols * kSPanel);
+    return sizeof(float) * ((size_t)kSPanel * L.ldp + (L.len + 8) + L.len + 4 * kSPanel) + 1024 + kWyBytes;
 }
 
 }  // namespace
