@@ -651,6 +651,9 @@ struct SideStream {
     std::mutex mu;
     cudaStream_t s2 = nullptr;
     cudaEvent_t fork = nullptr, join = nullptr;
+    // a second side stream for the split-K sums of the residual loop, with its events
+    cudaStream_t s3 = nullptr;
+    cudaEvent_t g2done = nullptr, reddone = nullptr;
     bool ok = false, tried = false;
 };
 static SideStream g_side[64];
@@ -666,7 +669,10 @@ static SideStream* side_stream(cudaStream_t s) {
         ss->tried = true;
         ss->ok = cudaStreamCreateWithFlags(&ss->s2, cudaStreamNonBlocking) == cudaSuccess &&
                  cudaEventCreateWithFlags(&ss->fork, cudaEventDisableTiming) == cudaSuccess &&
-                 cudaEventCreateWithFlags(&ss->join, cudaEventDisableTiming) == cudaSuccess;
+                 cudaEventCreateWithFlags(&ss->join, cudaEventDisableTiming) == cudaSuccess &&
+                 cudaStreamCreateWithFlags(&ss->s3, cudaStreamNonBlocking) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&ss->g2done, cudaEventDisableTiming) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&ss->reddone, cudaEventDisableTiming) == cudaSuccess;
     }
     if (!ss->ok) {
         ss->mu.unlock();
@@ -809,14 +815,26 @@ int refine_run(const float* A, int64_t m, int64_t n, int64_t lda, int k, const i
         e2.d = fp(L.Part);
         e2.ldd = k;
         e2.z_stride = (int64_t)nbb * k;
+        // (the previous block's sum must be done reading the slices before they are rewritten)
+        if (ss && b0 > 0 && cudaStreamWaitEvent(s, ss->reddone, 0) != cudaSuccess) return fail(ID_ECUDA);
         rc = gemm_tf32x3(TfOperand{fp(L.Rth), fp(L.Rtl), mp, nbb}, opCt, nbb, k, mp, L.splits, e2, gst, s);
         if (rc != ID_OK) return fail(rc);
-        k_reduce_split<<<grid_for((int64_t)nbb * kp), kRThreads, 0, s>>>(fp(L.Part), L.splits, nbb, k, kp,
-                                                                          fp(L.Hth) + b0 * kp, fp(L.Htl) + b0 * kp);
+        // the sum of the slices runs on the second side stream, beside the next block's
+        // residual product (which leaves SMs idle in its last wave)
+        cudaStream_t sr = s;
+        if (ss) {
+            if (cudaEventRecord(ss->g2done, s) != cudaSuccess || cudaStreamWaitEvent(ss->s3, ss->g2done, 0) != cudaSuccess)
+                return fail(ID_ECUDA);
+            sr = ss->s3;
+        }
+        k_reduce_split<<<grid_for((int64_t)nbb * kp), kRThreads, 0, sr>>>(fp(L.Part), L.splits, nbb, k, kp,
+                                                                           fp(L.Hth) + b0 * kp, fp(L.Htl) + b0 * kp);
+        if (ss && cudaEventRecord(ss->reddone, ss->s3) != cudaSuccess) return fail(ID_ECUDA);
     }
-    // join: the products below need U^{-1}
+    // join: the products below need U^{-1} and every block's sum
     if (ss) {
-        const bool jw = cudaStreamWaitEvent(s, ss->join, 0) == cudaSuccess;
+        const bool jw = cudaStreamWaitEvent(s, ss->join, 0) == cudaSuccess &&
+                        cudaStreamWaitEvent(s, ss->reddone, 0) == cudaSuccess;
         ss->mu.unlock();
         if (!jw) return ID_ECUDA;
     }
