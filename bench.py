@@ -504,40 +504,37 @@ def rid_rooflines(per, hbm_peak, peak_src):
 
 
 def rid_e2e(gbid, A, om, steps):
-    """IDs/s through the public call with host buffers: every step copies A and
-    Omega from pinned host memory, runs the randomized ID and copies J and Z back."""
+    """IDs/s through the public host-buffer entry point for a stream of IDs
+    (id_rid_pipe): every ID copies its A and Omega from pinned host memory and
+    its J, Z and status back; the copies of neighbouring IDs overlap the current
+    ID on the device. Timed on the host clock from the first submit until the
+    last ID's outputs are on the host (the copy streams are the pipe's own), so
+    the first ID's input copy, which nothing overlaps, is inside."""
+    import ctypes
+    import time
+
     import torch
 
     Ah = A.cpu().pin_memory()
     Oh = om.cpu().pin_memory()
-    Ad = torch.empty_like(A)
-    Od = torch.empty_like(om)
-    ws = gbid.rid_workspace(RM, RN, RL, RK, device=A.device)
-    J = torch.empty(RK, dtype=torch.int32, device=A.device)
-    Z = torch.empty(RK, RN, dtype=torch.float32, device=A.device)
     Jh = torch.empty(RK, dtype=torch.int32, pin_memory=True)
     Zh = torch.empty(RK, RN, dtype=torch.float32, pin_memory=True)
-
-    def step():
-        Ad.copy_(Ah, non_blocking=True)
-        Od.copy_(Oh, non_blocking=True)
-        gbid.id_decompose_randomized(Ad, Od, RK, workspace=ws, out=(J, Z), sync=False)
-        Jh.copy_(J, non_blocking=True)
-        Zh.copy_(Z, non_blocking=True)
-
-    step()
+    pipe = gbid.RandomizedPipeline(RM, RN, RL, RK, device=A.device)
+    for _ in range(2):   # warm-up: both slots once
+        pipe.submit(Ah, Oh, Jh, Zh)
+    pipe.synchronize()
     torch.cuda.synchronize()
-    s = torch.cuda.current_stream()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(s)
+    t0 = time.perf_counter()
     for _ in range(steps):
-        step()
-    e1.record(s)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / steps
+        pipe.submit(Ah, Oh, Jh, Zh)
+    infos = pipe.synchronize()
+    ms = (time.perf_counter() - t0) * 1e3 / steps
+    pipe.close()
+    if any(i["status"] != gbid.ID_OK for i in infos):
+        raise RuntimeError(f"pipelined ID status {[i['status_name'] for i in infos]}")
     h2d = Ah.numel() * 4 + Oh.numel() * 2
-    d2h = Jh.numel() * 4 + Zh.numel() * 4
-    del Ah, Oh, Ad, Od, ws
+    d2h = Jh.numel() * 4 + Zh.numel() * 4 + ctypes.sizeof(gbid.IdInfo)
+    del Ah, Oh
     return 1000.0 / ms, h2d, d2h
 
 
@@ -1136,7 +1133,7 @@ def run_gbid(args):
     kernels, dom = rid_rooflines(per, hbm_peak, peak_src)
     fl = rid_flops()
     eff = sum(fl.values()) / (mean_ms * 1e-3) / 1e12
-    e2e_v, h2d, d2h = rid_e2e(gbid, A, om, max(2, min(args.steps, 5)))
+    e2e_v, h2d, d2h = rid_e2e(gbid, A, om, max(3, min(2 * args.steps, 20)))
     e2e_v = aggregate_rate(max_over_ranks(1000.0 / e2e_v, world, dev), world)
     cpu = None
     if cpu_ok:

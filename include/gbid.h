@@ -257,6 +257,46 @@ int id_decompose_randomized(const void* A, id_dtype dtype, int64_t m, int64_t n,
                             int32_t* J, void* Z, int64_t ldz, void* work, size_t work_bytes, id_info* info,
                             void* stream);
 
+/* id_rid_pipe -- randomized IDs (Sec. 2.2) of a stream of HOST matrices of one
+ * size, for serving: consecutive IDs overlap, so that the host-to-device copy of
+ * ID i+1's inputs and the device-to-host copy of ID i-1's outputs run while ID i
+ * runs on the caller's stream. Each submitted ID is id_decompose_randomized on
+ * device copies of its inputs: the same J, Z and id_info, bit for bit.
+ *
+ * The pipe keeps two device slots (A, Omega, J, Z and the status of one ID each)
+ * and one randomized workspace, all carved from the caller's DEVICE buffer; it
+ * creates two streams (one per copy direction) and six events on the current
+ * device, its only resources. The copy into a slot waits for the compute of the
+ * ID that last used it; the compute of an ID waits for its inputs and for the
+ * copy-out of that slot's previous outputs.
+ *
+ * id_rid_pipe_workspace_size(m, n, l, k, opts): bytes of `work` (0 for sizes
+ *   id_decompose_randomized rejects).
+ * id_rid_pipe_create(&pipe, m, n, l, k, opts, work, work_bytes): work 256-byte
+ *   aligned, at least the size above; opts (may be NULL) is copied. Returns
+ *   ID_OK, ID_EINVAL, ID_ENOMEM (work too small) or ID_ECUDA.
+ * id_rid_pipe_submit(pipe, A_host, lda, Omega_host, ldo, J_host, Z_host, ldz,
+ *   info_host, stream): enqueues one ID and returns without waiting. A_host: m x n
+ *   FP32 row-major, lda >= n; Omega_host: l x m BF16 row-major, ldo >= m; J_host:
+ *   k int32; Z_host: k x n FP32 row-major, ldz >= n; info_host: an id_info that
+ *   receives the ID's status, or NULL. All host buffers should be pinned
+ *   (pageable ones make the copies synchronous); inputs must stay unchanged and
+ *   outputs unread until id_rid_pipe_sync returns. Consecutive submits must use
+ *   the same stream. Returns ID_OK, ID_EINVAL or ID_ECUDA (the ID's own status
+ *   arrives in *info_host).
+ * id_rid_pipe_sync(pipe): waits until every submitted ID's outputs are on the
+ *   host. Returns ID_OK or ID_ECUDA.
+ * id_rid_pipe_destroy(pipe): waits as id_rid_pipe_sync, then releases the
+ *   streams and events (the caller frees `work`). NULL is ignored. */
+typedef struct id_rid_pipe id_rid_pipe;
+size_t id_rid_pipe_workspace_size(int64_t m, int64_t n, int64_t l, int64_t k, const id_opts* opts);
+int id_rid_pipe_create(id_rid_pipe** pipe, int64_t m, int64_t n, int64_t l, int64_t k, const id_opts* opts,
+                       void* work, size_t work_bytes);
+int id_rid_pipe_submit(id_rid_pipe* pipe, const float* A_host, int64_t lda, const uint16_t* Omega_host, int64_t ldo,
+                       int32_t* J_host, float* Z_host, int64_t ldz, id_info* info_host, void* stream);
+int id_rid_pipe_sync(id_rid_pipe* pipe);
+void id_rid_pipe_destroy(id_rid_pipe* pipe);
+
 /* id_decompose_sampled -- the paper's randomized algorithm, Optim RID
  * (Sec. 2.2): sample p columns of A without replacement (the sample is an
  * input: the caller draws it; the paper takes p = k + floor(0.2 k)), run the

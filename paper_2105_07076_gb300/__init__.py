@@ -92,6 +92,11 @@ _SIG = {
     "id_rid_workspace_size": (ctypes.c_size_t, [_I64, _I64, _I64, _I64, _P]),
     "id_decompose_randomized": (ctypes.c_int, [_P, ctypes.c_int, _I64, _I64, _I64, _P, _I64, _I64, _I64, _P, _P, _P,
                                                _I64, _P, ctypes.c_size_t, _P, _P]),
+    "id_rid_pipe_workspace_size": (ctypes.c_size_t, [_I64, _I64, _I64, _I64, _P]),
+    "id_rid_pipe_create": (ctypes.c_int, [_P, _I64, _I64, _I64, _I64, _P, _P, ctypes.c_size_t]),
+    "id_rid_pipe_submit": (ctypes.c_int, [_P, _P, _I64, _P, _I64, _P, _P, _I64, _P, _P]),
+    "id_rid_pipe_sync": (ctypes.c_int, [_P]),
+    "id_rid_pipe_destroy": (None, [_P]),
     "id_batched_problem_workspace_size": (ctypes.c_size_t, [ctypes.c_int, _I64, _I64, _I64]),
     "id_decompose_batched": (ctypes.c_int, [_P, _I64, ctypes.c_int, _P, ctypes.c_size_t, _P, _P]),
     "id_batched_config_count": (ctypes.c_int, [ctypes.c_int]),
@@ -612,6 +617,75 @@ def read_info(workspace: Workspace) -> dict:
     if rc in _CALL_ERRORS:
         raise IdError(rc, "id_info_read")
     return info.as_dict()
+
+
+class RandomizedPipeline:
+    """Randomized IDs of a stream of HOST matrices of one size (id_rid_pipe): each
+    submit enqueues one ID and returns at once; the host-to-device copy of the next
+    ID's inputs and the copy-back of the previous ID's J and Z overlap the current
+    ID on the device. Each ID equals id_decompose_randomized on the same inputs.
+
+    Inputs: A (m x n float32, CPU, row-major), omega (l x m bfloat16, CPU); outputs:
+    J (k int32), Z (k x n float32), CPU tensors. Pinned host tensors keep the
+    copies asynchronous. Inputs must not change, nor outputs be read, until
+    synchronize() returns."""
+
+    def __init__(self, m: int, n: int, l: int, k: int, *, nb: int = 0, refine: bool = True, device="cuda"):
+        self.m, self.n, self.l, self.k = m, n, l, k
+        self._opts = _opts(nb, refine)
+        nbytes = int(lib().id_rid_pipe_workspace_size(m, n, l, k, ctypes.byref(self._opts)))
+        if nbytes == 0:
+            raise IdError(ID_EINVAL, "id_rid_pipe_workspace_size")
+        self.device = torch.device(device)
+        self.buf = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self._pipe = ctypes.c_void_p()
+        self._infos = []   # IdInfo structs the device writes into (kept alive until synchronize)
+        self._keep = []    # host tensors referenced by enqueued copies
+        with torch.cuda.device(self.device):
+            rc = lib().id_rid_pipe_create(ctypes.byref(self._pipe), m, n, l, k, ctypes.byref(self._opts),
+                                          self.buf.data_ptr(), nbytes)
+        if rc != ID_OK:
+            raise IdError(rc, "id_rid_pipe_create")
+
+    def submit(self, A: torch.Tensor, omega: torch.Tensor, J: torch.Tensor, Z: torch.Tensor) -> int:
+        """Enqueue one ID on the current stream; returns its index (for results())."""
+        for t, name, dt, shape in ((A, "A", torch.float32, (self.m, self.n)),
+                                   (omega, "omega", torch.bfloat16, (self.l, self.m)),
+                                   (J, "J", torch.int32, (self.k,)), (Z, "Z", torch.float32, (self.k, self.n))):
+            if t.is_cuda or t.dtype != dt or tuple(t.shape) != shape or t.stride(-1) != 1:
+                raise ValueError(f"{name} must be a CPU {dt} tensor of shape {shape} with unit last stride")
+        # the status lands in pinned memory (a copy into pageable memory would wait for the ID)
+        info = torch.zeros(ctypes.sizeof(IdInfo), dtype=torch.uint8, pin_memory=True)
+        with torch.cuda.device(self.device):
+            rc = lib().id_rid_pipe_submit(self._pipe, A.data_ptr(), A.stride(0), omega.data_ptr(), omega.stride(0),
+                                          J.data_ptr(), Z.data_ptr(), Z.stride(0), info.data_ptr(),
+                                          _stream(self.device))
+        if rc != ID_OK:
+            raise IdError(rc, "id_rid_pipe_submit")
+        self._infos.append(info)
+        self._keep.append((A, omega, J, Z))
+        return len(self._infos) - 1
+
+    def synchronize(self) -> list:
+        """Wait until every submitted ID's outputs are on the host; returns their info dicts."""
+        rc = lib().id_rid_pipe_sync(self._pipe)
+        if rc != ID_OK:
+            raise IdError(rc, "id_rid_pipe_sync")
+        out = [IdInfo.from_address(i.data_ptr()).as_dict() for i in self._infos]
+        self._infos, self._keep = [], []
+        return out
+
+    def close(self):
+        if self._pipe:
+            lib().id_rid_pipe_destroy(self._pipe)
+            self._pipe = ctypes.c_void_p()
+            self._infos, self._keep = [], []
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def id_decompose_host(A: torch.Tensor, k: int, *, nb: int = 0, engine: int = ENGINE_AUTO,

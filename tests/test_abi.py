@@ -374,6 +374,13 @@ int main(void) {
     CHECK(id_batched_config_get(ID_F32, 0, &c) == ID_OK && c.threads % 32 == 0);
     CHECK(id_decompose(NULL, ID_F64, 100, 300, 300, 20, NULL, NULL, NULL, 300, NULL, 0, NULL, NULL) == ID_EINVAL);
     CHECK(id_launch_count(ID_F64, 100, 300, 400, NULL) == -1);
+    CHECK(id_rid_pipe_workspace_size(256, 1024, 74, 64, NULL) > 2 * id_rid_workspace_size(256, 1024, 74, 64, NULL) / 2);
+    CHECK(id_rid_pipe_workspace_size(256, 1024, 74, 75, NULL) == 0);   /* k > l */
+    id_rid_pipe* pipe = NULL;
+    CHECK(id_rid_pipe_create(&pipe, 256, 1024, 74, 64, NULL, NULL, 0) == ID_EINVAL && pipe == NULL);
+    CHECK(id_rid_pipe_submit(NULL, NULL, 0, NULL, 0, NULL, NULL, 0, NULL, NULL) == ID_EINVAL);
+    CHECK(id_rid_pipe_sync(NULL) == ID_EINVAL);
+    id_rid_pipe_destroy(NULL);
     printf("ok\n");
     return 0;
 }
@@ -400,6 +407,28 @@ def test_header_is_plain_c_and_callable_from_c(gbid, tmp_path):
     assert r.returncode == 0, r.stderr
     r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
     assert r.returncode == 0 and r.stdout.strip() == "ok", r.stdout + r.stderr
+
+
+def test_rid_pipe_rules(gbid):
+    """The pipelined randomized entry points: sizes and argument errors, all
+    decided on the host before any CUDA call."""
+    L = gbid.lib()
+    one = L.id_rid_workspace_size(256, 1024, 74, 64, None)
+    both = L.id_rid_pipe_workspace_size(256, 1024, 74, 64, None)
+    # two slots of A (256 x 1024 FP32), Omega (74 x 256 BF16), J, Z (64 x 1024 FP32), status
+    assert both >= one + 2 * (256 * 1024 * 4 + 74 * 256 * 2 + 64 * 4 + 64 * 1024 * 4)
+    assert L.id_rid_pipe_workspace_size(256, 1024, 74, 75, None) == 0     # k > l
+    assert L.id_rid_workspace_size(2048, 4096, 700, 64, None) == 0          # l > 640
+    assert L.id_rid_pipe_workspace_size(2048, 4096, 700, 64, None) == 0
+    pipe = ctypes.c_void_p()
+    assert L.id_rid_pipe_create(ctypes.byref(pipe), 256, 1024, 74, 64, None, None, 0) == gbid.ID_EINVAL
+    assert L.id_rid_pipe_create(None, 256, 1024, 74, 64, None, 256, both) == gbid.ID_EINVAL
+    assert L.id_rid_pipe_create(ctypes.byref(pipe), 256, 1024, 74, 64, None, 255 * 256 + 8, both) == gbid.ID_EINVAL
+    assert L.id_rid_pipe_create(ctypes.byref(pipe), 256, 1024, 74, 64, None, 256 * 256, both - 1) == gbid.ID_ENOMEM
+    assert not pipe.value
+    assert L.id_rid_pipe_submit(None, None, 0, None, 0, None, None, 0, None, None) == gbid.ID_EINVAL
+    assert L.id_rid_pipe_sync(None) == gbid.ID_EINVAL
+    L.id_rid_pipe_destroy(None)
 
 
 def test_cpu_tensors_are_refused_not_computed(gbid):
