@@ -639,8 +639,10 @@ class RandomizedPipeline:
         self.device = torch.device(device)
         self.buf = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
         self._pipe = ctypes.c_void_p()
-        self._infos = []   # IdInfo structs the device writes into (kept alive until synchronize)
+        self._infos = []   # pinned status records the device writes into (kept alive until synchronize)
         self._keep = []    # host tensors referenced by enqueued copies
+        # pinned chunks of 64 status records, allocated ahead of the submits
+        self._pools = [torch.zeros(64, ctypes.sizeof(IdInfo), dtype=torch.uint8, pin_memory=True)]
         with torch.cuda.device(self.device):
             rc = lib().id_rid_pipe_create(ctypes.byref(self._pipe), m, n, l, k, ctypes.byref(self._opts),
                                           self.buf.data_ptr(), nbytes)
@@ -654,8 +656,13 @@ class RandomizedPipeline:
                                    (J, "J", torch.int32, (self.k,)), (Z, "Z", torch.float32, (self.k, self.n))):
             if t.is_cuda or t.dtype != dt or tuple(t.shape) != shape or t.stride(-1) != 1:
                 raise ValueError(f"{name} must be a CPU {dt} tensor of shape {shape} with unit last stride")
-        # the status lands in pinned memory (a copy into pageable memory would wait for the ID)
-        info = torch.zeros(ctypes.sizeof(IdInfo), dtype=torch.uint8, pin_memory=True)
+        # the status lands in pinned memory (a copy into pageable memory would wait for the ID); the
+        # records come from chunks allocated ahead, since pinning memory between submits can
+        # wait for the device
+        i = len(self._infos)
+        if i == 64 * len(self._pools):
+            self._pools.append(torch.zeros(64, ctypes.sizeof(IdInfo), dtype=torch.uint8, pin_memory=True))
+        info = self._pools[i // 64][i % 64]
         with torch.cuda.device(self.device):
             rc = lib().id_rid_pipe_submit(self._pipe, A.data_ptr(), A.stride(0), omega.data_ptr(), omega.stride(0),
                                           J.data_ptr(), Z.data_ptr(), Z.stride(0), info.data_ptr(),
@@ -673,13 +680,14 @@ class RandomizedPipeline:
             raise IdError(rc, "id_rid_pipe_sync")
         out = [IdInfo.from_address(i.data_ptr()).as_dict() for i in self._infos]
         self._infos, self._keep = [], []
+        del self._pools[1:]   # the first chunk serves the next round of submits
         return out
 
     def close(self):
         if self._pipe:
             lib().id_rid_pipe_destroy(self._pipe)
             self._pipe = ctypes.c_void_p()
-            self._infos, self._keep = [], []
+            self._infos, self._keep, self._pools = [], [], []
 
     def __del__(self):
         try:
