@@ -133,3 +133,19 @@ def test_headline_units_match_the_stated_figures():
     assert 2.0 * 16384 * 512 * (32768 - 512) == pytest.approx(5.4e11, rel=1e-2)
     assert bench.bytes_cpqr(522, 32768, 512, 4) == pytest.approx(17.9e9, rel=1e-2)
     assert bench.rid_oracle_rate(1.0) == pytest.approx(bench.RID_CPU_COLS / bench.RN)
+
+
+def test_roofline_is_the_longest_single_kernel():
+    """The line's roofline is the CPQR kernel's (one launch per ID), even when
+    the refinement stage, spread over many launches, takes longer; its achieved
+    figure is the CPQR's algorithmic bytes over that launch's time."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    per = {"cpqr": 7.5, "refine": 8.7, "sketch": 0.95}
+    out, dom = bench.rid_rooflines(per, 6774.0, "measured")
+    assert dom == "cpqr"
+    r = out["cpqr"]
+    assert r["achieved"] == bench.bytes_cpqr(bench.RL, bench.RN, bench.RK, 4) / 7.5e-3 / 1e9
+    assert abs(r["frac"] - r["achieved"] / 6774.0) < 1e-12 and r["unit"] == "GB/s"
+    assert set(out) == {"cpqr", "refine", "sketch"}
