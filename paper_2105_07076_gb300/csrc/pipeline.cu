@@ -174,6 +174,8 @@ int id_rid_pipe_submit(id_rid_pipe* p, const float* A_host, int64_t lda, const u
 
 int id_rid_pipe_sync(id_rid_pipe* p) {
     if (!p) return ID_EINVAL;
-    // every ID's copy-out waits for its compute, which waits for its copy-in
-    return cudaStreamSynchronize(p->d2h) == cudaSuccess ? ID_OK : ID_ECUDA;
+    // every ID's copy-out waits for its compute, which waits for its copy-in; the copy-in stream
+    // too, for a submit that failed after its inputs were enqueued
+    return cudaStreamSynchronize(p->h2d) == cudaSuccess && cudaStreamSynchronize(p->d2h) == cudaSuccess ? ID_OK
+                                                                                                        : ID_ECUDA;
 }
